@@ -1,0 +1,234 @@
+"""Oracle parameter preparation for RelRes-LJ, FP64, restated from Section 2.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Everything here follows the paper's notation:
+
+* FG atom types carry ``eps``/``sig``; cross terms by a mixing rule
+  (geometric in Section 2.3; Lorentz-Berthelot is the other usual rule).
+* The CG pair parameters come from the zero-order multipole sum rule, Eq. 4,
+  which for LJ becomes Eq. 13: with A_k = sum_{mu nu} eps_{mu nu} sig_{mu nu}^k
+  over the FG sites of the two groups, sig^CG = (A12/A6)^(1/6) and
+  eps^CG = A6^2/A12.  Eq. 15 is the per-site form under geometric mixing.
+* Eq. 14: a type pair gets eps^CG only when both types are hybrid sites.
+* Eq. 16-18: quartic smoothing polynomials f(delta) = sum gamma_m delta^m.
+  Eq. 17 switches an interaction off over [r-, r+]; Eq. 18 switches one on.
+* Eq. 19: the shift constants Gamma_{c-}, Gamma_{s+}, Gamma_{s-}.
+
+Readings of the paper taken here (each is pinned by a test):
+
+1. Eq. 18's gamma_{4+}: the printed sign of the u'' term is negative.  Solving
+   the five conditions of Eq. 8 gives +u''(r+)/(4 dr^2); only that value meets
+   f''(dr) = u''(r+), and the printed gamma_{0+} agrees only with it.  We use
+   the derived value.
+2. A smoothing zone of zero width (r- = r+, allowed in Section 2.5): the zone
+   is empty, so only f(0) matters; gamma_3 = gamma_4 = 0 there (Eq. 17/18 would
+   divide by zero).
+3. ``shift=False`` (the ``pair_modify shift no`` of Section 2.5) sets
+   Gamma_{c-} to zero, and Gamma_{s+}, Gamma_{s-} are then formed from Eq. 19
+   with that zero, so the energy stays continuous at r_{s-} and r_{s+} and jumps
+   only at r_{c+}.  Forces do not depend on any Gamma.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+MIX_GEOMETRIC = "geometric"
+MIX_LB = "lb"
+
+# Row layout of one type-pair record (must match ``oracle_pair`` in
+# relres_oracle.c, which is this package's own C part).
+ROW_FIELDS = (
+    ["eps_fg", "sig_fg", "eps_cg", "sig_cg", "rsm", "rsp", "rcm", "rcp"]
+    + [f"g_fg_m{m}" for m in range(5)]
+    + [f"g_cg_p{m}" for m in range(5)]
+    + [f"g_cg_m{m}" for m in range(5)]
+    + ["Gam_cm", "Gam_sp", "Gam_sm"]
+)
+ROW_LEN = len(ROW_FIELDS)  # 26
+
+
+def lj(r: float, eps: float, sig: float) -> tuple[float, float, float]:
+    """Eq. 11 / Eq. 12: u(r) = 4 eps [(sig/r)^12 - (sig/r)^6] and its first two
+    r-derivatives, written out analytically."""
+    s6 = (sig / r) ** 6
+    s12 = s6 * s6
+    u = 4.0 * eps * (s12 - s6)
+    du = 4.0 * eps * (-12.0 * s12 + 6.0 * s6) / r
+    d2u = 4.0 * eps * (156.0 * s12 - 42.0 * s6) / (r * r)
+    return u, du, d2u
+
+
+def mix_fg(eps, sig, rule: str = MIX_GEOMETRIC):
+    """FG cross parameters for every type pair.
+
+    Geometric (Section 2.3): eps_ab = sqrt(eps_a eps_b), sig_ab = sqrt(sig_a sig_b).
+    Lorentz-Berthelot: eps geometric, sig arithmetic mean.
+    """
+    eps = np.asarray(eps, dtype=np.float64)
+    sig = np.asarray(sig, dtype=np.float64)
+    E = np.sqrt(np.outer(eps, eps))
+    if rule == MIX_GEOMETRIC:
+        S = np.sqrt(np.outer(sig, sig))
+    elif rule == MIX_LB:
+        S = 0.5 * (sig[:, None] + sig[None, :])
+    else:
+        raise ValueError(f"unknown mixing rule {rule!r}")
+    return E, S
+
+
+def cg_pair_eq13(comp_i, comp_j, E, S) -> tuple[float, float]:
+    """Eq. 13: CG pair parameters of groups i and j.
+
+    ``comp_i[t]`` is the number of FG sites of type t in group i (the hybrid
+    site included); E, S are the mixed FG parameters.  Returns (eps^CG, sig^CG).
+    """
+    A6 = 0.0
+    A12 = 0.0
+    nt = len(comp_i)
+    for mu in range(nt):
+        for nu in range(nt):
+            mult = comp_i[mu] * comp_j[nu]
+            if mult == 0:
+                continue
+            A6 += mult * E[mu, nu] * S[mu, nu] ** 6
+            A12 += mult * E[mu, nu] * S[mu, nu] ** 12
+    if A6 <= 0.0 or A12 <= 0.0:
+        return 0.0, 0.0
+    sig_cg = (A12 ** (1.0 / 6.0)) / (A6 ** (1.0 / 6.0))
+    eps_cg = A6 * A6 / A12
+    return eps_cg, sig_cg
+
+
+def cg_site_eq15(eps_sites, sig_sites) -> tuple[float, float]:
+    """Eq. 15: per-site CG parameters of one group under geometric mixing.
+
+    ``eps_sites``/``sig_sites`` list the FG parameters of every site of the
+    group.  Returns (eps_l^CG, sig_l^CG).  Pair values then follow by the
+    geometric mean (Section 2.3).
+    """
+    b6 = sum(math.sqrt(e * s ** 6) for e, s in zip(eps_sites, sig_sites))
+    b12 = sum(math.sqrt(e * s ** 12) for e, s in zip(eps_sites, sig_sites))
+    sig_l = b12 ** (1.0 / 3.0) / b6 ** (1.0 / 3.0)
+    eps_l = b6 ** 4 / b12 ** 2
+    return eps_l, sig_l
+
+
+def cg_table_eq13(eps, sig, is_hybrid, group_comp, rule: str = MIX_GEOMETRIC):
+    """CG parameters for every type pair (Eq. 13 for the group pair, then Eq. 14).
+
+    ``group_comp[a]`` (length n_types) is the composition of the group whose
+    hybrid site has type a; it is ignored for ordinary types.  Pairs with an
+    ordinary type get eps^CG = 0 (Eq. 14) and sig^CG = 0.
+    """
+    nt = len(eps)
+    E, S = mix_fg(eps, sig, rule)
+    EC = np.zeros((nt, nt))
+    SC = np.zeros((nt, nt))
+    for a in range(nt):
+        for b in range(nt):
+            if is_hybrid[a] and is_hybrid[b]:
+                EC[a, b], SC[a, b] = cg_pair_eq13(group_comp[a], group_comp[b], E, S)
+    return EC, SC
+
+
+def switch_off(u: float, du: float, d2u: float, dr: float) -> np.ndarray:
+    """Eq. 17: coefficients of f_-(delta), which matches u, u', u'' at delta=0
+    and has zero slope and curvature at delta=dr (conditions Eq. 7)."""
+    g = np.zeros(5)
+    g[0] = u
+    g[1] = du
+    g[2] = 0.5 * d2u
+    if dr > 0.0:
+        g[3] = -du / dr ** 2 - 2.0 * d2u / (3.0 * dr)
+        g[4] = du / (2.0 * dr ** 3) + d2u / (4.0 * dr ** 2)
+    return g
+
+
+def switch_on(u: float, du: float, d2u: float, dr: float) -> np.ndarray:
+    """Eq. 18 (gamma_4 sign as derived from Eq. 8, reading 1 above): f_+(delta)
+    has zero slope and curvature at delta=0 and matches u, u', u'' at delta=dr."""
+    g = np.zeros(5)
+    g[0] = u - 0.5 * du * dr + d2u * dr ** 2 / 12.0
+    if dr > 0.0:
+        g[3] = du / dr ** 2 - d2u / (3.0 * dr)
+        g[4] = -du / (2.0 * dr ** 3) + d2u / (4.0 * dr ** 2)
+    return g
+
+
+def poly(g, delta: float) -> float:
+    """Eq. 16: f(delta) = sum_{m=0..4} gamma_m delta^m."""
+    return sum(g[m] * delta ** m for m in range(5))
+
+
+def pair_row(eps_fg, sig_fg, eps_cg, sig_cg, radii, shift: bool = True) -> np.ndarray:
+    """One type-pair record: LJ parameters, the four radii, the three smoothing
+    polynomials (Eq. 17, Eq. 18, Eq. 17) and the shifts (Eq. 19).
+
+    radii = (r_s-, r_s+, r_c-, r_c+) with r_s- <= r_s+ <= r_c- <= r_c+
+    (Section 2.5).
+    """
+    rsm, rsp, rcm, rcp = (float(x) for x in radii)
+    if not (0.0 < rsm <= rsp <= rcm <= rcp):
+        raise ValueError("radii must satisfy 0 < r_s- <= r_s+ <= r_c- <= r_c+")
+    d_s = rsp - rsm
+    d_c = rcp - rcm
+    # f_{s-}^{FG}: switches the FG interaction off over [r_s-, r_s+].
+    g_fg_m = switch_off(*lj(rsm, eps_fg, sig_fg), d_s) if eps_fg != 0.0 else np.zeros(5)
+    if eps_cg != 0.0:
+        # f_{s+}^{CG}: switches the CG interaction on over [r_s-, r_s+].
+        g_cg_p = switch_on(*lj(rsp, eps_cg, sig_cg), d_s)
+        # f_{c-}^{CG}: switches the CG interaction off over [r_c-, r_c+].
+        g_cg_m = switch_off(*lj(rcm, eps_cg, sig_cg), d_c)
+    else:
+        g_cg_p = np.zeros(5)
+        g_cg_m = np.zeros(5)
+    # Eq. 19 (Eq. 9 written with the polynomials).
+    gam_cm = poly(g_cg_m, d_c) if shift else 0.0
+    gam_sp = gam_cm + poly(g_fg_m, d_s)
+    gam_sm = gam_sp - g_cg_p[0]
+    row = np.concatenate((
+        [eps_fg, sig_fg, eps_cg, sig_cg, rsm, rsp, rcm, rcp],
+        g_fg_m, g_cg_p, g_cg_m,
+        [gam_cm, gam_sp, gam_sm],
+    )).astype(np.float64)
+    assert row.shape == (ROW_LEN,)
+    return row
+
+
+def pair_table(eps, sig, is_hybrid, radii, mixing: str = MIX_GEOMETRIC,
+               eps_cg=None, sig_cg=None, group_comp=None, shift: bool = True,
+               radii_pair=None) -> np.ndarray:
+    """Table of ``pair_row`` records for all n_types x n_types type pairs,
+    row-major (a * n_types + b).
+
+    CG parameters come either explicitly (``eps_cg``/``sig_cg`` per type pair,
+    like the ``pair_coeff`` of Section 2.5) or from Eq. 13 with ``group_comp``.
+    In both cases Eq. 14 zeroes eps^CG of every pair with an ordinary type.
+    ``radii_pair`` (n_types x n_types x 4) overrides the global radii per pair.
+    """
+    nt = len(eps)
+    E, S = mix_fg(eps, sig, mixing)
+    if eps_cg is None:
+        if group_comp is None:
+            EC = np.zeros((nt, nt))
+            SC = np.zeros((nt, nt))
+        else:
+            EC, SC = cg_table_eq13(eps, sig, is_hybrid, group_comp, mixing)
+    else:
+        EC = np.array(eps_cg, dtype=np.float64).reshape(nt, nt)
+        SC = np.array(sig_cg, dtype=np.float64).reshape(nt, nt)
+    tab = np.zeros((nt * nt, ROW_LEN))
+    for a in range(nt):
+        for b in range(nt):
+            ecg = EC[a, b] if (is_hybrid[a] and is_hybrid[b]) else 0.0
+            rr = radii if radii_pair is None else np.asarray(radii_pair)[a, b]
+            tab[a * nt + b] = pair_row(E[a, b], S[a, b], ecg, SC[a, b], rr, shift)
+    return tab
+
+
+def row_dict(row) -> dict:
+    """Name the fields of one record (for tests and reports)."""
+    return {k: float(v) for k, v in zip(ROW_FIELDS, row)}
