@@ -1,0 +1,410 @@
+"""Benchmark: RelRes vs FG-only Lennard-Jones MD on one GB300 (atom-steps/s).
+
+Workload: neopentane-like liquid, 200 000 molecules = 1 000 000 united atoms
+(central C hybrid + 4 CH3), 0.58 g/cm^3 (L = 345.7 A), RelRes radii r_s 6-7 A,
+r_c 13-14 A, CG parameters from the multipole sum rule, skin 2 A, FP32 pair
+terms with FP64 totals and integration, dt = 2 fs, CSVR thermostat at 260 K.
+A step is one full velocity-Verlet step: drift, rebuild check (and rebuild when
+an atom moved more than skin/2), RelRes pair forces over the FG and CG lists,
+bonded terms, kinetic energy and thermostat.
+
+The same system is then run as the plain FG reference (LJ smoothed to zero
+over [13, 14) A, no CG term) for the speedup; and the oracle (FP64, O(N^2)) is
+timed on a bounded sample of the same workload on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s RelRes vs FG-only LJ (same GB300, 1M atoms); pair-kernel % roofline"
+FALLBACK_HBM_GBS = 6800.0
+PAIR_SRC = os.path.join(ROOT, "paper_2104_10231_gb300", "csrc", "pair.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_fg_neopentane_1M.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-mol", type=int, default=200_000)
+    ap.add_argument("--equil", type=int, default=200, help="untimed equilibration steps")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-fg-only", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, n_atoms, box):
+    return {
+        "workload": (f"neopentane-like liquid, {args.n_mol} molecules ({n_atoms} atoms), "
+                     f"L={box:.2f} A, RelRes r_s 6-7 A / r_c 13-14 A, CG by Eq. 13 sum rule, "
+                     "skin 2 A, dt 2 fs, CSVR 260 K"),
+        "n_atoms": n_atoms,
+        "precision": "FP32 pair terms from exact fixed-point differences; FP64 totals, "
+                     "velocities; 64-bit fixed-point positions",
+        "l2": "inputs larger than L2 (neighbour lists ~0.5 GB, state 64 MB)",
+        "parallelism": "replicas only (one independent system per GPU)",
+        "seed": 2104,
+    }
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per FG pair-kernel launch from the committed ncu summary, if
+    it was taken on the current pair.cu (sha256 prefix recorded there)."""
+    try:
+        src_sha = hashlib.sha256(open(PAIR_SRC, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("pair_cu_sha256_16") != src_sha:
+            return None
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_md_timed(torch, R, ctx, pos, vel, steps, dt, t_target, seed):
+    """K steps of relres_step bracketed by CUDA events on the context stream."""
+    stream = ctx.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(steps, dt, pos, vel, t_target=t_target, tau_fs=100.0, seed=seed)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2104_10231_gb300 import relres as R
+    from paper_2104_10231_gb300 import systems as S
+    from paper_2104_10231_gb300.build import build_library
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        build_library()
+    if dist:
+        dist.barrier()
+    R.load()
+
+    s = S.neopentane(n_mol=args.n_mol, seed=2104 + rank, temperature=260.0)
+    n = s.n_atoms
+    dt, temp = 2.0, 260.0
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s), stream=stream)
+        pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+        vel = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+        ctx.build_neighbors(pos, s.box)
+        # untimed: relax the lattice start, then warm up
+        if args.equil:
+            ctx.step(args.equil, dt, pos, vel, t_target=temp, tau_fs=100.0, seed=7)
+        ctx.step(args.warmup, dt, pos, vel, t_target=temp, tau_fs=100.0, seed=8)
+        torch.cuda.synchronize()
+        st0 = ctx.stats()
+        ctx.set_timing(True)
+        if dist:
+            dist.barrier()
+        with ClockSampler(local) as clk:
+            secs = run_md_timed(torch, R, ctx, pos, vel, args.steps, dt, temp, 9)
+        st1 = ctx.stats()
+        tim = ctx.timings()
+        ctx.set_timing(False)
+        if dist:
+            t = torch.tensor([secs], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            secs = float(t.item())
+            dist.barrier()
+
+        # end to end through the C ABI with host buffers: per step, copy the
+        # state in from pinned host memory, one relres_step, copy state and
+        # thermo row out
+        hp = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+        hv = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+        hth = torch.empty((1, R.RELRES_THERMO_COLS), dtype=torch.float64).pin_memory()
+        hp.copy_(pos.cpu())
+        hv.copy_(vel.cpu())
+        dth = torch.zeros((1, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+        ke = max(1, args.e2e_steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            pos.copy_(hp, non_blocking=True)
+            vel.copy_(hv, non_blocking=True)
+            ctx.step(1, dt, pos, vel, t_target=temp, tau_fs=100.0, seed=10, thermo_every=1,
+                     d_thermo=dth)
+            hp.copy_(pos, non_blocking=True)
+            hv.copy_(vel, non_blocking=True)
+            hth.copy_(dth, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_secs = time.perf_counter() - t0
+        e2e_value = n * ke / e2e_secs
+
+    value = world * n * args.steps / secs
+    ms_step = secs / args.steps * 1e3
+
+    # FG-only reference on the same configuration
+    fg = None
+    if not args.no_fg_only:
+        sf = S.fg_only(s)
+        with torch.cuda.stream(stream):
+            ctxf = R.Context(R.params_for(sf, R.RELRES_PREC_FP32), R.topology_for(sf), stream=stream)
+            posf = pos.clone()
+            velf = vel.clone()
+            ctxf.build_neighbors(posf, s.box)
+            ctxf.step(args.warmup, dt, posf, velf, t_target=temp, tau_fs=100.0, seed=8)
+            torch.cuda.synchronize()
+            ctxf.set_timing(True)
+            if dist:
+                dist.barrier()
+            secs_f = run_md_timed(torch, R, ctxf, posf, velf, args.steps, dt, temp, 9)
+            timf = ctxf.timings()
+            stf = ctxf.stats()
+            if dist:
+                t = torch.tensor([secs_f], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                secs_f = float(t.item())
+            ctxf.close()
+        fg = {"value": world * n * args.steps / secs_f, "ms_per_step": secs_f / args.steps * 1e3,
+              "pair_fg_ms_per_launch": timf["pair_fg"][0] / max(1, timf["pair_fg"][1]),
+              "mean_list": stf["mean_fg"], "rebuilds": stf["n_builds"]}
+    ctx_stats = st1
+    ctx.close()
+
+    # roofline of the dominant kernel: the RelRes pair kernel over the FG list
+    fg_ms = tim["pair_fg"][0] / max(1, tim["pair_fg"][1])
+    entries = ctx_stats["mean_fg"] * n
+    alg_bytes = entries * 20.0 + n * 40.0  # 4 B index + 16 B gather per entry; per atom 16 B pos, 4 B count, 4 B slot map, 16 B force
+    achieved = alg_bytes / (fg_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(),
+                "peak_source": peak_kind + " (hbm_gbs, copy)", "kernel": "k_pair<float, FG list>",
+                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": fg_ms}
+    kernel_ms = {k: round(v[0] / max(1, v[1]), 5) for k, v in tim.items()}
+    kernel_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in tim.values())), 4) for k, v in tim.items()}
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "atom-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded neopentane-like liquid; the paper's systems are not available)",
+        "config": workload_config(args, n, float(s.box[0])),
+        "ns_per_day": dt * 1e-6 * (args.steps / secs) * 86400.0,
+        "fg_only": fg,
+        "speedup_vs_fg_only": (value / fg["value"]) if fg else None,
+        "roofline": roofline,
+        "kernel_ms_per_launch": kernel_ms,
+        "kernel_time_share": kernel_share,
+        "lists": {"mean_fg": ctx_stats["mean_fg"], "mean_cg": ctx_stats["mean_cg"],
+                  "cap_fg": ctx_stats["cap_fg"], "cap_cg": ctx_stats["cap_cg"],
+                  "rebuilds_in_timed_region": ctx_stats["n_builds"] - st0["n_builds"]},
+        "gpu_launches": ctx_stats["n_launches"] - st0["n_launches"],
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": "atom-steps/s", "h2d_bytes_per_step": 2 * 24 * n,
+                "d2h_bytes_per_step": 2 * 24 * n + 8 * R.RELRES_THERMO_COLS,
+                "steps": ke, "how": "relres_step(1) per step with H2D/D2H of positions+velocities"},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def _oracle_rows_rate(s, seconds, rng_seed=0):
+    """Oracle (FP64, all-pairs) force rows of the full system on all host
+    cores: rows/s = atom-steps/s of a full force evaluation."""
+    import numpy as np
+
+    from oracle import core as O
+
+    table = O.table_for(s)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(rng_seed)
+    probe = rng.choice(s.n_atoms, size=cores, replace=False)
+    t0 = time.perf_counter()
+    O.pair_forces_rows(s.pos, s.box, s.types, table, s.n_types, probe, s.excl, n_threads=cores)
+    dt_probe = time.perf_counter() - t0
+    n_rows = max(cores, int(cores * seconds / max(dt_probe, 1e-6)))
+    n_rows = min(n_rows, s.n_atoms)
+    rows = rng.choice(s.n_atoms, size=n_rows, replace=False)
+    t0 = time.perf_counter()
+    O.pair_forces_rows(s.pos, s.box, s.types, table, s.n_types, rows, s.excl, n_threads=cores)
+    el = time.perf_counter() - t0
+    return n_rows, el, cores
+
+
+def cpu_baseline(s, seconds):
+    n_rows, el, cores = _oracle_rows_rate(s, seconds)
+    return {"value": n_rows / el, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 all-pairs Eq. 20 force rows of {n_rows} random atoms of the "
+                      f"{s.n_atoms}-atom system ({el:.1f} s); one step needs all rows"}
+
+
+def reference(args):
+    """The oracle as the reference arm: each step is a bounded sample of force
+    rows of the same 1M-atom workload, on the host cores (rank 0 only)."""
+    import numpy as np
+
+    from oracle import core as O
+    from paper_2104_10231_gb300 import systems as S
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.core import build_oracle
+
+    build_oracle()
+    s = S.neopentane(n_mol=args.n_mol, seed=2104, temperature=260.0)
+    table = O.table_for(s)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(1)
+    rows_per_step = cores
+
+    def one():
+        rows = rng.choice(s.n_atoms, size=rows_per_step, replace=False)
+        O.pair_forces_rows(s.pos, s.box, s.types, table, s.n_types, rows, s.excl, n_threads=cores)
+
+    for _ in range(max(0, args.warmup)):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t0
+    value = rows_per_step * args.steps / el
+    print(json.dumps({
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "atom-steps/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded neopentane-like liquid)",
+        "config": workload_config(args, s.n_atoms, float(s.box[0])),
+        "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{rows_per_step} random full force rows per step of the "
+                                   f"{s.n_atoms}-atom system"},
+        "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference(a)
+    else:
+        ours(a)

@@ -1,0 +1,294 @@
+/*
+ * relres.h -- C ABI of librelres: GB300 (sm_103a) Relative Resolution
+ * Lennard-Jones molecular dynamics.
+ *
+ * Method: M. Chaimovich & A. Chaimovich, "Relative Resolution: A
+ * Computationally Efficient Implementation in LAMMPS", arXiv:2104.10231.
+ * Near atom pairs interact through fine-grained (FG) LJ, switched off over
+ * [r_s-, r_s+); pairs of hybrid sites (one per group of atoms) also interact
+ * through coarse-grained (CG) LJ, switched on over the same shell and off over
+ * [r_c-, r_c+).  The pair potential is Eq. 20 (Section 2.5), with the CG
+ * parameters of Eq. 13 (Section 2.3), the smoothing polynomials of Eq. 16-18
+ * (Section 2.4) and the shifts of Eq. 19.
+ *
+ * Conventions for every entry point
+ *  - Units: kcal/mol, Angstrom, fs, g/mol, K ("real" units).
+ *  - Pointers named d_* are CUDA device pointers owned by the caller; all
+ *    other pointers are host pointers, read during the call only (the context
+ *    copies what it keeps).  Positions and forces are row-major n_atoms x 3
+ *    doubles (x0 y0 z0 x1 ...), in the caller's atom order.
+ *  - Work is enqueued on the CUDA stream given to relres_create; calls return
+ *    after it is enqueued unless stated otherwise.  Calls that must inspect a
+ *    device status word (list overflow, rebuild, non-finite) synchronise that
+ *    stream.
+ *  - No call throws, traps or aborts.  Every call returns a relres_status;
+ *    relres_last_error() gives a message for the last failure of a context.
+ *  - A context is thread-compatible, not thread-safe: one host thread at a
+ *    time per context.
+ */
+#ifndef RELRES_H
+#define RELRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RELRES_MAX_TYPES 8
+#define RELRES_THERMO_COLS 10 /* E_fg E_cg E_bonded KE Wxx Wyy Wzz Wxy Wxz Wyz */
+#define RELRES_PAIR_FIELDS 26 /* see relres_prepare_table */
+
+typedef enum relres_status {
+  RELRES_OK = 0,
+  RELRES_ERR_ARG = 1,           /* invalid argument: sizes, NULL, radii order, eps/sigma range */
+  RELRES_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  RELRES_ERR_BOX = 3,           /* a cutoff does not fit the box (needs r_c+ < L/2 per axis) */
+  RELRES_ERR_LIST_OVERFLOW = 4, /* neighbour list still too small after automatic regrowth */
+  RELRES_ERR_NONFINITE = 5,     /* a non-finite position, force or energy */
+  RELRES_ERR_STATE = 6,         /* call order: e.g. compute before topology / neighbours */
+  RELRES_ERR_NOMEM = 7          /* device or host allocation failed */
+} relres_status;
+
+enum relres_mixing { RELRES_MIX_GEOMETRIC = 0, RELRES_MIX_LB = 1 };
+
+/* RELRES_PREC_FP64: every pair and bonded term in FP64 (small systems).
+ * RELRES_PREC_FP32: pair terms in FP32 from exact fixed-point coordinate
+ * differences; per-atom sums in FP32; energy/virial totals, velocities and
+ * positions in FP64 (64-bit fixed point for positions inside relres_step). */
+enum relres_precision { RELRES_PREC_FP64 = 0, RELRES_PREC_FP32 = 1 };
+
+typedef struct relres_ctx relres_ctx;
+
+/*
+ * Pair-style parameters (the pair_style / pair_coeff / pair_modify data of
+ * Section 2.5).
+ *   n_types        1..RELRES_MAX_TYPES atom types.
+ *   eps_fg, sig_fg [n_types] FG LJ parameters per type (Eq. 11); eps >= 0,
+ *                  sig > 0.
+ *   is_hybrid      [n_types] 1 if sites of this type are hybrid (carry the CG
+ *                  interaction of their group, Section 2.1), else 0.
+ *   mixing         FG cross terms: geometric (eps, sig geometric means, Section
+ *                  2.3) or Lorentz-Berthelot (sig arithmetic mean).
+ *   eps_cg, sig_cg [n_types*n_types] explicit CG pair parameters (row-major
+ *                  a*n_types+b), or NULL to derive them with Eq. 13.  Pairs
+ *                  with an ordinary type must have eps_cg == 0 (Eq. 14);
+ *                  otherwise RELRES_ERR_ARG.
+ *   group_comp     [n_types*n_types] used when eps_cg == NULL: row a lists how
+ *                  many FG sites of each type make up the group whose hybrid
+ *                  site has type a (the hybrid site included).  Eq. 13 then
+ *                  gives eps^CG and sig^CG of every hybrid type pair.  Rows of
+ *                  ordinary types are ignored.
+ *   r_si r_so r_ci r_co   the global radii r_s- <= r_s+ <= r_c- <= r_c+ (>0).
+ *                  r- == r+ removes a smoothing zone.
+ *   radii_pair     [n_types*n_types*4] per-pair override of the four radii
+ *                  (symmetric), or NULL.
+ *   shift          1: Eq. 19 in full (Gamma_{c-} = f_{c-}^{CG}(dr_c)); 0: the
+ *                  "pair_modify shift no" of Section 2.5, Gamma_{c-} = 0 (and
+ *                  Gamma_{s+}, Gamma_{s-} formed from Eq. 19 with that zero).
+ *   skin           Verlet-list skin (Angstrom, >= 0); lists are rebuilt when
+ *                  an atom has moved more than skin/2 since the last build.
+ *   precision      RELRES_PREC_FP64 or RELRES_PREC_FP32.
+ */
+typedef struct relres_params {
+  int n_types;
+  const double* eps_fg;
+  const double* sig_fg;
+  const int* is_hybrid;
+  int mixing;
+  const double* eps_cg;
+  const double* sig_cg;
+  const int* group_comp;
+  double r_si, r_so, r_ci, r_co;
+  const double* radii_pair;
+  int shift;
+  double skin;
+  int precision;
+} relres_params;
+
+/*
+ * Molecular topology (host arrays, copied).
+ *   type            [n_atoms] 0..n_types-1.
+ *   mass_by_type    [n_types] g/mol, > 0.
+ *   excl_offsets    [n_atoms+1], excl_index [excl_offsets[n_atoms]]: CSR lists
+ *                   of the partners of each atom whose pair interaction is
+ *                   removed (1-2, 1-3, ... as the force field wants); must be
+ *                   symmetric.  Both NULL: no exclusions.  Applied to the FG
+ *                   and the CG part alike.
+ *   bonds           [2*n_bonds] atom pairs, bond_type [n_bonds] into
+ *                   bond_k/bond_r0 [n_bond_types]: E = K (r - r0)^2.
+ *   angles          [3*n_angles] (i, vertex, k), angle_type into angle_k /
+ *                   angle_theta0 (radians): E = K (theta - theta0)^2.
+ *   dihedrals       [4*n_dihedrals], dihedral_type into dihedral_k
+ *                   [4*n_dihedral_types] = K1..K4 of the OPLS form
+ *                   E = 1/2 [K1(1+cos p) + K2(1-cos 2p) + K3(1+cos 3p) + K4(1-cos 4p)].
+ * Counts may be 0 with NULL arrays.
+ */
+typedef struct relres_topology {
+  int n_atoms;
+  const int* type;
+  const double* mass_by_type;
+  const int* excl_offsets;
+  const int* excl_index;
+  int n_bonds;
+  const int* bonds;
+  const int* bond_type;
+  int n_bond_types;
+  const double* bond_k;
+  const double* bond_r0;
+  int n_angles;
+  const int* angles;
+  const int* angle_type;
+  int n_angle_types;
+  const double* angle_k;
+  const double* angle_theta0;
+  int n_dihedrals;
+  const int* dihedrals;
+  const int* dihedral_type;
+  int n_dihedral_types;
+  const double* dihedral_k;
+} relres_topology;
+
+typedef struct relres_stats {
+  int n_atoms, n_hybrid;
+  int cap_fg, cap_cg;            /* list slots per atom / per hybrid */
+  int max_fg, max_cg;            /* longest list at the last build */
+  double mean_fg, mean_cg;       /* mean list length at the last build */
+  double list_radius_fg;         /* max r_s+ + skin */
+  double list_radius_cg;         /* max r_c+ + skin_cg (0 without CG pairs) */
+  double skin_cg;                /* CG skin after clamping to L/2 - r_c+ */
+  int grid_fg[3], grid_cg[3];    /* cells per axis */
+  long long n_builds;            /* list builds since create */
+  long long n_steps;             /* MD steps since create (also the thermostat counter) */
+  int has_cg;                    /* 1 if any hybrid pair has eps^CG > 0 */
+  long long n_launches;          /* CUDA kernels this context has launched */
+} relres_stats;
+
+/* Kernel classes of relres_get_timings. */
+enum relres_timing_class {
+  RELRES_T_DRIFT = 0,    /* kick + drift + sorted scatter + rebuild trigger */
+  RELRES_T_REBUILD = 1,  /* binning, scan, scatter, in-cell sort, pack */
+  RELRES_T_LISTS = 2,    /* FG and CG Verlet lists */
+  RELRES_T_PAIR_FG = 3,  /* RelRes pair kernel over the FG list */
+  RELRES_T_PAIR_CG = 4,  /* RelRes pair kernel over the CG list */
+  RELRES_T_FINISH = 5,   /* force sum + bonded terms + kinetic energy */
+  RELRES_T_THERMO = 6,   /* reductions + CSVR factor */
+  RELRES_T_NCLASS = 7
+};
+
+/*
+ * Host-only (no GPU needed): validate p and fill out[n_types*n_types*26]
+ * with the per-pair quantities of Section 2, in FP64, pair a*n_types+b:
+ *   eps_fg sig_fg eps_cg sig_cg r_s- r_s+ r_c- r_c+,
+ *   gamma_{m-}^{FG} m=0..4 (Eq. 17 at r_s-), gamma_{m+}^{CG} (Eq. 18 at r_s+,
+ *   gamma_4 with the sign that satisfies Eq. 8), gamma_{m-}^{CG} (Eq. 17 at
+ *   r_c-), Gamma_{c-} Gamma_{s+} Gamma_{s-} (Eq. 19).
+ * out_len is the capacity in doubles.  Errors: RELRES_ERR_ARG.
+ */
+relres_status relres_prepare_table(const relres_params* p, double* out, int out_len);
+
+/*
+ * Host-only: CG pair parameters of Eq. 13 for two groups given by FG site
+ * compositions comp_i/comp_j [n_types] over per-type eps/sig with the given
+ * mixing rule.  Writes *eps_cg, *sig_cg.  Errors: RELRES_ERR_ARG.
+ */
+relres_status relres_cg_params(int n_types, const double* eps_fg, const double* sig_fg,
+                               int mixing, const int* comp_i, const int* comp_j,
+                               double* eps_cg, double* sig_cg);
+
+/*
+ * Create a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  The context owns every
+ * internal device buffer and frees it in relres_destroy.
+ * Errors: RELRES_ERR_ARG (invalid parameters, as relres_prepare_table),
+ * RELRES_ERR_CUDA, RELRES_ERR_NOMEM.  *out is NULL on failure.
+ */
+relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda_stream);
+
+/* Set atoms, masses, exclusions and bonded terms (replaces earlier ones).
+ * Errors: RELRES_ERR_ARG (index out of range, asymmetric exclusions, type out
+ * of range), RELRES_ERR_NOMEM, RELRES_ERR_CUDA. */
+relres_status relres_set_topology(relres_ctx* ctx, const relres_topology* t);
+
+/*
+ * Bin atoms into cells and build both Verlet lists (the FG list over all
+ * atoms within max r_s+ + skin, the CG list over hybrid sites within max r_c+
+ * + skin_cg), with exclusions removed.  d_pos: [n_atoms*3] device doubles, any
+ * periodic image.  box: host double[3], orthorhombic edge lengths.
+ * Sets the box used by later calls.  Synchronises the stream.
+ * The CG skin is clamped to L/2 - r_c+ - 1e-6 when the box is small
+ * (relres_get_stats reports it).  Grows list capacity as needed.
+ * Errors: RELRES_ERR_STATE (no topology), RELRES_ERR_BOX (r_s+ + skin or r_c+
+ * not below L/2), RELRES_ERR_LIST_OVERFLOW, RELRES_ERR_NONFINITE, RELRES_ERR_CUDA.
+ */
+relres_status relres_build_neighbors(relres_ctx* ctx, const double* d_pos, const double box[3]);
+
+/*
+ * One force evaluation at d_pos [n_atoms*3] (device): RelRes pair terms
+ * (Eq. 20 over both lists) plus bonded terms.
+ *   d_forces [n_atoms*3] device, overwritten (kcal/mol/A).
+ *   d_energy [4] device or NULL: E_fg, E_cg, E_bonded, total, where E_fg + E_cg
+ *            is the RelRes pair energy of Eq. 3 split exactly into the part
+ *            on the FG list (r < r_s+) and the part on the CG list.
+ *   d_virial [6] device or NULL: pair virial W_ab = sum_{i<j} (r_i-r_j)_a
+ *            F_ij,b, order xx yy zz xy xz yz.
+ * Lists are rebuilt first if any atom moved more than skin/2 since the last
+ * build.  Synchronises the stream.
+ * Errors: RELRES_ERR_STATE (no lists yet), RELRES_ERR_LIST_OVERFLOW,
+ * RELRES_ERR_NONFINITE, RELRES_ERR_CUDA.
+ */
+relres_status relres_compute(relres_ctx* ctx, const double* d_pos, double* d_forces,
+                             double* d_energy, double* d_virial);
+
+/*
+ * n_steps of velocity Verlet (dt_fs) on d_pos/d_vel [n_atoms*3] (device,
+ * updated in place; positions are returned wrapped into [0, L)).  Velocities
+ * are A/fs.  Lists are rebuilt on the device whenever an atom has moved more
+ * than skin/2.  t_target > 0 applies the CSVR thermostat (Bussi, Donadio &
+ * Parrinello 2007) with time constant tau_fs after each step, N_f = 3N - 3,
+ * drawing its random numbers from splitmix64 keyed by seed and the context's
+ * step counter; t_target <= 0 is NVE.
+ *   thermo_every > 0 and d_thermo != NULL: after every thermo_every-th step,
+ *   row k of d_thermo [n_steps/thermo_every][RELRES_THERMO_COLS] receives
+ *   E_fg E_cg E_bonded KE Wxx Wyy Wzz Wxy Wxz Wyz at that step.
+ * Forces at the incoming positions are reused from the previous call when
+ * d_pos still holds the positions that call returned; otherwise recomputed.
+ * On an error the state is rolled back to the last completed block of steps
+ * (blocks of up to 100 steps) and the error is returned.
+ * Errors: RELRES_ERR_STATE, RELRES_ERR_LIST_OVERFLOW, RELRES_ERR_NONFINITE,
+ * RELRES_ERR_ARG, RELRES_ERR_CUDA.
+ */
+relres_status relres_step(relres_ctx* ctx, int n_steps, double dt_fs, double* d_pos,
+                          double* d_vel, double t_target, double tau_fs, uint64_t seed,
+                          int thermo_every, double* d_thermo);
+
+/* Set the step counter (thermostat random stream position), e.g. on resume. */
+relres_status relres_set_step_counter(relres_ctx* ctx, long long step);
+
+/* Statistics of the last build and counters (host struct). */
+relres_status relres_get_stats(relres_ctx* ctx, relres_stats* out);
+
+/*
+ * Kernel timing.  enable != 0 makes relres_compute and relres_step record a
+ * CUDA event pair on the context stream around every kernel class of
+ * relres_timing_class (gated rebuild kernels included, also when they find
+ * nothing to do) and accumulate the elapsed times; enable == 0 stops it.
+ * relres_set_timing always clears the totals.
+ * relres_get_timings writes, for the first n classes, the total milliseconds
+ * (ms[k]) and the number of timed launches (counts[k]; either may be NULL).
+ */
+relres_status relres_set_timing(relres_ctx* ctx, int enable);
+relres_status relres_get_timings(relres_ctx* ctx, double* ms, long long* counts, int n);
+
+/* Message for the last failure of ctx (owned by ctx; "" if none). */
+const char* relres_last_error(relres_ctx* ctx);
+
+/* Free everything the context owns.  NULL is a no-op. */
+void relres_destroy(relres_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RELRES_H */

@@ -48,6 +48,9 @@ def lib():
             L.oracle_pair_forces.argtypes = [C.c_int, dp, dp, ip, C.c_int, dp, ip, ip, dp, dp,
                                              dp, C.c_int]
             L.oracle_pair_forces.restype = C.c_int
+            L.oracle_pair_forces_rows.argtypes = [C.c_int, dp, dp, ip, C.c_int, dp, ip, ip,
+                                                  C.c_int, ip, dp, dp, C.c_int]
+            L.oracle_pair_forces_rows.restype = C.c_int
             L.oracle_bonded.argtypes = [C.c_int, dp, dp, C.c_int, ip, ip, dp, dp, C.c_int, ip,
                                         ip, dp, dp, C.c_int, ip, ip, dp, dp, dp]
             L.oracle_bonded.restype = C.c_int
@@ -104,6 +107,23 @@ def pair_forces(pos, box, types, table, n_types, excl=None, n_threads=0):
     lib().oracle_pair_forces(n, _dp(pos), _dp(box), _ip(types), n_types, _dp(table), _ip(eo),
                              _ip(ei), _dp(f), _dp(e), _dp(w), int(n_threads))
     return f, float(e[0]), w
+
+
+def pair_forces_rows(pos, box, types, table, n_types, rows, excl=None, n_threads=0):
+    """Eq. 20 forces (len(rows) x 3) and half pair energies of the listed atoms
+    against all atoms: the same sum as pair_forces, for a subset of rows."""
+    pos = _d(pos)
+    box = _d(box)
+    types = _i(types)
+    table = _d(table)
+    rows = _i(rows)
+    f = np.zeros((len(rows), 3))
+    e = np.zeros(len(rows))
+    eo, ei = (None, None) if excl is None else (_i(excl[0]), _i(excl[1]))
+    lib().oracle_pair_forces_rows(pos.shape[0], _dp(pos), _dp(box), _ip(types), n_types,
+                                  _dp(table), _ip(eo), _ip(ei), len(rows), _ip(rows), _dp(f),
+                                  _dp(e), int(n_threads))
+    return f, e
 
 
 class _Topo(C.Structure):

@@ -151,6 +151,43 @@ int oracle_pair_forces(int n, const double* pos, const double* box, const int* t
   return 0;
 }
 
+/*
+ * The same all-pairs sum restricted to the rows of `rows` (n_rows atoms):
+ * forces[3*k..] = F of atom rows[k] from every other non-excluded atom, and
+ * energy[k] = half of that atom's pair energies (so that the rows of all atoms
+ * would add up to the total).  Used for bounded samples of large systems.
+ */
+int oracle_pair_forces_rows(int n, const double* pos, const double* box, const int* type, int nt,
+                            const oracle_pair* table, const int* excl_off, const int* excl_idx,
+                            int n_rows, const int* rows, double* forces, double* energy,
+                            int n_threads) {
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int k = 0; k < n_rows; ++k) {
+    const int i = rows[k];
+    double fi[3] = {0, 0, 0}, ei = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i || is_excluded(excl_off, excl_idx, i, j)) continue;
+      double d[3];
+      for (int a = 0; a < 3; ++a) d[a] = min_image(pos[3 * i + a] - pos[3 * j + a], box[a]);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double u, du;
+      eq20(&table[type[i] * nt + type[j]], r, &u, &du);
+      if (u == 0.0 && du == 0.0) continue;
+      double s = -du / r;
+      for (int a = 0; a < 3; ++a) fi[a] += s * d[a];
+      ei += 0.5 * u;
+    }
+    for (int a = 0; a < 3; ++a) forces[3 * k + a] = fi[a];
+    if (energy) energy[k] = ei;
+  }
+  return 0;
+}
+
 /* ---------------------------------------------------------------- bonded */
 
 static void sub_mi(const double* pos, const double* box, int a, int b, double* d) {

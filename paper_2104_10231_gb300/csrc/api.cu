@@ -1,0 +1,690 @@
+// C ABI of librelres (include/relres.h): context life cycle, topology, list
+// builds, force evaluation and MD steps.  Host code only; kernels live in
+// neighbor.cu, pair.cu and md.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "relres_internal.h"
+
+using namespace relres;
+
+namespace {
+
+constexpr double kBoltz = 0.0019872042586408316;  // kcal/mol/K (R / 4184 J/kcal)
+constexpr int kBlockSteps = 100;                  // steps between host status checks
+
+relres_status fail(relres_ctx* c, relres_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(c, RELRES_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+int blocks(int n) { return std::max(1, (n + 255) / 256); }
+
+unsigned long long morton3(unsigned x, unsigned y, unsigned z) {
+  auto spread = [](unsigned v) {
+    unsigned long long r = 0;
+    for (int b = 0; b < 21; ++b) r |= (unsigned long long)((v >> b) & 1u) << (3 * b);
+    return r;
+  };
+  return spread(x) | (spread(y) << 1) | (spread(z) << 2);
+}
+
+// Cells per axis: the largest count whose cells are at least r_list wide.
+relres_status setup_grid(relres_ctx* c, Grid* g, double rlist) {
+  int n[3];
+  for (int d = 0; d < 3; ++d) n[d] = std::max(1, int(std::floor(c->box[d] / rlist)));
+  if (g->d_rank_of && n[0] == g->n[0] && n[1] == g->n[1] && n[2] == g->n[2]) return RELRES_OK;
+  const long long nc = (long long)n[0] * n[1] * n[2];
+  if (nc > (1ll << 28)) return fail(c, RELRES_ERR_ARG, "too many cells");
+  std::vector<std::pair<unsigned long long, int>> order;
+  order.reserve(size_t(nc));
+  for (int x = 0; x < n[0]; ++x)
+    for (int y = 0; y < n[1]; ++y)
+      for (int z = 0; z < n[2]; ++z) order.push_back({morton3(x, y, z), (x * n[1] + y) * n[2] + z});
+  std::sort(order.begin(), order.end());
+  std::vector<int> rank(static_cast<size_t>(nc));
+  for (size_t k = 0; k < order.size(); ++k) rank[size_t(order[k].second)] = int(k);
+  for (int d = 0; d < 3; ++d) g->n[d] = n[d];
+  g->ncell = int(nc);
+  CK(dalloc(&g->d_rank_of, size_t(nc)));
+  CK(dalloc(&g->d_start, size_t(nc) + 1));
+  CK(dalloc(&g->d_count, size_t(nc)));
+  CK(cudaMemcpy(g->d_rank_of, rank.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
+  CK(cudaMemset(g->d_count, 0, sizeof(int) * nc));
+  CK(cudaMemset(g->d_start, 0, sizeof(int) * (nc + 1)));
+  return RELRES_OK;
+}
+
+relres_status read_state(relres_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RELRES_OK;
+}
+
+int round_cap(double x, int limit) {
+  int v = int(std::ceil(x));
+  v = (v + 7) / 8 * 8;
+  return std::max(8, std::min(v, std::max(8, limit)));
+}
+
+relres_status alloc_lists(relres_ctx* c) {
+  CK(dalloc(&c->d_nbr_fg, size_t(c->cap_fg) * c->n));
+  if (c->has_cg && c->n_h > 0) CK(dalloc(&c->d_nbr_cg, size_t(c->cap_cg) * c->n_h));
+  return RELRES_OK;
+}
+
+// Rebuild both lists at the current fixed-point positions, growing capacity
+// until everything fits.
+relres_status host_rebuild(relres_ctx* c) {
+  CK(launch_flags_and(c, ~(unsigned)(F_REBUILD | F_OVERFLOW_FG | F_OVERFLOW_CG)));
+  CK(launch_rebuild(c, nullptr));
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    CK(launch_lists(c, nullptr));
+    relres_status s = read_state(c);
+    if (s != RELRES_OK) return s;
+    const DevState& h = *c->h_state;
+    const bool of = (h.flags & F_OVERFLOW_FG) != 0, oc = (h.flags & F_OVERFLOW_CG) != 0;
+    if (!of && !oc) {
+      c->last_max_fg = h.max_fg;
+      c->last_max_cg = h.max_cg;
+      c->last_mean_fg = c->n ? double(h.tot_fg) / c->n : 0.0;
+      c->last_mean_cg = c->n_h ? double(h.tot_cg) / c->n_h : 0.0;
+      c->have_lists = true;
+      c->n_builds += 1;
+      return RELRES_OK;
+    }
+    if (of) c->cap_fg = round_cap(h.max_fg * 1.2 + 8, c->n);
+    if (oc) c->cap_cg = round_cap(h.max_cg * 1.2 + 8, c->n_h);
+    s = alloc_lists(c);
+    if (s != RELRES_OK) return s;
+    CK(launch_flags_and(c, ~(unsigned)(F_OVERFLOW_FG | F_OVERFLOW_CG)));
+    // list statistics are reset by the scan of a full rebuild; reset here too
+    CK(cudaMemsetAsync(&c->d_state->max_fg, 0, 2 * sizeof(int), c->stream));
+    CK(cudaMemsetAsync(&c->d_state->tot_fg, 0, 2 * sizeof(unsigned long long), c->stream));
+  }
+  return fail(c, RELRES_ERR_LIST_OVERFLOW, "neighbour list overflow after regrowth");
+}
+
+// ---- kernel timing: event pairs around each kernel class, read after a sync
+cudaError_t tic(relres_ctx* c, int cls) {
+  while (c->ev_used + 2 > c->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    c->ev_pool.push_back(e);
+  }
+  relres_ctx::Mark m{cls, c->ev_pool[c->ev_used], c->ev_pool[c->ev_used + 1]};
+  c->ev_used += 2;
+  c->marks.push_back(m);
+  return cudaEventRecord(m.a, c->stream);
+}
+
+cudaError_t toc(relres_ctx* c) { return cudaEventRecord(c->marks.back().b, c->stream); }
+
+relres_status flush_timing(relres_ctx* c) {
+  for (const relres_ctx::Mark& m : c->marks) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, m.a, m.b));
+    c->t_ms[m.cls] += ms;
+    c->t_cnt[m.cls] += 1;
+  }
+  c->marks.clear();
+  c->ev_used = 0;
+  return RELRES_OK;
+}
+
+#define TIMED(cls, call)        \
+  do {                          \
+    if (c->timing) CK(tic(c, cls)); \
+    CK(call);                   \
+    if (c->timing) CK(toc(c));  \
+  } while (0)
+
+// Forces at the positions already converted into d_xfx (F_tot, FP64 copy optional).
+relres_status forces_now(relres_ctx* c, int ev_mode, double* d_forces, double* d_energy,
+                         double* d_virial) {
+  relres_status s = read_state(c);
+  if (s != RELRES_OK) return s;
+  if (c->h_state->flags & F_NONFINITE) {
+    CK(launch_flags_and(c, ~(unsigned)F_NONFINITE));
+    return fail(c, RELRES_ERR_NONFINITE, "non-finite position");
+  }
+  if (c->h_state->flags & F_REBUILD) {
+    s = host_rebuild(c);
+    if (s != RELRES_OK) return s;
+  }
+  TIMED(RELRES_T_PAIR_FG, launch_pairs(c, ev_mode, 1));
+  if (c->has_cg && c->n_h > 0) TIMED(RELRES_T_PAIR_CG, launch_pairs(c, ev_mode, 2));
+  TIMED(RELRES_T_FINISH, launch_finish(c, ev_mode, d_forces, false));
+  if (ev_mode == 1) TIMED(RELRES_T_THERMO, launch_reduce_out(c, d_energy, d_virial));
+  s = read_state(c);
+  if (s != RELRES_OK) return s;
+  s = flush_timing(c);
+  if (s != RELRES_OK) return s;
+  if (c->h_state->flags & F_NONFINITE) {
+    CK(launch_flags_and(c, ~(unsigned)F_NONFINITE));
+    c->forces_valid = false;
+    return fail(c, RELRES_ERR_NONFINITE, "non-finite force");
+  }
+  c->forces_valid = true;
+  return RELRES_OK;
+}
+
+size_t force_bytes(const relres_ctx* c) { return size_t(c->n) * (c->fp64 ? 24 : 16); }
+
+
+
+}  // namespace
+
+extern "C" {
+
+relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda_stream) {
+  if (!out) return RELRES_ERR_ARG;
+  *out = nullptr;
+  relres_ctx* c = new (std::nothrow) relres_ctx();
+  if (!c) return RELRES_ERR_NOMEM;
+  const std::string e = build_pair_records(p, &c->recs);
+  if (!e.empty()) {
+    delete c;
+    return RELRES_ERR_ARG;
+  }
+  c->prm = *p;
+  c->n_types = p->n_types;
+  c->eps_fg.assign(p->eps_fg, p->eps_fg + p->n_types);
+  c->sig_fg.assign(p->sig_fg, p->sig_fg + p->n_types);
+  c->is_hybrid.assign(p->is_hybrid, p->is_hybrid + p->n_types);
+  // keep no caller pointers
+  c->prm.eps_fg = c->eps_fg.data();
+  c->prm.sig_fg = c->sig_fg.data();
+  c->prm.is_hybrid = c->is_hybrid.data();
+  c->prm.eps_cg = c->prm.sig_cg = nullptr;
+  c->prm.group_comp = nullptr;
+  c->prm.radii_pair = nullptr;
+  c->fp64 = p->precision == RELRES_PREC_FP64;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  build_kernel_tables(c->recs, &c->tab_f, &c->tab_d);
+  for (const PairRecord& r : c->recs) {
+    c->rlist_fg_cut = std::max(c->rlist_fg_cut, r.rsp);
+    if (r.eps_cg > 0.0) {
+      c->has_cg = true;
+      c->rlist_cg_cut = std::max(c->rlist_cg_cut, r.rcp);
+    }
+  }
+  for (int t = 0; t < c->n_types; ++t)
+    if (c->has_cg && c->is_hybrid[t]) c->hyb_mask |= 1 << t;
+  const size_t tb = c->fp64 ? sizeof(PairTab<double>) * c->tab_d.size()
+                            : sizeof(PairTab<float>) * c->tab_f.size();
+  cudaError_t ce = cudaMalloc(&c->d_tab, tb);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpy(c->d_tab, c->fp64 ? static_cast<const void*>(c->tab_d.data())
+                                      : static_cast<const void*>(c->tab_f.data()),
+                    tb, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_state, sizeof(DevState));
+  if (ce == cudaSuccess) ce = cudaMemset(c->d_state, 0, sizeof(DevState));
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_snap_state, sizeof(DevState));
+  if (ce == cudaSuccess) ce = cudaMallocHost(&c->h_state, sizeof(DevState));
+  if (ce != cudaSuccess) {
+    relres_destroy(c);
+    return ce == cudaErrorMemoryAllocation ? RELRES_ERR_NOMEM : RELRES_ERR_CUDA;
+  }
+  std::memset(c->h_state, 0, sizeof(DevState));
+  *out = c;
+  return RELRES_OK;
+}
+
+relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
+  if (!c) return RELRES_ERR_ARG;
+  if (!t || t->n_atoms < 1 || !t->type || !t->mass_by_type)
+    return fail(c, RELRES_ERR_ARG, "topology needs n_atoms >= 1, type and mass_by_type");
+  const int n = t->n_atoms;
+  for (int k = 0; k < c->n_types; ++k)
+    if (!(t->mass_by_type[k] > 0.0) || !std::isfinite(t->mass_by_type[k]))
+      return fail(c, RELRES_ERR_ARG, "masses must be finite and > 0");
+  for (int i = 0; i < n; ++i)
+    if (t->type[i] < 0 || t->type[i] >= c->n_types) return fail(c, RELRES_ERR_ARG, "atom type out of range");
+  // exclusions
+  std::vector<int> eoff(size_t(n) + 1, 0), eidx;
+  if ((t->excl_offsets == nullptr) != (t->excl_index == nullptr))
+    return fail(c, RELRES_ERR_ARG, "excl_offsets and excl_index go together");
+  if (t->excl_offsets) {
+    if (t->excl_offsets[0] != 0) return fail(c, RELRES_ERR_ARG, "excl_offsets[0] must be 0");
+    for (int i = 0; i < n; ++i) {
+      if (t->excl_offsets[i + 1] < t->excl_offsets[i]) return fail(c, RELRES_ERR_ARG, "excl_offsets must be non-decreasing");
+      eoff[i + 1] = t->excl_offsets[i + 1];
+    }
+    eidx.assign(t->excl_index, t->excl_index + eoff[n]);
+    for (int i = 0; i < n; ++i)
+      for (int k = eoff[i]; k < eoff[i + 1]; ++k) {
+        const int j = eidx[k];
+        if (j < 0 || j >= n || j == i) return fail(c, RELRES_ERR_ARG, "exclusion index out of range");
+        bool sym = false;
+        for (int m = eoff[j]; m < eoff[j + 1]; ++m) sym |= eidx[m] == i;
+        if (!sym) return fail(c, RELRES_ERR_ARG, "exclusions must be symmetric");
+      }
+  }
+  // bonded terms and the per-atom incident lists
+  auto check_terms = [&](int count, const int* atoms, int width, const int* types, int ntypes) {
+    if (count == 0) return true;
+    if (!atoms || !types || ntypes < 1) return false;
+    for (int k = 0; k < count; ++k) {
+      if (types[k] < 0 || types[k] >= ntypes) return false;
+      for (int w = 0; w < width; ++w)
+        if (atoms[width * k + w] < 0 || atoms[width * k + w] >= n) return false;
+    }
+    return true;
+  };
+  if (t->n_bonds < 0 || t->n_angles < 0 || t->n_dihedrals < 0 ||
+      !check_terms(t->n_bonds, t->bonds, 2, t->bond_type, t->n_bond_types) ||
+      !check_terms(t->n_angles, t->angles, 3, t->angle_type, t->n_angle_types) ||
+      !check_terms(t->n_dihedrals, t->dihedrals, 4, t->dihedral_type, t->n_dihedral_types))
+    return fail(c, RELRES_ERR_ARG, "bonded term index or type out of range");
+  if ((t->n_bonds && (!t->bond_k || !t->bond_r0)) || (t->n_angles && (!t->angle_k || !t->angle_theta0)) ||
+      (t->n_dihedrals && !t->dihedral_k))
+    return fail(c, RELRES_ERR_ARG, "bonded parameters missing");
+  if (t->n_bonds + t->n_angles + t->n_dihedrals >= (1 << 28))
+    return fail(c, RELRES_ERR_ARG, "too many bonded terms");
+  std::vector<std::vector<int>> inc(static_cast<size_t>(n));
+  std::vector<int4> hb(size_t(std::max(1, t->n_bonds))), ha(size_t(std::max(1, t->n_angles))),
+      hd(size_t(std::max(1, t->n_dihedrals)));
+  std::vector<int> hdt(size_t(std::max(1, t->n_dihedrals)), 0);
+  for (int k = 0; k < t->n_bonds; ++k) {
+    hb[k] = make_int4(t->bonds[2 * k], t->bonds[2 * k + 1], t->bond_type[k], 0);
+    for (int r = 0; r < 2; ++r) inc[size_t(t->bonds[2 * k + r])].push_back((0 << 30) | (r << 28) | k);
+  }
+  for (int k = 0; k < t->n_angles; ++k) {
+    ha[k] = make_int4(t->angles[3 * k], t->angles[3 * k + 1], t->angles[3 * k + 2], t->angle_type[k]);
+    for (int r = 0; r < 3; ++r) inc[size_t(t->angles[3 * k + r])].push_back((1 << 30) | (r << 28) | k);
+  }
+  for (int k = 0; k < t->n_dihedrals; ++k) {
+    hd[k] = make_int4(t->dihedrals[4 * k], t->dihedrals[4 * k + 1], t->dihedrals[4 * k + 2],
+                      t->dihedrals[4 * k + 3]);
+    hdt[k] = t->dihedral_type[k];
+    for (int r = 0; r < 4; ++r) inc[size_t(t->dihedrals[4 * k + r])].push_back((2 << 30) | (r << 28) | k);
+  }
+  std::vector<int> ioff(size_t(n) + 1, 0), iall;
+  for (int i = 0; i < n; ++i) {
+    ioff[i + 1] = ioff[i] + int(inc[i].size());
+    iall.insert(iall.end(), inc[i].begin(), inc[i].end());
+  }
+  std::vector<double> bp(2 * size_t(std::max(1, t->n_bond_types)), 0.0),
+      ap(2 * size_t(std::max(1, t->n_angle_types)), 0.0), dp(4 * size_t(std::max(1, t->n_dihedral_types)), 0.0);
+  for (int k = 0; k < t->n_bond_types && t->n_bonds; ++k) {
+    bp[2 * k] = t->bond_k[k];
+    bp[2 * k + 1] = t->bond_r0[k];
+  }
+  for (int k = 0; k < t->n_angle_types && t->n_angles; ++k) {
+    ap[2 * k] = t->angle_k[k];
+    ap[2 * k + 1] = t->angle_theta0[k];
+  }
+  for (int k = 0; k < 4 * t->n_dihedral_types && t->n_dihedrals; ++k) dp[k] = t->dihedral_k[k];
+
+  c->n = n;
+  c->h_type.assign(t->type, t->type + n);
+  c->mass_by_type.assign(t->mass_by_type, t->mass_by_type + c->n_types);
+  c->n_h = 0;
+  std::vector<int> rank_cg(static_cast<size_t>(n), -1);
+  for (int i = 0; i < n; ++i)
+    if ((c->hyb_mask >> c->h_type[i]) & 1) ++c->n_h;
+  c->n_bonds = t->n_bonds;
+  c->n_angles = t->n_angles;
+  c->n_dih = t->n_dihedrals;
+  const int nh = std::max(1, c->n_h);
+  c->nb_fg = blocks(n);
+  c->nb_cg = blocks(nh);
+  c->nb_fin = blocks(n);
+  const size_t fb = size_t(n) * (c->fp64 ? 24 : 16);
+  CK(dalloc(&c->d_type, n));
+  CK(dalloc(&c->d_excl_off, size_t(n) + 1));
+  CK(dalloc(&c->d_excl_idx, std::max<size_t>(1, eidx.size())));
+  CK(dalloc(&c->d_bonds, hb.size()));
+  CK(dalloc(&c->d_angles, ha.size()));
+  CK(dalloc(&c->d_dihs, hd.size()));
+  CK(dalloc(&c->d_dih_type, hdt.size()));
+  CK(dalloc(&c->d_bond_par, bp.size()));
+  CK(dalloc(&c->d_angle_par, ap.size()));
+  CK(dalloc(&c->d_dih_par, dp.size()));
+  CK(dalloc(&c->d_inc_off, ioff.size()));
+  CK(dalloc(&c->d_inc, std::max<size_t>(1, iall.size())));
+  CK(dalloc(&c->d_xfx, 3 * size_t(n)));
+  CK(dalloc(&c->d_ref, size_t(n)));
+  CK(dalloc(&c->d_cell_fg, size_t(n)));
+  CK(dalloc(&c->d_cell_cg, size_t(n)));
+  CK(dalloc(&c->d_perm_fg, size_t(n)));
+  CK(dalloc(&c->d_rank_fg, size_t(n)));
+  CK(dalloc(&c->d_perm_cg, size_t(nh)));
+  CK(dalloc(&c->d_rank_cg, size_t(n)));
+  CK(dalloc(&c->d_pos_fg, size_t(n)));
+  CK(dalloc(&c->d_pos_cg, size_t(nh)));
+  if (c->fp64) {
+    CK(dalloc(&c->d_pos_fg64, size_t(n)));
+    CK(dalloc(&c->d_pos_cg64, size_t(nh)));
+  }
+  CK(dalloc(&c->d_cnt_fg, size_t(n)));
+  CK(dalloc(&c->d_cnt_cg, size_t(nh)));
+  CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_f_fg), fb));
+  CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_f_cg), fb));
+  CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_f_tot), fb));
+  CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_snap_f), fb));
+  CK(dalloc(&c->d_snap_x, 3 * size_t(n)));
+  CK(dalloc(&c->d_snap_v, 3 * size_t(n)));
+  CK(dalloc(&c->d_part_fg, size_t(c->nb_fg) * kNQ));
+  CK(dalloc(&c->d_part_cg, size_t(c->nb_cg) * kNQ));
+  CK(dalloc(&c->d_part_fin, size_t(c->nb_fin) * 2));
+  CK(cudaMemcpy(c->d_type, c->h_type.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_excl_off, eoff.data(), sizeof(int) * eoff.size(), cudaMemcpyHostToDevice));
+  if (!eidx.empty()) CK(cudaMemcpy(c->d_excl_idx, eidx.data(), sizeof(int) * eidx.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_bonds, hb.data(), sizeof(int4) * hb.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_angles, ha.data(), sizeof(int4) * ha.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_dihs, hd.data(), sizeof(int4) * hd.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_dih_type, hdt.data(), sizeof(int) * hdt.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_bond_par, bp.data(), sizeof(double) * bp.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_angle_par, ap.data(), sizeof(double) * ap.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_dih_par, dp.data(), sizeof(double) * dp.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_inc_off, ioff.data(), sizeof(int) * ioff.size(), cudaMemcpyHostToDevice));
+  if (!iall.empty()) CK(cudaMemcpy(c->d_inc, iall.data(), sizeof(int) * iall.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_rank_cg, rank_cg.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemset(c->d_f_cg, 0, fb));
+  c->have_topo = true;
+  c->have_lists = false;
+  c->forces_valid = false;
+  c->cap_fg = c->cap_cg = 0;
+  return RELRES_OK;
+}
+
+relres_status relres_build_neighbors(relres_ctx* c, const double* d_pos, const double box[3]) {
+  if (!c) return RELRES_ERR_ARG;
+  if (!c->have_topo) return fail(c, RELRES_ERR_STATE, "relres_set_topology first");
+  if (!d_pos || !box) return fail(c, RELRES_ERR_ARG, "d_pos and box are required");
+  for (int d = 0; d < 3; ++d)
+    if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(c, RELRES_ERR_ARG, "box edges must be finite and > 0");
+  const double lmin = std::min(box[0], std::min(box[1], box[2]));
+  const double rfg = c->rlist_fg_cut + c->prm.skin;
+  if (!(rfg < 0.5 * lmin)) return fail(c, RELRES_ERR_BOX, "r_s+ + skin must be below half the box");
+  double skin_cg = c->prm.skin;
+  if (c->has_cg) {
+    if (!(c->rlist_cg_cut < 0.5 * lmin)) return fail(c, RELRES_ERR_BOX, "r_c+ must be below half the box");
+    skin_cg = std::min(skin_cg, 0.5 * lmin - c->rlist_cg_cut - 1e-6);
+  }
+  const bool same_box = c->have_box && box[0] == c->box[0] && box[1] == c->box[1] && box[2] == c->box[2];
+  for (int d = 0; d < 3; ++d) c->box[d] = box[d];
+  c->skin_cg = skin_cg;
+  c->have_box = true;
+  if (!same_box) c->forces_valid = false;
+  relres_status s = setup_grid(c, &c->gfg, rfg);
+  if (s != RELRES_OK) return s;
+  if (c->has_cg && c->n_h > 0) {
+    s = setup_grid(c, &c->gcg, c->rlist_cg_cut + skin_cg);
+    if (s != RELRES_OK) return s;
+  }
+  if (c->cap_fg == 0) {
+    const double vol = box[0] * box[1] * box[2];
+    const double pi43 = 4.18879020478639;
+    c->cap_fg = round_cap(1.3 * pi43 * rfg * rfg * rfg * c->n / vol + 24, c->n);
+    const double rcg = c->rlist_cg_cut + skin_cg;
+    c->cap_cg = round_cap(1.3 * pi43 * rcg * rcg * rcg * c->n_h / vol + 24, c->n_h);
+    s = alloc_lists(c);
+    if (s != RELRES_OK) return s;
+  }
+  const bool had = c->have_lists;
+  c->have_lists = false;  // no sorted scatter before the first pack
+  CK(launch_convert(c, d_pos));
+  c->have_lists = had;
+  s = read_state(c);
+  if (s != RELRES_OK) return s;
+  if (c->h_state->flags & F_NONFINITE) {
+    CK(launch_flags_and(c, ~(unsigned)F_NONFINITE));
+    return fail(c, RELRES_ERR_NONFINITE, "non-finite position");
+  }
+  c->forces_valid = false;
+  return host_rebuild(c);
+}
+
+relres_status relres_compute(relres_ctx* c, const double* d_pos, double* d_forces, double* d_energy,
+                             double* d_virial) {
+  if (!c) return RELRES_ERR_ARG;
+  if (!c->have_lists) return fail(c, RELRES_ERR_STATE, "relres_build_neighbors first");
+  if (!d_pos || !d_forces) return fail(c, RELRES_ERR_ARG, "d_pos and d_forces are required");
+  CK(launch_convert(c, d_pos));
+  return forces_now(c, (d_energy || d_virial) ? 1 : 0, d_forces, d_energy, d_virial);
+}
+
+relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_pos, double* d_vel,
+                          double t_target, double tau_fs, uint64_t seed, int thermo_every,
+                          double* d_thermo) {
+  if (!c) return RELRES_ERR_ARG;
+  if (!c->have_lists) return fail(c, RELRES_ERR_STATE, "relres_build_neighbors first");
+  if (n_steps < 0 || !(dt_fs > 0.0) || !std::isfinite(dt_fs) || !d_pos || !d_vel || thermo_every < 0 ||
+      (t_target > 0.0 && !(tau_fs > 0.0)))
+    return fail(c, RELRES_ERR_ARG, "invalid step arguments");
+  if (n_steps == 0) return RELRES_OK;
+  if (c->n < 2 && t_target > 0.0) return fail(c, RELRES_ERR_ARG, "the thermostat needs at least 2 atoms");
+  StepParams sp{};
+  sp.dt = dt_fs;
+  sp.t_target = t_target;
+  sp.tau = tau_fs;
+  sp.n_f = 3.0 * c->n - 3.0;
+  sp.kt = 0.5 * sp.n_f * kBoltz * t_target;
+  sp.seed = seed;
+  sp.thermo_every = (d_thermo && thermo_every > 0) ? thermo_every : 0;
+  sp.thermo = sp.thermo_every ? d_thermo : nullptr;
+
+  // forces at the incoming positions: reuse when d_pos is what we returned last
+  CK(launch_flags_and(c, ~(unsigned)F_DIRTY));
+  CK(launch_check_cache(c, d_pos));
+  relres_status s = read_state(c);
+  if (s != RELRES_OK) return s;
+  if ((c->h_state->flags & F_DIRTY) || !c->forces_valid) {
+    CK(launch_convert(c, d_pos));
+    s = forces_now(c, 0, nullptr, nullptr, nullptr);
+    if (s != RELRES_OK) return s;
+  }
+  CK(launch_set_ab(c, 1.0, 1.0, 0));
+  const unsigned* gate = &c->d_state->flags;
+  const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
+  int done = 0, retries = 0;
+  while (done < n_steps) {
+    const int blk = std::min(kBlockSteps, n_steps - done);
+    CK(cudaMemcpyAsync(c->d_snap_x, c->d_xfx, xb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_snap_v, d_vel, vb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_snap_f, c->d_f_tot, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
+    for (int k = 0; k < blk; ++k) {
+      TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel));
+      TIMED(RELRES_T_REBUILD, launch_rebuild(c, gate));
+      TIMED(RELRES_T_LISTS, launch_lists(c, gate));
+      TIMED(RELRES_T_PAIR_FG, launch_pairs(c, 2, 1));
+      if (c->has_cg && c->n_h > 0) TIMED(RELRES_T_PAIR_CG, launch_pairs(c, 2, 2));
+      TIMED(RELRES_T_FINISH, launch_finish_step(c, sp, d_vel));
+      TIMED(RELRES_T_THERMO, launch_thermo(c, sp));
+    }
+    s = read_state(c);
+    if (s != RELRES_OK) return s;
+    s = flush_timing(c);
+    if (s != RELRES_OK) return s;
+    const unsigned fl = c->h_state->flags;
+    if (fl & (F_OVERFLOW_FG | F_OVERFLOW_CG | F_NONFINITE)) {
+      // roll back to the start of this block
+      CK(cudaMemcpyAsync(c->d_xfx, c->d_snap_x, xb, cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(d_vel, c->d_snap_v, vb, cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(c->d_f_tot, c->d_snap_f, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(c->d_state, c->d_snap_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
+      if (fl & F_NONFINITE) {
+        CK(launch_write_back(c, d_pos, d_vel, dt_fs));
+        CK(cudaStreamSynchronize(c->stream));
+        c->forces_valid = true;
+        return fail(c, RELRES_ERR_NONFINITE, "non-finite force during relres_step");
+      }
+      if (++retries > 8) return fail(c, RELRES_ERR_LIST_OVERFLOW, "repeated list overflow");
+      s = read_state(c);
+      if (s != RELRES_OK) return s;
+      if (fl & F_OVERFLOW_FG) c->cap_fg = round_cap(std::max(c->h_state->max_fg, c->cap_fg) * 1.25 + 8, c->n);
+      if (fl & F_OVERFLOW_CG) c->cap_cg = round_cap(std::max(c->h_state->max_cg, c->cap_cg) * 1.25 + 8, c->n_h);
+      s = alloc_lists(c);
+      if (s != RELRES_OK) return s;
+      s = host_rebuild(c);  // lists at the restored positions; F_tot is still theirs
+      if (s != RELRES_OK) return s;
+      continue;
+    }
+    done += blk;
+  }
+  CK(launch_write_back(c, d_pos, d_vel, dt_fs));
+  s = read_state(c);
+  if (s != RELRES_OK) return s;
+  c->n_steps += n_steps;
+  c->step_counter = c->h_state->step;
+  c->forces_valid = true;
+  return RELRES_OK;
+}
+
+relres_status relres_set_step_counter(relres_ctx* c, long long step) {
+  if (!c || step < 0) return RELRES_ERR_ARG;
+  relres_status s = read_state(c);
+  if (s != RELRES_OK) return s;
+  c->h_state->step = (unsigned long long)step;
+  CK(cudaMemcpyAsync(&c->d_state->step, &c->h_state->step, sizeof(unsigned long long),
+                     cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->step_counter = (unsigned long long)step;
+  return RELRES_OK;
+}
+
+relres_status relres_get_stats(relres_ctx* c, relres_stats* o) {
+  if (!c || !o) return RELRES_ERR_ARG;
+  relres_status s = read_state(c);
+  if (s != RELRES_OK) return s;
+  std::memset(o, 0, sizeof(*o));
+  o->n_atoms = c->n;
+  o->n_hybrid = c->n_h;
+  o->cap_fg = c->cap_fg;
+  o->cap_cg = c->cap_cg;
+  o->max_fg = c->h_state->max_fg;
+  o->max_cg = c->h_state->max_cg;
+  o->mean_fg = c->n ? double(c->h_state->tot_fg) / c->n : 0.0;
+  o->mean_cg = c->n_h ? double(c->h_state->tot_cg) / c->n_h : 0.0;
+  o->list_radius_fg = c->rlist_fg_cut + c->prm.skin;
+  o->list_radius_cg = c->has_cg ? c->rlist_cg_cut + c->skin_cg : 0.0;
+  o->skin_cg = c->skin_cg;
+  for (int d = 0; d < 3; ++d) {
+    o->grid_fg[d] = c->gfg.n[d];
+    o->grid_cg[d] = c->gcg.n[d];
+  }
+  o->n_builds = c->n_builds + c->h_state->n_builds;
+  o->n_steps = (long long)c->h_state->step;
+  o->has_cg = c->has_cg ? 1 : 0;
+  o->n_launches = c->n_launches;
+  return RELRES_OK;
+}
+
+relres_status relres_set_timing(relres_ctx* c, int enable) {
+  if (!c) return RELRES_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  relres_status s = flush_timing(c);
+  if (s != RELRES_OK) return s;
+  c->timing = enable != 0;
+  for (int k = 0; k < RELRES_T_NCLASS; ++k) {
+    c->t_ms[k] = 0.0;
+    c->t_cnt[k] = 0;
+  }
+  return RELRES_OK;
+}
+
+relres_status relres_get_timings(relres_ctx* c, double* ms, long long* counts, int n) {
+  if (!c || n < 0) return RELRES_ERR_ARG;
+  for (int k = 0; k < n && k < RELRES_T_NCLASS; ++k) {
+    if (ms) ms[k] = c->t_ms[k];
+    if (counts) counts[k] = c->t_cnt[k];
+  }
+  for (int k = RELRES_T_NCLASS; k < n; ++k) {
+    if (ms) ms[k] = 0.0;
+    if (counts) counts[k] = 0;
+  }
+  return RELRES_OK;
+}
+
+const char* relres_last_error(relres_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void relres_destroy(relres_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  dfree(c->d_tab);
+  dfree(c->d_cdt);
+  dfree(c->d_mass);
+  dfree(c->d_type);
+  dfree(c->d_excl_off);
+  dfree(c->d_excl_idx);
+  dfree(c->d_bonds);
+  dfree(c->d_angles);
+  dfree(c->d_dihs);
+  dfree(c->d_dih_type);
+  dfree(c->d_bond_par);
+  dfree(c->d_angle_par);
+  dfree(c->d_dih_par);
+  dfree(c->d_inc_off);
+  dfree(c->d_inc);
+  dfree(c->d_vir_dummy);
+  for (Grid* g : {&c->gfg, &c->gcg}) {
+    dfree(g->d_rank_of);
+    dfree(g->d_start);
+    dfree(g->d_count);
+  }
+  dfree(c->d_xfx);
+  dfree(c->d_ref);
+  dfree(c->d_cell_fg);
+  dfree(c->d_cell_cg);
+  dfree(c->d_perm_fg);
+  dfree(c->d_rank_fg);
+  dfree(c->d_perm_cg);
+  dfree(c->d_rank_cg);
+  dfree(c->d_pos_fg);
+  dfree(c->d_pos_cg);
+  dfree(c->d_pos_fg64);
+  dfree(c->d_pos_cg64);
+  dfree(c->d_nbr_fg);
+  dfree(c->d_cnt_fg);
+  dfree(c->d_nbr_cg);
+  dfree(c->d_cnt_cg);
+  dfree(c->d_f_fg);
+  dfree(c->d_f_cg);
+  dfree(c->d_f_tot);
+  dfree(c->d_part_fg);
+  dfree(c->d_part_cg);
+  dfree(c->d_part_fin);
+  dfree(c->d_state);
+  dfree(c->d_out_scratch);
+  dfree(c->d_snap_x);
+  dfree(c->d_snap_v);
+  dfree(c->d_snap_f);
+  dfree(c->d_snap_state);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Device helpers shared by the librelres kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "relres_internal.h"
+
+namespace relres {
+
+constexpr int kThreads = 256;
+
+// Positions are periodic 64-bit fixed point: u = frac(x / L) * 2^64.  Integer
+// differences wrap modulo 2^64, which is exactly the minimum image of an
+// orthorhombic box, and the upper 32 bits give the 32-bit form the FP32 pair
+// kernels read (resolution L / 2^32, 8e-8 A for L = 345 A).
+__device__ __forceinline__ unsigned long long to_fixed(double x, double inv_l) {
+  double s = x * inv_l;
+  s -= floor(s);
+  if (!(s < 1.0)) s = 0.0;
+  return __double2ull_rz(s * 18446744073709551616.0);
+}
+
+__device__ __forceinline__ double from_fixed(unsigned long long u, double l_2m64) {
+  return __ull2double_rn(u) * l_2m64;
+}
+
+__device__ __forceinline__ int hi32(unsigned long long u) { return int(unsigned(u >> 32)); }
+
+// wrapped difference a - b of 32-bit periodic coordinates
+__device__ __forceinline__ float dfix32(int a, int b, float scale) {
+  return float(int(unsigned(a) - unsigned(b))) * scale;
+}
+
+__device__ __forceinline__ double dfix64(long long a, long long b, double scale) {
+  return __ll2double_rn((long long)((unsigned long long)a - (unsigned long long)b)) * scale;
+}
+
+// cell coordinate of a 32-bit periodic coordinate on an n-cell axis: floor(frac * n)
+__device__ __forceinline__ int cell_of(int h, int n) {
+  return int((unsigned long long)unsigned(h) * unsigned(n) >> 32);
+}
+
+__device__ __forceinline__ bool gate_closed(const unsigned* gate) {
+  return gate != nullptr && (*(volatile const unsigned*)gate & F_REBUILD) == 0u;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NV values per thread; result valid in thread 0.
+// `sh` must hold (blockDim.x / 32) * NV elements.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[wid * NV + q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      T s = T(0);
+      for (int w = 0; w < nw; ++w) s += sh[w * NV + q];
+      v[q] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ long long to_fix_sum(double v) { return __double2ll_rn(v * kFix); }
+
+}  // namespace relres

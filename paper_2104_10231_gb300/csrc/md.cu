@@ -1,0 +1,672 @@
+// Positions, bonded terms, velocity Verlet, CSVR thermostat and reductions.
+//
+// State inside relres_step: positions are 64-bit periodic fixed point
+// (exact, wrap-free increments; resolution L/2^64), velocities FP64.  The two
+// half kicks of consecutive velocity-Verlet steps are merged: the velocity
+// array holds u = v(n - 1/2) during a call, and one drift kernel per step does
+//     u <- a u + b c F(n),   c = dt / (2 m),   x <- x + dt u
+// with (a, b) = (1, 1) on the first step of a call (u = v(0)) and
+// (alpha, alpha + 1) afterwards, alpha the CSVR factor of step n (1 for NVE):
+// that is v(n) = u + c F(n), v(n) <- alpha v(n), u <- v(n) + c F(n).  The
+// kinetic energy for the thermostat and the thermo output is formed from
+// u + c F(n) in the finish kernel.  At the end of a call the velocities are
+// returned as v(N) = a u + (b - 1) c F(N) and positions as doubles in [0, L).
+//
+// Bonded forces are computed per atom from the CSR list of the terms it takes
+// part in (each term recomputed by each of its atoms): no atomics, and each
+// term's energy is counted by its first atom.
+#include "common.cuh"
+
+namespace relres {
+
+constexpr double kFtm2v = 4.184e-4;        // (kcal/mol/A)/(g/mol) -> A/fs^2
+constexpr double kMvv2e = 1.0 / 4.184e-4;  // (g/mol)(A/fs)^2 -> kcal/mol
+
+struct TypeConsts {
+  double cdt[RELRES_MAX_TYPES];   // dt / (2 m) * ftm2v
+  double mass[RELRES_MAX_TYPES];  // g/mol
+};
+
+struct BoxConsts {
+  double inv_l[3];   // 1 / L
+  double l_2m64[3];  // L / 2^64
+  double dts[3];     // dt * 2^64 / L  (A/fs -> fixed-point units per step)
+  float s32[3];      // L / 2^32
+  double s64[3];     // L / 2^64
+};
+
+static BoxConsts box_consts(const relres_ctx* c, double dt) {
+  BoxConsts b;
+  for (int d = 0; d < 3; ++d) {
+    b.inv_l[d] = 1.0 / c->box[d];
+    b.l_2m64[d] = c->box[d] / 18446744073709551616.0;
+    b.dts[d] = dt * 18446744073709551616.0 / c->box[d];
+    b.s32[d] = float(c->box[d] / 4294967296.0);
+    b.s64[d] = c->box[d] / 18446744073709551616.0;
+  }
+  return b;
+}
+
+// ----------------------------------------------------------------- positions
+
+__device__ __forceinline__ void scatter_sorted(int i, int t, unsigned long long x, unsigned long long y,
+                                               unsigned long long z, const int* rank_fg,
+                                               const int* rank_cg, int4* pos_fg, int4* pos_cg,
+                                               Pos64* pos_fg64, Pos64* pos_cg64) {
+  const int4 h = make_int4(hi32(x), hi32(y), hi32(z), t);
+  const int sf = rank_fg[i];
+  pos_fg[sf] = h;
+  if (pos_fg64) pos_fg64[sf] = Pos64{(long long)x, (long long)y, (long long)z, t};
+  if (rank_cg) {
+    const int sc = rank_cg[i];
+    if (sc >= 0) {
+      pos_cg[sc] = h;
+      if (pos_cg64) pos_cg64[sc] = Pos64{(long long)x, (long long)y, (long long)z, t};
+    }
+  }
+}
+
+__device__ __forceinline__ bool moved_beyond(const int4& ref, unsigned long long x, unsigned long long y,
+                                             unsigned long long z, const BoxConsts& b, float thr2) {
+  const float dx = dfix32(hi32(x), ref.x, b.s32[0]);
+  const float dy = dfix32(hi32(y), ref.y, b.s32[1]);
+  const float dz = dfix32(hi32(z), ref.z, b.s32[2]);
+  return dx * dx + dy * dy + dz * dz > thr2;
+}
+
+__global__ void k_convert(int n, const double* __restrict__ pos, const int* __restrict__ type,
+                          unsigned long long* __restrict__ xfx, BoxConsts b, bool have_lists,
+                          const int* rank_fg, const int* rank_cg, int4* pos_fg, int4* pos_cg,
+                          Pos64* pos_fg64, Pos64* pos_cg64, const int4* ref, float thr2,
+                          DevState* st) {
+  bool rebuild = false, bad = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned long long u[3];
+    for (int d = 0; d < 3; ++d) {
+      const double x = pos[3 * i + d];
+      bad |= !isfinite(x);
+      u[d] = to_fixed(x, b.inv_l[d]);
+      xfx[3 * i + d] = u[d];
+    }
+    if (have_lists) {
+      scatter_sorted(i, type[i], u[0], u[1], u[2], rank_fg, rank_cg, pos_fg, pos_cg, pos_fg64, pos_cg64);
+      rebuild |= moved_beyond(ref[i], u[0], u[1], u[2], b, thr2);
+    }
+  }
+  if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&st->flags, F_REBUILD);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, F_NONFINITE);
+}
+
+__global__ void k_check_cache(int n, const double* __restrict__ pos,
+                              const unsigned long long* __restrict__ xfx, BoxConsts b, DevState* st) {
+  bool dirty = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      double x = from_fixed(xfx[3 * i + d], b.l_2m64[d]);
+      if (x >= 1.0 / b.inv_l[d]) x = 0.0;
+      dirty |= __double_as_longlong(x) != __double_as_longlong(pos[3 * i + d]);
+    }
+  if (__syncthreads_or(dirty) && threadIdx.x == 0) atomicOr(&st->flags, F_DIRTY);
+}
+
+// ----------------------------------------------------------------- bonded
+
+struct BondedArgs {
+  const int* inc_off;
+  const int* inc;
+  const int4* bonds;
+  const int4* angles;
+  const int4* dihs;
+  const int* dih_type;
+  const double* bond_par;   // k, r0
+  const double* angle_par;  // k, theta0
+  const double* dih_par;    // K1..K4
+};
+
+template <typename R>
+__device__ __forceinline__ void dvec(const unsigned long long* x, int a, int b, const BoxConsts& bc, R d[3]);
+
+template <>
+__device__ __forceinline__ void dvec<float>(const unsigned long long* x, int a, int b,
+                                            const BoxConsts& bc, float d[3]) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) d[q] = dfix32(hi32(x[3 * a + q]), hi32(x[3 * b + q]), bc.s32[q]);
+}
+template <>
+__device__ __forceinline__ void dvec<double>(const unsigned long long* x, int a, int b,
+                                             const BoxConsts& bc, double d[3]) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) d[q] = dfix64((long long)x[3 * a + q], (long long)x[3 * b + q], bc.s64[q]);
+}
+
+template <typename R>
+__device__ __forceinline__ R dot3(const R a[3], const R b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+template <typename R>
+__device__ __forceinline__ void cross3(const R a[3], const R b[3], R c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Force on the atom playing `role` in term `item`; adds the term energy when
+// role == 0.
+template <typename R>
+__device__ void bonded_term(const BondedArgs& B, const unsigned long long* xfx, const BoxConsts& bc,
+                            int item, R f[3], R& e) {
+  const int kind = (item >> 30) & 3, role = (item >> 28) & 3, t = item & 0x0fffffff;
+  if (kind == 0) {
+    const int4 bd = B.bonds[t];
+    R d[3];
+    dvec<R>(xfx, bd.x, bd.y, bc, d);
+    const R r = sqrt(dot3(d, d));
+    const R k = R(B.bond_par[2 * bd.z]), r0 = R(B.bond_par[2 * bd.z + 1]);
+    const R g = R(-2) * k * (r - r0) / r;  // force on bd.x along d
+    const R sgn = role == 0 ? R(1) : R(-1);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) f[q] += sgn * g * d[q];
+    if (role == 0) e += k * (r - r0) * (r - r0);
+  } else if (kind == 1) {
+    const int4 an = B.angles[t];
+    R r1[3], r2[3];
+    dvec<R>(xfx, an.x, an.y, bc, r1);
+    dvec<R>(xfx, an.z, an.y, bc, r2);
+    const R n1 = sqrt(dot3(r1, r1)), n2 = sqrt(dot3(r2, r2));
+    R c = dot3(r1, r2) / (n1 * n2);
+    c = c > R(1) ? R(1) : (c < R(-1) ? R(-1) : c);
+    const R th = acos(c);
+    R s = sqrt(R(1) - c * c);
+    if (s < R(1e-6)) s = R(1e-6);
+    const R k = R(B.angle_par[2 * an.w]), t0 = R(B.angle_par[2 * an.w + 1]);
+    const R pref = R(2) * k * (th - t0) / s;
+    R fa[3], fb[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      fa[q] = pref * (r2[q] / (n1 * n2) - c * r1[q] / (n1 * n1));
+      fb[q] = pref * (r1[q] / (n1 * n2) - c * r2[q] / (n2 * n2));
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) f[q] += role == 0 ? fa[q] : (role == 2 ? fb[q] : -(fa[q] + fb[q]));
+    if (role == 0) e += k * (th - t0) * (th - t0);
+  } else {
+    const int4 dh = B.dihs[t];
+    const double* K = B.dih_par + 4 * B.dih_type[t];
+    R b1[3], b2[3], b3[3], m1[3], m2[3];
+    dvec<R>(xfx, dh.y, dh.x, bc, b1);
+    dvec<R>(xfx, dh.z, dh.y, bc, b2);
+    dvec<R>(xfx, dh.w, dh.z, bc, b3);
+    cross3(b1, b2, m1);
+    cross3(b2, b3, m2);
+    const R nb2 = sqrt(dot3(b2, b2));
+    const R phi = atan2(nb2 * dot3(b1, m2), dot3(m1, m2));
+    const R k1 = R(K[0]), k2 = R(K[1]), k3 = R(K[2]), k4 = R(K[3]);
+    const R dE = R(0.5) * (-k1 * sin(phi) + R(2) * k2 * sin(R(2) * phi) - R(3) * k3 * sin(R(3) * phi) +
+                           R(4) * k4 * sin(R(4) * phi));
+    const R mm1 = dot3(m1, m1), mm2 = dot3(m2, m2);
+    const R p12 = dot3(b1, b2), p32 = dot3(b3, b2);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      R g;
+      if (role == 0)
+        g = -nb2 / mm1 * m1[q];
+      else if (role == 3)
+        g = nb2 / mm2 * m2[q];
+      else if (role == 1)
+        g = nb2 / mm1 * m1[q] + p12 / (mm1 * nb2) * m1[q] + p32 / (mm2 * nb2) * m2[q];
+      else
+        g = -nb2 / mm2 * m2[q] - p12 / (mm1 * nb2) * m1[q] - p32 / (mm2 * nb2) * m2[q];
+      f[q] -= dE * g;
+    }
+    if (role == 0)
+      e += R(0.5) * (k1 * (R(1) + cos(phi)) + k2 * (R(1) - cos(R(2) * phi)) +
+                     k3 * (R(1) + cos(R(3) * phi)) + k4 * (R(1) - cos(R(4) * phi)));
+  }
+}
+
+// ----------------------------------------------------------------- finish
+
+template <typename R>
+using ForceT = typename std::conditional<std::is_same<R, float>::value, float4, double>::type;
+
+__device__ __forceinline__ void load_force(const float4* f, int i, float v[3]) {
+  const float4 q = f[i];
+  v[0] = q.x;
+  v[1] = q.y;
+  v[2] = q.z;
+}
+__device__ __forceinline__ void load_force(const double* f, int i, double v[3]) {
+  v[0] = f[3 * i];
+  v[1] = f[3 * i + 1];
+  v[2] = f[3 * i + 2];
+}
+__device__ __forceinline__ void save_force(float4* f, int i, const float v[3]) {
+  f[i] = make_float4(v[0], v[1], v[2], 0.f);
+}
+__device__ __forceinline__ void save_force(double* f, int i, const double v[3]) {
+  f[3 * i] = v[0];
+  f[3 * i + 1] = v[1];
+  f[3 * i + 2] = v[2];
+}
+
+template <typename R>
+struct FinishArgs {
+  int n;
+  const ForceT<R>* f_fg;
+  const ForceT<R>* f_cg;  // null without CG
+  const int* type;
+  int hyb_mask;
+  BondedArgs B;
+  const unsigned long long* xfx;
+  BoxConsts bc;
+  const double* vel;  // u (half-step velocities) for the kinetic energy, or null
+  TypeConsts tc;
+  ForceT<R>* f_tot;
+  double* f_out;      // optional FP64 copy in caller order
+  long long* partial; // [gridDim.x][2]: KE, E_bonded
+  DevState* st;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mode) {
+  const bool ev = ev_mode == 1 || (ev_mode == 2 && a.st->ev);
+  R acc[2] = {R(0), R(0)};
+  bool bad = false;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) {
+    const int t = a.type[i];
+    R f[3];
+    load_force(a.f_fg, i, f);
+    if (a.f_cg && ((a.hyb_mask >> t) & 1)) {
+      R g[3];
+      load_force(a.f_cg, i, g);
+      f[0] += g[0];
+      f[1] += g[1];
+      f[2] += g[2];
+    }
+    R eb = R(0);
+    for (int k = a.B.inc_off[i]; k < a.B.inc_off[i + 1]; ++k)
+      bonded_term<R>(a.B, a.xfx, a.bc, a.B.inc[k], f, eb);
+    bad = !(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]));
+    save_force(a.f_tot, i, f);
+    if (a.f_out) {
+      a.f_out[3 * i] = double(f[0]);
+      a.f_out[3 * i + 1] = double(f[1]);
+      a.f_out[3 * i + 2] = double(f[2]);
+    }
+    if (a.vel) {
+      const R c = R(a.tc.cdt[t]);
+      R v2 = R(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const R v = R(a.vel[3 * i + q]) + c * f[q];
+        v2 += v * v;
+      }
+      acc[0] = R(0.5 * a.tc.mass[t] * kMvv2e) * v2;
+    }
+    if (ev) acc[1] = eb;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&a.st->flags, F_NONFINITE);
+  __shared__ R sh[(kThreads / 32) * 2];
+  block_sum<R, 2>(acc, sh);
+  if (threadIdx.x == 0) {
+    a.partial[2 * blockIdx.x] = to_fix_sum(double(acc[0]));
+    a.partial[2 * blockIdx.x + 1] = to_fix_sum(double(acc[1]));
+  }
+}
+
+// ----------------------------------------------------------------- drift
+
+template <typename R>
+struct DriftArgs {
+  int n;
+  double* vel;  // u, updated
+  unsigned long long* xfx;
+  const ForceT<R>* f_tot;
+  const int* type;
+  TypeConsts tc;
+  BoxConsts bc;
+  const int* rank_fg;
+  const int* rank_cg;
+  int4* pos_fg;
+  int4* pos_cg;
+  Pos64* pos_fg64;
+  Pos64* pos_cg64;
+  const int4* ref;
+  float thr2;
+  int thermo_every;
+  DevState* st;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_drift(DriftArgs<R> a) {
+  const double ca = a.st->a, cb = a.st->b;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    a.st->ev = a.thermo_every > 0 && ((a.st->local_step + 1) % a.thermo_every) == 0;
+  bool rebuild = false;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) {
+    const int t = a.type[i];
+    R f[3];
+    load_force(a.f_tot, i, f);
+    const R bc = R(cb * a.tc.cdt[t]);
+    unsigned long long x[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      // the kick increment in the force's precision, accumulated in FP64
+      const double u = fma(ca, a.vel[3 * i + q], double(bc * f[q]));
+      a.vel[3 * i + q] = u;
+      x[q] = a.xfx[3 * i + q] + (unsigned long long)__double2ll_rn(u * a.bc.dts[q]);
+      a.xfx[3 * i + q] = x[q];
+    }
+    scatter_sorted(i, t, x[0], x[1], x[2], a.rank_fg, a.rank_cg, a.pos_fg, a.pos_cg, a.pos_fg64,
+                   a.pos_cg64);
+    rebuild = moved_beyond(a.ref[i], x[0], x[1], x[2], a.bc, a.thr2);
+  }
+  if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&a.st->flags, F_REBUILD);
+}
+
+// ----------------------------------------------------------------- thermostat
+
+// splitmix64 (Steele, Lea & Flood 2014) as a counter-based generator: the
+// (c+1)-th output of the sequence started at `key`.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long key, unsigned long long c) {
+  unsigned long long z = key + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double uniform01(unsigned long long key, unsigned long long& c) {
+  // (0, 1]: top 53 bits plus one ulp
+  return (double(mix64(key, c++) >> 11) + 1.0) * 1.1102230246251565e-16;
+}
+__device__ double gauss(unsigned long long key, unsigned long long& c) {
+  const double u1 = uniform01(key, c), u2 = uniform01(key, c);
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+// Marsaglia & Tsang (2000) gamma(shape, 1) for shape >= 1
+__device__ double gamma_mt(double shape, unsigned long long key, unsigned long long& c) {
+  const double d = shape - 1.0 / 3.0, k = 1.0 / sqrt(9.0 * d);
+  for (int it = 0; it < 1000; ++it) {
+    const double x = gauss(key, c);
+    double v = 1.0 + k * x;
+    if (v <= 0.0) continue;
+    v = v * v * v;
+    if (log(uniform01(key, c)) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+  }
+  return d;
+}
+// Bussi-Donadio-Parrinello (2007) velocity-rescaling factor for one step.
+__device__ double csvr_factor(double ke, const StepParams& sp, unsigned long long step) {
+  unsigned long long c = step << 20;
+  const double e = exp(-sp.dt / sp.tau);
+  const double r1 = gauss(sp.seed, c);
+  const double s = 2.0 * gamma_mt(0.5 * (sp.n_f - 1.0), sp.seed, c);
+  const double kn = ke + (1.0 - e) * (sp.kt / sp.n_f * (r1 * r1 + s) - ke) +
+                    2.0 * r1 * sqrt(e * (1.0 - e) * ke * sp.kt / sp.n_f);
+  return sqrt(kn / ke);
+}
+
+struct ReduceArgs {
+  const long long* part_fg;
+  int nb_fg;
+  const long long* part_cg;
+  int nb_cg;
+  const long long* part_fin;
+  int nb_fin;
+};
+
+// Sums of the fixed-point partials: out[0..kNQ) FG, [kNQ..2kNQ) CG, [2kNQ] KE,
+// [2kNQ+1] E_bonded.  Integer sums: exact and independent of order.
+__device__ void reduce_partials(const ReduceArgs& r, bool with_pairs, long long* out) {
+  constexpr int NO = 2 * kNQ + 2;
+  long long loc[NO];
+#pragma unroll
+  for (int q = 0; q < NO; ++q) loc[q] = 0;
+  for (int b = threadIdx.x; b < r.nb_fin; b += blockDim.x) {
+    loc[2 * kNQ] += r.part_fin[2 * b];
+    loc[2 * kNQ + 1] += r.part_fin[2 * b + 1];
+  }
+  if (with_pairs) {
+    for (int b = threadIdx.x; b < r.nb_fg; b += blockDim.x)
+#pragma unroll
+      for (int q = 0; q < kNQ; ++q) loc[q] += r.part_fg[b * kNQ + q];
+    if (r.part_cg)
+      for (int b = threadIdx.x; b < r.nb_cg; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < kNQ; ++q) loc[kNQ + q] += r.part_cg[b * kNQ + q];
+  }
+  __shared__ long long sh[(1024 / 32) * NO];
+  block_sum<long long, NO>(loc, sh);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NO; ++q) out[q] = loc[q];
+}
+
+__global__ void k_thermo(ReduceArgs r, StepParams sp, DevState* st) {
+  __shared__ long long tot[2 * kNQ + 2];
+  const bool ev = st->ev != 0;
+  reduce_partials(r, ev, tot);
+  if (threadIdx.x != 0) return;
+  const double ke = double(tot[2 * kNQ]) / kFix;
+  double alpha = 1.0;
+  if (sp.t_target > 0.0 && ke > 0.0) alpha = csvr_factor(ke, sp, st->step);
+  st->alpha = alpha;
+  st->a = alpha;
+  st->b = alpha + 1.0;
+  if (ev && sp.thermo) {
+    double* row = sp.thermo + (size_t)st->thermo_row * RELRES_THERMO_COLS;
+    row[0] = double(tot[0]) / kFix;
+    row[1] = double(tot[kNQ]) / kFix;
+    row[2] = double(tot[2 * kNQ + 1]) / kFix;
+    row[3] = ke * alpha * alpha;
+    for (int q = 1; q < kNQ; ++q) row[3 + q] = double(tot[q] + tot[kNQ + q]) / kFix;
+    st->thermo_row += 1;
+  }
+  st->local_step += 1;
+  st->step += 1;
+  if (st->flags & F_REBUILD) {
+    st->n_builds += 1;
+    st->flags &= ~F_REBUILD;
+  }
+}
+
+__global__ void k_reduce_out(ReduceArgs r, double* energy, double* virial) {
+  __shared__ long long tot[2 * kNQ + 2];
+  reduce_partials(r, true, tot);
+  if (threadIdx.x != 0) return;
+  const double efg = double(tot[0]) / kFix, ecg = double(tot[kNQ]) / kFix;
+  const double eb = double(tot[2 * kNQ + 1]) / kFix;
+  if (energy) {
+    energy[0] = efg;
+    energy[1] = ecg;
+    energy[2] = eb;
+    energy[3] = efg + ecg + eb;
+  }
+  if (virial)
+    for (int q = 1; q < kNQ; ++q) virial[q - 1] = double(tot[q] + tot[kNQ + q]) / kFix;
+}
+
+__global__ void k_set_ab(DevState* st, double a, double b) {
+  st->a = a;
+  st->b = b;
+  st->local_step = 0;
+  st->thermo_row = 0;
+  st->ev = 0;
+}
+
+template <typename R>
+__global__ void k_finish_md(int n, const DevState* st, const double* vel_u,
+                            const ForceT<R>* __restrict__ f_tot, const int* __restrict__ type,
+                            TypeConsts tc, const unsigned long long* __restrict__ xfx, BoxConsts bc,
+                            double* vel_out, double* __restrict__ pos_out) {
+  const double ca = st->a, cb1 = st->b - 1.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int t = type[i];
+    R f[3];
+    load_force(f_tot, i, f);
+    const R c = R(cb1 * tc.cdt[t]);
+    for (int q = 0; q < 3; ++q) {
+      vel_out[3 * i + q] = fma(ca, vel_u[3 * i + q], double(c * f[q]));
+      double x = from_fixed(xfx[3 * i + q], bc.l_2m64[q]);
+      if (x >= 1.0 / bc.inv_l[q]) x = 0.0;
+      pos_out[3 * i + q] = x;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- launchers
+
+static int grid_for(int n) {
+  const int b = (n + kThreads - 1) / kThreads;
+  return b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b);
+}
+
+static TypeConsts type_consts(const relres_ctx* c, double dt) {
+  TypeConsts t{};
+  for (int k = 0; k < c->n_types; ++k) {
+    t.mass[k] = c->mass_by_type[k];
+    t.cdt[k] = 0.5 * dt / c->mass_by_type[k] * kFtm2v;
+  }
+  return t;
+}
+
+static float trigger_thr2(const relres_ctx* c) {
+  double skin = c->prm.skin;
+  if (c->has_cg && c->n_h > 0 && c->skin_cg < skin) skin = c->skin_cg;
+  const double h = 0.5 * skin;
+  return float(h * h);
+}
+
+cudaError_t launch_convert(relres_ctx* c, const double* d_pos) {
+  const BoxConsts b = box_consts(c, 0.0);
+  k_convert<<<grid_for(c->n), kThreads, 0, c->stream>>>(
+      c->n, d_pos, c->d_type, c->d_xfx, b, c->have_lists, c->d_rank_fg,
+      (c->has_cg && c->n_h > 0) ? c->d_rank_cg : nullptr, c->d_pos_fg, c->d_pos_cg, c->d_pos_fg64,
+      c->d_pos_cg64, c->d_ref, trigger_thr2(c), c->d_state);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_cache(relres_ctx* c, const double* d_pos) {
+  k_check_cache<<<grid_for(c->n), kThreads, 0, c->stream>>>(c->n, d_pos, c->d_xfx, box_consts(c, 0.0),
+                                                            c->d_state);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+static BondedArgs bonded_args(const relres_ctx* c) {
+  return BondedArgs{c->d_inc_off, c->d_inc, c->d_bonds, c->d_angles, c->d_dihs, c->d_dih_type,
+                    c->d_bond_par, c->d_angle_par, c->d_dih_par};
+}
+
+template <typename R>
+static cudaError_t launch_finish_t(relres_ctx* c, int ev_mode, double* d_forces_out, const double* vel,
+                                   double dt) {
+  FinishArgs<R> a{c->n,
+                  static_cast<const ForceT<R>*>(c->d_f_fg),
+                  (c->has_cg && c->n_h > 0) ? static_cast<const ForceT<R>*>(c->d_f_cg) : nullptr,
+                  c->d_type,
+                  c->hyb_mask,
+                  bonded_args(c),
+                  c->d_xfx,
+                  box_consts(c, dt),
+                  vel,
+                  type_consts(c, dt),
+                  static_cast<ForceT<R>*>(c->d_f_tot),
+                  d_forces_out,
+                  c->d_part_fin,
+                  c->d_state};
+  k_finish<R><<<c->nb_fin, kThreads, 0, c->stream>>>(a, ev_mode);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(relres_ctx* c, int ev_mode, double* d_forces_out, bool with_ke) {
+  (void)with_ke;
+  return c->fp64 ? launch_finish_t<double>(c, ev_mode, d_forces_out, nullptr, 0.0)
+                 : launch_finish_t<float>(c, ev_mode, d_forces_out, nullptr, 0.0);
+}
+
+cudaError_t launch_finish_step(relres_ctx* c, const StepParams& sp, const double* d_vel) {
+  return c->fp64 ? launch_finish_t<double>(c, 2, nullptr, d_vel, sp.dt)
+                 : launch_finish_t<float>(c, 2, nullptr, d_vel, sp.dt);
+}
+
+static ReduceArgs reduce_args(const relres_ctx* c) {
+  const bool cg = c->has_cg && c->n_h > 0;
+  return ReduceArgs{c->d_part_fg, c->nb_fg, cg ? c->d_part_cg : nullptr, cg ? c->nb_cg : 0,
+                    c->d_part_fin, c->nb_fin};
+}
+
+cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial) {
+  k_reduce_out<<<1, 1024, 0, c->stream>>>(reduce_args(c), d_energy, d_virial);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d_vel) {
+  const bool cg = c->has_cg && c->n_h > 0;
+  DriftArgs<R> a{c->n,
+                 d_vel,
+                 c->d_xfx,
+                 static_cast<const ForceT<R>*>(c->d_f_tot),
+                 c->d_type,
+                 type_consts(c, sp.dt),
+                 box_consts(c, sp.dt),
+                 c->d_rank_fg,
+                 cg ? c->d_rank_cg : nullptr,
+                 c->d_pos_fg,
+                 c->d_pos_cg,
+                 c->d_pos_fg64,
+                 c->d_pos_cg64,
+                 c->d_ref,
+                 trigger_thr2(c),
+                 sp.thermo_every,
+                 c->d_state};
+  k_drift<R><<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(a);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel) {
+  return c->fp64 ? launch_drift_t<double>(c, sp, d_vel) : launch_drift_t<float>(c, sp, d_vel);
+}
+
+cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp) {
+  k_thermo<<<1, 1024, 0, c->stream>>>(reduce_args(c), sp, c->d_state);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev) {
+  (void)ev;
+  k_set_ab<<<1, 1, 0, c->stream>>>(c->d_state, a, b);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+__global__ void k_flags_and(DevState* st, unsigned keep) { st->flags &= keep; }
+
+cudaError_t launch_flags_and(relres_ctx* c, unsigned keep) {
+  k_flags_and<<<1, 1, 0, c->stream>>>(c->d_state, keep);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, double dt) {
+  const BoxConsts b = box_consts(c, dt);
+  const TypeConsts t = type_consts(c, dt);
+  if (c->fp64)
+    k_finish_md<double><<<grid_for(c->n), kThreads, 0, c->stream>>>(
+        c->n, c->d_state, d_vel, static_cast<const double*>(c->d_f_tot), c->d_type, t, c->d_xfx, b,
+        d_vel, d_pos);
+  else
+    k_finish_md<float><<<grid_for(c->n), kThreads, 0, c->stream>>>(
+        c->n, c->d_state, d_vel, static_cast<const float4*>(c->d_f_tot), c->d_type, t, c->d_xfx, b,
+        d_vel, d_pos);
+  ++c->n_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace relres

@@ -1,0 +1,250 @@
+// Internal declarations of librelres (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/relres.h"
+
+namespace relres {
+
+// ------------------------------------------------------------------ tables
+
+// FP64 per-type-pair quantities of Section 2 (exported by relres_prepare_table).
+struct PairRecord {
+  double eps_fg = 0, sig_fg = 0, eps_cg = 0, sig_cg = 0;
+  double rsm = 0, rsp = 0, rcm = 0, rcp = 0;
+  double g_fg_m[5] = {0, 0, 0, 0, 0};  // f_{s-}^{FG}  (Eq. 17)
+  double g_cg_p[5] = {0, 0, 0, 0, 0};  // f_{s+}^{CG}  (Eq. 18)
+  double g_cg_m[5] = {0, 0, 0, 0, 0};  // f_{c-}^{CG}  (Eq. 17)
+  double gam_cm = 0, gam_sp = 0, gam_sm = 0;  // Eq. 19
+};
+
+// Kernel form of one type pair.  The pair kernels evaluate Eq. 20 split
+// exactly into a part on the FG list and a part on the CG list:
+//   FG part: u^FG(r) - f_{s-}(dr_s) for r < r_s-;  f_{s-}(r - r_s-) - f_{s-}(dr_s)
+//            on [r_s-, r_s+);  0 beyond.
+//   CG part: f_{s+}(0) - Gamma_{c-} for r < r_s-;  f_{s+}(r - r_s-) - Gamma_{c-} on
+//            [r_s-, r_s+);  u^CG(r) - Gamma_{c-} on [r_s+, r_c-);
+//            f_{c-}(r - r_c-) - Gamma_{c-} on [r_c-, r_c+);  0 beyond.
+// The sum reproduces Gamma_{s+} and Gamma_{s-} of Eq. 19.  An odd number of
+// 4-byte words per row keeps shared-memory rows on different banks.
+template <typename R>
+struct PairTab {
+  R c12f, c6f, f12f, f6f;   // FG LJ: 4 eps sig^12, 4 eps sig^6, and x12 / x6
+  R rsm, rsm2, rsp2;        // r_s-, r_s-^2, r_s+^2
+  R fg[5];                  // f_{s-}^{FG} coefficients
+  R fgd[4];                 // its derivative: g1, 2 g2, 3 g3, 4 g4
+  R e_fg_shift;             // f_{s-}^{FG}(dr_s)
+  R c12c, c6c, f12c, f6c;   // CG LJ
+  R rcm, rcm2, rcp2;        // r_c-, r_c-^2, r_c+^2
+  R on0, on3, on4, ond3, ond4;  // f_{s+}^{CG}: gamma_0, gamma_3, gamma_4, 3 gamma_3, 4 gamma_4
+  R cgo[5];                 // f_{c-}^{CG}
+  R cgod[4];                // its derivative
+  R gam_cm;                 // Gamma_{c-}
+  R e_cg_close;             // f_{s+}^{CG}(0) - Gamma_{c-}
+  R pad;
+};
+static_assert(sizeof(PairTab<float>) % 8 == 4, "odd row length in words");
+
+std::string build_pair_records(const relres_params* p, std::vector<PairRecord>* out);
+void build_kernel_tables(const std::vector<PairRecord>& recs, std::vector<PairTab<float>>* tf,
+                         std::vector<PairTab<double>>* td);
+void mix_pair(int mixing, double ea, double sa, double eb, double sb, double* e, double* s);
+bool sum_rule(int nt, const double* eps, const double* sig, int mixing, const int* ci,
+              const int* cj, double* eps_cg, double* sig_cg);
+
+// ------------------------------------------------------------------ device state
+
+enum : unsigned {
+  F_REBUILD = 1u,       // an atom moved more than skin/2 since the last build
+  F_OVERFLOW_FG = 2u,   // an FG list exceeded its capacity at the last build
+  F_OVERFLOW_CG = 4u,
+  F_NONFINITE = 8u,     // a non-finite force
+  F_DIRTY = 16u,        // incoming positions differ from the cached state
+};
+
+struct DevState {
+  unsigned flags;
+  int max_fg, max_cg;
+  int ev;                   // this step evaluates energy and virial
+  double a, b;              // next drift: u <- a u + b (dt/2m) F
+  double alpha;             // last thermostat factor
+  unsigned long long step;  // global step counter (thermostat random stream)
+  long long local_step;     // steps done in the current relres_step call
+  long long n_builds;
+  unsigned long long tot_fg, tot_cg;  // list entries at the last build
+  int thermo_row;
+  int pad;
+};
+
+// Energy / virial partial sums are 64-bit fixed point (value * 2^32): exact,
+// order-independent integer reductions.
+constexpr double kFix = 4294967296.0;
+constexpr int kNQ = 7;  // E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
+
+struct Pos64 {  // FP64 mode sorted position: 64-bit fixed-point x, y, z and type
+  long long x, y, z, t;
+};
+
+// Call-constant step parameters (kernel arguments).
+struct StepParams {
+  double dt;
+  double t_target, tau, n_f, kt;  // CSVR
+  unsigned long long seed;
+  int thermo_every;
+  double* thermo;  // device [rows][RELRES_THERMO_COLS] or null
+};
+
+struct Grid {
+  int n[3];
+  int ncell;
+  int* d_rank_of = nullptr;  // [n0*n1*n2] -> dense cell rank (Morton order)
+  int* d_start = nullptr;    // [ncell+1]
+  int* d_count = nullptr;    // [ncell] counts / cursors (zero between builds)
+};
+
+// ------------------------------------------------------------------ context
+}  // namespace relres
+
+struct relres_ctx {
+  // parameters
+  relres_params prm{};
+  std::vector<double> eps_fg, sig_fg;
+  std::vector<int> is_hybrid;
+  int n_types = 0;
+  int hyb_mask = 0;
+  bool has_cg = false;
+  bool fp64 = false;
+  std::vector<relres::PairRecord> recs;
+  std::vector<relres::PairTab<float>> tab_f;
+  std::vector<relres::PairTab<double>> tab_d;
+  double rlist_fg_cut = 0, rlist_cg_cut = 0;  // max r_s+, max r_c+ over pairs
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // device tables
+  void* d_tab = nullptr;  // PairTab<float or double>[n_types^2]
+  double* d_cdt = nullptr;   // per type: (dt/2m) * ftm2v  (set per step call)
+  double* d_mass = nullptr;  // per type mass
+
+  // topology
+  int n = 0, n_h = 0;
+  bool have_topo = false;
+  std::vector<int> h_type;
+  std::vector<double> mass_by_type;
+  int* d_type = nullptr;
+  int* d_excl_off = nullptr;
+  int* d_excl_idx = nullptr;
+  int n_bonds = 0, n_angles = 0, n_dih = 0;
+  int4* d_bonds = nullptr;      // i, j, type, 0
+  int4* d_angles = nullptr;     // i, vertex, k, type
+  int4* d_dihs = nullptr;       // i, j, k, l
+  int* d_dih_type = nullptr;
+  double* d_bond_par = nullptr;   // k, r0 per type
+  double* d_angle_par = nullptr;  // k, theta0 per type
+  double* d_dih_par = nullptr;    // K1..K4 per type
+  int* d_inc_off = nullptr;   // incident terms per atom (CSR)
+  int* d_inc = nullptr;       // (kind << 30) | (role << 28) | term
+  long long* d_vir_dummy = nullptr;
+
+  // box and grids
+  bool have_box = false;
+  double box[3] = {0, 0, 0};
+  double skin_cg = 0;
+  relres::Grid gfg, gcg;
+  bool have_lists = false;
+
+  // positions and sorting
+  unsigned long long* d_xfx = nullptr;  // [n*3] 64-bit fixed point, caller order
+  int4* d_ref = nullptr;                // [n] hi32 positions at the last build
+  int* d_cell_fg = nullptr;
+  int* d_cell_cg = nullptr;
+  int* d_perm_fg = nullptr;             // FG slot -> atom
+  int* d_rank_fg = nullptr;             // atom -> FG slot
+  int* d_perm_cg = nullptr;             // CG slot -> atom
+  int* d_rank_cg = nullptr;             // atom -> CG slot, -1 for ordinary
+  int4* d_pos_fg = nullptr;             // [n] sorted hi32 positions + type
+  int4* d_pos_cg = nullptr;             // [n_h]
+  relres::Pos64* d_pos_fg64 = nullptr;  // FP64 mode
+  relres::Pos64* d_pos_cg64 = nullptr;
+
+  // lists
+  int cap_fg = 0, cap_cg = 0;
+  int* d_nbr_fg = nullptr;  // [cap_fg][n]   column-major: entry k of slot s at k*n + s
+  int* d_cnt_fg = nullptr;  // [n]
+  int* d_nbr_cg = nullptr;  // [cap_cg][n_h]
+  int* d_cnt_cg = nullptr;  // [n_h]
+  int last_max_fg = 0, last_max_cg = 0;
+  double last_mean_fg = 0, last_mean_cg = 0;
+
+  // forces (caller order): float4 per atom (FP32) or double[3] per atom (FP64)
+  void* d_f_fg = nullptr;
+  void* d_f_cg = nullptr;
+  void* d_f_tot = nullptr;
+  bool forces_valid = false;
+
+  // reductions
+  long long* d_part_fg = nullptr;   // [blocks][kNQ]
+  long long* d_part_cg = nullptr;
+  long long* d_part_fin = nullptr;  // [blocks][2]: KE, E_bonded
+  int nb_fg = 0, nb_cg = 0, nb_fin = 0;
+  relres::DevState* d_state = nullptr;
+  relres::DevState* h_state = nullptr;  // pinned mirror
+  double* d_out_scratch = nullptr;      // [16]
+
+  // rollback snapshot for relres_step
+  unsigned long long* d_snap_x = nullptr;
+  double* d_snap_v = nullptr;
+  void* d_snap_f = nullptr;
+  relres::DevState* d_snap_state = nullptr;
+
+  long long n_builds = 0;
+  long long n_steps = 0;
+  unsigned long long step_counter = 0;
+
+  // instrumentation
+  long long n_launches = 0;
+  bool timing = false;
+  struct Mark {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<Mark> marks;
+  size_t ev_used = 0;
+  double t_ms[RELRES_T_NCLASS] = {};
+  long long t_cnt[RELRES_T_NCLASS] = {};
+};
+
+namespace relres {
+
+// ------------------------------------------------------------------ launchers
+// All launchers enqueue on ctx->stream and return cudaGetLastError().
+
+// positions
+cudaError_t launch_convert(relres_ctx* c, const double* d_pos);
+cudaError_t launch_check_cache(relres_ctx* c, const double* d_pos);
+cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, double dt);
+
+// neighbour lists; gate: device flag word (rebuild only if F_REBUILD set) or null
+cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate);
+cudaError_t launch_lists(relres_ctx* c, const unsigned* gate);
+
+// pair and finish; ev_mode 0 = never, 1 = always, 2 = per step (DevState::ev)
+// which: 1 = FG-list kernel, 2 = CG-list kernel, 3 = both
+cudaError_t launch_pairs(relres_ctx* c, int ev_mode, int which = 3);
+cudaError_t launch_finish(relres_ctx* c, int ev_mode, double* d_forces_out, bool with_ke);
+cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial);
+
+// MD
+cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel);
+cudaError_t launch_finish_step(relres_ctx* c, const StepParams& sp, const double* d_vel);
+cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp);
+cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev);
+cudaError_t launch_flags_and(relres_ctx* c, unsigned keep);
+
+}  // namespace relres

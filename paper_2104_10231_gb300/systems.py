@@ -139,16 +139,29 @@ def _place_rigid(template, sites, k, box, rng, min_dist=3.0, max_rounds=200):
         pairs.append(np.stack([np.arange(n_mol)[ok], partner[ok]], axis=1))
     pairs = np.concatenate(pairs)
     pairs = pairs[pairs[:, 0] != pairs[:, 1]]
+
+    def too_close(pp):
+        out = []
+        for c0 in range(0, len(pp), 100_000):
+            ch = pp[c0:c0 + 100_000]
+            d = coords[ch[:, 0]][:, :, None, :] - coords[ch[:, 1]][:, None, :, :]
+            d -= box * np.round(d / box)
+            dmin2 = (d * d).sum(-1).reshape(len(ch), -1).min(1)
+            out.append(ch[dmin2 < min_dist * min_dist])
+        return np.concatenate(out) if out else pp[:0]
+
+    check = pairs
     for _ in range(max_rounds):
-        d = coords[pairs[:, 0]][:, :, None, :] - coords[pairs[:, 1]][:, None, :, :]
-        d -= box * np.round(d / box)
-        dmin = np.sqrt((d * d).sum(-1)).reshape(len(pairs), -1).min(1)
-        bad = pairs[dmin < min_dist]
+        bad = too_close(check)
         if len(bad) == 0:
             return coords.reshape(-1, 3)
         redo = np.unique(bad.max(axis=1))
         Rn = random_rotations(rng, len(redo))
         coords[redo] = np.einsum("mij,sj->msi", Rn, template) + sites[redo][:, None, :]
+        # only pairs that involve a re-drawn molecule can have changed
+        moved = np.zeros(n_mol, bool)
+        moved[redo] = True
+        check = pairs[moved[pairs[:, 0]] | moved[pairs[:, 1]]]
     raise RuntimeError("could not remove initial overlaps")
 
 
@@ -402,9 +415,9 @@ def block_copolymer(n_chain=200, n_bead=100, block=50, density=0.75, temperature
 
 def fg_only(system, r_inner=13.0, r_outer=14.0):
     """The same system set up as the plain FG reference of the paper (r_s -> r_c,
-    no CG interaction): r_s- = r_c- = r_inner, r_s+ = r_c+ = r_outer and every
-    type ordinary, so only the FG LJ term, smoothed to zero over
-    [r_inner, r_outer), remains."""
+    no CG interaction): r_s- = r_inner, r_s+ = r_c- = r_c+ = r_outer (the
+    radii must stay ordered) and every type ordinary, so only the FG LJ term,
+    smoothed to zero over [r_inner, r_outer), remains."""
     return system.subset_copy(name=system.name + "_fg_only",
                               is_hybrid=np.zeros_like(system.is_hybrid),
-                              radii=(r_inner, r_outer, r_inner, r_outer))
+                              radii=(r_inner, r_outer, r_outer, r_outer))

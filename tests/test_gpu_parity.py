@@ -1,0 +1,235 @@
+"""GPU parity of librelres against the FP64 oracle (through the C ABI).
+
+Error measures (the tolerances of the method's specification):
+  forces: max_i |F_i - F_i^ref| / rms_i |F_i^ref|  <= 1e-5
+  energy: |E - E^ref| / |E^ref|                      <= 1e-7
+FP64 mode must meet far tighter bounds (1e-10); FP32 mode (FP32 pair terms
+from exact fixed-point coordinate differences) the ones above.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import core as O
+from paper_2104_10231_gb300 import relres as R
+from paper_2104_10231_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-5
+E_TOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2104_10231_gb300.build import build_library
+
+    build_library()
+    R.load()
+    return T
+
+
+def _dev(torch, a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def gpu_compute(torch, system, precision, shift=True, pos=None):
+    ctx = R.Context(R.params_for(system, precision, shift), R.topology_for(system))
+    p = _dev(torch, system.pos if pos is None else pos)
+    ctx.build_neighbors(p, system.box)
+    f = torch.empty_like(p)
+    e = torch.zeros(4, dtype=torch.float64, device="cuda")
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.compute(p, f, e, w)
+    torch.cuda.synchronize()
+    out = f.cpu().numpy(), e.cpu().numpy(), w.cpu().numpy(), ctx.stats()
+    ctx.close()
+    return out
+
+
+def oracle_compute(system, shift=True, pos=None):
+    pos = system.pos if pos is None else pos
+    tab = O.table_for(system, shift)
+    f, e, w = O.pair_forces(pos, system.box, system.types, tab, system.n_types, system.excl)
+    fb, eb = O.bonded(pos, system.box, system.topo)
+    return f + fb, e, float(eb.sum()), w
+
+
+def force_err(f, ref):
+    rms = math.sqrt((ref * ref).sum(1).mean())
+    return float(np.abs(f - ref).max() / rms)
+
+
+def check(torch, system, precision, f_tol, e_tol, shift=True):
+    f, e, w, st = gpu_compute(torch, system, precision, shift)
+    fr, er, ebr, wr = oracle_compute(system, shift)
+    ferr = force_err(f, fr)
+    eerr = abs(e[0] + e[1] - er) / abs(er)
+    berr = abs(e[2] - ebr) / max(1.0, abs(ebr))
+    werr = float(np.abs(w - wr).max() / np.abs(wr[:3]).max())
+    print(f"{system.name} prec={precision}: force {ferr:.2e} energy {eerr:.2e} "
+          f"bonded {berr:.2e} virial {werr:.2e}  lists {st['mean_fg']:.1f}/{st['mean_cg']:.1f}")
+    assert ferr <= f_tol, ferr
+    assert eerr <= e_tol, eerr
+    assert berr <= e_tol, berr
+    assert werr <= 10 * f_tol, werr
+    assert e[3] == pytest.approx(e[0] + e[1] + e[2], rel=1e-14, abs=1e-12)
+    return ferr, eerr
+
+
+def test_fp64_propane_full_config(torch):
+    check(torch, S.propane(), R.RELRES_PREC_FP64, 1e-10, 1e-10)
+
+
+def test_fp64_propane_no_shift(torch):
+    check(torch, S.propane(), R.RELRES_PREC_FP64, 1e-10, 1e-10, shift=False)
+
+
+def test_fp32_propane_full_config(torch):
+    check(torch, S.propane(), R.RELRES_PREC_FP32, F_TOL, E_TOL)
+
+
+def test_fp32_neopentane_2500_atoms(torch):
+    check(torch, S.neopentane(n_mol=500), R.RELRES_PREC_FP32, F_TOL, E_TOL)
+
+
+def test_fp64_neopentane_2500_atoms(torch):
+    check(torch, S.neopentane(n_mol=500), R.RELRES_PREC_FP64, 1e-10, 1e-10)
+
+
+def test_fp32_fg_only_reference(torch):
+    check(torch, S.fg_only(S.neopentane(n_mol=500)), R.RELRES_PREC_FP32, F_TOL, E_TOL)
+
+
+def test_fp32_ragged_sizes(torch):
+    # sizes that are not multiples of the 256-thread block, several cells per axis
+    for n_mol in (251, 343):
+        check(torch, S.neopentane(n_mol=n_mol, seed=3), R.RELRES_PREC_FP32, F_TOL, E_TOL)
+
+
+def _brute_force_list_count(system, rlist, hybrid_only):
+    pos, L = system.pos, system.box
+    sel = np.arange(system.n_atoms)
+    if hybrid_only:
+        sel = sel[system.is_hybrid[system.types] == 1]
+    p = pos[sel]
+    off, idx = system.excl
+    total = 0
+    for a in range(len(sel)):
+        d = p - p[a]
+        d -= L * np.round(d / L)
+        r2 = (d * d).sum(1)
+        hit = np.nonzero(r2 < rlist * rlist)[0]
+        hit = hit[hit != a]
+        ex = set(idx[off[sel[a]]:off[sel[a] + 1]].tolist())
+        total += sum(1 for h in hit if sel[h] not in ex)
+    return total
+
+
+def test_list_sizes_match_brute_force(torch):
+    s = S.neopentane(n_mol=300, seed=5)
+    _, _, _, st = gpu_compute(torch, s, R.RELRES_PREC_FP32)
+    nfg = _brute_force_list_count(s, st["list_radius_fg"], False)
+    ncg = _brute_force_list_count(s, st["list_radius_cg"], True)
+    assert round(st["mean_fg"] * s.n_atoms) == nfg
+    assert round(st["mean_cg"] * s.n_hybrid) == ncg
+
+
+def _gpu_md(torch, system, precision, n_steps, dt, t_target=0.0, seed=0, every=1):
+    ctx = R.Context(R.params_for(system, precision), R.topology_for(system))
+    p = _dev(torch, system.pos)
+    v = _dev(torch, system.vel)
+    ctx.build_neighbors(p, system.box)
+    rows = n_steps // every if every else 0
+    th = torch.zeros((max(rows, 1), R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+    ctx.step(n_steps, dt, p, v, t_target=t_target, tau_fs=100.0, seed=seed, thermo_every=every,
+             d_thermo=th)
+    torch.cuda.synchronize()
+    out = p.cpu().numpy(), v.cpu().numpy(), th.cpu().numpy(), ctx.stats()
+    ctx.close()
+    return out
+
+
+def _oracle_md(system, n_steps, dt, t_target=0.0, seed=0):
+    tab = O.table_for(system)
+    return O.md(system.pos, system.vel, system.box, system.masses, system.types, tab,
+                system.n_types, system.excl, system.topo, n_steps, dt, t_target=t_target,
+                tau=100.0, seed=seed)
+
+
+def _wrapped_diff(a, b, L):
+    d = a - b
+    return d - L * np.round(d / L)
+
+
+def test_fp64_nve_trajectory_matches_oracle(torch):
+    s = S.propane()
+    p, v, th, st = _gpu_md(torch, s, R.RELRES_PREC_FP64, 40, 1.0)
+    po, vo, tho = _oracle_md(s, 40, 1.0)
+    assert np.abs(_wrapped_diff(p, po, s.box)).max() < 1e-9
+    assert np.abs(v - vo).max() < 1e-10
+    np.testing.assert_allclose(th[:, 0] + th[:, 1], tho[:, 0], rtol=1e-9)
+    np.testing.assert_allclose(th[:, 2], tho[:, 1], rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(th[:, 3], tho[:, 2], rtol=1e-9)
+    assert np.all(p >= 0.0) and np.all(p < s.box)
+
+
+def test_fp64_csvr_trajectory_matches_oracle(torch):
+    s = S.propane()
+    p, v, th, st = _gpu_md(torch, s, R.RELRES_PREC_FP64, 30, 1.0, t_target=230.0, seed=11)
+    po, vo, tho = _oracle_md(s, 30, 1.0, t_target=230.0, seed=11)
+    np.testing.assert_allclose(th[:, 3], tho[:, 2], rtol=1e-8)
+    assert np.abs(_wrapped_diff(p, po, s.box)).max() < 1e-8
+
+
+def test_fp32_trajectory_tracks_oracle_and_rebuilds(torch):
+    # long enough for several device-side list rebuilds
+    s = S.propane()
+    p, v, th, st = _gpu_md(torch, s, R.RELRES_PREC_FP32, 200, 1.0, every=10)
+    assert st["n_builds"] >= 2
+    # forces at the final positions: stepping context (lists rebuilt on the
+    # device) vs a fresh build vs the oracle
+    f, e, w, _ = gpu_compute(torch, s, R.RELRES_PREC_FP32, pos=p)
+    fr, er, ebr, wr = oracle_compute(s, pos=p)
+    assert force_err(f, fr) <= F_TOL
+
+
+def test_fp32_nve_energy_drift(torch):
+    s = S.propane()
+    _, _, th, _ = _gpu_md(torch, s, R.RELRES_PREC_FP32, 1000, 1.0, every=10)
+    etot = th[:, 0] + th[:, 1] + th[:, 2] + th[:, 3]
+    ke = th[:, 3].mean()
+    # the lattice start relaxes in the first ~50 fs; look at the rest
+    tail = etot[10:]
+    drift = abs(tail[-1] - tail[0]) / ke
+    assert drift < 2e-3, drift
+
+
+def test_box_too_small_is_an_error(torch):
+    s = S.propane(n_mol=64, box=25.0)
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    with pytest.raises(R.RelresError) as ei:
+        ctx.build_neighbors(p, s.box)
+    assert ei.value.status == 3
+    ctx.close()
+
+
+def test_nonfinite_position_is_an_error(torch):
+    s = S.propane()
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    ctx.build_neighbors(p, s.box)
+    bad = p.clone()
+    bad[5, 1] = float("nan")
+    f = torch.empty_like(p)
+    with pytest.raises(R.RelresError) as ei:
+        ctx.compute(bad, f)
+    assert ei.value.status == 5
+    # the context stays usable
+    ctx.compute(p, f)
+    ctx.close()

@@ -1,0 +1,129 @@
+"""Host-side checks of the C-ABI library (no GPU calls).
+
+* librelres.so loads and exports every entry point include/relres.h declares.
+* relres_prepare_table (the library's own C++ parameter preparation: mixing,
+  Eq. 13, Eq. 17/18, Eq. 19) equals the oracle's pair table.
+* relres_cg_params reproduces Table 1 through Eq. 13 under geometric mixing.
+* Invalid parameters come back as RELRES_ERR_ARG, never a crash.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import params as P
+from paper_2104_10231_gb300 import relres as R
+from paper_2104_10231_gb300 import systems as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_10231_gb300.build import build_library
+
+    build_library()
+    return R.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "relres.h")).read()
+    decl = r"^(?:relres_status|void|const char\s*\*)\s*(relres_[a-z_]+)\s*\("
+    return sorted(set(re.findall(decl, src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "relres_step" in names and "relres_compute" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(names) == sorted(R.EXPORTED)
+
+
+def _compare(sysobj, shift=True):
+    p = R.params_for(sysobj, shift=shift)
+    got = R.relres_prepare_table(p)
+    want = P.pair_table(sysobj.eps_fg, sysobj.sig_fg, sysobj.is_hybrid, sysobj.radii,
+                        mixing=sysobj.mixing, group_comp=sysobj.group_comp, shift=shift)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("shift", [True, False])
+def test_prepare_table_matches_oracle_propane(lib, shift):
+    _compare(S.propane(n_mol=8), shift)
+
+
+def test_prepare_table_matches_oracle_neopentane(lib):
+    _compare(S.neopentane(n_mol=27))
+
+
+def test_prepare_table_matches_oracle_copolymer_types(lib):
+    s = S.neopentane(n_mol=8)
+    s = s.subset_copy(eps_fg=np.array([0.0914, 0.195, 0.0914, 0.195]),
+                      sig_fg=np.array([3.95, 3.75, 3.95, 3.75]),
+                      is_hybrid=np.array([0, 0, 1, 1], np.int32),
+                      group_comp=np.array([[0, 0, 0, 0], [0, 0, 0, 0], [4, 0, 1, 0], [0, 4, 0, 1]]),
+                      mixing="geometric", radii=(5.5, 6.5, 12.0, 14.0))
+    _compare(s)
+
+
+def test_prepare_table_fg_only_limit(lib):
+    _compare(S.fg_only(S.neopentane(n_mol=8)))
+
+
+def test_prepare_table_explicit_cg_and_pair_radii(lib):
+    eps = [0.3, 0.2, 0.25]
+    sig = [3.9, 3.7, 4.1]
+    hyb = [1, 0, 1]
+    ecg = np.array([[2.0, 0.0, 1.5], [0.0, 0.0, 0.0], [1.5, 0.0, 1.2]])
+    scg = np.array([[4.0, 3.9, 4.2], [3.9, 3.9, 3.9], [4.2, 3.9, 4.3]])
+    rp = np.zeros((3, 3, 4))
+    for a in range(3):
+        for b in range(3):
+            rs = np.sqrt([6.0, 6.5, 7.0][a] * [6.0, 6.5, 7.0][b])
+            rp[a, b] = (rs - 0.5, rs + 0.5, 13.0, 14.0)
+    p = R.make_params(eps, sig, hyb, (6, 7, 13, 14), 2.0, mixing=R.RELRES_MIX_GEOMETRIC,
+                      eps_cg=ecg, sig_cg=scg, radii_pair=rp)
+    got = R.relres_prepare_table(p)
+    want = P.pair_table(eps, sig, hyb, (6, 7, 13, 14), mixing=P.MIX_GEOMETRIC, eps_cg=ecg,
+                        sig_cg=scg, radii_pair=rp)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+def test_cg_params_reproduce_table1(lib):
+    from tests.test_oracle_params import _load_table1
+
+    for name, sites, ce, cs in _load_table1():
+        eps = [x[0] for x in sites]
+        sig = [x[1] for x in sites]
+        comp = [1] * len(sites)
+        # every site its own type: the group is all types once
+        e, s = R.relres_cg_params(eps, sig, R.RELRES_MIX_GEOMETRIC, comp, comp) if len(sites) <= 8 else (0, 0)
+        assert e == pytest.approx(ce, rel=5e-4), name
+        assert s == pytest.approx(cs, rel=5e-4), name
+
+
+@pytest.mark.parametrize("bad", ["radii", "eps", "cg_ordinary", "ntypes", "mixing"])
+def test_invalid_parameters_are_rejected(lib, bad):
+    kw = dict(eps_fg=[0.3, 0.2], sig_fg=[3.9, 3.7], is_hybrid=[1, 0], radii=(6, 7, 13, 14),
+              skin=2.0, group_comp=[[1, 2], [0, 0]])
+    if bad == "radii":
+        kw["radii"] = (7, 6, 13, 14)
+    elif bad == "eps":
+        kw["eps_fg"] = [-0.3, 0.2]
+    elif bad == "cg_ordinary":
+        kw.pop("group_comp")
+        kw["eps_cg"] = [[1.0, 0.5], [0.5, 0.0]]
+        kw["sig_cg"] = [[4.0, 4.0], [4.0, 4.0]]
+    elif bad == "ntypes":
+        kw["eps_fg"] = [0.1] * 9
+        kw["sig_fg"] = [3.9] * 9
+        kw["is_hybrid"] = [0] * 9
+        kw.pop("group_comp")
+    elif bad == "mixing":
+        kw["mixing"] = 7
+    p = R.make_params(**kw)
+    with pytest.raises(R.RelresError) as ei:
+        R.relres_prepare_table(p)
+    assert ei.value.status == 1

@@ -123,6 +123,16 @@ def test_single_pair_across_boundary():
         assert f[0, 0] == pytest.approx(-du[0], rel=1e-10, abs=1e-15)
 
 
+def test_row_subset_equals_full_sum():
+    pos, box, types, tab, excl = _random_system(n=70, seed=23)
+    f, e, _ = O.pair_forces(pos, box, types, tab, 3, excl)
+    rows = np.array([0, 3, 17, 69, 42])
+    fr, er = O.pair_forces_rows(pos, box, types, tab, 3, rows, excl)
+    np.testing.assert_allclose(fr, f[rows], rtol=1e-13, atol=1e-13)
+    _, eall = O.pair_forces_rows(pos, box, types, tab, 3, np.arange(70), excl)
+    assert eall.sum() == pytest.approx(e, rel=1e-12)
+
+
 def test_exclusion_removes_pair():
     tab = P.pair_table([0.3], [3.9], [1], RADII, group_comp=[[1]])
     pos = np.array([[5.0, 5.0, 5.0], [9.0, 5.0, 5.0]])
