@@ -250,6 +250,13 @@ relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda
   if (ce == cudaSuccess) ce = cudaMemset(c->d_state, 0, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMalloc(&c->d_snap_state, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMallocHost(&c->h_state, sizeof(DevState));
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_dummy, 256);
+  if (ce == cudaSuccess) ce = cudaMemset(c->d_dummy, 0, 256);
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_open, sizeof(unsigned));
+  if (ce == cudaSuccess) {
+    const unsigned open = F_REBUILD;
+    ce = cudaMemcpy(c->d_open, &open, sizeof(unsigned), cudaMemcpyHostToDevice);
+  }
   if (ce != cudaSuccess) {
     relres_destroy(c);
     return ce == cudaErrorMemoryAllocation ? RELRES_ERR_NOMEM : RELRES_ERR_CUDA;
@@ -361,6 +368,8 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   c->nb_fin = blocks(n);
   const size_t fb = size_t(n) * (c->fp64 ? 24 : 16);
   CK(dalloc(&c->d_type, n));
+  CK(dalloc(&c->d_cdt, RELRES_MAX_TYPES));
+  CK(dalloc(&c->d_mass, RELRES_MAX_TYPES));
   CK(dalloc(&c->d_excl_off, size_t(n) + 1));
   CK(dalloc(&c->d_excl_idx, std::max<size_t>(1, eidx.size())));
   CK(dalloc(&c->d_bonds, hb.size()));
@@ -398,6 +407,8 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(&c->d_part_cg, size_t(c->nb_cg) * kNQ));
   CK(dalloc(&c->d_part_fin, size_t(c->nb_fin) * 2));
   CK(cudaMemcpy(c->d_type, c->h_type.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_mass, c->mass_by_type.data(), sizeof(double) * c->n_types, cudaMemcpyHostToDevice));
+  CK(cudaMemset(c->d_cdt, 0, sizeof(double) * RELRES_MAX_TYPES));
   CK(cudaMemcpy(c->d_excl_off, eoff.data(), sizeof(int) * eoff.size(), cudaMemcpyHostToDevice));
   if (!eidx.empty()) CK(cudaMemcpy(c->d_excl_idx, eidx.data(), sizeof(int) * eidx.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->d_bonds, hb.data(), sizeof(int4) * hb.size(), cudaMemcpyHostToDevice));
@@ -505,6 +516,7 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
     s = forces_now(c, 0, nullptr, nullptr, nullptr);
     if (s != RELRES_OK) return s;
   }
+  CK(upload_type_consts(c, dt_fs));
   CK(launch_set_ab(c, 1.0, 1.0, 0));
   const unsigned* gate = &c->d_state->flags;
   const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
@@ -682,6 +694,8 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_snap_v);
   dfree(c->d_snap_f);
   dfree(c->d_snap_state);
+  dfree(c->d_dummy);
+  dfree(c->d_open);
   if (c->h_state) cudaFreeHost(c->h_state);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;

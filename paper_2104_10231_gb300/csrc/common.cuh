@@ -5,6 +5,21 @@
 
 #include "relres_internal.h"
 
+// Every launcher counts its kernels.  Building with -DRELRES_DEBUG_SYNC also
+// synchronises after each launch and reports the first failing kernel site.
+#ifdef RELRES_DEBUG_SYNC
+#include <cstdio>
+#define RELRES_LAUNCHED(c)                                                                   \
+  do {                                                                                       \
+    ++(c)->n_launches;                                                                       \
+    const cudaError_t e_ = cudaDeviceSynchronize();                                          \
+    if (e_ != cudaSuccess) std::fprintf(stderr, "relres: %s:%d %s\n", __FILE__, __LINE__,    \
+                                        cudaGetErrorString(e_));                             \
+  } while (0)
+#else
+#define RELRES_LAUNCHED(c) (++(c)->n_launches)
+#endif
+
 namespace relres {
 
 constexpr int kThreads = 256;
@@ -40,8 +55,12 @@ __device__ __forceinline__ int cell_of(int h, int n) {
   return int((unsigned long long)unsigned(h) * unsigned(n) >> 32);
 }
 
+// No kernel ever receives a null pointer: optional buffers come with an int
+// flag and a valid (possibly unused) pointer.  `gate` points at the device flag
+// word of a step (rebuild only when F_REBUILD is set) or at a word that always
+// has it set.
 __device__ __forceinline__ bool gate_closed(const unsigned* gate) {
-  return gate != nullptr && (*(volatile const unsigned*)gate & F_REBUILD) == 0u;
+  return (*(volatile const unsigned*)gate & F_REBUILD) == 0u;
 }
 
 template <typename T>

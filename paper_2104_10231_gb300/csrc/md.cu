@@ -15,6 +15,10 @@
 // Bonded forces are computed per atom from the CSR list of the terms it takes
 // part in (each term recomputed by each of its atoms): no atomics, and each
 // term's energy is counted by its first atom.
+//
+// Kernel parameters are only read directly (never through a pointer or a
+// reference, never indexed with a run-time index); per-type constants live in
+// small device arrays.
 #include "common.cuh"
 
 namespace relres {
@@ -22,90 +26,108 @@ namespace relres {
 constexpr double kFtm2v = 4.184e-4;        // (kcal/mol/A)/(g/mol) -> A/fs^2
 constexpr double kMvv2e = 1.0 / 4.184e-4;  // (g/mol)(A/fs)^2 -> kcal/mol
 
-struct TypeConsts {
-  double cdt[RELRES_MAX_TYPES];   // dt / (2 m) * ftm2v
-  double mass[RELRES_MAX_TYPES];  // g/mol
-};
-
 struct BoxConsts {
-  double inv_l[3];   // 1 / L
-  double l_2m64[3];  // L / 2^64
-  double dts[3];     // dt * 2^64 / L  (A/fs -> fixed-point units per step)
-  float s32[3];      // L / 2^32
-  double s64[3];     // L / 2^64
+  double inv_l0, inv_l1, inv_l2;     // 1 / L
+  double l64_0, l64_1, l64_2;        // L / 2^64
+  double dts0, dts1, dts2;           // dt * 2^64 / L  (A/fs -> fixed-point units per step)
+  float s32_0, s32_1, s32_2;         // L / 2^32
+  double l0, l1, l2;                 // L
 };
 
 static BoxConsts box_consts(const relres_ctx* c, double dt) {
   BoxConsts b;
-  for (int d = 0; d < 3; ++d) {
-    b.inv_l[d] = 1.0 / c->box[d];
-    b.l_2m64[d] = c->box[d] / 18446744073709551616.0;
-    b.dts[d] = dt * 18446744073709551616.0 / c->box[d];
-    b.s32[d] = float(c->box[d] / 4294967296.0);
-    b.s64[d] = c->box[d] / 18446744073709551616.0;
-  }
+  b.inv_l0 = 1.0 / c->box[0];
+  b.inv_l1 = 1.0 / c->box[1];
+  b.inv_l2 = 1.0 / c->box[2];
+  b.l64_0 = c->box[0] / 18446744073709551616.0;
+  b.l64_1 = c->box[1] / 18446744073709551616.0;
+  b.l64_2 = c->box[2] / 18446744073709551616.0;
+  b.dts0 = dt * 18446744073709551616.0 / c->box[0];
+  b.dts1 = dt * 18446744073709551616.0 / c->box[1];
+  b.dts2 = dt * 18446744073709551616.0 / c->box[2];
+  b.s32_0 = float(c->box[0] / 4294967296.0);
+  b.s32_1 = float(c->box[1] / 4294967296.0);
+  b.s32_2 = float(c->box[2] / 4294967296.0);
+  b.l0 = c->box[0];
+  b.l1 = c->box[1];
+  b.l2 = c->box[2];
   return b;
 }
+
+template <typename R>
+struct Sc3 {  // per-axis scale of a fixed-point difference
+  R s0, s1, s2;
+};
 
 // ----------------------------------------------------------------- positions
 
 __device__ __forceinline__ void scatter_sorted(int i, int t, unsigned long long x, unsigned long long y,
                                                unsigned long long z, const int* rank_fg,
-                                               const int* rank_cg, int4* pos_fg, int4* pos_cg,
-                                               Pos64* pos_fg64, Pos64* pos_cg64) {
+                                               const int* rank_cg, int with_cg, int4* pos_fg,
+                                               int4* pos_cg, int fp64, Pos64* pos_fg64,
+                                               Pos64* pos_cg64) {
   const int4 h = make_int4(hi32(x), hi32(y), hi32(z), t);
   const int sf = rank_fg[i];
   pos_fg[sf] = h;
-  if (pos_fg64) pos_fg64[sf] = Pos64{(long long)x, (long long)y, (long long)z, t};
-  if (rank_cg) {
+  if (fp64) pos_fg64[sf] = Pos64{(long long)x, (long long)y, (long long)z, t};
+  if (with_cg) {
     const int sc = rank_cg[i];
     if (sc >= 0) {
       pos_cg[sc] = h;
-      if (pos_cg64) pos_cg64[sc] = Pos64{(long long)x, (long long)y, (long long)z, t};
+      if (fp64) pos_cg64[sc] = Pos64{(long long)x, (long long)y, (long long)z, t};
     }
   }
 }
 
-__device__ __forceinline__ bool moved_beyond(const int4& ref, unsigned long long x, unsigned long long y,
-                                             unsigned long long z, const BoxConsts& b, float thr2) {
-  const float dx = dfix32(hi32(x), ref.x, b.s32[0]);
-  const float dy = dfix32(hi32(y), ref.y, b.s32[1]);
-  const float dz = dfix32(hi32(z), ref.z, b.s32[2]);
+__device__ __forceinline__ bool moved_beyond(int4 ref, unsigned long long x, unsigned long long y,
+                                             unsigned long long z, Sc3<float> s, float thr2) {
+  const float dx = dfix32(hi32(x), ref.x, s.s0);
+  const float dy = dfix32(hi32(y), ref.y, s.s1);
+  const float dz = dfix32(hi32(z), ref.z, s.s2);
   return dx * dx + dy * dy + dz * dz > thr2;
 }
 
 __global__ void k_convert(int n, const double* __restrict__ pos, const int* __restrict__ type,
-                          unsigned long long* __restrict__ xfx, BoxConsts b, bool have_lists,
-                          const int* rank_fg, const int* rank_cg, int4* pos_fg, int4* pos_cg,
-                          Pos64* pos_fg64, Pos64* pos_cg64, const int4* ref, float thr2,
-                          DevState* st) {
+                          unsigned long long* __restrict__ xfx, BoxConsts b, int have_lists,
+                          const int* rank_fg, const int* rank_cg, int with_cg, int4* pos_fg,
+                          int4* pos_cg, int fp64, Pos64* pos_fg64, Pos64* pos_cg64, const int4* ref,
+                          float thr2, DevState* st) {
+  const double il0 = b.inv_l0, il1 = b.inv_l1, il2 = b.inv_l2;
+  const Sc3<float> s{b.s32_0, b.s32_1, b.s32_2};
   bool rebuild = false, bad = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    unsigned long long u[3];
-    for (int d = 0; d < 3; ++d) {
-      const double x = pos[3 * i + d];
-      bad |= !isfinite(x);
-      u[d] = to_fixed(x, b.inv_l[d]);
-      xfx[3 * i + d] = u[d];
-    }
+    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
+    const unsigned long long ux = to_fixed(x, il0), uy = to_fixed(y, il1), uz = to_fixed(z, il2);
+    xfx[3 * i] = ux;
+    xfx[3 * i + 1] = uy;
+    xfx[3 * i + 2] = uz;
     if (have_lists) {
-      scatter_sorted(i, type[i], u[0], u[1], u[2], rank_fg, rank_cg, pos_fg, pos_cg, pos_fg64, pos_cg64);
-      rebuild |= moved_beyond(ref[i], u[0], u[1], u[2], b, thr2);
+      scatter_sorted(i, type[i], ux, uy, uz, rank_fg, rank_cg, with_cg, pos_fg, pos_cg, fp64, pos_fg64,
+                     pos_cg64);
+      rebuild |= moved_beyond(ref[i], ux, uy, uz, s, thr2);
     }
   }
   if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&st->flags, F_REBUILD);
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, F_NONFINITE);
 }
 
+__device__ __forceinline__ double back_to_double(unsigned long long u, double l64, double l) {
+  const double x = from_fixed(u, l64);
+  return x >= l ? 0.0 : x;
+}
+
 __global__ void k_check_cache(int n, const double* __restrict__ pos,
                               const unsigned long long* __restrict__ xfx, BoxConsts b, DevState* st) {
+  const double a0 = b.l64_0, a1 = b.l64_1, a2 = b.l64_2, l0 = b.l0, l1 = b.l1, l2 = b.l2;
   bool dirty = false;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    for (int d = 0; d < 3; ++d) {
-      double x = from_fixed(xfx[3 * i + d], b.l_2m64[d]);
-      if (x >= 1.0 / b.inv_l[d]) x = 0.0;
-      dirty |= __double_as_longlong(x) != __double_as_longlong(pos[3 * i + d]);
-    }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    dirty |= __double_as_longlong(back_to_double(xfx[3 * i], a0, l0)) != __double_as_longlong(pos[3 * i]);
+    dirty |= __double_as_longlong(back_to_double(xfx[3 * i + 1], a1, l1)) !=
+             __double_as_longlong(pos[3 * i + 1]);
+    dirty |= __double_as_longlong(back_to_double(xfx[3 * i + 2], a2, l2)) !=
+             __double_as_longlong(pos[3 * i + 2]);
+  }
   if (__syncthreads_or(dirty) && threadIdx.x == 0) atomicOr(&st->flags, F_DIRTY);
 }
 
@@ -123,20 +145,15 @@ struct BondedArgs {
   const double* dih_par;    // K1..K4
 };
 
-template <typename R>
-__device__ __forceinline__ void dvec(const unsigned long long* x, int a, int b, const BoxConsts& bc, R d[3]);
-
-template <>
-__device__ __forceinline__ void dvec<float>(const unsigned long long* x, int a, int b,
-                                            const BoxConsts& bc, float d[3]) {
-#pragma unroll
-  for (int q = 0; q < 3; ++q) d[q] = dfix32(hi32(x[3 * a + q]), hi32(x[3 * b + q]), bc.s32[q]);
+__device__ __forceinline__ void dvec(const unsigned long long* x, int a, int b, Sc3<float> s, float d[3]) {
+  d[0] = dfix32(hi32(x[3 * a]), hi32(x[3 * b]), s.s0);
+  d[1] = dfix32(hi32(x[3 * a + 1]), hi32(x[3 * b + 1]), s.s1);
+  d[2] = dfix32(hi32(x[3 * a + 2]), hi32(x[3 * b + 2]), s.s2);
 }
-template <>
-__device__ __forceinline__ void dvec<double>(const unsigned long long* x, int a, int b,
-                                             const BoxConsts& bc, double d[3]) {
-#pragma unroll
-  for (int q = 0; q < 3; ++q) d[q] = dfix64((long long)x[3 * a + q], (long long)x[3 * b + q], bc.s64[q]);
+__device__ __forceinline__ void dvec(const unsigned long long* x, int a, int b, Sc3<double> s, double d[3]) {
+  d[0] = dfix64((long long)x[3 * a], (long long)x[3 * b], s.s0);
+  d[1] = dfix64((long long)x[3 * a + 1], (long long)x[3 * b + 1], s.s1);
+  d[2] = dfix64((long long)x[3 * a + 2], (long long)x[3 * b + 2], s.s2);
 }
 
 template <typename R>
@@ -153,13 +170,13 @@ __device__ __forceinline__ void cross3(const R a[3], const R b[3], R c[3]) {
 // Force on the atom playing `role` in term `item`; adds the term energy when
 // role == 0.
 template <typename R>
-__device__ void bonded_term(const BondedArgs& B, const unsigned long long* xfx, const BoxConsts& bc,
-                            int item, R f[3], R& e) {
+__device__ __forceinline__ void bonded_term(BondedArgs B, const unsigned long long* xfx, Sc3<R> sc,
+                                            int item, R f[3], R& e) {
   const int kind = (item >> 30) & 3, role = (item >> 28) & 3, t = item & 0x0fffffff;
   if (kind == 0) {
     const int4 bd = B.bonds[t];
     R d[3];
-    dvec<R>(xfx, bd.x, bd.y, bc, d);
+    dvec(xfx, bd.x, bd.y, sc, d);
     const R r = sqrt(dot3(d, d));
     const R k = R(B.bond_par[2 * bd.z]), r0 = R(B.bond_par[2 * bd.z + 1]);
     const R g = R(-2) * k * (r - r0) / r;  // force on bd.x along d
@@ -170,8 +187,8 @@ __device__ void bonded_term(const BondedArgs& B, const unsigned long long* xfx, 
   } else if (kind == 1) {
     const int4 an = B.angles[t];
     R r1[3], r2[3];
-    dvec<R>(xfx, an.x, an.y, bc, r1);
-    dvec<R>(xfx, an.z, an.y, bc, r2);
+    dvec(xfx, an.x, an.y, sc, r1);
+    dvec(xfx, an.z, an.y, sc, r2);
     const R n1 = sqrt(dot3(r1, r1)), n2 = sqrt(dot3(r2, r2));
     R c = dot3(r1, r2) / (n1 * n2);
     c = c > R(1) ? R(1) : (c < R(-1) ? R(-1) : c);
@@ -180,22 +197,20 @@ __device__ void bonded_term(const BondedArgs& B, const unsigned long long* xfx, 
     if (s < R(1e-6)) s = R(1e-6);
     const R k = R(B.angle_par[2 * an.w]), t0 = R(B.angle_par[2 * an.w + 1]);
     const R pref = R(2) * k * (th - t0) / s;
-    R fa[3], fb[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      fa[q] = pref * (r2[q] / (n1 * n2) - c * r1[q] / (n1 * n1));
-      fb[q] = pref * (r1[q] / (n1 * n2) - c * r2[q] / (n2 * n2));
+      const R fa = pref * (r2[q] / (n1 * n2) - c * r1[q] / (n1 * n1));
+      const R fb = pref * (r1[q] / (n1 * n2) - c * r2[q] / (n2 * n2));
+      f[q] += role == 0 ? fa : (role == 2 ? fb : -(fa + fb));
     }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) f[q] += role == 0 ? fa[q] : (role == 2 ? fb[q] : -(fa[q] + fb[q]));
     if (role == 0) e += k * (th - t0) * (th - t0);
   } else {
     const int4 dh = B.dihs[t];
     const double* K = B.dih_par + 4 * B.dih_type[t];
     R b1[3], b2[3], b3[3], m1[3], m2[3];
-    dvec<R>(xfx, dh.y, dh.x, bc, b1);
-    dvec<R>(xfx, dh.z, dh.y, bc, b2);
-    dvec<R>(xfx, dh.w, dh.z, bc, b3);
+    dvec(xfx, dh.y, dh.x, sc, b1);
+    dvec(xfx, dh.z, dh.y, sc, b2);
+    dvec(xfx, dh.w, dh.z, sc, b3);
     cross3(b1, b2, m1);
     cross3(b2, b3, m2);
     const R nb2 = sqrt(dot3(b2, b2));
@@ -253,23 +268,29 @@ template <typename R>
 struct FinishArgs {
   int n;
   const ForceT<R>* f_fg;
-  const ForceT<R>* f_cg;  // null without CG
+  const ForceT<R>* f_cg;
+  int with_cg;
   const int* type;
   int hyb_mask;
   BondedArgs B;
   const unsigned long long* xfx;
-  BoxConsts bc;
-  const double* vel;  // u (half-step velocities) for the kinetic energy, or null
-  TypeConsts tc;
+  Sc3<R> sc;
+  const double* vel;   // u (half-step velocities) for the kinetic energy
+  int with_ke;
+  const double* cdt;   // per type: dt / (2 m) * ftm2v
+  const double* mass;  // per type
   ForceT<R>* f_tot;
-  double* f_out;      // optional FP64 copy in caller order
-  long long* partial; // [gridDim.x][2]: KE, E_bonded
+  double* f_out;       // FP64 copy in caller order
+  int with_out;
+  long long* partial;  // [gridDim.x][2]: KE, E_bonded
   DevState* st;
 };
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mode) {
   const bool ev = ev_mode == 1 || (ev_mode == 2 && a.st->ev);
+  const BondedArgs B = a.B;
+  const Sc3<R> sc = a.sc;
   R acc[2] = {R(0), R(0)};
   bool bad = false;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mod
     const int t = a.type[i];
     R f[3];
     load_force(a.f_fg, i, f);
-    if (a.f_cg && ((a.hyb_mask >> t) & 1)) {
+    if (a.with_cg && ((a.hyb_mask >> t) & 1)) {
       R g[3];
       load_force(a.f_cg, i, g);
       f[0] += g[0];
@@ -285,24 +306,23 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mod
       f[2] += g[2];
     }
     R eb = R(0);
-    for (int k = a.B.inc_off[i]; k < a.B.inc_off[i + 1]; ++k)
-      bonded_term<R>(a.B, a.xfx, a.bc, a.B.inc[k], f, eb);
+    for (int k = B.inc_off[i]; k < B.inc_off[i + 1]; ++k) bonded_term<R>(B, a.xfx, sc, B.inc[k], f, eb);
     bad = !(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]));
     save_force(a.f_tot, i, f);
-    if (a.f_out) {
+    if (a.with_out) {
       a.f_out[3 * i] = double(f[0]);
       a.f_out[3 * i + 1] = double(f[1]);
       a.f_out[3 * i + 2] = double(f[2]);
     }
-    if (a.vel) {
-      const R c = R(a.tc.cdt[t]);
+    if (a.with_ke) {
+      const R c = R(a.cdt[t]);
       R v2 = R(0);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const R v = R(a.vel[3 * i + q]) + c * f[q];
         v2 += v * v;
       }
-      acc[0] = R(0.5 * a.tc.mass[t] * kMvv2e) * v2;
+      acc[0] = R(0.5 * a.mass[t] * kMvv2e) * v2;
     }
     if (ev) acc[1] = eb;
   }
@@ -324,12 +344,15 @@ struct DriftArgs {
   unsigned long long* xfx;
   const ForceT<R>* f_tot;
   const int* type;
-  TypeConsts tc;
-  BoxConsts bc;
+  const double* cdt;
+  double dts0, dts1, dts2;
+  Sc3<float> s32;
   const int* rank_fg;
   const int* rank_cg;
+  int with_cg;
   int4* pos_fg;
   int4* pos_cg;
+  int fp64;
   Pos64* pos_fg64;
   Pos64* pos_cg64;
   const int4* ref;
@@ -349,19 +372,20 @@ __global__ void __launch_bounds__(kThreads) k_drift(DriftArgs<R> a) {
     const int t = a.type[i];
     R f[3];
     load_force(a.f_tot, i, f);
-    const R bc = R(cb * a.tc.cdt[t]);
+    const R bc = R(cb * a.cdt[t]);
+    const double dts[3] = {a.dts0, a.dts1, a.dts2};
     unsigned long long x[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       // the kick increment in the force's precision, accumulated in FP64
       const double u = fma(ca, a.vel[3 * i + q], double(bc * f[q]));
       a.vel[3 * i + q] = u;
-      x[q] = a.xfx[3 * i + q] + (unsigned long long)__double2ll_rn(u * a.bc.dts[q]);
+      x[q] = a.xfx[3 * i + q] + (unsigned long long)__double2ll_rn(u * dts[q]);
       a.xfx[3 * i + q] = x[q];
     }
-    scatter_sorted(i, t, x[0], x[1], x[2], a.rank_fg, a.rank_cg, a.pos_fg, a.pos_cg, a.pos_fg64,
-                   a.pos_cg64);
-    rebuild = moved_beyond(a.ref[i], x[0], x[1], x[2], a.bc, a.thr2);
+    scatter_sorted(i, t, x[0], x[1], x[2], a.rank_fg, a.rank_cg, a.with_cg, a.pos_fg, a.pos_cg, a.fp64,
+                   a.pos_fg64, a.pos_cg64);
+    rebuild = moved_beyond(a.ref[i], x[0], x[1], x[2], a.s32, a.thr2);
   }
   if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&a.st->flags, F_REBUILD);
 }
@@ -397,13 +421,14 @@ __device__ double gamma_mt(double shape, unsigned long long key, unsigned long l
   return d;
 }
 // Bussi-Donadio-Parrinello (2007) velocity-rescaling factor for one step.
-__device__ double csvr_factor(double ke, const StepParams& sp, unsigned long long step) {
+__device__ double csvr_factor(double ke, double dt, double tau, double n_f, double kt,
+                              unsigned long long seed, unsigned long long step) {
   unsigned long long c = step << 20;
-  const double e = exp(-sp.dt / sp.tau);
-  const double r1 = gauss(sp.seed, c);
-  const double s = 2.0 * gamma_mt(0.5 * (sp.n_f - 1.0), sp.seed, c);
-  const double kn = ke + (1.0 - e) * (sp.kt / sp.n_f * (r1 * r1 + s) - ke) +
-                    2.0 * r1 * sqrt(e * (1.0 - e) * ke * sp.kt / sp.n_f);
+  const double e = exp(-dt / tau);
+  const double r1 = gauss(seed, c);
+  const double s = 2.0 * gamma_mt(0.5 * (n_f - 1.0), seed, c);
+  const double kn = ke + (1.0 - e) * (kt / n_f * (r1 * r1 + s) - ke) +
+                    2.0 * r1 * sqrt(e * (1.0 - e) * ke * kt / n_f);
   return sqrt(kn / ke);
 }
 
@@ -412,13 +437,14 @@ struct ReduceArgs {
   int nb_fg;
   const long long* part_cg;
   int nb_cg;
+  int with_cg;
   const long long* part_fin;
   int nb_fin;
 };
 
 // Sums of the fixed-point partials: out[0..kNQ) FG, [kNQ..2kNQ) CG, [2kNQ] KE,
 // [2kNQ+1] E_bonded.  Integer sums: exact and independent of order.
-__device__ void reduce_partials(const ReduceArgs& r, bool with_pairs, long long* out) {
+__device__ __forceinline__ void reduce_partials(ReduceArgs r, bool with_pairs, long long* out) {
   constexpr int NO = 2 * kNQ + 2;
   long long loc[NO];
 #pragma unroll
@@ -431,7 +457,7 @@ __device__ void reduce_partials(const ReduceArgs& r, bool with_pairs, long long*
     for (int b = threadIdx.x; b < r.nb_fg; b += blockDim.x)
 #pragma unroll
       for (int q = 0; q < kNQ; ++q) loc[q] += r.part_fg[b * kNQ + q];
-    if (r.part_cg)
+    if (r.with_cg)
       for (int b = threadIdx.x; b < r.nb_cg; b += blockDim.x)
 #pragma unroll
         for (int q = 0; q < kNQ; ++q) loc[kNQ + q] += r.part_cg[b * kNQ + q];
@@ -439,26 +465,31 @@ __device__ void reduce_partials(const ReduceArgs& r, bool with_pairs, long long*
   __shared__ long long sh[(1024 / 32) * NO];
   block_sum<long long, NO>(loc, sh);
   if (threadIdx.x == 0)
+#pragma unroll
     for (int q = 0; q < NO; ++q) out[q] = loc[q];
 }
 
 __global__ void k_thermo(ReduceArgs r, StepParams sp, DevState* st) {
   __shared__ long long tot[2 * kNQ + 2];
   const bool ev = st->ev != 0;
-  reduce_partials(r, ev, tot);
+  const ReduceArgs rr = r;
+  reduce_partials(rr, ev, tot);
   if (threadIdx.x != 0) return;
   const double ke = double(tot[2 * kNQ]) / kFix;
   double alpha = 1.0;
-  if (sp.t_target > 0.0 && ke > 0.0) alpha = csvr_factor(ke, sp, st->step);
+  if (sp.t_target > 0.0 && ke > 0.0)
+    alpha = csvr_factor(ke, sp.dt, sp.tau, sp.n_f, sp.kt, sp.seed, st->step);
   st->alpha = alpha;
   st->a = alpha;
   st->b = alpha + 1.0;
-  if (ev && sp.thermo) {
-    double* row = sp.thermo + (size_t)st->thermo_row * RELRES_THERMO_COLS;
+  double* thermo = sp.thermo;
+  if (ev && sp.thermo_every > 0) {
+    double* row = thermo + (size_t)st->thermo_row * RELRES_THERMO_COLS;
     row[0] = double(tot[0]) / kFix;
     row[1] = double(tot[kNQ]) / kFix;
     row[2] = double(tot[2 * kNQ + 1]) / kFix;
     row[3] = ke * alpha * alpha;
+#pragma unroll
     for (int q = 1; q < kNQ; ++q) row[3 + q] = double(tot[q] + tot[kNQ + q]) / kFix;
     st->thermo_row += 1;
   }
@@ -470,19 +501,21 @@ __global__ void k_thermo(ReduceArgs r, StepParams sp, DevState* st) {
   }
 }
 
-__global__ void k_reduce_out(ReduceArgs r, double* energy, double* virial) {
+__global__ void k_reduce_out(ReduceArgs r, double* energy, int with_e, double* virial, int with_w) {
   __shared__ long long tot[2 * kNQ + 2];
-  reduce_partials(r, true, tot);
+  const ReduceArgs rr = r;
+  reduce_partials(rr, true, tot);
   if (threadIdx.x != 0) return;
   const double efg = double(tot[0]) / kFix, ecg = double(tot[kNQ]) / kFix;
   const double eb = double(tot[2 * kNQ + 1]) / kFix;
-  if (energy) {
+  if (with_e) {
     energy[0] = efg;
     energy[1] = ecg;
     energy[2] = eb;
     energy[3] = efg + ecg + eb;
   }
-  if (virial)
+  if (with_w)
+#pragma unroll
     for (int q = 1; q < kNQ; ++q) virial[q - 1] = double(tot[q] + tot[kNQ + q]) / kFix;
 }
 
@@ -494,23 +527,25 @@ __global__ void k_set_ab(DevState* st, double a, double b) {
   st->ev = 0;
 }
 
+__global__ void k_flags_and(DevState* st, unsigned keep) { st->flags &= keep; }
+
 template <typename R>
 __global__ void k_finish_md(int n, const DevState* st, const double* vel_u,
                             const ForceT<R>* __restrict__ f_tot, const int* __restrict__ type,
-                            TypeConsts tc, const unsigned long long* __restrict__ xfx, BoxConsts bc,
-                            double* vel_out, double* __restrict__ pos_out) {
+                            const double* __restrict__ cdt, const unsigned long long* __restrict__ xfx,
+                            BoxConsts b, double* vel_out, double* __restrict__ pos_out) {
   const double ca = st->a, cb1 = st->b - 1.0;
+  const double a0 = b.l64_0, a1 = b.l64_1, a2 = b.l64_2, l0 = b.l0, l1 = b.l1, l2 = b.l2;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int t = type[i];
     R f[3];
     load_force(f_tot, i, f);
-    const R c = R(cb1 * tc.cdt[t]);
-    for (int q = 0; q < 3; ++q) {
-      vel_out[3 * i + q] = fma(ca, vel_u[3 * i + q], double(c * f[q]));
-      double x = from_fixed(xfx[3 * i + q], bc.l_2m64[q]);
-      if (x >= 1.0 / bc.inv_l[q]) x = 0.0;
-      pos_out[3 * i + q] = x;
-    }
+    const R c = R(cb1 * cdt[t]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) vel_out[3 * i + q] = fma(ca, vel_u[3 * i + q], double(c * f[q]));
+    pos_out[3 * i] = back_to_double(xfx[3 * i], a0, l0);
+    pos_out[3 * i + 1] = back_to_double(xfx[3 * i + 1], a1, l1);
+    pos_out[3 * i + 2] = back_to_double(xfx[3 * i + 2], a2, l2);
   }
 }
 
@@ -521,15 +556,6 @@ static int grid_for(int n) {
   return b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b);
 }
 
-static TypeConsts type_consts(const relres_ctx* c, double dt) {
-  TypeConsts t{};
-  for (int k = 0; k < c->n_types; ++k) {
-    t.mass[k] = c->mass_by_type[k];
-    t.cdt[k] = 0.5 * dt / c->mass_by_type[k] * kFtm2v;
-  }
-  return t;
-}
-
 static float trigger_thr2(const relres_ctx* c) {
   double skin = c->prm.skin;
   if (c->has_cg && c->n_h > 0 && c->skin_cg < skin) skin = c->skin_cg;
@@ -537,20 +563,33 @@ static float trigger_thr2(const relres_ctx* c) {
   return float(h * h);
 }
 
+static Sc3<float> s32_of(const relres_ctx* c) {
+  return Sc3<float>{float(c->box[0] / 4294967296.0), float(c->box[1] / 4294967296.0),
+                    float(c->box[2] / 4294967296.0)};
+}
+
+cudaError_t upload_type_consts(relres_ctx* c, double dt) {
+  for (int k = 0; k < c->n_types; ++k) c->h_cdt[k] = 0.5 * dt / c->mass_by_type[k] * kFtm2v;
+  return cudaMemcpyAsync(c->d_cdt, c->h_cdt.data(), sizeof(double) * c->n_types,
+                         cudaMemcpyHostToDevice, c->stream);
+}
+
+static Pos64* p64(relres_ctx* c, Pos64* p) { return c->fp64 ? p : static_cast<Pos64*>(c->d_dummy); }
+
 cudaError_t launch_convert(relres_ctx* c, const double* d_pos) {
   const BoxConsts b = box_consts(c, 0.0);
   k_convert<<<grid_for(c->n), kThreads, 0, c->stream>>>(
-      c->n, d_pos, c->d_type, c->d_xfx, b, c->have_lists, c->d_rank_fg,
-      (c->has_cg && c->n_h > 0) ? c->d_rank_cg : nullptr, c->d_pos_fg, c->d_pos_cg, c->d_pos_fg64,
-      c->d_pos_cg64, c->d_ref, trigger_thr2(c), c->d_state);
-  ++c->n_launches;
+      c->n, d_pos, c->d_type, c->d_xfx, b, c->have_lists ? 1 : 0, c->d_rank_fg, c->d_rank_cg,
+      (c->has_cg && c->n_h > 0) ? 1 : 0, c->d_pos_fg, c->d_pos_cg, c->fp64 ? 1 : 0, p64(c, c->d_pos_fg64),
+      p64(c, c->d_pos_cg64), c->d_ref, trigger_thr2(c), c->d_state);
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_check_cache(relres_ctx* c, const double* d_pos) {
   k_check_cache<<<grid_for(c->n), kThreads, 0, c->stream>>>(c->n, d_pos, c->d_xfx, box_consts(c, 0.0),
                                                             c->d_state);
-  ++c->n_launches;
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
@@ -560,72 +599,86 @@ static BondedArgs bonded_args(const relres_ctx* c) {
 }
 
 template <typename R>
-static cudaError_t launch_finish_t(relres_ctx* c, int ev_mode, double* d_forces_out, const double* vel,
-                                   double dt) {
+static cudaError_t launch_finish_t(relres_ctx* c, int ev_mode, double* d_forces_out, const double* vel) {
+  const int with_cg = (c->has_cg && c->n_h > 0) ? 1 : 0;
+  const double k = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
   FinishArgs<R> a{c->n,
                   static_cast<const ForceT<R>*>(c->d_f_fg),
-                  (c->has_cg && c->n_h > 0) ? static_cast<const ForceT<R>*>(c->d_f_cg) : nullptr,
+                  static_cast<const ForceT<R>*>(c->d_f_cg),
+                  with_cg,
                   c->d_type,
                   c->hyb_mask,
                   bonded_args(c),
                   c->d_xfx,
-                  box_consts(c, dt),
-                  vel,
-                  type_consts(c, dt),
+                  Sc3<R>{R(c->box[0] / k), R(c->box[1] / k), R(c->box[2] / k)},
+                  vel ? vel : static_cast<const double*>(c->d_dummy),
+                  vel ? 1 : 0,
+                  c->d_cdt,
+                  c->d_mass,
                   static_cast<ForceT<R>*>(c->d_f_tot),
-                  d_forces_out,
+                  d_forces_out ? d_forces_out : static_cast<double*>(c->d_dummy),
+                  d_forces_out ? 1 : 0,
                   c->d_part_fin,
                   c->d_state};
   k_finish<R><<<c->nb_fin, kThreads, 0, c->stream>>>(a, ev_mode);
-  ++c->n_launches;
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finish(relres_ctx* c, int ev_mode, double* d_forces_out, bool with_ke) {
   (void)with_ke;
-  return c->fp64 ? launch_finish_t<double>(c, ev_mode, d_forces_out, nullptr, 0.0)
-                 : launch_finish_t<float>(c, ev_mode, d_forces_out, nullptr, 0.0);
+  return c->fp64 ? launch_finish_t<double>(c, ev_mode, d_forces_out, nullptr)
+                 : launch_finish_t<float>(c, ev_mode, d_forces_out, nullptr);
 }
 
 cudaError_t launch_finish_step(relres_ctx* c, const StepParams& sp, const double* d_vel) {
-  return c->fp64 ? launch_finish_t<double>(c, 2, nullptr, d_vel, sp.dt)
-                 : launch_finish_t<float>(c, 2, nullptr, d_vel, sp.dt);
+  (void)sp;
+  return c->fp64 ? launch_finish_t<double>(c, 2, nullptr, d_vel)
+                 : launch_finish_t<float>(c, 2, nullptr, d_vel);
 }
 
 static ReduceArgs reduce_args(const relres_ctx* c) {
   const bool cg = c->has_cg && c->n_h > 0;
-  return ReduceArgs{c->d_part_fg, c->nb_fg, cg ? c->d_part_cg : nullptr, cg ? c->nb_cg : 0,
+  return ReduceArgs{c->d_part_fg, c->nb_fg, c->d_part_cg, cg ? c->nb_cg : 0, cg ? 1 : 0,
                     c->d_part_fin, c->nb_fin};
 }
 
 cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial) {
-  k_reduce_out<<<1, 1024, 0, c->stream>>>(reduce_args(c), d_energy, d_virial);
-  ++c->n_launches;
+  double* dd = static_cast<double*>(c->d_dummy);
+  k_reduce_out<<<1, 1024, 0, c->stream>>>(reduce_args(c), d_energy ? d_energy : dd, d_energy ? 1 : 0,
+                                          d_virial ? d_virial : dd, d_virial ? 1 : 0);
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
 template <typename R>
 static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d_vel) {
   const bool cg = c->has_cg && c->n_h > 0;
+  const BoxConsts b = box_consts(c, sp.dt);
   DriftArgs<R> a{c->n,
                  d_vel,
                  c->d_xfx,
                  static_cast<const ForceT<R>*>(c->d_f_tot),
                  c->d_type,
-                 type_consts(c, sp.dt),
-                 box_consts(c, sp.dt),
+                 c->d_cdt,
+                 b.dts0,
+                 b.dts1,
+                 b.dts2,
+                 s32_of(c),
                  c->d_rank_fg,
-                 cg ? c->d_rank_cg : nullptr,
+                 c->d_rank_cg,
+                 cg ? 1 : 0,
                  c->d_pos_fg,
                  c->d_pos_cg,
-                 c->d_pos_fg64,
-                 c->d_pos_cg64,
+                 c->fp64 ? 1 : 0,
+                 p64(c, c->d_pos_fg64),
+                 p64(c, c->d_pos_cg64),
                  c->d_ref,
                  trigger_thr2(c),
                  sp.thermo_every,
                  c->d_state};
   k_drift<R><<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(a);
-  ++c->n_launches;
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
@@ -634,38 +687,41 @@ cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel) {
 }
 
 cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp) {
-  k_thermo<<<1, 1024, 0, c->stream>>>(reduce_args(c), sp, c->d_state);
-  ++c->n_launches;
+  StepParams q = sp;
+  if (q.thermo == nullptr) {
+    q.thermo = static_cast<double*>(c->d_dummy);
+    q.thermo_every = 0;
+  }
+  k_thermo<<<1, 1024, 0, c->stream>>>(reduce_args(c), q, c->d_state);
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev) {
   (void)ev;
   k_set_ab<<<1, 1, 0, c->stream>>>(c->d_state, a, b);
-  ++c->n_launches;
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
-__global__ void k_flags_and(DevState* st, unsigned keep) { st->flags &= keep; }
-
 cudaError_t launch_flags_and(relres_ctx* c, unsigned keep) {
   k_flags_and<<<1, 1, 0, c->stream>>>(c->d_state, keep);
-  ++c->n_launches;
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, double dt) {
-  const BoxConsts b = box_consts(c, dt);
-  const TypeConsts t = type_consts(c, dt);
+  (void)dt;
+  const BoxConsts b = box_consts(c, 0.0);
   if (c->fp64)
     k_finish_md<double><<<grid_for(c->n), kThreads, 0, c->stream>>>(
-        c->n, c->d_state, d_vel, static_cast<const double*>(c->d_f_tot), c->d_type, t, c->d_xfx, b,
-        d_vel, d_pos);
+        c->n, c->d_state, d_vel, static_cast<const double*>(c->d_f_tot), c->d_type, c->d_cdt,
+        c->d_xfx, b, d_vel, d_pos);
   else
     k_finish_md<float><<<grid_for(c->n), kThreads, 0, c->stream>>>(
-        c->n, c->d_state, d_vel, static_cast<const float4*>(c->d_f_tot), c->d_type, t, c->d_xfx, b,
-        d_vel, d_pos);
-  ++c->n_launches;
+        c->n, c->d_state, d_vel, static_cast<const float4*>(c->d_f_tot), c->d_type, c->d_cdt,
+        c->d_xfx, b, d_vel, d_pos);
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 

@@ -22,16 +22,17 @@ namespace relres {
 
 struct GridArgs {
   int n0, n1, n2, ncell;
+  int valid;  // 0: the grid is not used (no CG interaction); pointers are stand-ins
   const int* rank_of;
   int* start;
   int* count;
 };
 
 static GridArgs grid_args(const Grid& g) {
-  return GridArgs{g.n[0], g.n[1], g.n[2], g.ncell, g.d_rank_of, g.d_start, g.d_count};
+  return GridArgs{g.n[0], g.n[1], g.n[2], g.ncell, 1, g.d_rank_of, g.d_start, g.d_count};
 }
 
-__device__ __forceinline__ int cell_rank(const GridArgs& g, int h0, int h1, int h2) {
+__device__ __forceinline__ int cell_rank(GridArgs g, int h0, int h1, int h2) {
   const int c0 = cell_of(h0, g.n0), c1 = cell_of(h1, g.n1), c2 = cell_of(h2, g.n2);
   return g.rank_of[(c0 * g.n1 + c1) * g.n2 + c2];
 }
@@ -45,7 +46,7 @@ __global__ void k_bin(int n, const unsigned* gate, const unsigned long long* __r
     const int cf = cell_rank(gf, h0, h1, h2);
     cell_fg[i] = cf;
     atomicAdd(&gf.count[cf], 1);
-    if (gc.count != nullptr && ((hyb_mask >> type[i]) & 1)) {
+    if (gc.valid && ((hyb_mask >> type[i]) & 1)) {
       const int cc = cell_rank(gc, h0, h1, h2);
       cell_cg[i] = cc;
       atomicAdd(&gc.count[cc], 1);
@@ -63,8 +64,12 @@ __global__ void k_scan(const unsigned* gate, GridArgs g0, GridArgs g1, DevState*
     st->tot_fg = 0;
     st->tot_cg = 0;
   }
-  const GridArgs g = blockIdx.x == 0 ? g0 : g1;
-  if (g.count == nullptr) return;
+  GridArgs g;
+  if (blockIdx.x == 0)
+    g = g0;
+  else
+    g = g1;
+  if (!g.valid) return;
   __shared__ int sh[1024 / 32];
   const int nt = blockDim.x;
   const int per = (g.ncell + nt - 1) / nt;
@@ -110,7 +115,7 @@ __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ t
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int cf = cell_fg[i];
     perm_fg[gf.start[cf] + atomicAdd(&gf.count[cf], 1)] = i;
-    if (gc.count != nullptr && ((hyb_mask >> type[i]) & 1)) {
+    if (gc.valid && ((hyb_mask >> type[i]) & 1)) {
       const int cc = cell_cg[i];
       perm_cg[gc.start[cc] + atomicAdd(&gc.count[cc], 1)] = i;
     }
@@ -122,11 +127,16 @@ __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ t
 __global__ void k_sort_cells(const unsigned* gate, GridArgs gf, GridArgs gc,
                              int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
   if (gate_closed(gate)) return;
-  const int total = gf.ncell + (gc.count ? gc.ncell : 0);
+  const GridArgs a = gf, b = gc;
+  const int total = a.ncell + (b.valid ? b.ncell : 0);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const bool fg = t < gf.ncell;
-    const GridArgs& g = fg ? gf : gc;
-    const int c = fg ? t : t - gf.ncell;
+    const bool fg = t < a.ncell;
+    GridArgs g;
+    if (fg)
+      g = a;
+    else
+      g = b;
+    const int c = fg ? t : t - a.ncell;
     int* perm = fg ? perm_fg : perm_cg;
     const int b = g.start[c], e = g.start[c + 1];
     for (int k = b + 1; k < e; ++k) {
@@ -147,7 +157,7 @@ __global__ void k_pack(int n, int n_h, const unsigned* gate, const unsigned long
                        const int* __restrict__ perm_cg, int* __restrict__ rank_fg,
                        int* __restrict__ rank_cg, int4* __restrict__ pos_fg,
                        int4* __restrict__ pos_cg, Pos64* __restrict__ pos_fg64,
-                       Pos64* __restrict__ pos_cg64, int4* __restrict__ ref) {
+                       Pos64* __restrict__ pos_cg64, int fp64, int4* __restrict__ ref) {
   if (gate_closed(gate)) return;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const int i = perm_fg[s];
@@ -157,13 +167,13 @@ __global__ void k_pack(int n, int n_h, const unsigned* gate, const unsigned long
     const int4 h = make_int4(hi32(x), hi32(y), hi32(z), t);
     pos_fg[s] = h;
     ref[i] = h;
-    if (pos_fg64) pos_fg64[s] = Pos64{(long long)x, (long long)y, (long long)z, t};
-    if (s < n_h && perm_cg != nullptr) {
+    if (fp64) pos_fg64[s] = Pos64{(long long)x, (long long)y, (long long)z, t};
+    if (s < n_h) {
       const int j = perm_cg[s];
       const unsigned long long xj = xfx[3 * j], yj = xfx[3 * j + 1], zj = xfx[3 * j + 2];
       rank_cg[j] = s;
       pos_cg[s] = make_int4(hi32(xj), hi32(yj), hi32(zj), type[j]);
-      if (pos_cg64) pos_cg64[s] = Pos64{(long long)xj, (long long)yj, (long long)zj, type[j]};
+      if (fp64) pos_cg64[s] = Pos64{(long long)xj, (long long)yj, (long long)zj, type[j]};
     }
   }
 }
@@ -244,30 +254,36 @@ static int blocks_for(int n) {
 }
 
 cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
+  if (gate == nullptr) gate = c->d_open;
   const GridArgs gf = grid_args(c->gfg);
   GridArgs gc = grid_args(c->gcg);
-  if (!c->has_cg || c->n_h == 0) gc.count = nullptr;
+  if (!c->has_cg || c->n_h == 0) {
+    gc = gf;  // stand-in pointers, never used
+    gc.valid = 0;
+  }
+  Pos64* p64f = c->fp64 ? c->d_pos_fg64 : static_cast<Pos64*>(c->d_dummy);
+  Pos64* p64c = c->fp64 ? c->d_pos_cg64 : static_cast<Pos64*>(c->d_dummy);
   const int nb = blocks_for(c->n);
   k_bin<<<nb, kThreads, 0, c->stream>>>(c->n, gate, c->d_xfx, c->d_type, c->hyb_mask, gf, gc,
                                         c->d_cell_fg, c->d_cell_cg);
-  ++c->n_launches;
+  RELRES_LAUNCHED(c);
   k_scan<<<2, 1024, 0, c->stream>>>(gate, gf, gc, c->d_state);
-  ++c->n_launches;
+  RELRES_LAUNCHED(c);
   k_scatter<<<nb, kThreads, 0, c->stream>>>(c->n, gate, c->d_type, c->hyb_mask, gf, gc, c->d_cell_fg,
                                             c->d_cell_cg, c->d_perm_fg, c->d_perm_cg);
-  ++c->n_launches;
-  const int ncells = gf.ncell + (gc.count ? gc.ncell : 0);
+  RELRES_LAUNCHED(c);
+  const int ncells = gf.ncell + (gc.valid ? gc.ncell : 0);
   k_sort_cells<<<blocks_for(ncells), kThreads, 0, c->stream>>>(gate, gf, gc, c->d_perm_fg, c->d_perm_cg);
-  ++c->n_launches;
-  k_pack<<<nb, kThreads, 0, c->stream>>>(c->n, gc.count ? c->n_h : 0, gate, c->d_xfx, c->d_type,
-                                         c->d_perm_fg, gc.count ? c->d_perm_cg : nullptr, c->d_rank_fg,
-                                         c->d_rank_cg, c->d_pos_fg, c->d_pos_cg, c->d_pos_fg64,
-                                         c->d_pos_cg64, c->d_ref);
-  ++c->n_launches;
+  RELRES_LAUNCHED(c);
+  k_pack<<<nb, kThreads, 0, c->stream>>>(c->n, gc.valid ? c->n_h : 0, gate, c->d_xfx, c->d_type,
+                                         c->d_perm_fg, c->d_perm_cg, c->d_rank_fg, c->d_rank_cg,
+                                         c->d_pos_fg, c->d_pos_cg, p64f, p64c, c->fp64 ? 1 : 0, c->d_ref);
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
+  if (gate == nullptr) gate = c->d_open;
   const float s0 = float(c->box[0] / 4294967296.0), s1 = float(c->box[1] / 4294967296.0),
               s2 = float(c->box[2] / 4294967296.0);
   DevState* st = c->d_state;
@@ -277,7 +293,7 @@ cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
                c->d_excl_off, c->d_excl_idx, c->cap_fg, c->d_nbr_fg, c->d_cnt_fg, &st->max_fg,
                &st->tot_fg, &st->flags, F_OVERFLOW_FG};
     k_list<<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(gate, a);
-    ++c->n_launches;
+    RELRES_LAUNCHED(c);
   }
   if (c->has_cg && c->n_h > 0) {
     const double rl = c->rlist_cg_cut + c->skin_cg;
@@ -285,7 +301,7 @@ cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
                c->d_excl_off, c->d_excl_idx, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg, &st->max_cg,
                &st->tot_cg, &st->flags, F_OVERFLOW_CG};
     k_list<<<(c->n_h + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(gate, a);
-    ++c->n_launches;
+    RELRES_LAUNCHED(c);
   }
   return cudaGetLastError();
 }

@@ -126,7 +126,7 @@ __device__ __forceinline__ bool cg_term(const PairTab<R>& T, R r2, R& fr, R& ep)
 }
 
 template <typename R, bool CG, bool EV>
-__device__ __forceinline__ void pair_body(const PairArgs<R>& a, const PairTab<R>* tab) {
+__device__ __forceinline__ void pair_body(PairArgs<R> a, const PairTab<R>* tab) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   R fx = R(0), fy = R(0), fz = R(0);
   R acc[kNQ];
@@ -212,14 +212,14 @@ static cudaError_t launch_pairs_t(relres_ctx* c, int ev_mode, int which) {
                   static_cast<const PairTab<R>*>(c->d_tab), c->n_types, sx, sy, sz,
                   static_cast<F*>(c->d_f_fg), c->d_part_fg, c->d_state};
     k_pair<R, false><<<(c->n + kThreads - 1) / kThreads, kThreads, smem, c->stream>>>(a, ev_mode);
-    ++c->n_launches;
+    RELRES_LAUNCHED(c);
   }
   if ((which & 2) && c->has_cg && c->n_h > 0) {
     PairArgs<R> a{c->n_h, pcg, c->d_nbr_cg, c->d_cnt_cg, c->d_perm_cg,
                   static_cast<const PairTab<R>*>(c->d_tab), c->n_types, sx, sy, sz,
                   static_cast<F*>(c->d_f_cg), c->d_part_cg, c->d_state};
     k_pair<R, true><<<(c->n_h + kThreads - 1) / kThreads, kThreads, smem, c->stream>>>(a, ev_mode);
-    ++c->n_launches;
+    RELRES_LAUNCHED(c);
   }
   return cudaGetLastError();
 }

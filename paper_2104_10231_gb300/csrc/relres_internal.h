@@ -130,6 +130,7 @@ struct relres_ctx {
   void* d_tab = nullptr;  // PairTab<float or double>[n_types^2]
   double* d_cdt = nullptr;   // per type: (dt/2m) * ftm2v  (set per step call)
   double* d_mass = nullptr;  // per type mass
+  std::vector<double> h_cdt = std::vector<double>(RELRES_MAX_TYPES, 0.0);
 
   // topology
   int n = 0, n_h = 0;
@@ -193,6 +194,8 @@ struct relres_ctx {
   long long* d_part_fin = nullptr;  // [blocks][2]: KE, E_bonded
   int nb_fg = 0, nb_cg = 0, nb_fin = 0;
   relres::DevState* d_state = nullptr;
+  unsigned* d_open = nullptr;  // device word that always reads F_REBUILD (un-gated launches)
+  void* d_dummy = nullptr;     // valid target for pointer arguments a kernel does not use
   relres::DevState* h_state = nullptr;  // pinned mirror
   double* d_out_scratch = nullptr;      // [16]
 
@@ -241,6 +244,7 @@ cudaError_t launch_finish(relres_ctx* c, int ev_mode, double* d_forces_out, bool
 cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial);
 
 // MD
+cudaError_t upload_type_consts(relres_ctx* c, double dt);
 cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel);
 cudaError_t launch_finish_step(relres_ctx* c, const StepParams& sp, const double* d_vel);
 cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp);
