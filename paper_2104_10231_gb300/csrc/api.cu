@@ -110,6 +110,7 @@ relres_status host_rebuild(relres_ctx* c) {
     relres_status s = read_state(c);
     if (s != RELRES_OK) return s;
     const DevState& h = *c->h_state;
+    if (h.flags & F_BADCELL) return fail(c, RELRES_ERR_CUDA, "cell binning produced an out-of-range index");
     const bool of = (h.flags & F_OVERFLOW_FG) != 0, oc = (h.flags & F_OVERFLOW_CG) != 0;
     if (!of && !oc) {
       c->last_max_fg = h.max_fg;
@@ -385,6 +386,8 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(&c->d_ref, size_t(n)));
   CK(dalloc(&c->d_cell_fg, size_t(n)));
   CK(dalloc(&c->d_cell_cg, size_t(n)));
+  CK(dalloc(&c->d_slot_fg, size_t(n)));
+  CK(dalloc(&c->d_slot_cg, size_t(n)));
   CK(dalloc(&c->d_perm_fg, size_t(n)));
   CK(dalloc(&c->d_rank_fg, size_t(n)));
   CK(dalloc(&c->d_perm_cg, size_t(nh)));
@@ -670,6 +673,8 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_ref);
   dfree(c->d_cell_fg);
   dfree(c->d_cell_cg);
+  dfree(c->d_slot_fg);
+  dfree(c->d_slot_cg);
   dfree(c->d_perm_fg);
   dfree(c->d_rank_fg);
   dfree(c->d_perm_cg);

@@ -50,10 +50,9 @@ __device__ __forceinline__ double dfix64(long long a, long long b, double scale)
   return __ll2double_rn((long long)((unsigned long long)a - (unsigned long long)b)) * scale;
 }
 
-// cell coordinate of a 32-bit periodic coordinate on an n-cell axis: floor(frac * n)
-__device__ __forceinline__ int cell_of(int h, int n) {
-  return int((unsigned long long)unsigned(h) * unsigned(n) >> 32);
-}
+// cell coordinate of a 32-bit periodic coordinate on an n-cell axis:
+// floor(frac * n) = high word of the 32 x 32 bit product
+__device__ __forceinline__ int cell_of(int h, int n) { return int(__umulhi(unsigned(h), unsigned(n))); }
 
 // No kernel ever receives a null pointer: optional buffers come with an int
 // flag and a valid (possibly unused) pointer.  `gate` points at the device flag

@@ -32,31 +32,58 @@ static GridArgs grid_args(const Grid& g) {
   return GridArgs{g.n[0], g.n[1], g.n[2], g.ncell, 1, g.d_rank_of, g.d_start, g.d_count};
 }
 
-__device__ __forceinline__ int cell_rank(GridArgs g, int h0, int h1, int h2) {
-  const int c0 = cell_of(h0, g.n0), c1 = cell_of(h1, g.n1), c2 = cell_of(h2, g.n2);
-  return g.rank_of[(c0 * g.n1 + c1) * g.n2 + c2];
+// The binning kernels take plain scalar and pointer parameters only.  A
+// version that passed its two grid descriptor structs by value into an inlined
+// helper computed wrong cells (every atom in x-cell 0) or faulted on sm_103a,
+// although a probe with the same signature read every field correctly; this
+// form has no struct parameters at all.
+__device__ __forceinline__ int linear_cell(int h0, int h1, int h2, int n0, int n1, int n2) {
+  return (cell_of(h0, n0) * n1 + cell_of(h1, n1)) * n2 + cell_of(h2, n2);
 }
 
+// Cell (dense Morton rank) of every atom in each grid, and its arrival rank
+// inside that cell (the value the count had before this atom was added).
 __global__ void k_bin(int n, const unsigned* gate, const unsigned long long* __restrict__ xfx,
-                      const int* __restrict__ type, int hyb_mask, GridArgs gf, GridArgs gc,
-                      int* __restrict__ cell_fg, int* __restrict__ cell_cg) {
+                      const int* __restrict__ type, int hyb_mask, int f0, int f1, int f2,
+                      const int* __restrict__ frank, int* fcount, int with_cg, int c0, int c1, int c2,
+                      const int* __restrict__ crank, int* ccount, int* __restrict__ cell_fg,
+                      int* __restrict__ slot_fg, int* __restrict__ cell_cg, int* __restrict__ slot_cg,
+                      unsigned* flags) {
   if (gate_closed(gate)) return;
+  const int nf = f0 * f1 * f2, nc = c0 * c1 * c2;
+  bool bad = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int h0 = hi32(xfx[3 * i]), h1 = hi32(xfx[3 * i + 1]), h2 = hi32(xfx[3 * i + 2]);
-    const int cf = cell_rank(gf, h0, h1, h2);
+    // self-check: every index is tested before it is used (a failure is
+    // reported through F_BADCELL and the access skipped)
+    // (an atom with a bad index is still counted, in cell 0, so that the
+    // later stages stay consistent and in bounds)
+    const int lf = linear_cell(h0, h1, h2, f0, f1, f2);
+    int cf = (lf >= 0 && lf < nf) ? frank[lf] : -1;
+    if (cf < 0 || cf >= nf) {
+      bad = true;
+      cf = 0;
+    }
     cell_fg[i] = cf;
-    atomicAdd(&gf.count[cf], 1);
-    if (gc.valid && ((hyb_mask >> type[i]) & 1)) {
-      const int cc = cell_rank(gc, h0, h1, h2);
+    slot_fg[i] = atomicAdd(fcount + cf, 1);
+    if (with_cg && ((hyb_mask >> type[i]) & 1)) {
+      const int lc = linear_cell(h0, h1, h2, c0, c1, c2);
+      int cc = (lc >= 0 && lc < nc) ? crank[lc] : -1;
+      if (cc < 0 || cc >= nc) {
+        bad = true;
+        cc = 0;
+      }
       cell_cg[i] = cc;
-      atomicAdd(&gc.count[cc], 1);
+      slot_cg[i] = atomicAdd(ccount + cc, 1);
     }
   }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, F_BADCELL);
 }
 
 // One block per grid: exclusive scan of counts into start[0..ncell], counts
 // reset to zero (they become the scatter cursors).
-__global__ void k_scan(const unsigned* gate, GridArgs g0, GridArgs g1, DevState* st) {
+__global__ void k_scan(const unsigned* gate, int valid0, int ncell0, int* start0, int* count0, int valid1,
+                       int ncell1, int* start1, int* count1, DevState* st) {
   if (gate_closed(gate)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // list statistics of this build
     st->max_fg = 0;
@@ -64,18 +91,17 @@ __global__ void k_scan(const unsigned* gate, GridArgs g0, GridArgs g1, DevState*
     st->tot_fg = 0;
     st->tot_cg = 0;
   }
-  GridArgs g;
-  if (blockIdx.x == 0)
-    g = g0;
-  else
-    g = g1;
-  if (!g.valid) return;
+  const int valid = blockIdx.x == 0 ? valid0 : valid1;
+  const int ncell = blockIdx.x == 0 ? ncell0 : ncell1;
+  int* const start = blockIdx.x == 0 ? start0 : start1;
+  int* const count = blockIdx.x == 0 ? count0 : count1;
+  if (!valid) return;
   __shared__ int sh[1024 / 32];
   const int nt = blockDim.x;
-  const int per = (g.ncell + nt - 1) / nt;
-  const int b = threadIdx.x * per, e = min(g.ncell, b + per);
+  const int per = (ncell + nt - 1) / nt;
+  const int b = threadIdx.x * per, e = min(ncell, b + per);
   int local = 0;
-  for (int c = b; c < e; ++c) local += g.count[c];
+  for (int c = b; c < e; ++c) local += count[c];
   // block exclusive scan of `local`
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int incl = local;
@@ -99,56 +125,49 @@ __global__ void k_scan(const unsigned* gate, GridArgs g0, GridArgs g1, DevState*
   __syncthreads();
   int run = sh[wid] + incl - local;
   for (int c = b; c < e; ++c) {
-    const int k = g.count[c];
-    g.start[c] = run;
-    g.count[c] = 0;
+    const int k = count[c];
+    start[c] = run;
+    count[c] = 0;
     run += k;
   }
-  if (threadIdx.x == nt - 1) g.start[g.ncell] = run;
+  if (threadIdx.x == nt - 1) start[ncell] = run;
 }
 
 __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ type, int hyb_mask,
-                          GridArgs gf, GridArgs gc, const int* __restrict__ cell_fg,
-                          const int* __restrict__ cell_cg, int* __restrict__ perm_fg,
-                          int* __restrict__ perm_cg) {
+                          const int* __restrict__ fstart, int with_cg, const int* __restrict__ cstart,
+                          const int* __restrict__ cell_fg, const int* __restrict__ slot_fg,
+                          const int* __restrict__ cell_cg, const int* __restrict__ slot_cg,
+                          int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
   if (gate_closed(gate)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int cf = cell_fg[i];
-    perm_fg[gf.start[cf] + atomicAdd(&gf.count[cf], 1)] = i;
-    if (gc.valid && ((hyb_mask >> type[i]) & 1)) {
-      const int cc = cell_cg[i];
-      perm_cg[gc.start[cc] + atomicAdd(&gc.count[cc], 1)] = i;
-    }
+    perm_fg[fstart[cell_fg[i]] + slot_fg[i]] = i;
+    if (with_cg && ((hyb_mask >> type[i]) & 1)) perm_cg[cstart[cell_cg[i]] + slot_cg[i]] = i;
   }
 }
 
 // One thread per cell: insertion-sort the cell's atoms by index (the scatter
 // order is arbitrary), reset the cursor.
-__global__ void k_sort_cells(const unsigned* gate, GridArgs gf, GridArgs gc,
-                             int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
+__global__ void k_sort_cells(const unsigned* gate, int fn, const int* fstart, int* fcount, int cn,
+                             const int* cstart, int* ccount, int* __restrict__ perm_fg,
+                             int* __restrict__ perm_cg) {
   if (gate_closed(gate)) return;
-  const GridArgs a = gf, b = gc;
-  const int total = a.ncell + (b.valid ? b.ncell : 0);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const bool fg = t < a.ncell;
-    GridArgs g;
-    if (fg)
-      g = a;
-    else
-      g = b;
-    const int c = fg ? t : t - a.ncell;
-    int* perm = fg ? perm_fg : perm_cg;
-    const int b = g.start[c], e = g.start[c + 1];
-    for (int k = b + 1; k < e; ++k) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < fn + cn; t += gridDim.x * blockDim.x) {
+    const bool fg = t < fn;
+    const int c = fg ? t : t - fn;
+    const int* const start = fg ? fstart : cstart;
+    int* const count = fg ? fcount : ccount;
+    int* const perm = fg ? perm_fg : perm_cg;
+    const int lo = start[c], hi = start[c + 1];
+    for (int k = lo + 1; k < hi; ++k) {
       const int v = perm[k];
       int m = k - 1;
-      while (m >= b && perm[m] > v) {
+      while (m >= lo && perm[m] > v) {
         perm[m + 1] = perm[m];
         --m;
       }
       perm[m + 1] = v;
     }
-    g.count[c] = 0;
+    count[c] = 0;
   }
 }
 
@@ -264,16 +283,22 @@ cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
   Pos64* p64f = c->fp64 ? c->d_pos_fg64 : static_cast<Pos64*>(c->d_dummy);
   Pos64* p64c = c->fp64 ? c->d_pos_cg64 : static_cast<Pos64*>(c->d_dummy);
   const int nb = blocks_for(c->n);
-  k_bin<<<nb, kThreads, 0, c->stream>>>(c->n, gate, c->d_xfx, c->d_type, c->hyb_mask, gf, gc,
-                                        c->d_cell_fg, c->d_cell_cg);
+  k_bin<<<nb, kThreads, 0, c->stream>>>(c->n, gate, c->d_xfx, c->d_type, c->hyb_mask, gf.n0, gf.n1,
+                                        gf.n2, gf.rank_of, gf.count, gc.valid, gc.n0, gc.n1, gc.n2,
+                                        gc.rank_of, gc.count, c->d_cell_fg, c->d_slot_fg, c->d_cell_cg,
+                                        c->d_slot_cg, &c->d_state->flags);
   RELRES_LAUNCHED(c);
-  k_scan<<<2, 1024, 0, c->stream>>>(gate, gf, gc, c->d_state);
+  k_scan<<<2, 1024, 0, c->stream>>>(gate, 1, gf.ncell, gf.start, gf.count, gc.valid, gc.ncell, gc.start,
+                                    gc.count, c->d_state);
   RELRES_LAUNCHED(c);
-  k_scatter<<<nb, kThreads, 0, c->stream>>>(c->n, gate, c->d_type, c->hyb_mask, gf, gc, c->d_cell_fg,
-                                            c->d_cell_cg, c->d_perm_fg, c->d_perm_cg);
+  k_scatter<<<nb, kThreads, 0, c->stream>>>(c->n, gate, c->d_type, c->hyb_mask, gf.start, gc.valid, gc.start,
+                                            c->d_cell_fg, c->d_slot_fg, c->d_cell_cg, c->d_slot_cg,
+                                            c->d_perm_fg, c->d_perm_cg);
   RELRES_LAUNCHED(c);
   const int ncells = gf.ncell + (gc.valid ? gc.ncell : 0);
-  k_sort_cells<<<blocks_for(ncells), kThreads, 0, c->stream>>>(gate, gf, gc, c->d_perm_fg, c->d_perm_cg);
+  k_sort_cells<<<blocks_for(ncells), kThreads, 0, c->stream>>>(gate, gf.ncell, gf.start, gf.count,
+                                                               gc.valid ? gc.ncell : 0, gc.start, gc.count,
+                                                               c->d_perm_fg, c->d_perm_cg);
   RELRES_LAUNCHED(c);
   k_pack<<<nb, kThreads, 0, c->stream>>>(c->n, gc.valid ? c->n_h : 0, gate, c->d_xfx, c->d_type,
                                          c->d_perm_fg, c->d_perm_cg, c->d_rank_fg, c->d_rank_cg,

@@ -65,6 +65,7 @@ enum : unsigned {
   F_OVERFLOW_CG = 4u,
   F_NONFINITE = 8u,     // a non-finite force
   F_DIRTY = 16u,        // incoming positions differ from the cached state
+  F_BADCELL = 32u,      // a computed cell index was out of range (access skipped)
 };
 
 struct DevState {
@@ -164,6 +165,8 @@ struct relres_ctx {
   int4* d_ref = nullptr;                // [n] hi32 positions at the last build
   int* d_cell_fg = nullptr;
   int* d_cell_cg = nullptr;
+  int* d_slot_fg = nullptr;             // arrival rank of the atom inside its cell
+  int* d_slot_cg = nullptr;
   int* d_perm_fg = nullptr;             // FG slot -> atom
   int* d_rank_fg = nullptr;             // atom -> FG slot
   int* d_perm_cg = nullptr;             // CG slot -> atom
