@@ -247,6 +247,10 @@ relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda
     ce = cudaMemcpy(c->d_tab, c->fp64 ? static_cast<const void*>(c->tab_d.data())
                                       : static_cast<const void*>(c->tab_f.data()),
                     tb, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_tabd, sizeof(PairTab<double>) * c->tab_d.size());
+  if (ce == cudaSuccess)
+    ce = cudaMemcpy(c->d_tabd, c->tab_d.data(), sizeof(PairTab<double>) * c->tab_d.size(),
+                    cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMalloc(&c->d_state, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMemset(c->d_state, 0, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMalloc(&c->d_snap_state, sizeof(DevState));
@@ -380,6 +384,25 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(&c->d_bond_par, bp.size()));
   CK(dalloc(&c->d_angle_par, ap.size()));
   CK(dalloc(&c->d_dih_par, dp.size()));
+  std::vector<float> bfp(4 * (bp.size() / 2), 0.f), afp(8 * (ap.size() / 2), 0.f);
+  for (size_t k = 0; k < bp.size() / 2; ++k) {
+    bfp[4 * k] = float(bp[2 * k]);
+    bfp[4 * k + 1] = float(bp[2 * k + 1]);
+    bfp[4 * k + 2] = float(bp[2 * k + 1] - double(bfp[4 * k + 1]));
+  }
+  for (size_t k = 0; k < ap.size() / 2; ++k) {
+    const double t0 = ap[2 * k + 1], c0 = std::cos(t0), s0 = std::sin(t0);
+    afp[8 * k] = float(ap[2 * k]);
+    afp[8 * k + 1] = float(t0);
+    afp[8 * k + 2] = float(c0);
+    afp[8 * k + 3] = float(c0 - double(afp[8 * k + 2]));
+    afp[8 * k + 4] = float(s0);
+    afp[8 * k + 5] = float(s0 - double(afp[8 * k + 4]));
+  }
+  CK(dalloc(&c->d_bond_fpar, bfp.size()));
+  CK(dalloc(&c->d_angle_fpar, afp.size()));
+  CK(cudaMemcpy(c->d_bond_fpar, bfp.data(), sizeof(float) * bfp.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_angle_fpar, afp.data(), sizeof(float) * afp.size(), cudaMemcpyHostToDevice));
   CK(dalloc(&c->d_inc_off, ioff.size()));
   CK(dalloc(&c->d_inc, std::max<size_t>(1, iall.size())));
   CK(dalloc(&c->d_xfx, 3 * size_t(n)));
@@ -544,6 +567,7 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
     s = flush_timing(c);
     if (s != RELRES_OK) return s;
     const unsigned fl = c->h_state->flags;
+    if (fl & F_BADCELL) return fail(c, RELRES_ERR_CUDA, "cell binning produced an out-of-range index");
     if (fl & (F_OVERFLOW_FG | F_OVERFLOW_CG | F_NONFINITE)) {
       // roll back to the start of this block
       CK(cudaMemcpyAsync(c->d_xfx, c->d_snap_x, xb, cudaMemcpyDeviceToDevice, c->stream));
@@ -649,6 +673,7 @@ void relres_destroy(relres_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   dfree(c->d_tab);
+  dfree(c->d_tabd);
   dfree(c->d_cdt);
   dfree(c->d_mass);
   dfree(c->d_type);
@@ -661,6 +686,8 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_bond_par);
   dfree(c->d_angle_par);
   dfree(c->d_dih_par);
+  dfree(c->d_bond_fpar);
+  dfree(c->d_angle_fpar);
   dfree(c->d_inc_off);
   dfree(c->d_inc);
   dfree(c->d_vir_dummy);

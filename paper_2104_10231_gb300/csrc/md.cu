@@ -143,7 +143,58 @@ struct BondedArgs {
   const double* bond_par;   // k, r0
   const double* angle_par;  // k, theta0
   const double* dih_par;    // K1..K4
+  const float* bond_fpar;   // FP32 path: k, r0 (hi, lo), 0
+  const float* angle_fpar;  // FP32 path: k, theta0, cos theta0 (hi, lo), sin theta0 (hi, lo), 0, 0
 };
+
+// ---- float-float ("double-single") arithmetic for the FP32 bonded path.
+// A value is hi + lo with |lo| <= ulp(hi)/2.  The rounding intrinsics keep
+// the error-free transformations from being contracted into FMAs.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff ff_quick(float a, float b) {  // requires |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff t = ff_two_sum(a.hi, b.hi);
+  return ff_quick(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = fmaf(a.hi, b.hi, -p);
+  return ff_quick(p, __fadd_rn(e, __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi))));
+}
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  if (!(a.hi > 0.f)) return ff{0.f, 0.f};
+  const float r = sqrtf(a.hi);
+  const float p = __fmul_rn(r, r);
+  const float pe = fmaf(r, r, -p);
+  return ff_quick(r, __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo), __fmul_rn(2.f, r)));
+}
+__device__ __forceinline__ float ff_val(ff a) { return __fadd_rn(a.hi, a.lo); }
+// exact 64-bit fixed-point difference a - b, scaled to Angstrom
+__device__ __forceinline__ ff ff_fixed_diff(unsigned long long a, unsigned long long b, ff scale) {
+  const long long d = (long long)(a - b);
+  const float hi = __ll2float_rn(d);
+  const float lo = __ll2float_rn(d - __float2ll_rn(hi));
+  return ff_mul(ff_quick(hi, lo), scale);
+}
+__device__ __forceinline__ void ff_vec(const unsigned long long* x, int a, int b, ff s0, ff s1, ff s2, ff v[3]) {
+  v[0] = ff_fixed_diff(x[3 * a], x[3 * b], s0);
+  v[1] = ff_fixed_diff(x[3 * a + 1], x[3 * b + 1], s1);
+  v[2] = ff_fixed_diff(x[3 * a + 2], x[3 * b + 2], s2);
+}
+__device__ __forceinline__ ff ff_dot(const ff a[3], const ff b[3]) {
+  return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
+}
 
 __device__ __forceinline__ void dvec(const unsigned long long* x, int a, int b, Sc3<float> s, float d[3]) {
   d[0] = dfix32(hi32(x[3 * a]), hi32(x[3 * b]), s.s0);
@@ -239,6 +290,69 @@ __device__ __forceinline__ void bonded_term(BondedArgs B, const unsigned long lo
   }
 }
 
+// FP32 bonded term.  Bonds and angles sit near their minimum, where the
+// force is proportional to a small difference (r - r0, theta - theta0); those
+// differences are formed in float-float arithmetic from the exact 64-bit
+// fixed-point coordinate differences, so that the force keeps FP32 relative
+// accuracy.  theta - theta0 = atan2(|a x b| cos t0 - (a.b) sin t0,
+// (a.b) cos t0 + |a x b| sin t0) needs no division and no acos.  The
+// dihedral (no stiff minimum) stays in plain FP32.
+__device__ __forceinline__ void bonded_term_ff(BondedArgs B, const unsigned long long* xfx, ff q0, ff q1,
+                                               ff q2, Sc3<float> sc, int item, float f[3], float& e) {
+  const int kind = (item >> 30) & 3, role = (item >> 28) & 3, t = item & 0x0fffffff;
+  if (kind == 0) {
+    const int4 bd = B.bonds[t];
+    const float* P = B.bond_fpar + 4 * bd.z;
+    ff d[3];
+    ff_vec(xfx, bd.x, bd.y, q0, q1, q2, d);
+    const ff r = ff_sqrt(ff_dot(d, d));
+    const float dr = ff_val(ff_sub(r, ff{P[1], P[2]}));
+    const float rf = ff_val(r);
+    const float g = -2.f * P[0] * dr / rf;  // force on bd.x along d
+    const float sgn = role == 0 ? 1.f : -1.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) f[q] += sgn * g * ff_val(d[q]);
+    if (role == 0) e += P[0] * dr * dr;
+  } else if (kind == 1) {
+    const int4 an = B.angles[t];
+    const float* P = B.angle_fpar + 8 * an.w;
+    ff a[3], b[3];
+    ff_vec(xfx, an.x, an.y, q0, q1, q2, a);
+    ff_vec(xfx, an.z, an.y, q0, q1, q2, b);
+    const ff dot = ff_dot(a, b);
+    ff cr[3];
+    cr[0] = ff_sub(ff_mul(a[1], b[2]), ff_mul(a[2], b[1]));
+    cr[1] = ff_sub(ff_mul(a[2], b[0]), ff_mul(a[0], b[2]));
+    cr[2] = ff_sub(ff_mul(a[0], b[1]), ff_mul(a[1], b[0]));
+    const ff cn = ff_sqrt(ff_dot(cr, cr));
+    const ff c0{P[2], P[3]}, s0{P[4], P[5]};
+    const ff X = ff_sub(ff_mul(cn, c0), ff_mul(dot, s0));
+    const ff Y = ff_add(ff_mul(dot, c0), ff_mul(cn, s0));
+    const float dth = atan2f(ff_val(X), ff_val(Y));
+    float r1[3], r2[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      r1[q] = ff_val(a[q]);
+      r2[q] = ff_val(b[q]);
+    }
+    const float n1 = sqrtf(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+    const float n2 = sqrtf(r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2]);
+    const float c = ff_val(dot) / (n1 * n2);
+    float sn = ff_val(cn) / (n1 * n2);
+    if (sn < 1e-6f) sn = 1e-6f;
+    const float pref = 2.f * P[0] * dth / sn;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float fa = pref * (r2[q] / (n1 * n2) - c * r1[q] / (n1 * n1));
+      const float fb = pref * (r1[q] / (n1 * n2) - c * r2[q] / (n2 * n2));
+      f[q] += role == 0 ? fa : (role == 2 ? fb : -(fa + fb));
+    }
+    if (role == 0) e += P[0] * dth * dth;
+  } else {
+    bonded_term<float>(B, xfx, sc, item, f, e);
+  }
+}
+
 // ----------------------------------------------------------------- finish
 
 template <typename R>
@@ -275,6 +389,7 @@ struct FinishArgs {
   BondedArgs B;
   const unsigned long long* xfx;
   Sc3<R> sc;
+  float q0h, q0l, q1h, q1l, q2h, q2l;  // L / 2^64 per axis as float-float (FP32 path)
   const double* vel;   // u (half-step velocities) for the kinetic energy
   int with_ke;
   const double* cdt;   // per type: dt / (2 m) * ftm2v
@@ -306,7 +421,13 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mod
       f[2] += g[2];
     }
     R eb = R(0);
-    for (int k = B.inc_off[i]; k < B.inc_off[i + 1]; ++k) bonded_term<R>(B, a.xfx, sc, B.inc[k], f, eb);
+    if constexpr (std::is_same<R, float>::value) {
+      const ff q0{a.q0h, a.q0l}, q1{a.q1h, a.q1l}, q2{a.q2h, a.q2l};
+      for (int k = B.inc_off[i]; k < B.inc_off[i + 1]; ++k)
+        bonded_term_ff(B, a.xfx, q0, q1, q2, sc, B.inc[k], f, eb);
+    } else {
+      for (int k = B.inc_off[i]; k < B.inc_off[i + 1]; ++k) bonded_term<R>(B, a.xfx, sc, B.inc[k], f, eb);
+    }
     bad = !(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]));
     save_force(a.f_tot, i, f);
     if (a.with_out) {
@@ -327,11 +448,12 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mod
     if (ev) acc[1] = eb;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&a.st->flags, F_NONFINITE);
-  __shared__ R sh[(kThreads / 32) * 2];
-  block_sum<R, 2>(acc, sh);
+  double accd[2] = {double(acc[0]), double(acc[1])};
+  __shared__ double sh[(kThreads / 32) * 2];
+  block_sum<double, 2>(accd, sh);
   if (threadIdx.x == 0) {
-    a.partial[2 * blockIdx.x] = to_fix_sum(double(acc[0]));
-    a.partial[2 * blockIdx.x + 1] = to_fix_sum(double(acc[1]));
+    a.partial[2 * blockIdx.x] = to_fix_sum(accd[0]);
+    a.partial[2 * blockIdx.x + 1] = to_fix_sum(accd[1]);
   }
 }
 
@@ -594,8 +716,14 @@ cudaError_t launch_check_cache(relres_ctx* c, const double* d_pos) {
 }
 
 static BondedArgs bonded_args(const relres_ctx* c) {
-  return BondedArgs{c->d_inc_off, c->d_inc, c->d_bonds, c->d_angles, c->d_dihs, c->d_dih_type,
-                    c->d_bond_par, c->d_angle_par, c->d_dih_par};
+  return BondedArgs{c->d_inc_off,   c->d_inc,       c->d_bonds,     c->d_angles,   c->d_dihs,
+                    c->d_dih_type,  c->d_bond_par,  c->d_angle_par, c->d_dih_par,  c->d_bond_fpar,
+                    c->d_angle_fpar};
+}
+
+static void ff_split(double v, float* hi, float* lo) {
+  *hi = float(v);
+  *lo = float(v - double(*hi));
 }
 
 template <typename R>
@@ -611,6 +739,7 @@ static cudaError_t launch_finish_t(relres_ctx* c, int ev_mode, double* d_forces_
                   bonded_args(c),
                   c->d_xfx,
                   Sc3<R>{R(c->box[0] / k), R(c->box[1] / k), R(c->box[2] / k)},
+                  0.f, 0.f, 0.f, 0.f, 0.f, 0.f,
                   vel ? vel : static_cast<const double*>(c->d_dummy),
                   vel ? 1 : 0,
                   c->d_cdt,
@@ -620,6 +749,9 @@ static cudaError_t launch_finish_t(relres_ctx* c, int ev_mode, double* d_forces_
                   d_forces_out ? 1 : 0,
                   c->d_part_fin,
                   c->d_state};
+  ff_split(c->box[0] / 18446744073709551616.0, &a.q0h, &a.q0l);
+  ff_split(c->box[1] / 18446744073709551616.0, &a.q1h, &a.q1l);
+  ff_split(c->box[2] / 18446744073709551616.0, &a.q2h, &a.q2l);
   k_finish<R><<<c->nb_fin, kThreads, 0, c->stream>>>(a, ev_mode);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();

@@ -70,8 +70,10 @@ struct PairArgs {
   const int* cnt;
   const int* perm;
   const PairTab<R>* tab;
+  const PairTab<double>* tabd;  // FP64 table: energies of the FP32 path are evaluated in FP64
   int nt;
   R sx, sy, sz;
+  double sxd, syd, szd;  // L / 2^32 (FP32 path) for the FP64 energy
   typename std::conditional<std::is_same<R, float>::value, float4, double>::type* f_out;
   long long* partial;  // [gridDim.x][kNQ]
   const DevState* st;
@@ -125,23 +127,38 @@ __device__ __forceinline__ bool cg_term(const PairTab<R>& T, R r2, R& fr, R& ep)
   return true;
 }
 
+__device__ __forceinline__ double dfix32d(int a, int b, double scale) {
+  return double(int(unsigned(a) - unsigned(b))) * scale;
+}
+
+// One slot's walk over its list.  Energies: FP32 path -> FP64 evaluation from
+// the exact coordinate differences (energy steps only); FP64 path -> FP64.
 template <typename R, bool CG, bool EV>
-__device__ __forceinline__ void pair_body(PairArgs<R> a, const PairTab<R>* tab) {
+__device__ __forceinline__ void pair_body(int nslots, const typename PosOf<R>::T* __restrict__ pos,
+                                          const int* __restrict__ nbr, const int* __restrict__ cnt,
+                                          const int* __restrict__ perm, const PairTab<R>* tab,
+                                          const PairTab<double>* tabd, int nt, R sx, R sy, R sz,
+                                          double sxd, double syd, double szd,
+                                          typename std::conditional<std::is_same<R, float>::value,
+                                                                    float4, double>::type* f_out,
+                                          long long* partial) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   R fx = R(0), fy = R(0), fz = R(0);
+  double e_acc = 0.0;
   R acc[kNQ];
 #pragma unroll
   for (int q = 0; q < kNQ; ++q) acc[q] = R(0);
-  if (s < a.nslots) {
-    const auto pi = a.pos[s];
-    const PairTab<R>* trow = tab + ptype(pi) * a.nt;
-    const int m = a.cnt[s];
-    const int* nb = a.nbr + s;
+  if (s < nslots) {
+    const auto pi = pos[s];
+    const PairTab<R>* trow = tab + ptype(pi) * nt;
+    const PairTab<double>* trowd = tabd + ptype(pi) * nt;
+    const int m = cnt[s];
+    const int* nb = nbr + s;
     for (int k = 0; k < m; ++k) {
-      const int j = __ldg(nb + (size_t)k * a.nslots);
-      const auto pj = load_pos(a.pos, j);
+      const int j = __ldg(nb + (size_t)k * nslots);
+      const auto pj = load_pos(pos, j);
       R dx, dy, dz;
-      delta(pi, pj, a.sx, a.sy, a.sz, dx, dy, dz);
+      delta(pi, pj, sx, sy, sz, dx, dy, dz);
       const R r2 = dx * dx + dy * dy + dz * dz;
       const PairTab<R>& T = trow[ptype(pj)];
       R fr, ep;
@@ -151,7 +168,7 @@ __device__ __forceinline__ void pair_body(PairArgs<R> a, const PairTab<R>* tab) 
         fy += fr * dy;
         fz += fr * dz;
         if (EV) {
-          acc[0] += ep;
+          if constexpr (std::is_same<R, double>::value) acc[0] += ep;
           acc[1] += fr * dx * dx;
           acc[2] += fr * dy * dy;
           acc[3] += fr * dz * dz;
@@ -160,44 +177,73 @@ __device__ __forceinline__ void pair_body(PairArgs<R> a, const PairTab<R>* tab) 
           acc[6] += fr * dy * dz;
         }
       }
+      if constexpr (EV && std::is_same<R, float>::value) {
+        const double ex = dfix32d(pi.x, pj.x, sxd), ey = dfix32d(pi.y, pj.y, syd),
+                     ez = dfix32d(pi.z, pj.z, szd);
+        double frd, epd;
+        const PairTab<double>& Td = trowd[ptype(pj)];
+        if (CG ? cg_term<double, true>(Td, ex * ex + ey * ey + ez * ez, frd, epd)
+               : fg_term<double, true>(Td, ex * ex + ey * ey + ez * ez, frd, epd))
+          e_acc += epd;
+      }
     }
-    store_force(a.f_out, a.perm[s], fx, fy, fz);
+    store_force(f_out, perm[s], fx, fy, fz);
   }
   if (EV) {
-    __shared__ R sh[(kThreads / 32) * kNQ];
-    block_sum<R, kNQ>(acc, sh);
+    // per-thread sums are R (FP64 for the energy); the block sum is taken in FP64
+    double accd[kNQ];
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) accd[q] = double(acc[q]);
+    if constexpr (std::is_same<R, float>::value) accd[0] = e_acc;
+    __shared__ double sh[(kThreads / 32) * kNQ];
+    block_sum<double, kNQ>(accd, sh);
     if (threadIdx.x == 0) {
       // full lists: every pair was visited from both ends
 #pragma unroll
-      for (int q = 0; q < kNQ; ++q) a.partial[blockIdx.x * kNQ + q] = to_fix_sum(0.5 * double(acc[q]));
+      for (int q = 0; q < kNQ; ++q) partial[blockIdx.x * kNQ + q] = to_fix_sum(0.5 * accd[q]);
     }
   }
 }
 
 template <typename R, bool CG>
 __global__ void __launch_bounds__(kThreads) k_pair(PairArgs<R> a, int ev_mode) {
-  extern __shared__ unsigned char smem_raw[];
-  PairTab<R>* tab = reinterpret_cast<PairTab<R>*>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrow = a.nt * a.nt;
-  const int words = nrow * int(sizeof(PairTab<R>) / sizeof(int));
-  const int* src = reinterpret_cast<const int*>(a.tab);
-  int* dst = reinterpret_cast<int*>(smem_raw);
-  for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+  PairTab<R>* tab = reinterpret_cast<PairTab<R>*>(smem_raw);
+  PairTab<double>* tabd = reinterpret_cast<PairTab<double>*>(
+      smem_raw + ((sizeof(PairTab<R>) * nrow + 15) / 16) * 16);
+  {
+    const int words = nrow * int(sizeof(PairTab<R>) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(a.tab);
+    int* dst = reinterpret_cast<int*>(tab);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+  }
+  if constexpr (std::is_same<R, float>::value) {
+    const int words = nrow * int(sizeof(PairTab<double>) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(a.tabd);
+    int* dst = reinterpret_cast<int*>(tabd);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+  }
   __syncthreads();
   const bool ev = ev_mode == 1 || (ev_mode == 2 && a.st->ev);
   if (ev)
-    pair_body<R, CG, true>(a, tab);
+    pair_body<R, CG, true>(a.nslots, a.pos, a.nbr, a.cnt, a.perm, tab, tabd, a.nt, a.sx, a.sy, a.sz, a.sxd,
+                           a.syd, a.szd, a.f_out, a.partial);
   else
-    pair_body<R, CG, false>(a, tab);
+    pair_body<R, CG, false>(a.nslots, a.pos, a.nbr, a.cnt, a.perm, tab, tabd, a.nt, a.sx, a.sy, a.sz, a.sxd,
+                            a.syd, a.szd, a.f_out, a.partial);
 }
 
 template <typename R>
 static cudaError_t launch_pairs_t(relres_ctx* c, int ev_mode, int which) {
   using F = typename std::conditional<std::is_same<R, float>::value, float4, double>::type;
-  const R sx = R(c->box[0] / (std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0));
-  const R sy = R(c->box[1] / (std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0));
-  const R sz = R(c->box[2] / (std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0));
-  const size_t smem = sizeof(PairTab<R>) * c->n_types * c->n_types;
+  const double unit = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
+  const R sx = R(c->box[0] / unit), sy = R(c->box[1] / unit), sz = R(c->box[2] / unit);
+  const double sxd = c->box[0] / 4294967296.0, syd = c->box[1] / 4294967296.0,
+               szd = c->box[2] / 4294967296.0;
+  const int nrow = c->n_types * c->n_types;
+  size_t smem = ((sizeof(PairTab<R>) * nrow + 15) / 16) * 16;
+  if (std::is_same<R, float>::value) smem += sizeof(PairTab<double>) * nrow;
   const typename PosOf<R>::T* pfg;
   const typename PosOf<R>::T* pcg;
   if constexpr (std::is_same<R, float>::value) {
@@ -207,17 +253,17 @@ static cudaError_t launch_pairs_t(relres_ctx* c, int ev_mode, int which) {
     pfg = c->d_pos_fg64;
     pcg = c->d_pos_cg64;
   }
+  const PairTab<R>* tab = static_cast<const PairTab<R>*>(c->d_tab);
+  const PairTab<double>* tabd = static_cast<const PairTab<double>*>(c->d_tabd);
   if (which & 1) {
-    PairArgs<R> a{c->n, pfg, c->d_nbr_fg, c->d_cnt_fg, c->d_perm_fg,
-                  static_cast<const PairTab<R>*>(c->d_tab), c->n_types, sx, sy, sz,
-                  static_cast<F*>(c->d_f_fg), c->d_part_fg, c->d_state};
+    PairArgs<R> a{c->n, pfg, c->d_nbr_fg, c->d_cnt_fg, c->d_perm_fg, tab, tabd, c->n_types, sx, sy, sz,
+                  sxd, syd, szd, static_cast<F*>(c->d_f_fg), c->d_part_fg, c->d_state};
     k_pair<R, false><<<(c->n + kThreads - 1) / kThreads, kThreads, smem, c->stream>>>(a, ev_mode);
     RELRES_LAUNCHED(c);
   }
   if ((which & 2) && c->has_cg && c->n_h > 0) {
-    PairArgs<R> a{c->n_h, pcg, c->d_nbr_cg, c->d_cnt_cg, c->d_perm_cg,
-                  static_cast<const PairTab<R>*>(c->d_tab), c->n_types, sx, sy, sz,
-                  static_cast<F*>(c->d_f_cg), c->d_part_cg, c->d_state};
+    PairArgs<R> a{c->n_h, pcg, c->d_nbr_cg, c->d_cnt_cg, c->d_perm_cg, tab, tabd, c->n_types, sx, sy, sz,
+                  sxd, syd, szd, static_cast<F*>(c->d_f_cg), c->d_part_cg, c->d_state};
     k_pair<R, true><<<(c->n_h + kThreads - 1) / kThreads, kThreads, smem, c->stream>>>(a, ev_mode);
     RELRES_LAUNCHED(c);
   }

@@ -129,6 +129,7 @@ struct relres_ctx {
 
   // device tables
   void* d_tab = nullptr;  // PairTab<float or double>[n_types^2]
+  void* d_tabd = nullptr; // PairTab<double>[n_types^2] (energies of the FP32 path)
   double* d_cdt = nullptr;   // per type: (dt/2m) * ftm2v  (set per step call)
   double* d_mass = nullptr;  // per type mass
   std::vector<double> h_cdt = std::vector<double>(RELRES_MAX_TYPES, 0.0);
@@ -149,6 +150,8 @@ struct relres_ctx {
   double* d_bond_par = nullptr;   // k, r0 per type
   double* d_angle_par = nullptr;  // k, theta0 per type
   double* d_dih_par = nullptr;    // K1..K4 per type
+  float* d_bond_fpar = nullptr;   // FP32 path: k, r0 hi, r0 lo, 0 per type
+  float* d_angle_fpar = nullptr;  // FP32 path: k, theta0, cos hi/lo, sin hi/lo, 0, 0 per type
   int* d_inc_off = nullptr;   // incident terms per atom (CSR)
   int* d_inc = nullptr;       // (kind << 30) | (role << 28) | term
   long long* d_vir_dummy = nullptr;
