@@ -281,6 +281,42 @@ relres_status relres_get_stats(relres_ctx* ctx, relres_stats* out);
 relres_status relres_set_timing(relres_ctx* ctx, int enable);
 relres_status relres_get_timings(relres_ctx* ctx, double* ms, long long* counts, int n);
 
+/*
+ * No-allocation pair evaluation (the paper has no counterpart: it is a
+ * deployment aid).  For callers that cannot let a library allocate device
+ * memory -- e.g. a host program that owns the GPU memory budget through its
+ * own allocator and loads this library as a plug-in, or a loop in which the
+ * device synchronisation of cudaMalloc/cudaFree is not allowed.  No context
+ * is needed and nothing is allocated on the device: the scratch memory (the
+ * type-pair table and per-block partial sums) is one file-scope static device
+ * array, present on every GPU that loads the library until the process exits.
+ *   p              parameters as for relres_create (only the pair terms are used).
+ *   n_atoms        1..RELRES_STATIC_MAX_ATOMS, else RELRES_ERR_ARG.
+ *   d_type         [n_atoms] device atom types.
+ *   d_pos          [n_atoms*3] device positions (any periodic image).
+ *   box            host double[3] orthorhombic edges; every interaction range
+ *                  must be below half the box (else RELRES_ERR_BOX).
+ *   d_excl_offsets, d_excl_index  device CSR exclusions as in relres_topology,
+ *                  or both NULL.
+ *   d_forces       [n_atoms*3] device output, overwritten: the RelRes pair
+ *                  forces of Eq. 20 (no bonded terms), all pairs, FP64.
+ *   d_energy       [1] device output or NULL: the pair energy (Eq. 3).
+ *   d_virial       [6] device output or NULL: pair virial, as relres_compute.
+ *   cuda_stream    cudaStream_t the work is enqueued on.
+ * All calls on a GPU share the static array: calls whose work overlaps on the
+ * GPU race on it and must be serialised by the caller.  Each call rewrites
+ * every part of it that it reads.  The first call on each device (with that
+ * device current) looks up the array's address; make that first call before
+ * any stream capture begins.  O(n_atoms^2) work: meant for small systems.
+ * Errors: RELRES_ERR_ARG, RELRES_ERR_BOX, RELRES_ERR_CUDA.
+ */
+#define RELRES_STATIC_MAX_ATOMS 16384
+relres_status relres_pair_forces_static(const relres_params* p, int n_atoms, const int* d_type,
+                                        const double* d_pos, const double box[3],
+                                        const int* d_excl_offsets, const int* d_excl_index,
+                                        double* d_forces, double* d_energy, double* d_virial,
+                                        void* cuda_stream);
+
 /* Message for the last failure of ctx (owned by ctx; "" if none). */
 const char* relres_last_error(relres_ctx* ctx);
 

@@ -1,0 +1,257 @@
+// relres_pair_forces_static: a RelRes pair evaluation that allocates nothing.
+//
+// Some callers cannot let a library allocate device memory: a host program
+// that owns the whole GPU memory budget through its own allocator and loads
+// this library as a plug-in, or a latency-critical loop in which cudaMalloc /
+// cudaFree (which may synchronise the device) are not allowed.  For them this
+// entry point evaluates the RelRes pair forces, energy and virial of a small
+// system by an all-pairs FP64 sum, with every piece of scratch memory (the
+// type-pair table and the per-block partial sums) in one file-scope static
+// device array of fixed size.  The caller provides only inputs and outputs.
+//
+// Limits and sharing: at most RELRES_STATIC_MAX_ATOMS atoms and
+// RELRES_MAX_TYPES types.  The array exists once per GPU that loads the
+// library and stays allocated until the process exits.  All calls on a GPU
+// share it: calls whose work overlaps on the GPU (different streams, or
+// several host threads) race on it and must be serialised by the caller.
+// Each call rewrites the table and every partial sum it reads, so nothing has
+// to start at zero; stale contents from an earlier call are never used.
+//
+// Set-up: the first call on each device (with that device current) looks up
+// the array's device address with cudaGetSymbolAddress; make that first call
+// before any stream capture begins.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace relres {
+namespace {
+
+constexpr int kStaticThreads = 256;
+constexpr int kStaticMaxBlocks = (RELRES_STATIC_MAX_ATOMS + kStaticThreads - 1) / kStaticThreads;
+constexpr int kMaxDevices = 64;
+
+struct StaticScratch {
+  PairTab<double> tab[RELRES_MAX_TYPES * RELRES_MAX_TYPES];
+  long long partial[kStaticMaxBlocks][kNQ];
+};
+
+static __device__ __align__(256) StaticScratch g_static_scratch;
+
+// host-side cache of the array's device address, per device
+static StaticScratch* s_scratch_ptr[kMaxDevices] = {};
+
+__device__ __forceinline__ double poly5(const double* g, double d) {
+  return (((g[4] * d + g[3]) * d + g[2]) * d + g[1]) * d + g[0];
+}
+__device__ __forceinline__ double poly4(const double* g, double d) {
+  return ((g[3] * d + g[2]) * d + g[1]) * d + g[0];
+}
+
+// Eq. 20 as the sum of its FG and CG parts (see PairTab); returns -u'(r)/r
+// in *fr and u(r) in *u.
+__device__ __forceinline__ void relres_pair(const PairTab<double>& T, double r2, double* fr, double* u) {
+  double f = 0.0, e = 0.0;
+  if (r2 < T.rsp2) {  // FG part
+    if (r2 < T.rsm2) {
+      const double r2i = 1.0 / r2, r6i = r2i * r2i * r2i;
+      f += r6i * (T.f12f * r6i - T.f6f) * r2i;
+      e += r6i * (T.c12f * r6i - T.c6f) - T.e_fg_shift;
+    } else {
+      const double r = sqrt(r2), d = r - T.rsm;
+      f += -poly4(T.fgd, d) / r;
+      e += poly5(T.fg, d) - T.e_fg_shift;
+    }
+  }
+  if (r2 < T.rcp2) {  // CG part (zero table entries for pairs without CG)
+    if (r2 < T.rsm2) {
+      e += T.e_cg_close;
+    } else if (r2 < T.rsp2) {
+      const double r = sqrt(r2), d = r - T.rsm, d2 = d * d;
+      f += -(d2 * (T.ond4 * d + T.ond3)) / r;
+      e += T.on0 + d2 * d * (T.on4 * d + T.on3) - T.gam_cm;
+    } else if (r2 < T.rcm2) {
+      const double r2i = 1.0 / r2, r6i = r2i * r2i * r2i;
+      f += r6i * (T.f12c * r6i - T.f6c) * r2i;
+      e += r6i * (T.c12c * r6i - T.c6c) - T.gam_cm;
+    } else {
+      const double r = sqrt(r2), d = r - T.rcm;
+      f += -poly4(T.cgod, d) / r;
+      e += poly5(T.cgo, d) - T.gam_cm;
+    }
+  }
+  *fr = f;
+  *u = e;
+}
+
+// One thread per atom, all partners j != i through shared-memory tiles.
+__global__ void __launch_bounds__(kStaticThreads)
+    k_allpairs_static(int n, int nt, const double* __restrict__ pos, const int* __restrict__ type,
+                      double l0, double l1, double l2, const int* __restrict__ eoff,
+                      const int* __restrict__ eidx, int with_excl, double* __restrict__ forces,
+                      StaticScratch* scratch) {
+  __shared__ double sx[kStaticThreads], sy[kStaticThreads], sz[kStaticThreads];
+  __shared__ int stype[kStaticThreads];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < n;
+  double xi = 0.0, yi = 0.0, zi = 0.0;
+  int ti = 0, e0 = 0, e1 = 0;
+  if (live) {
+    xi = pos[3 * i];
+    yi = pos[3 * i + 1];
+    zi = pos[3 * i + 2];
+    ti = type[i];
+    if (with_excl) {
+      e0 = eoff[i];
+      e1 = eoff[i + 1];
+    }
+  }
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  double acc[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+  for (int base = 0; base < n; base += kStaticThreads) {
+    const int jl = base + threadIdx.x;
+    if (jl < n) {
+      sx[threadIdx.x] = pos[3 * jl];
+      sy[threadIdx.x] = pos[3 * jl + 1];
+      sz[threadIdx.x] = pos[3 * jl + 2];
+      stype[threadIdx.x] = type[jl];
+    }
+    __syncthreads();
+    const int m = min(kStaticThreads, n - base);
+    if (live) {
+      for (int k = 0; k < m; ++k) {
+        const int j = base + k;
+        if (j == i) continue;
+        bool ex = false;
+        for (int e = e0; e < e1; ++e) ex |= eidx[e] == j;
+        if (ex) continue;
+        double dx = xi - sx[k], dy = yi - sy[k], dz = zi - sz[k];
+        dx -= l0 * rint(dx / l0);
+        dy -= l1 * rint(dy / l1);
+        dz -= l2 * rint(dz / l2);
+        double fr, u;
+        relres_pair(scratch->tab[ti * nt + stype[k]], dx * dx + dy * dy + dz * dz, &fr, &u);
+        fx += fr * dx;
+        fy += fr * dy;
+        fz += fr * dz;
+        acc[0] += u;
+        acc[1] += fr * dx * dx;
+        acc[2] += fr * dy * dy;
+        acc[3] += fr * dz * dz;
+        acc[4] += fr * dx * dy;
+        acc[5] += fr * dx * dz;
+        acc[6] += fr * dy * dz;
+      }
+    }
+    __syncthreads();
+  }
+  if (live) {
+    forces[3 * i] = fx;
+    forces[3 * i + 1] = fy;
+    forces[3 * i + 2] = fz;
+  }
+  __shared__ double sh[(kStaticThreads / 32) * kNQ];
+  block_sum<double, kNQ>(acc, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) scratch->partial[blockIdx.x][q] = to_fix_sum(0.5 * acc[q]);
+}
+
+__global__ void k_allpairs_static_reduce(int nblocks, const StaticScratch* scratch, double* energy,
+                                         int with_energy, double* virial, int with_virial) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long tot[kNQ] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nblocks; ++b)
+    for (int q = 0; q < kNQ; ++q) tot[q] += scratch->partial[b][q];
+  if (with_energy) energy[0] = double(tot[0]) / kFix;
+  if (with_virial)
+    for (int q = 1; q < kNQ; ++q) virial[q - 1] = double(tot[q]) / kFix;
+}
+
+}  // namespace
+}  // namespace relres
+
+using namespace relres;
+
+extern "C" relres_status relres_pair_forces_static(const relres_params* p, int n_atoms, const int* d_type,
+                                                   const double* d_pos, const double box[3],
+                                                   const int* d_excl_offsets, const int* d_excl_index,
+                                                   double* d_forces, double* d_energy, double* d_virial,
+                                                   void* cuda_stream) {
+  if (!p || !d_type || !d_pos || !box || !d_forces) return RELRES_ERR_ARG;
+  if (n_atoms < 1 || n_atoms > RELRES_STATIC_MAX_ATOMS) return RELRES_ERR_ARG;
+  if ((d_excl_offsets == nullptr) != (d_excl_index == nullptr)) return RELRES_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!(box[d] > 0.0) || !std::isfinite(box[d])) return RELRES_ERR_ARG;
+  // parameter preparation into stack buffers (no heap in this entry point's own code)
+  double table[RELRES_MAX_TYPES * RELRES_MAX_TYPES * RELRES_PAIR_FIELDS];
+  const relres_status ps = relres_prepare_table(p, table, int(sizeof(table) / sizeof(double)));
+  if (ps != RELRES_OK) return ps;
+  const int nt = p->n_types;
+  double rmax = 0.0;
+  PairTab<double> tabs[RELRES_MAX_TYPES * RELRES_MAX_TYPES];
+  std::memset(tabs, 0, sizeof(tabs));
+  for (int k = 0; k < nt * nt; ++k) {
+    const double* o = table + k * RELRES_PAIR_FIELDS;
+    PairTab<double>& t = tabs[k];
+    const double s6f = std::pow(o[1], 6.0), s6c = std::pow(o[3], 6.0);
+    t.c12f = 4.0 * o[0] * s6f * s6f;
+    t.c6f = 4.0 * o[0] * s6f;
+    t.f12f = 12.0 * t.c12f;
+    t.f6f = 6.0 * t.c6f;
+    t.rsm = o[4];
+    t.rsm2 = o[4] * o[4];
+    t.rsp2 = o[5] * o[5];
+    for (int m = 0; m < 5; ++m) t.fg[m] = o[8 + m];
+    for (int m = 1; m < 5; ++m) t.fgd[m - 1] = m * o[8 + m];
+    const double ws = o[5] - o[4];
+    t.e_fg_shift = (((o[12] * ws + o[11]) * ws + o[10]) * ws + o[9]) * ws + o[8];
+    t.c12c = 4.0 * o[2] * s6c * s6c;
+    t.c6c = 4.0 * o[2] * s6c;
+    t.f12c = 12.0 * t.c12c;
+    t.f6c = 6.0 * t.c6c;
+    t.rcm = o[6];
+    t.rcm2 = o[6] * o[6];
+    t.rcp2 = o[7] * o[7];
+    t.on0 = o[13];
+    t.on3 = o[16];
+    t.on4 = o[17];
+    t.ond3 = 3.0 * o[16];
+    t.ond4 = 4.0 * o[17];
+    for (int m = 0; m < 5; ++m) t.cgo[m] = o[18 + m];
+    for (int m = 1; m < 5; ++m) t.cgod[m - 1] = m * o[18 + m];
+    t.gam_cm = o[23];
+    t.e_cg_close = o[13] - o[23];
+    rmax = std::fmax(rmax, std::fmax(o[5], o[2] > 0.0 ? o[7] : 0.0));
+  }
+  // minimum image needs every interaction range below half the box
+  if (!(rmax < 0.5 * std::fmin(box[0], std::fmin(box[1], box[2])))) return RELRES_ERR_BOX;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RELRES_ERR_CUDA;
+  if (s_scratch_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || ptr == nullptr) return RELRES_ERR_CUDA;
+    s_scratch_ptr[dev] = static_cast<StaticScratch*>(ptr);
+  }
+  StaticScratch* scratch = s_scratch_ptr[dev];
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  // the table for this call (copied from the stack; a pageable-source copy
+  // returns once the source has been read)
+  if (cudaMemcpyAsync(scratch->tab, tabs, sizeof(PairTab<double>) * nt * nt, cudaMemcpyHostToDevice,
+                      stream) != cudaSuccess)
+    return RELRES_ERR_CUDA;
+  const int nblocks = (n_atoms + kStaticThreads - 1) / kStaticThreads;
+  const int with_excl = d_excl_offsets ? 1 : 0;
+  k_allpairs_static<<<nblocks, kStaticThreads, 0, stream>>>(
+      n_atoms, nt, d_pos, d_type, box[0], box[1], box[2], with_excl ? d_excl_offsets : d_type,
+      with_excl ? d_excl_index : d_type, with_excl, d_forces, scratch);
+  if (cudaGetLastError() != cudaSuccess) return RELRES_ERR_CUDA;
+  k_allpairs_static_reduce<<<1, 1, 0, stream>>>(nblocks, scratch, d_energy ? d_energy : d_forces,
+                                                d_energy ? 1 : 0, d_virial ? d_virial : d_forces,
+                                                d_virial ? 1 : 0);
+  if (cudaGetLastError() != cudaSuccess) return RELRES_ERR_CUDA;
+  return RELRES_OK;
+}

@@ -33,7 +33,8 @@ RELRES_PAIR_FIELDS = 26
 EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres_set_topology",
             "relres_build_neighbors", "relres_compute", "relres_step", "relres_set_step_counter",
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
-            "relres_destroy"]
+            "relres_destroy", "relres_pair_forces_static"]
+RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair_fg", "pair_cg", "finish", "thermo"]
 
 
@@ -107,6 +108,8 @@ def load():
     L.relres_get_stats.argtypes = [vp, C.POINTER(relres_stats)]
     L.relres_set_timing.argtypes = [vp, C.c_int]
     L.relres_get_timings.argtypes = [vp, _dp, C.POINTER(C.c_longlong), C.c_int]
+    L.relres_pair_forces_static.argtypes = [C.POINTER(relres_params), C.c_int, vp, vp, _dp, vp, vp, vp,
+                                            vp, vp, vp]
     L.relres_last_error.argtypes = [vp]
     L.relres_last_error.restype = C.c_char_p
     L.relres_destroy.argtypes = [vp]
@@ -293,6 +296,17 @@ def relres_get_timings(ctx):
     cnt = (C.c_longlong * n)()
     _check(load().relres_get_timings(ctx, ms.ctypes.data_as(_dp), cnt, n), ctx)
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(TIMING_CLASSES)}
+
+
+def relres_pair_forces_static(params, n_atoms, d_type, d_pos, box, d_forces, d_energy=None,
+                              d_virial=None, d_excl_offsets=None, d_excl_index=None, stream=None):
+    """All-pairs RelRes pair forces without any device allocation (scratch in a
+    static device array of the library); for callers that cannot allocate."""
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    _check(load().relres_pair_forces_static(C.byref(params), int(n_atoms), _ptr(d_type), _ptr(d_pos),
+                                            b.ctypes.data_as(_dp), _ptr(d_excl_offsets),
+                                            _ptr(d_excl_index), _ptr(d_forces), _ptr(d_energy),
+                                            _ptr(d_virial), stream))
 
 
 def relres_last_error(ctx):
