@@ -290,13 +290,12 @@ __device__ __forceinline__ void bonded_term(BondedArgs B, const unsigned long lo
   }
 }
 
-// FP32 bonded term.  Bonds and angles sit near their minimum, where the
-// force is proportional to a small difference (r - r0, theta - theta0); those
-// differences are formed in float-float arithmetic from the exact 64-bit
-// fixed-point coordinate differences, so that the force keeps FP32 relative
-// accuracy.  theta - theta0 = atan2(|a x b| cos t0 - (a.b) sin t0,
-// (a.b) cos t0 + |a x b| sin t0) needs no division and no acos.  The
-// dihedral (no stiff minimum) stays in plain FP32.
+// FP32 bonded term.  Bonds sit near their minimum with a stiff spring, so
+// the force 2k (r - r0) needs r - r0 far below FP32 resolution: r is formed
+// in float-float arithmetic from the exact 64-bit fixed-point difference.
+// Angles use theta - theta0 = atan2(|a x b| cos t0 - (a.b) sin t0,
+// (a.b) cos t0 + |a x b| sin t0) in FP32 (no acos, no loss near theta0);
+// dihedrals (no stiff minimum) are plain FP32.
 __device__ __forceinline__ void bonded_term_ff(BondedArgs B, const unsigned long long* xfx, ff q0, ff q1,
                                                ff q2, Sc3<float> sc, int item, float f[3], float& e) {
   const int kind = (item >> 30) & 3, role = (item >> 28) & 3, t = item & 0x0fffffff;
@@ -314,37 +313,32 @@ __device__ __forceinline__ void bonded_term_ff(BondedArgs B, const unsigned long
     for (int q = 0; q < 3; ++q) f[q] += sgn * g * ff_val(d[q]);
     if (role == 0) e += P[0] * dr * dr;
   } else if (kind == 1) {
+    // FP32 suffices here: with the division-free form below the angle error
+    // stays near 1e-7 rad (force error ~2K 1e-7 / r), and no acos is needed
     const int4 an = B.angles[t];
     const float* P = B.angle_fpar + 8 * an.w;
-    ff a[3], b[3];
-    ff_vec(xfx, an.x, an.y, q0, q1, q2, a);
-    ff_vec(xfx, an.z, an.y, q0, q1, q2, b);
-    const ff dot = ff_dot(a, b);
-    ff cr[3];
-    cr[0] = ff_sub(ff_mul(a[1], b[2]), ff_mul(a[2], b[1]));
-    cr[1] = ff_sub(ff_mul(a[2], b[0]), ff_mul(a[0], b[2]));
-    cr[2] = ff_sub(ff_mul(a[0], b[1]), ff_mul(a[1], b[0]));
-    const ff cn = ff_sqrt(ff_dot(cr, cr));
-    const ff c0{P[2], P[3]}, s0{P[4], P[5]};
-    const ff X = ff_sub(ff_mul(cn, c0), ff_mul(dot, s0));
-    const ff Y = ff_add(ff_mul(dot, c0), ff_mul(cn, s0));
-    const float dth = atan2f(ff_val(X), ff_val(Y));
     float r1[3], r2[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      r1[q] = ff_val(a[q]);
-      r2[q] = ff_val(b[q]);
-    }
-    const float n1 = sqrtf(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
-    const float n2 = sqrtf(r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2]);
-    const float c = ff_val(dot) / (n1 * n2);
-    float sn = ff_val(cn) / (n1 * n2);
+    dvec(xfx, an.x, an.y, sc, r1);
+    dvec(xfx, an.z, an.y, sc, r2);
+    const float dot = r1[0] * r2[0] + r1[1] * r2[1] + r1[2] * r2[2];
+    const float cx = r1[1] * r2[2] - r1[2] * r2[1];
+    const float cy = r1[2] * r2[0] - r1[0] * r2[2];
+    const float cz = r1[0] * r2[1] - r1[1] * r2[0];
+    const float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+    const float c0 = P[2], s0 = P[4];
+    const float dth = atan2f(cn * c0 - dot * s0, dot * c0 + cn * s0);
+    const float q1 = r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2];
+    const float q2 = r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2];
+    const float inv12 = rsqrtf(q1 * q2);  // 1 / (|r1| |r2|)
+    const float c = dot * inv12;
+    float sn = cn * inv12;
     if (sn < 1e-6f) sn = 1e-6f;
     const float pref = 2.f * P[0] * dth / sn;
+    const float i11 = 1.f / q1, i22 = 1.f / q2;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const float fa = pref * (r2[q] / (n1 * n2) - c * r1[q] / (n1 * n1));
-      const float fb = pref * (r1[q] / (n1 * n2) - c * r2[q] / (n2 * n2));
+      const float fa = pref * (r2[q] * inv12 - c * r1[q] * i11);
+      const float fb = pref * (r1[q] * inv12 - c * r2[q] * i22);
       f[q] += role == 0 ? fa : (role == 2 ? fb : -(fa + fb));
     }
     if (role == 0) e += P[0] * dth * dth;
