@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "atom-steps/s RelRes vs FG-only LJ (same GB300, 1M atoms); pair-kernel % roofline"
 FALLBACK_HBM_GBS = 6800.0
 PAIR_SRC = os.path.join(ROOT, "paper_2104_10231_gb300", "csrc", "pair.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_fg_neopentane_1M.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_neopentane_1M.txt")
 
 
 def parse():
@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--n-mol", type=int, default=200_000)
     ap.add_argument("--equil", type=int, default=200, help="untimed equilibration steps")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--thermo-every", type=int, default=100,
+                    help="energy/virial/temperature row every this many timed steps (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fg-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -63,6 +65,7 @@ def workload_config(args, n_atoms, box):
                      "velocities; 64-bit fixed-point positions",
         "l2": "inputs larger than L2 (neighbour lists ~0.5 GB, state 64 MB)",
         "parallelism": "replicas only (one independent system per GPU)",
+        "thermo_every": args.thermo_every,
         "seed": 2104,
     }
 
@@ -147,14 +150,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_md_timed(torch, R, ctx, pos, vel, steps, dt, t_target, seed):
-    """K steps of relres_step bracketed by CUDA events on the context stream."""
+def run_md_timed(torch, R, ctx, pos, vel, steps, dt, t_target, seed, thermo_every):
+    """K steps of relres_step bracketed by CUDA events on the context stream,
+    with a thermo row (energies, virial, temperature) every `thermo_every`
+    steps."""
     stream = ctx.stream
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    rows = max(1, steps // thermo_every) if thermo_every > 0 else 1
+    thermo = torch.zeros((rows, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     e0.record(stream)
-    ctx.step(steps, dt, pos, vel, t_target=t_target, tau_fs=100.0, seed=seed)
+    ctx.step(steps, dt, pos, vel, t_target=t_target, tau_fs=100.0, seed=seed,
+             thermo_every=thermo_every if thermo_every > 0 else 0, d_thermo=thermo)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3
@@ -202,7 +210,7 @@ def ours(args):
         if dist:
             dist.barrier()
         with ClockSampler(local) as clk:
-            secs = run_md_timed(torch, R, ctx, pos, vel, args.steps, dt, temp, 9)
+            secs = run_md_timed(torch, R, ctx, pos, vel, args.steps, dt, temp, 9, args.thermo_every)
         st1 = ctx.stats()
         tim = ctx.timings()
         ctx.set_timing(False)
@@ -253,7 +261,7 @@ def ours(args):
             ctxf.set_timing(True)
             if dist:
                 dist.barrier()
-            secs_f = run_md_timed(torch, R, ctxf, posf, velf, args.steps, dt, temp, 9)
+            secs_f = run_md_timed(torch, R, ctxf, posf, velf, args.steps, dt, temp, 9, args.thermo_every)
             timf = ctxf.timings()
             stf = ctxf.stats()
             if dist:
@@ -262,21 +270,23 @@ def ours(args):
                 secs_f = float(t.item())
             ctxf.close()
         fg = {"value": world * n * args.steps / secs_f, "ms_per_step": secs_f / args.steps * 1e3,
-              "pair_fg_ms_per_launch": timf["pair_fg"][0] / max(1, timf["pair_fg"][1]),
+              "pair_ms_per_launch": timf["pair"][0] / max(1, timf["pair"][1]),
               "mean_list": stf["mean_fg"], "rebuilds": stf["n_builds"]}
     ctx_stats = st1
     ctx.close()
 
-    # roofline of the dominant kernel: the RelRes pair kernel over the FG list
-    fg_ms = tim["pair_fg"][0] / max(1, tim["pair_fg"][1])
-    entries = ctx_stats["mean_fg"] * n
-    alg_bytes = entries * 20.0 + n * 40.0  # 4 B index + 16 B gather per entry; per atom 16 B pos, 4 B count, 4 B slot map, 16 B force
-    achieved = alg_bytes / (fg_ms * 1e-3) / 1e9
+    # roofline of the dominant kernel: the RelRes pair kernel (FG and CG lists, one launch)
+    pair_ms = tim["pair"][0] / max(1, tim["pair"][1])
+    n_h = ctx_stats["n_hybrid"]
+    entries = ctx_stats["mean_fg"] * n + ctx_stats["mean_cg"] * n_h
+    # 4 B index + 16 B gather per entry; per slot 16 B position, 4 B count, 4 B slot map, 16 B force
+    alg_bytes = entries * 20.0 + (n + n_h) * 40.0
+    achieved = alg_bytes / (pair_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": recorded_traffic(),
-                "peak_source": peak_kind + " (hbm_gbs, copy)", "kernel": "k_pair<float, FG list>",
-                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": fg_ms}
+                "peak_source": peak_kind + " (hbm_gbs, copy)", "kernel": "k_pair<float> (FG + CG lists)",
+                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": pair_ms}
     kernel_ms = {k: round(v[0] / max(1, v[1]), 5) for k, v in tim.items()}
     kernel_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in tim.values())), 4) for k, v in tim.items()}
 

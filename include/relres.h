@@ -170,11 +170,10 @@ enum relres_timing_class {
   RELRES_T_DRIFT = 0,    /* kick + drift + sorted scatter + rebuild trigger */
   RELRES_T_REBUILD = 1,  /* binning, scan, scatter, in-cell sort, pack */
   RELRES_T_LISTS = 2,    /* FG and CG Verlet lists */
-  RELRES_T_PAIR_FG = 3,  /* RelRes pair kernel over the FG list */
-  RELRES_T_PAIR_CG = 4,  /* RelRes pair kernel over the CG list */
-  RELRES_T_FINISH = 5,   /* force sum + bonded terms + kinetic energy */
-  RELRES_T_THERMO = 6,   /* reductions + CSVR factor */
-  RELRES_T_NCLASS = 7
+  RELRES_T_PAIR = 3,     /* RelRes pair kernel over the FG and CG lists (one launch) */
+  RELRES_T_FINISH = 4,   /* force sum + bonded terms + kinetic energy */
+  RELRES_T_THERMO = 5,   /* reductions + CSVR factor */
+  RELRES_T_NCLASS = 6
 };
 
 /*

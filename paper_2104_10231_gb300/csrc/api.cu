@@ -88,10 +88,13 @@ relres_status read_state(relres_ctx* c) {
   return RELRES_OK;
 }
 
+// list capacity: a multiple of 8 (the lists are stored in chunks of 4), at
+// most the number of possible partners rounded up
 int round_cap(double x, int limit) {
   int v = int(std::ceil(x));
   v = (v + 7) / 8 * 8;
-  return std::max(8, std::min(v, std::max(8, limit)));
+  const int lim = (std::max(8, limit) + 7) / 8 * 8;
+  return std::max(8, std::min(v, lim));
 }
 
 relres_status alloc_lists(relres_ctx* c) {
@@ -181,8 +184,7 @@ relres_status forces_now(relres_ctx* c, int ev_mode, double* d_forces, double* d
     s = host_rebuild(c);
     if (s != RELRES_OK) return s;
   }
-  TIMED(RELRES_T_PAIR_FG, launch_pairs(c, ev_mode, 1));
-  if (c->has_cg && c->n_h > 0) TIMED(RELRES_T_PAIR_CG, launch_pairs(c, ev_mode, 2));
+  TIMED(RELRES_T_PAIR, launch_pairs(c, ev_mode == 1));
   TIMED(RELRES_T_FINISH, launch_finish(c, ev_mode, d_forces, false));
   if (ev_mode == 1) TIMED(RELRES_T_THERMO, launch_reduce_out(c, d_energy, d_virial));
   s = read_state(c);
@@ -557,8 +559,9 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
       TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel));
       TIMED(RELRES_T_REBUILD, launch_rebuild(c, gate));
       TIMED(RELRES_T_LISTS, launch_lists(c, gate));
-      TIMED(RELRES_T_PAIR_FG, launch_pairs(c, 2, 1));
-      if (c->has_cg && c->n_h > 0) TIMED(RELRES_T_PAIR_CG, launch_pairs(c, 2, 2));
+      // energy steps are known here: the device sets DevState::ev by the same rule
+      const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
+      TIMED(RELRES_T_PAIR, launch_pairs(c, ev_step));
       TIMED(RELRES_T_FINISH, launch_finish_step(c, sp, d_vel));
       TIMED(RELRES_T_THERMO, launch_thermo(c, sp));
     }

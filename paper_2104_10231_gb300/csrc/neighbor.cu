@@ -239,6 +239,10 @@ __global__ void __launch_bounds__(kThreads) k_list(const unsigned* gate, ListArg
   const int ny = axis_cells(cell_of(p.y, a.g.n1), a.g.n1, cy);
   const int nz = axis_cells(cell_of(p.z, a.g.n2), a.g.n2, cz);
   int count = 0;
+  // entries are stored in chunks of four (one 16-byte store per chunk):
+  // entry k of slot s at int (((k >> 2) * nslots + s) << 2) + (k & 3)
+  int4* const out4 = reinterpret_cast<int4*>(a.nbr) + s;
+  int4 buf = make_int4(s, s, s, s);
   for (int ix = 0; ix < nx; ++ix)
     for (int iy = 0; iy < ny; ++iy)
       for (int iz = 0; iz < nz; ++iz) {
@@ -257,11 +261,21 @@ __global__ void __launch_bounds__(kThreads) k_list(const unsigned* gate, ListArg
             for (int e = e0; e < e1; ++e) ex |= (a.excl_idx[e] == j);
             if (ex) continue;
           }
-          if (count < a.cap) a.nbr[(size_t)count * a.nslots + s] = t;
+          if (count < a.cap) {
+            const int q = count & 3;
+            buf.x = q == 0 ? t : buf.x;
+            buf.y = q == 1 ? t : buf.y;
+            buf.z = q == 2 ? t : buf.z;
+            buf.w = q == 3 ? t : buf.w;
+            if (q == 3) out4[size_t(count >> 2) * a.nslots] = buf;
+          }
           ++count;
         }
       }
-  a.cnt[s] = min(count, a.cap);
+  // the last partial chunk (its padding lanes hold earlier indices, never read as partners)
+  const int kept = min(count, a.cap);
+  if (kept & 3) out4[size_t(kept >> 2) * a.nslots] = buf;
+  a.cnt[s] = kept;
   atomicMax(a.max_out, count);
   atomicAdd(a.total_out, (unsigned long long)count);
   if (count > a.cap) atomicOr(a.flags, a.overflow_bit);

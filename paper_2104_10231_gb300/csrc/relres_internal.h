@@ -181,7 +181,7 @@ struct relres_ctx {
 
   // lists
   int cap_fg = 0, cap_cg = 0;
-  int* d_nbr_fg = nullptr;  // [cap_fg][n]   column-major: entry k of slot s at k*n + s
+  int* d_nbr_fg = nullptr;  // [cap_fg/4][n][4]: entry k of slot s at ((k/4)*n + s)*4 + k%4
   int* d_cnt_fg = nullptr;  // [n]
   int* d_nbr_cg = nullptr;  // [cap_cg][n_h]
   int* d_cnt_cg = nullptr;  // [n_h]
@@ -245,7 +245,8 @@ cudaError_t launch_lists(relres_ctx* c, const unsigned* gate);
 
 // pair and finish; ev_mode 0 = never, 1 = always, 2 = per step (DevState::ev)
 // which: 1 = FG-list kernel, 2 = CG-list kernel, 3 = both
-cudaError_t launch_pairs(relres_ctx* c, int ev_mode, int which = 3);
+// pair kernel over both lists in one launch; ev: energy and virial partials too
+cudaError_t launch_pairs(relres_ctx* c, bool ev, int which = 3);
 cudaError_t launch_finish(relres_ctx* c, int ev_mode, double* d_forces_out, bool with_ke);
 cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial);
 

@@ -35,7 +35,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
             "relres_destroy", "relres_pair_forces_static"]
 RELRES_STATIC_MAX_ATOMS = 16384
-TIMING_CLASSES = ["drift", "rebuild", "lists", "pair_fg", "pair_cg", "finish", "thermo"]
+TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo"]
 
 
 class RelresError(RuntimeError):
