@@ -15,7 +15,6 @@ using namespace relres;
 namespace {
 
 constexpr double kBoltz = 0.0019872042586408316;  // kcal/mol/K (R / 4184 J/kcal)
-constexpr int kBlockSteps = 100;                  // steps between host status checks
 
 relres_status fail(relres_ctx* c, relres_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -45,7 +44,6 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
-int blocks(int n) { return std::max(1, (n + 255) / 256); }
 
 unsigned long long morton3(unsigned x, unsigned y, unsigned z) {
   auto spread = [](unsigned v) {
@@ -184,8 +182,9 @@ relres_status forces_now(relres_ctx* c, int ev_mode, double* d_forces, double* d
     s = host_rebuild(c);
     if (s != RELRES_OK) return s;
   }
+  CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
   TIMED(RELRES_T_PAIR, launch_pairs(c, ev_mode == 1));
-  TIMED(RELRES_T_FINISH, launch_finish(c, ev_mode, d_forces, false));
+  TIMED(RELRES_T_FINISH, launch_finish(c, ev_mode == 1, d_forces, nullptr));
   if (ev_mode == 1) TIMED(RELRES_T_THERMO, launch_reduce_out(c, d_energy, d_virial));
   s = read_state(c);
   if (s != RELRES_OK) return s;
@@ -259,6 +258,10 @@ relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda
   if (ce == cudaSuccess) ce = cudaMallocHost(&c->h_state, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMalloc(&c->d_dummy, 256);
   if (ce == cudaSuccess) ce = cudaMemset(c->d_dummy, 0, 256);
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_acc, sizeof(long long) * kNAcc);
+  if (ce == cudaSuccess) ce = cudaMemset(c->d_acc, 0, sizeof(long long) * kNAcc);
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_draws, sizeof(double) * 2 * kBlockSteps);
+  if (ce == cudaSuccess) ce = cudaMemset(c->d_draws, 0, sizeof(double) * 2 * kBlockSteps);
   if (ce == cudaSuccess) ce = cudaMalloc(&c->d_open, sizeof(unsigned));
   if (ce == cudaSuccess) {
     const unsigned open = F_REBUILD;
@@ -370,9 +373,6 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   c->n_angles = t->n_angles;
   c->n_dih = t->n_dihedrals;
   const int nh = std::max(1, c->n_h);
-  c->nb_fg = blocks(n);
-  c->nb_cg = blocks(nh);
-  c->nb_fin = blocks(n);
   const size_t fb = size_t(n) * (c->fp64 ? 24 : 16);
   CK(dalloc(&c->d_type, n));
   CK(dalloc(&c->d_cdt, RELRES_MAX_TYPES));
@@ -431,9 +431,9 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_snap_f), fb));
   CK(dalloc(&c->d_snap_x, 3 * size_t(n)));
   CK(dalloc(&c->d_snap_v, 3 * size_t(n)));
-  CK(dalloc(&c->d_part_fg, size_t(c->nb_fg) * kNQ));
-  CK(dalloc(&c->d_part_cg, size_t(c->nb_cg) * kNQ));
-  CK(dalloc(&c->d_part_fin, size_t(c->nb_fin) * 2));
+  const size_t n_slots = 2 * size_t(c->n_bonds) + 3 * size_t(c->n_angles) + 4 * size_t(c->n_dih);
+  CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_tf),
+            std::max<size_t>(1, n_slots) * (c->fp64 ? 24 : 16)));
   CK(cudaMemcpy(c->d_type, c->h_type.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->d_mass, c->mass_by_type.data(), sizeof(double) * c->n_types, cudaMemcpyHostToDevice));
   CK(cudaMemset(c->d_cdt, 0, sizeof(double) * RELRES_MAX_TYPES));
@@ -546,6 +546,7 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
   }
   CK(upload_type_consts(c, dt_fs));
   CK(launch_set_ab(c, 1.0, 1.0, 0));
+  CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
   const unsigned* gate = &c->d_state->flags;
   const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
   int done = 0, retries = 0;
@@ -555,6 +556,7 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
     CK(cudaMemcpyAsync(c->d_snap_v, d_vel, vb, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_snap_f, c->d_f_tot, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_csvr_draws(c, sp, blk));
     for (int k = 0; k < blk; ++k) {
       TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel));
       TIMED(RELRES_T_REBUILD, launch_rebuild(c, gate));
@@ -562,8 +564,8 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
       // energy steps are known here: the device sets DevState::ev by the same rule
       const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
       TIMED(RELRES_T_PAIR, launch_pairs(c, ev_step));
-      TIMED(RELRES_T_FINISH, launch_finish_step(c, sp, d_vel));
-      TIMED(RELRES_T_THERMO, launch_thermo(c, sp));
+      TIMED(RELRES_T_FINISH, launch_finish(c, ev_step, nullptr, d_vel));
+      TIMED(RELRES_T_THERMO, launch_thermo(c, sp, k));
     }
     s = read_state(c);
     if (s != RELRES_OK) return s;
@@ -720,9 +722,9 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_f_fg);
   dfree(c->d_f_cg);
   dfree(c->d_f_tot);
-  dfree(c->d_part_fg);
-  dfree(c->d_part_cg);
-  dfree(c->d_part_fin);
+  dfree(c->d_tf);
+  dfree(c->d_acc);
+  dfree(c->d_draws);
   dfree(c->d_state);
   dfree(c->d_out_scratch);
   dfree(c->d_snap_x);

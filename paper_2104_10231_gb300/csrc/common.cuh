@@ -93,4 +93,10 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* sh) {
 
 __device__ __forceinline__ long long to_fix_sum(double v) { return __double2ll_rn(v * kFix); }
 
+// Integer accumulators: a block's FP64 sum is converted to 64-bit fixed point
+// and added with an integer atomic (exact, independent of order).
+__device__ __forceinline__ void acc_add(long long* acc, double v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)to_fix_sum(v));
+}
+
 }  // namespace relres

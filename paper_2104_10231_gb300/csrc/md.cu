@@ -134,8 +134,6 @@ __global__ void k_check_cache(int n, const double* __restrict__ pos,
 // ----------------------------------------------------------------- bonded
 
 struct BondedArgs {
-  const int* inc_off;
-  const int* inc;
   const int4* bonds;
   const int4* angles;
   const int4* dihs;
@@ -218,133 +216,138 @@ __device__ __forceinline__ void cross3(const R a[3], const R b[3], R c[3]) {
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// Force on the atom playing `role` in term `item`; adds the term energy when
-// role == 0.
+// ---- one bonded term, forces on all of its atoms.  A term is evaluated once,
+// by one thread, and its force on each atom (role 0..arity-1) goes to its own
+// scratch slot; the finish kernel gathers each atom's slots (no atomics).
+// Return value: the term energy.
+
 template <typename R>
-__device__ __forceinline__ void bonded_term(BondedArgs B, const unsigned long long* xfx, Sc3<R> sc,
-                                            int item, R f[3], R& e) {
-  const int kind = (item >> 30) & 3, role = (item >> 28) & 3, t = item & 0x0fffffff;
-  if (kind == 0) {
-    const int4 bd = B.bonds[t];
-    R d[3];
-    dvec(xfx, bd.x, bd.y, sc, d);
-    const R r = sqrt(dot3(d, d));
-    const R k = R(B.bond_par[2 * bd.z]), r0 = R(B.bond_par[2 * bd.z + 1]);
-    const R g = R(-2) * k * (r - r0) / r;  // force on bd.x along d
-    const R sgn = role == 0 ? R(1) : R(-1);
+__device__ __forceinline__ R bond_forces(const BondedArgs& B, const unsigned long long* xfx, Sc3<R> sc,
+                                         int t, R f[2][3]) {
+  const int4 bd = B.bonds[t];
+  R d[3];
+  dvec(xfx, bd.x, bd.y, sc, d);
+  const R r = sqrt(dot3(d, d));
+  const R k = R(B.bond_par[2 * bd.z]), r0 = R(B.bond_par[2 * bd.z + 1]);
+  const R g = R(-2) * k * (r - r0) / r;  // force on bd.x along d
 #pragma unroll
-    for (int q = 0; q < 3; ++q) f[q] += sgn * g * d[q];
-    if (role == 0) e += k * (r - r0) * (r - r0);
-  } else if (kind == 1) {
-    const int4 an = B.angles[t];
-    R r1[3], r2[3];
-    dvec(xfx, an.x, an.y, sc, r1);
-    dvec(xfx, an.z, an.y, sc, r2);
-    const R n1 = sqrt(dot3(r1, r1)), n2 = sqrt(dot3(r2, r2));
-    R c = dot3(r1, r2) / (n1 * n2);
-    c = c > R(1) ? R(1) : (c < R(-1) ? R(-1) : c);
-    const R th = acos(c);
-    R s = sqrt(R(1) - c * c);
-    if (s < R(1e-6)) s = R(1e-6);
-    const R k = R(B.angle_par[2 * an.w]), t0 = R(B.angle_par[2 * an.w + 1]);
-    const R pref = R(2) * k * (th - t0) / s;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const R fa = pref * (r2[q] / (n1 * n2) - c * r1[q] / (n1 * n1));
-      const R fb = pref * (r1[q] / (n1 * n2) - c * r2[q] / (n2 * n2));
-      f[q] += role == 0 ? fa : (role == 2 ? fb : -(fa + fb));
-    }
-    if (role == 0) e += k * (th - t0) * (th - t0);
-  } else {
-    const int4 dh = B.dihs[t];
-    const double* K = B.dih_par + 4 * B.dih_type[t];
-    R b1[3], b2[3], b3[3], m1[3], m2[3];
-    dvec(xfx, dh.y, dh.x, sc, b1);
-    dvec(xfx, dh.z, dh.y, sc, b2);
-    dvec(xfx, dh.w, dh.z, sc, b3);
-    cross3(b1, b2, m1);
-    cross3(b2, b3, m2);
-    const R nb2 = sqrt(dot3(b2, b2));
-    const R phi = atan2(nb2 * dot3(b1, m2), dot3(m1, m2));
-    const R k1 = R(K[0]), k2 = R(K[1]), k3 = R(K[2]), k4 = R(K[3]);
-    const R dE = R(0.5) * (-k1 * sin(phi) + R(2) * k2 * sin(R(2) * phi) - R(3) * k3 * sin(R(3) * phi) +
-                           R(4) * k4 * sin(R(4) * phi));
-    const R mm1 = dot3(m1, m1), mm2 = dot3(m2, m2);
-    const R p12 = dot3(b1, b2), p32 = dot3(b3, b2);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      R g;
-      if (role == 0)
-        g = -nb2 / mm1 * m1[q];
-      else if (role == 3)
-        g = nb2 / mm2 * m2[q];
-      else if (role == 1)
-        g = nb2 / mm1 * m1[q] + p12 / (mm1 * nb2) * m1[q] + p32 / (mm2 * nb2) * m2[q];
-      else
-        g = -nb2 / mm2 * m2[q] - p12 / (mm1 * nb2) * m1[q] - p32 / (mm2 * nb2) * m2[q];
-      f[q] -= dE * g;
-    }
-    if (role == 0)
-      e += R(0.5) * (k1 * (R(1) + cos(phi)) + k2 * (R(1) - cos(R(2) * phi)) +
-                     k3 * (R(1) + cos(R(3) * phi)) + k4 * (R(1) - cos(R(4) * phi)));
+  for (int q = 0; q < 3; ++q) {
+    f[0][q] = g * d[q];
+    f[1][q] = -f[0][q];
   }
+  return k * (r - r0) * (r - r0);
 }
 
-// FP32 bonded term.  Bonds sit near their minimum with a stiff spring, so
-// the force 2k (r - r0) needs r - r0 far below FP32 resolution: r is formed
-// in float-float arithmetic from the exact 64-bit fixed-point difference.
-// Angles use theta - theta0 = atan2(|a x b| cos t0 - (a.b) sin t0,
-// (a.b) cos t0 + |a x b| sin t0) in FP32 (no acos, no loss near theta0);
-// dihedrals (no stiff minimum) are plain FP32.
-__device__ __forceinline__ void bonded_term_ff(BondedArgs B, const unsigned long long* xfx, ff q0, ff q1,
-                                               ff q2, Sc3<float> sc, int item, float f[3], float& e) {
-  const int kind = (item >> 30) & 3, role = (item >> 28) & 3, t = item & 0x0fffffff;
-  if (kind == 0) {
-    const int4 bd = B.bonds[t];
-    const float* P = B.bond_fpar + 4 * bd.z;
-    ff d[3];
-    ff_vec(xfx, bd.x, bd.y, q0, q1, q2, d);
-    const ff r = ff_sqrt(ff_dot(d, d));
-    const float dr = ff_val(ff_sub(r, ff{P[1], P[2]}));
-    const float rf = ff_val(r);
-    const float g = -2.f * P[0] * dr / rf;  // force on bd.x along d
-    const float sgn = role == 0 ? 1.f : -1.f;
+template <typename R>
+__device__ __forceinline__ R angle_forces(const BondedArgs& B, const unsigned long long* xfx, Sc3<R> sc,
+                                          int t, R f[3][3]) {
+  const int4 an = B.angles[t];
+  R r1[3], r2[3];
+  dvec(xfx, an.x, an.y, sc, r1);
+  dvec(xfx, an.z, an.y, sc, r2);
+  const R n1 = sqrt(dot3(r1, r1)), n2 = sqrt(dot3(r2, r2));
+  R c = dot3(r1, r2) / (n1 * n2);
+  c = c > R(1) ? R(1) : (c < R(-1) ? R(-1) : c);
+  const R th = acos(c);
+  R s = sqrt(R(1) - c * c);
+  if (s < R(1e-6)) s = R(1e-6);
+  const R k = R(B.angle_par[2 * an.w]), t0 = R(B.angle_par[2 * an.w + 1]);
+  const R pref = R(2) * k * (th - t0) / s;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) f[q] += sgn * g * ff_val(d[q]);
-    if (role == 0) e += P[0] * dr * dr;
-  } else if (kind == 1) {
-    // FP32 suffices here: with the division-free form below the angle error
-    // stays near 1e-7 rad (force error ~2K 1e-7 / r), and no acos is needed
-    const int4 an = B.angles[t];
-    const float* P = B.angle_fpar + 8 * an.w;
-    float r1[3], r2[3];
-    dvec(xfx, an.x, an.y, sc, r1);
-    dvec(xfx, an.z, an.y, sc, r2);
-    const float dot = r1[0] * r2[0] + r1[1] * r2[1] + r1[2] * r2[2];
-    const float cx = r1[1] * r2[2] - r1[2] * r2[1];
-    const float cy = r1[2] * r2[0] - r1[0] * r2[2];
-    const float cz = r1[0] * r2[1] - r1[1] * r2[0];
-    const float cn = sqrtf(cx * cx + cy * cy + cz * cz);
-    const float c0 = P[2], s0 = P[4];
-    const float dth = atan2f(cn * c0 - dot * s0, dot * c0 + cn * s0);
-    const float q1 = r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2];
-    const float q2 = r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2];
-    const float inv12 = rsqrtf(q1 * q2);  // 1 / (|r1| |r2|)
-    const float c = dot * inv12;
-    float sn = cn * inv12;
-    if (sn < 1e-6f) sn = 1e-6f;
-    const float pref = 2.f * P[0] * dth / sn;
-    const float i11 = 1.f / q1, i22 = 1.f / q2;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float fa = pref * (r2[q] * inv12 - c * r1[q] * i11);
-      const float fb = pref * (r1[q] * inv12 - c * r2[q] * i22);
-      f[q] += role == 0 ? fa : (role == 2 ? fb : -(fa + fb));
-    }
-    if (role == 0) e += P[0] * dth * dth;
-  } else {
-    bonded_term<float>(B, xfx, sc, item, f, e);
+  for (int q = 0; q < 3; ++q) {
+    f[0][q] = pref * (r2[q] / (n1 * n2) - c * r1[q] / (n1 * n1));
+    f[2][q] = pref * (r1[q] / (n1 * n2) - c * r2[q] / (n2 * n2));
+    f[1][q] = -(f[0][q] + f[2][q]);
   }
+  return k * (th - t0) * (th - t0);
+}
+
+template <typename R>
+__device__ __forceinline__ R dihedral_forces(const BondedArgs& B, const unsigned long long* xfx, Sc3<R> sc,
+                                             int t, R f[4][3]) {
+  const int4 dh = B.dihs[t];
+  const double* K = B.dih_par + 4 * B.dih_type[t];
+  R b1[3], b2[3], b3[3], m1[3], m2[3];
+  dvec(xfx, dh.y, dh.x, sc, b1);
+  dvec(xfx, dh.z, dh.y, sc, b2);
+  dvec(xfx, dh.w, dh.z, sc, b3);
+  cross3(b1, b2, m1);
+  cross3(b2, b3, m2);
+  const R nb2 = sqrt(dot3(b2, b2));
+  const R phi = atan2(nb2 * dot3(b1, m2), dot3(m1, m2));
+  const R k1 = R(K[0]), k2 = R(K[1]), k3 = R(K[2]), k4 = R(K[3]);
+  const R dE = R(0.5) * (-k1 * sin(phi) + R(2) * k2 * sin(R(2) * phi) - R(3) * k3 * sin(R(3) * phi) +
+                         R(4) * k4 * sin(R(4) * phi));
+  const R mm1 = dot3(m1, m1), mm2 = dot3(m2, m2);
+  const R p12 = dot3(b1, b2), p32 = dot3(b3, b2);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    // gradient of phi with respect to each atom (Blondel & Karplus form)
+    const R g0 = -nb2 / mm1 * m1[q];
+    const R g3 = nb2 / mm2 * m2[q];
+    const R h = p12 / (mm1 * nb2) * m1[q] + p32 / (mm2 * nb2) * m2[q];
+    f[0][q] = -dE * g0;
+    f[1][q] = -dE * (-g0 + h);
+    f[2][q] = -dE * (-g3 - h);
+    f[3][q] = -dE * g3;
+  }
+  return R(0.5) * (k1 * (R(1) + cos(phi)) + k2 * (R(1) - cos(R(2) * phi)) + k3 * (R(1) + cos(R(3) * phi)) +
+                   k4 * (R(1) - cos(R(4) * phi)));
+}
+
+// FP32 bond.  Bonds sit near their minimum with a stiff spring, so the force
+// 2k (r - r0) needs r - r0 far below FP32 resolution: r is formed in
+// float-float arithmetic from the exact 64-bit fixed-point difference.
+__device__ __forceinline__ float bond_forces_ff(const BondedArgs& B, const unsigned long long* xfx, ff q0,
+                                                ff q1, ff q2, int t, float f[2][3]) {
+  const int4 bd = B.bonds[t];
+  const float* P = B.bond_fpar + 4 * bd.z;
+  ff d[3];
+  ff_vec(xfx, bd.x, bd.y, q0, q1, q2, d);
+  const ff r = ff_sqrt(ff_dot(d, d));
+  const float dr = ff_val(ff_sub(r, ff{P[1], P[2]}));
+  const float rf = ff_val(r);
+  const float g = -2.f * P[0] * dr / rf;  // force on bd.x along d
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    f[0][q] = g * ff_val(d[q]);
+    f[1][q] = -f[0][q];
+  }
+  return P[0] * dr * dr;
+}
+
+// FP32 angle through theta - theta0 = atan2(|a x b| cos t0 - (a.b) sin t0,
+// (a.b) cos t0 + |a x b| sin t0): no acos and no loss near theta0, so the
+// angle error stays near 1e-7 rad (force error ~2K 1e-7 / r).
+__device__ __forceinline__ float angle_forces_f32(const BondedArgs& B, const unsigned long long* xfx,
+                                                  Sc3<float> sc, int t, float f[3][3]) {
+  const int4 an = B.angles[t];
+  const float* P = B.angle_fpar + 8 * an.w;
+  float r1[3], r2[3];
+  dvec(xfx, an.x, an.y, sc, r1);
+  dvec(xfx, an.z, an.y, sc, r2);
+  const float dot = r1[0] * r2[0] + r1[1] * r2[1] + r1[2] * r2[2];
+  const float cx = r1[1] * r2[2] - r1[2] * r2[1];
+  const float cy = r1[2] * r2[0] - r1[0] * r2[2];
+  const float cz = r1[0] * r2[1] - r1[1] * r2[0];
+  const float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+  const float c0 = P[2], s0 = P[4];
+  const float dth = atan2f(cn * c0 - dot * s0, dot * c0 + cn * s0);
+  const float q1 = r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2];
+  const float q2 = r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2];
+  const float inv12 = rsqrtf(q1 * q2);  // 1 / (|r1| |r2|)
+  const float c = dot * inv12;
+  float sn = cn * inv12;
+  if (sn < 1e-6f) sn = 1e-6f;
+  const float pref = 2.f * P[0] * dth / sn;
+  const float i11 = 1.f / q1, i22 = 1.f / q2;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    f[0][q] = pref * (r2[q] * inv12 - c * r1[q] * i11);
+    f[2][q] = pref * (r1[q] * inv12 - c * r2[q] * i22);
+    f[1][q] = -(f[0][q] + f[2][q]);
+  }
+  return P[0] * dth * dth;
 }
 
 // ----------------------------------------------------------------- finish
@@ -373,6 +376,57 @@ __device__ __forceinline__ void save_force(double* f, int i, const double v[3]) 
 }
 
 template <typename R>
+struct BondedKArgs {
+  int nb, na, nd;  // bonds, angles, dihedrals: threads [0, nb), [nb, nb + na), [nb + na, nb + na + nd)
+  BondedArgs B;
+  const unsigned long long* xfx;
+  Sc3<R> sc;
+  float q0h, q0l, q1h, q1l, q2h, q2l;  // L / 2^64 per axis as float-float (FP32 path)
+  ForceT<R>* tf;  // slots: bonds 2 per term from 0, angles 3 per term from 2 nb, dihedrals 4 from 2 nb + 3 na
+  long long* acc;
+};
+
+template <int NR, typename R>
+__device__ __forceinline__ void save_slots(ForceT<R>* tf, size_t base, const R f[NR][3]) {
+#pragma unroll
+  for (int r = 0; r < NR; ++r) save_force(tf, int(base + r), f[r]);
+}
+
+template <typename R, bool EV>
+__global__ void __launch_bounds__(kThreads) k_bonded(BondedKArgs<R> a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  R e = R(0);
+  const Sc3<R> sc = a.sc;
+  if (t < a.nb) {
+    R f[2][3];
+    if constexpr (std::is_same<R, float>::value)
+      e = bond_forces_ff(a.B, a.xfx, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, t, f);
+    else
+      e = bond_forces<R>(a.B, a.xfx, sc, t, f);
+    save_slots<2, R>(a.tf, 2 * size_t(t), f);
+  } else if (t < a.nb + a.na) {
+    const int u = t - a.nb;
+    R f[3][3];
+    if constexpr (std::is_same<R, float>::value)
+      e = angle_forces_f32(a.B, a.xfx, sc, u, f);
+    else
+      e = angle_forces<R>(a.B, a.xfx, sc, u, f);
+    save_slots<3, R>(a.tf, 2 * size_t(a.nb) + 3 * size_t(u), f);
+  } else if (t < a.nb + a.na + a.nd) {
+    const int u = t - a.nb - a.na;
+    R f[4][3];
+    e = dihedral_forces<R>(a.B, a.xfx, sc, u, f);
+    save_slots<4, R>(a.tf, 2 * size_t(a.nb) + 3 * size_t(a.na) + 4 * size_t(u), f);
+  }
+  if (EV) {
+    double v[1] = {double(e)};
+    __shared__ double sh[kThreads / 32];
+    block_sum<double, 1>(v, sh);
+    if (threadIdx.x == 0) acc_add(a.acc + kAccEb, v[0]);
+  }
+}
+
+template <typename R>
 struct FinishArgs {
   int n;
   const ForceT<R>* f_fg;
@@ -380,10 +434,10 @@ struct FinishArgs {
   int with_cg;
   const int* type;
   int hyb_mask;
-  BondedArgs B;
-  const unsigned long long* xfx;
-  Sc3<R> sc;
-  float q0h, q0l, q1h, q1l, q2h, q2l;  // L / 2^64 per axis as float-float (FP32 path)
+  const int* inc_off;
+  const int* inc;
+  const ForceT<R>* tf;
+  int base1, base2;    // first slot of the angles, of the dihedrals
   const double* vel;   // u (half-step velocities) for the kinetic energy
   int with_ke;
   const double* cdt;   // per type: dt / (2 m) * ftm2v
@@ -391,16 +445,15 @@ struct FinishArgs {
   ForceT<R>* f_tot;
   double* f_out;       // FP64 copy in caller order
   int with_out;
-  long long* partial;  // [gridDim.x][2]: KE, E_bonded
+  long long* acc;
   DevState* st;
 };
 
+// Total force per atom: FG part + CG part + the slots of its bonded terms;
+// kinetic energy of u + c F for the thermostat.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mode) {
-  const bool ev = ev_mode == 1 || (ev_mode == 2 && a.st->ev);
-  const BondedArgs B = a.B;
-  const Sc3<R> sc = a.sc;
-  R acc[2] = {R(0), R(0)};
+__global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a) {
+  R ke = R(0);
   bool bad = false;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) {
@@ -414,13 +467,17 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mod
       f[1] += g[1];
       f[2] += g[2];
     }
-    R eb = R(0);
-    if constexpr (std::is_same<R, float>::value) {
-      const ff q0{a.q0h, a.q0l}, q1{a.q1h, a.q1l}, q2{a.q2h, a.q2l};
-      for (int k = B.inc_off[i]; k < B.inc_off[i + 1]; ++k)
-        bonded_term_ff(B, a.xfx, q0, q1, q2, sc, B.inc[k], f, eb);
-    } else {
-      for (int k = B.inc_off[i]; k < B.inc_off[i + 1]; ++k) bonded_term<R>(B, a.xfx, sc, B.inc[k], f, eb);
+    const int k1 = a.inc_off[i + 1];
+    for (int k = a.inc_off[i]; k < k1; ++k) {
+      const int item = a.inc[k];
+      const int kind = (item >> 30) & 3, role = (item >> 28) & 3, term = item & 0x0fffffff;
+      const int slot = kind == 0 ? 2 * term + role
+                                 : (kind == 1 ? a.base1 + 3 * term + role : a.base2 + 4 * term + role);
+      R g[3];
+      load_force(a.tf, slot, g);
+      f[0] += g[0];
+      f[1] += g[1];
+      f[2] += g[2];
     }
     bad = !(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]));
     save_force(a.f_tot, i, f);
@@ -437,17 +494,15 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a, int ev_mod
         const R v = R(a.vel[3 * i + q]) + c * f[q];
         v2 += v * v;
       }
-      acc[0] = R(0.5 * a.mass[t] * kMvv2e) * v2;
+      ke = R(0.5 * a.mass[t] * kMvv2e) * v2;
     }
-    if (ev) acc[1] = eb;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&a.st->flags, F_NONFINITE);
-  double accd[2] = {double(acc[0]), double(acc[1])};
-  __shared__ double sh[(kThreads / 32) * 2];
-  block_sum<double, 2>(accd, sh);
-  if (threadIdx.x == 0) {
-    a.partial[2 * blockIdx.x] = to_fix_sum(accd[0]);
-    a.partial[2 * blockIdx.x + 1] = to_fix_sum(accd[1]);
+  if (a.with_ke) {
+    double v[1] = {double(ke)};
+    __shared__ double sh[kThreads / 32];
+    block_sum<double, 1>(v, sh);
+    if (threadIdx.x == 0) acc_add(a.acc + kAccKe, v[0]);
   }
 }
 
@@ -536,79 +591,59 @@ __device__ double gamma_mt(double shape, unsigned long long key, unsigned long l
   }
   return d;
 }
-// Bussi-Donadio-Parrinello (2007) velocity-rescaling factor for one step.
-__device__ double csvr_factor(double ke, double dt, double tau, double n_f, double kt,
-                              unsigned long long seed, unsigned long long step) {
+// Bussi-Donadio-Parrinello (2007) velocity rescaling.  The two random
+// numbers of step `step` (a normal deviate r1 and a chi-square deviate s with
+// n_f - 1 degrees of freedom, drawn as twice a gamma(n_f/2 - 1/2) deviate)
+// depend only on the seed and the step, so a block of steps has them drawn
+// in parallel ahead of time.
+__device__ void csvr_draws(double n_f, unsigned long long seed, unsigned long long step, double& r1,
+                           double& s) {
   unsigned long long c = step << 20;
+  r1 = gauss(seed, c);
+  s = 2.0 * gamma_mt(0.5 * (n_f - 1.0), seed, c);
+}
+__device__ double csvr_alpha(double ke, double dt, double tau, double n_f, double kt, double r1, double s) {
   const double e = exp(-dt / tau);
-  const double r1 = gauss(seed, c);
-  const double s = 2.0 * gamma_mt(0.5 * (n_f - 1.0), seed, c);
   const double kn = ke + (1.0 - e) * (kt / n_f * (r1 * r1 + s) - ke) +
                     2.0 * r1 * sqrt(e * (1.0 - e) * ke * kt / n_f);
   return sqrt(kn / ke);
 }
 
-struct ReduceArgs {
-  const long long* part_fg;
-  int nb_fg;
-  const long long* part_cg;
-  int nb_cg;
-  int with_cg;
-  const long long* part_fin;
-  int nb_fin;
-};
-
-// Sums of the fixed-point partials: out[0..kNQ) FG, [kNQ..2kNQ) CG, [2kNQ] KE,
-// [2kNQ+1] E_bonded.  Integer sums: exact and independent of order.
-__device__ __forceinline__ void reduce_partials(ReduceArgs r, bool with_pairs, long long* out) {
-  constexpr int NO = 2 * kNQ + 2;
-  long long loc[NO];
-#pragma unroll
-  for (int q = 0; q < NO; ++q) loc[q] = 0;
-  for (int b = threadIdx.x; b < r.nb_fin; b += blockDim.x) {
-    loc[2 * kNQ] += r.part_fin[2 * b];
-    loc[2 * kNQ + 1] += r.part_fin[2 * b + 1];
-  }
-  if (with_pairs) {
-    for (int b = threadIdx.x; b < r.nb_fg; b += blockDim.x)
-#pragma unroll
-      for (int q = 0; q < kNQ; ++q) loc[q] += r.part_fg[b * kNQ + q];
-    if (r.with_cg)
-      for (int b = threadIdx.x; b < r.nb_cg; b += blockDim.x)
-#pragma unroll
-        for (int q = 0; q < kNQ; ++q) loc[kNQ + q] += r.part_cg[b * kNQ + q];
-  }
-  __shared__ long long sh[(1024 / 32) * NO];
-  block_sum<long long, NO>(loc, sh);
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int q = 0; q < NO; ++q) out[q] = loc[q];
+// Draws for the steps st->step + k, k < count (one thread each).
+__global__ void k_csvr_draws(double n_f, unsigned long long seed, int count, const DevState* st,
+                             double* draws) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  double r1, s;
+  csvr_draws(n_f, seed, st->step + (unsigned long long)k, r1, s);
+  draws[2 * k] = r1;
+  draws[2 * k + 1] = s;
 }
 
-__global__ void k_thermo(ReduceArgs r, StepParams sp, DevState* st) {
-  __shared__ long long tot[2 * kNQ + 2];
+// End of a step (one thread): thermostat factor from the kinetic energy,
+// thermo row on energy steps, counters, and the accumulators cleared for the
+// next step.  `draw` points at this step's (r1, s).
+__global__ void k_thermo(long long* acc, StepParams sp, DevState* st, const double* draw) {
   const bool ev = st->ev != 0;
-  const ReduceArgs rr = r;
-  reduce_partials(rr, ev, tot);
-  if (threadIdx.x != 0) return;
-  const double ke = double(tot[2 * kNQ]) / kFix;
+  const double ke = double(acc[kAccKe]) / kFix;
   double alpha = 1.0;
-  if (sp.t_target > 0.0 && ke > 0.0)
-    alpha = csvr_factor(ke, sp.dt, sp.tau, sp.n_f, sp.kt, sp.seed, st->step);
+  if (sp.t_target > 0.0 && ke > 0.0) alpha = csvr_alpha(ke, sp.dt, sp.tau, sp.n_f, sp.kt, draw[0], draw[1]);
   st->alpha = alpha;
   st->a = alpha;
   st->b = alpha + 1.0;
   double* thermo = sp.thermo;
   if (ev && sp.thermo_every > 0) {
     double* row = thermo + (size_t)st->thermo_row * RELRES_THERMO_COLS;
-    row[0] = double(tot[0]) / kFix;
-    row[1] = double(tot[kNQ]) / kFix;
-    row[2] = double(tot[2 * kNQ + 1]) / kFix;
+    row[0] = double(acc[kAccFg]) / kFix;
+    row[1] = double(acc[kAccCg]) / kFix;
+    row[2] = double(acc[kAccEb]) / kFix;
     row[3] = ke * alpha * alpha;
 #pragma unroll
-    for (int q = 1; q < kNQ; ++q) row[3 + q] = double(tot[q] + tot[kNQ + q]) / kFix;
+    for (int q = 1; q < kNQ; ++q) row[3 + q] = double(acc[kAccFg + q] + acc[kAccCg + q]) / kFix;
     st->thermo_row += 1;
   }
+#pragma unroll
+  for (int q = 0; q < kNAcc; ++q) acc[q] = 0;
   st->local_step += 1;
   st->step += 1;
   if (st->flags & F_REBUILD) {
@@ -617,13 +652,10 @@ __global__ void k_thermo(ReduceArgs r, StepParams sp, DevState* st) {
   }
 }
 
-__global__ void k_reduce_out(ReduceArgs r, double* energy, int with_e, double* virial, int with_w) {
-  __shared__ long long tot[2 * kNQ + 2];
-  const ReduceArgs rr = r;
-  reduce_partials(rr, true, tot);
-  if (threadIdx.x != 0) return;
-  const double efg = double(tot[0]) / kFix, ecg = double(tot[kNQ]) / kFix;
-  const double eb = double(tot[2 * kNQ + 1]) / kFix;
+// Energies and virial of relres_compute (one thread); clears the accumulators.
+__global__ void k_reduce_out(long long* acc, double* energy, int with_e, double* virial, int with_w) {
+  const double efg = double(acc[kAccFg]) / kFix, ecg = double(acc[kAccCg]) / kFix;
+  const double eb = double(acc[kAccEb]) / kFix;
   if (with_e) {
     energy[0] = efg;
     energy[1] = ecg;
@@ -632,7 +664,9 @@ __global__ void k_reduce_out(ReduceArgs r, double* energy, int with_e, double* v
   }
   if (with_w)
 #pragma unroll
-    for (int q = 1; q < kNQ; ++q) virial[q - 1] = double(tot[q] + tot[kNQ + q]) / kFix;
+    for (int q = 1; q < kNQ; ++q) virial[q - 1] = double(acc[kAccFg + q] + acc[kAccCg + q]) / kFix;
+#pragma unroll
+  for (int q = 0; q < kNAcc; ++q) acc[q] = 0;
 }
 
 __global__ void k_set_ab(DevState* st, double a, double b) {
@@ -710,9 +744,8 @@ cudaError_t launch_check_cache(relres_ctx* c, const double* d_pos) {
 }
 
 static BondedArgs bonded_args(const relres_ctx* c) {
-  return BondedArgs{c->d_inc_off,   c->d_inc,       c->d_bonds,     c->d_angles,   c->d_dihs,
-                    c->d_dih_type,  c->d_bond_par,  c->d_angle_par, c->d_dih_par,  c->d_bond_fpar,
-                    c->d_angle_fpar};
+  return BondedArgs{c->d_bonds,     c->d_angles,    c->d_dihs,     c->d_dih_type, c->d_bond_par,
+                    c->d_angle_par, c->d_dih_par,   c->d_bond_fpar, c->d_angle_fpar};
 }
 
 static void ff_split(double v, float* hi, float* lo) {
@@ -721,19 +754,45 @@ static void ff_split(double v, float* hi, float* lo) {
 }
 
 template <typename R>
-static cudaError_t launch_finish_t(relres_ctx* c, int ev_mode, double* d_forces_out, const double* vel) {
-  const int with_cg = (c->has_cg && c->n_h > 0) ? 1 : 0;
+static cudaError_t launch_bonded_t(relres_ctx* c, bool ev) {
+  const int nt = c->n_bonds + c->n_angles + c->n_dih;
+  if (nt == 0) return cudaSuccess;
   const double k = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
+  BondedKArgs<R> a{};
+  a.nb = c->n_bonds;
+  a.na = c->n_angles;
+  a.nd = c->n_dih;
+  a.B = bonded_args(c);
+  a.xfx = c->d_xfx;
+  a.sc = Sc3<R>{R(c->box[0] / k), R(c->box[1] / k), R(c->box[2] / k)};
+  ff_split(c->box[0] / 18446744073709551616.0, &a.q0h, &a.q0l);
+  ff_split(c->box[1] / 18446744073709551616.0, &a.q1h, &a.q1l);
+  ff_split(c->box[2] / 18446744073709551616.0, &a.q2h, &a.q2l);
+  a.tf = static_cast<ForceT<R>*>(c->d_tf);
+  a.acc = c->d_acc;
+  const int nblk = (nt + kThreads - 1) / kThreads;
+  if (ev)
+    k_bonded<R, true><<<nblk, kThreads, 0, c->stream>>>(a);
+  else
+    k_bonded<R, false><<<nblk, kThreads, 0, c->stream>>>(a);
+  RELRES_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_finish_t(relres_ctx* c, double* d_forces_out, const double* vel) {
+  const int with_cg = (c->has_cg && c->n_h > 0) ? 1 : 0;
   FinishArgs<R> a{c->n,
                   static_cast<const ForceT<R>*>(c->d_f_fg),
                   static_cast<const ForceT<R>*>(c->d_f_cg),
                   with_cg,
                   c->d_type,
                   c->hyb_mask,
-                  bonded_args(c),
-                  c->d_xfx,
-                  Sc3<R>{R(c->box[0] / k), R(c->box[1] / k), R(c->box[2] / k)},
-                  0.f, 0.f, 0.f, 0.f, 0.f, 0.f,
+                  c->d_inc_off,
+                  c->d_inc,
+                  static_cast<const ForceT<R>*>(c->d_tf),
+                  2 * c->n_bonds,
+                  2 * c->n_bonds + 3 * c->n_angles,
                   vel ? vel : static_cast<const double*>(c->d_dummy),
                   vel ? 1 : 0,
                   c->d_cdt,
@@ -741,38 +800,33 @@ static cudaError_t launch_finish_t(relres_ctx* c, int ev_mode, double* d_forces_
                   static_cast<ForceT<R>*>(c->d_f_tot),
                   d_forces_out ? d_forces_out : static_cast<double*>(c->d_dummy),
                   d_forces_out ? 1 : 0,
-                  c->d_part_fin,
+                  c->d_acc,
                   c->d_state};
-  ff_split(c->box[0] / 18446744073709551616.0, &a.q0h, &a.q0l);
-  ff_split(c->box[1] / 18446744073709551616.0, &a.q1h, &a.q1l);
-  ff_split(c->box[2] / 18446744073709551616.0, &a.q2h, &a.q2l);
-  k_finish<R><<<c->nb_fin, kThreads, 0, c->stream>>>(a, ev_mode);
+  k_finish<R><<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(a);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish(relres_ctx* c, int ev_mode, double* d_forces_out, bool with_ke) {
-  (void)with_ke;
-  return c->fp64 ? launch_finish_t<double>(c, ev_mode, d_forces_out, nullptr)
-                 : launch_finish_t<float>(c, ev_mode, d_forces_out, nullptr);
-}
-
-cudaError_t launch_finish_step(relres_ctx* c, const StepParams& sp, const double* d_vel) {
-  (void)sp;
-  return c->fp64 ? launch_finish_t<double>(c, 2, nullptr, d_vel)
-                 : launch_finish_t<float>(c, 2, nullptr, d_vel);
-}
-
-static ReduceArgs reduce_args(const relres_ctx* c) {
-  const bool cg = c->has_cg && c->n_h > 0;
-  return ReduceArgs{c->d_part_fg, c->nb_fg, c->d_part_cg, cg ? c->nb_cg : 0, cg ? 1 : 0,
-                    c->d_part_fin, c->nb_fin};
+cudaError_t launch_finish(relres_ctx* c, bool ev, double* d_forces_out, const double* d_vel) {
+  if (c->fp64) {
+    const cudaError_t e = launch_bonded_t<double>(c, ev);
+    return e != cudaSuccess ? e : launch_finish_t<double>(c, d_forces_out, d_vel);
+  }
+  const cudaError_t e = launch_bonded_t<float>(c, ev);
+  return e != cudaSuccess ? e : launch_finish_t<float>(c, d_forces_out, d_vel);
 }
 
 cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial) {
   double* dd = static_cast<double*>(c->d_dummy);
-  k_reduce_out<<<1, 1024, 0, c->stream>>>(reduce_args(c), d_energy ? d_energy : dd, d_energy ? 1 : 0,
-                                          d_virial ? d_virial : dd, d_virial ? 1 : 0);
+  k_reduce_out<<<1, 1, 0, c->stream>>>(c->d_acc, d_energy ? d_energy : dd, d_energy ? 1 : 0,
+                                       d_virial ? d_virial : dd, d_virial ? 1 : 0);
+  RELRES_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csvr_draws(relres_ctx* c, const StepParams& sp, int count) {
+  if (!(sp.t_target > 0.0) || count <= 0) return cudaSuccess;
+  k_csvr_draws<<<(count + 127) / 128, 128, 0, c->stream>>>(sp.n_f, sp.seed, count, c->d_state, c->d_draws);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
@@ -812,13 +866,13 @@ cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel) {
   return c->fp64 ? launch_drift_t<double>(c, sp, d_vel) : launch_drift_t<float>(c, sp, d_vel);
 }
 
-cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp) {
+cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp, int k) {
   StepParams q = sp;
   if (q.thermo == nullptr) {
     q.thermo = static_cast<double*>(c->d_dummy);
     q.thermo_every = 0;
   }
-  k_thermo<<<1, 1024, 0, c->stream>>>(reduce_args(c), q, c->d_state);
+  k_thermo<<<1, 1, 0, c->stream>>>(c->d_acc, q, c->d_state, c->d_draws + 2 * k);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }

@@ -19,8 +19,8 @@
 // region selected without branches.  The owner accumulates its force in
 // registers and writes it once (no atomics).  Energy and virial are computed
 // only on the steps that need them (EV template): they are reduced per block
-// (warp shuffles, then shared memory) and written as 64-bit fixed-point
-// partial sums.  The FP64 variant (R = double) reads 64-bit fixed-point
+// (warp shuffles, then shared memory) and added to 64-bit fixed-point
+// accumulators with integer atomics.  The FP64 variant (R = double) reads 64-bit fixed-point
 // positions and computes every term in double.
 #include "common.cuh"
 
@@ -191,7 +191,7 @@ struct ListWalk {
   const int* cnt;
   const int* perm;
   ForceOut<R>* f_out;
-  long long* partial;  // [blocks of this list][kNQ]
+  long long* acc;  // kNQ accumulators of this list (energy, six virial components)
 };
 
 template <typename R>
@@ -316,7 +316,7 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
     if (threadIdx.x == 0) {
       // full lists: every pair was visited from both ends
 #pragma unroll
-      for (int q = 0; q < kNQ; ++q) L.partial[blk * kNQ + q] = to_fix_sum(0.5 * accd[q]);
+      for (int q = 0; q < kNQ; ++q) acc_add(L.acc + q, 0.5 * accd[q]);
     }
   }
 }
@@ -399,10 +399,10 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   if (nb_fg + nb_cg == 0) return cudaSuccess;
   a.nblk_cg = nb_cg;
   a.fg = ListWalk<R>{c->n, pfg, c->d_nbr_fg, c->d_cnt_fg, c->d_perm_fg,
-                     static_cast<ForceOut<R>*>(c->d_f_fg), c->d_part_fg};
+                     static_cast<ForceOut<R>*>(c->d_f_fg), c->d_acc + kAccFg};
   // without a CG list the CG walk is never entered; its pointers are stand-ins
   a.cg = do_cg ? ListWalk<R>{c->n_h, pcg, c->d_nbr_cg, c->d_cnt_cg, c->d_perm_cg,
-                             static_cast<ForceOut<R>*>(c->d_f_cg), c->d_part_cg}
+                             static_cast<ForceOut<R>*>(c->d_f_cg), c->d_acc + kAccCg}
                : a.fg;
   const size_t smem = pair_smem<R>(c->n_types, ev);
   if (ev)

@@ -86,6 +86,9 @@ struct DevState {
 // order-independent integer reductions.
 constexpr double kFix = 4294967296.0;
 constexpr int kNQ = 7;  // E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
+// accumulator slots: FG pair sums, CG pair sums, kinetic energy, bonded energy
+constexpr int kAccFg = 0, kAccCg = kNQ, kAccKe = 2 * kNQ, kAccEb = 2 * kNQ + 1, kNAcc = 2 * kNQ + 2;
+constexpr int kBlockSteps = 100;  // steps between host status checks in relres_step
 
 struct Pos64 {  // FP64 mode sorted position: 64-bit fixed-point x, y, z and type
   long long x, y, z, t;
@@ -194,11 +197,11 @@ struct relres_ctx {
   void* d_f_tot = nullptr;
   bool forces_valid = false;
 
-  // reductions
-  long long* d_part_fg = nullptr;   // [blocks][kNQ]
-  long long* d_part_cg = nullptr;
-  long long* d_part_fin = nullptr;  // [blocks][2]: KE, E_bonded
-  int nb_fg = 0, nb_cg = 0, nb_fin = 0;
+  // bonded-term force slots: bonds 2 per term, then angles 3, then dihedrals 4
+  void* d_tf = nullptr;
+  // reductions: 64-bit fixed-point accumulators (kNAcc), cleared by their reader
+  long long* d_acc = nullptr;
+  double* d_draws = nullptr;  // CSVR random numbers of the current block of steps, 2 per step
   relres::DevState* d_state = nullptr;
   unsigned* d_open = nullptr;  // device word that always reads F_REBUILD (un-gated launches)
   void* d_dummy = nullptr;     // valid target for pointer arguments a kernel does not use
@@ -243,18 +246,20 @@ cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, doubl
 cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate);
 cudaError_t launch_lists(relres_ctx* c, const unsigned* gate);
 
-// pair and finish; ev_mode 0 = never, 1 = always, 2 = per step (DevState::ev)
-// which: 1 = FG-list kernel, 2 = CG-list kernel, 3 = both
-// pair kernel over both lists in one launch; ev: energy and virial partials too
+// Forces.  ev: this evaluation also adds energies and virial to the
+// accumulators (d_acc).  The pair kernel covers both lists in one launch
+// (which: 1 = FG list only, 2 = CG list only, 3 = both).  launch_finish runs
+// the bonded-term kernel and the per-atom force sum; with d_vel it also adds
+// the kinetic energy of u + c F.
 cudaError_t launch_pairs(relres_ctx* c, bool ev, int which = 3);
-cudaError_t launch_finish(relres_ctx* c, int ev_mode, double* d_forces_out, bool with_ke);
+cudaError_t launch_finish(relres_ctx* c, bool ev, double* d_forces_out, const double* d_vel);
 cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial);
 
 // MD
 cudaError_t upload_type_consts(relres_ctx* c, double dt);
 cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel);
-cudaError_t launch_finish_step(relres_ctx* c, const StepParams& sp, const double* d_vel);
-cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp);
+cudaError_t launch_csvr_draws(relres_ctx* c, const StepParams& sp, int count);
+cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp, int k);
 cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev);
 cudaError_t launch_flags_and(relres_ctx* c, unsigned keep);
 
