@@ -69,6 +69,12 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // Block-wide sum of NV values per thread; result valid in thread 0.
 // `sh` must hold (blockDim.x / 32) * NV elements.
 template <typename T, int NV>

@@ -4,18 +4,19 @@
 // neighbour lists with different cutoffs -- every atom lists its near
 // neighbours within r_s+ (+ skin) for the FG part, and only hybrid sites list
 // each other within r_c+ (+ skin) for the CG part.  Here both lists are full
-// (each pair stored on both atoms, so the pair kernels write every force
-// exactly once without atomics), column-major (entry k of slot s at k*n + s,
-// so a warp's 32 index loads are one 128-byte transaction), and hold sorted
-// slot indices: atoms are counting-sorted into cells visited in Morton order,
-// which keeps the position gathers of the pair kernels local in L1/L2.
+// (each pair stored on both atoms, so the pair kernel writes every force
+// exactly once without atomics), stored in chunks of four entries per slot
+// (entry k of slot s at int (((k >> 2) * nslots + s) << 2) + (k & 3), so a
+// warp reads 512 contiguous bytes per chunk), and hold sorted slot indices:
+// atoms are counting-sorted into cells visited in Morton order, which keeps
+// the position gathers of the pair kernel local in L1/L2.
 //
 // Rebuild sequence: k_bin (cell of every atom, counts) -> k_scan (exclusive
-// scan per grid) -> k_scatter (slot = start + atomic cursor) -> k_sort_cells
+// scan per grid) -> k_scatter (slot = start + arrival rank) -> k_sort_cells
 // (atom order inside each cell, so lists are deterministic) -> k_pack (sorted
 // positions, ranks, reference positions for the displacement trigger) ->
-// k_list (FG and CG lists).  Every kernel can be gated on the device rebuild
-// flag, so the whole sequence can sit inside a CUDA graph step.
+// k_list (FG and CG lists in one launch).  Every kernel can be gated on the
+// device rebuild flag, so the whole sequence can sit inside a CUDA graph step.
 #include "common.cuh"
 
 namespace relres {
@@ -145,29 +146,41 @@ __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ t
   }
 }
 
-// One thread per cell: insertion-sort the cell's atoms by index (the scatter
-// order is arbitrary), reset the cursor.
+// One warp per cell: the cell's atoms put in index order (the scatter order
+// is arbitrary).  Up to 32 atoms: each lane counts the smaller indices of its
+// cell (register shuffles) and writes its atom to that rank; larger cells
+// fall back to an insertion sort by one lane.  Resets the cell cursor.
 __global__ void k_sort_cells(const unsigned* gate, int fn, const int* fstart, int* fcount, int cn,
                              const int* cstart, int* ccount, int* __restrict__ perm_fg,
                              int* __restrict__ perm_cg) {
   if (gate_closed(gate)) return;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < fn + cn; t += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < fn + cn; t += nwarps) {
     const bool fg = t < fn;
     const int c = fg ? t : t - fn;
     const int* const start = fg ? fstart : cstart;
     int* const count = fg ? fcount : ccount;
     int* const perm = fg ? perm_fg : perm_cg;
-    const int lo = start[c], hi = start[c + 1];
-    for (int k = lo + 1; k < hi; ++k) {
-      const int v = perm[k];
-      int m = k - 1;
-      while (m >= lo && perm[m] > v) {
-        perm[m + 1] = perm[m];
-        --m;
+    const int lo = start[c], hi = start[c + 1], m = hi - lo;
+    if (m <= 32) {
+      const int v = lane < m ? perm[lo + lane] : 0x7fffffff;
+      int rank = 0;
+      for (int k = 0; k < m; ++k) rank += __shfl_sync(0xffffffffu, v, k) < v ? 1 : 0;
+      __syncwarp();
+      if (lane < m) perm[lo + rank] = v;
+    } else if (lane == 0) {
+      for (int k = lo + 1; k < hi; ++k) {
+        const int v = perm[k];
+        int q = k - 1;
+        while (q >= lo && perm[q] > v) {
+          perm[q + 1] = perm[q];
+          --q;
+        }
+        perm[q + 1] = v;
       }
-      perm[m + 1] = v;
     }
-    count[c] = 0;
+    if (lane == 0) count[c] = 0;
   }
 }
 
@@ -201,6 +214,7 @@ struct ListArgs {
   int nslots;
   const int4* pos;
   const int* perm;
+  const int* rank;  // atom -> slot of this list (-1: not in it)
   GridArgs g;
   float sx, sy, sz;
   float rl2;
@@ -226,64 +240,215 @@ __device__ __forceinline__ int axis_cells(int c, int n, int (&out)[3]) {
   return n;
 }
 
-__global__ void __launch_bounds__(kThreads) k_list(const unsigned* gate, ListArgs a) {
-  if (gate_closed(gate)) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.nslots) return;
-  const int4 p = a.pos[s];
-  const int i = a.perm[s];
-  const int e0 = a.excl_off ? a.excl_off[i] : 0;
-  const int e1 = a.excl_off ? a.excl_off[i + 1] : 0;
-  int cx[3], cy[3], cz[3];
-  const int nx = axis_cells(cell_of(p.x, a.g.n0), a.g.n0, cx);
-  const int ny = axis_cells(cell_of(p.y, a.g.n1), a.g.n1, cy);
-  const int nz = axis_cells(cell_of(p.z, a.g.n2), a.g.n2, cz);
-  int count = 0;
-  // entries are stored in chunks of four (one 16-byte store per chunk):
-  // entry k of slot s at int (((k >> 2) * nslots + s) << 2) + (k & 3)
-  int4* const out4 = reinterpret_cast<int4*>(a.nbr) + s;
-  int4 buf = make_int4(s, s, s, s);
-  for (int ix = 0; ix < nx; ++ix)
-    for (int iy = 0; iy < ny; ++iy)
-      for (int iz = 0; iz < nz; ++iz) {
-        const int c = a.g.rank_of[(cx[ix] * a.g.n1 + cy[iy]) * a.g.n2 + cz[iz]];
-        const int tb = a.g.start[c], te = a.g.start[c + 1];
-        for (int t = tb; t < te; ++t) {
-          if (t == s) continue;
-          const int4 q = a.pos[t];
-          const float dx = dfix32(p.x, q.x, a.sx);
-          const float dy = dfix32(p.y, q.y, a.sy);
-          const float dz = dfix32(p.z, q.z, a.sz);
-          if (dx * dx + dy * dy + dz * dz >= a.rl2) continue;
-          if (e1 > e0) {
-            const int j = a.perm[t];
-            bool ex = false;
-            for (int e = e0; e < e1; ++e) ex |= (a.excl_idx[e] == j);
-            if (ex) continue;
-          }
-          if (count < a.cap) {
-            const int q = count & 3;
-            buf.x = q == 0 ? t : buf.x;
-            buf.y = q == 1 ? t : buf.y;
-            buf.z = q == 2 ? t : buf.z;
-            buf.w = q == 3 ? t : buf.w;
-            if (q == 3) out4[size_t(count >> 2) * a.nslots] = buf;
-          }
-          ++count;
-        }
+constexpr int kListThreads = 128;  // 4 warps per cell
+
+__device__ __forceinline__ float wrap1(float d, float l, float il) { return d - l * rintf(d * il); }
+
+// One cell atom (slot s, relative position p) against a staged window: 32
+// candidates per iteration, accepted ones appended at k in window order.
+// Returns the new count.
+template <bool WRAP>
+__device__ __forceinline__ int scan_window(const float4* s_pos, int wn, int s, float px, float py, float pz,
+                                           float rl2, float lx, float ly, float lz, const int (&ex)[8], int ne,
+                                           int e0, const int* excl_idx, const int* perm, int* nbr, int nslots,
+                                           int cap, int k) {
+  const int lane = threadIdx.x & 31;
+  for (int j0 = 0; j0 < wn; j0 += 32) {
+    const int jj = j0 + lane;
+    bool acc = false;
+    int t = -1;
+    if (jj < wn) {
+      const float4 q = s_pos[jj];
+      t = __float_as_int(q.w);
+      float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+      if (WRAP) {
+        dx = wrap1(dx, lx, 1.f / lx);
+        dy = wrap1(dy, ly, 1.f / ly);
+        dz = wrap1(dz, lz, 1.f / lz);
       }
-  // the last partial chunk (its padding lanes hold earlier indices, never read as partners)
-  const int kept = min(count, a.cap);
-  if (kept & 3) out4[size_t(kept >> 2) * a.nslots] = buf;
-  a.cnt[s] = kept;
-  atomicMax(a.max_out, count);
-  atomicAdd(a.total_out, (unsigned long long)count);
-  if (count > a.cap) atomicOr(a.flags, a.overflow_bit);
+      acc = t != s && dx * dx + dy * dy + dz * dz < rl2;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc = acc && t != ex[e];
+    if (acc && ne > 8) {
+      const int tj = perm[t];
+      for (int e = 8; e < ne; ++e) acc = acc && excl_idx[e0 + e] != tj;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, acc);
+    const int kk = k + __popc(b & ((1u << lane) - 1u));
+    if (acc && kk < cap) nbr[((size_t(kk >> 2) * nslots + s) << 2) + (kk & 3)] = t;
+    k += __popc(b);
+  }
+  return k;
+}
+constexpr int kListWindow = 1024;  // candidates staged in shared memory at a time
+constexpr int kListGroup = 64;     // cell atoms handled per pass
+
+// One block per cell (CG-grid cells first, then FG-grid cells).  The block
+// stages the atoms of the cell's 27-cell neighbourhood in shared memory as
+// FP32 coordinates relative to the cell's first atom (from the exact wrapped
+// 32-bit differences; the list radius carries the skin, so FP32 rounding
+// near the list radius cannot lose a pair inside the interaction range), then
+// each warp takes one atom of the cell at a time and tests 32 staged
+// candidates per iteration; accepted candidates are appended in candidate
+// order (ballot + prefix count), so the list is deterministic.
+__device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg, int ncell_cg, int cb) {
+  __shared__ float4 s_pos[kListWindow];  // x, y, z relative; w = slot index bits
+  __shared__ int s_cstart[27], s_coff[28];
+  __shared__ int s_k[kListGroup];
+  __shared__ int s_max;
+  __shared__ unsigned long long s_tot;
+  const bool is_cg = cb < ncell_cg;
+  // the list of this block, field by field (parameters are only read directly)
+  struct {
+    int nslots;
+    const int4* pos;
+    const int* perm;
+    const int* rank;
+    int n0, n1, n2;
+    const int* rank_of;
+    const int* start;
+    float sx, sy, sz, rl2;
+    const int* excl_off;
+    const int* excl_idx;
+    int cap;
+    int* nbr;
+    int* cnt;
+    int* max_out;
+    unsigned long long* total_out;
+    unsigned* flags;
+    unsigned overflow_bit;
+  } a;
+#define RELRES_PICK(f) a.f = is_cg ? cg.f : fg.f
+  RELRES_PICK(nslots);
+  RELRES_PICK(pos);
+  RELRES_PICK(perm);
+  RELRES_PICK(rank);
+  RELRES_PICK(sx);
+  RELRES_PICK(sy);
+  RELRES_PICK(sz);
+  RELRES_PICK(rl2);
+  RELRES_PICK(excl_off);
+  RELRES_PICK(excl_idx);
+  RELRES_PICK(cap);
+  RELRES_PICK(nbr);
+  RELRES_PICK(cnt);
+  RELRES_PICK(max_out);
+  RELRES_PICK(total_out);
+  RELRES_PICK(flags);
+  RELRES_PICK(overflow_bit);
+#undef RELRES_PICK
+  a.n0 = is_cg ? cg.g.n0 : fg.g.n0;
+  a.n1 = is_cg ? cg.g.n1 : fg.g.n1;
+  a.n2 = is_cg ? cg.g.n2 : fg.g.n2;
+  a.rank_of = is_cg ? cg.g.rank_of : fg.g.rank_of;
+  a.start = is_cg ? cg.g.start : fg.g.start;
+  const int c = is_cg ? cb : cb - ncell_cg;
+  const int i0 = a.start[c];
+  const int ni = a.start[c + 1] - i0;
+  if (ni == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int4 ref = a.pos[i0];
+  if (threadIdx.x == 0) {
+    int cx[3], cy[3], cz[3];
+    const int nx = axis_cells(cell_of(ref.x, a.n0), a.n0, cx);
+    const int ny = axis_cells(cell_of(ref.y, a.n1), a.n1, cy);
+    const int nz = axis_cells(cell_of(ref.z, a.n2), a.n2, cz);
+    int m = 0, off = 0;
+    for (int ix = 0; ix < nx; ++ix)
+      for (int iy = 0; iy < ny; ++iy)
+        for (int iz = 0; iz < nz; ++iz) {
+          const int cc = a.rank_of[(cx[ix] * a.n1 + cy[iy]) * a.n2 + cz[iz]];
+          const int b = a.start[cc];
+          s_cstart[m] = b;
+          s_coff[m] = off;
+          off += a.start[cc + 1] - b;
+          ++m;
+        }
+    for (int k = m; k < 28; ++k) s_coff[k] = off;
+    s_max = 0;
+    s_tot = 0ull;
+  }
+  __syncthreads();
+  const int total = s_coff[27];
+  // With 4 or more cells per axis every staged offset from the reference atom
+  // and every candidate offset is below L/2, so plain differences of the
+  // relative coordinates are minimum images; smaller grids wrap explicitly.
+  const bool wrap = a.n0 < 4 || a.n1 < 4 || a.n2 < 4;
+  const float lx = a.sx * 4294967296.f, ly = a.sy * 4294967296.f, lz = a.sz * 4294967296.f;
+  int blk_max = 0;
+  unsigned long long blk_tot = 0ull;
+  for (int g0 = 0; g0 < ni; g0 += kListGroup) {
+    const int ng = min(kListGroup, ni - g0);
+    for (int k = threadIdx.x; k < ng; k += blockDim.x) s_k[k] = 0;
+    for (int w0 = 0; w0 < total; w0 += kListWindow) {
+      const int wn = min(kListWindow, total - w0);
+      __syncthreads();
+      for (int k = threadIdx.x; k < wn; k += blockDim.x) {
+        const int gidx = w0 + k;
+        int m = 0;  // stencil cell holding candidate gidx
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (m + step < 28 && s_coff[m + step] <= gidx) m += step;
+        const int t = s_cstart[m] + (gidx - s_coff[m]);
+        const int4 q = a.pos[t];
+        s_pos[k] = make_float4(dfix32(q.x, ref.x, a.sx), dfix32(q.y, ref.y, a.sy), dfix32(q.z, ref.z, a.sz),
+                               __int_as_float(t));
+      }
+      __syncthreads();
+      for (int il = warp; il < ng; il += blockDim.x >> 5) {
+        const int s = i0 + g0 + il;
+        const int4 p = a.pos[s];
+        const float px = dfix32(p.x, ref.x, a.sx), py = dfix32(p.y, ref.y, a.sy), pz = dfix32(p.z, ref.z, a.sz);
+        // excluded partners as slots of this list (up to 8 in registers; more: checked in global memory)
+        const int atom = a.perm[s];
+        const int e0 = a.excl_off[atom], ne = a.excl_off[atom + 1] - e0;
+        int ex[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) ex[e] = e < ne ? a.rank[a.excl_idx[e0 + e]] : -1;
+        const int k = wrap ? scan_window<true>(s_pos, wn, s, px, py, pz, a.rl2, lx, ly, lz, ex, ne, e0,
+                                               a.excl_idx, a.perm, a.nbr, a.nslots, a.cap, s_k[il])
+                           : scan_window<false>(s_pos, wn, s, px, py, pz, a.rl2, lx, ly, lz, ex, ne, e0,
+                                                a.excl_idx, a.perm, a.nbr, a.nslots, a.cap, s_k[il]);
+        if (lane == 0) s_k[il] = k;
+      }
+    }
+    __syncthreads();
+    for (int il = threadIdx.x; il < ng; il += blockDim.x) {
+      const int k = s_k[il];
+      a.cnt[i0 + g0 + il] = min(k, a.cap);
+      blk_max = max(blk_max, k);
+      blk_tot += (unsigned long long)k;
+    }
+    __syncthreads();  // s_k is reused by the next group
+  }
+  // block statistics, then one atomic each
+  blk_max = warp_max(blk_max);
+  blk_tot = warp_sum(blk_tot);
+  if (lane == 0) {
+    atomicMax(&s_max, blk_max);
+    atomicAdd(&s_tot, blk_tot);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(a.max_out, s_max);
+    atomicAdd(a.total_out, s_tot);
+    if (s_max > a.cap) atomicOr(a.flags, a.overflow_bit);
+  }
+  __syncthreads();  // shared memory is reused by the next cell
 }
 
+__global__ void __launch_bounds__(kListThreads) k_list(const unsigned* gate, ListArgs fg, ListArgs cg,
+                                                       int ncell_cg) {
+  if (gate_closed(gate)) return;
+  const int ncell = ncell_cg + fg.g.ncell;
+  for (int cb = blockIdx.x; cb < ncell; cb += gridDim.x) list_cell(fg, cg, ncell_cg, cb);
+}
+
+// grid-stride kernels: at most four blocks per SM (a closed gate then costs one small launch)
 static int blocks_for(int n) {
   const int b = (n + kThreads - 1) / kThreads;
-  return b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b);
+  return b < 1 ? 1 : (b > 152 * 4 ? 152 * 4 : b);
 }
 
 cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
@@ -310,7 +475,7 @@ cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
                                             c->d_perm_fg, c->d_perm_cg);
   RELRES_LAUNCHED(c);
   const int ncells = gf.ncell + (gc.valid ? gc.ncell : 0);
-  k_sort_cells<<<blocks_for(ncells), kThreads, 0, c->stream>>>(gate, gf.ncell, gf.start, gf.count,
+  k_sort_cells<<<blocks_for(32 * ncells), kThreads, 0, c->stream>>>(gate, gf.ncell, gf.start, gf.count,
                                                                gc.valid ? gc.ncell : 0, gc.start, gc.count,
                                                                c->d_perm_fg, c->d_perm_cg);
   RELRES_LAUNCHED(c);
@@ -326,22 +491,23 @@ cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
   const float s0 = float(c->box[0] / 4294967296.0), s1 = float(c->box[1] / 4294967296.0),
               s2 = float(c->box[2] / 4294967296.0);
   DevState* st = c->d_state;
-  {
-    const double rl = c->rlist_fg_cut + c->prm.skin;
-    ListArgs a{c->n, c->d_pos_fg, c->d_perm_fg, grid_args(c->gfg), s0, s1, s2, float(rl * rl),
-               c->d_excl_off, c->d_excl_idx, c->cap_fg, c->d_nbr_fg, c->d_cnt_fg, &st->max_fg,
-               &st->tot_fg, &st->flags, F_OVERFLOW_FG};
-    k_list<<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(gate, a);
-    RELRES_LAUNCHED(c);
-  }
+  const double rf = c->rlist_fg_cut + c->prm.skin;
+  const ListArgs fg{c->n, c->d_pos_fg, c->d_perm_fg, c->d_rank_fg, grid_args(c->gfg), s0, s1, s2,
+                    float(rf * rf), c->d_excl_off, c->d_excl_idx, c->cap_fg, c->d_nbr_fg, c->d_cnt_fg,
+                    &st->max_fg, &st->tot_fg, &st->flags, F_OVERFLOW_FG};
+  ListArgs cg = fg;  // stand-in when there is no CG list (its blocks are not launched)
+  int ncell_cg = 0;
   if (c->has_cg && c->n_h > 0) {
-    const double rl = c->rlist_cg_cut + c->skin_cg;
-    ListArgs a{c->n_h, c->d_pos_cg, c->d_perm_cg, grid_args(c->gcg), s0, s1, s2, float(rl * rl),
-               c->d_excl_off, c->d_excl_idx, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg, &st->max_cg,
-               &st->tot_cg, &st->flags, F_OVERFLOW_CG};
-    k_list<<<(c->n_h + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(gate, a);
-    RELRES_LAUNCHED(c);
+    const double rc = c->rlist_cg_cut + c->skin_cg;
+    cg = ListArgs{c->n_h, c->d_pos_cg, c->d_perm_cg, c->d_rank_cg, grid_args(c->gcg), s0, s1, s2,
+                  float(rc * rc), c->d_excl_off, c->d_excl_idx, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg,
+                  &st->max_cg, &st->tot_cg, &st->flags, F_OVERFLOW_CG};
+    ncell_cg = c->gcg.ncell;
   }
+  // persistent: one wave of blocks walks the cells (a closed gate costs one small launch)
+  const int nb = std::min(ncell_cg + c->gfg.ncell, 152 * 8);
+  k_list<<<nb, kListThreads, 0, c->stream>>>(gate, fg, cg, ncell_cg);
+  RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 

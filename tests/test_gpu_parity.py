@@ -178,6 +178,18 @@ def test_fp64_nve_trajectory_matches_oracle(torch):
     assert np.all(p >= 0.0) and np.all(p < s.box)
 
 
+def test_fp64_propane_1000_nve_steps(torch):
+    # the propane-like configuration: 216 molecules, FP64, 1000 NVE steps at 1 fs
+    s = S.propane()
+    p, v, th, st = _gpu_md(torch, s, R.RELRES_PREC_FP64, 1000, 1.0, every=10)
+    po, vo, tho = _oracle_md(s, 1000, 1.0)
+    tho = tho[9::10]
+    assert st["n_builds"] >= 2
+    np.testing.assert_allclose(th[:, 0] + th[:, 1], tho[:, 0], rtol=1e-8)
+    np.testing.assert_allclose(th[:, 3], tho[:, 2], rtol=1e-8)
+    assert np.abs(_wrapped_diff(p, po, s.box)).max() < 1e-6
+
+
 def test_fp64_csvr_trajectory_matches_oracle(torch):
     s = S.propane()
     p, v, th, st = _gpu_md(torch, s, R.RELRES_PREC_FP64, 30, 1.0, t_target=230.0, seed=11)

@@ -1,0 +1,189 @@
+"""GPU parity at the workload sizes and on the degenerate cases of the method.
+
+* The 20 000-atom neopentane-like liquid (FP32) and the 20 000-atom block
+  copolymer melt (FP32, dihedrals, intrachain CG pairs) against the full FP64
+  oracle.
+* The 1 000 000-atom neopentane-like liquid in the configuration the benchmark
+  times (FP32, CSVR at 260 K, dt = 2 fs, lists rebuilt on the device): forces
+  of sampled atoms against oracle rows (each row is the full O(N) sum of that
+  atom), bonded forces against the oracle, and energy / virial against the
+  FP64 mode of the library (which the small-size tests pin to the oracle).
+* Degenerate cases: zero-width switching shells (r_- = r_+ removes a shell),
+  every atom a hybrid of its own group (n = 1, so u^CG = u^FG by Eq. 13), and
+  a single pair swept through all five regions of Eq. 20.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import core as O
+from paper_2104_10231_gb300 import relres as R
+from paper_2104_10231_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-5
+E_TOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2104_10231_gb300.build import build_library
+
+    build_library()
+    R.load()
+    return T
+
+
+def _dev(torch, a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _compute(torch, system, precision, pos=None, ctx=None):
+    own = ctx is None
+    if own:
+        ctx = R.Context(R.params_for(system, precision), R.topology_for(system))
+    p = _dev(torch, system.pos if pos is None else pos)
+    if own:
+        ctx.build_neighbors(p, system.box)
+    f = torch.empty_like(p)
+    e = torch.zeros(4, dtype=torch.float64, device="cuda")
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.compute(p, f, e, w)
+    torch.cuda.synchronize()
+    out = f.cpu().numpy(), e.cpu().numpy(), w.cpu().numpy()
+    if own:
+        ctx.close()
+    return out
+
+
+def _oracle(system, pos=None):
+    pos = system.pos if pos is None else pos
+    tab = O.table_for(system)
+    f, e, w = O.pair_forces(pos, system.box, system.types, tab, system.n_types, system.excl)
+    fb, eb = O.bonded(pos, system.box, system.topo)
+    return f + fb, e, float(eb.sum()), w
+
+
+def _ferr(f, ref):
+    rms = math.sqrt((ref * ref).sum(1).mean())
+    return float(np.abs(f - ref).max() / rms)
+
+
+def _check_full(torch, system, precision, f_tol, e_tol):
+    f, e, w = _compute(torch, system, precision)
+    fr, er, ebr, wr = _oracle(system)
+    ferr = _ferr(f, fr)
+    eerr = abs(e[0] + e[1] - er) / abs(er)
+    berr = abs(e[2] - ebr) / max(1.0, abs(ebr))
+    werr = float(np.abs(w - wr).max() / np.abs(wr[:3]).max())
+    print(f"{system.name} N={system.n_atoms}: force {ferr:.2e} energy {eerr:.2e} bonded {berr:.2e} "
+          f"virial {werr:.2e}")
+    assert ferr <= f_tol, ferr
+    assert eerr <= e_tol, eerr
+    assert berr <= e_tol, berr
+    assert werr <= 10 * f_tol, werr
+
+
+def test_fp32_neopentane_20000_atoms(torch):
+    _check_full(torch, S.neopentane(n_mol=4000), R.RELRES_PREC_FP32, F_TOL, E_TOL)
+
+
+def test_fp32_block_copolymer_20000_atoms(torch):
+    s = S.block_copolymer()
+    assert s.n_atoms == 20000 and len(s.topo["dihedrals"]) > 0
+    _check_full(torch, s, R.RELRES_PREC_FP32, F_TOL, E_TOL)
+
+
+def test_fp64_block_copolymer_2000_atoms(torch):
+    _check_full(torch, S.block_copolymer(n_chain=20), R.RELRES_PREC_FP64, 1e-10, 1e-10)
+
+
+def test_fp32_neopentane_1m_atoms_bench_configuration(torch):
+    s = S.neopentane(n_mol=200_000)
+    assert s.n_atoms == 1_000_000
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    v = _dev(torch, s.vel)
+    ctx.build_neighbors(p, s.box)
+    th = torch.zeros((3, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+    ctx.step(60, 2.0, p, v, t_target=260.0, tau_fs=100.0, seed=5, thermo_every=20, d_thermo=th)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    assert st["n_builds"] >= 2  # the first build plus at least one device-side rebuild
+    pos = p.cpu().numpy()
+    f, e, w = _compute(torch, s, R.RELRES_PREC_FP32, pos=pos, ctx=ctx)
+    ctx.close()
+    assert np.all(np.isfinite(f))
+
+    # sampled rows against the oracle: pair part (full rows) + bonded part
+    rng = np.random.default_rng(17)
+    rows = np.sort(rng.choice(s.n_atoms, size=256, replace=False)).astype(np.int32)
+    tab = O.table_for(s)
+    fp, _ = O.pair_forces_rows(pos, s.box, s.types, tab, s.n_types, rows, s.excl)
+    fb, _ = O.bonded(pos, s.box, s.topo)
+    fr = fp + fb[rows]
+    rms = math.sqrt((fr * fr).sum(1).mean())
+    err = float(np.abs(f[rows] - fr).max() / rms)
+    print(f"1M atoms, 256 sampled rows: force {err:.2e}")
+    assert err <= F_TOL, err
+
+    # energies and virial: FP32 mode against the FP64 mode at the same positions
+    f64, e64, w64 = _compute(torch, s, R.RELRES_PREC_FP64, pos=pos)
+    eerr = abs((e[0] + e[1]) - (e64[0] + e64[1])) / abs(e64[0] + e64[1])
+    berr = abs(e[2] - e64[2]) / abs(e64[2])
+    werr = float(np.abs(w - w64).max() / np.abs(w64[:3]).max())
+    ferr64 = _ferr(f, f64)
+    print(f"1M atoms vs FP64 mode: energy {eerr:.2e} bonded {berr:.2e} virial {werr:.2e} force {ferr64:.2e}")
+    assert eerr <= E_TOL and berr <= E_TOL
+    assert werr <= 10 * F_TOL and ferr64 <= F_TOL
+    # the thermo row of the last step holds the same energies
+    row = th[-1].cpu().numpy()
+    assert row[0] + row[1] == pytest.approx(e[0] + e[1], rel=1e-9)
+    assert row[2] == pytest.approx(e[2], rel=1e-6)
+
+
+def test_zero_width_shells(torch):
+    # r_s- = r_s+ and r_c- = r_c+: no smoothing shells, hard switches of Eq. 20
+    s = S.neopentane(n_mol=400, seed=9).subset_copy(radii=(6.5, 6.5, 13.5, 13.5))
+    _check_full(torch, s, R.RELRES_PREC_FP64, 1e-10, 1e-10)
+    _check_full(torch, s, R.RELRES_PREC_FP32, F_TOL, E_TOL)
+
+
+def test_every_atom_its_own_hybrid(torch):
+    # n = 1: each atom is the CG site of its own group, so Eq. 13 gives
+    # u^CG = u^FG and every atom is in both lists
+    base = S.neopentane(n_mol=400, seed=4)
+    s = base.subset_copy(name="neopentane_all_hybrid", is_hybrid=np.ones(2, np.int32),
+                         group_comp=np.eye(2, dtype=np.int32))
+    assert s.n_hybrid == s.n_atoms
+    _check_full(torch, s, R.RELRES_PREC_FP64, 1e-10, 1e-10)
+    _check_full(torch, s, R.RELRES_PREC_FP32, F_TOL, E_TOL)
+
+
+def _pair_system(r):
+    """Two hybrid atoms of one type (a one-atom group) at distance r."""
+    pos = np.array([[20.0, 20.0, 20.0], [20.0 + r, 20.0, 20.0]])
+    eo = np.zeros(3, np.int32)
+    return S.System("pair", pos, np.zeros((2, 3)), np.zeros(2, np.int32), np.array([0, 1], np.int32),
+                    np.full(3, 45.0), ["X"], np.array([15.035]), np.array([0.195]), np.array([3.75]),
+                    np.array([1], np.int32), np.array([[1]], np.int32), (6.0, 7.0, 13.0, 14.0), "lb",
+                    2.0, S._empty_topo(), eo, np.zeros(0, np.int32), 0.0, 1.0, 0)
+
+
+def test_single_pair_through_all_regions(torch):
+    # below r_s-, in the FG shell, CG LJ, CG shell, beyond r_c+
+    for r in (3.9, 5.5, 6.4, 6.999, 7.0, 9.0, 12.9, 13.5, 13.999, 14.5):
+        s = _pair_system(r)
+        for prec, tol in ((R.RELRES_PREC_FP64, 1e-10), (R.RELRES_PREC_FP32, 2e-6)):
+            f, e, w = _compute(torch, s, prec)
+            fr, er, _, wr = _oracle(s)
+            scale = max(1e-3, float(np.abs(fr).max()))
+            assert np.abs(f - fr).max() <= tol * scale, (r, prec, f, fr)
+            assert abs(e[0] + e[1] - er) <= 1e-9 * max(1.0, abs(er)), (r, prec, e, er)
+            # Newton's third law holds exactly in both modes
+            assert np.abs(f[0] + f[1]).max() <= 1e-12 * scale
