@@ -269,11 +269,28 @@ relres_status relres_set_step_counter(relres_ctx* ctx, long long step);
 relres_status relres_get_stats(relres_ctx* ctx, relres_stats* out);
 
 /*
+ * Step execution mode (an implementation choice; the paper has no
+ * counterpart).  enable != 0 (the default) runs relres_step as one CUDA graph
+ * per block of up to 100 steps: the list rebuild of every step is a
+ * conditional node that a one-thread kernel opens only when the device-side
+ * displacement trigger fired, so steps without a rebuild launch no binning or
+ * list kernels.  The graph is captured on first use and reused while the
+ * step arguments, the timing mode and the context's buffers stay the same
+ * (re-captured otherwise).  enable == 0 launches the kernels on the stream
+ * one by one, the rebuild kernels gated on the device flag.  Both modes give
+ * bit-identical results.  Waits for the context stream; drops a captured
+ * graph.
+ */
+relres_status relres_set_graphs(relres_ctx* ctx, int enable);
+
+/*
  * Kernel timing.  enable != 0 makes relres_compute and relres_step record a
  * CUDA event pair on the context stream around every kernel class of
- * relres_timing_class (gated rebuild kernels included, also when they find
- * nothing to do) and accumulate the elapsed times; enable == 0 stops it.
- * relres_set_timing always clears the totals.
+ * relres_timing_class and accumulate the elapsed times; enable == 0 stops it.
+ * On the stream path the gated rebuild kernels are timed also when they find
+ * nothing to do; in graph mode (relres_set_graphs) RELRES_T_REBUILD times the
+ * decision kernel plus the conditional rebuild node (binning and both lists)
+ * and RELRES_T_LISTS stays empty.  relres_set_timing always clears the totals.
  * relres_get_timings writes, for the first n classes, the total milliseconds
  * (ms[k]) and the number of timed launches (counts[k]; either may be NULL).
  */

@@ -56,6 +56,7 @@ unsigned long long morton3(unsigned x, unsigned y, unsigned z) {
 
 // Cells per axis: the largest count whose cells are at least r_list wide.
 relres_status setup_grid(relres_ctx* c, Grid* g, double rlist) {
+  ++c->buf_gen;
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = std::max(1, int(std::floor(c->box[d] / rlist)));
   if (g->d_rank_of && n[0] == g->n[0] && n[1] == g->n[1] && n[2] == g->n[2]) return RELRES_OK;
@@ -96,6 +97,7 @@ int round_cap(double x, int limit) {
 }
 
 relres_status alloc_lists(relres_ctx* c) {
+  ++c->buf_gen;
   CK(dalloc(&c->d_nbr_fg, size_t(c->cap_fg) * c->n));
   if (c->has_cg && c->n_h > 0) CK(dalloc(&c->d_nbr_cg, size_t(c->cap_cg) * c->n_h));
   return RELRES_OK;
@@ -136,6 +138,14 @@ relres_status host_rebuild(relres_ctx* c) {
 
 // ---- kernel timing: event pairs around each kernel class, read after a sync
 cudaError_t tic(relres_ctx* c, int cls) {
+  if (c->cap_marks) {  // capturing a step graph: the graph owns its (pre-created) events
+    if (c->cap_used + 2 > c->cap_events->size()) return cudaErrorInvalidValue;
+    relres_ctx::Mark m{cls, (*c->cap_events)[c->cap_used], (*c->cap_events)[c->cap_used + 1]};
+    c->cap_used += 2;
+    c->cap_marks->push_back(m);
+    // external: a real event-record node (a plain record would only become a graph edge)
+    return cudaEventRecordWithFlags(m.a, c->stream, cudaEventRecordExternal);
+  }
   while (c->ev_used + 2 > c->ev_pool.size()) {
     cudaEvent_t e;
     cudaError_t r = cudaEventCreate(&e);
@@ -148,7 +158,10 @@ cudaError_t tic(relres_ctx* c, int cls) {
   return cudaEventRecord(m.a, c->stream);
 }
 
-cudaError_t toc(relres_ctx* c) { return cudaEventRecord(c->marks.back().b, c->stream); }
+cudaError_t toc(relres_ctx* c) {
+  if (c->cap_marks) return cudaEventRecordWithFlags(c->cap_marks->back().b, c->stream, cudaEventRecordExternal);
+  return cudaEventRecord(c->marks.back().b, c->stream);
+}
 
 relres_status flush_timing(relres_ctx* c) {
   for (const relres_ctx::Mark& m : c->marks) {
@@ -278,6 +291,7 @@ relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda
 
 relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   if (!c) return RELRES_ERR_ARG;
+  ++c->buf_gen;
   if (!t || t->n_atoms < 1 || !t->type || !t->mass_by_type)
     return fail(c, RELRES_ERR_ARG, "topology needs n_atoms >= 1, type and mass_by_type");
   const int n = t->n_atoms;
@@ -458,6 +472,7 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
 }
 
 relres_status relres_build_neighbors(relres_ctx* c, const double* d_pos, const double box[3]) {
+  if (c) ++c->buf_gen;
   if (!c) return RELRES_ERR_ARG;
   if (!c->have_topo) return fail(c, RELRES_ERR_STATE, "relres_set_topology first");
   if (!d_pos || !box) return fail(c, RELRES_ERR_ARG, "d_pos and box are required");
@@ -514,6 +529,155 @@ relres_status relres_compute(relres_ctx* c, const double* d_pos, double* d_force
   return forces_now(c, (d_energy || d_virial) ? 1 : 0, d_forces, d_energy, d_virial);
 }
 
+// ---- relres_step: one block of steps, recorded either on the stream (the
+// rebuild kernels gated on the device flag) or into a CUDA graph (the
+// rebuild of each step behind a conditional node).
+
+static void drop_step_graph(relres_ctx* c) {
+  if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
+  for (cudaEvent_t e : c->sg.events) cudaEventDestroy(e);
+  c->sg = relres_ctx::StepGraph{};
+}
+
+// The conditional rebuild node of one step, added to the graph being captured
+// on c->stream; its body (binning + lists, ungated) is captured on a second
+// stream.
+static relres_status add_rebuild_node(relres_ctx* c) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(c->stream, &st, nullptr, &g, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive) return fail(c, RELRES_ERR_CUDA, "stream is not capturing");
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  CK(launch_decide(c, h));
+  CK(cudaStreamGetCaptureInfo(c->stream, &st, nullptr, &g, &deps, nullptr, &nd));
+  std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const cudaStream_t main = c->stream;
+  CK(cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  c->stream = c->body_stream;
+  const cudaError_t e1 = launch_rebuild(c, c->d_open);
+  const cudaError_t e2 = e1 == cudaSuccess ? launch_lists(c, c->d_open) : e1;
+  c->stream = main;
+  cudaGraph_t out = nullptr;
+  const cudaError_t e3 = cudaStreamEndCapture(c->body_stream, &out);
+  CK(e2);
+  CK(e3);
+  CK(cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return RELRES_OK;
+}
+
+// The work of one block of blk steps starting after `done` steps of the call.
+static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d_vel, int blk, int done,
+                                  bool graph) {
+  const unsigned* gate = &c->d_state->flags;
+  const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
+  CK(cudaMemcpyAsync(c->d_snap_x, c->d_xfx, xb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_snap_v, d_vel, vb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_snap_f, c->d_f_tot, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
+  CK(launch_csvr_draws(c, sp, blk));
+  for (int k = 0; k < blk; ++k) {
+    TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel));
+    if (graph) {
+      if (c->timing) CK(tic(c, RELRES_T_REBUILD));
+      relres_status s = add_rebuild_node(c);
+      if (s != RELRES_OK) return s;
+      if (c->timing) CK(toc(c));
+    } else {
+      TIMED(RELRES_T_REBUILD, launch_rebuild(c, gate));
+      TIMED(RELRES_T_LISTS, launch_lists(c, gate));
+    }
+    // energy steps are known here: the device sets DevState::ev by the same rule
+    const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
+    TIMED(RELRES_T_PAIR, launch_pairs(c, ev_step));
+    TIMED(RELRES_T_FINISH, launch_finish(c, ev_step, nullptr, d_vel));
+    TIMED(RELRES_T_THERMO, launch_thermo(c, sp, k));
+  }
+  return RELRES_OK;
+}
+
+// Instantiated graph for this block (re-captured when an input changed).
+static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_vel, int blk, int done) {
+  relres_ctx::StepGraph& g = c->sg;
+  const int phase = sp.thermo_every > 0 ? done % sp.thermo_every : 0;
+  if (g.valid && g.blk == blk && g.ev_phase == phase && g.thermo_every == sp.thermo_every &&
+      g.timing == int(c->timing) && g.dt == sp.dt && g.t_target == sp.t_target && g.tau == sp.tau &&
+      g.n_f == sp.n_f && g.kt == sp.kt && g.seed == sp.seed && g.vel == d_vel && g.thermo == sp.thermo &&
+      g.gen == c->buf_gen)
+    return RELRES_OK;
+  drop_step_graph(c);
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (!c->body_stream) CK(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking));
+  if (c->timing) {
+    g.events.resize(size_t(blk) * 2 * RELRES_T_NCLASS);
+    for (cudaEvent_t& e : g.events) CK(cudaEventCreate(&e));
+  }
+  const long long n0 = c->n_launches;
+  const cudaStream_t main = c->stream;
+  c->stream = c->cap_stream;
+  if (c->timing) {
+    c->cap_marks = &g.marks;
+    c->cap_events = &g.events;
+    c->cap_used = 0;
+  }
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  relres_status s = e == cudaSuccess ? record_block(c, sp, d_vel, blk, done, true) : RELRES_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->stream, &graph) : e;
+  c->stream = main;
+  c->cap_marks = nullptr;
+  c->cap_events = nullptr;
+  const long long captured = c->n_launches - n0;
+  c->n_launches = n0;
+  if (s == RELRES_OK && e2 != cudaSuccess) s = fail(c, RELRES_ERR_CUDA, cudaGetErrorString(e2));
+  if (s == RELRES_OK) {
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (e != cudaSuccess) s = fail(c, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (s != RELRES_OK) {
+    drop_step_graph(c);
+    return s;
+  }
+  // kernels: per step the rebuild body holds 6 (5 binning stages + lists) and
+  // the decide kernel 1 sits in the parent
+  g.k_body = 6;
+  g.k_parent = captured - g.k_body * blk;
+  g.valid = true;
+  g.blk = blk;
+  g.ev_phase = phase;
+  g.thermo_every = sp.thermo_every;
+  g.timing = int(c->timing);
+  g.dt = sp.dt;
+  g.t_target = sp.t_target;
+  g.tau = sp.tau;
+  g.n_f = sp.n_f;
+  g.kt = sp.kt;
+  g.seed = sp.seed;
+  g.vel = d_vel;
+  g.thermo = sp.thermo;
+  g.gen = c->buf_gen;
+  return RELRES_OK;
+}
+
+relres_status relres_set_graphs(relres_ctx* c, int enable) {
+  if (!c) return RELRES_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  drop_step_graph(c);
+  c->use_graphs = enable != 0;
+  return RELRES_OK;
+}
+
 relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_pos, double* d_vel,
                           double t_target, double tau_fs, uint64_t seed, int thermo_every,
                           double* d_thermo) {
@@ -547,30 +711,33 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
   CK(upload_type_consts(c, dt_fs));
   CK(launch_set_ab(c, 1.0, 1.0, 0));
   CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
-  const unsigned* gate = &c->d_state->flags;
   const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
   int done = 0, retries = 0;
   while (done < n_steps) {
     const int blk = std::min(kBlockSteps, n_steps - done);
-    CK(cudaMemcpyAsync(c->d_snap_x, c->d_xfx, xb, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_snap_v, d_vel, vb, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_snap_f, c->d_f_tot, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
-    CK(launch_csvr_draws(c, sp, blk));
-    for (int k = 0; k < blk; ++k) {
-      TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel));
-      TIMED(RELRES_T_REBUILD, launch_rebuild(c, gate));
-      TIMED(RELRES_T_LISTS, launch_lists(c, gate));
-      // energy steps are known here: the device sets DevState::ev by the same rule
-      const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
-      TIMED(RELRES_T_PAIR, launch_pairs(c, ev_step));
-      TIMED(RELRES_T_FINISH, launch_finish(c, ev_step, nullptr, d_vel));
-      TIMED(RELRES_T_THERMO, launch_thermo(c, sp, k));
+    const long long builds0 = c->h_state->n_builds;
+    if (c->use_graphs) {
+      s = step_graph(c, sp, d_vel, blk, done);
+      if (s != RELRES_OK) return s;
+      CK(cudaGraphLaunch(c->sg.exec, c->stream));
+    } else {
+      s = record_block(c, sp, d_vel, blk, done, false);
+      if (s != RELRES_OK) return s;
     }
     s = read_state(c);
     if (s != RELRES_OK) return s;
     s = flush_timing(c);
     if (s != RELRES_OK) return s;
+    if (c->use_graphs) {
+      c->n_launches += c->sg.k_parent + c->sg.k_body * std::max(0LL, c->h_state->n_builds - builds0);
+      if (c->timing)
+        for (const relres_ctx::Mark& m : c->sg.marks) {
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, m.a, m.b));
+          c->t_ms[m.cls] += ms;
+          c->t_cnt[m.cls] += 1;
+        }
+    }
     const unsigned fl = c->h_state->flags;
     if (fl & F_BADCELL) return fail(c, RELRES_ERR_CUDA, "cell binning produced an out-of-range index");
     if (fl & (F_OVERFLOW_FG | F_OVERFLOW_CG | F_NONFINITE)) {
@@ -677,6 +844,9 @@ const char* relres_last_error(relres_ctx* c) { return c ? c->err.c_str() : "null
 void relres_destroy(relres_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_step_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->body_stream) cudaStreamDestroy(c->body_stream);
   dfree(c->d_tab);
   dfree(c->d_tabd);
   dfree(c->d_cdt);

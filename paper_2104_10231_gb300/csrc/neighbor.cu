@@ -486,6 +486,18 @@ cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
   return cudaGetLastError();
 }
 
+// One thread: open the rebuild node of this step of a CUDA graph iff the
+// displacement trigger fired (F_REBUILD is set by the drift kernel).
+__global__ void k_decide(const DevState* st, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, (st->flags & F_REBUILD) ? 1u : 0u);
+}
+
+cudaError_t launch_decide(relres_ctx* c, cudaGraphConditionalHandle h) {
+  k_decide<<<1, 1, 0, c->stream>>>(c->d_state, h);
+  RELRES_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
   if (gate == nullptr) gate = c->d_open;
   const float s0 = float(c->box[0] / 4294967296.0), s1 = float(c->box[1] / 4294967296.0),

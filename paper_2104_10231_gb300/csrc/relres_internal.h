@@ -228,6 +228,32 @@ struct relres_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<Mark> marks;
   size_t ev_used = 0;
+
+  // CUDA graph of one block of MD steps (relres_step): the list rebuild of
+  // each step is a conditional node whose flag a one-thread kernel sets from
+  // the device displacement trigger.  Everything below is baked into the
+  // instantiated graph; it is re-captured when any of it changes.
+  bool use_graphs = true;
+  long long buf_gen = 0;  // bumped whenever a buffer a graph may reference is reallocated
+  struct StepGraph {
+    bool valid = false;
+    int blk = 0, ev_phase = 0, thermo_every = 0, timing = 0;
+    double dt = 0, t_target = 0, tau = 0, n_f = 0, kt = 0;
+    unsigned long long seed = 0;
+    const double* vel = nullptr;
+    double* thermo = nullptr;
+    long long gen = -1;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<Mark> marks;          // event pairs recorded by the graph's own nodes
+    std::vector<cudaEvent_t> events;  // owned by the graph
+    long long k_parent = 0;           // kernels per launch outside the rebuild bodies
+    long long k_body = 0;             // kernels per executed rebuild body
+  } sg;
+  cudaStream_t cap_stream = nullptr;   // capture of the step graph
+  cudaStream_t body_stream = nullptr;  // capture of the conditional rebuild bodies
+  std::vector<Mark>* cap_marks = nullptr;     // non-null while capturing with timing
+  std::vector<cudaEvent_t>* cap_events = nullptr;
+  size_t cap_used = 0;
   double t_ms[RELRES_T_NCLASS] = {};
   long long t_cnt[RELRES_T_NCLASS] = {};
 };
@@ -244,6 +270,8 @@ cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, doubl
 
 // neighbour lists; gate: device flag word (rebuild only if F_REBUILD set) or null
 cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate);
+// sets the conditional of a graph's rebuild node from the device flag word
+cudaError_t launch_decide(relres_ctx* c, cudaGraphConditionalHandle h);
 cudaError_t launch_lists(relres_ctx* c, const unsigned* gate);
 
 // Forces.  ev: this evaluation also adds energies and virial to the

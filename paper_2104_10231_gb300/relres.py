@@ -33,7 +33,7 @@ RELRES_PAIR_FIELDS = 26
 EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres_set_topology",
             "relres_build_neighbors", "relres_compute", "relres_step", "relres_set_step_counter",
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
-            "relres_destroy", "relres_pair_forces_static"]
+            "relres_destroy", "relres_pair_forces_static", "relres_set_graphs"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo"]
 
@@ -107,6 +107,7 @@ def load():
     L.relres_set_step_counter.argtypes = [vp, C.c_longlong]
     L.relres_get_stats.argtypes = [vp, C.POINTER(relres_stats)]
     L.relres_set_timing.argtypes = [vp, C.c_int]
+    L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_get_timings.argtypes = [vp, _dp, C.POINTER(C.c_longlong), C.c_int]
     L.relres_pair_forces_static.argtypes = [C.POINTER(relres_params), C.c_int, vp, vp, _dp, vp, vp, vp,
                                             vp, vp, vp]
@@ -289,6 +290,10 @@ def relres_set_timing(ctx, enable):
     _check(load().relres_set_timing(ctx, 1 if enable else 0), ctx)
 
 
+def relres_set_graphs(ctx, enable):
+    _check(load().relres_set_graphs(ctx, 1 if enable else 0), ctx)
+
+
 def relres_get_timings(ctx):
     """{class: (total_ms, launches)} for the kernel classes of relres.h."""
     n = len(TIMING_CLASSES)
@@ -352,6 +357,9 @@ class Context:
 
     def set_timing(self, enable):
         relres_set_timing(self.ctx, enable)
+
+    def set_graphs(self, enable):
+        relres_set_graphs(self.ctx, enable)
 
     def timings(self):
         return relres_get_timings(self.ctx)

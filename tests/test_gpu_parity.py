@@ -221,6 +221,35 @@ def test_fp32_nve_energy_drift(torch):
     assert drift < 2e-3, drift
 
 
+def test_graph_and_stream_paths_agree_bitwise(torch):
+    # relres_step as CUDA graphs (conditional rebuild nodes) and as stream
+    # launches (rebuild kernels gated on the device flag): same bits, same
+    # rebuilds; repeated calls reuse the captured graph
+    s = S.neopentane(n_mol=500, seed=12)
+    outs = []
+    for graphs in (True, False):
+        ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+        ctx.set_graphs(graphs)
+        p = _dev(torch, s.pos)
+        v = _dev(torch, s.vel)
+        ctx.build_neighbors(p, s.box)
+        th = torch.zeros((30, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+        ctx.set_timing(True)
+        for _ in range(3):
+            ctx.step(100, 2.0, p, v, t_target=260.0, tau_fs=100.0, seed=3, thermo_every=10, d_thermo=th)
+        torch.cuda.synchronize()
+        outs.append((p.cpu().numpy(), v.cpu().numpy(), th.cpu().numpy(), ctx.stats(), ctx.timings()))
+        ctx.close()
+    (pg, vg, tg, sg, mg), (ps, vs, ts, ss, ms) = outs
+    assert sg["n_builds"] == ss["n_builds"] and sg["n_builds"] >= 3
+    assert np.array_equal(pg, ps) and np.array_equal(vg, vs) and np.array_equal(tg, ts)
+    # 300 steps plus the force evaluation at the start of the first call
+    assert mg["pair"][1] == ms["pair"][1] == 301
+    assert mg["rebuild"][1] == 300 and mg["rebuild"][0] > 0.0
+    # graph mode launches no binning or list kernel on steps without a rebuild
+    assert sg["n_launches"] < ss["n_launches"]
+
+
 def test_box_too_small_is_an_error(torch):
     s = S.propane(n_mol=64, box=25.0)
     ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
