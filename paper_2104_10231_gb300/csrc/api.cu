@@ -98,6 +98,9 @@ int round_cap(double x, int limit) {
 
 relres_status alloc_lists(relres_ctx* c) {
   ++c->buf_gen;
+  // list offsets are 32-bit inside the list kernel
+  if (double(c->cap_fg) * c->n >= 2147483648.0 || double(c->cap_cg) * c->n_h >= 2147483648.0)
+    return fail(c, RELRES_ERR_NOMEM, "neighbour list larger than 2^31 entries");
   CK(dalloc(&c->d_nbr_fg, size_t(c->cap_fg) * c->n));
   if (c->has_cg && c->n_h > 0) CK(dalloc(&c->d_nbr_cg, size_t(c->cap_cg) * c->n_h));
   return RELRES_OK;
@@ -377,6 +380,9 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   for (int k = 0; k < 4 * t->n_dihedral_types && t->n_dihedrals; ++k) dp[k] = t->dihedral_k[k];
 
   c->n = n;
+  c->excl_window = 0;
+  for (int i = 0; i < n; ++i)
+    for (int m = eoff[i]; m < eoff[i + 1]; ++m) c->excl_window = std::max(c->excl_window, std::abs(eidx[m] - i));
   c->h_type.assign(t->type, t->type + n);
   c->mass_by_type.assign(t->mass_by_type, t->mass_by_type + c->n_types);
   c->n_h = 0;

@@ -214,12 +214,12 @@ struct ListArgs {
   int nslots;
   const int4* pos;
   const int* perm;
-  const int* rank;  // atom -> slot of this list (-1: not in it)
   GridArgs g;
   float sx, sy, sz;
   float rl2;
   const int* excl_off;
   const int* excl_idx;
+  int excl_window;  // every excluded pair (i, j) has |i - j| <= excl_window (atom ids)
   int cap;
   int* nbr;
   int* cnt;
@@ -244,44 +244,44 @@ constexpr int kListThreads = 128;  // 4 warps per cell
 
 __device__ __forceinline__ float wrap1(float d, float l, float il) { return d - l * rintf(d * il); }
 
-// One cell atom (slot s, relative position p) against a staged window: 32
-// candidates per iteration, accepted ones appended at k in window order.
-// Returns the new count.
+// One cell atom (slot s, atom id ai, relative position p) against a staged
+// window padded to a multiple of 32 (padding sits far outside every cutoff):
+// 32 candidates per iteration, accepted ones appended at k in window order.
+// Exclusions: a candidate whose atom id lies within the exclusion window of
+// ai (this includes ai itself) is checked against ai's exclusion list; all
+// others cannot be excluded.  Returns the new count.
 template <bool WRAP>
-__device__ __forceinline__ int scan_window(const float4* s_pos, int wn, int s, float px, float py, float pz,
-                                           float rl2, float lx, float ly, float lz, const int (&ex)[8], int ne,
-                                           int e0, const int* excl_idx, const int* perm, int* nbr, int nslots,
-                                           int cap, int k) {
+__device__ __forceinline__ int scan_window(const float4* s_pos, const int* s_atom, int wn32, int ai,
+                                           float px, float py, float pz, float rl2, float lx, float ly,
+                                           float lz, int e0, int e1, const int* excl_idx, int win,
+                                           int* nbr_s, unsigned stride, int cap, int k) {
   const int lane = threadIdx.x & 31;
-  for (int j0 = 0; j0 < wn; j0 += 32) {
-    const int jj = j0 + lane;
-    bool acc = false;
-    int t = -1;
-    if (jj < wn) {
-      const float4 q = s_pos[jj];
-      t = __float_as_int(q.w);
-      float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-      if (WRAP) {
-        dx = wrap1(dx, lx, 1.f / lx);
-        dy = wrap1(dy, ly, 1.f / ly);
-        dz = wrap1(dz, lz, 1.f / lz);
-      }
-      acc = t != s && dx * dx + dy * dy + dz * dz < rl2;
+  const unsigned below = (1u << lane) - 1u;
+  for (int j0 = 0; j0 < wn32; j0 += 32) {
+    const float4 q = s_pos[j0 + lane];
+    float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+    if (WRAP) {
+      dx = wrap1(dx, lx, 1.f / lx);
+      dy = wrap1(dy, ly, 1.f / ly);
+      dz = wrap1(dz, lz, 1.f / lz);
     }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) acc = acc && t != ex[e];
-    if (acc && ne > 8) {
-      const int tj = perm[t];
-      for (int e = 8; e < ne; ++e) acc = acc && excl_idx[e0 + e] != tj;
+    bool acc = dx * dx + dy * dy + dz * dz < rl2;
+    const int aj = s_atom[j0 + lane];
+    if (WRAP) acc = acc && aj >= 0;  // wrapped padding can land anywhere
+    if (acc && unsigned(aj - ai + win) <= unsigned(2 * win)) {
+      acc = aj != ai;
+      for (int e = e0; e < e1; ++e) acc = acc && excl_idx[e] != aj;
     }
     const unsigned b = __ballot_sync(0xffffffffu, acc);
-    const int kk = k + __popc(b & ((1u << lane) - 1u));
-    if (acc && kk < cap) nbr[((size_t(kk >> 2) * nslots + s) << 2) + (kk & 3)] = t;
+    const int kk = k + __popc(b & below);
+    // entry kk of this slot: int ((kk >> 2) * nslots + s) * 4 + (kk & 3)
+    if (acc && kk < cap) nbr_s[unsigned(kk >> 2) * stride + unsigned(kk & 3)] = __float_as_int(q.w);
     k += __popc(b);
   }
   return k;
 }
-constexpr int kListWindow = 1024;  // candidates staged in shared memory at a time
+
+constexpr int kListWindow = 1024;  // candidates staged in shared memory at a time (a multiple of 32)
 constexpr int kListGroup = 64;     // cell atoms handled per pass
 
 // One block per cell (CG-grid cells first, then FG-grid cells).  The block
@@ -294,6 +294,7 @@ constexpr int kListGroup = 64;     // cell atoms handled per pass
 // order (ballot + prefix count), so the list is deterministic.
 __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg, int ncell_cg, int cb) {
   __shared__ float4 s_pos[kListWindow];  // x, y, z relative; w = slot index bits
+  __shared__ int s_atom[kListWindow];    // atom id of each staged candidate
   __shared__ int s_cstart[27], s_coff[28];
   __shared__ int s_k[kListGroup];
   __shared__ int s_max;
@@ -304,7 +305,7 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
     int nslots;
     const int4* pos;
     const int* perm;
-    const int* rank;
+    int excl_window;
     int n0, n1, n2;
     const int* rank_of;
     const int* start;
@@ -323,7 +324,7 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
   RELRES_PICK(nslots);
   RELRES_PICK(pos);
   RELRES_PICK(perm);
-  RELRES_PICK(rank);
+  RELRES_PICK(excl_window);
   RELRES_PICK(sx);
   RELRES_PICK(sy);
   RELRES_PICK(sz);
@@ -384,32 +385,37 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
     for (int w0 = 0; w0 < total; w0 += kListWindow) {
       const int wn = min(kListWindow, total - w0);
       __syncthreads();
-      for (int k = threadIdx.x; k < wn; k += blockDim.x) {
-        const int gidx = w0 + k;
-        int m = 0;  // stencil cell holding candidate gidx
+      const int wn32 = (wn + 31) & ~31;
+      for (int k = threadIdx.x; k < wn32; k += blockDim.x) {
+        if (k < wn) {
+          const int gidx = w0 + k;
+          int m = 0;  // stencil cell holding candidate gidx
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (m + step < 28 && s_coff[m + step] <= gidx) m += step;
-        const int t = s_cstart[m] + (gidx - s_coff[m]);
-        const int4 q = a.pos[t];
-        s_pos[k] = make_float4(dfix32(q.x, ref.x, a.sx), dfix32(q.y, ref.y, a.sy), dfix32(q.z, ref.z, a.sz),
-                               __int_as_float(t));
+          for (int step = 16; step > 0; step >>= 1)
+            if (m + step < 28 && s_coff[m + step] <= gidx) m += step;
+          const int t = s_cstart[m] + (gidx - s_coff[m]);
+          const int4 q = a.pos[t];
+          s_pos[k] = make_float4(dfix32(q.x, ref.x, a.sx), dfix32(q.y, ref.y, a.sy),
+                                 dfix32(q.z, ref.z, a.sz), __int_as_float(t));
+          s_atom[k] = a.perm[t];
+        } else {  // padding: never within a list radius
+          s_pos[k] = make_float4(3.0e18f, 3.0e18f, 3.0e18f, __int_as_float(0));
+          s_atom[k] = -1;
+        }
       }
       __syncthreads();
       for (int il = warp; il < ng; il += blockDim.x >> 5) {
         const int s = i0 + g0 + il;
         const int4 p = a.pos[s];
         const float px = dfix32(p.x, ref.x, a.sx), py = dfix32(p.y, ref.y, a.sy), pz = dfix32(p.z, ref.z, a.sz);
-        // excluded partners as slots of this list (up to 8 in registers; more: checked in global memory)
-        const int atom = a.perm[s];
-        const int e0 = a.excl_off[atom], ne = a.excl_off[atom + 1] - e0;
-        int ex[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) ex[e] = e < ne ? a.rank[a.excl_idx[e0 + e]] : -1;
-        const int k = wrap ? scan_window<true>(s_pos, wn, s, px, py, pz, a.rl2, lx, ly, lz, ex, ne, e0,
-                                               a.excl_idx, a.perm, a.nbr, a.nslots, a.cap, s_k[il])
-                           : scan_window<false>(s_pos, wn, s, px, py, pz, a.rl2, lx, ly, lz, ex, ne, e0,
-                                                a.excl_idx, a.perm, a.nbr, a.nslots, a.cap, s_k[il]);
+        const int ai = a.perm[s];
+        const int e0 = a.excl_off[ai], e1 = a.excl_off[ai + 1];
+        int* const nbr_s = a.nbr + 4 * size_t(s);
+        const unsigned stride = 4u * unsigned(a.nslots);
+        const int k = wrap ? scan_window<true>(s_pos, s_atom, wn32, ai, px, py, pz, a.rl2, lx, ly, lz, e0, e1,
+                                               a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il])
+                           : scan_window<false>(s_pos, s_atom, wn32, ai, px, py, pz, a.rl2, lx, ly, lz, e0, e1,
+                                                a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il]);
         if (lane == 0) s_k[il] = k;
       }
     }
@@ -504,15 +510,15 @@ cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
               s2 = float(c->box[2] / 4294967296.0);
   DevState* st = c->d_state;
   const double rf = c->rlist_fg_cut + c->prm.skin;
-  const ListArgs fg{c->n, c->d_pos_fg, c->d_perm_fg, c->d_rank_fg, grid_args(c->gfg), s0, s1, s2,
-                    float(rf * rf), c->d_excl_off, c->d_excl_idx, c->cap_fg, c->d_nbr_fg, c->d_cnt_fg,
+  const ListArgs fg{c->n, c->d_pos_fg, c->d_perm_fg, grid_args(c->gfg), s0, s1, s2, float(rf * rf),
+                    c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_fg, c->d_nbr_fg, c->d_cnt_fg,
                     &st->max_fg, &st->tot_fg, &st->flags, F_OVERFLOW_FG};
   ListArgs cg = fg;  // stand-in when there is no CG list (its blocks are not launched)
   int ncell_cg = 0;
   if (c->has_cg && c->n_h > 0) {
     const double rc = c->rlist_cg_cut + c->skin_cg;
-    cg = ListArgs{c->n_h, c->d_pos_cg, c->d_perm_cg, c->d_rank_cg, grid_args(c->gcg), s0, s1, s2,
-                  float(rc * rc), c->d_excl_off, c->d_excl_idx, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg,
+    cg = ListArgs{c->n_h, c->d_pos_cg, c->d_perm_cg, grid_args(c->gcg), s0, s1, s2, float(rc * rc),
+                  c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg,
                   &st->max_cg, &st->tot_cg, &st->flags, F_OVERFLOW_CG};
     ncell_cg = c->gcg.ncell;
   }

@@ -144,6 +144,7 @@ struct relres_ctx {
   std::vector<double> mass_by_type;
   int* d_type = nullptr;
   int* d_excl_off = nullptr;
+  int excl_window = 0;  // max |i - j| over excluded pairs
   int* d_excl_idx = nullptr;
   int n_bonds = 0, n_angles = 0, n_dih = 0;
   int4* d_bonds = nullptr;      // i, j, type, 0
