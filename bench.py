@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--n-mol", type=int, default=200_000)
     ap.add_argument("--equil", type=int, default=200, help="untimed equilibration steps")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the step kernels one by one on the stream instead of CUDA graphs "
+                         "(same kernels; ncu cannot list kernels inside graphs with conditional nodes)")
     ap.add_argument("--thermo-every", type=int, default=100,
                     help="energy/virial/temperature row every this many timed steps (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -66,6 +69,7 @@ def workload_config(args, n_atoms, box):
         "l2": "inputs larger than L2 (neighbour lists ~0.5 GB, state 64 MB)",
         "parallelism": "replicas only (one independent system per GPU)",
         "thermo_every": args.thermo_every,
+        "execution": "stream launches" if args.no_graphs else "CUDA graph per 100 steps, conditional rebuild node",
         "seed": 2104,
     }
 
@@ -197,6 +201,7 @@ def ours(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s), stream=stream)
+        ctx.set_graphs(not args.no_graphs)
         pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
         vel = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
         ctx.build_neighbors(pos, s.box)
@@ -253,6 +258,7 @@ def ours(args):
         sf = S.fg_only(s)
         with torch.cuda.stream(stream):
             ctxf = R.Context(R.params_for(sf, R.RELRES_PREC_FP32), R.topology_for(sf), stream=stream)
+            ctxf.set_graphs(not args.no_graphs)
             posf = pos.clone()
             velf = vel.clone()
             ctxf.build_neighbors(posf, s.box)

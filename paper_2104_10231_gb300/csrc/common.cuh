@@ -99,6 +99,56 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* sh) {
 
 __device__ __forceinline__ long long to_fix_sum(double v) { return __double2ll_rn(v * kFix); }
 
+// ---- float-float ("double-single") arithmetic (Dekker 1971; Knuth's
+// two-sum) for the FP32 path where FP32 alone is not enough: stiff bonds and
+// the pair energies of energy steps.  A value is hi + lo with |lo| <=
+// ulp(hi)/2.  The rounding intrinsics keep the error-free transformations
+// from being contracted into FMAs.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff ff_quick(float a, float b) {  // requires |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff t = ff_two_sum(a.hi, b.hi);
+  return ff_quick(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = fmaf(a.hi, b.hi, -p);
+  return ff_quick(p, __fadd_rn(e, __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi))));
+}
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  if (!(a.hi > 0.f)) return ff{0.f, 0.f};
+  const float r = sqrtf(a.hi);
+  const float p = __fmul_rn(r, r);
+  const float pe = fmaf(r, r, -p);
+  return ff_quick(r, __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo), __fmul_rn(2.f, r)));
+}
+__device__ __forceinline__ float ff_val(ff a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ ff ff_from(float a) { return ff{a, 0.f}; }
+// 1/a: FP32 estimate and one Newton step in float-float
+__device__ __forceinline__ ff ff_rcp(ff a) {
+  const float y = __frcp_rn(a.hi);
+  const ff e = ff_sub(ff_from(1.f), ff_mul(a, ff_from(y)));
+  return ff_add(ff_from(y), ff_mul(ff_from(y), e));
+}
+// exact wrapped 32-bit fixed-point difference a - b, times the box scale s
+__device__ __forceinline__ ff ff_fixed_diff32(int a, int b, ff s) {
+  const int d = int(unsigned(a) - unsigned(b));
+  const float hi = __int2float_rn(d);
+  const float lo = __int2float_rn(d - __float2int_rn(hi));
+  return ff_mul(ff_quick(hi, lo), s);
+}
+
 // Integer accumulators: a block's FP64 sum is converted to 64-bit fixed point
 // and added with an integer atomic (exact, independent of order).
 __device__ __forceinline__ void acc_add(long long* acc, double v) {

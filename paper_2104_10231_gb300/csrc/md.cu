@@ -145,39 +145,6 @@ struct BondedArgs {
   const float* angle_fpar;  // FP32 path: k, theta0, cos theta0 (hi, lo), sin theta0 (hi, lo), 0, 0
 };
 
-// ---- float-float ("double-single") arithmetic for the FP32 bonded path.
-// A value is hi + lo with |lo| <= ulp(hi)/2.  The rounding intrinsics keep
-// the error-free transformations from being contracted into FMAs.
-struct ff {
-  float hi, lo;
-};
-__device__ __forceinline__ ff ff_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ ff ff_quick(float a, float b) {  // requires |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const ff t = ff_two_sum(a.hi, b.hi);
-  return ff_quick(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  const float e = fmaf(a.hi, b.hi, -p);
-  return ff_quick(p, __fadd_rn(e, __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi))));
-}
-__device__ __forceinline__ ff ff_sqrt(ff a) {
-  if (!(a.hi > 0.f)) return ff{0.f, 0.f};
-  const float r = sqrtf(a.hi);
-  const float p = __fmul_rn(r, r);
-  const float pe = fmaf(r, r, -p);
-  return ff_quick(r, __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo), __fmul_rn(2.f, r)));
-}
-__device__ __forceinline__ float ff_val(ff a) { return __fadd_rn(a.hi, a.lo); }
 // exact 64-bit fixed-point difference a - b, scaled to Angstrom
 __device__ __forceinline__ ff ff_fixed_diff(unsigned long long a, unsigned long long b, ff scale) {
   const long long d = (long long)(a - b);

@@ -82,7 +82,8 @@ __global__ void k_bin(int n, const unsigned* gate, const unsigned long long* __r
 }
 
 // One block per grid: exclusive scan of counts into start[0..ncell], counts
-// reset to zero (they become the scatter cursors).
+// reset to zero (they become the scatter cursors).  Tiles of 4 cells per
+// thread, scanned block-wide with warp shuffles, a running carry between tiles.
 __global__ void k_scan(const unsigned* gate, int valid0, int ncell0, int* start0, int* count0, int valid1,
                        int ncell1, int* start1, int* count1, DevState* st) {
   if (gate_closed(gate)) return;
@@ -98,40 +99,48 @@ __global__ void k_scan(const unsigned* gate, int valid0, int ncell0, int* start0
   int* const count = blockIdx.x == 0 ? count0 : count1;
   if (!valid) return;
   __shared__ int sh[1024 / 32];
-  const int nt = blockDim.x;
-  const int per = (ncell + nt - 1) / nt;
-  const int b = threadIdx.x * per, e = min(ncell, b + per);
-  int local = 0;
-  for (int c = b; c < e; ++c) local += count[c];
-  // block exclusive scan of `local`
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int incl = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) sh[wid] = incl;
+  __shared__ int s_carry;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  if (wid == 0) {
-    int v = lane < (nt >> 5) ? sh[lane] : 0;
-    int iv = v;
+  for (int base = 0; base < ncell; base += 4 * blockDim.x) {
+    const int c0 = base + 4 * threadIdx.x;
+    int v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = c0 + q < ncell ? count[c0 + q] : 0;
+    const int tsum = v[0] + v[1] + v[2] + v[3];
+    int incl = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, iv, o);
-      if (lane >= o) iv += t;
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    if (lane < (nt >> 5)) sh[lane] = iv - v;
+    if (lane == 31) sh[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      }
+      if (lane < nw) sh[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const int carry = s_carry;
+    int run = carry + (wid > 0 ? sh[wid - 1] : 0) + incl - tsum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (c0 + q < ncell) {
+        start[c0 + q] = run;
+        count[c0 + q] = 0;
+        run += v[q];
+      }
+    __syncthreads();  // every thread has read s_carry and sh
+    if (threadIdx.x == 0) s_carry = carry + sh[nw - 1];
+    __syncthreads();
   }
-  __syncthreads();
-  int run = sh[wid] + incl - local;
-  for (int c = b; c < e; ++c) {
-    const int k = count[c];
-    start[c] = run;
-    count[c] = 0;
-    run += k;
-  }
-  if (threadIdx.x == nt - 1) start[ncell] = run;
+  if (threadIdx.x == 0) start[ncell] = s_carry;
 }
 
 __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ type, int hyb_mask,
@@ -147,14 +156,17 @@ __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ t
 }
 
 // One warp per cell: the cell's atoms put in index order (the scatter order
-// is arbitrary).  Up to 32 atoms: each lane counts the smaller indices of its
-// cell (register shuffles) and writes its atom to that rank; larger cells
-// fall back to an insertion sort by one lane.  Resets the cell cursor.
-__global__ void k_sort_cells(const unsigned* gate, int fn, const int* fstart, int* fcount, int cn,
-                             const int* cstart, int* ccount, int* __restrict__ perm_fg,
-                             int* __restrict__ perm_cg) {
+// is arbitrary).  Each atom's new place is the number of smaller indices in
+// its cell: up to 32 atoms counted from registers (shuffles), up to 256 from a
+// per-warp shared-memory copy; larger cells fall back to an insertion sort by
+// one lane.  Resets the cell cursor.
+constexpr int kSortSmem = 256;
+__global__ void __launch_bounds__(kThreads) k_sort_cells(const unsigned* gate, int fn, const int* fstart,
+                                                         int* fcount, int cn, const int* cstart, int* ccount,
+                                                         int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
   if (gate_closed(gate)) return;
-  const int lane = threadIdx.x & 31;
+  __shared__ int s_v[kThreads / 32][kSortSmem];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < fn + cn; t += nwarps) {
     const bool fg = t < fn;
@@ -169,6 +181,17 @@ __global__ void k_sort_cells(const unsigned* gate, int fn, const int* fstart, in
       for (int k = 0; k < m; ++k) rank += __shfl_sync(0xffffffffu, v, k) < v ? 1 : 0;
       __syncwarp();
       if (lane < m) perm[lo + rank] = v;
+    } else if (m <= kSortSmem) {
+      int* const sv = s_v[wid];
+      for (int k = lane; k < m; k += 32) sv[k] = perm[lo + k];
+      __syncwarp();
+      for (int k = lane; k < m; k += 32) {
+        const int v = sv[k];
+        int rank = 0;
+        for (int q = 0; q < m; ++q) rank += sv[q] < v ? 1 : 0;
+        perm[lo + rank] = v;
+      }
+      __syncwarp();  // the copy is reused by this warp's next cell
     } else if (lane == 0) {
       for (int k = lo + 1; k < hi; ++k) {
         const int v = perm[k];

@@ -18,9 +18,10 @@
 // entry gets an exact wrapped integer difference converted to FP32 and its
 // region selected without branches.  The owner accumulates its force in
 // registers and writes it once (no atomics).  Energy and virial are computed
-// only on the steps that need them (EV template): they are reduced per block
-// (warp shuffles, then shared memory) and added to 64-bit fixed-point
-// accumulators with integer atomics.  The FP64 variant (R = double) reads 64-bit fixed-point
+// only on the steps that need them (EV template); pair energies of the FP32
+// path are float-float (see FgE), reduced per block in FP64 (warp shuffles,
+// then shared memory) and added to 64-bit fixed-point accumulators with
+// integer atomics.  The FP64 variant (R = double) reads 64-bit fixed-point
 // positions and computes every term in double.
 #include "common.cuh"
 
@@ -58,10 +59,22 @@ __device__ __forceinline__ int ptype(const Pos64& p) { return int(p.t); }
 __device__ __forceinline__ int4 load_pos(const int4* p, int j) { return __ldg(p + j); }
 __device__ __forceinline__ Pos64 load_pos(const Pos64* p, int j) { return p[j]; }
 
+// FP64 1/x and 1/sqrt(x) from the FP32 hardware estimate plus one Newton
+// step (relative error ~1e-14; FP64 division and square root are many times
+// slower on this part).
+__device__ __forceinline__ double rcp_d(double x) {
+  const double y = double(__frcp_rn(float(x)));
+  return y * fma(-x, y, 2.0);
+}
+__device__ __forceinline__ double rsqrt_d(double x) {
+  const double y = double(rsqrtf(float(x)));
+  return y * fma(-0.5 * x * y, y, 1.5);
+}
+
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ double recip(double x) { return rcp_d(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt_d(x); }
 
 __device__ __forceinline__ void store_force(float4* f, int i, float x, float y, float z) {
   f[i] = make_float4(x, y, z, 0.f);
@@ -134,6 +147,74 @@ struct CgRow {
   float4 d;  // 3 g3, 4 g4, -, -
 };
 
+// Energy constants of one type pair for the FP32 path (energy steps) as
+// float-float values.  Pair energies of energy steps are evaluated in
+// float-float arithmetic (~48-bit): in FP32 alone, rounding that is the same
+// for every pair of a type (constants, the box scale, approximate
+// reciprocals) biases the total, and the FG and CG parts largely cancel in
+// it, so 1e-7 of the total is out of reach; FP64 proper runs at a small
+// fraction of the FP32 rate on this part.
+struct FgE {
+  ff c12, c6, shift, rsm, g[5];
+};
+struct CgE {
+  ff c12, c6, gam, rsm, rcm, on0, on3, on4, close, g[5];
+};
+__device__ __forceinline__ ff split_ff(double v) {
+  const float h = float(v);
+  return ff{h, float(v - double(h))};
+}
+__device__ __forceinline__ void pack_energy_rows(const PairTab<double>& t, FgE& f, CgE& c) {
+  f.c12 = split_ff(t.c12f);
+  f.c6 = split_ff(t.c6f);
+  f.shift = split_ff(t.e_fg_shift);
+  f.rsm = split_ff(t.rsm);
+  c.c12 = split_ff(t.c12c);
+  c.c6 = split_ff(t.c6c);
+  c.gam = split_ff(t.gam_cm);
+  c.rsm = split_ff(t.rsm);
+  c.rcm = split_ff(t.rcm);
+  c.on0 = split_ff(t.on0);
+  c.on3 = split_ff(t.on3);
+  c.on4 = split_ff(t.on4);
+  c.close = split_ff(t.e_cg_close);
+  for (int m = 0; m < 5; ++m) {
+    f.g[m] = split_ff(t.fg[m]);
+    c.g[m] = split_ff(t.cgo[m]);
+  }
+}
+__device__ __forceinline__ ff poly5_ff(const ff (&g)[5], ff d) {
+  ff p = g[4];
+#pragma unroll
+  for (int m = 3; m >= 0; --m) p = ff_add(ff_mul(p, d), g[m]);
+  return p;
+}
+__device__ __forceinline__ ff lj_ff(const ff& c12, const ff& c6, ff r2i) {
+  const ff r6i = ff_mul(ff_mul(r2i, r2i), r2i);
+  return ff_sub(ff_mul(c12, ff_mul(r6i, r6i)), ff_mul(c6, r6i));
+}
+// FG energy of a pair inside r_s+ (regions chosen on the leading part: the
+// potential is C2 at r_s-, so a pair rounded across it changes nothing)
+__device__ __forceinline__ ff fg_energy_ff(const FgE& T, float rsm2, ff r2) {
+  const ff e = r2.hi < rsm2 ? lj_ff(T.c12, T.c6, ff_rcp(r2)) : poly5_ff(T.g, ff_sub(ff_sqrt(r2), T.rsm));
+  return ff_sub(e, T.shift);
+}
+// CG energy of a pair inside r_c+
+__device__ __forceinline__ ff cg_energy_ff(const CgE& T, float4 radii2, ff r2) {
+  if (r2.hi < radii2.x) return T.close;
+  ff e;
+  if (r2.hi < radii2.y) {
+    const ff d = ff_sub(ff_sqrt(r2), T.rsm);
+    const ff d3 = ff_mul(ff_mul(d, d), d);
+    e = ff_add(T.on0, ff_mul(d3, ff_add(ff_mul(T.on4, d), T.on3)));
+  } else if (r2.hi < radii2.z) {
+    e = lj_ff(T.c12, T.c6, ff_rcp(r2));
+  } else {
+    e = poly5_ff(T.g, ff_sub(ff_sqrt(r2), T.rcm));
+  }
+  return ff_sub(e, T.gam);
+}
+
 __device__ __forceinline__ void pack_rows(const PairTab<float>& t, FgRow& f, CgRow& g) {
   f.a = make_float4(t.rsm2, t.rsp2, t.f12f, t.f6f);
   f.b = make_float4(t.rsm, t.fgd[0], t.fgd[1], t.fgd[2]);
@@ -179,10 +260,6 @@ __device__ __forceinline__ float cg_force(const CgRow& T, float r2) {
   return (r2 < a.x || !(r2 < a.w)) ? 0.f : fr;
 }
 
-__device__ __forceinline__ double dfix32d(int a, int b, double scale) {
-  return double(int(unsigned(a) - unsigned(b))) * scale;
-}
-
 template <typename R>
 struct ListWalk {
   int nslots;
@@ -199,17 +276,18 @@ struct PairLaunch {
   int nblk_cg;  // blocks [0, nblk_cg) walk the CG list, the rest the FG list
   ListWalk<R> fg, cg;
   const PairTab<R>* tab;
-  const PairTab<double>* tabd;  // FP64 table: energies of the FP32 path are evaluated in FP64
+  const PairTab<double>* tabd;  // FP64 table: source of the split energy constants of the FP32 path
   int nt;
   R sx, sy, sz;
-  double sxd, syd, szd;  // L / 2^32 (FP32 path) for the FP64 energy
+  float sxl, syl, szl;  // FP32 path: lo parts of L / 2^32 (float-float energies)
 };
 
 struct SmemTabs {
   const void* tab;
-  const PairTab<double>* tabd;
   const FgRow* fgr;
   const CgRow* cgr;
+  const FgE* fge;
+  const CgE* cge;
 };
 
 // Per-thread accumulators of one walk.
@@ -217,7 +295,8 @@ template <typename R>
 struct Acc {
   R fx = R(0), fy = R(0), fz = R(0);
   R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-  double e = 0.0;
+  R e = R(0);            // FP64 path: per-thread energy
+  ff eff = ff{0.f, 0.f};  // FP32 path: per-thread energy in float-float
 };
 
 template <typename R, bool CG, bool EV>
@@ -241,14 +320,17 @@ __device__ __forceinline__ void entry(const typename PosOf<R>::T& pi, const type
       A.w[3] += fr * dx * dy;
       A.w[4] += fr * dx * dz;
       A.w[5] += fr * dy * dz;
-      if (valid) {
-        const double ex = dfix32d(pi.x, pj.x, a.sxd), ey = dfix32d(pi.y, pj.y, a.syd),
-                     ez = dfix32d(pi.z, pj.z, a.szd);
-        const PairTab<double>& Td = S.tabd[row];
-        double frd, epd;
-        if (CG ? cg_term<double, true>(Td, ex * ex + ey * ey + ez * ez, frd, epd)
-               : fg_term<double, true>(Td, ex * ex + ey * ey + ez * ez, frd, epd))
-          A.e += epd;
+      // float-float energy inside the cutoff only (padding entries carry
+      // r2 = 3e38; the energy and its slope vanish at the cutoff, so the FP32
+      // decision is harmless), from the exact integer coordinate differences
+      const float rcut2 = CG ? S.cgr[row].a.w : S.fgr[row].a.y;
+      if (r2 < rcut2) {
+        const ff ex = ff_fixed_diff32(pi.x, pj.x, ff{a.sx, a.sxl});
+        const ff ey = ff_fixed_diff32(pi.y, pj.y, ff{a.sy, a.syl});
+        const ff ez = ff_fixed_diff32(pi.z, pj.z, ff{a.sz, a.szl});
+        const ff r2e = ff_add(ff_add(ff_mul(ex, ex), ff_mul(ey, ey)), ff_mul(ez, ez));
+        A.eff = ff_add(A.eff, CG ? cg_energy_ff(S.cge[row], S.cgr[row].a, r2e)
+                                 : fg_energy_ff(S.fge[row], S.fgr[row].a.x, r2e));
       }
     }
   } else {
@@ -308,7 +390,7 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
   if (EV) {
     // per-thread sums are R (FP64 for the energy); the block sum is taken in FP64
     double accd[kNQ];
-    accd[0] = A.e;
+    accd[0] = std::is_same<R, float>::value ? double(A.eff.hi) + double(A.eff.lo) : double(A.e);
 #pragma unroll
     for (int q = 0; q < 6; ++q) accd[q + 1] = double(A.w[q]);
     __shared__ double sh[(kThreads / 32) * kNQ];
@@ -339,12 +421,11 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairLaunch<R> a) {
     S.fgr = fgr;
     S.cgr = cgr;
     if (EV) {
-      PairTab<double>* tabd = reinterpret_cast<PairTab<double>*>(carve(sizeof(PairTab<double>) * nrow));
-      const int words = nrow * int(sizeof(PairTab<double>) / sizeof(int));
-      const int* src = reinterpret_cast<const int*>(a.tabd);
-      int* dst = reinterpret_cast<int*>(tabd);
-      for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
-      S.tabd = tabd;
+      FgE* fge = reinterpret_cast<FgE*>(carve(sizeof(FgE) * nrow));
+      CgE* cge = reinterpret_cast<CgE*>(carve(sizeof(CgE) * nrow));
+      for (int r = threadIdx.x; r < nrow; r += blockDim.x) pack_energy_rows(a.tabd[r], fge[r], cge[r]);
+      S.fge = fge;
+      S.cge = cge;
     }
   } else {
     PairTab<R>* tab = reinterpret_cast<PairTab<R>*>(carve(sizeof(PairTab<R>) * nrow));
@@ -366,7 +447,8 @@ static size_t pair_smem(int nt, bool ev) {
   const size_t nrow = size_t(nt) * nt;
   auto up = [](size_t b) { return (b + 15) / 16 * 16; };
   if (std::is_same<R, float>::value)
-    return up(sizeof(FgRow) * nrow) + up(sizeof(CgRow) * nrow) + (ev ? up(sizeof(PairTab<double>) * nrow) : 0);
+    return up(sizeof(FgRow) * nrow) + up(sizeof(CgRow) * nrow) +
+           (ev ? up(sizeof(FgE) * nrow) + up(sizeof(CgE) * nrow) : 0);
   return up(sizeof(PairTab<R>) * nrow);
 }
 
@@ -377,9 +459,9 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   a.sx = R(c->box[0] / unit);
   a.sy = R(c->box[1] / unit);
   a.sz = R(c->box[2] / unit);
-  a.sxd = c->box[0] / 4294967296.0;
-  a.syd = c->box[1] / 4294967296.0;
-  a.szd = c->box[2] / 4294967296.0;
+  a.sxl = float(c->box[0] / unit - double(a.sx));
+  a.syl = float(c->box[1] / unit - double(a.sy));
+  a.szl = float(c->box[2] / unit - double(a.sz));
   a.nt = c->n_types;
   a.tab = static_cast<const PairTab<R>*>(c->d_tab);
   a.tabd = static_cast<const PairTab<double>*>(c->d_tabd);
