@@ -170,10 +170,11 @@ enum relres_timing_class {
   RELRES_T_DRIFT = 0,    /* kick + drift + sorted scatter + rebuild trigger */
   RELRES_T_REBUILD = 1,  /* binning, scan, scatter, in-cell sort, pack */
   RELRES_T_LISTS = 2,    /* FG and CG Verlet lists */
-  RELRES_T_PAIR = 3,     /* RelRes pair kernel over the FG and CG lists (one launch) */
+  RELRES_T_PAIR = 3,     /* RelRes pair kernel over the FG and CG lists (one launch), forces only */
   RELRES_T_FINISH = 4,   /* force sum + bonded terms + kinetic energy */
   RELRES_T_THERMO = 5,   /* reductions + CSVR factor */
-  RELRES_T_NCLASS = 6
+  RELRES_T_PAIR_EV = 6,  /* pair kernel on energy steps (forces + energy + virial) */
+  RELRES_T_NCLASS = 7
 };
 
 /*

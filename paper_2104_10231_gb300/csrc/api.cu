@@ -199,7 +199,7 @@ relres_status forces_now(relres_ctx* c, int ev_mode, double* d_forces, double* d
     if (s != RELRES_OK) return s;
   }
   CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
-  TIMED(RELRES_T_PAIR, launch_pairs(c, ev_mode == 1));
+  TIMED(ev_mode == 1 ? RELRES_T_PAIR_EV : RELRES_T_PAIR, launch_pairs(c, ev_mode == 1));
   TIMED(RELRES_T_FINISH, launch_finish(c, ev_mode == 1, d_forces, nullptr));
   if (ev_mode == 1) TIMED(RELRES_T_THERMO, launch_reduce_out(c, d_energy, d_virial));
   s = read_state(c);
@@ -605,7 +605,7 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
     }
     // energy steps are known here: the device sets DevState::ev by the same rule
     const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
-    TIMED(RELRES_T_PAIR, launch_pairs(c, ev_step));
+    TIMED(ev_step ? RELRES_T_PAIR_EV : RELRES_T_PAIR, launch_pairs(c, ev_step));
     TIMED(RELRES_T_FINISH, launch_finish(c, ev_step, nullptr, d_vel));
     TIMED(RELRES_T_THERMO, launch_thermo(c, sp, k));
   }

@@ -35,7 +35,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs"]
 RELRES_STATIC_MAX_ATOMS = 16384
-TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo"]
+TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev"]
 
 
 class RelresError(RuntimeError):

@@ -243,8 +243,10 @@ def test_graph_and_stream_paths_agree_bitwise(torch):
     (pg, vg, tg, sg, mg), (ps, vs, ts, ss, ms) = outs
     assert sg["n_builds"] == ss["n_builds"] and sg["n_builds"] >= 3
     assert np.array_equal(pg, ps) and np.array_equal(vg, vs) and np.array_equal(tg, ts)
-    # 300 steps plus the force evaluation at the start of the first call
-    assert mg["pair"][1] == ms["pair"][1] == 301
+    # 300 steps (30 of them energy steps) plus the force evaluation at the
+    # start of the first call
+    assert mg["pair"][1] == ms["pair"][1] == 271
+    assert mg["pair_ev"][1] == ms["pair_ev"][1] == 30
     assert mg["rebuild"][1] == 300 and mg["rebuild"][0] > 0.0
     # graph mode launches no binning or list kernel on steps without a rebuild
     assert sg["n_launches"] < ss["n_launches"]
