@@ -51,6 +51,12 @@ def lib():
             L.oracle_pair_forces_rows.argtypes = [C.c_int, dp, dp, ip, C.c_int, dp, ip, ip,
                                                   C.c_int, ip, dp, dp, C.c_int]
             L.oracle_pair_forces_rows.restype = C.c_int
+            L.oracle_u_tilde_d2.argtypes = [dp, dp, C.c_long, dp]
+            L.oracle_pair_param_grads.argtypes = [C.c_int, dp, dp, ip, C.c_int, dp, dp, ip, ip, dp,
+                                                  C.c_double, dp, C.c_int]
+            L.oracle_pair_param_grads.restype = C.c_int
+            L.oracle_pair_hvp.argtypes = [C.c_int, dp, dp, ip, C.c_int, dp, ip, ip, dp, dp, C.c_int]
+            L.oracle_pair_hvp.restype = C.c_int
             L.oracle_bonded.argtypes = [C.c_int, dp, dp, C.c_int, ip, ip, dp, dp, C.c_int, ip,
                                         ip, dp, dp, C.c_int, ip, ip, dp, dp, dp]
             L.oracle_bonded.restype = C.c_int
@@ -124,6 +130,53 @@ def pair_forces_rows(pos, box, types, table, n_types, rows, excl=None, n_threads
                                   _dp(table), _ip(eo), _ip(ei), len(rows), _ip(rows), _dp(f),
                                   _dp(e), int(n_threads))
     return f, e
+
+
+def u_tilde_d2(row, r):
+    """Second r-derivative of Eq. 20 for one record at the distances r."""
+    row = _d(row)
+    r = _d(np.atleast_1d(r))
+    out = np.zeros_like(r)
+    lib().oracle_u_tilde_d2(_dp(row), _dp(r), r.size, _dp(out))
+    return out
+
+
+def pair_param_grads(pos, box, types, table, dtable, n_types, g_energy=0.0, g_forces=None, excl=None,
+                     n_threads=0):
+    """d L / d (eps_fg, sig_fg, eps_cg, sig_cg) of every record (n_types^2 x 4)
+    for L with dL/dE_pair = g_energy and dL/dF_i = g_forces[i] (or None)."""
+    pos = _d(pos)
+    box = _d(box)
+    types = _i(types)
+    table = _d(table)
+    dtable = _d(dtable)
+    gf = None if g_forces is None else _d(g_forces)
+    out = np.zeros(n_types * n_types * 4)
+    eo, ei = (None, None) if excl is None else (_i(excl[0]), _i(excl[1]))
+    lib().oracle_pair_param_grads(pos.shape[0], _dp(pos), _dp(box), _ip(types), n_types, _dp(table),
+                                  _dp(dtable), _ip(eo), _ip(ei), None if gf is None else _dp(gf),
+                                  float(g_energy), _dp(out), int(n_threads))
+    return out.reshape(n_types * n_types, 4)
+
+
+def pair_hvp(pos, box, types, table, n_types, v, excl=None, n_threads=0):
+    """Hessian of the pair energy times v (n x 3): sum_j h_ij (v_i - v_j)."""
+    pos = _d(pos)
+    box = _d(box)
+    types = _i(types)
+    table = _d(table)
+    v = _d(v)
+    out = np.zeros_like(pos)
+    eo, ei = (None, None) if excl is None else (_i(excl[0]), _i(excl[1]))
+    lib().oracle_pair_hvp(pos.shape[0], _dp(pos), _dp(box), _ip(types), n_types, _dp(table), _ip(eo),
+                          _ip(ei), _dp(v), _dp(out), int(n_threads))
+    return out
+
+
+def table_derivs_for(system, shift: bool = True):
+    """Derivative records (n_types^2, 4, 26) matching ``table_for``."""
+    return P.table_derivs(system.eps_fg, system.sig_fg, system.is_hybrid, system.radii,
+                          mixing=system.mixing, group_comp=system.group_comp, shift=shift)
 
 
 class _Topo(C.Structure):

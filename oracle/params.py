@@ -232,3 +232,104 @@ def pair_table(eps, sig, is_hybrid, radii, mixing: str = MIX_GEOMETRIC,
 def row_dict(row) -> dict:
     """Name the fields of one record (for tests and reports)."""
     return {k: float(v) for k, v in zip(ROW_FIELDS, row)}
+
+
+# ----------------------------------------------------------------- derivatives
+#
+# Parameter derivatives of Eq. 20 for the differentiable form of the method.
+# Every smoothing coefficient of Eq. 17 / Eq. 18 is a fixed linear combination
+# of (u, u', u'') at one radius, and Eq. 19 combines the coefficients
+# linearly, so the derivative of a record with respect to eps or sig is the
+# same construction applied to the derivatives of (u, u', u'') -- written out
+# below from Eq. 11 / Eq. 12 directly.
+
+PARAMS = ("eps_fg", "sig_fg", "eps_cg", "sig_cg")
+
+
+def lj_dparams(r: float, eps: float, sig: float):
+    """d/d eps and d/d sig of (u, u', u'') of Eq. 11 at r: two triples."""
+    s6 = (sig / r) ** 6
+    s12 = s6 * s6
+    d_eps = (4.0 * (s12 - s6), 4.0 * (-12.0 * s12 + 6.0 * s6) / r,
+             4.0 * (156.0 * s12 - 42.0 * s6) / (r * r))
+    # d(s^k)/d sig = k s^k / sig
+    d_sig = (4.0 * eps * (12.0 * s12 - 6.0 * s6) / sig,
+             4.0 * eps * (-144.0 * s12 + 36.0 * s6) / (r * sig),
+             4.0 * eps * (1872.0 * s12 - 252.0 * s6) / (r * r * sig))
+    return d_eps, d_sig
+
+
+def pair_row_derivs(eps_fg, sig_fg, eps_cg, sig_cg, radii, shift: bool = True) -> np.ndarray:
+    """(4, ROW_LEN): derivative of every field of ``pair_row`` with respect to
+    eps_fg, sig_fg, eps_cg, sig_cg (in that order).  The CG rows are zero
+    where eps_cg = 0 (Eq. 14 pairs carry no CG parameters)."""
+    rsm, rsp, rcm, rcp = (float(x) for x in radii)
+    d_s = rsp - rsm
+    d_c = rcp - rcm
+    out = np.zeros((4, ROW_LEN))
+    zero = np.zeros(5)
+    fg_e, fg_s = lj_dparams(rsm, eps_fg, sig_fg)
+    if eps_cg != 0.0:
+        on_e, on_s = lj_dparams(rsp, eps_cg, sig_cg)
+        off_e, off_s = lj_dparams(rcm, eps_cg, sig_cg)
+    for k in range(4):
+        g_fg_m = zero
+        g_cg_p = zero
+        g_cg_m = zero
+        if k == 0 and eps_fg != 0.0:
+            g_fg_m = switch_off(*fg_e, d_s)
+        elif k == 1 and eps_fg != 0.0:
+            g_fg_m = switch_off(*fg_s, d_s)
+        elif k == 2 and eps_cg != 0.0:
+            g_cg_p = switch_on(*on_e, d_s)
+            g_cg_m = switch_off(*off_e, d_c)
+        elif k == 3 and eps_cg != 0.0:
+            g_cg_p = switch_on(*on_s, d_s)
+            g_cg_m = switch_off(*off_s, d_c)
+        gam_cm = poly(g_cg_m, d_c) if shift else 0.0
+        gam_sp = gam_cm + poly(g_fg_m, d_s)
+        gam_sm = gam_sp - g_cg_p[0]
+        head = np.zeros(8)
+        head[k] = 1.0
+        out[k] = np.concatenate((head, g_fg_m, g_cg_p, g_cg_m, [gam_cm, gam_sp, gam_sm]))
+    return out
+
+
+def table_derivs(eps, sig, is_hybrid, radii, mixing: str = MIX_GEOMETRIC, eps_cg=None, sig_cg=None,
+                 group_comp=None, shift: bool = True) -> np.ndarray:
+    """(n_types^2, 4, ROW_LEN): ``pair_row_derivs`` of every record of
+    ``pair_table`` (same arguments), row-major (a * n_types + b)."""
+    tab = pair_table(eps, sig, is_hybrid, radii, mixing, eps_cg, sig_cg, group_comp, shift)
+    nt = len(eps)
+    out = np.zeros((nt * nt, 4, ROW_LEN))
+    for k in range(nt * nt):
+        r = tab[k]
+        out[k] = pair_row_derivs(r[0], r[1], r[2], r[3], r[4:8], shift)
+    return out
+
+
+def chain_to_types(grad_rows, eps, sig, mixing: str = MIX_GEOMETRIC):
+    """Per-record gradients (n_types^2, 4) -- d/d of (eps_fg, sig_fg, eps_cg,
+    sig_cg) of each record -- to the per-type FG parameters through the mixing
+    rule (both records (a, b) and (b, a) depend on eps_a), and the CG ones
+    taken per record (independent leaves).  Returns (d_eps[nt], d_sig[nt],
+    d_eps_cg[nt, nt], d_sig_cg[nt, nt])."""
+    eps = np.asarray(eps, dtype=np.float64)
+    sig = np.asarray(sig, dtype=np.float64)
+    nt = len(eps)
+    g = np.asarray(grad_rows, dtype=np.float64).reshape(nt, nt, 4)
+    d_eps = np.zeros(nt)
+    d_sig = np.zeros(nt)
+    for p in range(nt):
+        for q in range(nt):
+            # eps_pq = sqrt(eps_p eps_q)
+            if eps[p] > 0.0 and eps[q] > 0.0:
+                d_eps[p] += g[p, q, 0] * 0.5 * math.sqrt(eps[q] / eps[p])
+                d_eps[q] += g[p, q, 0] * 0.5 * math.sqrt(eps[p] / eps[q])
+            if mixing == MIX_LB:  # sig_pq = (sig_p + sig_q) / 2
+                d_sig[p] += 0.5 * g[p, q, 1]
+                d_sig[q] += 0.5 * g[p, q, 1]
+            else:  # sig_pq = sqrt(sig_p sig_q)
+                d_sig[p] += g[p, q, 1] * 0.5 * math.sqrt(sig[q] / sig[p])
+                d_sig[q] += g[p, q, 1] * 0.5 * math.sqrt(sig[p] / sig[q])
+    return d_eps, d_sig, g[:, :, 2].copy(), g[:, :, 3].copy()

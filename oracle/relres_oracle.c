@@ -10,6 +10,12 @@
  *     (Eq. 3), minimum image in an orthorhombic periodic box, O(N^2), one
  *     full row per atom (F_i sums over all j != i; energy and virial take half
  *     of each ordered pair).
+ *   - oracle_u_tilde_d2, oracle_pair_param_grads, oracle_pair_hvp: second
+ *     r-derivative of Eq. 20, the gradient of a function of the pair energy
+ *     and forces with respect to every record's eps/sig (through the
+ *     derivatives of Eq. 17-19), and the Hessian-vector product of the pair
+ *     energy -- the differentiable form of the method, by direct
+ *     differentiation.
  *   - oracle_bonded: harmonic bonds E = K (r - r0)^2, harmonic angles
  *     E = K (theta - theta0)^2, OPLS dihedrals
  *     E = 1/2 [K1 (1 + cos phi) + K2 (1 - cos 2phi) + K3 (1 + cos 3phi)
@@ -95,6 +101,180 @@ static int is_excluded(const int* off, const int* idx, int i, int j) {
     if (idx[k] == j) return 1;
   return 0;
 }
+
+/* ---- derivatives for the differentiable form ------------------------------ */
+
+/* Eq. 11 with its second r-derivative. */
+static void lj_u2(double r, double eps, double sig, double* d2u) {
+  if (eps == 0.0) { *d2u = 0.0; return; }
+  double s6 = pow(sig / r, 6.0);
+  double s12 = s6 * s6;
+  *d2u = 4.0 * eps * (156.0 * s12 - 42.0 * s6) / (r * r);
+}
+
+static double poly_d2(const double* g, double d) {
+  return 2.0 * g[2] + 6.0 * g[3] * d + 12.0 * g[4] * d * d;
+}
+
+/* Second r-derivative of Eq. 20, region by region. */
+static double eq20_d2(const oracle_pair* p, double r) {
+  double v;
+  if (r < p->rsm) {
+    lj_u2(r, p->eps_fg, p->sig_fg, &v);
+    return v;
+  }
+  if (r < p->rsp) {
+    double g[5];
+    for (int m = 0; m < 5; ++m) g[m] = p->g_fg_m[m] + p->g_cg_p[m];
+    return poly_d2(g, r - p->rsm);
+  }
+  if (r < p->rcm) {
+    lj_u2(r, p->eps_cg, p->sig_cg, &v);
+    return v;
+  }
+  if (r < p->rcp) return poly_d2(p->g_cg_m, r - p->rcm);
+  return 0.0;
+}
+
+void oracle_u_tilde_d2(const oracle_pair* p, const double* r, long n, double* d2u) {
+  for (long k = 0; k < n; ++k) d2u[k] = eq20_d2(p, r[k]);
+}
+
+/* d/d eps and d/d sig of u(r) and u'(r) of Eq. 11 (k = 0: eps, 1: sig). */
+static void lj_dparam(double r, double eps, double sig, int k, double* du, double* dup) {
+  double s6 = pow(sig / r, 6.0);
+  double s12 = s6 * s6;
+  if (k == 0) {
+    *du = 4.0 * (s12 - s6);
+    *dup = 4.0 * (-12.0 * s12 + 6.0 * s6) / r;
+  } else {
+    *du = 4.0 * eps * (12.0 * s12 - 6.0 * s6) / sig;
+    *dup = 4.0 * eps * (-144.0 * s12 + 36.0 * s6) / (r * sig);
+  }
+}
+
+/*
+ * Derivative of Eq. 20 (value dv[k] and r-derivative dd[k]) with respect to
+ * the four parameters of the record (k: eps_fg, sig_fg, eps_cg, sig_cg).
+ * dp[k] holds the derivative of every record field with respect to parameter
+ * k (oracle/params.py: pair_row_derivs), so polynomial regions differentiate
+ * through their coefficients and the LJ regions analytically.
+ */
+static void eq20_dparam(const oracle_pair* p, const oracle_pair* dp, double r, double* dv, double* dd) {
+  for (int k = 0; k < 4; ++k) {
+    double a = 0.0, b = 0.0, f, df;
+    if (r < p->rsm) {
+      if (k < 2 && p->eps_fg != 0.0) lj_dparam(r, p->eps_fg, p->sig_fg, k, &a, &b);
+      a -= dp[k].gam_sm;
+    } else if (r < p->rsp) {
+      double g[5];
+      for (int m = 0; m < 5; ++m) g[m] = dp[k].g_fg_m[m] + dp[k].g_cg_p[m];
+      poly_u(g, r - p->rsm, &f, &df);
+      a = f - dp[k].gam_sp;
+      b = df;
+    } else if (r < p->rcm) {
+      if (k >= 2 && p->eps_cg != 0.0) lj_dparam(r, p->eps_cg, p->sig_cg, k - 2, &a, &b);
+      a -= dp[k].gam_cm;
+    } else if (r < p->rcp) {
+      poly_u(dp[k].g_cg_m, r - p->rcm, &f, &df);
+      a = f - dp[k].gam_cm;
+      b = df;
+    }
+    dv[k] = a;
+    dd[k] = b;
+  }
+}
+
+/*
+ * Gradient of a scalar L(E, F) of the pair energy E and the pair forces F with
+ * respect to the parameters of every record, given gE = dL/dE and gF[i] =
+ * dL/dF_i (may be NULL): out[(a*nt + b)*4 + k].  Each ordered pair (i, j)
+ * counts half of its energy derivative, and g_i . dF_ij/dparam, in the record
+ * of (type i, type j).
+ */
+int oracle_pair_param_grads(int n, const double* pos, const double* box, const int* type, int nt,
+                            const oracle_pair* table, const oracle_pair* dtable, const int* excl_off,
+                            const int* excl_idx, const double* gF, double gE, double* out,
+                            int n_threads) {
+  const int nr = nt * nt * 4;
+  for (int q = 0; q < nr; ++q) out[q] = 0.0;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+#pragma omp parallel
+  {
+    double* loc = (double*)calloc((size_t)nr, sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < n; ++j) {
+        if (j == i || is_excluded(excl_off, excl_idx, i, j)) continue;
+        double d[3];
+        for (int a = 0; a < 3; ++a) d[a] = min_image(pos[3 * i + a] - pos[3 * j + a], box[a]);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const int row = type[i] * nt + type[j];
+        const oracle_pair* p = &table[row];
+        if (r >= p->rcp) continue;
+        double dv[4], dd[4];
+        eq20_dparam(p, &dtable[4 * row], r, dv, dd);
+        double gr = 0.0; /* g_i . (r_i - r_j)/r */
+        if (gF)
+          for (int a = 0; a < 3; ++a) gr += gF[3 * i + a] * d[a] / r;
+        for (int k = 0; k < 4; ++k) {
+          /* F_ij = -u'(r) (r_i - r_j)/r */
+          loc[4 * row + k] += 0.5 * gE * dv[k] - dd[k] * gr;
+        }
+      }
+    }
+#pragma omp critical
+    for (int q = 0; q < nr; ++q) out[q] += loc[q];
+    free(loc);
+  }
+  return 0;
+}
+
+/*
+ * Hessian-vector product of the pair energy: out_i = sum_j h_ij (v_i - v_j),
+ * h_ij = u''(r) rhat rhat^T + (u'(r)/r) (I - rhat rhat^T), rhat = (r_i - r_j)/r.
+ * (The pair forces change by -H v along v.)
+ */
+int oracle_pair_hvp(int n, const double* pos, const double* box, const int* type, int nt,
+                    const oracle_pair* table, const int* excl_off, const int* excl_idx, const double* v,
+                    double* out, int n_threads) {
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int i = 0; i < n; ++i) {
+    double o[3] = {0, 0, 0};
+    for (int j = 0; j < n; ++j) {
+      if (j == i || is_excluded(excl_off, excl_idx, i, j)) continue;
+      double d[3];
+      for (int a = 0; a < 3; ++a) d[a] = min_image(pos[3 * i + a] - pos[3 * j + a], box[a]);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      const oracle_pair* p = &table[type[i] * nt + type[j]];
+      if (r >= p->rcp) continue;
+      double u, du;
+      eq20(p, r, &u, &du);
+      const double d2u = eq20_d2(p, r);
+      double w[3], rw = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        w[a] = v[3 * i + a] - v[3 * j + a];
+        rw += d[a] / r * w[a];
+      }
+      for (int a = 0; a < 3; ++a) {
+        const double ra = d[a] / r;
+        o[a] += d2u * rw * ra + du / r * (w[a] - rw * ra);
+      }
+    }
+    for (int a = 0; a < 3; ++a) out[3 * i + a] = o[a];
+  }
+  return 0;
+}
+
 
 /*
  * Pair forces, energy and virial of Eq. 20 over all non-excluded pairs.
