@@ -270,6 +270,50 @@ relres_status relres_set_step_counter(relres_ctx* ctx, long long step);
 relres_status relres_get_stats(relres_ctx* ctx, relres_stats* out);
 
 /*
+ * Replace the LJ parameters of a context (eps_fg, sig_fg and the CG pair
+ * parameters, explicit or by Eq. 13) without rebuilding its lists: the
+ * differentiable form treats them as variables.  n_types, is_hybrid, mixing,
+ * precision, shift, skin, every radius and the set of type pairs with
+ * eps^CG > 0 must stay as at relres_create (RELRES_ERR_ARG otherwise, the
+ * context unchanged).  Waits for the context stream.  Cached forces are
+ * dropped (the next relres_step recomputes them).
+ */
+relres_status relres_set_params(relres_ctx* ctx, const relres_params* p);
+
+/*
+ * Backward pass of the RelRes pair interaction, Eq. 20 summed over pairs
+ * (Eq. 3): the differentiable form of Section 2.5's potential.  For a scalar
+ * L(E, F) of the pair energy E and the pair forces F (bonded terms are not
+ * part of it), given
+ *   grad_energy      dL/dE,
+ *   d_grad_forces    [n_atoms*3] device, dL/dF_i (caller order), or NULL for 0,
+ * at the positions d_pos ([n_atoms*3] device, as for relres_compute; the
+ * lists are reused, or rebuilt if an atom moved more than half the skin), it
+ * writes
+ *   d_grad_pos       [n_atoms*3] device, dL/dx_i = grad_energy dE/dx_i -
+ *                    sum_j h_ij (g_i - g_j) with the pair Hessian blocks
+ *                    h_ij = u~'' rhat rhat^T + (u~'/r)(I - rhat rhat^T)
+ *                    (a Hessian-vector product; u~'' exists in every region
+ *                    thanks to the C2 smoothing of Eq. 7-8); may be NULL,
+ *   grad_c           [n_types^2 * 4] host: per type pair (a*n_types + b)
+ *                    dL/dC12 and dL/dC6 of the FG part, then of the CG part,
+ *                    with C12 = 4 eps sig^12, C6 = 4 eps sig^6 (each part is
+ *                    linear in them: Eq. 17-19 are linear in the potential);
+ *                    record (a, b) collects half of every (a, b) pair and the
+ *                    force terms of the type-a atoms; may be NULL,
+ *   d_eps_fg, d_sig_fg  [n_types] host: dL/d eps_fg, dL/d sig_fg per type
+ *                    through the mixing rule; may be NULL,
+ *   d_eps_cg, d_sig_cg  [n_types^2] host: dL/d eps^CG, dL/d sig^CG per
+ *                    record, the CG parameters taken as independent
+ *                    variables (no chain through Eq. 13); may be NULL.
+ * FP32 contexts evaluate in FP32 with FP64 totals, FP64 contexts in FP64.
+ * Synchronises the context stream (the host outputs are read back).
+ */
+relres_status relres_backward(relres_ctx* ctx, const double* d_pos, const double* d_grad_forces,
+                              double grad_energy, double* d_grad_pos, double* grad_c, double* d_eps_fg,
+                              double* d_sig_fg, double* d_eps_cg, double* d_sig_cg);
+
+/*
  * Step execution mode (an implementation choice; the paper has no
  * counterpart).  enable != 0 (the default) runs relres_step as one CUDA graph
  * per block of up to 100 steps: the list rebuild of every step is a

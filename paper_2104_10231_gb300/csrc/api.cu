@@ -268,6 +268,15 @@ relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda
   if (ce == cudaSuccess)
     ce = cudaMemcpy(c->d_tabd, c->tab_d.data(), sizeof(PairTab<double>) * c->tab_d.size(),
                     cudaMemcpyHostToDevice);
+  build_basis_tables(c->recs, p->shift, &c->basis_f, &c->basis_d);
+  const size_t bb = c->fp64 ? sizeof(BasisTab<double>) * c->basis_d.size()
+                            : sizeof(BasisTab<float>) * c->basis_f.size();
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_basis, bb);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpy(c->d_basis, c->fp64 ? static_cast<const void*>(c->basis_d.data())
+                                        : static_cast<const void*>(c->basis_f.data()),
+                    bb, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_gc, sizeof(double) * 4 * c->recs.size());
   if (ce == cudaSuccess) ce = cudaMalloc(&c->d_state, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMemset(c->d_state, 0, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMalloc(&c->d_snap_state, sizeof(DevState));
@@ -295,6 +304,7 @@ relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda
 relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   if (!c) return RELRES_ERR_ARG;
   ++c->buf_gen;
+  c->grad_n = 0;  // gradient buffers follow the atom counts
   if (!t || t->n_atoms < 1 || !t->type || !t->mass_by_type)
     return fail(c, RELRES_ERR_ARG, "topology needs n_atoms >= 1, type and mass_by_type");
   const int n = t->n_atoms;
@@ -684,6 +694,119 @@ relres_status relres_set_graphs(relres_ctx* c, int enable) {
   return RELRES_OK;
 }
 
+relres_status relres_set_params(relres_ctx* c, const relres_params* p) {
+  if (!c || !p) return RELRES_ERR_ARG;
+  std::vector<PairRecord> recs;
+  const std::string e = build_pair_records(p, &recs);
+  if (!e.empty()) return fail(c, RELRES_ERR_ARG, e.c_str());
+  if (p->n_types != c->n_types || p->mixing != c->prm.mixing || p->precision != c->prm.precision ||
+      p->shift != c->prm.shift || p->skin != c->prm.skin)
+    return fail(c, RELRES_ERR_ARG, "relres_set_params: n_types, mixing, precision, shift and skin must not change");
+  for (int t = 0; t < c->n_types; ++t)
+    if (p->is_hybrid[t] != c->is_hybrid[t]) return fail(c, RELRES_ERR_ARG, "relres_set_params: is_hybrid changed");
+  for (size_t k = 0; k < recs.size(); ++k) {
+    const PairRecord &a = recs[k], &b = c->recs[k];
+    if (a.rsm != b.rsm || a.rsp != b.rsp || a.rcm != b.rcm || a.rcp != b.rcp ||
+        (a.eps_cg > 0.0) != (b.eps_cg > 0.0))
+      return fail(c, RELRES_ERR_ARG, "relres_set_params: radii and the set of CG pairs must not change");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  c->recs = recs;
+  c->eps_fg.assign(p->eps_fg, p->eps_fg + p->n_types);
+  c->sig_fg.assign(p->sig_fg, p->sig_fg + p->n_types);
+  build_kernel_tables(c->recs, &c->tab_f, &c->tab_d);
+  build_basis_tables(c->recs, p->shift, &c->basis_f, &c->basis_d);
+  if (c->fp64) {
+    CK(cudaMemcpy(c->d_tab, c->tab_d.data(), sizeof(PairTab<double>) * c->tab_d.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_basis, c->basis_d.data(), sizeof(BasisTab<double>) * c->basis_d.size(),
+                  cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(c->d_tab, c->tab_f.data(), sizeof(PairTab<float>) * c->tab_f.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_basis, c->basis_f.data(), sizeof(BasisTab<float>) * c->basis_f.size(),
+                  cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(c->d_tabd, c->tab_d.data(), sizeof(PairTab<double>) * c->tab_d.size(), cudaMemcpyHostToDevice));
+  c->forces_valid = false;
+  return RELRES_OK;
+}
+
+// dL/d(C12, C6) per record -> dL/d(eps, sig) per record (C12 = 4 eps sig^12,
+// C6 = 4 eps sig^6), then the FG ones to the per-type parameters through the
+// mixing rule (records (a, b) and (b, a) both depend on type a).
+static void chain_params(const relres_ctx* c, const double* gc, double* d_eps_fg, double* d_sig_fg,
+                         double* d_eps_cg, double* d_sig_cg) {
+  const int nt = c->n_types;
+  std::vector<double> de(nt, 0.0), ds(nt, 0.0);
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const int row = a * nt + b;
+      const PairRecord& r = c->recs[row];
+      const double* g = gc + 4 * row;
+      const double sf = r.sig_fg, sc = r.sig_cg;
+      const double sf6 = std::pow(sf, 6.0), sc6 = std::pow(sc, 6.0);
+      const double e_f = 4.0 * sf6 * sf6 * g[0] + 4.0 * sf6 * g[1];
+      const double s_f = 48.0 * r.eps_fg * sf6 * sf6 / sf * g[0] + 24.0 * r.eps_fg * sf6 / sf * g[1];
+      if (d_eps_cg) d_eps_cg[row] = r.eps_cg > 0.0 ? 4.0 * sc6 * sc6 * g[2] + 4.0 * sc6 * g[3] : 0.0;
+      if (d_sig_cg)
+        d_sig_cg[row] =
+            r.eps_cg > 0.0 ? 48.0 * r.eps_cg * sc6 * sc6 / sc * g[2] + 24.0 * r.eps_cg * sc6 / sc * g[3] : 0.0;
+      const double ea = c->eps_fg[a], eb = c->eps_fg[b], sa = c->sig_fg[a], sb = c->sig_fg[b];
+      if (ea > 0.0 && eb > 0.0) {  // eps_ab = sqrt(eps_a eps_b)
+        de[a] += e_f * 0.5 * std::sqrt(eb / ea);
+        de[b] += e_f * 0.5 * std::sqrt(ea / eb);
+      }
+      if (c->prm.mixing == RELRES_MIX_LB) {  // sig_ab = (sig_a + sig_b) / 2
+        ds[a] += 0.5 * s_f;
+        ds[b] += 0.5 * s_f;
+      } else {  // sig_ab = sqrt(sig_a sig_b)
+        ds[a] += s_f * 0.5 * std::sqrt(sb / sa);
+        ds[b] += s_f * 0.5 * std::sqrt(sa / sb);
+      }
+    }
+  if (d_eps_fg) std::copy(de.begin(), de.end(), d_eps_fg);
+  if (d_sig_fg) std::copy(ds.begin(), ds.end(), d_sig_fg);
+}
+
+relres_status relres_backward(relres_ctx* c, const double* d_pos, const double* d_grad_forces, double grad_energy,
+                              double* d_grad_pos, double* grad_c, double* d_eps_fg, double* d_sig_fg,
+                              double* d_eps_cg, double* d_sig_cg) {
+  if (!c) return RELRES_ERR_ARG;
+  if (!c->have_lists) return fail(c, RELRES_ERR_STATE, "relres_build_neighbors first");
+  if (!d_pos || !std::isfinite(grad_energy)) return fail(c, RELRES_ERR_ARG, "invalid backward arguments");
+  // positions into the device state (lists rebuilt if an atom moved too far)
+  CK(launch_convert(c, d_pos));
+  relres_status s = read_state(c);
+  if (s != RELRES_OK) return s;
+  if (c->h_state->flags & F_NONFINITE) {
+    CK(launch_flags_and(c, ~(unsigned)F_NONFINITE));
+    return fail(c, RELRES_ERR_NONFINITE, "non-finite position");
+  }
+  if (c->h_state->flags & F_REBUILD) {
+    s = host_rebuild(c);
+    if (s != RELRES_OK) return s;
+  }
+  c->forces_valid = false;
+  // gradient buffers (allocated on first use)
+  if (c->grad_n != c->n) {
+    const size_t vb = c->fp64 ? 24 : 16;
+    CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_g_fg), vb * c->n));
+    CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_g_cg), vb * std::max(1, c->n_h)));
+    CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_gx_fg), vb * c->n));
+    CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_gx_cg), vb * c->n));
+    CK(dalloc(&c->d_zero_n3, 3 * size_t(c->n)));
+    CK(cudaMemsetAsync(c->d_gx_cg, 0, vb * c->n, c->stream));  // ordinary atoms keep zero
+    CK(cudaMemsetAsync(c->d_zero_n3, 0, sizeof(double) * 3 * c->n, c->stream));
+    c->grad_n = c->n;
+  }
+  CK(launch_pair_grad(c, d_grad_forces, grad_energy, d_grad_pos));
+  std::vector<double> gc(4 * c->recs.size());
+  CK(cudaMemcpyAsync(gc.data(), c->d_gc, sizeof(double) * gc.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (grad_c) std::copy(gc.begin(), gc.end(), grad_c);
+  chain_params(c, gc.data(), d_eps_fg, d_sig_fg, d_eps_cg, d_sig_cg);
+  return RELRES_OK;
+}
+
 relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_pos, double* d_vel,
                           double t_target, double tau_fs, uint64_t seed, int thermo_every,
                           double* d_thermo) {
@@ -899,6 +1022,13 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_f_cg);
   dfree(c->d_f_tot);
   dfree(c->d_tf);
+  dfree(c->d_basis);
+  dfree(c->d_gc);
+  dfree(c->d_g_fg);
+  dfree(c->d_g_cg);
+  dfree(c->d_gx_fg);
+  dfree(c->d_gx_cg);
+  dfree(c->d_zero_n3);
   dfree(c->d_acc);
   dfree(c->d_draws);
   dfree(c->d_state);

@@ -218,6 +218,56 @@ void build_kernel_tables(const std::vector<PairRecord>& recs, std::vector<PairTa
   }
 }
 
+namespace {
+// r^-k and its first two derivatives
+void powk3(double r, int k, double* u, double* du, double* d2u) {
+  const double v = std::pow(r, -double(k));
+  *u = v;
+  *du = -k * v / r;
+  *d2u = k * (k + 1.0) * v / (r * r);
+}
+}  // namespace
+
+template <typename R>
+static void fill_basis_row(const PairRecord& r, int shift, BasisTab<R>* t) {
+  std::memset(t, 0, sizeof(*t));
+  t->rsm = R(r.rsm);
+  t->rsp = R(r.rsp);
+  t->rcm = R(r.rcm);
+  t->rcp = R(r.rcp);
+  const double ws = r.rsp - r.rsm, wc = r.rcp - r.rcm;
+  const int kk[2] = {12, 6};
+  for (int b = 0; b < 2; ++b) {
+    double u, du, d2u, g[5];
+    powk3(r.rsm, kk[b], &u, &du, &d2u);
+    coeffs_off(u, du, d2u, ws, g);
+    for (int m = 0; m < 5; ++m) t->fg[b][m] = R(g[m]);
+    t->fg_sh[b] = R(horner5(g, ws));
+    powk3(r.rsp, kk[b], &u, &du, &d2u);
+    coeffs_on(u, du, d2u, ws, g);
+    for (int m = 0; m < 5; ++m) t->on[b][m] = R(g[m]);
+    powk3(r.rcm, kk[b], &u, &du, &d2u);
+    coeffs_off(u, du, d2u, wc, g);
+    for (int m = 0; m < 5; ++m) t->off[b][m] = R(g[m]);
+    t->gam[b] = R(shift ? horner5(g, wc) : 0.0);
+  }
+  const double s6f = std::pow(r.sig_fg, 6.0), s6c = std::pow(r.sig_cg, 6.0);
+  t->c12f = R(4.0 * r.eps_fg * s6f * s6f);
+  t->c6f = R(4.0 * r.eps_fg * s6f);
+  t->c12c = R(4.0 * r.eps_cg * s6c * s6c);
+  t->c6c = R(4.0 * r.eps_cg * s6c);
+}
+
+void build_basis_tables(const std::vector<PairRecord>& recs, int shift, std::vector<BasisTab<float>>* tf,
+                        std::vector<BasisTab<double>>* td) {
+  tf->resize(recs.size());
+  td->resize(recs.size());
+  for (size_t k = 0; k < recs.size(); ++k) {
+    fill_basis_row(recs[k], shift, &(*tf)[k]);
+    fill_basis_row(recs[k], shift, &(*td)[k]);
+  }
+}
+
 }  // namespace relres
 
 using namespace relres;

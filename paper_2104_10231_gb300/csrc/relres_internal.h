@@ -50,7 +50,23 @@ struct PairTab {
 };
 static_assert(sizeof(PairTab<float>) % 8 == 4, "odd row length in words");
 
+// Basis form of one type pair for the differentiable path.  Every smoothing
+// coefficient (Eq. 17, Eq. 18) and shift (Eq. 19) is linear in the potential,
+// so each part of Eq. 20 is C12 phi12(r) - C6 phi6(r), with phik the same
+// construction applied to r^-k.  The rows hold, for k = 12 and 6: the FG
+// switch-off polynomial and its shift f(dr_s), the CG switch-on and
+// switch-off polynomials and Gamma_{c-}; and the current coefficients.
+template <typename R>
+struct BasisTab {
+  R rsm, rsp, rcm, rcp;
+  R fg[2][5], fg_sh[2];             // FG part: f_{s-}[r^-k], f_{s-}[r^-k](dr_s)  (k = 12, 6)
+  R on[2][5], off[2][5], gam[2];    // CG part: f_{s+}[r^-k], f_{c-}[r^-k], Gamma_{c-}[r^-k]
+  R c12f, c6f, c12c, c6c;           // 4 eps sig^12, 4 eps sig^6 (FG, CG)
+};
+
 std::string build_pair_records(const relres_params* p, std::vector<PairRecord>* out);
+void build_basis_tables(const std::vector<PairRecord>& recs, int shift, std::vector<BasisTab<float>>* tf,
+                        std::vector<BasisTab<double>>* td);
 void build_kernel_tables(const std::vector<PairRecord>& recs, std::vector<PairTab<float>>* tf,
                          std::vector<PairTab<double>>* td);
 void mix_pair(int mixing, double ea, double sa, double eb, double sb, double* e, double* s);
@@ -129,6 +145,19 @@ struct relres_ctx {
   double rlist_fg_cut = 0, rlist_cg_cut = 0;  // max r_s+, max r_c+ over pairs
   cudaStream_t stream = nullptr;
   std::string err;
+
+  // differentiable path: basis tables (BasisTab<float or double>[n_types^2]),
+  // per-type-pair gradient totals, and lazily allocated gradient buffers
+  std::vector<relres::BasisTab<float>> basis_f;
+  std::vector<relres::BasisTab<double>> basis_d;
+  void* d_basis = nullptr;
+  double* d_gc = nullptr;     // [n_types^2][4]
+  void* d_g_fg = nullptr;     // dL/dF in FG slot order
+  void* d_g_cg = nullptr;     // dL/dF in CG slot order
+  void* d_gx_fg = nullptr;    // dL/dx, FG part, caller order
+  void* d_gx_cg = nullptr;    // dL/dx, CG part (hybrids), caller order
+  double* d_zero_n3 = nullptr;
+  int grad_n = 0;             // atoms the gradient buffers were allocated for
 
   // device tables
   void* d_tab = nullptr;  // PairTab<float or double>[n_types^2]
@@ -283,6 +312,9 @@ cudaError_t launch_lists(relres_ctx* c, const unsigned* gate);
 cudaError_t launch_pairs(relres_ctx* c, bool ev, int which = 3);
 cudaError_t launch_finish(relres_ctx* c, bool ev, double* d_forces_out, const double* d_vel);
 cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial);
+// backward pass of the pair interaction (grad.cu): per-type-pair totals into
+// d_gc, dL/dx (FP64, caller order) into d_grad_pos if non-null
+cudaError_t launch_pair_grad(relres_ctx* c, const double* d_grad_forces, double g_energy, double* d_grad_pos);
 
 // MD
 cudaError_t upload_type_consts(relres_ctx* c, double dt);

@@ -33,7 +33,8 @@ RELRES_PAIR_FIELDS = 26
 EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres_set_topology",
             "relres_build_neighbors", "relres_compute", "relres_step", "relres_set_step_counter",
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
-            "relres_destroy", "relres_pair_forces_static", "relres_set_graphs"]
+            "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
+            "relres_backward"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev"]
 
@@ -108,6 +109,8 @@ def load():
     L.relres_get_stats.argtypes = [vp, C.POINTER(relres_stats)]
     L.relres_set_timing.argtypes = [vp, C.c_int]
     L.relres_set_graphs.argtypes = [vp, C.c_int]
+    L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
+    L.relres_backward.argtypes = [vp, vp, vp, C.c_double, vp, _dp, _dp, _dp, _dp, _dp]
     L.relres_get_timings.argtypes = [vp, _dp, C.POINTER(C.c_longlong), C.c_int]
     L.relres_pair_forces_static.argtypes = [C.POINTER(relres_params), C.c_int, vp, vp, _dp, vp, vp, vp,
                                             vp, vp, vp]
@@ -290,6 +293,27 @@ def relres_set_timing(ctx, enable):
     _check(load().relres_set_timing(ctx, 1 if enable else 0), ctx)
 
 
+def relres_set_params(ctx, params):
+    _check(load().relres_set_params(ctx, C.byref(params)), ctx)
+
+
+def relres_backward(ctx, n_types, d_pos, d_grad_forces, grad_energy, d_grad_pos=None):
+    """Backward pass of the pair interaction; returns the host gradients
+    {"grad_c": (n_types^2, 4), "eps_fg", "sig_fg": (n_types,), "eps_cg",
+    "sig_cg": (n_types, n_types)} and writes dL/dx into d_grad_pos."""
+    nt = int(n_types)
+    gc = np.zeros(nt * nt * 4)
+    de = np.zeros(nt)
+    ds = np.zeros(nt)
+    dec = np.zeros(nt * nt)
+    dsc = np.zeros(nt * nt)
+    _check(load().relres_backward(ctx, _ptr(d_pos), _ptr(d_grad_forces), float(grad_energy), _ptr(d_grad_pos),
+                                  gc.ctypes.data_as(_dp), de.ctypes.data_as(_dp), ds.ctypes.data_as(_dp),
+                                  dec.ctypes.data_as(_dp), dsc.ctypes.data_as(_dp)), ctx)
+    return {"grad_c": gc.reshape(nt * nt, 4), "eps_fg": de, "sig_fg": ds, "eps_cg": dec.reshape(nt, nt),
+            "sig_cg": dsc.reshape(nt, nt)}
+
+
 def relres_set_graphs(ctx, enable):
     _check(load().relres_set_graphs(ctx, 1 if enable else 0), ctx)
 
@@ -360,6 +384,13 @@ class Context:
 
     def set_graphs(self, enable):
         relres_set_graphs(self.ctx, enable)
+
+    def set_params(self, params):
+        self.params = params
+        relres_set_params(self.ctx, params)
+
+    def backward(self, d_pos, d_grad_forces, grad_energy, d_grad_pos=None):
+        return relres_backward(self.ctx, self.params.n_types, d_pos, d_grad_forces, grad_energy, d_grad_pos)
 
     def timings(self):
         return relres_get_timings(self.ctx)
