@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fg-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiable (backward) leg")
     return ap.parse_args()
 
 
@@ -320,12 +321,16 @@ def ours(args):
         "lists": {"mean_fg": ctx_stats["mean_fg"], "mean_cg": ctx_stats["mean_cg"],
                   "cap_fg": ctx_stats["cap_fg"], "cap_cg": ctx_stats["cap_cg"],
                   "rebuilds_in_timed_region": ctx_stats["n_builds"] - st0["n_builds"]},
+        "pair_launch": {"threads_per_atom": ctx_stats["pair_tpa"], "block": ctx_stats["pair_block"],
+                        "chosen_by": "autotuner (first relres_step)"},
         "gpu_launches": ctx_stats["n_launches"] - st0["n_launches"],
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": "atom-steps/s", "h2d_bytes_per_step": 2 * 24 * n,
                 "d2h_bytes_per_step": 2 * 24 * n + 8 * R.RELRES_THERMO_COLS,
                 "steps": ke, "how": "relres_step(1) per step with H2D/D2H of positions+velocities"},
     }
+    if not args.no_diff:
+        out["differentiable"] = differentiable_leg(torch, R, S, stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
     if dist:
@@ -333,6 +338,49 @@ def ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def differentiable_leg(torch, R, S, stream, n_snap=64, n_mol=4000):
+    """Forward (forces + energy) and backward (force-matching loss: dL/dF =
+    2 (F - F_ref), dL/dE = 1) of the RelRes pair interaction through the C ABI
+    on seeded snapshots of the 20 000-atom neopentane-like liquid (FP32 with
+    FP64 totals): one context, lists rebuilt per snapshot as needed."""
+    import numpy as np
+
+    base = S.neopentane(n_mol=n_mol, seed=2104)
+    rng = np.random.default_rng(11)
+    n = base.n_atoms
+    with torch.cuda.stream(stream):
+        ctx = R.Context(R.params_for(base, R.RELRES_PREC_FP32),
+                        R.make_topology(base.types, base.mass_by_type, base.excl, None), stream=stream)
+        snaps = [torch.tensor(base.pos + rng.normal(scale=0.15, size=base.pos.shape), dtype=torch.float64,
+                              device="cuda") for _ in range(n_snap)]
+        f = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        f_ref = torch.zeros_like(f)
+        e = torch.zeros(4, dtype=torch.float64, device="cuda")
+        gx = torch.empty_like(f)
+        ctx.build_neighbors(snaps[0], base.box)
+        for p in snaps[:3]:  # warm-up
+            ctx.compute(p, f, e)
+            ctx.backward(p, 2.0 * (f - f_ref), 1.0, gx)
+        torch.cuda.synchronize()
+        t_fwd = t_bwd = 0.0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for p in snaps:
+            ev[0].record(stream)
+            ctx.compute(p, f, e)
+            ev[1].record(stream)
+            g = 2.0 * (f - f_ref)
+            ctx.backward(p, g, 1.0, gx)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            t_fwd += ev[0].elapsed_time(ev[1])
+            t_bwd += ev[1].elapsed_time(ev[2])
+        ctx.close()
+    return {"workload": f"{n_snap} seeded snapshots of the {n}-atom neopentane-like liquid (0.15 A noise), "
+                        "FP32 forward with energies, force-matching backward",
+            "ms_per_snapshot_forward": t_fwd / n_snap, "ms_per_snapshot_backward": t_bwd / n_snap,
+            "snapshots_per_s": n_snap / ((t_fwd + t_bwd) * 1e-3)}
 
 
 def _oracle_rows_rate(s, seconds, rng_seed=0):

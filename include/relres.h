@@ -163,6 +163,7 @@ typedef struct relres_stats {
   long long n_steps;             /* MD steps since create (also the thermostat counter) */
   int has_cg;                    /* 1 if any hybrid pair has eps^CG > 0 */
   long long n_launches;          /* CUDA kernels this context has launched */
+  int pair_tpa, pair_block;      /* forces-only pair kernel: threads per atom, block size */
 } relres_stats;
 
 /* Kernel classes of relres_get_timings. */
@@ -327,6 +328,18 @@ relres_status relres_backward(relres_ctx* ctx, const double* d_pos, const double
  * graph.
  */
 relres_status relres_set_graphs(relres_ctx* ctx, int enable);
+
+/*
+ * Launch configuration of the forces-only FP32 pair kernel (an implementation
+ * choice; the paper has no counterpart): config -1 (the default) lets the
+ * first relres_step time every configuration -- threads sharing one atom's
+ * list (1, 2, 4, 8) x block size -- on the context's own lists and keep the
+ * fastest (systems under 20 000 atoms keep configuration 0); config 0..6
+ * fixes one (0: one thread per atom, 256 per block).  The choice is reported
+ * in relres_stats.  Results agree within rounding (the summation order of an
+ * atom's partners changes with the number of threads).
+ */
+relres_status relres_set_pair_config(relres_ctx* ctx, int config);
 
 /*
  * Kernel timing.  enable != 0 makes relres_compute and relres_step record a

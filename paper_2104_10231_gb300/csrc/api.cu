@@ -545,6 +545,52 @@ relres_status relres_compute(relres_ctx* c, const double* d_pos, double* d_force
   return forces_now(c, (d_energy || d_virial) ? 1 : 0, d_forces, d_energy, d_virial);
 }
 
+// ---- autotuner of the forces-only pair kernel: every launch configuration
+// (threads per slot x block size) is timed on the context's own lists and the
+// fastest is kept.  Runs once per context, at the first relres_step (the step
+// graph bakes the choice in); forces-only launches write only the per-list
+// force scratch, which the next evaluation overwrites.
+static relres_status autotune_pairs(relres_ctx* c) {
+  c->tuned = true;
+  if (c->tune_mode >= 0 || c->fp64 || c->n < 20000) {
+    c->pair_cfg = c->tune_mode >= 0 ? c->tune_mode : 0;
+    return RELRES_OK;
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_cfg = 0;
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < kNPairConfigs && err == cudaSuccess; ++k) {
+    c->pair_cfg = k;
+    err = launch_pairs(c, false);  // warm-up
+    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) err = launch_pairs(c, false);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && ms < best) {
+      best = ms;
+      best_cfg = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->pair_cfg = best_cfg;
+  CK(err);
+  return RELRES_OK;
+}
+
+relres_status relres_set_pair_config(relres_ctx* c, int config) {
+  if (!c || config < -1 || config >= kNPairConfigs) return RELRES_ERR_ARG;
+  c->tune_mode = config;
+  c->tuned = false;
+  c->pair_cfg = config >= 0 ? config : 0;
+  return RELRES_OK;
+}
+
 // ---- relres_step: one block of steps, recorded either on the stream (the
 // rebuild kernels gated on the device flag) or into a CUDA graph (the
 // rebuild of each step behind a conditional node).
@@ -627,7 +673,7 @@ static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_v
   relres_ctx::StepGraph& g = c->sg;
   const int phase = sp.thermo_every > 0 ? done % sp.thermo_every : 0;
   if (g.valid && g.blk == blk && g.ev_phase == phase && g.thermo_every == sp.thermo_every &&
-      g.timing == int(c->timing) && g.dt == sp.dt && g.t_target == sp.t_target && g.tau == sp.tau &&
+      g.timing == int(c->timing) && g.pair_cfg == c->pair_cfg && g.dt == sp.dt && g.t_target == sp.t_target && g.tau == sp.tau &&
       g.n_f == sp.n_f && g.kt == sp.kt && g.seed == sp.seed && g.vel == d_vel && g.thermo == sp.thermo &&
       g.gen == c->buf_gen)
     return RELRES_OK;
@@ -674,6 +720,7 @@ static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_v
   g.ev_phase = phase;
   g.thermo_every = sp.thermo_every;
   g.timing = int(c->timing);
+  g.pair_cfg = c->pair_cfg;
   g.dt = sp.dt;
   g.t_target = sp.t_target;
   g.tau = sp.tau;
@@ -837,6 +884,10 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
     s = forces_now(c, 0, nullptr, nullptr, nullptr);
     if (s != RELRES_OK) return s;
   }
+  if (!c->tuned) {
+    s = autotune_pairs(c);
+    if (s != RELRES_OK) return s;
+  }
   CK(upload_type_consts(c, dt_fs));
   CK(launch_set_ab(c, 1.0, 1.0, 0));
   CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
@@ -922,6 +973,8 @@ relres_status relres_get_stats(relres_ctx* c, relres_stats* o) {
   std::memset(o, 0, sizeof(*o));
   o->n_atoms = c->n;
   o->n_hybrid = c->n_h;
+  o->pair_tpa = kPairConfigs[c->pair_cfg].tpa;
+  o->pair_block = kPairConfigs[c->pair_cfg].bs;
   o->cap_fg = c->cap_fg;
   o->cap_cg = c->cap_cg;
   o->max_fg = c->h_state->max_fg;

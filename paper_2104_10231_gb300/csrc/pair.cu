@@ -356,11 +356,16 @@ __device__ __forceinline__ void entry(const typename PosOf<R>::T& pi, const type
   }
 }
 
-// One slot's walk over its list, four entries per iteration.
-template <typename R, bool CG, bool EV>
+// One slot's walk over its list, four entries per iteration.  TPA lanes share
+// one slot (threads per atom, chosen by the autotuner): lane q of the slot
+// takes chunks q, q + TPA, ... and the partial forces are summed with warp
+// shuffles.  Energy steps use TPA = 1.
+template <typename R, bool CG, bool EV, int TPA>
 __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTabs& S,
                                      const PairLaunch<R>& a) {
-  const int s = blk * blockDim.x + threadIdx.x;
+  const int t = blk * blockDim.x + threadIdx.x;
+  const int s = t / TPA;
+  const int q = t % TPA;
   Acc<R> A;
   if (s < L.nslots) {
     const auto pi = L.pos[s];
@@ -369,10 +374,10 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
     const int nch = (m + 3) >> 2;
     const int4* nb4 = reinterpret_cast<const int4*>(L.nbr) + s;
     int4 jj = make_int4(s, s, s, s);
-    if (nch > 0) jj = __ldcs(nb4);
-    for (int ch = 0; ch < nch; ++ch) {
+    if (q < nch) jj = __ldcs(nb4 + size_t(q) * L.nslots);
+    for (int ch = q; ch < nch; ch += TPA) {
       int4 jn = jj;
-      if (ch + 1 < nch) jn = __ldcs(nb4 + size_t(ch + 1) * L.nslots);
+      if (ch + TPA < nch) jn = __ldcs(nb4 + size_t(ch + TPA) * L.nslots);
       const int rem = m - 4 * ch;  // >= 1
       const int j1 = rem > 1 ? jj.y : s, j2 = rem > 2 ? jj.z : s, j3 = rem > 3 ? jj.w : s;
       const auto p0 = load_pos(L.pos, jj.x);
@@ -385,26 +390,34 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
       entry<R, CG, EV>(pi, p3, rem > 3, row0, S, a, A);
       jj = jn;
     }
-    store_force(L.f_out, L.perm[s], A.fx, A.fy, A.fz);
   }
+  if (TPA > 1) {  // every lane of the warp takes part (TPA divides 32)
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1) {
+      A.fx += __shfl_xor_sync(0xffffffffu, A.fx, o);
+      A.fy += __shfl_xor_sync(0xffffffffu, A.fy, o);
+      A.fz += __shfl_xor_sync(0xffffffffu, A.fz, o);
+    }
+  }
+  if (s < L.nslots && q == 0) store_force(L.f_out, L.perm[s], A.fx, A.fy, A.fz);
   if (EV) {
     // per-thread sums are R (FP64 for the energy); the block sum is taken in FP64
     double accd[kNQ];
     accd[0] = std::is_same<R, float>::value ? double(A.eff.hi) + double(A.eff.lo) : double(A.e);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) accd[q + 1] = double(A.w[q]);
-    __shared__ double sh[(kThreads / 32) * kNQ];
+    for (int k = 0; k < 6; ++k) accd[k + 1] = double(A.w[k]);
+    __shared__ double sh[(1024 / 32) * kNQ];
     block_sum<double, kNQ>(accd, sh);
     if (threadIdx.x == 0) {
       // full lists: every pair was visited from both ends
 #pragma unroll
-      for (int q = 0; q < kNQ; ++q) acc_add(L.acc + q, 0.5 * accd[q]);
+      for (int k = 0; k < kNQ; ++k) acc_add(L.acc + k, 0.5 * accd[k]);
     }
   }
 }
 
-template <typename R, bool EV>
-__global__ void __launch_bounds__(kThreads) k_pair(PairLaunch<R> a) {
+template <typename R, bool EV, int TPA, int BS>
+__global__ void __launch_bounds__(BS) k_pair(PairLaunch<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrow = a.nt * a.nt;
   size_t off = 0;
@@ -437,9 +450,9 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairLaunch<R> a) {
   }
   __syncthreads();
   if (int(blockIdx.x) < a.nblk_cg)
-    walk<R, true, EV>(a.cg, blockIdx.x, S, a);
+    walk<R, true, EV, TPA>(a.cg, blockIdx.x, S, a);
   else
-    walk<R, false, EV>(a.fg, blockIdx.x - a.nblk_cg, S, a);
+    walk<R, false, EV, TPA>(a.fg, blockIdx.x - a.nblk_cg, S, a);
 }
 
 template <typename R>
@@ -476,10 +489,6 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   }
   const bool do_fg = (which & 1) != 0;
   const bool do_cg = (which & 2) && c->has_cg && c->n_h > 0;
-  const int nb_fg = do_fg ? (c->n + kThreads - 1) / kThreads : 0;
-  const int nb_cg = do_cg ? (c->n_h + kThreads - 1) / kThreads : 0;
-  if (nb_fg + nb_cg == 0) return cudaSuccess;
-  a.nblk_cg = nb_cg;
   a.fg = ListWalk<R>{c->n, pfg, c->d_nbr_fg, c->d_cnt_fg, c->d_perm_fg,
                      static_cast<ForceOut<R>*>(c->d_f_fg), c->d_acc + kAccFg};
   // without a CG list the CG walk is never entered; its pointers are stand-ins
@@ -487,10 +496,41 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
                              static_cast<ForceOut<R>*>(c->d_f_cg), c->d_acc + kAccCg}
                : a.fg;
   const size_t smem = pair_smem<R>(c->n_types, ev);
-  if (ev)
-    k_pair<R, true><<<nb_cg + nb_fg, kThreads, smem, c->stream>>>(a);
-  else
-    k_pair<R, false><<<nb_cg + nb_fg, kThreads, smem, c->stream>>>(a);
+  // energy steps and FP64: one thread per slot, 256 per block; forces-only
+  // FP32: the autotuned (threads per slot, block size)
+  int tpa = 1, bs = kThreads;
+  if (std::is_same<R, float>::value && !ev) {
+    tpa = kPairConfigs[c->pair_cfg].tpa;
+    bs = kPairConfigs[c->pair_cfg].bs;
+  }
+  const int per = bs / tpa;  // slots per block
+  const int nb_fg = do_fg ? (c->n + per - 1) / per : 0;
+  const int nb_cg = do_cg ? (c->n_h + per - 1) / per : 0;
+  if (nb_fg + nb_cg == 0) return cudaSuccess;
+  a.nblk_cg = nb_cg;
+  const int grid = nb_cg + nb_fg;
+  if (ev) {
+    k_pair<R, true, 1, kThreads><<<grid, kThreads, smem, c->stream>>>(a);
+  } else if (!std::is_same<R, float>::value) {
+    k_pair<R, false, 1, kThreads><<<grid, kThreads, smem, c->stream>>>(a);
+  } else {
+    switch (c->pair_cfg) {
+#define RELRES_PAIR_CASE(k, T, B) \
+  case k:                         \
+    k_pair<R, false, T, B><<<grid, B, smem, c->stream>>>(a); \
+    break;
+      RELRES_PAIR_CASE(0, 1, 256)
+      RELRES_PAIR_CASE(1, 1, 128)
+      RELRES_PAIR_CASE(2, 1, 512)
+      RELRES_PAIR_CASE(3, 2, 256)
+      RELRES_PAIR_CASE(4, 4, 256)
+      RELRES_PAIR_CASE(5, 8, 256)
+      RELRES_PAIR_CASE(6, 2, 128)
+#undef RELRES_PAIR_CASE
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }

@@ -106,6 +106,15 @@ constexpr int kNQ = 7;  // E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
 constexpr int kAccFg = 0, kAccCg = kNQ, kAccKe = 2 * kNQ, kAccEb = 2 * kNQ + 1, kNAcc = 2 * kNQ + 2;
 constexpr int kBlockSteps = 100;  // steps between host status checks in relres_step
 
+// Launch configurations of the forces-only FP32 pair kernel: threads per slot
+// (lanes that share one atom's list) and block size.  Index 0 is the default;
+// the autotuner (relres_step, first call) times all of them.
+struct PairConfig {
+  int tpa, bs;
+};
+constexpr PairConfig kPairConfigs[] = {{1, 256}, {1, 128}, {1, 512}, {2, 256}, {4, 256}, {8, 256}, {2, 128}};
+constexpr int kNPairConfigs = int(sizeof(kPairConfigs) / sizeof(kPairConfigs[0]));
+
 struct Pos64 {  // FP64 mode sorted position: 64-bit fixed-point x, y, z and type
   long long x, y, z, t;
 };
@@ -263,11 +272,14 @@ struct relres_ctx {
   // each step is a conditional node whose flag a one-thread kernel sets from
   // the device displacement trigger.  Everything below is baked into the
   // instantiated graph; it is re-captured when any of it changes.
+  int pair_cfg = 0;        // index into kPairConfigs
+  int tune_mode = -1;      // -1: autotune on the first relres_step; >= 0: fixed configuration
+  bool tuned = false;
   bool use_graphs = true;
   long long buf_gen = 0;  // bumped whenever a buffer a graph may reference is reallocated
   struct StepGraph {
     bool valid = false;
-    int blk = 0, ev_phase = 0, thermo_every = 0, timing = 0;
+    int blk = 0, ev_phase = 0, thermo_every = 0, timing = 0, pair_cfg = 0;
     double dt = 0, t_target = 0, tau = 0, n_f = 0, kt = 0;
     unsigned long long seed = 0;
     const double* vel = nullptr;

@@ -34,7 +34,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_build_neighbors", "relres_compute", "relres_step", "relres_set_step_counter",
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
-            "relres_backward"]
+            "relres_backward", "relres_set_pair_config"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev"]
 
@@ -75,7 +75,7 @@ class relres_stats(C.Structure):
                 ("list_radius_fg", C.c_double), ("list_radius_cg", C.c_double),
                 ("skin_cg", C.c_double), ("grid_fg", C.c_int * 3), ("grid_cg", C.c_int * 3),
                 ("n_builds", C.c_longlong), ("n_steps", C.c_longlong), ("has_cg", C.c_int),
-                ("n_launches", C.c_longlong)]
+                ("n_launches", C.c_longlong), ("pair_tpa", C.c_int), ("pair_block", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -110,6 +110,7 @@ def load():
     L.relres_set_timing.argtypes = [vp, C.c_int]
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
+    L.relres_set_pair_config.argtypes = [vp, C.c_int]
     L.relres_backward.argtypes = [vp, vp, vp, C.c_double, vp, _dp, _dp, _dp, _dp, _dp]
     L.relres_get_timings.argtypes = [vp, _dp, C.POINTER(C.c_longlong), C.c_int]
     L.relres_pair_forces_static.argtypes = [C.POINTER(relres_params), C.c_int, vp, vp, _dp, vp, vp, vp,
@@ -293,6 +294,10 @@ def relres_set_timing(ctx, enable):
     _check(load().relres_set_timing(ctx, 1 if enable else 0), ctx)
 
 
+def relres_set_pair_config(ctx, config):
+    _check(load().relres_set_pair_config(ctx, int(config)), ctx)
+
+
 def relres_set_params(ctx, params):
     _check(load().relres_set_params(ctx, C.byref(params)), ctx)
 
@@ -384,6 +389,9 @@ class Context:
 
     def set_graphs(self, enable):
         relres_set_graphs(self.ctx, enable)
+
+    def set_pair_config(self, config):
+        relres_set_pair_config(self.ctx, config)
 
     def set_params(self, params):
         self.params = params

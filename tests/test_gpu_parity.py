@@ -252,6 +252,38 @@ def test_graph_and_stream_paths_agree_bitwise(torch):
     assert sg["n_launches"] < ss["n_launches"]
 
 
+def test_every_pair_launch_configuration_matches_oracle(torch):
+    # threads per atom 1/2/4/8 x block sizes: each within the force tolerance
+    s = S.neopentane(n_mol=500, seed=6)
+    fr, er, ebr, wr = oracle_compute(s)
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    ctx.build_neighbors(p, s.box)
+    f = torch.empty_like(p)
+    for cfg in range(7):
+        ctx.set_pair_config(cfg)
+        ctx.compute(p, f)
+        torch.cuda.synchronize()
+        err = force_err(f.cpu().numpy(), fr)
+        st = ctx.stats()
+        print(f"pair config {cfg} (tpa {st['pair_tpa']}, block {st['pair_block']}): force {err:.2e}")
+        assert err <= F_TOL, (cfg, err)
+    ctx.close()
+
+
+def test_autotuner_picks_a_configuration(torch):
+    s = S.neopentane(n_mol=5000, seed=2)  # 25 000 atoms: above the tuning threshold
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    v = _dev(torch, s.vel)
+    ctx.build_neighbors(p, s.box)
+    ctx.step(5, 2.0, p, v)
+    st = ctx.stats()
+    assert st["pair_tpa"] in (1, 2, 4, 8) and st["pair_block"] in (128, 256, 512)
+    print(f"autotuned: tpa {st['pair_tpa']} block {st['pair_block']}")
+    ctx.close()
+
+
 def test_box_too_small_is_an_error(torch):
     s = S.propane(n_mol=64, box=25.0)
     ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
