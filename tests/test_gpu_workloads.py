@@ -187,3 +187,49 @@ def test_single_pair_through_all_regions(torch):
             assert abs(e[0] + e[1] - er) <= 1e-9 * max(1.0, abs(er)), (r, prec, e, er)
             # Newton's third law holds exactly in both modes
             assert np.abs(f[0] + f[1]).max() <= 1e-12 * scale
+
+
+def _geometric_rs_radii(rs_by_type, d_s=1.0, r_c=13.5, d_c=1.0):
+    """Per-type-pair radii with r_s mixed geometrically across groups
+    (sqrt(r_s,a r_s,b)), shells of width d_s around r_s and d_c around r_c."""
+    nt = len(rs_by_type)
+    rad = np.zeros((nt, nt, 4))
+    for a in range(nt):
+        for b in range(nt):
+            rs = math.sqrt(rs_by_type[a] * rs_by_type[b])
+            rad[a, b] = (rs - d_s / 2, rs + d_s / 2, r_c - d_c / 2, r_c + d_c / 2)
+    return rad
+
+
+@pytest.mark.parametrize("precision,f_tol,e_tol", [(R.RELRES_PREC_FP64, 1e-10, 1e-10),
+                                                   (R.RELRES_PREC_FP32, F_TOL, E_TOL)])
+def test_block_copolymer_with_per_pair_radii(torch, precision, f_tol, e_tol):
+    # A groups r_s = 6 A, B groups r_s = 7 A, cross pairs the geometric mean
+    from oracle import params as P
+
+    s = S.block_copolymer(n_chain=40)
+    rad = _geometric_rs_radii([6.0, 7.0, 6.0, 7.0])
+    mixing = R.RELRES_MIX_LB
+    params = R.make_params(s.eps_fg, s.sig_fg, s.is_hybrid, s.radii, s.skin, mixing=mixing,
+                           group_comp=s.group_comp, precision=precision, radii_pair=rad)
+    ctx = R.Context(params, R.topology_for(s))
+    p = _dev(torch, s.pos)
+    ctx.build_neighbors(p, s.box)
+    f = torch.empty_like(p)
+    e = torch.zeros(4, dtype=torch.float64, device="cuda")
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.compute(p, f, e, w)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ctx.close()
+    tab = P.pair_table(s.eps_fg, s.sig_fg, s.is_hybrid, s.radii, mixing=s.mixing, group_comp=s.group_comp,
+                       radii_pair=rad)
+    fr, er, wr = O.pair_forces(s.pos, s.box, s.types, tab, s.n_types, s.excl)
+    fb, eb = O.bonded(s.pos, s.box, s.topo)
+    fr = fr + fb
+    ferr = _ferr(f.cpu().numpy(), fr)
+    eerr = abs(float(e[0] + e[1]) - er) / abs(er)
+    print(f"copolymer per-pair radii prec={precision}: force {ferr:.2e} energy {eerr:.2e} "
+          f"list radius FG {st['list_radius_fg']:.2f}")
+    assert st["list_radius_fg"] == pytest.approx(7.5 + s.skin)
+    assert ferr <= f_tol and eerr <= e_tol
