@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-fg-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable (backward) leg")
+    ap.add_argument("--batch-replicas", type=int, default=128,
+                    help="replicas of the batched leg (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -331,6 +334,8 @@ def ours(args):
     }
     if not args.no_diff:
         out["differentiable"] = differentiable_leg(torch, R, S, stream)
+    if args.batch_replicas > 0:
+        out["batched"] = batched_leg(torch, R, S, args.batch_replicas, args.batch_steps)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
     if dist:
@@ -338,6 +343,71 @@ def ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def batched_leg(torch, R, S, n_rep, steps, seed=4242):
+    """Independent replicas of uneven sizes advanced together (relres_batch:
+    one CUDA graph per block of steps for all of them) against the same
+    replicas advanced one after the other (one relres_step call each)."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(1000, 50001, size=n_rep)
+    temps = rng.uniform(200.0, 300.0, size=n_rep)
+    systems = []
+    for k in range(n_rep):
+        if k % 2 == 0:  # propane-like (3 sites), k^3 molecules on the lattice spacing of 216 in 31.8 A
+            kk = max(7, int(round((int(sizes[k]) / 3) ** (1 / 3))))
+            systems.append(S.propane(n_mol=kk ** 3, box=31.8 * kk / 6, temperature=temps[k], seed=seed + k))
+        else:  # neopentane-like (5 sites)
+            systems.append(S.neopentane(n_mol=max(200, int(sizes[k]) // 5), temperature=temps[k], seed=seed + k))
+    n_atoms = int(sum(s.n_atoms for s in systems))
+
+    def make():
+        ctxs = []
+        for s in systems:
+            ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+            p = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+            v = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+            ctx.build_neighbors(p, s.box)
+            ctxs.append((ctx, p, v))
+        return ctxs
+
+    seeds = list(range(n_rep))
+    # batched
+    ctxs = make()
+    batch = R.Batch([c for c, _, _ in ctxs])
+    pos = [p for _, p, _ in ctxs]
+    vel = [v for _, _, v in ctxs]
+    batch.step(20, 2.0, pos, vel, temps, 100.0, seeds)  # warm-up: autotuning, graph capture
+    batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)  # capture of the timed block shape
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    batch.close()
+    for c, _, _ in ctxs:
+        c.close()
+    # one after the other
+    ctxs = make()
+    for (c, p, v), t, sd in zip(ctxs, temps, seeds):
+        c.step(20, 2.0, p, v, t_target=t, seed=sd)
+        c.step(steps, 2.0, p, v, t_target=t, seed=sd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (c, p, v), t, sd in zip(ctxs, temps, seeds):
+        c.step(steps, 2.0, p, v, t_target=t, seed=sd)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    for c, _, _ in ctxs:
+        c.close()
+    return {"workload": f"{n_rep} replicas, seeded sizes 1k-50k atoms ({n_atoms} atoms in all), alternately "
+                        "propane-like (k^3 molecules) and neopentane-like, T in U[200, 300] K, CSVR, dt 2 fs, FP32",
+            "steps": steps, "value": n_atoms * steps / t_batch, "unit": "atom-steps/s",
+            "ms_per_step": t_batch / steps * 1e3,
+            "one_after_the_other": {"value": n_atoms * steps / t_seq, "ms_per_step": t_seq / steps * 1e3},
+            "timing": "host wall clock around relres_batch_step with a device synchronize on both sides"}
 
 
 def differentiable_leg(torch, R, S, stream, n_snap=64, n_mol=4000):

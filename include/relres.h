@@ -330,6 +330,33 @@ relres_status relres_backward(relres_ctx* ctx, const double* d_pos, const double
 relres_status relres_set_graphs(relres_ctx* ctx, int enable);
 
 /*
+ * Batches of independent replicas (an implementation choice; the paper has no
+ * counterpart).  relres_batch_create groups n_ctx contexts (each created,
+ * given its topology and neighbour lists as usual; any sizes and boxes; not
+ * owned: destroy them after the batch).  relres_batch_step advances all of
+ * them by n_steps like relres_step, with per-replica arrays
+ *   d_pos[r], d_vel[r]   device positions / velocities of replica r,
+ *   t_target[r], seed[r] thermostat target (<= 0: NVE) and random stream,
+ *   d_thermo             NULL or per-replica thermo buffers (may be NULL),
+ * and common dt_fs, tau_fs, thermo_every.  Each block of up to 100 steps is
+ * one CUDA graph launch holding every replica's block on its own branch (its
+ * list rebuilds as conditional nodes), so the replicas run concurrently.
+ * Results are bit-identical to stepping each context alone with the same
+ * arguments.  If any replica's list overflows, every replica returns to the
+ * block start and the block is repeated with larger lists.  cuda_stream: the
+ * stream the graphs run on (NULL: the batch creates its own).  Errors name the
+ * replica (relres_batch_last_error).  Per-class kernel timing is not recorded
+ * in batches.
+ */
+typedef struct relres_batch relres_batch;
+relres_status relres_batch_create(relres_batch** out, relres_ctx* const* ctxs, int n_ctx, void* cuda_stream);
+relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, double* const* d_pos,
+                                double* const* d_vel, const double* t_target, double tau_fs, const uint64_t* seed,
+                                int thermo_every, double* const* d_thermo);
+const char* relres_batch_last_error(relres_batch* batch);
+void relres_batch_destroy(relres_batch* batch);
+
+/*
  * Launch configuration of the forces-only FP32 pair kernel (an implementation
  * choice; the paper has no counterpart): config -1 (the default) lets the
  * first relres_step time every configuration -- threads sharing one atom's

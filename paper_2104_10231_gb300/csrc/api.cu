@@ -854,16 +854,26 @@ relres_status relres_backward(relres_ctx* c, const double* d_pos, const double* 
   return RELRES_OK;
 }
 
-relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_pos, double* d_vel,
-                          double t_target, double tau_fs, uint64_t seed, int thermo_every,
-                          double* d_thermo) {
-  if (!c) return RELRES_ERR_ARG;
+// State back to the snapshot taken at the start of the current block.
+static relres_status rollback_block(relres_ctx* c, double* d_vel) {
+  const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
+  CK(cudaMemcpyAsync(c->d_xfx, c->d_snap_x, xb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(d_vel, c->d_snap_v, vb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_f_tot, c->d_snap_f, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_state, c->d_snap_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
+  return RELRES_OK;
+}
+
+// ---- relres_step in three phases (shared with relres_batch_step)
+
+// Validation, forces at the incoming positions, autotuning, per-call constants.
+static relres_status step_begin(relres_ctx* c, int n_steps, double dt_fs, double* d_pos, double* d_vel,
+                                double t_target, double tau_fs, uint64_t seed, int thermo_every, double* d_thermo,
+                                StepParams* out) {
   if (!c->have_lists) return fail(c, RELRES_ERR_STATE, "relres_build_neighbors first");
   if (n_steps < 0 || !(dt_fs > 0.0) || !std::isfinite(dt_fs) || !d_pos || !d_vel || thermo_every < 0 ||
       (t_target > 0.0 && !(tau_fs > 0.0)))
     return fail(c, RELRES_ERR_ARG, "invalid step arguments");
-  if (n_steps == 0) return RELRES_OK;
-  if (c->n < 2 && t_target > 0.0) return fail(c, RELRES_ERR_ARG, "the thermostat needs at least 2 atoms");
   StepParams sp{};
   sp.dt = dt_fs;
   sp.t_target = t_target;
@@ -873,6 +883,9 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
   sp.seed = seed;
   sp.thermo_every = (d_thermo && thermo_every > 0) ? thermo_every : 0;
   sp.thermo = sp.thermo_every ? d_thermo : nullptr;
+  *out = sp;
+  if (n_steps == 0) return RELRES_OK;
+  if (c->n < 2 && t_target > 0.0) return fail(c, RELRES_ERR_ARG, "the thermostat needs at least 2 atoms");
 
   // forces at the incoming positions: reuse when d_pos is what we returned last
   CK(launch_flags_and(c, ~(unsigned)F_DIRTY));
@@ -891,7 +904,296 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
   CK(upload_type_consts(c, dt_fs));
   CK(launch_set_ab(c, 1.0, 1.0, 0));
   CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
-  const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
+  return read_state(c);  // also orders the setup before work on other streams
+}
+
+// After a block has run: status, timing and launch accounting; on a list
+// overflow the state goes back to the block start with larger lists
+// (*retry = true); a non-finite force ends the call.
+static relres_status block_end(relres_ctx* c, double* d_pos, double* d_vel, double dt_fs, long long builds0,
+                               bool graph, int* retries, bool* retry) {
+  *retry = false;
+  relres_status s = read_state(c);
+  if (s != RELRES_OK) return s;
+  s = flush_timing(c);
+  if (s != RELRES_OK) return s;
+  if (graph) {
+    c->n_launches += c->sg.k_parent + c->sg.k_body * std::max(0LL, c->h_state->n_builds - builds0);
+    if (c->timing)
+      for (const relres_ctx::Mark& m : c->sg.marks) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, m.a, m.b));
+        c->t_ms[m.cls] += ms;
+        c->t_cnt[m.cls] += 1;
+      }
+  }
+  const unsigned fl = c->h_state->flags;
+  if (fl & F_BADCELL) return fail(c, RELRES_ERR_CUDA, "cell binning produced an out-of-range index");
+  if (fl & (F_OVERFLOW_FG | F_OVERFLOW_CG | F_NONFINITE)) {
+    s = rollback_block(c, d_vel);
+    if (s != RELRES_OK) return s;
+    if (fl & F_NONFINITE) {
+      CK(launch_write_back(c, d_pos, d_vel, dt_fs));
+      CK(cudaStreamSynchronize(c->stream));
+      c->forces_valid = true;
+      return fail(c, RELRES_ERR_NONFINITE, "non-finite force during relres_step");
+    }
+    if (++*retries > 8) return fail(c, RELRES_ERR_LIST_OVERFLOW, "repeated list overflow");
+    s = read_state(c);
+    if (s != RELRES_OK) return s;
+    if (fl & F_OVERFLOW_FG) c->cap_fg = round_cap(std::max(c->h_state->max_fg, c->cap_fg) * 1.25 + 8, c->n);
+    if (fl & F_OVERFLOW_CG) c->cap_cg = round_cap(std::max(c->h_state->max_cg, c->cap_cg) * 1.25 + 8, c->n_h);
+    s = alloc_lists(c);
+    if (s != RELRES_OK) return s;
+    s = host_rebuild(c);  // lists at the restored positions; F_tot is still theirs
+    if (s != RELRES_OK) return s;
+    *retry = true;
+  }
+  return RELRES_OK;
+}
+
+// Positions and velocities back to the caller, counters.
+static relres_status step_end(relres_ctx* c, int n_steps, double* d_pos, double* d_vel, double dt_fs) {
+  CK(launch_write_back(c, d_pos, d_vel, dt_fs));
+  relres_status s = read_state(c);
+  if (s != RELRES_OK) return s;
+  c->n_steps += n_steps;
+  c->step_counter = c->h_state->step;
+  c->forces_valid = true;
+  return RELRES_OK;
+}
+
+// ---- batches of independent replicas: one CUDA graph per block of steps
+// holds every replica's block on its own branch (fork/join inside one stream
+// capture), each with its conditional rebuild nodes and autotuned pair
+// launch, so independent systems of any size run concurrently from one graph
+// launch and the host checks status once per block for all of them.
+
+struct BatchKey {
+  const double* vel;
+  double* thermo;
+  double t_target, n_f;
+  unsigned long long seed;
+  long long gen;
+  int pair_cfg;
+  bool operator==(const BatchKey& o) const {
+    return vel == o.vel && thermo == o.thermo && t_target == o.t_target && n_f == o.n_f && seed == o.seed &&
+           gen == o.gen && pair_cfg == o.pair_cfg;
+  }
+};
+
+struct relres_batch {
+  std::vector<relres_ctx*> ctx;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> fork;
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  cudaGraphExec_t exec = nullptr;
+  bool valid = false;
+  int blk = 0, phase = 0, thermo_every = 0;
+  double dt = 0, tau = 0;
+  std::vector<BatchKey> keys;
+  std::vector<long long> k_parent;
+  bool own_stream = false;
+  std::string err;
+};
+
+static relres_status batch_fail(relres_batch* b, relres_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+
+static void batch_drop_graph(relres_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->valid = false;
+}
+
+static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>& sp, double* const* d_vel, int blk,
+                                 int done) {
+  const int nr = int(b->ctx.size());
+  const int phase = sp[0].thermo_every > 0 ? done % sp[0].thermo_every : 0;
+  std::vector<BatchKey> keys(nr);
+  for (int r = 0; r < nr; ++r)
+    keys[r] = BatchKey{d_vel[r], sp[r].thermo, sp[r].t_target, sp[r].n_f, sp[r].seed, b->ctx[r]->buf_gen,
+                       b->ctx[r]->pair_cfg};
+  if (b->valid && b->blk == blk && b->phase == phase && b->thermo_every == sp[0].thermo_every &&
+      b->dt == sp[0].dt && b->tau == sp[0].tau && b->keys == keys)
+    return RELRES_OK;
+  batch_drop_graph(b);
+  for (int r = 0; r < nr; ++r)  // each replica captures its rebuild bodies on its own stream
+    if (!b->ctx[r]->body_stream) {
+      const cudaError_t eb = cudaStreamCreateWithFlags(&b->ctx[r]->body_stream, cudaStreamNonBlocking);
+      if (eb != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(eb));
+    }
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  e = cudaEventRecord(b->ev_fork, b->stream);
+  relres_status s = RELRES_OK;
+  b->k_parent.assign(nr, 0);
+  for (int r = 0; r < nr && s == RELRES_OK && e == cudaSuccess; ++r) {
+    relres_ctx* c = b->ctx[r];
+    e = cudaStreamWaitEvent(b->fork[r], b->ev_fork, 0);
+    if (e != cudaSuccess) break;
+    const cudaStream_t own = c->stream;
+    const bool timing = c->timing;
+    const long long n0 = c->n_launches;
+    c->stream = b->fork[r];
+    c->timing = false;  // per-class timing is not recorded in batches
+    s = record_block(c, sp[r], d_vel[r], blk, done, true);
+    if (s != RELRES_OK) b->err = "replica " + std::to_string(r) + " (capture): " + c->err;
+    b->k_parent[r] = (c->n_launches - n0) - 6LL * blk;
+    c->stream = own;
+    c->timing = timing;
+    c->n_launches = n0;
+    if (s == RELRES_OK) e = cudaEventRecord(b->ev_join[r], b->fork[r]);
+    if (s == RELRES_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[r], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (s == RELRES_OK && e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  if (s == RELRES_OK && e2 != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e2));
+  if (s == RELRES_OK) {
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (g) cudaGraphDestroy(g);
+  if (s != RELRES_OK) {
+    batch_drop_graph(b);
+    return s;
+  }
+  b->valid = true;
+  b->blk = blk;
+  b->phase = phase;
+  b->thermo_every = sp[0].thermo_every;
+  b->dt = sp[0].dt;
+  b->tau = sp[0].tau;
+  b->keys = keys;
+  return RELRES_OK;
+}
+
+relres_status relres_batch_create(relres_batch** out, relres_ctx* const* ctxs, int n_ctx, void* cuda_stream) {
+  if (!out || !ctxs || n_ctx < 1) return RELRES_ERR_ARG;
+  *out = nullptr;
+  for (int r = 0; r < n_ctx; ++r) {
+    if (!ctxs[r]) return RELRES_ERR_ARG;
+    for (int q = 0; q < r; ++q)
+      if (ctxs[q] == ctxs[r]) return RELRES_ERR_ARG;
+  }
+  relres_batch* b = new (std::nothrow) relres_batch();
+  if (!b) return RELRES_ERR_NOMEM;
+  b->ctx.assign(ctxs, ctxs + n_ctx);
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = e == cudaSuccess;
+  }
+  b->fork.assign(n_ctx, nullptr);
+  b->ev_join.assign(n_ctx, nullptr);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int r = 0; r < n_ctx && e == cudaSuccess; ++r) {
+    e = cudaStreamCreateWithFlags(&b->fork[r], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[r], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    relres_batch_destroy(b);
+    return e == cudaErrorMemoryAllocation ? RELRES_ERR_NOMEM : RELRES_ERR_CUDA;
+  }
+  *out = b;
+  return RELRES_OK;
+}
+
+relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, double* const* d_pos,
+                                double* const* d_vel, const double* t_target, double tau_fs, const uint64_t* seed,
+                                int thermo_every, double* const* d_thermo) {
+  if (!b) return RELRES_ERR_ARG;
+  if (!d_pos || !d_vel || !t_target || !seed) return batch_fail(b, RELRES_ERR_ARG, "missing per-replica arrays");
+  const int nr = int(b->ctx.size());
+  std::vector<StepParams> sp(nr);
+  for (int r = 0; r < nr; ++r) {
+    relres_status s = step_begin(b->ctx[r], n_steps, dt_fs, d_pos[r], d_vel[r], t_target[r], tau_fs, seed[r],
+                                 thermo_every, d_thermo ? d_thermo[r] : nullptr, &sp[r]);
+    if (s != RELRES_OK)
+      return batch_fail(b, s, "replica " + std::to_string(r) + ": " + b->ctx[r]->err);
+  }
+  if (n_steps == 0) return RELRES_OK;
+  int done = 0, retries = 0;
+  while (done < n_steps) {
+    const int blk = std::min(kBlockSteps, n_steps - done);
+    std::vector<long long> builds0(nr);
+    for (int r = 0; r < nr; ++r) builds0[r] = b->ctx[r]->h_state->n_builds;
+    relres_status s = batch_graph(b, sp, d_vel, blk, done);
+    if (s != RELRES_OK) return s;
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+    std::vector<unsigned> flags(nr);
+    bool overflow = false;
+    for (int r = 0; r < nr; ++r) {
+      relres_ctx* c = b->ctx[r];
+      s = read_state(c);
+      if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + c->err);
+      c->n_launches += b->k_parent[r] + 6LL * std::max(0LL, c->h_state->n_builds - builds0[r]);
+      flags[r] = c->h_state->flags;
+      if (flags[r] & F_BADCELL)
+        return batch_fail(b, RELRES_ERR_CUDA, "replica " + std::to_string(r) + ": out-of-range cell index");
+      if (flags[r] & F_NONFINITE) {
+        for (int q = 0; q < nr; ++q) rollback_block(b->ctx[q], d_vel[q]);
+        for (int q = 0; q < nr; ++q) step_end(b->ctx[q], 0, d_pos[q], d_vel[q], dt_fs);
+        return batch_fail(b, RELRES_ERR_NONFINITE, "replica " + std::to_string(r) + ": non-finite force");
+      }
+      overflow |= (flags[r] & (F_OVERFLOW_FG | F_OVERFLOW_CG)) != 0;
+    }
+    if (overflow) {  // every replica back to the block start; larger lists where they overflowed
+      if (++retries > 8) return batch_fail(b, RELRES_ERR_LIST_OVERFLOW, "repeated list overflow");
+      for (int r = 0; r < nr; ++r) {
+        relres_ctx* c = b->ctx[r];
+        s = rollback_block(c, d_vel[r]);
+        if (s == RELRES_OK) s = read_state(c);
+        if (s == RELRES_OK && (flags[r] & (F_OVERFLOW_FG | F_OVERFLOW_CG))) {
+          if (flags[r] & F_OVERFLOW_FG) c->cap_fg = round_cap(std::max(c->h_state->max_fg, c->cap_fg) * 1.25 + 8, c->n);
+          if (flags[r] & F_OVERFLOW_CG)
+            c->cap_cg = round_cap(std::max(c->h_state->max_cg, c->cap_cg) * 1.25 + 8, c->n_h);
+          s = alloc_lists(c);
+          if (s == RELRES_OK) s = host_rebuild(c);
+        }
+        if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + c->err);
+      }
+      continue;
+    }
+    done += blk;
+  }
+  for (int r = 0; r < nr; ++r) {
+    relres_status s = step_end(b->ctx[r], n_steps, d_pos[r], d_vel[r], dt_fs);
+    if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + b->ctx[r]->err);
+  }
+  return RELRES_OK;
+}
+
+const char* relres_batch_last_error(relres_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void relres_batch_destroy(relres_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  for (cudaStream_t st : b->fork)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->ev_join)
+    if (ev) cudaEventDestroy(ev);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_pos, double* d_vel,
+                          double t_target, double tau_fs, uint64_t seed, int thermo_every,
+                          double* d_thermo) {
+  if (!c) return RELRES_ERR_ARG;
+  StepParams sp{};
+  relres_status s = step_begin(c, n_steps, dt_fs, d_pos, d_vel, t_target, tau_fs, seed, thermo_every, d_thermo, &sp);
+  if (s != RELRES_OK || n_steps == 0) return s;
   int done = 0, retries = 0;
   while (done < n_steps) {
     const int blk = std::min(kBlockSteps, n_steps - done);
@@ -904,54 +1206,12 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
       s = record_block(c, sp, d_vel, blk, done, false);
       if (s != RELRES_OK) return s;
     }
-    s = read_state(c);
+    bool retry = false;
+    s = block_end(c, d_pos, d_vel, dt_fs, builds0, c->use_graphs, &retries, &retry);
     if (s != RELRES_OK) return s;
-    s = flush_timing(c);
-    if (s != RELRES_OK) return s;
-    if (c->use_graphs) {
-      c->n_launches += c->sg.k_parent + c->sg.k_body * std::max(0LL, c->h_state->n_builds - builds0);
-      if (c->timing)
-        for (const relres_ctx::Mark& m : c->sg.marks) {
-          float ms = 0.f;
-          CK(cudaEventElapsedTime(&ms, m.a, m.b));
-          c->t_ms[m.cls] += ms;
-          c->t_cnt[m.cls] += 1;
-        }
-    }
-    const unsigned fl = c->h_state->flags;
-    if (fl & F_BADCELL) return fail(c, RELRES_ERR_CUDA, "cell binning produced an out-of-range index");
-    if (fl & (F_OVERFLOW_FG | F_OVERFLOW_CG | F_NONFINITE)) {
-      // roll back to the start of this block
-      CK(cudaMemcpyAsync(c->d_xfx, c->d_snap_x, xb, cudaMemcpyDeviceToDevice, c->stream));
-      CK(cudaMemcpyAsync(d_vel, c->d_snap_v, vb, cudaMemcpyDeviceToDevice, c->stream));
-      CK(cudaMemcpyAsync(c->d_f_tot, c->d_snap_f, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-      CK(cudaMemcpyAsync(c->d_state, c->d_snap_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
-      if (fl & F_NONFINITE) {
-        CK(launch_write_back(c, d_pos, d_vel, dt_fs));
-        CK(cudaStreamSynchronize(c->stream));
-        c->forces_valid = true;
-        return fail(c, RELRES_ERR_NONFINITE, "non-finite force during relres_step");
-      }
-      if (++retries > 8) return fail(c, RELRES_ERR_LIST_OVERFLOW, "repeated list overflow");
-      s = read_state(c);
-      if (s != RELRES_OK) return s;
-      if (fl & F_OVERFLOW_FG) c->cap_fg = round_cap(std::max(c->h_state->max_fg, c->cap_fg) * 1.25 + 8, c->n);
-      if (fl & F_OVERFLOW_CG) c->cap_cg = round_cap(std::max(c->h_state->max_cg, c->cap_cg) * 1.25 + 8, c->n_h);
-      s = alloc_lists(c);
-      if (s != RELRES_OK) return s;
-      s = host_rebuild(c);  // lists at the restored positions; F_tot is still theirs
-      if (s != RELRES_OK) return s;
-      continue;
-    }
-    done += blk;
+    if (!retry) done += blk;
   }
-  CK(launch_write_back(c, d_pos, d_vel, dt_fs));
-  s = read_state(c);
-  if (s != RELRES_OK) return s;
-  c->n_steps += n_steps;
-  c->step_counter = c->h_state->step;
-  c->forces_valid = true;
-  return RELRES_OK;
+  return step_end(c, n_steps, d_pos, d_vel, dt_fs);
 }
 
 relres_status relres_set_step_counter(relres_ctx* c, long long step) {

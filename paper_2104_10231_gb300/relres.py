@@ -34,7 +34,8 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_build_neighbors", "relres_compute", "relres_step", "relres_set_step_counter",
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
-            "relres_backward", "relres_set_pair_config"]
+            "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
+            "relres_batch_last_error", "relres_batch_destroy"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev"]
 
@@ -111,6 +112,13 @@ def load():
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
     L.relres_set_pair_config.argtypes = [vp, C.c_int]
+    L.relres_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
+    L.relres_batch_step.argtypes = [vp, C.c_int, C.c_double, C.POINTER(vp), C.POINTER(vp), _dp, C.c_double,
+                                    C.POINTER(C.c_uint64), C.c_int, C.POINTER(vp)]
+    L.relres_batch_last_error.argtypes = [vp]
+    L.relres_batch_last_error.restype = C.c_char_p
+    L.relres_batch_destroy.argtypes = [vp]
+    L.relres_batch_destroy.restype = None
     L.relres_backward.argtypes = [vp, vp, vp, C.c_double, vp, _dp, _dp, _dp, _dp, _dp]
     L.relres_get_timings.argtypes = [vp, _dp, C.POINTER(C.c_longlong), C.c_int]
     L.relres_pair_forces_static.argtypes = [C.POINTER(relres_params), C.c_int, vp, vp, _dp, vp, vp, vp,
@@ -120,7 +128,7 @@ def load():
     L.relres_destroy.argtypes = [vp]
     L.relres_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("relres_last_error", "relres_destroy"):
+        if name not in ("relres_last_error", "relres_destroy", "relres_batch_last_error", "relres_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -413,3 +421,38 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Independent replicas (Context objects, any sizes) advanced together:
+    relres_batch_step runs every block of steps of all of them as one CUDA
+    graph.  The contexts stay owned by the caller; close the batch first."""
+
+    def __init__(self, contexts, stream=None):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.ctx for c in self.contexts])
+        self._arr = arr
+        h = C.c_void_p()
+        st = None if stream is None else C.c_void_p(stream.cuda_stream)
+        _check(load().relres_batch_create(C.byref(h), arr, len(self.contexts), st))
+        self.handle = h
+
+    def step(self, n_steps, dt_fs, d_pos, d_vel, t_target, tau_fs=100.0, seeds=None, thermo_every=0,
+             d_thermo=None):
+        n = len(self.contexts)
+        vp = C.c_void_p
+        pos = (vp * n)(*[_ptr(x) for x in d_pos])
+        vel = (vp * n)(*[_ptr(x) for x in d_vel])
+        tt = np.asarray(t_target, dtype=np.float64).reshape(n)
+        sd = (C.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else range(n))])
+        th = None if d_thermo is None else (vp * n)(*[_ptr(x) for x in d_thermo])
+        st = load().relres_batch_step(self.handle, int(n_steps), float(dt_fs), pos, vel,
+                                      tt.ctypes.data_as(_dp), float(tau_fs), sd, int(thermo_every), th)
+        if st != RELRES_OK:
+            msg = (load().relres_batch_last_error(self.handle) or b"").decode()
+            raise RelresError(st, msg)
+
+    def close(self):
+        if self.handle:
+            load().relres_batch_destroy(self.handle)
+            self.handle = None

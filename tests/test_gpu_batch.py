@@ -1,0 +1,92 @@
+"""Batches of independent replicas (relres_batch_step): every block of steps of
+all replicas runs as one CUDA graph; the results must be bit-identical to
+stepping each context alone with the same arguments."""
+import numpy as np
+import pytest
+
+from paper_2104_10231_gb300 import relres as R
+from paper_2104_10231_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2104_10231_gb300.build import build_library
+
+    build_library()
+    R.load()
+    return T
+
+
+def _systems():
+    # the two chemistries of the batched workload, uneven sizes and temperatures
+    return [S.propane(n_mol=216, temperature=230.0, seed=1),
+            S.neopentane(n_mol=500, temperature=260.0, seed=2),
+            S.neopentane(n_mol=300, temperature=200.0, seed=3),
+            S.propane(n_mol=400, box=31.8 * (400 / 216) ** (1 / 3), temperature=290.0, seed=4),
+            S.neopentane(n_mol=5000, temperature=240.0, seed=5)]
+
+
+def _contexts(torch, systems, pair_cfg):
+    out = []
+    for s in systems:
+        ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+        if pair_cfg is not None:
+            ctx.set_pair_config(pair_cfg)
+        p = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+        v = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+        ctx.build_neighbors(p, s.box)
+        th = torch.zeros((25, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+        out.append((ctx, p, v, th))
+    return out
+
+
+def test_batch_matches_each_replica_stepped_alone(torch):
+    systems = _systems()
+    temps = [s.temperature for s in systems]
+    seeds = [11, 12, 13, 14, 15]
+    # alone
+    solo = _contexts(torch, systems, 0)
+    for (ctx, p, v, th), t, sd in zip(solo, temps, seeds):
+        for _ in range(2):
+            ctx.step(125, 2.0, p, v, t_target=t, tau_fs=100.0, seed=sd, thermo_every=10, d_thermo=th)
+    torch.cuda.synchronize()
+    # batched (two calls: the captured graph is reused for the second)
+    batch_ctx = _contexts(torch, systems, 0)
+    batch = R.Batch([c for c, _, _, _ in batch_ctx])
+    for _ in range(2):
+        batch.step(125, 2.0, [p for _, p, _, _ in batch_ctx], [v for _, _, v, _ in batch_ctx], temps, 100.0, seeds,
+                   thermo_every=10, d_thermo=[th for _, _, _, th in batch_ctx])
+    torch.cuda.synchronize()
+    for k, ((c1, p1, v1, t1), (c2, p2, v2, t2)) in enumerate(zip(solo, batch_ctx)):
+        s1, s2 = c1.stats(), c2.stats()
+        assert s1["n_builds"] == s2["n_builds"] and s1["n_steps"] == s2["n_steps"] == 250, k
+        assert np.array_equal(p1.cpu().numpy(), p2.cpu().numpy()), k
+        assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy()), k
+        assert np.array_equal(t1.cpu().numpy(), t2.cpu().numpy()), k
+    assert max(c.stats()["n_builds"] for c, _, _, _ in batch_ctx) >= 3
+    batch.close()
+    for c, _, _, _ in solo + batch_ctx:
+        c.close()
+
+
+def test_batch_with_autotuned_replicas_runs_and_conserves_momentum(torch):
+    systems = _systems()[1:]
+    ctxs = _contexts(torch, systems, None)
+    batch = R.Batch([c for c, _, _, _ in ctxs])
+    batch.step(200, 2.0, [p for _, p, _, _ in ctxs], [v for _, _, v, _ in ctxs], [0.0] * len(ctxs), 100.0,
+               list(range(len(ctxs))))
+    torch.cuda.synchronize()
+    for (c, p, v, _), s in zip(ctxs, systems):
+        st = c.stats()
+        assert st["n_steps"] == 200 and st["pair_tpa"] in (1, 2, 4, 8)
+        m = s.mass_by_type[s.types][:, None]
+        mom = (m * v.cpu().numpy()).sum(0)
+        assert np.abs(mom).max() < 1e-6 * (m * np.abs(v.cpu().numpy())).sum(), mom
+    batch.close()
+    for c, _, _, _ in ctxs:
+        c.close()
