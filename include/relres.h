@@ -380,6 +380,16 @@ relres_status relres_set_pair_config(relres_ctx* ctx, int config);
  * (ms[k]) and the number of timed launches (counts[k]; either may be NULL).
  */
 relres_status relres_set_timing(relres_ctx* ctx, int enable);
+
+/*
+ * Sampled kernel timing: like relres_set_timing with enable != 0, but only the
+ * classes whose bit (1 << relres_timing_class) is set in class_mask, and inside
+ * relres_step only on steps k of a call with k % every == 0 (every >= 1).
+ * Event records inside the step graphs cost a few microseconds each, so a
+ * sparse sample times a kernel without slowing the steps around it.
+ * class_mask 0 stops timing.  Clears the totals.
+ */
+relres_status relres_set_timing_sampled(relres_ctx* ctx, unsigned class_mask, int every);
 relres_status relres_get_timings(relres_ctx* ctx, double* ms, long long* counts, int n);
 
 /*

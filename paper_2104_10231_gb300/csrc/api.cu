@@ -178,11 +178,16 @@ relres_status flush_timing(relres_ctx* c) {
   return RELRES_OK;
 }
 
-#define TIMED(cls, call)        \
-  do {                          \
-    if (c->timing) CK(tic(c, cls)); \
-    CK(call);                   \
-    if (c->timing) CK(toc(c));  \
+static bool timed_now(const relres_ctx* c, int cls) {
+  return c->timing && ((c->timing_mask >> cls) & 1u) && (c->cur_step % c->timing_every) == 0;
+}
+
+#define TIMED(cls, call)                     \
+  do {                                       \
+    const bool t_ = timed_now(c, cls);       \
+    if (t_) CK(tic(c, cls));                 \
+    CK(call);                                \
+    if (t_) CK(toc(c));                      \
   } while (0)
 
 // Forces at the positions already converted into d_xfx (F_tot, FP64 copy optional).
@@ -649,12 +654,14 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
   CK(cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
   CK(launch_csvr_draws(c, sp, blk));
   for (int k = 0; k < blk; ++k) {
+    c->cur_step = done + k;
     TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel));
     if (graph) {
-      if (c->timing) CK(tic(c, RELRES_T_REBUILD));
+      const bool t_ = timed_now(c, RELRES_T_REBUILD);
+      if (t_) CK(tic(c, RELRES_T_REBUILD));
       relres_status s = add_rebuild_node(c);
       if (s != RELRES_OK) return s;
-      if (c->timing) CK(toc(c));
+      if (t_) CK(toc(c));
     } else {
       TIMED(RELRES_T_REBUILD, launch_rebuild(c, gate));
       TIMED(RELRES_T_LISTS, launch_lists(c, gate));
@@ -665,6 +672,7 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
     TIMED(RELRES_T_FINISH, launch_finish(c, ev_step, nullptr, d_vel));
     TIMED(RELRES_T_THERMO, launch_thermo(c, sp, k));
   }
+  c->cur_step = 0;
   return RELRES_OK;
 }
 
@@ -672,7 +680,9 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
 static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_vel, int blk, int done) {
   relres_ctx::StepGraph& g = c->sg;
   const int phase = sp.thermo_every > 0 ? done % sp.thermo_every : 0;
+  const int t_phase = done % c->timing_every;
   if (g.valid && g.blk == blk && g.ev_phase == phase && g.thermo_every == sp.thermo_every &&
+      g.t_mask == c->timing_mask && g.t_every == c->timing_every && g.t_phase == t_phase &&
       g.timing == int(c->timing) && g.pair_cfg == c->pair_cfg && g.dt == sp.dt && g.t_target == sp.t_target && g.tau == sp.tau &&
       g.n_f == sp.n_f && g.kt == sp.kt && g.seed == sp.seed && g.vel == d_vel && g.thermo == sp.thermo &&
       g.gen == c->buf_gen)
@@ -721,6 +731,9 @@ static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_v
   g.thermo_every = sp.thermo_every;
   g.timing = int(c->timing);
   g.pair_cfg = c->pair_cfg;
+  g.t_mask = c->timing_mask;
+  g.t_every = c->timing_every;
+  g.t_phase = t_phase;
   g.dt = sp.dt;
   g.t_target = sp.t_target;
   g.tau = sp.tau;
@@ -1255,12 +1268,29 @@ relres_status relres_get_stats(relres_ctx* c, relres_stats* o) {
   return RELRES_OK;
 }
 
+relres_status relres_set_timing_sampled(relres_ctx* c, unsigned class_mask, int every) {
+  if (!c || every < 1) return RELRES_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  relres_status s = flush_timing(c);
+  if (s != RELRES_OK) return s;
+  c->timing = class_mask != 0;
+  c->timing_mask = class_mask;
+  c->timing_every = every;
+  for (int k = 0; k < RELRES_T_NCLASS; ++k) {
+    c->t_ms[k] = 0.0;
+    c->t_cnt[k] = 0;
+  }
+  return RELRES_OK;
+}
+
 relres_status relres_set_timing(relres_ctx* c, int enable) {
   if (!c) return RELRES_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   relres_status s = flush_timing(c);
   if (s != RELRES_OK) return s;
   c->timing = enable != 0;
+  c->timing_mask = ~0u;
+  c->timing_every = 1;
   for (int k = 0; k < RELRES_T_NCLASS; ++k) {
     c->t_ms[k] = 0.0;
     c->t_cnt[k] = 0;

@@ -260,6 +260,9 @@ struct relres_ctx {
   // instrumentation
   long long n_launches = 0;
   bool timing = false;
+  unsigned timing_mask = ~0u;  // timed classes (bit k: relres_timing_class k)
+  int timing_every = 1;        // time only every timing_every-th step of a call
+  int cur_step = 0;            // step of the call being recorded (0 outside relres_step)
   struct Mark {
     int cls;
     cudaEvent_t a, b;
@@ -279,7 +282,8 @@ struct relres_ctx {
   long long buf_gen = 0;  // bumped whenever a buffer a graph may reference is reallocated
   struct StepGraph {
     bool valid = false;
-    int blk = 0, ev_phase = 0, thermo_every = 0, timing = 0, pair_cfg = 0;
+    int blk = 0, ev_phase = 0, thermo_every = 0, timing = 0, pair_cfg = 0, t_every = 1, t_phase = 0;
+    unsigned t_mask = 0;
     double dt = 0, t_target = 0, tau = 0, n_f = 0, kt = 0;
     unsigned long long seed = 0;
     const double* vel = nullptr;

@@ -35,7 +35,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
-            "relres_batch_last_error", "relres_batch_destroy"]
+            "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev"]
 
@@ -109,6 +109,7 @@ def load():
     L.relres_set_step_counter.argtypes = [vp, C.c_longlong]
     L.relres_get_stats.argtypes = [vp, C.POINTER(relres_stats)]
     L.relres_set_timing.argtypes = [vp, C.c_int]
+    L.relres_set_timing_sampled.argtypes = [vp, C.c_uint, C.c_int]
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
     L.relres_set_pair_config.argtypes = [vp, C.c_int]
@@ -394,6 +395,13 @@ class Context:
 
     def set_timing(self, enable):
         relres_set_timing(self.ctx, enable)
+
+    def set_timing_sampled(self, classes, every):
+        """Time only the named classes (TIMING_CLASSES names), every k-th step."""
+        mask = 0
+        for name in classes:
+            mask |= 1 << TIMING_CLASSES.index(name)
+        _check(load().relres_set_timing_sampled(self.ctx, mask, int(every)), self.ctx)
 
     def set_graphs(self, enable):
         relres_set_graphs(self.ctx, enable)
