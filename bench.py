@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--batch-replicas", type=int, default=128,
                     help="replicas of the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--pair-config", type=int, default=-1,
+                    help="fix the pair-kernel launch configuration (0..6) instead of autotuning")
     return ap.parse_args()
 
 
@@ -213,6 +215,7 @@ def ours(args):
     with torch.cuda.stream(stream):
         ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s), stream=stream)
         ctx.set_graphs(not args.no_graphs)
+        ctx.set_pair_config(args.pair_config)
         pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
         vel = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
         ctx.build_neighbors(pos, s.box)
