@@ -359,28 +359,100 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
     return fail(c, RELRES_ERR_ARG, "bonded parameters missing");
   if (t->n_bonds + t->n_angles + t->n_dihedrals >= (1 << 28))
     return fail(c, RELRES_ERR_ARG, "too many bonded terms");
+  // Terms of each kind in the order of their lowest atom (so that a run of
+  // whole molecules owns a contiguous range of every kind, see segments below),
+  // and the per-atom lists of incident terms in that order.
+  auto order_by_min_atom = [&](int count, const int* atoms, int width) {
+    std::vector<int> ord(size_t(std::max(0, count)));
+    std::vector<int> lo(size_t(std::max(0, count)));
+    for (int k = 0; k < count; ++k) {
+      ord[k] = k;
+      int m = atoms[width * k];
+      for (int w = 1; w < width; ++w) m = std::min(m, atoms[width * k + w]);
+      lo[k] = m;
+    }
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return lo[x] < lo[y]; });
+    return ord;
+  };
+  const std::vector<int> ob = order_by_min_atom(t->n_bonds, t->bonds, 2);
+  const std::vector<int> oa = order_by_min_atom(t->n_angles, t->angles, 3);
+  const std::vector<int> od = order_by_min_atom(t->n_dihedrals, t->dihedrals, 4);
   std::vector<std::vector<int>> inc(static_cast<size_t>(n));
   std::vector<int4> hb(size_t(std::max(1, t->n_bonds))), ha(size_t(std::max(1, t->n_angles))),
       hd(size_t(std::max(1, t->n_dihedrals)));
   std::vector<int> hdt(size_t(std::max(1, t->n_dihedrals)), 0);
+  // atoms spanned by each term (sorted order), for the segment boundaries
+  std::vector<int> span_lo, span_hi;
   for (int k = 0; k < t->n_bonds; ++k) {
-    hb[k] = make_int4(t->bonds[2 * k], t->bonds[2 * k + 1], t->bond_type[k], 0);
-    for (int r = 0; r < 2; ++r) inc[size_t(t->bonds[2 * k + r])].push_back((0 << 30) | (r << 28) | k);
+    const int q = ob[k];
+    hb[k] = make_int4(t->bonds[2 * q], t->bonds[2 * q + 1], t->bond_type[q], 0);
+    for (int r = 0; r < 2; ++r) inc[size_t(t->bonds[2 * q + r])].push_back((0 << 30) | (r << 28) | k);
+    span_lo.push_back(std::min(hb[k].x, hb[k].y));
+    span_hi.push_back(std::max(hb[k].x, hb[k].y));
   }
   for (int k = 0; k < t->n_angles; ++k) {
-    ha[k] = make_int4(t->angles[3 * k], t->angles[3 * k + 1], t->angles[3 * k + 2], t->angle_type[k]);
-    for (int r = 0; r < 3; ++r) inc[size_t(t->angles[3 * k + r])].push_back((1 << 30) | (r << 28) | k);
+    const int q = oa[k];
+    ha[k] = make_int4(t->angles[3 * q], t->angles[3 * q + 1], t->angles[3 * q + 2], t->angle_type[q]);
+    for (int r = 0; r < 3; ++r) inc[size_t(t->angles[3 * q + r])].push_back((1 << 30) | (r << 28) | k);
+    span_lo.push_back(std::min({ha[k].x, ha[k].y, ha[k].z}));
+    span_hi.push_back(std::max({ha[k].x, ha[k].y, ha[k].z}));
   }
   for (int k = 0; k < t->n_dihedrals; ++k) {
-    hd[k] = make_int4(t->dihedrals[4 * k], t->dihedrals[4 * k + 1], t->dihedrals[4 * k + 2],
-                      t->dihedrals[4 * k + 3]);
-    hdt[k] = t->dihedral_type[k];
-    for (int r = 0; r < 4; ++r) inc[size_t(t->dihedrals[4 * k + r])].push_back((2 << 30) | (r << 28) | k);
+    const int q = od[k];
+    hd[k] = make_int4(t->dihedrals[4 * q], t->dihedrals[4 * q + 1], t->dihedrals[4 * q + 2],
+                      t->dihedrals[4 * q + 3]);
+    hdt[k] = t->dihedral_type[q];
+    for (int r = 0; r < 4; ++r) inc[size_t(t->dihedrals[4 * q + r])].push_back((2 << 30) | (r << 28) | k);
+    span_lo.push_back(std::min({hd[k].x, hd[k].y, hd[k].z, hd[k].w}));
+    span_hi.push_back(std::max({hd[k].x, hd[k].y, hd[k].z, hd[k].w}));
   }
   std::vector<int> ioff(size_t(n) + 1, 0), iall;
   for (int i = 0; i < n; ++i) {
     ioff[i + 1] = ioff[i] + int(inc[i].size());
     iall.insert(iall.end(), inc[i].begin(), inc[i].end());
+  }
+  // Segments: runs of at most kSegAtoms atoms that no bonded term crosses,
+  // each with the contiguous range of its terms of every kind.  The fused
+  // bonded + force-sum kernel gives one block to each segment; without a valid
+  // segmentation (a molecule larger than a segment) the two-kernel path runs.
+  std::vector<int> seg;
+  int seg_slots = 0;
+  bool seg_ok = true;
+  {
+    std::vector<int> cross(size_t(n) + 2, 0);  // > 0: a term spans the boundary before atom a
+    for (size_t k = 0; k < span_lo.size(); ++k) {
+      cross[size_t(span_lo[k]) + 1] += 1;
+      cross[size_t(span_hi[k]) + 1] -= 1;
+    }
+    for (int a = 1; a <= n; ++a) cross[a] += cross[a - 1];
+    auto first_ge = [](const std::vector<int4>& v, int count, int which, int atom) {
+      int lo = 0, hi = count;
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        const int4 q = v[mid];
+        int m = std::min(q.x, q.y);
+        if (which >= 1) m = std::min(m, q.z);
+        if (which >= 2) m = std::min(m, q.w);
+        if (m < atom) lo = mid + 1; else hi = mid;
+      }
+      return lo;
+    };
+    int a0 = 0;
+    while (a0 < n && seg_ok) {
+      int a1 = std::min(n, a0 + kSegAtoms);
+      while (a1 > a0 && a1 < n && cross[a1] > 0) --a1;
+      if (a1 == a0) {
+        seg_ok = false;
+        break;
+      }
+      const int b0 = first_ge(hb, t->n_bonds, 0, a0), b1 = first_ge(hb, t->n_bonds, 0, a1);
+      const int g0 = first_ge(ha, t->n_angles, 1, a0), g1 = first_ge(ha, t->n_angles, 1, a1);
+      const int d0 = first_ge(hd, t->n_dihedrals, 2, a0), d1 = first_ge(hd, t->n_dihedrals, 2, a1);
+      seg.insert(seg.end(), {a0, a1, b0, b1, g0, g1, d0, d1});
+      seg_slots = std::max(seg_slots, 2 * (b1 - b0) + 3 * (g1 - g0) + 4 * (d1 - d0));
+      a0 = a1;
+    }
+    if (size_t(std::max(1, seg_slots)) * 24 > kSegSmemMax) seg_ok = false;
   }
   std::vector<double> bp(2 * size_t(std::max(1, t->n_bond_types)), 0.0),
       ap(2 * size_t(std::max(1, t->n_angle_types)), 0.0), dp(4 * size_t(std::max(1, t->n_dihedral_types)), 0.0);
@@ -483,6 +555,13 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(cudaMemcpy(c->d_dih_par, dp.data(), sizeof(double) * dp.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->d_inc_off, ioff.data(), sizeof(int) * ioff.size(), cudaMemcpyHostToDevice));
   if (!iall.empty()) CK(cudaMemcpy(c->d_inc, iall.data(), sizeof(int) * iall.size(), cudaMemcpyHostToDevice));
+  c->seg_ok = seg_ok && !seg.empty();
+  c->n_seg = int(seg.size() / 8);
+  c->seg_slots = std::max(1, seg_slots);
+  if (c->seg_ok) {
+    CK(dalloc(&c->d_seg, seg.size()));
+    CK(cudaMemcpy(c->d_seg, seg.data(), sizeof(int) * seg.size(), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(c->d_rank_cg, rank_cg.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CK(cudaMemset(c->d_f_cg, 0, fb));
   c->have_topo = true;
@@ -1365,6 +1444,7 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_f_cg);
   dfree(c->d_f_tot);
   dfree(c->d_tf);
+  dfree(c->d_seg);
   dfree(c->d_basis);
   dfree(c->d_gc);
   dfree(c->d_g_fg);

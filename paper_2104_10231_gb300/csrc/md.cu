@@ -473,6 +473,130 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a) {
   }
 }
 
+// ---- fused bonded terms + force sum, one block per segment of whole molecules
+// (at most kSegAtoms atoms that no bonded term crosses).  The block evaluates
+// its segment's terms into shared-memory slots (one per atom of a term), then
+// each thread sums one atom's pair forces and slots: the same arithmetic as
+// k_bonded + k_finish without the global slot array.
+
+template <typename R>
+struct SegArgs {
+  const int* seg;  // [n_seg][8]: atoms [a0, a1), bonds [b0, b1), angles, dihedrals
+  BondedArgs B;
+  const unsigned long long* xfx;
+  Sc3<R> sc;
+  float q0h, q0l, q1h, q1l, q2h, q2l;
+  const ForceT<R>* f_fg;
+  const ForceT<R>* f_cg;
+  int with_cg;
+  const int* type;
+  int hyb_mask;
+  const int* inc_off;
+  const int* inc;
+  const double* vel;
+  int with_ke;
+  const double* cdt;
+  const double* mass;
+  ForceT<R>* f_tot;
+  double* f_out;
+  int with_out;
+  long long* acc;
+  DevState* st;
+};
+
+template <typename R, bool EV>
+__global__ void __launch_bounds__(kThreads) k_finish_seg(SegArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ForceT<R>* slot = reinterpret_cast<ForceT<R>*>(smem_raw);
+  const int* g = a.seg + 8 * blockIdx.x;
+  const int a0 = g[0], a1 = g[1], b0 = g[2], b1 = g[3], g0 = g[4], g1 = g[5], d0 = g[6], d1 = g[7];
+  const int nb = b1 - b0, na = g1 - g0, nd = d1 - d0;
+  const int base_a = 2 * nb, base_d = base_a + 3 * na;
+  const Sc3<R> sc = a.sc;
+  R e = R(0);
+  for (int q = threadIdx.x; q < nb + na + nd; q += blockDim.x) {
+    if (q < nb) {
+      R f[2][3];
+      if constexpr (std::is_same<R, float>::value)
+        e += bond_forces_ff(a.B, a.xfx, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, b0 + q, f);
+      else
+        e += bond_forces<R>(a.B, a.xfx, sc, b0 + q, f);
+      save_slots<2, R>(slot, 2 * size_t(q), f);
+    } else if (q < nb + na) {
+      const int u = q - nb;
+      R f[3][3];
+      if constexpr (std::is_same<R, float>::value)
+        e += angle_forces_f32(a.B, a.xfx, sc, g0 + u, f);
+      else
+        e += angle_forces<R>(a.B, a.xfx, sc, g0 + u, f);
+      save_slots<3, R>(slot, base_a + 3 * size_t(u), f);
+    } else {
+      const int u = q - nb - na;
+      R f[4][3];
+      e += dihedral_forces<R>(a.B, a.xfx, sc, d0 + u, f);
+      save_slots<4, R>(slot, base_d + 4 * size_t(u), f);
+    }
+  }
+  if (EV) {
+    double v[1] = {double(e)};
+    __shared__ double sh_e[kThreads / 32];
+    block_sum<double, 1>(v, sh_e);
+    if (threadIdx.x == 0) acc_add(a.acc + kAccEb, v[0]);
+  }
+  __syncthreads();
+  R ke = R(0);
+  bool bad = false;
+  const int i = a0 + threadIdx.x;
+  if (i < a1) {
+    const int t = a.type[i];
+    R f[3];
+    load_force(a.f_fg, i, f);
+    if (a.with_cg && ((a.hyb_mask >> t) & 1)) {
+      R h[3];
+      load_force(a.f_cg, i, h);
+      f[0] += h[0];
+      f[1] += h[1];
+      f[2] += h[2];
+    }
+    const int k1 = a.inc_off[i + 1];
+    for (int k = a.inc_off[i]; k < k1; ++k) {
+      const int item = a.inc[k];
+      const int kind = (item >> 30) & 3, role = (item >> 28) & 3, term = item & 0x0fffffff;
+      const int s = kind == 0 ? 2 * (term - b0) + role
+                              : (kind == 1 ? base_a + 3 * (term - g0) + role : base_d + 4 * (term - d0) + role);
+      R h[3];
+      load_force(slot, s, h);
+      f[0] += h[0];
+      f[1] += h[1];
+      f[2] += h[2];
+    }
+    bad = !(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]));
+    save_force(a.f_tot, i, f);
+    if (a.with_out) {
+      a.f_out[3 * i] = double(f[0]);
+      a.f_out[3 * i + 1] = double(f[1]);
+      a.f_out[3 * i + 2] = double(f[2]);
+    }
+    if (a.with_ke) {
+      const R c = R(a.cdt[t]);
+      R v2 = R(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const R v = R(a.vel[3 * i + q]) + c * f[q];
+        v2 += v * v;
+      }
+      ke = R(0.5 * a.mass[t] * kMvv2e) * v2;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&a.st->flags, F_NONFINITE);
+  if (a.with_ke) {
+    double v[1] = {double(ke)};
+    __shared__ double sh_k[kThreads / 32];
+    block_sum<double, 1>(v, sh_k);
+    if (threadIdx.x == 0) acc_add(a.acc + kAccKe, v[0]);
+  }
+}
+
 // ----------------------------------------------------------------- drift
 
 template <typename R>
@@ -774,7 +898,46 @@ static cudaError_t launch_finish_t(relres_ctx* c, double* d_forces_out, const do
   return cudaGetLastError();
 }
 
+template <typename R>
+static cudaError_t launch_finish_seg_t(relres_ctx* c, bool ev, double* d_forces_out, const double* vel) {
+  const double k = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
+  SegArgs<R> a{};
+  a.seg = c->d_seg;
+  a.B = bonded_args(c);
+  a.xfx = c->d_xfx;
+  a.sc = Sc3<R>{R(c->box[0] / k), R(c->box[1] / k), R(c->box[2] / k)};
+  ff_split(c->box[0] / 18446744073709551616.0, &a.q0h, &a.q0l);
+  ff_split(c->box[1] / 18446744073709551616.0, &a.q1h, &a.q1l);
+  ff_split(c->box[2] / 18446744073709551616.0, &a.q2h, &a.q2l);
+  a.f_fg = static_cast<const ForceT<R>*>(c->d_f_fg);
+  a.f_cg = static_cast<const ForceT<R>*>(c->d_f_cg);
+  a.with_cg = (c->has_cg && c->n_h > 0) ? 1 : 0;
+  a.type = c->d_type;
+  a.hyb_mask = c->hyb_mask;
+  a.inc_off = c->d_inc_off;
+  a.inc = c->d_inc;
+  a.vel = vel ? vel : static_cast<const double*>(c->d_dummy);
+  a.with_ke = vel ? 1 : 0;
+  a.cdt = c->d_cdt;
+  a.mass = c->d_mass;
+  a.f_tot = static_cast<ForceT<R>*>(c->d_f_tot);
+  a.f_out = d_forces_out ? d_forces_out : static_cast<double*>(c->d_dummy);
+  a.with_out = d_forces_out ? 1 : 0;
+  a.acc = c->d_acc;
+  a.st = c->d_state;
+  const size_t smem = size_t(c->seg_slots) * (std::is_same<R, float>::value ? 16 : 24);
+  if (ev)
+    k_finish_seg<R, true><<<c->n_seg, kThreads, smem, c->stream>>>(a);
+  else
+    k_finish_seg<R, false><<<c->n_seg, kThreads, smem, c->stream>>>(a);
+  RELRES_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finish(relres_ctx* c, bool ev, double* d_forces_out, const double* d_vel) {
+  if (c->seg_ok && c->use_seg)
+    return c->fp64 ? launch_finish_seg_t<double>(c, ev, d_forces_out, d_vel)
+                   : launch_finish_seg_t<float>(c, ev, d_forces_out, d_vel);
   if (c->fp64) {
     const cudaError_t e = launch_bonded_t<double>(c, ev);
     return e != cudaSuccess ? e : launch_finish_t<double>(c, d_forces_out, d_vel);

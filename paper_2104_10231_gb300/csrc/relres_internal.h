@@ -105,6 +105,8 @@ constexpr int kNQ = 7;  // E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
 // accumulator slots: FG pair sums, CG pair sums, kinetic energy, bonded energy
 constexpr int kAccFg = 0, kAccCg = kNQ, kAccKe = 2 * kNQ, kAccEb = 2 * kNQ + 1, kNAcc = 2 * kNQ + 2;
 constexpr int kBlockSteps = 100;  // steps between host status checks in relres_step
+constexpr int kSegAtoms = 256;       // atoms per segment (one block of the fused force sum)
+constexpr size_t kSegSmemMax = 48 * 1024;  // shared memory of a segment's term slots
 
 // Launch configurations of the forces-only FP32 pair kernel: threads per slot
 // (lanes that share one atom's list) and block size.  Index 0 is the default;
@@ -238,6 +240,12 @@ struct relres_ctx {
 
   // bonded-term force slots: bonds 2 per term, then angles 3, then dihedrals 4
   void* d_tf = nullptr;
+  // segments of whole molecules for the fused bonded + force-sum kernel:
+  // [n_seg][8] = atom range, then the bond, angle and dihedral ranges
+  int* d_seg = nullptr;
+  int n_seg = 0, seg_slots = 0;
+  bool seg_ok = false;
+  bool use_seg = true;  // the fused kernel where segments exist (relres_set_option)
   // reductions: 64-bit fixed-point accumulators (kNAcc), cleared by their reader
   long long* d_acc = nullptr;
   double* d_draws = nullptr;  // CSVR random numbers of the current block of steps, 2 per step

@@ -233,3 +233,13 @@ def test_block_copolymer_with_per_pair_radii(torch, precision, f_tol, e_tol):
           f"list radius FG {st['list_radius_fg']:.2f}")
     assert st["list_radius_fg"] == pytest.approx(7.5 + s.skin)
     assert ferr <= f_tol and eerr <= e_tol
+
+
+@pytest.mark.parametrize("precision,f_tol,e_tol", [(R.RELRES_PREC_FP64, 1e-10, 1e-10),
+                                                   (R.RELRES_PREC_FP32, F_TOL, E_TOL)])
+def test_chains_longer_than_a_force_segment(torch, precision, f_tol, e_tol):
+    # 300-bead chains: no run of whole molecules fits the fused bonded + force-sum
+    # kernel's 256-atom segment, so the bonded kernel + per-atom sum path runs
+    s = S.block_copolymer(n_chain=12, n_bead=300, block=150, density=0.5)
+    assert s.n_atoms == 3600
+    _check_full(torch, s, precision, f_tol, e_tol)
