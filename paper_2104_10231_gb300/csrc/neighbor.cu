@@ -276,8 +276,8 @@ __device__ __forceinline__ float wrap1(float d, float l, float il) { return d - 
 template <bool WRAP>
 __device__ __forceinline__ int scan_window(const float4* s_pos, const int* s_atom, int wn32, int ai,
                                            float px, float py, float pz, float rl2, float lx, float ly,
-                                           float lz, int e0, int e1, const int* excl_idx, int win,
-                                           int* nbr_s, unsigned stride, int cap, int k) {
+                                           float lz, const int (&ex)[8], int e0, int e1, const int* excl_idx,
+                                           int win, int* nbr_s, unsigned stride, int cap, int k) {
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
   for (int j0 = 0; j0 < wn32; j0 += 32) {
@@ -292,8 +292,11 @@ __device__ __forceinline__ int scan_window(const float4* s_pos, const int* s_ato
     const int aj = s_atom[j0 + lane];
     if (WRAP) acc = acc && aj >= 0;  // wrapped padding can land anywhere
     if (acc && unsigned(aj - ai + win) <= unsigned(2 * win)) {
+      // the first eight excluded partners are in registers (-1 where unused)
       acc = aj != ai;
-      for (int e = e0; e < e1; ++e) acc = acc && excl_idx[e] != aj;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc = acc && ex[e] != aj;
+      for (int e = e0 + 8; e < e1; ++e) acc = acc && excl_idx[e] != aj;
     }
     const unsigned b = __ballot_sync(0xffffffffu, acc);
     const int kk = k + __popc(b & below);
@@ -433,12 +436,15 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
         const float px = dfix32(p.x, ref.x, a.sx), py = dfix32(p.y, ref.y, a.sy), pz = dfix32(p.z, ref.z, a.sz);
         const int ai = a.perm[s];
         const int e0 = a.excl_off[ai], e1 = a.excl_off[ai + 1];
+        int ex[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) ex[e] = e0 + e < e1 ? a.excl_idx[e0 + e] : -1;
         int* const nbr_s = a.nbr + 4 * size_t(s);
         const unsigned stride = 4u * unsigned(a.nslots);
-        const int k = wrap ? scan_window<true>(s_pos, s_atom, wn32, ai, px, py, pz, a.rl2, lx, ly, lz, e0, e1,
-                                               a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il])
-                           : scan_window<false>(s_pos, s_atom, wn32, ai, px, py, pz, a.rl2, lx, ly, lz, e0, e1,
-                                                a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il]);
+        const int k = wrap ? scan_window<true>(s_pos, s_atom, wn32, ai, px, py, pz, a.rl2, lx, ly, lz, ex, e0,
+                                               e1, a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il])
+                           : scan_window<false>(s_pos, s_atom, wn32, ai, px, py, pz, a.rl2, lx, ly, lz, ex, e0,
+                                                e1, a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il]);
         if (lane == 0) s_k[il] = k;
       }
     }
