@@ -348,6 +348,15 @@ relres_status relres_set_graphs(relres_ctx* ctx, int enable);
  * replica (relres_batch_last_error).  Per-class kernel timing is not recorded
  * in batches.
  */
+/*
+ * Set the capacities of the FG and CG lists (entries per slot, rounded up to a
+ * multiple of 8) and rebuild the lists at the current positions; a capacity
+ * too small for them grows as on an overflow.  Later overflows inside
+ * relres_step roll the step block back and grow the lists automatically, so
+ * this only bounds the memory a caller is willing to start with.  Synchronous.
+ */
+relres_status relres_set_list_caps(relres_ctx* ctx, int cap_fg, int cap_cg);
+
 typedef struct relres_batch relres_batch;
 relres_status relres_batch_create(relres_batch** out, relres_ctx* const* ctxs, int n_ctx, void* cuda_stream);
 relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, double* const* d_pos,

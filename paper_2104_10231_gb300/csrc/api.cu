@@ -667,6 +667,20 @@ static relres_status autotune_pairs(relres_ctx* c) {
   return RELRES_OK;
 }
 
+relres_status relres_set_list_caps(relres_ctx* c, int cap_fg, int cap_cg) {
+  if (!c || cap_fg < 1 || cap_cg < 1) return RELRES_ERR_ARG;
+  if (!c->have_lists) return fail(c, RELRES_ERR_STATE, "relres_build_neighbors first");
+  CK(cudaStreamSynchronize(c->stream));
+  c->cap_fg = round_cap(cap_fg, c->n);
+  c->cap_cg = round_cap(cap_cg, c->n_h);
+  relres_status s = alloc_lists(c);
+  if (s != RELRES_OK) return s;
+  s = host_rebuild(c);  // at the current positions; grows a capacity that is too small
+  if (s != RELRES_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return RELRES_OK;
+}
+
 relres_status relres_set_pair_config(relres_ctx* c, int config) {
   if (!c || config < -1 || config >= kNPairConfigs) return RELRES_ERR_ARG;
   c->tune_mode = config;

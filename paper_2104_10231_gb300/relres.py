@@ -35,7 +35,8 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
-            "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled"]
+            "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled",
+            "relres_set_list_caps"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev"]
 
@@ -110,6 +111,7 @@ def load():
     L.relres_get_stats.argtypes = [vp, C.POINTER(relres_stats)]
     L.relres_set_timing.argtypes = [vp, C.c_int]
     L.relres_set_timing_sampled.argtypes = [vp, C.c_uint, C.c_int]
+    L.relres_set_list_caps.argtypes = [vp, C.c_int, C.c_int]
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
     L.relres_set_pair_config.argtypes = [vp, C.c_int]
@@ -405,6 +407,9 @@ class Context:
 
     def set_graphs(self, enable):
         relres_set_graphs(self.ctx, enable)
+
+    def set_list_caps(self, cap_fg, cap_cg):
+        _check(load().relres_set_list_caps(self.ctx, int(cap_fg), int(cap_cg)), self.ctx)
 
     def set_pair_config(self, config):
         relres_set_pair_config(self.ctx, config)

@@ -284,6 +284,46 @@ def test_autotuner_picks_a_configuration(torch):
     ctx.close()
 
 
+def test_list_overflow_inside_a_step_block_rolls_back_and_grows(torch):
+    # lists sized exactly for the first build: a later device-side rebuild
+    # overflows, the block is rolled back, the lists grow, the block reruns;
+    # the forces at the end still match the oracle
+    s = S.neopentane(n_mol=500, seed=31)
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    v = _dev(torch, s.vel)
+    ctx.build_neighbors(p, s.box)
+    st0 = ctx.stats()
+    ctx.set_list_caps(st0["max_fg"], st0["max_cg"])
+    c1 = ctx.stats()
+    ctx.step(600, 2.0, p, v, t_target=260.0, tau_fs=100.0, seed=4)
+    torch.cuda.synchronize()
+    s1 = ctx.stats()
+    assert s1["n_steps"] == 600
+    assert s1["cap_fg"] > c1["cap_fg"] or s1["cap_cg"] > c1["cap_cg"], (c1, s1)  # grew during the steps
+    pos = p.cpu().numpy()
+    f = torch.empty_like(p)
+    ctx.compute(p, f)
+    torch.cuda.synchronize()
+    ctx.close()
+    fr, _, _, _ = oracle_compute(s, pos=pos)
+    assert force_err(f.cpu().numpy(), fr) <= F_TOL
+
+
+def test_list_overflow_at_the_first_build_grows_the_lists(torch):
+    # molecules crowded into half of a box twice as long: the capacity guessed
+    # from the mean density is too small for the real one
+    base = S.neopentane(n_mol=400, seed=32)
+    pos = base.pos.copy()
+    box = base.box.copy()
+    box[0] *= 2.0
+    s = base.subset_copy(pos=pos, box=box)
+    f, e, w, st = gpu_compute(torch, s, R.RELRES_PREC_FP32)
+    fr, er, ebr, wr = oracle_compute(s)
+    assert force_err(f, fr) <= F_TOL
+    assert abs(e[0] + e[1] - er) / abs(er) <= E_TOL
+
+
 def test_box_too_small_is_an_error(torch):
     s = S.propane(n_mol=64, box=25.0)
     ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
