@@ -12,6 +12,10 @@
 
 using namespace relres;
 
+extern "C" {
+static relres_status autotune_pairs(relres_ctx* c);  // defined with the C entry points below
+}
+
 namespace {
 
 constexpr double kBoltz = 0.0019872042586408316;  // kcal/mol/K (R / 4184 J/kcal)
@@ -201,6 +205,10 @@ relres_status forces_now(relres_ctx* c, int ev_mode, double* d_forces, double* d
   }
   if (c->h_state->flags & F_REBUILD) {
     s = host_rebuild(c);
+    if (s != RELRES_OK) return s;
+  }
+  if (!c->tuned) {
+    s = autotune_pairs(c);
     if (s != RELRES_OK) return s;
   }
   CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));

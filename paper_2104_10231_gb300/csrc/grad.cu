@@ -194,8 +194,8 @@ __device__ __forceinline__ void grad_walk(const GradWalk<R>& W, int blk, const B
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_pair_grad(GradLaunch<R> a) {
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_pair_grad(GradLaunch<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrow = a.nt * a.nt;
   BasisTab<R>* tab = reinterpret_cast<BasisTab<R>*>(smem_raw);
@@ -284,14 +284,19 @@ static cudaError_t launch_grad_t(relres_ctx* c, const double* d_grad_forces, dou
   }
   a.fg = GradWalk<R>{c->n, pfg, c->d_nbr_fg, c->d_cnt_fg, c->d_perm_fg, gfg, xfg};
   a.cg = do_cg ? GradWalk<R>{c->n_h, pcg, c->d_nbr_cg, c->d_cnt_cg, c->d_perm_cg, gcg, xcg} : a.fg;
-  const int nb_fg = (c->n + kThreads - 1) / kThreads;
-  const int nb_cg = do_cg ? (c->n_h + kThreads - 1) / kThreads : 0;
+  // small systems: 64-thread blocks, so that the launch covers every SM
+  const int bs = c->n < 200000 ? 64 : kThreads;
+  const int nb_fg = (c->n + bs - 1) / bs;
+  const int nb_cg = do_cg ? (c->n_h + bs - 1) / bs : 0;
   a.nblk_cg = nb_cg;
   const int nrow = c->n_types * c->n_types;
   const size_t smem = ((sizeof(BasisTab<R>) * nrow + 15) / 16) * 16 + sizeof(double) * 2 * nrow;
   const cudaError_t ez = cudaMemsetAsync(c->d_gc, 0, sizeof(double) * 4 * nrow, c->stream);
   if (ez != cudaSuccess) return ez;
-  k_pair_grad<R><<<nb_cg + nb_fg, kThreads, smem, c->stream>>>(a);
+  if (bs == 64)
+    k_pair_grad<R, 64><<<nb_cg + nb_fg, 64, smem, c->stream>>>(a);
+  else
+    k_pair_grad<R, kThreads><<<nb_cg + nb_fg, kThreads, smem, c->stream>>>(a);
   RELRES_LAUNCHED(c);
   if (d_grad_pos) {
     k_sum_gx<R><<<grid_for(c->n), kThreads, 0, c->stream>>>(c->n, xfg, xcg, do_cg ? 1 : 0, d_grad_pos);
