@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--batch-replicas", type=int, default=128,
                     help="replicas of the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--prune", type=float, default=0.5,
+                    help="pruning margin of the neighbour lists in Angstrom (0: pair kernels walk the full lists)")
     ap.add_argument("--pair-config", type=int, default=-1,
                     help="fix the pair-kernel launch configuration (0..6) instead of autotuning")
     return ap.parse_args()
@@ -76,6 +78,9 @@ def workload_config(args, n_atoms, box):
         "parallelism": "replicas only (one independent system per GPU)",
         "thermo_every": args.thermo_every,
         "execution": "stream launches" if args.no_graphs else "CUDA graph per 100 steps, conditional rebuild node",
+        "lists": (f"rebuilt at skin/2 = 1 A displacement; pair kernels walk lists pruned to the cutoff + "
+                  f"{args.prune} A, re-pruned at {args.prune / 2} A displacement") if args.prune > 0 else
+                 "rebuilt at skin/2 = 1 A displacement; pair kernels walk the full lists",
         "seed": 2104,
     }
 
@@ -90,19 +95,22 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic():
-    """DRAM bytes per FG pair-kernel launch from the committed ncu summary, if
-    it was taken on the current pair.cu (sha256 prefix recorded there)."""
+def recorded_traffic(p_prune):
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
+    was taken on the current pair.cu (sha256 prefix recorded there): the mean
+    over plain launches and pruning launches (a fraction p_prune)."""
     try:
         src_sha = hashlib.sha256(open(PAIR_SRC, "rb").read()).hexdigest()[:16]
         vals = {}
         for line in open(TRAFFIC_FILE):
-            if ":" in line:
+            if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
         if vals.get("pair_cu_sha256_16") != src_sha:
             return None
-        return float(vals["dram_bytes_per_launch_full_size"])
+        plain = float(vals["dram_bytes_plain_launch_full_size"])
+        prune = float(vals["dram_bytes_pruning_launch_full_size"])
+        return (1.0 - p_prune) * plain + p_prune * prune
     except Exception:
         return None
 
@@ -216,6 +224,7 @@ def ours(args):
         ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s), stream=stream)
         ctx.set_graphs(not args.no_graphs)
         ctx.set_pair_config(args.pair_config)
+        ctx.set_prune(args.prune)
         pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
         vel = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
         ctx.build_neighbors(pos, s.box)
@@ -279,6 +288,7 @@ def ours(args):
         with torch.cuda.stream(stream):
             ctxf = R.Context(R.params_for(sf, R.RELRES_PREC_FP32), R.topology_for(sf), stream=stream)
             ctxf.set_graphs(not args.no_graphs)
+            ctxf.set_prune(args.prune)
             posf = pos.clone()
             velf = vel.clone()
             ctxf.build_neighbors(posf, s.box)
@@ -299,7 +309,7 @@ def ours(args):
             ctxf.close()
         fg = {"value": world * n * args.steps / secs_f, "ms_per_step": secs_f / args.steps * 1e3,
               "pair_ms_per_launch": timf["pair"][0] / max(1, timf["pair"][1]),
-              "mean_list": stf["mean_fg"], "rebuilds": stf["n_builds"]}
+              "mean_list": stf["mean_fg"], "mean_list_pruned": stf["mean_fg_pruned"], "rebuilds": stf["n_builds"]}
     ctx_stats = st1
     ctx.close()
 
@@ -307,17 +317,33 @@ def ours(args):
     # one launch) as it runs on every step that needs no energy
     pair_ms = tim_pair["pair"][0] / max(1, tim_pair["pair"][1])
     n_h = ctx_stats["n_hybrid"]
-    entries = ctx_stats["mean_fg"] * n + ctx_stats["mean_cg"] * n_h
-    # 4 B index + 16 B gather per entry; per slot 16 B position, 4 B count, 4 B slot map, 16 B force
-    alg_bytes = entries * 20.0 + (n + n_h) * 40.0
+    prunes = ctx_stats["n_prunes"] - st0["n_prunes"]
+    full = ctx_stats["mean_fg"] * n + ctx_stats["mean_cg"] * n_h
+    if args.prune > 0 and prunes > 0:
+        # entries the pair kernel walked: the pruned lists of the passes in the
+        # timed region, except on pruning steps (a fraction p_prune of the
+        # launches), which walk the full lists and write the pruned ones
+        mean_fg = (ctx_stats["mean_fg_pruned"] * ctx_stats["n_prunes"] - st0["mean_fg_pruned"] * st0["n_prunes"]) / prunes
+        mean_cg = (ctx_stats["mean_cg_pruned"] * ctx_stats["n_prunes"] - st0["mean_cg_pruned"] * st0["n_prunes"]) / prunes
+        p_prune = prunes / args.steps
+    else:
+        mean_fg, mean_cg, p_prune = ctx_stats["mean_fg"], ctx_stats["mean_cg"], 0.0
+    walked = mean_fg * n + mean_cg * n_h
+    # 4 B index + 16 B gather per entry; per slot 16 B position, 4 B count, 4 B slot map, 16 B force;
+    # a pruning launch also writes 4 B per kept entry, 4 B per slot count and 16 B per atom reference
+    alg_plain = walked * 20.0 + (n + n_h) * 40.0
+    alg_prune = full * 20.0 + walked * 4.0 + (n + n_h) * 44.0 + n * 16.0
+    alg_bytes = (1.0 - p_prune) * alg_plain + p_prune * alg_prune
     achieved = alg_bytes / (pair_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(),
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(p_prune),
                 "peak_source": peak_kind + " (hbm_gbs, copy)", "kernel": "k_pair<float, forces only> (FG + CG lists)",
                 "alg_bytes_per_launch": alg_bytes, "ms_per_launch": pair_ms,
+                "pruning_launch_fraction": p_prune,
                 "launches_timed": tim_pair["pair"][1],
-                "how": "CUDA events around the pair launch on 1 step in 10 of the timed region"}
+                "how": "CUDA events around the pair launch on 1 step in 10 of the timed region; bytes are "
+                       "the mean over plain launches (pruned lists) and pruning launches (full lists)"}
     kernel_ms = {k: round(v[0] / max(1, v[1]), 5) for k, v in tim.items()}
     kernel_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in tim.values())), 4) for k, v in tim.items()}
 
@@ -345,7 +371,9 @@ def ours(args):
                                 "the steps by ~8 %, so the headline run times the pair kernel only)",
         "lists": {"mean_fg": ctx_stats["mean_fg"], "mean_cg": ctx_stats["mean_cg"],
                   "cap_fg": ctx_stats["cap_fg"], "cap_cg": ctx_stats["cap_cg"],
-                  "rebuilds_in_timed_region": ctx_stats["n_builds"] - st0["n_builds"]},
+                  "rebuilds_in_timed_region": ctx_stats["n_builds"] - st0["n_builds"],
+                  "prune_delta": ctx_stats["prune_delta"], "prunes_in_timed_region": prunes,
+                  "mean_fg_walked": mean_fg, "mean_cg_walked": mean_cg},
         "pair_launch": {"threads_per_atom": ctx_stats["pair_tpa"], "block": ctx_stats["pair_block"],
                         "chosen_by": "autotuner (first relres_step)"},
         "gpu_launches": ctx_stats["n_launches"] - st0["n_launches"],

@@ -164,6 +164,9 @@ typedef struct relres_stats {
   int has_cg;                    /* 1 if any hybrid pair has eps^CG > 0 */
   long long n_launches;          /* CUDA kernels this context has launched */
   int pair_tpa, pair_block;      /* forces-only pair kernel: threads per atom, block size */
+  double prune_delta;            /* pruning margin in Angstrom (0: pruning off) */
+  long long n_prunes;            /* pruning passes since create (each build is followed by one) */
+  double mean_fg_pruned, mean_cg_pruned;  /* mean pruned list length over all passes */
 } relres_stats;
 
 /* Kernel classes of relres_get_timings. */
@@ -175,7 +178,8 @@ enum relres_timing_class {
   RELRES_T_FINISH = 4,   /* force sum + bonded terms + kinetic energy */
   RELRES_T_THERMO = 5,   /* reductions + CSVR factor */
   RELRES_T_PAIR_EV = 6,  /* pair kernel on energy steps (forces + energy + virial) */
-  RELRES_T_NCLASS = 7
+  RELRES_T_PRUNE = 7,    /* pruning pass of both lists (relres_set_prune) */
+  RELRES_T_NCLASS = 8
 };
 
 /*
@@ -330,6 +334,34 @@ relres_status relres_backward(relres_ctx* ctx, const double* d_pos, const double
 relres_status relres_set_graphs(relres_ctx* ctx, int enable);
 
 /*
+ * Set the capacities of the FG and CG lists (entries per slot, rounded up to a
+ * multiple of 8) and rebuild the lists at the current positions; a capacity
+ * too small for them grows as on an overflow.  Later overflows inside
+ * relres_step roll the step block back and grow the lists automatically, so
+ * this only bounds the memory a caller is willing to start with.  Synchronous.
+ */
+relres_status relres_set_list_caps(relres_ctx* ctx, int cap_fg, int cap_cg);
+
+/*
+ * Dynamic pruning of the two lists (Section 2.6 keeps the lists; pruning is a
+ * property of this implementation).  The lists hold every pair within the
+ * interaction cutoff (r_s+ for the FG list, r_c+ for the CG list) + skin at
+ * the last build.  With delta > 0 a pruning pass copies, in list order, the
+ * entries whose current distance is below the cutoff + delta into a second
+ * pair of lists of the same capacity, and the pair kernels walk those.  A pass
+ * follows every build and runs again at the first step after an atom has
+ * moved more than delta/2 since the last pass.  The entries a pass drops
+ * contribute exactly zero, so forces, energies and trajectories are the same
+ * bits as without pruning when one thread walks each list (pair launch
+ * configurations 0-2 of relres_set_pair_config).  delta <= 0 turns pruning
+ * off (the pair kernels then walk the full lists and the second pair of lists
+ * is freed).  Default: delta = 0.5 A.  Rebuilds the lists at the current
+ * positions if they exist.  Synchronous.  Errors: RELRES_ERR_ARG (null
+ * context, non-finite delta).
+ */
+relres_status relres_set_prune(relres_ctx* ctx, double delta);
+
+/*
  * Batches of independent replicas (an implementation choice; the paper has no
  * counterpart).  relres_batch_create groups n_ctx contexts (each created,
  * given its topology and neighbour lists as usual; any sizes and boxes; not
@@ -348,15 +380,6 @@ relres_status relres_set_graphs(relres_ctx* ctx, int enable);
  * replica (relres_batch_last_error).  Per-class kernel timing is not recorded
  * in batches.
  */
-/*
- * Set the capacities of the FG and CG lists (entries per slot, rounded up to a
- * multiple of 8) and rebuild the lists at the current positions; a capacity
- * too small for them grows as on an overflow.  Later overflows inside
- * relres_step roll the step block back and grow the lists automatically, so
- * this only bounds the memory a caller is willing to start with.  Synchronous.
- */
-relres_status relres_set_list_caps(relres_ctx* ctx, int cap_fg, int cap_cg);
-
 typedef struct relres_batch relres_batch;
 relres_status relres_batch_create(relres_batch** out, relres_ctx* const* ctxs, int n_ctx, void* cuda_stream);
 relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, double* const* d_pos,

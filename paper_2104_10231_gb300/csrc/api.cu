@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -107,13 +108,28 @@ relres_status alloc_lists(relres_ctx* c) {
     return fail(c, RELRES_ERR_NOMEM, "neighbour list larger than 2^31 entries");
   CK(dalloc(&c->d_nbr_fg, size_t(c->cap_fg) * c->n));
   if (c->has_cg && c->n_h > 0) CK(dalloc(&c->d_nbr_cg, size_t(c->cap_cg) * c->n_h));
+  // pruned lists: same layout and capacity (a pruned list is never longer)
+  c->prune_on = c->prune_delta > 0.0;
+  if (c->prune_on) {
+    CK(dalloc(&c->d_nbr_fg_in, size_t(c->cap_fg) * c->n));
+    CK(dalloc(&c->d_cnt_fg_in, size_t(c->n)));
+    if (c->has_cg && c->n_h > 0) {
+      CK(dalloc(&c->d_nbr_cg_in, size_t(c->cap_cg) * c->n_h));
+      CK(dalloc(&c->d_cnt_cg_in, size_t(c->n_h)));
+    }
+  } else {
+    dfree(c->d_nbr_fg_in);
+    dfree(c->d_cnt_fg_in);
+    dfree(c->d_nbr_cg_in);
+    dfree(c->d_cnt_cg_in);
+  }
   return RELRES_OK;
 }
 
 // Rebuild both lists at the current fixed-point positions, growing capacity
 // until everything fits.
 relres_status host_rebuild(relres_ctx* c) {
-  CK(launch_flags_and(c, ~(unsigned)(F_REBUILD | F_OVERFLOW_FG | F_OVERFLOW_CG)));
+  CK(launch_flags_and(c, ~(unsigned)(F_REBUILD | F_PRUNE | F_OVERFLOW_FG | F_OVERFLOW_CG)));
   CK(launch_rebuild(c, nullptr));
   for (int attempt = 0; attempt < 4; ++attempt) {
     CK(launch_lists(c, nullptr));
@@ -129,6 +145,7 @@ relres_status host_rebuild(relres_ctx* c) {
       c->last_mean_cg = c->n_h ? double(h.tot_cg) / c->n_h : 0.0;
       c->have_lists = true;
       c->n_builds += 1;
+      CK(launch_prune(c, nullptr));  // pruned lists at the same positions
       return RELRES_OK;
     }
     if (of) c->cap_fg = round_cap(h.max_fg * 1.2 + 8, c->n);
@@ -194,6 +211,18 @@ static bool timed_now(const relres_ctx* c, int cls) {
     if (t_) CK(toc(c));                      \
   } while (0)
 
+// Lists valid at the positions already converted into d_xfx: a rebuild if an
+// atom moved more than skin/2 since the last build, else a pruning pass if an
+// atom moved more than delta/2 since the last one.
+relres_status refresh_lists(relres_ctx* c) {
+  if (c->h_state->flags & F_REBUILD) return host_rebuild(c);
+  if (c->h_state->flags & F_PRUNE) {
+    CK(launch_prune(c, nullptr));
+    CK(launch_flags_and(c, ~(unsigned)F_PRUNE));
+  }
+  return RELRES_OK;
+}
+
 // Forces at the positions already converted into d_xfx (F_tot, FP64 copy optional).
 relres_status forces_now(relres_ctx* c, int ev_mode, double* d_forces, double* d_energy,
                          double* d_virial) {
@@ -203,10 +232,8 @@ relres_status forces_now(relres_ctx* c, int ev_mode, double* d_forces, double* d
     CK(launch_flags_and(c, ~(unsigned)F_NONFINITE));
     return fail(c, RELRES_ERR_NONFINITE, "non-finite position");
   }
-  if (c->h_state->flags & F_REBUILD) {
-    s = host_rebuild(c);
-    if (s != RELRES_OK) return s;
-  }
+  s = refresh_lists(c);
+  if (s != RELRES_OK) return s;
   if (!c->tuned) {
     s = autotune_pairs(c);
     if (s != RELRES_OK) return s;
@@ -524,6 +551,7 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(&c->d_inc, std::max<size_t>(1, iall.size())));
   CK(dalloc(&c->d_xfx, 3 * size_t(n)));
   CK(dalloc(&c->d_ref, size_t(n)));
+  CK(dalloc(&c->d_ref_p, size_t(n)));
   CK(dalloc(&c->d_cell_fg, size_t(n)));
   CK(dalloc(&c->d_cell_cg, size_t(n)));
   CK(dalloc(&c->d_slot_fg, size_t(n)));
@@ -689,6 +717,23 @@ relres_status relres_set_list_caps(relres_ctx* c, int cap_fg, int cap_cg) {
   return RELRES_OK;
 }
 
+relres_status relres_set_prune(relres_ctx* c, double delta) {
+  if (!c || !std::isfinite(delta)) return RELRES_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  c->prune_delta = delta > 0.0 ? delta : 0.0;
+  if (!c->have_lists) {  // applied at the first build
+    c->prune_on = c->prune_delta > 0.0;
+    return RELRES_OK;
+  }
+  relres_status s = alloc_lists(c);
+  if (s != RELRES_OK) return s;
+  s = host_rebuild(c);  // both lists at the current positions
+  if (s != RELRES_OK) return s;
+  c->forces_valid = false;
+  CK(cudaStreamSynchronize(c->stream));
+  return RELRES_OK;
+}
+
 relres_status relres_set_pair_config(relres_ctx* c, int config) {
   if (!c || config < -1 || config >= kNPairConfigs) return RELRES_ERR_ARG;
   c->tune_mode = config;
@@ -707,20 +752,17 @@ static void drop_step_graph(relres_ctx* c) {
   c->sg = relres_ctx::StepGraph{};
 }
 
-// The conditional rebuild node of one step, added to the graph being captured
-// on c->stream; its body (binning + lists, ungated) is captured on a second
-// stream.
-static relres_status add_rebuild_node(relres_ctx* c) {
+// A conditional (IF) node added to the graph being captured on c->stream
+// after its current dependencies; `body` records the node's body on a second
+// stream (ungated launches).
+static relres_status add_conditional(relres_ctx* c, cudaGraphConditionalHandle h,
+                                     const std::function<cudaError_t()>& body) {
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
   CK(cudaStreamGetCaptureInfo(c->stream, &st, nullptr, &g, &deps, nullptr, &nd));
   if (st != cudaStreamCaptureStatusActive) return fail(c, RELRES_ERR_CUDA, "stream is not capturing");
-  cudaGraphConditionalHandle h;
-  CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-  CK(launch_decide(c, h));
-  CK(cudaStreamGetCaptureInfo(c->stream, &st, nullptr, &g, &deps, nullptr, &nd));
   std::vector<cudaGraphNode_t> dv(deps, deps + nd);
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
@@ -729,18 +771,58 @@ static relres_status add_rebuild_node(relres_ctx* c) {
   cp.conditional.size = 1;
   cudaGraphNode_t node;
   CK(cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
   const cudaStream_t main = c->stream;
-  CK(cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  CK(cudaStreamBeginCaptureToGraph(c->body_stream, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   c->stream = c->body_stream;
-  const cudaError_t e1 = launch_rebuild(c, c->d_open);
-  const cudaError_t e2 = e1 == cudaSuccess ? launch_lists(c, c->d_open) : e1;
+  const cudaError_t e1 = body();
   c->stream = main;
   cudaGraph_t out = nullptr;
-  const cudaError_t e3 = cudaStreamEndCapture(c->body_stream, &out);
+  const cudaError_t e2 = cudaStreamEndCapture(c->body_stream, &out);
+  CK(e1);
   CK(e2);
-  CK(e3);
   CK(cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return RELRES_OK;
+}
+
+// The conditional rebuild node of one step (binning + lists).  One one-thread
+// kernel sets its flag and, with a separate pruning pass (pruning on, several
+// threads per slot), the flag of the pruning node (*hp: a rebuild or the
+// pruning trigger fired), which record_pairs adds after it.
+static relres_status add_rebuild_node(relres_ctx* c, cudaGraphConditionalHandle* hp) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamGetCaptureInfo(c->stream, &st, nullptr, &g, nullptr, nullptr, nullptr));
+  if (st != cudaStreamCaptureStatusActive) return fail(c, RELRES_ERR_CUDA, "stream is not capturing");
+  cudaGraphConditionalHandle h;
+  *hp = 0;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  const bool separate = c->prune_on && !pairs_prune(c);
+  if (separate) CK(cudaGraphConditionalHandleCreate(hp, g, 0, cudaGraphCondAssignDefault));
+  CK(launch_decide(c, h, *hp, separate ? 1 : 0));
+  return add_conditional(c, h, [c]() {
+    const cudaError_t e = launch_rebuild(c, c->d_open);
+    return e == cudaSuccess ? launch_lists(c, c->d_open) : e;
+  });
+}
+
+// The pair evaluation of one step.  With pruning and one thread per slot the
+// pair kernel itself prunes on the steps that need it (it reads the device
+// flags); with several threads per slot a separate pruning pass runs first on
+// those steps (graph: a conditional node; stream: a launch gated on the flags).
+static relres_status record_pairs(relres_ctx* c, bool ev, bool graph, cudaGraphConditionalHandle hp) {
+  if (c->prune_on && !pairs_prune(c)) {
+    if (graph) {
+      const bool t_ = timed_now(c, RELRES_T_PRUNE);
+      if (t_) CK(tic(c, RELRES_T_PRUNE));
+      relres_status s = add_conditional(c, hp, [c]() { return launch_prune(c, c->d_open); });
+      if (s != RELRES_OK) return s;
+      if (t_) CK(toc(c));
+    } else {
+      TIMED(RELRES_T_PRUNE, launch_prune(c, &c->d_state->flags));
+    }
+  }
+  TIMED(ev ? RELRES_T_PAIR_EV : RELRES_T_PAIR, launch_pairs(c, ev));
   return RELRES_OK;
 }
 
@@ -757,19 +839,21 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
   for (int k = 0; k < blk; ++k) {
     c->cur_step = done + k;
     TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel));
+    // energy steps are known here: the device sets DevState::ev by the same rule
+    const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
+    cudaGraphConditionalHandle hp = 0;
     if (graph) {
       const bool t_ = timed_now(c, RELRES_T_REBUILD);
       if (t_) CK(tic(c, RELRES_T_REBUILD));
-      relres_status s = add_rebuild_node(c);
+      relres_status s = add_rebuild_node(c, &hp);
       if (s != RELRES_OK) return s;
       if (t_) CK(toc(c));
     } else {
       TIMED(RELRES_T_REBUILD, launch_rebuild(c, gate));
       TIMED(RELRES_T_LISTS, launch_lists(c, gate));
     }
-    // energy steps are known here: the device sets DevState::ev by the same rule
-    const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
-    TIMED(ev_step ? RELRES_T_PAIR_EV : RELRES_T_PAIR, launch_pairs(c, ev_step));
+    relres_status sp_ = record_pairs(c, ev_step, graph, hp);
+    if (sp_ != RELRES_OK) return sp_;
     TIMED(RELRES_T_FINISH, launch_finish(c, ev_step, nullptr, d_vel));
     TIMED(RELRES_T_THERMO, launch_thermo(c, sp, k));
   }
@@ -822,10 +906,11 @@ static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_v
     drop_step_graph(c);
     return s;
   }
-  // kernels: per step the rebuild body holds 6 (5 binning stages + lists) and
-  // the decide kernel 1 sits in the parent
+  // kernels: per step the rebuild body holds 6 (5 binning stages + lists),
+  // the pruning body 1, and the decide kernel sits in the parent
   g.k_body = 6;
-  g.k_parent = captured - g.k_body * blk;
+  g.k_prune = (c->prune_on && !pairs_prune(c)) ? 1 : 0;
+  g.k_parent = captured - (g.k_body + g.k_prune) * blk;
   g.valid = true;
   g.blk = blk;
   g.ev_phase = phase;
@@ -942,10 +1027,8 @@ relres_status relres_backward(relres_ctx* c, const double* d_pos, const double* 
     CK(launch_flags_and(c, ~(unsigned)F_NONFINITE));
     return fail(c, RELRES_ERR_NONFINITE, "non-finite position");
   }
-  if (c->h_state->flags & F_REBUILD) {
-    s = host_rebuild(c);
-    if (s != RELRES_OK) return s;
-  }
+  s = refresh_lists(c);
+  if (s != RELRES_OK) return s;
   c->forces_valid = false;
   // gradient buffers (allocated on first use)
   if (c->grad_n != c->n) {
@@ -1025,14 +1108,15 @@ static relres_status step_begin(relres_ctx* c, int n_steps, double dt_fs, double
 // overflow the state goes back to the block start with larger lists
 // (*retry = true); a non-finite force ends the call.
 static relres_status block_end(relres_ctx* c, double* d_pos, double* d_vel, double dt_fs, long long builds0,
-                               bool graph, int* retries, bool* retry) {
+                               long long prunes0, bool graph, int* retries, bool* retry) {
   *retry = false;
   relres_status s = read_state(c);
   if (s != RELRES_OK) return s;
   s = flush_timing(c);
   if (s != RELRES_OK) return s;
   if (graph) {
-    c->n_launches += c->sg.k_parent + c->sg.k_body * std::max(0LL, c->h_state->n_builds - builds0);
+    c->n_launches += c->sg.k_parent + c->sg.k_body * std::max(0LL, c->h_state->n_builds - builds0) +
+                     c->sg.k_prune * std::max(0LL, (long long)c->h_state->n_prunes - prunes0);
     if (c->timing)
       for (const relres_ctx::Mark& m : c->sg.marks) {
         float ms = 0.f;
@@ -1156,7 +1240,8 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
     c->timing = false;  // per-class timing is not recorded in batches
     s = record_block(c, sp[r], d_vel[r], blk, done, true);
     if (s != RELRES_OK) b->err = "replica " + std::to_string(r) + " (capture): " + c->err;
-    b->k_parent[r] = (c->n_launches - n0) - 6LL * blk;
+    const long long kpr = (c->prune_on && !pairs_prune(c)) ? 1 : 0;
+    b->k_parent[r] = (c->n_launches - n0) - (6LL + kpr) * blk;
     c->stream = own;
     c->timing = timing;
     c->n_launches = n0;
@@ -1236,8 +1321,11 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
   int done = 0, retries = 0;
   while (done < n_steps) {
     const int blk = std::min(kBlockSteps, n_steps - done);
-    std::vector<long long> builds0(nr);
-    for (int r = 0; r < nr; ++r) builds0[r] = b->ctx[r]->h_state->n_builds;
+    std::vector<long long> builds0(nr), prunes0(nr);
+    for (int r = 0; r < nr; ++r) {
+      builds0[r] = b->ctx[r]->h_state->n_builds;
+      prunes0[r] = (long long)b->ctx[r]->h_state->n_prunes;
+    }
     relres_status s = batch_graph(b, sp, d_vel, blk, done);
     if (s != RELRES_OK) return s;
     cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
@@ -1249,7 +1337,9 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
       relres_ctx* c = b->ctx[r];
       s = read_state(c);
       if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + c->err);
-      c->n_launches += b->k_parent[r] + 6LL * std::max(0LL, c->h_state->n_builds - builds0[r]);
+      const long long kpr = (c->prune_on && !pairs_prune(c)) ? 1 : 0;
+      c->n_launches += b->k_parent[r] + 6LL * std::max(0LL, c->h_state->n_builds - builds0[r]) +
+                       kpr * std::max(0LL, (long long)c->h_state->n_prunes - prunes0[r]);
       flags[r] = c->h_state->flags;
       if (flags[r] & F_BADCELL)
         return batch_fail(b, RELRES_ERR_CUDA, "replica " + std::to_string(r) + ": out-of-range cell index");
@@ -1311,7 +1401,7 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
   int done = 0, retries = 0;
   while (done < n_steps) {
     const int blk = std::min(kBlockSteps, n_steps - done);
-    const long long builds0 = c->h_state->n_builds;
+    const long long builds0 = c->h_state->n_builds, prunes0 = (long long)c->h_state->n_prunes;
     if (c->use_graphs) {
       s = step_graph(c, sp, d_vel, blk, done);
       if (s != RELRES_OK) return s;
@@ -1321,7 +1411,7 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
       if (s != RELRES_OK) return s;
     }
     bool retry = false;
-    s = block_end(c, d_pos, d_vel, dt_fs, builds0, c->use_graphs, &retries, &retry);
+    s = block_end(c, d_pos, d_vel, dt_fs, builds0, prunes0, c->use_graphs, &retries, &retry);
     if (s != RELRES_OK) return s;
     if (!retry) done += blk;
   }
@@ -1366,6 +1456,13 @@ relres_status relres_get_stats(relres_ctx* c, relres_stats* o) {
   o->n_steps = (long long)c->h_state->step;
   o->has_cg = c->has_cg ? 1 : 0;
   o->n_launches = c->n_launches;
+  o->prune_delta = c->prune_on ? c->prune_delta : 0.0;
+  o->n_prunes = (long long)c->h_state->n_prunes;
+  if (c->h_state->n_prunes > 0) {
+    const double np = double(c->h_state->n_prunes);
+    o->mean_fg_pruned = c->n ? double(c->h_state->tot_in_fg) / (np * c->n) : 0.0;
+    o->mean_cg_pruned = c->n_h ? double(c->h_state->tot_in_cg) / (np * c->n_h) : 0.0;
+  }
   return RELRES_OK;
 }
 
@@ -1446,6 +1543,7 @@ void relres_destroy(relres_ctx* c) {
   }
   dfree(c->d_xfx);
   dfree(c->d_ref);
+  dfree(c->d_ref_p);
   dfree(c->d_cell_fg);
   dfree(c->d_cell_cg);
   dfree(c->d_slot_fg);
@@ -1462,6 +1560,10 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_cnt_fg);
   dfree(c->d_nbr_cg);
   dfree(c->d_cnt_cg);
+  dfree(c->d_nbr_fg_in);
+  dfree(c->d_cnt_fg_in);
+  dfree(c->d_nbr_cg_in);
+  dfree(c->d_cnt_cg_in);
   dfree(c->d_f_fg);
   dfree(c->d_f_cg);
   dfree(c->d_f_tot);

@@ -56,10 +56,32 @@ __device__ __forceinline__ int cell_of(int h, int n) { return int(__umulhi(unsig
 
 // No kernel ever receives a null pointer: optional buffers come with an int
 // flag and a valid (possibly unused) pointer.  `gate` points at the device flag
-// word of a step (rebuild only when F_REBUILD is set) or at a word that always
-// has it set.
-__device__ __forceinline__ bool gate_closed(const unsigned* gate) {
-  return (*(volatile const unsigned*)gate & F_REBUILD) == 0u;
+// word of a step (rebuild only when F_REBUILD is set; pruning when F_REBUILD
+// or F_PRUNE is set) or at a word that always has F_REBUILD set.
+__device__ __forceinline__ bool gate_closed(const unsigned* gate, unsigned mask = F_REBUILD) {
+  return (*(volatile const unsigned*)gate & mask) == 0u;
+}
+
+// Pruning: append entry j to a slot's pruned list (chunked layout, slot
+// pointer out4 = list + slot as int4, k entries so far) if kept.  buf is a
+// shift register of the last four kept entries (oldest in x): once k reaches a
+// multiple of four it holds the chunk just completed, which is written as one
+// 16-byte store.  No branch depends on keep.
+__device__ __forceinline__ void keep_entry(bool keep, int j, int& k, int4& buf, int4* out4, int nslots) {
+  buf.x = keep ? buf.y : buf.x;
+  buf.y = keep ? buf.z : buf.y;
+  buf.z = keep ? buf.w : buf.z;
+  buf.w = keep ? j : buf.w;
+  k += keep ? 1 : 0;
+  if (keep && (k & 3) == 0) out4[size_t((k >> 2) - 1) * nslots] = buf;
+}
+// The last, partial chunk (k % 4 entries, the newest in buf.w).
+__device__ __forceinline__ void keep_tail(int k, const int4& buf, int4* out4, int nslots) {
+  const int r = k & 3;
+  if (r == 0) return;
+  const int4 t = r == 1 ? make_int4(buf.w, buf.w, buf.w, buf.w)
+                        : (r == 2 ? make_int4(buf.z, buf.w, buf.w, buf.w) : make_int4(buf.y, buf.z, buf.w, buf.w));
+  out4[size_t(k >> 2) * nslots] = t;
 }
 
 template <typename T>

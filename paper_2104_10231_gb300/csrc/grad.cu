@@ -282,8 +282,8 @@ static cudaError_t launch_grad_t(relres_ctx* c, const double* d_grad_forces, dou
     pfg = c->d_pos_fg64;
     pcg = c->d_pos_cg64;
   }
-  a.fg = GradWalk<R>{c->n, pfg, c->d_nbr_fg, c->d_cnt_fg, c->d_perm_fg, gfg, xfg};
-  a.cg = do_cg ? GradWalk<R>{c->n_h, pcg, c->d_nbr_cg, c->d_cnt_cg, c->d_perm_cg, gcg, xcg} : a.fg;
+  a.fg = GradWalk<R>{c->n, pfg, walk_nbr_fg(c), walk_cnt_fg(c), c->d_perm_fg, gfg, xfg};
+  a.cg = do_cg ? GradWalk<R>{c->n_h, pcg, walk_nbr_cg(c), walk_cnt_cg(c), c->d_perm_cg, gcg, xcg} : a.fg;
   // small systems: 64-thread blocks, so that the launch covers every SM
   const int bs = c->n < 200000 ? 64 : kThreads;
   const int nb_fg = (c->n + bs - 1) / bs;

@@ -91,10 +91,10 @@ __global__ void k_convert(int n, const double* __restrict__ pos, const int* __re
                           unsigned long long* __restrict__ xfx, BoxConsts b, int have_lists,
                           const int* rank_fg, const int* rank_cg, int with_cg, int4* pos_fg,
                           int4* pos_cg, int fp64, Pos64* pos_fg64, Pos64* pos_cg64, const int4* ref,
-                          float thr2, DevState* st) {
+                          float thr2, const int4* ref_p, float thr2_p, int prune, DevState* st) {
   const double il0 = b.inv_l0, il1 = b.inv_l1, il2 = b.inv_l2;
   const Sc3<float> s{b.s32_0, b.s32_1, b.s32_2};
-  bool rebuild = false, bad = false;
+  bool rebuild = false, reprune = false, bad = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
     bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
@@ -106,9 +106,11 @@ __global__ void k_convert(int n, const double* __restrict__ pos, const int* __re
       scatter_sorted(i, type[i], ux, uy, uz, rank_fg, rank_cg, with_cg, pos_fg, pos_cg, fp64, pos_fg64,
                      pos_cg64);
       rebuild |= moved_beyond(ref[i], ux, uy, uz, s, thr2);
+      if (prune) reprune |= moved_beyond(ref_p[i], ux, uy, uz, s, thr2_p);
     }
   }
   if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&st->flags, F_REBUILD);
+  if (__syncthreads_or(reprune) && threadIdx.x == 0) atomicOr(&st->flags, F_PRUNE);
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, F_NONFINITE);
 }
 
@@ -619,6 +621,9 @@ struct DriftArgs {
   Pos64* pos_cg64;
   const int4* ref;
   float thr2;
+  const int4* ref_p;  // positions at the last pruning pass (read if prune)
+  float thr2_p;
+  int prune;
   int thermo_every;
   DevState* st;
 };
@@ -628,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_drift(DriftArgs<R> a) {
   const double ca = a.st->a, cb = a.st->b;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     a.st->ev = a.thermo_every > 0 && ((a.st->local_step + 1) % a.thermo_every) == 0;
-  bool rebuild = false;
+  bool rebuild = false, reprune = false;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) {
     const int t = a.type[i];
@@ -648,8 +653,10 @@ __global__ void __launch_bounds__(kThreads) k_drift(DriftArgs<R> a) {
     scatter_sorted(i, t, x[0], x[1], x[2], a.rank_fg, a.rank_cg, a.with_cg, a.pos_fg, a.pos_cg, a.fp64,
                    a.pos_fg64, a.pos_cg64);
     rebuild = moved_beyond(a.ref[i], x[0], x[1], x[2], a.s32, a.thr2);
+    if (a.prune) reprune = moved_beyond(a.ref_p[i], x[0], x[1], x[2], a.s32, a.thr2_p);
   }
   if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&a.st->flags, F_REBUILD);
+  if (__syncthreads_or(reprune) && threadIdx.x == 0) atomicOr(&a.st->flags, F_PRUNE);
 }
 
 // ----------------------------------------------------------------- thermostat
@@ -741,6 +748,7 @@ __global__ void k_thermo(long long* acc, StepParams sp, DevState* st, const doub
     st->n_builds += 1;
     st->flags &= ~F_REBUILD;
   }
+  st->flags &= ~F_PRUNE;  // a pruning pass ran this step if it was set
 }
 
 // Energies and virial of relres_compute (one thread); clears the accumulators.
@@ -804,6 +812,12 @@ static float trigger_thr2(const relres_ctx* c) {
   return float(h * h);
 }
 
+// pruning trigger: half the pruning margin
+static float prune_thr2(const relres_ctx* c) {
+  const double h = 0.5 * c->prune_delta;
+  return float(h * h);
+}
+
 static Sc3<float> s32_of(const relres_ctx* c) {
   return Sc3<float>{float(c->box[0] / 4294967296.0), float(c->box[1] / 4294967296.0),
                     float(c->box[2] / 4294967296.0)};
@@ -822,7 +836,8 @@ cudaError_t launch_convert(relres_ctx* c, const double* d_pos) {
   k_convert<<<grid_for(c->n), kThreads, 0, c->stream>>>(
       c->n, d_pos, c->d_type, c->d_xfx, b, c->have_lists ? 1 : 0, c->d_rank_fg, c->d_rank_cg,
       (c->has_cg && c->n_h > 0) ? 1 : 0, c->d_pos_fg, c->d_pos_cg, c->fp64 ? 1 : 0, p64(c, c->d_pos_fg64),
-      p64(c, c->d_pos_cg64), c->d_ref, trigger_thr2(c), c->d_state);
+      p64(c, c->d_pos_cg64), c->d_ref, trigger_thr2(c), c->prune_on ? c->d_ref_p : c->d_ref, prune_thr2(c),
+      c->prune_on ? 1 : 0, c->d_state);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
@@ -985,6 +1000,9 @@ static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d
                  p64(c, c->d_pos_cg64),
                  c->d_ref,
                  trigger_thr2(c),
+                 c->prune_on ? c->d_ref_p : c->d_ref,
+                 prune_thr2(c),
+                 c->prune_on ? 1 : 0,
                  sp.thermo_every,
                  c->d_state};
   k_drift<R><<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(a);

@@ -17,6 +17,8 @@
 // positions, ranks, reference positions for the displacement trigger) ->
 // k_list (FG and CG lists in one launch).  Every kernel can be gated on the
 // device rebuild flag, so the whole sequence can sit inside a CUDA graph step.
+// The pair kernels walk pruned copies of the lists (k_prune below, or the pair
+// kernel's own pruning walk).
 #include "common.cuh"
 
 namespace relres {
@@ -522,13 +524,133 @@ cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
 }
 
 // One thread: open the rebuild node of this step of a CUDA graph iff the
-// displacement trigger fired (F_REBUILD is set by the drift kernel).
-__global__ void k_decide(const DevState* st, cudaGraphConditionalHandle h) {
-  cudaGraphSetConditional(h, (st->flags & F_REBUILD) ? 1u : 0u);
+// displacement trigger fired (F_REBUILD is set by the drift kernel), and
+// (with_prune) the pruning node iff either trigger fired.
+__global__ void k_decide(const DevState* st, cudaGraphConditionalHandle h, cudaGraphConditionalHandle hp,
+                         int with_prune) {
+  const unsigned f = st->flags;
+  cudaGraphSetConditional(h, (f & F_REBUILD) ? 1u : 0u);
+  if (with_prune) cudaGraphSetConditional(hp, (f & (F_REBUILD | F_PRUNE)) ? 1u : 0u);
 }
 
-cudaError_t launch_decide(relres_ctx* c, cudaGraphConditionalHandle h) {
-  k_decide<<<1, 1, 0, c->stream>>>(c->d_state, h);
+cudaError_t launch_decide(relres_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle hp,
+                          int with_prune) {
+  k_decide<<<1, 1, 0, c->stream>>>(c->d_state, h, hp, with_prune);
+  RELRES_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+// ---- dynamic pruning (two-level lists).  The lists above hold every pair
+// within the interaction cutoff + skin at the last build and stay valid until
+// an atom has moved skin/2.  A pruning pass keeps, in list order, the entries
+// whose current distance is below the interaction cutoff + delta; that list
+// holds every interacting pair until an atom has moved delta/2 since the pass
+// (two atoms then close in by at most delta), when the drift kernel sets
+// F_PRUNE and the next step prunes again.  Since the kept entries keep their
+// order and a dropped entry contributes exactly zero, the pair sums are
+// bit-identical to those over the full lists (one thread per slot).
+
+struct PruneList {
+  int nslots;
+  const int4* pos;  // sorted hi32 positions
+  const int* nbr;   // full list (chunked layout)
+  const int* cnt;
+  int* nbr_in;      // pruned list, same layout and capacity
+  int* cnt_in;
+  float rp2;        // (interaction cutoff + delta + slack)^2
+  unsigned long long* total;
+};
+
+struct PruneArgs {
+  int nblk_cg;  // blocks [0, nblk_cg) prune the CG list, the rest the FG list
+  PruneList fg, cg;
+  float sx, sy, sz;
+  const int* perm_fg;
+  int4* ref_p;  // positions of this pass, caller order (written by the FG blocks)
+  DevState* st;
+};
+
+constexpr int kPruneThreads = 256;
+
+__device__ __forceinline__ int prune_slot(const PruneList& L, int s, float sx, float sy, float sz) {
+  const int4 pi = L.pos[s];
+  const int m = L.cnt[s];
+  const int nch = (m + 3) >> 2;
+  const int4* nb4 = reinterpret_cast<const int4*>(L.nbr) + s;
+  int4* out4 = reinterpret_cast<int4*>(L.nbr_in) + s;
+  int k = 0;
+  int4 buf = make_int4(s, s, s, s);
+  int4 jj = nch > 0 ? __ldcs(nb4) : buf;
+  for (int ch = 0; ch < nch; ++ch) {
+    int4 jn = jj;
+    if (ch + 1 < nch) jn = __ldcs(nb4 + size_t(ch + 1) * L.nslots);
+    const int rem = m - 4 * ch;  // >= 1
+    const int j[4] = {jj.x, rem > 1 ? jj.y : s, rem > 2 ? jj.z : s, rem > 3 ? jj.w : s};
+    int4 p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = __ldg(L.pos + j[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float dx = dfix32(pi.x, p[q].x, sx), dy = dfix32(pi.y, p[q].y, sy), dz = dfix32(pi.z, p[q].z, sz);
+      keep_entry((q == 0 || rem > q) && dx * dx + dy * dy + dz * dz < L.rp2, j[q], k, buf, out4, L.nslots);
+    }
+    jj = jn;
+  }
+  keep_tail(k, buf, out4, L.nslots);
+  L.cnt_in[s] = k;
+  return k;
+}
+
+__global__ void __launch_bounds__(kPruneThreads) k_prune(const unsigned* gate, PruneArgs a) {
+  if (gate_closed(gate, F_REBUILD | F_PRUNE)) return;
+  const bool is_cg = int(blockIdx.x) < a.nblk_cg;
+  const int blk = is_cg ? blockIdx.x : blockIdx.x - a.nblk_cg;
+  const int s = blk * kPruneThreads + threadIdx.x;
+  unsigned long long kept = 0ull;
+  if (is_cg) {
+    if (s < a.cg.nslots) kept = prune_slot(a.cg, s, a.sx, a.sy, a.sz);
+  } else if (s < a.fg.nslots) {
+    kept = prune_slot(a.fg, s, a.sx, a.sy, a.sz);
+    a.ref_p[a.perm_fg[s]] = a.fg.pos[s];
+  }
+  __shared__ unsigned long long sh[kPruneThreads / 32];
+  kept = warp_sum(kept);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = kept;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0ull;
+    for (int w = 0; w < kPruneThreads / 32; ++w) t += sh[w];
+    atomicAdd(is_cg ? a.cg.total : a.fg.total, t);
+    if (blockIdx.x == 0) atomicAdd(&a.st->n_prunes, 1ull);
+  }
+}
+
+cudaError_t launch_prune(relres_ctx* c, const unsigned* gate) {
+  if (!c->prune_on) return cudaSuccess;
+  if (gate == nullptr) gate = c->d_open;
+  const float s0 = float(c->box[0] / 4294967296.0), s1 = float(c->box[1] / 4294967296.0),
+              s2 = float(c->box[2] / 4294967296.0);
+  DevState* st = c->d_state;
+  const double rf = c->rlist_fg_cut + c->prune_delta + kPruneSlack;
+  PruneArgs a;
+  a.fg = PruneList{c->n, c->d_pos_fg, c->d_nbr_fg, c->d_cnt_fg, c->d_nbr_fg_in, c->d_cnt_fg_in,
+                   float(rf * rf), &st->tot_in_fg};
+  a.cg = a.fg;  // stand-in when there is no CG list (no CG blocks are launched)
+  a.nblk_cg = 0;
+  if (c->has_cg && c->n_h > 0) {
+    const double rc = c->rlist_cg_cut + c->prune_delta + kPruneSlack;
+    a.cg = PruneList{c->n_h, c->d_pos_cg, c->d_nbr_cg, c->d_cnt_cg, c->d_nbr_cg_in, c->d_cnt_cg_in,
+                     float(rc * rc), &st->tot_in_cg};
+    a.nblk_cg = (c->n_h + kPruneThreads - 1) / kPruneThreads;
+  }
+  a.sx = s0;
+  a.sy = s1;
+  a.sz = s2;
+  a.perm_fg = c->d_perm_fg;
+  a.ref_p = c->d_ref_p;
+  a.st = st;
+  const int nb = a.nblk_cg + (c->n + kPruneThreads - 1) / kPruneThreads;
+  k_prune<<<nb, kPruneThreads, 0, c->stream>>>(gate, a);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }

@@ -264,11 +264,18 @@ template <typename R>
 struct ListWalk {
   int nslots;
   const typename PosOf<R>::T* pos;
-  const int* nbr;
+  const int* nbr;  // the list walked (pruned when pruning is on)
   const int* cnt;
   const int* perm;
   ForceOut<R>* f_out;
   long long* acc;  // kNQ accumulators of this list (energy, six virial components)
+  // pruning launches (PRN): walk the full list and write the pruned one
+  const int* nbr_full;
+  const int* cnt_full;
+  int* nbr_in;
+  int* cnt_in;
+  R rp2;  // (interaction cutoff + delta + slack)^2
+  unsigned long long* tot_in;
 };
 
 template <typename R>
@@ -280,6 +287,10 @@ struct PairLaunch {
   int nt;
   R sx, sy, sz;
   float sxl, syl, szl;  // FP32 path: lo parts of L / 2^32 (float-float energies)
+  const unsigned* gate;  // device flag word of the step
+  int prune_on;          // prune on this launch if F_REBUILD or F_PRUNE is set (TPA = 1 only)
+  int4* ref_p;  // PRN: positions of this pruning pass, caller order (FG walk)
+  DevState* st;
 };
 
 struct SmemTabs {
@@ -299,10 +310,12 @@ struct Acc {
   ff eff = ff{0.f, 0.f};  // FP32 path: per-thread energy in float-float
 };
 
+// One list entry; returns its squared distance (past every cutoff for a
+// padding entry), which a pruning launch compares with the pruning radius.
 template <typename R, bool CG, bool EV>
-__device__ __forceinline__ void entry(const typename PosOf<R>::T& pi, const typename PosOf<R>::T& pj,
-                                      bool valid, int row0, const SmemTabs& S, const PairLaunch<R>& a,
-                                      Acc<R>& A) {
+__device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typename PosOf<R>::T& pj,
+                                   bool valid, int row0, const SmemTabs& S, const PairLaunch<R>& a,
+                                   Acc<R>& A) {
   R dx, dy, dz;
   delta(pi, pj, a.sx, a.sy, a.sz, dx, dy, dz);
   const int row = row0 + ptype(pj);
@@ -333,8 +346,9 @@ __device__ __forceinline__ void entry(const typename PosOf<R>::T& pi, const type
                                  : fg_energy_ff(S.fge[row], S.fgr[row].a.x, r2e));
       }
     }
+    return r2;
   } else {
-    if (!valid) return;
+    if (!valid) return R(1e300);
     const R r2 = dx * dx + dy * dy + dz * dz;
     const PairTab<R>& T = static_cast<const PairTab<R>*>(S.tab)[row];
     R fr, ep;
@@ -353,26 +367,40 @@ __device__ __forceinline__ void entry(const typename PosOf<R>::T& pi, const type
         A.w[5] += fr * dy * dz;
       }
     }
+    return r2;
   }
+}
+
+__device__ __forceinline__ int4 ref_of(const int4& p) { return p; }
+__device__ __forceinline__ int4 ref_of(const Pos64& p) {
+  return make_int4(int(p.x >> 32), int(p.y >> 32), int(p.z >> 32), int(p.t));
 }
 
 // One slot's walk over its list, four entries per iteration.  TPA lanes share
 // one slot (threads per atom, chosen by the autotuner): lane q of the slot
 // takes chunks q, q + TPA, ... and the partial forces are summed with warp
 // shuffles.  Energy steps use TPA = 1.
-template <typename R, bool CG, bool EV, int TPA>
+// PRN (pruning launches, TPA = 1): the slot walks its full list, and every
+// entry within the pruning radius is appended, in list order, to its pruned
+// list; the forces are the same bits as a walk of the pruned list (a dropped
+// entry adds exactly zero).
+template <typename R, bool CG, bool EV, int TPA, bool PRN>
 __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTabs& S,
                                      const PairLaunch<R>& a) {
+  static_assert(!PRN || TPA == 1, "pruning launches use one thread per slot");
   const int t = blk * blockDim.x + threadIdx.x;
   const int s = t / TPA;
   const int q = t % TPA;
   Acc<R> A;
+  int kept = 0;
   if (s < L.nslots) {
     const auto pi = L.pos[s];
     const int row0 = ptype(pi) * a.nt;
-    const int m = L.cnt[s];
+    const int m = PRN ? L.cnt_full[s] : L.cnt[s];
     const int nch = (m + 3) >> 2;
-    const int4* nb4 = reinterpret_cast<const int4*>(L.nbr) + s;
+    const int4* nb4 = reinterpret_cast<const int4*>(PRN ? L.nbr_full : L.nbr) + s;
+    int4* out4 = reinterpret_cast<int4*>(L.nbr_in) + s;
+    int4 buf = make_int4(s, s, s, s);
     int4 jj = make_int4(s, s, s, s);
     if (q < nch) jj = __ldcs(nb4 + size_t(q) * L.nslots);
     for (int ch = q; ch < nch; ch += TPA) {
@@ -384,11 +412,31 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
       const auto p1 = load_pos(L.pos, j1);
       const auto p2 = load_pos(L.pos, j2);
       const auto p3 = load_pos(L.pos, j3);
-      entry<R, CG, EV>(pi, p0, true, row0, S, a, A);
-      entry<R, CG, EV>(pi, p1, rem > 1, row0, S, a, A);
-      entry<R, CG, EV>(pi, p2, rem > 2, row0, S, a, A);
-      entry<R, CG, EV>(pi, p3, rem > 3, row0, S, a, A);
+      const R r0 = entry<R, CG, EV>(pi, p0, true, row0, S, a, A);
+      const R r1 = entry<R, CG, EV>(pi, p1, rem > 1, row0, S, a, A);
+      const R r2 = entry<R, CG, EV>(pi, p2, rem > 2, row0, S, a, A);
+      const R r3 = entry<R, CG, EV>(pi, p3, rem > 3, row0, S, a, A);
+      if (PRN) {
+        keep_entry(r0 < L.rp2, jj.x, kept, buf, out4, L.nslots);
+        keep_entry(r1 < L.rp2, j1, kept, buf, out4, L.nslots);
+        keep_entry(r2 < L.rp2, j2, kept, buf, out4, L.nslots);
+        keep_entry(r3 < L.rp2, j3, kept, buf, out4, L.nslots);
+      }
       jj = jn;
+    }
+    if (PRN) {
+      keep_tail(kept, buf, out4, L.nslots);
+      L.cnt_in[s] = kept;
+      if (!CG) a.ref_p[L.perm[s]] = ref_of(pi);
+    }
+  }
+  if (PRN) {
+    unsigned long long v[1] = {(unsigned long long)kept};
+    __shared__ unsigned long long sh_k[1024 / 32];
+    block_sum<unsigned long long, 1>(v, sh_k);
+    if (threadIdx.x == 0) {
+      atomicAdd(L.tot_in, v[0]);
+      if (blockIdx.x == 0) atomicAdd(&a.st->n_prunes, 1ull);
     }
   }
   if (TPA > 1) {  // every lane of the warp takes part (TPA divides 32)
@@ -416,8 +464,18 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
   }
 }
 
+// Forces-only FP32 launches are held to 64 registers a thread (the occupancy
+// of the walk without pruning); the pruning walk lives in the same kernel.
+template <typename R, bool EV>
+constexpr int pair_min_blocks(int bs) {
+  return (std::is_same<R, float>::value && !EV) ? 65536 / (64 * bs) : 1;
+}
+
+// One launch per step: with pruning on (one thread per slot) the kernel reads
+// the device flags and, if a rebuild or the pruning trigger fired this step,
+// walks the full lists and writes the pruned ones as it goes.
 template <typename R, bool EV, int TPA, int BS>
-__global__ void __launch_bounds__(BS) k_pair(PairLaunch<R> a) {
+__global__ void __launch_bounds__(BS, pair_min_blocks<R, EV>(BS)) k_pair(PairLaunch<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrow = a.nt * a.nt;
   size_t off = 0;
@@ -449,10 +507,21 @@ __global__ void __launch_bounds__(BS) k_pair(PairLaunch<R> a) {
     S.tab = tab;
   }
   __syncthreads();
-  if (int(blockIdx.x) < a.nblk_cg)
-    walk<R, true, EV, TPA>(a.cg, blockIdx.x, S, a);
+  const bool cg = int(blockIdx.x) < a.nblk_cg;
+  const int blk = cg ? blockIdx.x : blockIdx.x - a.nblk_cg;
+  if constexpr (TPA == 1) {
+    if (a.prune_on && (*(volatile const unsigned*)a.gate & (F_REBUILD | F_PRUNE)) != 0u) {
+      if (cg)
+        walk<R, true, EV, 1, true>(a.cg, blk, S, a);
+      else
+        walk<R, false, EV, 1, true>(a.fg, blk, S, a);
+      return;
+    }
+  }
+  if (cg)
+    walk<R, true, EV, TPA, false>(a.cg, blk, S, a);
   else
-    walk<R, false, EV, TPA>(a.fg, blockIdx.x - a.nblk_cg, S, a);
+    walk<R, false, EV, TPA, false>(a.fg, blk, S, a);
 }
 
 template <typename R>
@@ -478,6 +547,9 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   a.nt = c->n_types;
   a.tab = static_cast<const PairTab<R>*>(c->d_tab);
   a.tabd = static_cast<const PairTab<double>*>(c->d_tabd);
+  a.gate = &c->d_state->flags;
+  a.ref_p = c->d_ref_p;
+  a.st = c->d_state;
   const typename PosOf<R>::T* pfg;
   const typename PosOf<R>::T* pcg;
   if constexpr (std::is_same<R, float>::value) {
@@ -489,12 +561,21 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   }
   const bool do_fg = (which & 1) != 0;
   const bool do_cg = (which & 2) && c->has_cg && c->n_h > 0;
-  a.fg = ListWalk<R>{c->n, pfg, c->d_nbr_fg, c->d_cnt_fg, c->d_perm_fg,
-                     static_cast<ForceOut<R>*>(c->d_f_fg), c->d_acc + kAccFg};
+  const R rf = R(c->rlist_fg_cut + c->prune_delta + kPruneSlack);
+  a.fg = ListWalk<R>{c->n, pfg, walk_nbr_fg(c), walk_cnt_fg(c), c->d_perm_fg,
+                     static_cast<ForceOut<R>*>(c->d_f_fg), c->d_acc + kAccFg,
+                     c->d_nbr_fg, c->d_cnt_fg, c->d_nbr_fg_in, c->d_cnt_fg_in, rf * rf,
+                     &c->d_state->tot_in_fg};
   // without a CG list the CG walk is never entered; its pointers are stand-ins
-  a.cg = do_cg ? ListWalk<R>{c->n_h, pcg, c->d_nbr_cg, c->d_cnt_cg, c->d_perm_cg,
-                             static_cast<ForceOut<R>*>(c->d_f_cg), c->d_acc + kAccCg}
-               : a.fg;
+  if (do_cg) {
+    const R rc = R(c->rlist_cg_cut + c->prune_delta + kPruneSlack);
+    a.cg = ListWalk<R>{c->n_h, pcg, walk_nbr_cg(c), walk_cnt_cg(c), c->d_perm_cg,
+                       static_cast<ForceOut<R>*>(c->d_f_cg), c->d_acc + kAccCg,
+                       c->d_nbr_cg, c->d_cnt_cg, c->d_nbr_cg_in, c->d_cnt_cg_in, rc * rc,
+                       &c->d_state->tot_in_cg};
+  } else {
+    a.cg = a.fg;
+  }
   const size_t smem = pair_smem<R>(c->n_types, ev);
   // energy steps and FP64: one thread per slot, 256 per block; forces-only
   // FP32: the autotuned (threads per slot, block size)
@@ -503,6 +584,7 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
     tpa = kPairConfigs[c->pair_cfg].tpa;
     bs = kPairConfigs[c->pair_cfg].bs;
   }
+  a.prune_on = (c->prune_on && tpa == 1) ? 1 : 0;
   const int per = bs / tpa;  // slots per block
   const int nb_fg = do_fg ? (c->n + per - 1) / per : 0;
   const int nb_cg = do_cg ? (c->n_h + per - 1) / per : 0;
@@ -533,6 +615,10 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   }
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
+}
+
+bool pairs_prune(const relres_ctx* c) {
+  return c->prune_on && (c->fp64 || kPairConfigs[c->pair_cfg].tpa == 1);
 }
 
 cudaError_t launch_pairs(relres_ctx* c, bool ev, int which) {

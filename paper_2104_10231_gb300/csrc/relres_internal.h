@@ -82,6 +82,7 @@ enum : unsigned {
   F_NONFINITE = 8u,     // a non-finite force
   F_DIRTY = 16u,        // incoming positions differ from the cached state
   F_BADCELL = 32u,      // a computed cell index was out of range (access skipped)
+  F_PRUNE = 64u,        // an atom moved more than delta/2 since the last pruning pass
 };
 
 struct DevState {
@@ -94,6 +95,8 @@ struct DevState {
   long long local_step;     // steps done in the current relres_step call
   long long n_builds;
   unsigned long long tot_fg, tot_cg;  // list entries at the last build
+  unsigned long long n_prunes;        // pruning passes (each rebuild is followed by one)
+  unsigned long long tot_in_fg, tot_in_cg;  // pruned-list entries summed over all passes
   int thermo_row;
   int pad;
 };
@@ -107,6 +110,8 @@ constexpr int kAccFg = 0, kAccCg = kNQ, kAccKe = 2 * kNQ, kAccEb = 2 * kNQ + 1, 
 constexpr int kBlockSteps = 100;  // steps between host status checks in relres_step
 constexpr int kSegAtoms = 256;       // atoms per segment (one block of the fused force sum)
 constexpr size_t kSegSmemMax = 48 * 1024;  // shared memory of a segment's term slots
+constexpr double kPruneDelta = 0.5;   // default margin of the pruned lists (Angstrom)
+constexpr double kPruneSlack = 1e-3;  // added to the pruning radius: covers FP32 rounding of distances
 
 // Launch configurations of the forces-only FP32 pair kernel: threads per slot
 // (lanes that share one atom's list) and block size.  Index 0 is the default;
@@ -210,6 +215,7 @@ struct relres_ctx {
   // positions and sorting
   unsigned long long* d_xfx = nullptr;  // [n*3] 64-bit fixed point, caller order
   int4* d_ref = nullptr;                // [n] hi32 positions at the last build
+  int4* d_ref_p = nullptr;              // [n] hi32 positions at the last pruning pass
   int* d_cell_fg = nullptr;
   int* d_cell_cg = nullptr;
   int* d_slot_fg = nullptr;             // arrival rank of the atom inside its cell
@@ -231,6 +237,15 @@ struct relres_ctx {
   int* d_cnt_cg = nullptr;  // [n_h]
   int last_max_fg = 0, last_max_cg = 0;
   double last_mean_fg = 0, last_mean_cg = 0;
+  // pruned lists (dynamic pruning): the entries of the lists above whose
+  // distance was below the interaction cutoff + prune_delta at the last
+  // pruning pass, same layout and capacity; the pair kernels walk these
+  double prune_delta = relres::kPruneDelta;  // <= 0: no pruning (pair kernels walk the lists above)
+  bool prune_on = false;                     // prune_delta > 0 and the inner lists are allocated
+  int* d_nbr_fg_in = nullptr;
+  int* d_cnt_fg_in = nullptr;
+  int* d_nbr_cg_in = nullptr;
+  int* d_cnt_cg_in = nullptr;
 
   // forces (caller order): float4 per atom (FP32) or double[3] per atom (FP64)
   void* d_f_fg = nullptr;
@@ -302,6 +317,7 @@ struct relres_ctx {
     std::vector<cudaEvent_t> events;  // owned by the graph
     long long k_parent = 0;           // kernels per launch outside the rebuild bodies
     long long k_body = 0;             // kernels per executed rebuild body
+    long long k_prune = 0;            // kernels per executed pruning body (separate pruning pass)
   } sg;
   cudaStream_t cap_stream = nullptr;   // capture of the step graph
   cudaStream_t body_stream = nullptr;  // capture of the conditional rebuild bodies
@@ -324,16 +340,27 @@ cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, doubl
 
 // neighbour lists; gate: device flag word (rebuild only if F_REBUILD set) or null
 cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate);
-// sets the conditional of a graph's rebuild node from the device flag word
-cudaError_t launch_decide(relres_ctx* c, cudaGraphConditionalHandle h);
+// sets the conditionals of a graph's rebuild node (F_REBUILD) and, with a
+// separate pruning pass (with_prune), of its pruning node (F_REBUILD or
+// F_PRUNE) from the device flag word
+cudaError_t launch_decide(relres_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle hp,
+                          int with_prune);
 cudaError_t launch_lists(relres_ctx* c, const unsigned* gate);
+// pruning pass: inner lists from the full ones at the current positions
+// (gate: runs if F_REBUILD or F_PRUNE is set)
+cudaError_t launch_prune(relres_ctx* c, const unsigned* gate);
 
 // Forces.  ev: this evaluation also adds energies and virial to the
 // accumulators (d_acc).  The pair kernel covers both lists in one launch
 // (which: 1 = FG list only, 2 = CG list only, 3 = both).  launch_finish runs
 // the bonded-term kernel and the per-atom force sum; with d_vel it also adds
 // the kinetic energy of u + c F.
+// With pruning on and one thread per slot, a launch that finds F_REBUILD or
+// F_PRUNE set walks the full lists and writes the pruned ones as it goes.
 cudaError_t launch_pairs(relres_ctx* c, bool ev, int which = 3);
+// whether this context's pair launches prune (pruning on, one thread per
+// slot); otherwise a separate pruning pass precedes them when it is due
+bool pairs_prune(const relres_ctx* c);
 cudaError_t launch_finish(relres_ctx* c, bool ev, double* d_forces_out, const double* d_vel);
 cudaError_t launch_reduce_out(relres_ctx* c, double* d_energy, double* d_virial);
 // backward pass of the pair interaction (grad.cu): per-type-pair totals into
@@ -347,5 +374,11 @@ cudaError_t launch_csvr_draws(relres_ctx* c, const StepParams& sp, int count);
 cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp, int k);
 cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev);
 cudaError_t launch_flags_and(relres_ctx* c, unsigned keep);
+
+// the lists the pair kernels walk: the pruned ones when pruning is on
+inline const int* walk_nbr_fg(const relres_ctx* c) { return c->prune_on ? c->d_nbr_fg_in : c->d_nbr_fg; }
+inline const int* walk_cnt_fg(const relres_ctx* c) { return c->prune_on ? c->d_cnt_fg_in : c->d_cnt_fg; }
+inline const int* walk_nbr_cg(const relres_ctx* c) { return c->prune_on ? c->d_nbr_cg_in : c->d_nbr_cg; }
+inline const int* walk_cnt_cg(const relres_ctx* c) { return c->prune_on ? c->d_cnt_cg_in : c->d_cnt_cg; }
 
 }  // namespace relres

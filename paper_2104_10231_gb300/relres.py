@@ -36,9 +36,9 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
             "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled",
-            "relres_set_list_caps"]
+            "relres_set_list_caps", "relres_set_prune"]
 RELRES_STATIC_MAX_ATOMS = 16384
-TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev"]
+TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev", "prune"]
 
 
 class RelresError(RuntimeError):
@@ -77,7 +77,9 @@ class relres_stats(C.Structure):
                 ("list_radius_fg", C.c_double), ("list_radius_cg", C.c_double),
                 ("skin_cg", C.c_double), ("grid_fg", C.c_int * 3), ("grid_cg", C.c_int * 3),
                 ("n_builds", C.c_longlong), ("n_steps", C.c_longlong), ("has_cg", C.c_int),
-                ("n_launches", C.c_longlong), ("pair_tpa", C.c_int), ("pair_block", C.c_int)]
+                ("n_launches", C.c_longlong), ("pair_tpa", C.c_int), ("pair_block", C.c_int),
+                ("prune_delta", C.c_double), ("n_prunes", C.c_longlong), ("mean_fg_pruned", C.c_double),
+                ("mean_cg_pruned", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -112,6 +114,7 @@ def load():
     L.relres_set_timing.argtypes = [vp, C.c_int]
     L.relres_set_timing_sampled.argtypes = [vp, C.c_uint, C.c_int]
     L.relres_set_list_caps.argtypes = [vp, C.c_int, C.c_int]
+    L.relres_set_prune.argtypes = [vp, C.c_double]
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
     L.relres_set_pair_config.argtypes = [vp, C.c_int]
@@ -410,6 +413,10 @@ class Context:
 
     def set_list_caps(self, cap_fg, cap_cg):
         _check(load().relres_set_list_caps(self.ctx, int(cap_fg), int(cap_cg)), self.ctx)
+
+    def set_prune(self, delta):
+        """Pruning margin of the lists in Angstrom (<= 0: no pruning)."""
+        _check(load().relres_set_prune(self.ctx, float(delta)), self.ctx)
 
     def set_pair_config(self, config):
         relres_set_pair_config(self.ctx, config)

@@ -1,0 +1,109 @@
+"""Precision of the two arithmetic modes, result by result, against the FP64
+oracle, and their NVE energy drift (|E(end) - E(start)| and the standard
+deviation of the total energy, both over the mean kinetic energy).
+
+FP64 mode: every term in FP64 from 64-bit fixed-point coordinates.  FP32 mode:
+pair forces in FP32 from exact integer coordinate differences with FP64 block
+sums, float-float pair energies on energy steps, float-float bond lengths, FP32
+angles and dihedrals, FP64 velocities and 64-bit fixed-point positions.  The
+test prints the table and holds each entry to its bound."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import core as O
+from paper_2104_10231_gb300 import relres as R
+from paper_2104_10231_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2104_10231_gb300.build import build_library
+
+    build_library()
+    R.load()
+    return T
+
+
+def _dev(torch, a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _errors(torch, s, precision):
+    ctx = R.Context(R.params_for(s, precision), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    ctx.build_neighbors(p, s.box)
+    f = torch.empty_like(p)
+    e = torch.zeros(4, dtype=torch.float64, device="cuda")
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.compute(p, f, e, w)
+    torch.cuda.synchronize()
+    ctx.close()
+    f, e, w = f.cpu().numpy(), e.cpu().numpy(), w.cpu().numpy()
+    tab = O.table_for(s)
+    fr, er, wr = O.pair_forces(s.pos, s.box, s.types, tab, s.n_types, s.excl)
+    fb, eb = O.bonded(s.pos, s.box, s.topo)
+    fr = fr + fb
+    rms = math.sqrt((fr * fr).sum(1).mean())
+    return {"force": float(np.abs(f - fr).max() / rms),
+            "E_pair": abs(e[0] + e[1] - er) / abs(er),
+            "E_bonded": abs(e[2] - eb.sum()) / max(1.0, abs(eb.sum())),
+            "virial": float(np.abs(w - wr).max() / np.abs(wr[:3]).max())}
+
+
+def _nve_drift(torch, s, precision, n_steps, dt):
+    ctx = R.Context(R.params_for(s, precision), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    v = _dev(torch, s.vel)
+    ctx.build_neighbors(p, s.box)
+    th = torch.zeros((n_steps // 10, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    ctx.step(n_steps, dt, p, v, thermo_every=10, d_thermo=th)
+    t1.record()
+    torch.cuda.synchronize()
+    ctx.close()
+    t = th.cpu().numpy()
+    etot = t[:, 0] + t[:, 1] + t[:, 2] + t[:, 3]
+    tail = etot[10:]  # after the lattice start has relaxed
+    return {"drift": abs(tail[-1] - tail[0]) / t[:, 3].mean(),
+            "fluct": float(tail.std() / t[:, 3].mean()),
+            "ms_per_step": t0.elapsed_time(t1) / n_steps}
+
+
+DRIFT_RUNS = (("NVE propane 216 mol, 1000 x 1 fs", lambda: S.propane(), 1000, 1.0),
+              ("NVE neopentane 4000 mol, 2000 x 2 fs", lambda: S.neopentane(n_mol=4000, seed=9), 2000, 2.0))
+
+
+def test_precision_modes_per_result(torch):
+    systems = [S.propane(), S.neopentane(n_mol=500, seed=7), S.block_copolymer(n_chain=20)]
+    table = {}
+    for prec, name in ((R.RELRES_PREC_FP64, "FP64"), (R.RELRES_PREC_FP32, "FP32")):
+        for s in systems:
+            table[(name, s.name)] = _errors(torch, s, prec)
+        for label, make, n, dt in DRIFT_RUNS:
+            table[(name, label)] = _nve_drift(torch, make(), prec, n, dt)
+    for (mode, sysname), errs in table.items():
+        print(f"{mode:5s} {sysname:40s} " + "  ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    for (mode, sysname), errs in table.items():
+        if "drift" in errs:
+            assert errs["drift"] < 5e-3 and errs["fluct"] < 5e-3, (mode, sysname, errs)
+            continue
+        if mode == "FP64":
+            assert max(errs.values()) < 1e-10, (sysname, errs)
+        else:
+            assert errs["force"] < 1e-5 and errs["E_pair"] < 1e-7 and errs["E_bonded"] < 1e-7, (sysname, errs)
+            assert errs["virial"] < 1e-4, (sysname, errs)
+    # FP32 arithmetic costs no energy conservation: the drift and the
+    # fluctuation of the total energy come from the time step, not the precision
+    for label, _, _, _ in DRIFT_RUNS:
+        d64, d32 = table[("FP64", label)], table[("FP32", label)]
+        assert d32["drift"] < 3.0 * d64["drift"] + 2e-4, (label, d32, d64)
+        assert d32["fluct"] < 1.5 * d64["fluct"] + 1e-5, (label, d32, d64)
