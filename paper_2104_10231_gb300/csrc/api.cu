@@ -487,7 +487,10 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
       seg_slots = std::max(seg_slots, 2 * (b1 - b0) + 3 * (g1 - g0) + 4 * (d1 - d0));
       a0 = a1;
     }
-    if (size_t(std::max(1, seg_slots)) * 24 > kSegSmemMax) seg_ok = false;
+    // shared memory of the segment kernels: term slots (float4 or 3 doubles)
+    // plus the segment's positions in the drift kernel
+    const size_t slot_bytes = c->fp64 ? 24 : 16;
+    if (size_t(std::max(1, seg_slots)) * slot_bytes + 24 * size_t(kSegAtoms) > kSegSmemMax) seg_ok = false;
   }
   std::vector<double> bp(2 * size_t(std::max(1, t->n_bond_types)), 0.0),
       ap(2 * size_t(std::max(1, t->n_angle_types)), 0.0), dp(4 * size_t(std::max(1, t->n_dihedral_types)), 0.0);
@@ -571,6 +574,7 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_f_fg), fb));
   CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_f_cg), fb));
   CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_f_tot), fb));
+  CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_f_bond), fb));
   CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_snap_f), fb));
   CK(dalloc(&c->d_snap_x, 3 * size_t(n)));
   CK(dalloc(&c->d_snap_v, 3 * size_t(n)));
@@ -838,9 +842,9 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
   CK(launch_csvr_draws(c, sp, blk));
   for (int k = 0; k < blk; ++k) {
     c->cur_step = done + k;
-    TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel));
     // energy steps are known here: the device sets DevState::ev by the same rule
     const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
+    TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel, ev_step));
     cudaGraphConditionalHandle hp = 0;
     if (graph) {
       const bool t_ = timed_now(c, RELRES_T_REBUILD);
@@ -854,8 +858,12 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
     }
     relres_status sp_ = record_pairs(c, ev_step, graph, hp);
     if (sp_ != RELRES_OK) return sp_;
-    TIMED(RELRES_T_FINISH, launch_finish(c, ev_step, nullptr, d_vel));
-    TIMED(RELRES_T_THERMO, launch_thermo(c, sp, k));
+    if (step_segments(c)) {  // bonded forces came with the drift; thermostat in k_sum's last block
+      TIMED(RELRES_T_FINISH, launch_end_of_step(c, sp, k, ev_step, d_vel));
+    } else {
+      TIMED(RELRES_T_FINISH, launch_finish(c, ev_step, nullptr, d_vel));
+      TIMED(RELRES_T_THERMO, launch_thermo(c, sp, k));
+    }
   }
   c->cur_step = 0;
   return RELRES_OK;
@@ -1567,6 +1575,7 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_f_fg);
   dfree(c->d_f_cg);
   dfree(c->d_f_tot);
+  dfree(c->d_f_bond);
   dfree(c->d_tf);
   dfree(c->d_seg);
   dfree(c->d_basis);

@@ -147,6 +147,18 @@ struct BondedArgs {
   const float* angle_fpar;  // FP32 path: k, theta0, cos theta0 (hi, lo), sin theta0 (hi, lo), 0, 0
 };
 
+// Where the bonded terms read 64-bit fixed-point positions: the global array
+// (caller order), or a segment's copy in shared memory (atoms a0, a0 + 1, ...).
+struct GPos {
+  const unsigned long long* x;
+  __device__ __forceinline__ unsigned long long operator()(int i, int q) const { return x[3 * i + q]; }
+};
+struct SPos {
+  const unsigned long long* s;
+  int a0;
+  __device__ __forceinline__ unsigned long long operator()(int i, int q) const { return s[3 * (i - a0) + q]; }
+};
+
 // exact 64-bit fixed-point difference a - b, scaled to Angstrom
 __device__ __forceinline__ ff ff_fixed_diff(unsigned long long a, unsigned long long b, ff scale) {
   const long long d = (long long)(a - b);
@@ -154,24 +166,27 @@ __device__ __forceinline__ ff ff_fixed_diff(unsigned long long a, unsigned long 
   const float lo = __ll2float_rn(d - __float2ll_rn(hi));
   return ff_mul(ff_quick(hi, lo), scale);
 }
-__device__ __forceinline__ void ff_vec(const unsigned long long* x, int a, int b, ff s0, ff s1, ff s2, ff v[3]) {
-  v[0] = ff_fixed_diff(x[3 * a], x[3 * b], s0);
-  v[1] = ff_fixed_diff(x[3 * a + 1], x[3 * b + 1], s1);
-  v[2] = ff_fixed_diff(x[3 * a + 2], x[3 * b + 2], s2);
+template <class X>
+__device__ __forceinline__ void ff_vec(const X& x, int a, int b, ff s0, ff s1, ff s2, ff v[3]) {
+  v[0] = ff_fixed_diff(x(a, 0), x(b, 0), s0);
+  v[1] = ff_fixed_diff(x(a, 1), x(b, 1), s1);
+  v[2] = ff_fixed_diff(x(a, 2), x(b, 2), s2);
 }
 __device__ __forceinline__ ff ff_dot(const ff a[3], const ff b[3]) {
   return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
 }
 
-__device__ __forceinline__ void dvec(const unsigned long long* x, int a, int b, Sc3<float> s, float d[3]) {
-  d[0] = dfix32(hi32(x[3 * a]), hi32(x[3 * b]), s.s0);
-  d[1] = dfix32(hi32(x[3 * a + 1]), hi32(x[3 * b + 1]), s.s1);
-  d[2] = dfix32(hi32(x[3 * a + 2]), hi32(x[3 * b + 2]), s.s2);
+template <class X>
+__device__ __forceinline__ void dvec(const X& x, int a, int b, Sc3<float> s, float d[3]) {
+  d[0] = dfix32(hi32(x(a, 0)), hi32(x(b, 0)), s.s0);
+  d[1] = dfix32(hi32(x(a, 1)), hi32(x(b, 1)), s.s1);
+  d[2] = dfix32(hi32(x(a, 2)), hi32(x(b, 2)), s.s2);
 }
-__device__ __forceinline__ void dvec(const unsigned long long* x, int a, int b, Sc3<double> s, double d[3]) {
-  d[0] = dfix64((long long)x[3 * a], (long long)x[3 * b], s.s0);
-  d[1] = dfix64((long long)x[3 * a + 1], (long long)x[3 * b + 1], s.s1);
-  d[2] = dfix64((long long)x[3 * a + 2], (long long)x[3 * b + 2], s.s2);
+template <class X>
+__device__ __forceinline__ void dvec(const X& x, int a, int b, Sc3<double> s, double d[3]) {
+  d[0] = dfix64((long long)x(a, 0), (long long)x(b, 0), s.s0);
+  d[1] = dfix64((long long)x(a, 1), (long long)x(b, 1), s.s1);
+  d[2] = dfix64((long long)x(a, 2), (long long)x(b, 2), s.s2);
 }
 
 template <typename R>
@@ -190,8 +205,8 @@ __device__ __forceinline__ void cross3(const R a[3], const R b[3], R c[3]) {
 // scratch slot; the finish kernel gathers each atom's slots (no atomics).
 // Return value: the term energy.
 
-template <typename R>
-__device__ __forceinline__ R bond_forces(const BondedArgs& B, const unsigned long long* xfx, Sc3<R> sc,
+template <typename R, class X>
+__device__ __forceinline__ R bond_forces(const BondedArgs& B, const X& xfx, Sc3<R> sc,
                                          int t, R f[2][3]) {
   const int4 bd = B.bonds[t];
   R d[3];
@@ -207,8 +222,8 @@ __device__ __forceinline__ R bond_forces(const BondedArgs& B, const unsigned lon
   return k * (r - r0) * (r - r0);
 }
 
-template <typename R>
-__device__ __forceinline__ R angle_forces(const BondedArgs& B, const unsigned long long* xfx, Sc3<R> sc,
+template <typename R, class X>
+__device__ __forceinline__ R angle_forces(const BondedArgs& B, const X& xfx, Sc3<R> sc,
                                           int t, R f[3][3]) {
   const int4 an = B.angles[t];
   R r1[3], r2[3];
@@ -231,8 +246,8 @@ __device__ __forceinline__ R angle_forces(const BondedArgs& B, const unsigned lo
   return k * (th - t0) * (th - t0);
 }
 
-template <typename R>
-__device__ __forceinline__ R dihedral_forces(const BondedArgs& B, const unsigned long long* xfx, Sc3<R> sc,
+template <typename R, class X>
+__device__ __forceinline__ R dihedral_forces(const BondedArgs& B, const X& xfx, Sc3<R> sc,
                                              int t, R f[4][3]) {
   const int4 dh = B.dihs[t];
   const double* K = B.dih_par + 4 * B.dih_type[t];
@@ -267,7 +282,8 @@ __device__ __forceinline__ R dihedral_forces(const BondedArgs& B, const unsigned
 // FP32 bond.  Bonds sit near their minimum with a stiff spring, so the force
 // 2k (r - r0) needs r - r0 far below FP32 resolution: r is formed in
 // float-float arithmetic from the exact 64-bit fixed-point difference.
-__device__ __forceinline__ float bond_forces_ff(const BondedArgs& B, const unsigned long long* xfx, ff q0,
+template <class X>
+__device__ __forceinline__ float bond_forces_ff(const BondedArgs& B, const X& xfx, ff q0,
                                                 ff q1, ff q2, int t, float f[2][3]) {
   const int4 bd = B.bonds[t];
   const float* P = B.bond_fpar + 4 * bd.z;
@@ -288,7 +304,8 @@ __device__ __forceinline__ float bond_forces_ff(const BondedArgs& B, const unsig
 // FP32 angle through theta - theta0 = atan2(|a x b| cos t0 - (a.b) sin t0,
 // (a.b) cos t0 + |a x b| sin t0): no acos and no loss near theta0, so the
 // angle error stays near 1e-7 rad (force error ~2K 1e-7 / r).
-__device__ __forceinline__ float angle_forces_f32(const BondedArgs& B, const unsigned long long* xfx,
+template <class X>
+__device__ __forceinline__ float angle_forces_f32(const BondedArgs& B, const X& xfx,
                                                   Sc3<float> sc, int t, float f[3][3]) {
   const int4 an = B.angles[t];
   const float* P = B.angle_fpar + 8 * an.w;
@@ -369,22 +386,22 @@ __global__ void __launch_bounds__(kThreads) k_bonded(BondedKArgs<R> a) {
   if (t < a.nb) {
     R f[2][3];
     if constexpr (std::is_same<R, float>::value)
-      e = bond_forces_ff(a.B, a.xfx, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, t, f);
+      e = bond_forces_ff(a.B, GPos{a.xfx}, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, t, f);
     else
-      e = bond_forces<R>(a.B, a.xfx, sc, t, f);
+      e = bond_forces<R>(a.B, GPos{a.xfx}, sc, t, f);
     save_slots<2, R>(a.tf, 2 * size_t(t), f);
   } else if (t < a.nb + a.na) {
     const int u = t - a.nb;
     R f[3][3];
     if constexpr (std::is_same<R, float>::value)
-      e = angle_forces_f32(a.B, a.xfx, sc, u, f);
+      e = angle_forces_f32(a.B, GPos{a.xfx}, sc, u, f);
     else
-      e = angle_forces<R>(a.B, a.xfx, sc, u, f);
+      e = angle_forces<R>(a.B, GPos{a.xfx}, sc, u, f);
     save_slots<3, R>(a.tf, 2 * size_t(a.nb) + 3 * size_t(u), f);
   } else if (t < a.nb + a.na + a.nd) {
     const int u = t - a.nb - a.na;
     R f[4][3];
-    e = dihedral_forces<R>(a.B, a.xfx, sc, u, f);
+    e = dihedral_forces<R>(a.B, GPos{a.xfx}, sc, u, f);
     save_slots<4, R>(a.tf, 2 * size_t(a.nb) + 3 * size_t(a.na) + 4 * size_t(u), f);
   }
   if (EV) {
@@ -520,22 +537,22 @@ __global__ void __launch_bounds__(kThreads) k_finish_seg(SegArgs<R> a) {
     if (q < nb) {
       R f[2][3];
       if constexpr (std::is_same<R, float>::value)
-        e += bond_forces_ff(a.B, a.xfx, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, b0 + q, f);
+        e += bond_forces_ff(a.B, GPos{a.xfx}, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, b0 + q, f);
       else
-        e += bond_forces<R>(a.B, a.xfx, sc, b0 + q, f);
+        e += bond_forces<R>(a.B, GPos{a.xfx}, sc, b0 + q, f);
       save_slots<2, R>(slot, 2 * size_t(q), f);
     } else if (q < nb + na) {
       const int u = q - nb;
       R f[3][3];
       if constexpr (std::is_same<R, float>::value)
-        e += angle_forces_f32(a.B, a.xfx, sc, g0 + u, f);
+        e += angle_forces_f32(a.B, GPos{a.xfx}, sc, g0 + u, f);
       else
-        e += angle_forces<R>(a.B, a.xfx, sc, g0 + u, f);
+        e += angle_forces<R>(a.B, GPos{a.xfx}, sc, g0 + u, f);
       save_slots<3, R>(slot, base_a + 3 * size_t(u), f);
     } else {
       const int u = q - nb - na;
       R f[4][3];
-      e += dihedral_forces<R>(a.B, a.xfx, sc, d0 + u, f);
+      e += dihedral_forces<R>(a.B, GPos{a.xfx}, sc, d0 + u, f);
       save_slots<4, R>(slot, base_d + 4 * size_t(u), f);
     }
   }
@@ -628,6 +645,30 @@ struct DriftArgs {
   DevState* st;
 };
 
+// One atom of the drift: u <- a u + b c F, x <- x + dt u, the sorted copies
+// of x, and the two displacement triggers.  Returns the new position in x.
+template <typename R>
+__device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, double ca, double cb,
+                                           unsigned long long x[3], bool& rebuild, bool& reprune) {
+  const int t = a.type[i];
+  R f[3];
+  load_force(a.f_tot, i, f);
+  const R bc = R(cb * a.cdt[t]);
+  const double dts[3] = {a.dts0, a.dts1, a.dts2};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    // the kick increment in the force's precision, accumulated in FP64
+    const double u = fma(ca, a.vel[3 * i + q], double(bc * f[q]));
+    a.vel[3 * i + q] = u;
+    x[q] = a.xfx[3 * i + q] + (unsigned long long)__double2ll_rn(u * dts[q]);
+    a.xfx[3 * i + q] = x[q];
+  }
+  scatter_sorted(i, t, x[0], x[1], x[2], a.rank_fg, a.rank_cg, a.with_cg, a.pos_fg, a.pos_cg, a.fp64,
+                 a.pos_fg64, a.pos_cg64);
+  rebuild = moved_beyond(a.ref[i], x[0], x[1], x[2], a.s32, a.thr2);
+  if (a.prune) reprune = moved_beyond(a.ref_p[i], x[0], x[1], x[2], a.s32, a.thr2_p);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_drift(DriftArgs<R> a) {
   const double ca = a.st->a, cb = a.st->b;
@@ -636,27 +677,106 @@ __global__ void __launch_bounds__(kThreads) k_drift(DriftArgs<R> a) {
   bool rebuild = false, reprune = false;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) {
-    const int t = a.type[i];
-    R f[3];
-    load_force(a.f_tot, i, f);
-    const R bc = R(cb * a.cdt[t]);
-    const double dts[3] = {a.dts0, a.dts1, a.dts2};
     unsigned long long x[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      // the kick increment in the force's precision, accumulated in FP64
-      const double u = fma(ca, a.vel[3 * i + q], double(bc * f[q]));
-      a.vel[3 * i + q] = u;
-      x[q] = a.xfx[3 * i + q] + (unsigned long long)__double2ll_rn(u * dts[q]);
-      a.xfx[3 * i + q] = x[q];
-    }
-    scatter_sorted(i, t, x[0], x[1], x[2], a.rank_fg, a.rank_cg, a.with_cg, a.pos_fg, a.pos_cg, a.fp64,
-                   a.pos_fg64, a.pos_cg64);
-    rebuild = moved_beyond(a.ref[i], x[0], x[1], x[2], a.s32, a.thr2);
-    if (a.prune) reprune = moved_beyond(a.ref_p[i], x[0], x[1], x[2], a.s32, a.thr2_p);
+    drift_atom(a, i, ca, cb, x, rebuild, reprune);
   }
   if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&a.st->flags, F_REBUILD);
   if (__syncthreads_or(reprune) && threadIdx.x == 0) atomicOr(&a.st->flags, F_PRUNE);
+}
+
+// ---- drift + bonded terms, one block per segment of whole molecules: the
+// block drifts its atoms (same arithmetic as k_drift), keeps their new
+// positions in shared memory, evaluates the segment's bonded terms from there
+// into shared-memory slots (same arithmetic as k_finish_seg) and writes each
+// atom's bonded force (its slots summed in incident-term order).  The bonded
+// forces of the new positions are thus ready before the pair kernel runs, and
+// k_sum only adds the three parts.
+
+template <typename R>
+struct DriftSegArgs {
+  DriftArgs<R> d;
+  const int* seg;  // [n_seg][8]: atoms [a0, a1), bonds [b0, b1), angles, dihedrals
+  BondedArgs B;
+  Sc3<R> sc;
+  float q0h, q0l, q1h, q1l, q2h, q2l;
+  const int* inc_off;
+  const int* inc;
+  ForceT<R>* f_bond;  // caller order
+  long long* acc;
+};
+
+template <typename R, bool EV>
+__global__ void __launch_bounds__(kThreads) k_drift_seg(DriftSegArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* sx = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSegAtoms][3]
+  ForceT<R>* slot = reinterpret_cast<ForceT<R>*>(smem_raw + sizeof(unsigned long long) * 3 * kSegAtoms);
+  const int* g = a.seg + 8 * blockIdx.x;
+  const int a0 = g[0], a1 = g[1], b0 = g[2], b1 = g[3], g0 = g[4], g1 = g[5], d0 = g[6], d1 = g[7];
+  const double ca = a.d.st->a, cb = a.d.st->b;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    a.d.st->ev = a.d.thermo_every > 0 && ((a.d.st->local_step + 1) % a.d.thermo_every) == 0;
+  bool rebuild = false, reprune = false;
+  const int i = a0 + threadIdx.x;
+  if (i < a1) {
+    unsigned long long x[3];
+    drift_atom(a.d, i, ca, cb, x, rebuild, reprune);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sx[3 * threadIdx.x + q] = x[q];
+  }
+  if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&a.d.st->flags, F_REBUILD);
+  if (__syncthreads_or(reprune) && threadIdx.x == 0) atomicOr(&a.d.st->flags, F_PRUNE);
+  // bonded terms of the segment from the new positions
+  const SPos xs{sx, a0};
+  const int nb = b1 - b0, na = g1 - g0, nd = d1 - d0;
+  const int base_a = 2 * nb, base_d = base_a + 3 * na;
+  const Sc3<R> sc = a.sc;
+  R e = R(0);
+  for (int q = threadIdx.x; q < nb + na + nd; q += blockDim.x) {
+    if (q < nb) {
+      R f[2][3];
+      if constexpr (std::is_same<R, float>::value)
+        e += bond_forces_ff(a.B, xs, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, b0 + q, f);
+      else
+        e += bond_forces<R>(a.B, xs, sc, b0 + q, f);
+      save_slots<2, R>(slot, 2 * size_t(q), f);
+    } else if (q < nb + na) {
+      const int u = q - nb;
+      R f[3][3];
+      if constexpr (std::is_same<R, float>::value)
+        e += angle_forces_f32(a.B, xs, sc, g0 + u, f);
+      else
+        e += angle_forces<R>(a.B, xs, sc, g0 + u, f);
+      save_slots<3, R>(slot, base_a + 3 * size_t(u), f);
+    } else {
+      const int u = q - nb - na;
+      R f[4][3];
+      e += dihedral_forces<R>(a.B, xs, sc, d0 + u, f);
+      save_slots<4, R>(slot, base_d + 4 * size_t(u), f);
+    }
+  }
+  if (EV) {
+    double v[1] = {double(e)};
+    __shared__ double sh_e[kThreads / 32];
+    block_sum<double, 1>(v, sh_e);
+    if (threadIdx.x == 0) acc_add(a.acc + kAccEb, v[0]);
+  }
+  __syncthreads();
+  if (i < a1) {
+    R f[3] = {R(0), R(0), R(0)};
+    const int k1 = a.inc_off[i + 1];
+    for (int k = a.inc_off[i]; k < k1; ++k) {
+      const int item = a.inc[k];
+      const int kind = (item >> 30) & 3, role = (item >> 28) & 3, term = item & 0x0fffffff;
+      const int s = kind == 0 ? 2 * (term - b0) + role
+                              : (kind == 1 ? base_a + 3 * (term - g0) + role : base_d + 4 * (term - d0) + role);
+      R h[3];
+      load_force(slot, s, h);
+      f[0] += h[0];
+      f[1] += h[1];
+      f[2] += h[2];
+    }
+    save_force(a.f_bond, i, f);
+  }
 }
 
 // ----------------------------------------------------------------- thermostat
@@ -720,8 +840,9 @@ __global__ void k_csvr_draws(double n_f, unsigned long long seed, int count, con
 
 // End of a step (one thread): thermostat factor from the kinetic energy,
 // thermo row on energy steps, counters, and the accumulators cleared for the
-// next step.  `draw` points at this step's (r1, s).
-__global__ void k_thermo(long long* acc, StepParams sp, DevState* st, const double* draw) {
+// next step.  `draw` points at this step's (r1, s).  The accumulators are read
+// through volatile loads (other blocks of the calling kernel added to them).
+__device__ void end_of_step(volatile long long* acc, const StepParams& sp, DevState* st, const double* draw) {
   const bool ev = st->ev != 0;
   const double ke = double(acc[kAccKe]) / kFix;
   double alpha = 1.0;
@@ -749,6 +870,91 @@ __global__ void k_thermo(long long* acc, StepParams sp, DevState* st, const doub
     st->flags &= ~F_REBUILD;
   }
   st->flags &= ~F_PRUNE;  // a pruning pass ran this step if it was set
+}
+
+__global__ void k_thermo(long long* acc, StepParams sp, DevState* st, const double* draw) {
+  end_of_step(acc, sp, st, draw);
+}
+
+// ---- end of a step with bonded forces from k_drift_seg: per atom the total
+// force F = F_FG + F_CG + F_bonded and the kinetic energy of u + c F; the last
+// block to finish (a ticket counter after a memory fence) runs the thermostat
+// and the step bookkeeping of k_thermo, so the step needs no separate launch.
+
+template <typename R>
+struct SumArgs {
+  int n;
+  const ForceT<R>* f_fg;
+  const ForceT<R>* f_cg;
+  int with_cg;
+  const ForceT<R>* f_bond;
+  const int* type;
+  int hyb_mask;
+  const double* vel;
+  const double* cdt;
+  const double* mass;
+  ForceT<R>* f_tot;
+  long long* acc;
+  DevState* st;
+  StepParams sp;
+  const double* draw;
+};
+
+template <typename R>
+__device__ __forceinline__ R sum_atom(const SumArgs<R>& a, int i, bool& bad) {
+  const int t = a.type[i];
+  R f[3], h[3];
+  load_force(a.f_fg, i, f);
+  if (a.with_cg && ((a.hyb_mask >> t) & 1)) {
+    load_force(a.f_cg, i, h);
+    f[0] += h[0];
+    f[1] += h[1];
+    f[2] += h[2];
+  }
+  load_force(a.f_bond, i, h);
+  f[0] += h[0];
+  f[1] += h[1];
+  f[2] += h[2];
+  bad |= !(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]));
+  save_force(a.f_tot, i, f);
+  const R c = R(a.cdt[t]);
+  R v2 = R(0);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const R v = R(a.vel[3 * i + q]) + c * f[q];
+    v2 += v * v;
+  }
+  return R(0.5 * a.mass[t] * kMvv2e) * v2;
+}
+
+// grid-stride (a few blocks per SM), one kinetic-energy atomic and one
+// ticket per block
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_sum(SumArgs<R> a) {
+  double ke = 0.0;
+  bool bad = false;
+  const int stride = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < a.n; i += 2 * stride) {  // two atoms in flight
+    const R k0 = sum_atom(a, i, bad);
+    const R k1 = sum_atom(a, i + stride, bad);
+    ke += double(k0) + double(k1);
+  }
+  if (i < a.n) ke += double(sum_atom(a, i, bad));
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&a.st->flags, F_NONFINITE);
+  double v[1] = {ke};
+  __shared__ double sh_k[kThreads / 32];
+  block_sum<double, 1>(v, sh_k);
+  if (threadIdx.x == 0) {
+    acc_add(a.acc + kAccKe, v[0]);
+    __threadfence();
+    const unsigned ticket = atomicAdd(&a.st->done_blocks, 1u);
+    if (ticket == gridDim.x - 1) {
+      __threadfence();
+      a.st->done_blocks = 0u;
+      end_of_step(a.acc, a.sp, a.st, a.draw);
+    }
+  }
 }
 
 // Energies and virial of relres_compute (one thread); clears the accumulators.
@@ -977,41 +1183,102 @@ cudaError_t launch_csvr_draws(relres_ctx* c, const StepParams& sp, int count) {
 }
 
 template <typename R>
-static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d_vel) {
+static DriftArgs<R> drift_args(relres_ctx* c, const StepParams& sp, double* d_vel) {
   const bool cg = c->has_cg && c->n_h > 0;
   const BoxConsts b = box_consts(c, sp.dt);
-  DriftArgs<R> a{c->n,
-                 d_vel,
-                 c->d_xfx,
-                 static_cast<const ForceT<R>*>(c->d_f_tot),
-                 c->d_type,
-                 c->d_cdt,
-                 b.dts0,
-                 b.dts1,
-                 b.dts2,
-                 s32_of(c),
-                 c->d_rank_fg,
-                 c->d_rank_cg,
-                 cg ? 1 : 0,
-                 c->d_pos_fg,
-                 c->d_pos_cg,
-                 c->fp64 ? 1 : 0,
-                 p64(c, c->d_pos_fg64),
-                 p64(c, c->d_pos_cg64),
-                 c->d_ref,
-                 trigger_thr2(c),
-                 c->prune_on ? c->d_ref_p : c->d_ref,
-                 prune_thr2(c),
-                 c->prune_on ? 1 : 0,
-                 sp.thermo_every,
-                 c->d_state};
-  k_drift<R><<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(a);
+  return DriftArgs<R>{c->n,
+                      d_vel,
+                      c->d_xfx,
+                      static_cast<const ForceT<R>*>(c->d_f_tot),
+                      c->d_type,
+                      c->d_cdt,
+                      b.dts0,
+                      b.dts1,
+                      b.dts2,
+                      s32_of(c),
+                      c->d_rank_fg,
+                      c->d_rank_cg,
+                      cg ? 1 : 0,
+                      c->d_pos_fg,
+                      c->d_pos_cg,
+                      c->fp64 ? 1 : 0,
+                      p64(c, c->d_pos_fg64),
+                      p64(c, c->d_pos_cg64),
+                      c->d_ref,
+                      trigger_thr2(c),
+                      c->prune_on ? c->d_ref_p : c->d_ref,
+                      prune_thr2(c),
+                      c->prune_on ? 1 : 0,
+                      sp.thermo_every,
+                      c->d_state};
+}
+
+template <typename R>
+static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev) {
+  if (step_segments(c)) {
+    const double k = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
+    DriftSegArgs<R> a{};
+    a.d = drift_args<R>(c, sp, d_vel);
+    a.seg = c->d_seg;
+    a.B = bonded_args(c);
+    a.sc = Sc3<R>{R(c->box[0] / k), R(c->box[1] / k), R(c->box[2] / k)};
+    ff_split(c->box[0] / 18446744073709551616.0, &a.q0h, &a.q0l);
+    ff_split(c->box[1] / 18446744073709551616.0, &a.q1h, &a.q1l);
+    ff_split(c->box[2] / 18446744073709551616.0, &a.q2h, &a.q2l);
+    a.inc_off = c->d_inc_off;
+    a.inc = c->d_inc;
+    a.f_bond = static_cast<ForceT<R>*>(c->d_f_bond);
+    a.acc = c->d_acc;
+    const size_t smem = sizeof(unsigned long long) * 3 * kSegAtoms +
+                        size_t(c->seg_slots) * (std::is_same<R, float>::value ? 16 : 24);
+    if (ev)
+      k_drift_seg<R, true><<<c->n_seg, kThreads, smem, c->stream>>>(a);
+    else
+      k_drift_seg<R, false><<<c->n_seg, kThreads, smem, c->stream>>>(a);
+  } else {
+    k_drift<R><<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(drift_args<R>(c, sp, d_vel));
+  }
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
 
-cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel) {
-  return c->fp64 ? launch_drift_t<double>(c, sp, d_vel) : launch_drift_t<float>(c, sp, d_vel);
+cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev) {
+  return c->fp64 ? launch_drift_t<double>(c, sp, d_vel, ev) : launch_drift_t<float>(c, sp, d_vel, ev);
+}
+
+template <typename R>
+static cudaError_t launch_sum_t(relres_ctx* c, const StepParams& sp, int k, const double* d_vel) {
+  SumArgs<R> a{};
+  a.n = c->n;
+  a.f_fg = static_cast<const ForceT<R>*>(c->d_f_fg);
+  a.f_cg = static_cast<const ForceT<R>*>(c->d_f_cg);
+  a.with_cg = (c->has_cg && c->n_h > 0) ? 1 : 0;
+  a.f_bond = static_cast<const ForceT<R>*>(c->d_f_bond);
+  a.type = c->d_type;
+  a.hyb_mask = c->hyb_mask;
+  a.vel = d_vel;
+  a.cdt = c->d_cdt;
+  a.mass = c->d_mass;
+  a.f_tot = static_cast<ForceT<R>*>(c->d_f_tot);
+  a.acc = c->d_acc;
+  a.st = c->d_state;
+  a.sp = sp;
+  if (a.sp.thermo == nullptr) {
+    a.sp.thermo = static_cast<double*>(c->d_dummy);
+    a.sp.thermo_every = 0;
+  }
+  a.draw = c->d_draws + 2 * k;
+  const int nb = std::max(1, std::min((c->n + kThreads - 1) / kThreads, 152 * 4));
+  k_sum<R><<<nb, kThreads, 0, c->stream>>>(a);
+  RELRES_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_end_of_step(relres_ctx* c, const StepParams& sp, int k, bool ev, double* d_vel) {
+  if (step_segments(c))
+    return c->fp64 ? launch_sum_t<double>(c, sp, k, d_vel) : launch_sum_t<float>(c, sp, k, d_vel);
+  cudaError_t e = launch_finish(c, ev, nullptr, d_vel);
+  return e != cudaSuccess ? e : launch_thermo(c, sp, k);
 }
 
 cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp, int k) {

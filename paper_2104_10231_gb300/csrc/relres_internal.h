@@ -98,7 +98,7 @@ struct DevState {
   unsigned long long n_prunes;        // pruning passes (each rebuild is followed by one)
   unsigned long long tot_in_fg, tot_in_cg;  // pruned-list entries summed over all passes
   int thermo_row;
-  int pad;
+  unsigned done_blocks;  // ticket counter of k_sum (zero between launches)
 };
 
 // Energy / virial partial sums are 64-bit fixed point (value * 2^32): exact,
@@ -109,7 +109,7 @@ constexpr int kNQ = 7;  // E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
 constexpr int kAccFg = 0, kAccCg = kNQ, kAccKe = 2 * kNQ, kAccEb = 2 * kNQ + 1, kNAcc = 2 * kNQ + 2;
 constexpr int kBlockSteps = 100;  // steps between host status checks in relres_step
 constexpr int kSegAtoms = 256;       // atoms per segment (one block of the fused force sum)
-constexpr size_t kSegSmemMax = 48 * 1024;  // shared memory of a segment's term slots
+constexpr size_t kSegSmemMax = 48 * 1024;  // shared memory of a segment kernel (term slots + positions)
 constexpr double kPruneDelta = 0.5;   // default margin of the pruned lists (Angstrom)
 constexpr double kPruneSlack = 1e-3;  // added to the pruning radius: covers FP32 rounding of distances
 
@@ -251,6 +251,7 @@ struct relres_ctx {
   void* d_f_fg = nullptr;
   void* d_f_cg = nullptr;
   void* d_f_tot = nullptr;
+  void* d_f_bond = nullptr;  // bonded forces from the segmented drift kernel
   bool forces_valid = false;
 
   // bonded-term force slots: bonds 2 per term, then angles 3, then dihedrals 4
@@ -369,11 +370,20 @@ cudaError_t launch_pair_grad(relres_ctx* c, const double* d_grad_forces, double 
 
 // MD
 cudaError_t upload_type_consts(relres_ctx* c, double dt);
-cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel);
+// drift of one step; where the atoms form segments of whole molecules it also
+// evaluates the bonded forces of the new positions (d_f_bond; energy if ev)
+cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev);
+// after the pair kernel: total forces, kinetic energy, thermostat and step
+// bookkeeping (k_sum with the thermostat in its last block, or the
+// finish + k_thermo pair where there are no segments)
+cudaError_t launch_end_of_step(relres_ctx* c, const StepParams& sp, int k, bool ev, double* d_vel);
 cudaError_t launch_csvr_draws(relres_ctx* c, const StepParams& sp, int count);
 cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp, int k);
 cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev);
 cudaError_t launch_flags_and(relres_ctx* c, unsigned keep);
+
+// MD steps take the segmented drift + bonded kernel and k_sum
+inline bool step_segments(const relres_ctx* c) { return c->seg_ok && c->use_seg; }
 
 // the lists the pair kernels walk: the pruned ones when pruning is on
 inline const int* walk_nbr_fg(const relres_ctx* c) { return c->prune_on ? c->d_nbr_fg_in : c->d_nbr_fg; }
