@@ -521,6 +521,8 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   const size_t fb = size_t(n) * (c->fp64 ? 24 : 16);
   CK(dalloc(&c->d_type, n));
   CK(dalloc(&c->d_cdt, RELRES_MAX_TYPES));
+  CK(dalloc(&c->d_cdt_ff, RELRES_MAX_TYPES));
+  CK(dalloc(&c->d_kec, RELRES_MAX_TYPES));
   CK(dalloc(&c->d_mass, RELRES_MAX_TYPES));
   CK(dalloc(&c->d_excl_off, size_t(n) + 1));
   CK(dalloc(&c->d_excl_idx, std::max<size_t>(1, eidx.size())));
@@ -578,6 +580,7 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_snap_f), fb));
   CK(dalloc(&c->d_snap_x, 3 * size_t(n)));
   CK(dalloc(&c->d_snap_v, 3 * size_t(n)));
+  CK(dalloc(&c->d_uff, 3 * size_t(n)));
   const size_t n_slots = 2 * size_t(c->n_bonds) + 3 * size_t(c->n_angles) + 4 * size_t(c->n_dih);
   CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_tf),
             std::max<size_t>(1, n_slots) * (c->fp64 ? 24 : 16)));
@@ -836,7 +839,7 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
   const unsigned* gate = &c->d_state->flags;
   const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
   CK(cudaMemcpyAsync(c->d_snap_x, c->d_xfx, xb, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->d_snap_v, d_vel, vb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_snap_v, vel_state(c, d_vel), vb, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_snap_f, c->d_f_tot, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
   CK(launch_csvr_draws(c, sp, blk));
@@ -1063,7 +1066,7 @@ relres_status relres_backward(relres_ctx* c, const double* d_pos, const double* 
 static relres_status rollback_block(relres_ctx* c, double* d_vel) {
   const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
   CK(cudaMemcpyAsync(c->d_xfx, c->d_snap_x, xb, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(d_vel, c->d_snap_v, vb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(vel_state(c, d_vel), c->d_snap_v, vb, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_f_tot, c->d_snap_f, force_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_state, c->d_snap_state, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
   return RELRES_OK;
@@ -1107,6 +1110,7 @@ static relres_status step_begin(relres_ctx* c, int n_steps, double dt_fs, double
     if (s != RELRES_OK) return s;
   }
   CK(upload_type_consts(c, dt_fs));
+  CK(launch_vel_in(c, d_vel));  // FP32: the float-float velocity state of the call
   CK(launch_set_ab(c, 1.0, 1.0, 0));
   CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
   return read_state(c);  // also orders the setup before work on other streams
@@ -1591,6 +1595,9 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_out_scratch);
   dfree(c->d_snap_x);
   dfree(c->d_snap_v);
+  dfree(c->d_uff);
+  dfree(c->d_cdt_ff);
+  dfree(c->d_kec);
   dfree(c->d_snap_f);
   dfree(c->d_snap_state);
   dfree(c->d_dummy);

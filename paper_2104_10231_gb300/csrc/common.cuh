@@ -156,6 +156,28 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
   return ff_quick(r, __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo), __fmul_rn(2.f, r)));
 }
 __device__ __forceinline__ float ff_val(ff a) { return __fadd_rn(a.hi, a.lo); }
+// float-float times float
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = fmaf(a.hi, b, -p);
+  return ff_quick(p, __fadd_rn(e, __fmul_rn(a.lo, b)));
+}
+// float -> int64, rounded to nearest (ties away from zero), by integer
+// operations on the bits (|v| < 2^62; zero, subnormals and anything below 1/2
+// give 0)
+__device__ __forceinline__ long long f2ll_rn(float v) {
+  const int b = __float_as_int(v);
+  const int e = min(((b >> 23) & 0xff) - 150, 38);  // v = m 2^e, m a 24-bit integer
+  const long long m = (long long)((b & 0x7fffff) | 0x800000);
+  long long r = 0;
+  if (e >= 0)
+    r = m << e;
+  else if (e > -25)
+    r = (m + (1ll << (-e - 1))) >> (-e);
+  return b < 0 ? -r : r;
+}
+// float-float -> int64 (both parts rounded separately)
+__device__ __forceinline__ long long ff2ll(ff v) { return f2ll_rn(v.hi) + f2ll_rn(v.lo); }
 __device__ __forceinline__ ff ff_from(float a) { return ff{a, 0.f}; }
 // 1/a: FP32 estimate and one Newton step in float-float
 __device__ __forceinline__ ff ff_rcp(ff a) {

@@ -54,6 +54,11 @@ static BoxConsts box_consts(const relres_ctx* c, double dt) {
   return b;
 }
 
+static void ff_split(double v, float* hi, float* lo) {
+  *hi = float(v);
+  *lo = float(v - double(*hi));
+}
+
 template <typename R>
 struct Sc3 {  // per-axis scale of a fixed-point difference
   R s0, s1, s2;
@@ -207,8 +212,7 @@ __device__ __forceinline__ void cross3(const R a[3], const R b[3], R c[3]) {
 
 template <typename R, class X>
 __device__ __forceinline__ R bond_forces(const BondedArgs& B, const X& xfx, Sc3<R> sc,
-                                         int t, R f[2][3]) {
-  const int4 bd = B.bonds[t];
+                                         int4 bd, R f[2][3]) {
   R d[3];
   dvec(xfx, bd.x, bd.y, sc, d);
   const R r = sqrt(dot3(d, d));
@@ -224,8 +228,7 @@ __device__ __forceinline__ R bond_forces(const BondedArgs& B, const X& xfx, Sc3<
 
 template <typename R, class X>
 __device__ __forceinline__ R angle_forces(const BondedArgs& B, const X& xfx, Sc3<R> sc,
-                                          int t, R f[3][3]) {
-  const int4 an = B.angles[t];
+                                          int4 an, R f[3][3]) {
   R r1[3], r2[3];
   dvec(xfx, an.x, an.y, sc, r1);
   dvec(xfx, an.z, an.y, sc, r2);
@@ -284,8 +287,7 @@ __device__ __forceinline__ R dihedral_forces(const BondedArgs& B, const X& xfx, 
 // float-float arithmetic from the exact 64-bit fixed-point difference.
 template <class X>
 __device__ __forceinline__ float bond_forces_ff(const BondedArgs& B, const X& xfx, ff q0,
-                                                ff q1, ff q2, int t, float f[2][3]) {
-  const int4 bd = B.bonds[t];
+                                                ff q1, ff q2, int4 bd, float f[2][3]) {
   const float* P = B.bond_fpar + 4 * bd.z;
   ff d[3];
   ff_vec(xfx, bd.x, bd.y, q0, q1, q2, d);
@@ -306,8 +308,7 @@ __device__ __forceinline__ float bond_forces_ff(const BondedArgs& B, const X& xf
 // angle error stays near 1e-7 rad (force error ~2K 1e-7 / r).
 template <class X>
 __device__ __forceinline__ float angle_forces_f32(const BondedArgs& B, const X& xfx,
-                                                  Sc3<float> sc, int t, float f[3][3]) {
-  const int4 an = B.angles[t];
+                                                  Sc3<float> sc, int4 an, float f[3][3]) {
   const float* P = B.angle_fpar + 8 * an.w;
   float r1[3], r2[3];
   dvec(xfx, an.x, an.y, sc, r1);
@@ -340,6 +341,22 @@ __device__ __forceinline__ float angle_forces_f32(const BondedArgs& B, const X& 
 
 template <typename R>
 using ForceT = typename std::conditional<std::is_same<R, float>::value, float4, double>::type;
+// velocity state u: float-float pairs (FP32 path) or doubles (FP64 path), [3n]
+template <typename R>
+using VelT = typename std::conditional<std::is_same<R, float>::value, float2, double>::type;
+
+// component k of u in the precision of the force arithmetic
+__device__ __forceinline__ float vel_r(const float2* v, int k) {
+  const float2 p = v[k];
+  return __fadd_rn(p.x, p.y);
+}
+__device__ __forceinline__ double vel_r(const double* v, int k) { return v[k]; }
+// component k of u in FP64
+__device__ __forceinline__ double vel_d(const float2* v, int k) {
+  const float2 p = v[k];
+  return double(p.x) + double(p.y);
+}
+__device__ __forceinline__ double vel_d(const double* v, int k) { return v[k]; }
 
 __device__ __forceinline__ void load_force(const float4* f, int i, float v[3]) {
   const float4 q = f[i];
@@ -386,17 +403,17 @@ __global__ void __launch_bounds__(kThreads) k_bonded(BondedKArgs<R> a) {
   if (t < a.nb) {
     R f[2][3];
     if constexpr (std::is_same<R, float>::value)
-      e = bond_forces_ff(a.B, GPos{a.xfx}, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, t, f);
+      e = bond_forces_ff(a.B, GPos{a.xfx}, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, a.B.bonds[t], f);
     else
-      e = bond_forces<R>(a.B, GPos{a.xfx}, sc, t, f);
+      e = bond_forces<R>(a.B, GPos{a.xfx}, sc, a.B.bonds[t], f);
     save_slots<2, R>(a.tf, 2 * size_t(t), f);
   } else if (t < a.nb + a.na) {
     const int u = t - a.nb;
     R f[3][3];
     if constexpr (std::is_same<R, float>::value)
-      e = angle_forces_f32(a.B, GPos{a.xfx}, sc, u, f);
+      e = angle_forces_f32(a.B, GPos{a.xfx}, sc, a.B.angles[u], f);
     else
-      e = angle_forces<R>(a.B, GPos{a.xfx}, sc, u, f);
+      e = angle_forces<R>(a.B, GPos{a.xfx}, sc, a.B.angles[u], f);
     save_slots<3, R>(a.tf, 2 * size_t(a.nb) + 3 * size_t(u), f);
   } else if (t < a.nb + a.na + a.nd) {
     const int u = t - a.nb - a.na;
@@ -424,7 +441,7 @@ struct FinishArgs {
   const int* inc;
   const ForceT<R>* tf;
   int base1, base2;    // first slot of the angles, of the dihedrals
-  const double* vel;   // u (half-step velocities) for the kinetic energy
+  const VelT<R>* vel;  // u (half-step velocities) for the kinetic energy
   int with_ke;
   const double* cdt;   // per type: dt / (2 m) * ftm2v
   const double* mass;  // per type
@@ -477,7 +494,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a) {
       R v2 = R(0);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const R v = R(a.vel[3 * i + q]) + c * f[q];
+        const R v = vel_r(a.vel, 3 * i + q) + c * f[q];
         v2 += v * v;
       }
       ke = R(0.5 * a.mass[t] * kMvv2e) * v2;
@@ -512,7 +529,7 @@ struct SegArgs {
   int hyb_mask;
   const int* inc_off;
   const int* inc;
-  const double* vel;
+  const VelT<R>* vel;
   int with_ke;
   const double* cdt;
   const double* mass;
@@ -537,17 +554,17 @@ __global__ void __launch_bounds__(kThreads) k_finish_seg(SegArgs<R> a) {
     if (q < nb) {
       R f[2][3];
       if constexpr (std::is_same<R, float>::value)
-        e += bond_forces_ff(a.B, GPos{a.xfx}, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, b0 + q, f);
+        e += bond_forces_ff(a.B, GPos{a.xfx}, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, a.B.bonds[b0 + q], f);
       else
-        e += bond_forces<R>(a.B, GPos{a.xfx}, sc, b0 + q, f);
+        e += bond_forces<R>(a.B, GPos{a.xfx}, sc, a.B.bonds[b0 + q], f);
       save_slots<2, R>(slot, 2 * size_t(q), f);
     } else if (q < nb + na) {
       const int u = q - nb;
       R f[3][3];
       if constexpr (std::is_same<R, float>::value)
-        e += angle_forces_f32(a.B, GPos{a.xfx}, sc, g0 + u, f);
+        e += angle_forces_f32(a.B, GPos{a.xfx}, sc, a.B.angles[g0 + u], f);
       else
-        e += angle_forces<R>(a.B, GPos{a.xfx}, sc, g0 + u, f);
+        e += angle_forces<R>(a.B, GPos{a.xfx}, sc, a.B.angles[g0 + u], f);
       save_slots<3, R>(slot, base_a + 3 * size_t(u), f);
     } else {
       const int u = q - nb - na;
@@ -601,7 +618,7 @@ __global__ void __launch_bounds__(kThreads) k_finish_seg(SegArgs<R> a) {
       R v2 = R(0);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const R v = R(a.vel[3 * i + q]) + c * f[q];
+        const R v = vel_r(a.vel, 3 * i + q) + c * f[q];
         v2 += v * v;
       }
       ke = R(0.5 * a.mass[t] * kMvv2e) * v2;
@@ -621,12 +638,14 @@ __global__ void __launch_bounds__(kThreads) k_finish_seg(SegArgs<R> a) {
 template <typename R>
 struct DriftArgs {
   int n;
-  double* vel;  // u, updated
+  VelT<R>* vel;  // u, updated
   unsigned long long* xfx;
   const ForceT<R>* f_tot;
   const int* type;
   const double* cdt;
+  const float2* cdt_ff;        // FP32 path
   double dts0, dts1, dts2;
+  float dts0h, dts0l, dts1h, dts1l, dts2h, dts2l;  // FP32 path: dts as float-float
   Sc3<float> s32;
   const int* rank_fg;
   const int* rank_cg;
@@ -648,20 +667,38 @@ struct DriftArgs {
 // One atom of the drift: u <- a u + b c F, x <- x + dt u, the sorted copies
 // of x, and the two displacement triggers.  Returns the new position in x.
 template <typename R>
-__device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, double ca, double cb,
-                                           unsigned long long x[3], bool& rebuild, bool& reprune) {
+__device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, unsigned long long x[3], bool& rebuild,
+                                           bool& reprune) {
   const int t = a.type[i];
   R f[3];
   load_force(a.f_tot, i, f);
-  const R bc = R(cb * a.cdt[t]);
-  const double dts[3] = {a.dts0, a.dts1, a.dts2};
+  if constexpr (std::is_same<R, float>::value) {
+    // float-float: u <- a u + b c F and the increment u dt 2^64 / L, with no
+    // FP64 instruction (FP64 runs at a small fraction of the FP32 rate here)
+    const ff ca{a.st->a_hi, a.st->a_lo}, cb{a.st->b_hi, a.st->b_lo};
+    const float2 cc = a.cdt_ff[t];
+    const ff bc = ff_mul(cb, ff{cc.x, cc.y});
+    const ff dts[3] = {ff{a.dts0h, a.dts0l}, ff{a.dts1h, a.dts1l}, ff{a.dts2h, a.dts2l}};
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    // the kick increment in the force's precision, accumulated in FP64
-    const double u = fma(ca, a.vel[3 * i + q], double(bc * f[q]));
-    a.vel[3 * i + q] = u;
-    x[q] = a.xfx[3 * i + q] + (unsigned long long)__double2ll_rn(u * dts[q]);
-    a.xfx[3 * i + q] = x[q];
+    for (int q = 0; q < 3; ++q) {
+      const float2 v = a.vel[3 * i + q];
+      const ff u = ff_add(ff_mul(ca, ff{v.x, v.y}), ff_mul_f(bc, f[q]));
+      a.vel[3 * i + q] = make_float2(u.hi, u.lo);
+      x[q] = a.xfx[3 * i + q] + (unsigned long long)ff2ll(ff_mul(u, dts[q]));
+      a.xfx[3 * i + q] = x[q];
+    }
+  } else {
+    const double ca = a.st->a, cb = a.st->b;
+    const R bc = R(cb * a.cdt[t]);
+    const double dts[3] = {a.dts0, a.dts1, a.dts2};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      // the kick increment in the force's precision, accumulated in FP64
+      const double u = fma(ca, a.vel[3 * i + q], double(bc * f[q]));
+      a.vel[3 * i + q] = u;
+      x[q] = a.xfx[3 * i + q] + (unsigned long long)__double2ll_rn(u * dts[q]);
+      a.xfx[3 * i + q] = x[q];
+    }
   }
   scatter_sorted(i, t, x[0], x[1], x[2], a.rank_fg, a.rank_cg, a.with_cg, a.pos_fg, a.pos_cg, a.fp64,
                  a.pos_fg64, a.pos_cg64);
@@ -671,14 +708,13 @@ __device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, double 
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_drift(DriftArgs<R> a) {
-  const double ca = a.st->a, cb = a.st->b;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     a.st->ev = a.thermo_every > 0 && ((a.st->local_step + 1) % a.thermo_every) == 0;
   bool rebuild = false, reprune = false;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) {
     unsigned long long x[3];
-    drift_atom(a, i, ca, cb, x, rebuild, reprune);
+    drift_atom(a, i, x, rebuild, reprune);
   }
   if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&a.st->flags, F_REBUILD);
   if (__syncthreads_or(reprune) && threadIdx.x == 0) atomicOr(&a.st->flags, F_PRUNE);
@@ -706,20 +742,27 @@ struct DriftSegArgs {
 };
 
 template <typename R, bool EV>
-__global__ void __launch_bounds__(kThreads) k_drift_seg(DriftSegArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 6 : 1) k_drift_seg(DriftSegArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* sx = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSegAtoms][3]
   ForceT<R>* slot = reinterpret_cast<ForceT<R>*>(smem_raw + sizeof(unsigned long long) * 3 * kSegAtoms);
   const int* g = a.seg + 8 * blockIdx.x;
   const int a0 = g[0], a1 = g[1], b0 = g[2], b1 = g[3], g0 = g[4], g1 = g[5], d0 = g[6], d1 = g[7];
-  const double ca = a.d.st->a, cb = a.d.st->b;
+  const int nb = b1 - b0, na = g1 - g0, nd = d1 - d0;
+  const int base_a = 2 * nb, base_d = base_a + 3 * na;
+  const int i = a0 + threadIdx.x;
+  // loads that do not depend on the drift, issued before it: the records of
+  // this thread's first two bond/angle terms and its atom's incident-term range
+  const int q0 = threadIdx.x, q1 = threadIdx.x + kThreads;
+  const int4 rec0 = q0 < nb ? a.B.bonds[b0 + q0] : (q0 < nb + na ? a.B.angles[g0 + q0 - nb] : make_int4(0, 0, 0, 0));
+  const int4 rec1 = q1 < nb ? a.B.bonds[b0 + q1] : (q1 < nb + na ? a.B.angles[g0 + q1 - nb] : make_int4(0, 0, 0, 0));
+  const int e0 = i < a1 ? a.inc_off[i] : 0, e1 = i < a1 ? a.inc_off[i + 1] : 0;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     a.d.st->ev = a.d.thermo_every > 0 && ((a.d.st->local_step + 1) % a.d.thermo_every) == 0;
   bool rebuild = false, reprune = false;
-  const int i = a0 + threadIdx.x;
   if (i < a1) {
     unsigned long long x[3];
-    drift_atom(a.d, i, ca, cb, x, rebuild, reprune);
+    drift_atom(a.d, i, x, rebuild, reprune);
 #pragma unroll
     for (int q = 0; q < 3; ++q) sx[3 * threadIdx.x + q] = x[q];
   }
@@ -727,25 +770,25 @@ __global__ void __launch_bounds__(kThreads) k_drift_seg(DriftSegArgs<R> a) {
   if (__syncthreads_or(reprune) && threadIdx.x == 0) atomicOr(&a.d.st->flags, F_PRUNE);
   // bonded terms of the segment from the new positions
   const SPos xs{sx, a0};
-  const int nb = b1 - b0, na = g1 - g0, nd = d1 - d0;
-  const int base_a = 2 * nb, base_d = base_a + 3 * na;
   const Sc3<R> sc = a.sc;
   R e = R(0);
-  for (int q = threadIdx.x; q < nb + na + nd; q += blockDim.x) {
+  for (int q = threadIdx.x, r = 0; q < nb + na + nd; q += blockDim.x, ++r) {
     if (q < nb) {
+      const int4 rc = r == 0 ? rec0 : (r == 1 ? rec1 : a.B.bonds[b0 + q]);
       R f[2][3];
       if constexpr (std::is_same<R, float>::value)
-        e += bond_forces_ff(a.B, xs, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, b0 + q, f);
+        e += bond_forces_ff(a.B, xs, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, rc, f);
       else
-        e += bond_forces<R>(a.B, xs, sc, b0 + q, f);
+        e += bond_forces<R>(a.B, xs, sc, rc, f);
       save_slots<2, R>(slot, 2 * size_t(q), f);
     } else if (q < nb + na) {
       const int u = q - nb;
+      const int4 rc = r == 0 ? rec0 : (r == 1 ? rec1 : a.B.angles[g0 + u]);
       R f[3][3];
       if constexpr (std::is_same<R, float>::value)
-        e += angle_forces_f32(a.B, xs, sc, g0 + u, f);
+        e += angle_forces_f32(a.B, xs, sc, rc, f);
       else
-        e += angle_forces<R>(a.B, xs, sc, g0 + u, f);
+        e += angle_forces<R>(a.B, xs, sc, rc, f);
       save_slots<3, R>(slot, base_a + 3 * size_t(u), f);
     } else {
       const int u = q - nb - na;
@@ -763,8 +806,7 @@ __global__ void __launch_bounds__(kThreads) k_drift_seg(DriftSegArgs<R> a) {
   __syncthreads();
   if (i < a1) {
     R f[3] = {R(0), R(0), R(0)};
-    const int k1 = a.inc_off[i + 1];
-    for (int k = a.inc_off[i]; k < k1; ++k) {
+    for (int k = e0; k < e1; ++k) {
       const int item = a.inc[k];
       const int kind = (item >> 30) & 3, role = (item >> 28) & 3, term = item & 0x0fffffff;
       const int s = kind == 0 ? 2 * (term - b0) + role
@@ -850,6 +892,10 @@ __device__ void end_of_step(volatile long long* acc, const StepParams& sp, DevSt
   st->alpha = alpha;
   st->a = alpha;
   st->b = alpha + 1.0;
+  st->a_hi = float(alpha);
+  st->a_lo = float(alpha - double(st->a_hi));
+  st->b_hi = float(alpha + 1.0);
+  st->b_lo = float((alpha + 1.0) - double(st->b_hi));
   double* thermo = sp.thermo;
   if (ev && sp.thermo_every > 0) {
     double* row = thermo + (size_t)st->thermo_row * RELRES_THERMO_COLS;
@@ -890,9 +936,11 @@ struct SumArgs {
   const ForceT<R>* f_bond;
   const int* type;
   int hyb_mask;
-  const double* vel;
+  const VelT<R>* vel;
   const double* cdt;
+  const float2* cdt_ff;
   const double* mass;
+  const float* kec;
   ForceT<R>* f_tot;
   long long* acc;
   DevState* st;
@@ -903,46 +951,55 @@ struct SumArgs {
 template <typename R>
 __device__ __forceinline__ R sum_atom(const SumArgs<R>& a, int i, bool& bad) {
   const int t = a.type[i];
-  R f[3], h[3];
+  R f[3], h[3], b[3];
   load_force(a.f_fg, i, f);
+  // the CG part is zero for ordinary atoms (never written): loaded without
+  // waiting for the type, added only for hybrids
+  if (a.with_cg) load_force(a.f_cg, i, h);
+  load_force(a.f_bond, i, b);
   if (a.with_cg && ((a.hyb_mask >> t) & 1)) {
-    load_force(a.f_cg, i, h);
     f[0] += h[0];
     f[1] += h[1];
     f[2] += h[2];
   }
-  load_force(a.f_bond, i, h);
-  f[0] += h[0];
-  f[1] += h[1];
-  f[2] += h[2];
+  f[0] += b[0];
+  f[1] += b[1];
+  f[2] += b[2];
   bad |= !(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]));
   save_force(a.f_tot, i, f);
-  const R c = R(a.cdt[t]);
+  R c, kc;
+  if constexpr (std::is_same<R, float>::value) {
+    c = a.cdt_ff[t].x;
+    kc = a.kec[t];
+  } else {
+    c = a.cdt[t];
+    kc = 0.5 * a.mass[t] * kMvv2e;
+  }
   R v2 = R(0);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const R v = R(a.vel[3 * i + q]) + c * f[q];
+    const R v = vel_r(a.vel, 3 * i + q) + c * f[q];
     v2 += v * v;
   }
-  return R(0.5 * a.mass[t] * kMvv2e) * v2;
+  return kc * v2;
 }
 
 // grid-stride (a few blocks per SM), one kinetic-energy atomic and one
 // ticket per block
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_sum(SumArgs<R> a) {
-  double ke = 0.0;
+  R ke = R(0);  // a few atoms per thread
   bool bad = false;
   const int stride = gridDim.x * blockDim.x;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   for (; i + stride < a.n; i += 2 * stride) {  // two atoms in flight
     const R k0 = sum_atom(a, i, bad);
     const R k1 = sum_atom(a, i + stride, bad);
-    ke += double(k0) + double(k1);
+    ke += k0 + k1;
   }
-  if (i < a.n) ke += double(sum_atom(a, i, bad));
+  if (i < a.n) ke += sum_atom(a, i, bad);
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&a.st->flags, F_NONFINITE);
-  double v[1] = {ke};
+  double v[1] = {double(ke)};
   __shared__ double sh_k[kThreads / 32];
   block_sum<double, 1>(v, sh_k);
   if (threadIdx.x == 0) {
@@ -977,6 +1034,10 @@ __global__ void k_reduce_out(long long* acc, double* energy, int with_e, double*
 __global__ void k_set_ab(DevState* st, double a, double b) {
   st->a = a;
   st->b = b;
+  st->a_hi = float(a);
+  st->a_lo = float(a - double(st->a_hi));
+  st->b_hi = float(b);
+  st->b_lo = float(b - double(st->b_hi));
   st->local_step = 0;
   st->thermo_row = 0;
   st->ev = 0;
@@ -984,8 +1045,17 @@ __global__ void k_set_ab(DevState* st, double a, double b) {
 
 __global__ void k_flags_and(DevState* st, unsigned keep) { st->flags &= keep; }
 
+// FP32 path: caller's FP64 velocities -> float-float state
+__global__ void k_vel_in(int n3, const double* __restrict__ vel, float2* __restrict__ uff) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n3; k += gridDim.x * blockDim.x) {
+    const double v = vel[k];
+    const float hi = float(v);
+    uff[k] = make_float2(hi, float(v - double(hi)));
+  }
+}
+
 template <typename R>
-__global__ void k_finish_md(int n, const DevState* st, const double* vel_u,
+__global__ void k_finish_md(int n, const DevState* st, const VelT<R>* vel_u,
                             const ForceT<R>* __restrict__ f_tot, const int* __restrict__ type,
                             const double* __restrict__ cdt, const unsigned long long* __restrict__ xfx,
                             BoxConsts b, double* vel_out, double* __restrict__ pos_out) {
@@ -997,7 +1067,7 @@ __global__ void k_finish_md(int n, const DevState* st, const double* vel_u,
     load_force(f_tot, i, f);
     const R c = R(cb1 * cdt[t]);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) vel_out[3 * i + q] = fma(ca, vel_u[3 * i + q], double(c * f[q]));
+    for (int q = 0; q < 3; ++q) vel_out[3 * i + q] = fma(ca, vel_d(vel_u, 3 * i + q), double(c * f[q]));
     pos_out[3 * i] = back_to_double(xfx[3 * i], a0, l0);
     pos_out[3 * i + 1] = back_to_double(xfx[3 * i + 1], a1, l1);
     pos_out[3 * i + 2] = back_to_double(xfx[3 * i + 2], a2, l2);
@@ -1030,9 +1100,33 @@ static Sc3<float> s32_of(const relres_ctx* c) {
 }
 
 cudaError_t upload_type_consts(relres_ctx* c, double dt) {
-  for (int k = 0; k < c->n_types; ++k) c->h_cdt[k] = 0.5 * dt / c->mass_by_type[k] * kFtm2v;
-  return cudaMemcpyAsync(c->d_cdt, c->h_cdt.data(), sizeof(double) * c->n_types,
-                         cudaMemcpyHostToDevice, c->stream);
+  std::vector<float2> cff(size_t(c->n_types));
+  std::vector<float> kec(size_t(c->n_types));
+  for (int k = 0; k < c->n_types; ++k) {
+    c->h_cdt[k] = 0.5 * dt / c->mass_by_type[k] * kFtm2v;
+    float hi, lo;
+    ff_split(c->h_cdt[k], &hi, &lo);
+    cff[size_t(k)] = make_float2(hi, lo);
+    kec[size_t(k)] = float(0.5 * c->mass_by_type[k] * kMvv2e);
+  }
+  cudaError_t e = cudaMemcpyAsync(c->d_cdt, c->h_cdt.data(), sizeof(double) * c->n_types, cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_cdt_ff, cff.data(), sizeof(float2) * c->n_types, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_kec, kec.data(), sizeof(float) * c->n_types, cudaMemcpyHostToDevice, c->stream);
+  // the host vectors must outlive the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e;
+}
+
+cudaError_t launch_vel_in(relres_ctx* c, const double* d_vel) {
+  if (c->fp64) return cudaSuccess;
+  const int n3 = 3 * c->n;
+  k_vel_in<<<std::max(1, std::min((n3 + kThreads - 1) / kThreads, 152 * 8)), kThreads, 0, c->stream>>>(
+      n3, d_vel, c->d_uff);
+  RELRES_LAUNCHED(c);
+  return cudaGetLastError();
 }
 
 static Pos64* p64(relres_ctx* c, Pos64* p) { return c->fp64 ? p : static_cast<Pos64*>(c->d_dummy); }
@@ -1060,10 +1154,6 @@ static BondedArgs bonded_args(const relres_ctx* c) {
                     c->d_angle_par, c->d_dih_par,   c->d_bond_fpar, c->d_angle_fpar};
 }
 
-static void ff_split(double v, float* hi, float* lo) {
-  *hi = float(v);
-  *lo = float(v - double(*hi));
-}
 
 template <typename R>
 static cudaError_t launch_bonded_t(relres_ctx* c, bool ev) {
@@ -1105,7 +1195,8 @@ static cudaError_t launch_finish_t(relres_ctx* c, double* d_forces_out, const do
                   static_cast<const ForceT<R>*>(c->d_tf),
                   2 * c->n_bonds,
                   2 * c->n_bonds + 3 * c->n_angles,
-                  vel ? vel : static_cast<const double*>(c->d_dummy),
+                  vel ? static_cast<const VelT<R>*>(vel_state(c, const_cast<double*>(vel)))
+                      : static_cast<const VelT<R>*>(c->d_dummy),
                   vel ? 1 : 0,
                   c->d_cdt,
                   c->d_mass,
@@ -1137,7 +1228,8 @@ static cudaError_t launch_finish_seg_t(relres_ctx* c, bool ev, double* d_forces_
   a.hyb_mask = c->hyb_mask;
   a.inc_off = c->d_inc_off;
   a.inc = c->d_inc;
-  a.vel = vel ? vel : static_cast<const double*>(c->d_dummy);
+  a.vel = vel ? static_cast<const VelT<R>*>(vel_state(c, const_cast<double*>(vel)))
+              : static_cast<const VelT<R>*>(c->d_dummy);
   a.with_ke = vel ? 1 : 0;
   a.cdt = c->d_cdt;
   a.mass = c->d_mass;
@@ -1186,15 +1278,26 @@ template <typename R>
 static DriftArgs<R> drift_args(relres_ctx* c, const StepParams& sp, double* d_vel) {
   const bool cg = c->has_cg && c->n_h > 0;
   const BoxConsts b = box_consts(c, sp.dt);
+  float h[6];
+  ff_split(b.dts0, &h[0], &h[1]);
+  ff_split(b.dts1, &h[2], &h[3]);
+  ff_split(b.dts2, &h[4], &h[5]);
   return DriftArgs<R>{c->n,
-                      d_vel,
+                      static_cast<VelT<R>*>(vel_state(c, d_vel)),
                       c->d_xfx,
                       static_cast<const ForceT<R>*>(c->d_f_tot),
                       c->d_type,
                       c->d_cdt,
+                      c->d_cdt_ff,
                       b.dts0,
                       b.dts1,
                       b.dts2,
+                      h[0],
+                      h[1],
+                      h[2],
+                      h[3],
+                      h[4],
+                      h[5],
                       s32_of(c),
                       c->d_rank_fg,
                       c->d_rank_cg,
@@ -1256,9 +1359,11 @@ static cudaError_t launch_sum_t(relres_ctx* c, const StepParams& sp, int k, cons
   a.f_bond = static_cast<const ForceT<R>*>(c->d_f_bond);
   a.type = c->d_type;
   a.hyb_mask = c->hyb_mask;
-  a.vel = d_vel;
+  a.vel = static_cast<const VelT<R>*>(vel_state(c, const_cast<double*>(d_vel)));
   a.cdt = c->d_cdt;
+  a.cdt_ff = c->d_cdt_ff;
   a.mass = c->d_mass;
+  a.kec = c->d_kec;
   a.f_tot = static_cast<ForceT<R>*>(c->d_f_tot);
   a.acc = c->d_acc;
   a.st = c->d_state;
@@ -1268,7 +1373,8 @@ static cudaError_t launch_sum_t(relres_ctx* c, const StepParams& sp, int k, cons
     a.sp.thermo_every = 0;
   }
   a.draw = c->d_draws + 2 * k;
-  const int nb = std::max(1, std::min((c->n + kThreads - 1) / kThreads, 152 * 4));
+  // one wave of resident blocks (44 registers a thread: five blocks per SM)
+  const int nb = std::max(1, std::min((c->n + kThreads - 1) / kThreads, 152 * 5));
   k_sum<R><<<nb, kThreads, 0, c->stream>>>(a);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
@@ -1310,12 +1416,12 @@ cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, doubl
   const BoxConsts b = box_consts(c, 0.0);
   if (c->fp64)
     k_finish_md<double><<<grid_for(c->n), kThreads, 0, c->stream>>>(
-        c->n, c->d_state, d_vel, static_cast<const double*>(c->d_f_tot), c->d_type, c->d_cdt,
-        c->d_xfx, b, d_vel, d_pos);
+        c->n, c->d_state, static_cast<const double*>(vel_state(c, d_vel)), static_cast<const double*>(c->d_f_tot),
+        c->d_type, c->d_cdt, c->d_xfx, b, d_vel, d_pos);
   else
     k_finish_md<float><<<grid_for(c->n), kThreads, 0, c->stream>>>(
-        c->n, c->d_state, d_vel, static_cast<const float4*>(c->d_f_tot), c->d_type, c->d_cdt,
-        c->d_xfx, b, d_vel, d_pos);
+        c->n, c->d_state, static_cast<const float2*>(vel_state(c, d_vel)), static_cast<const float4*>(c->d_f_tot),
+        c->d_type, c->d_cdt, c->d_xfx, b, d_vel, d_pos);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }

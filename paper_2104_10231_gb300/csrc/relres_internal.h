@@ -90,6 +90,7 @@ struct DevState {
   int max_fg, max_cg;
   int ev;                   // this step evaluates energy and virial
   double a, b;              // next drift: u <- a u + b (dt/2m) F
+  float a_hi, a_lo, b_hi, b_lo;  // the same as float-float (FP32 path)
   double alpha;             // last thermostat factor
   unsigned long long step;  // global step counter (thermostat random stream)
   long long local_step;     // steps done in the current relres_step call
@@ -179,6 +180,8 @@ struct relres_ctx {
   void* d_tab = nullptr;  // PairTab<float or double>[n_types^2]
   void* d_tabd = nullptr; // PairTab<double>[n_types^2] (energies of the FP32 path)
   double* d_cdt = nullptr;   // per type: (dt/2m) * ftm2v  (set per step call)
+  float2* d_cdt_ff = nullptr;  // the same as float-float (FP32 path)
+  float* d_kec = nullptr;      // per type: m / 2 in kcal/mol per (A/fs)^2, FP32
   double* d_mass = nullptr;  // per type mass
   std::vector<double> h_cdt = std::vector<double>(RELRES_MAX_TYPES, 0.0);
 
@@ -252,6 +255,10 @@ struct relres_ctx {
   void* d_f_cg = nullptr;
   void* d_f_tot = nullptr;
   void* d_f_bond = nullptr;  // bonded forces from the segmented drift kernel
+  // FP32 path: the velocity state of relres_step (u, see md.cu) as float-float
+  // pairs [3n] (the caller's FP64 velocities are read at the start of a call
+  // and written at its end); the FP64 path keeps u in the caller's array
+  float2* d_uff = nullptr;
   bool forces_valid = false;
 
   // bonded-term force slots: bonds 2 per term, then angles 3, then dihedrals 4
@@ -380,6 +387,12 @@ cudaError_t launch_end_of_step(relres_ctx* c, const StepParams& sp, int k, bool 
 cudaError_t launch_csvr_draws(relres_ctx* c, const StepParams& sp, int count);
 cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp, int k);
 cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev);
+// FP32 path: caller's velocities -> the float-float state (start of a call)
+cudaError_t launch_vel_in(relres_ctx* c, const double* d_vel);
+// the velocity state of a call: the float-float array (FP32) or the caller's (FP64)
+inline void* vel_state(relres_ctx* c, double* d_vel) {
+  return c->fp64 ? static_cast<void*>(d_vel) : static_cast<void*>(c->d_uff);
+}
 cudaError_t launch_flags_and(relres_ctx* c, unsigned keep);
 
 // MD steps take the segmented drift + bonded kernel and k_sum
