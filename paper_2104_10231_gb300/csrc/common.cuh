@@ -162,19 +162,25 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   const float e = fmaf(a.hi, b, -p);
   return ff_quick(p, __fadd_rn(e, __fmul_rn(a.lo, b)));
 }
-// float -> int64, rounded to nearest (ties away from zero), by integer
-// operations on the bits (|v| < 2^62; zero, subnormals and anything below 1/2
-// give 0)
+// float -> int64 rounded to nearest (ties to even), for |v| < 2^54, with
+// 32-bit conversions only (conversions to and from 64-bit integers run at the
+// FP64 rate on this part).  v = k 2^24 + rem: k = rint(v / 2^24) has at most
+// 24 significant bits (so float(k) and k 2^24 are exact) and rem = v - k 2^24
+// is exact with |rem| <= 2^23.
 __device__ __forceinline__ long long f2ll_rn(float v) {
-  const int b = __float_as_int(v);
-  const int e = min(((b >> 23) & 0xff) - 150, 38);  // v = m 2^e, m a 24-bit integer
-  const long long m = (long long)((b & 0x7fffff) | 0x800000);
-  long long r = 0;
-  if (e >= 0)
-    r = m << e;
-  else if (e > -25)
-    r = (m + (1ll << (-e - 1))) >> (-e);
-  return b < 0 ? -r : r;
+  const int k = __float2int_rn(__fmul_rn(v, 5.9604644775390625e-8f));
+  const float rem = __fsub_rn(v, __fmul_rn(__int2float_rn(k), 16777216.f));
+  return (long long)k * 16777216ll + (long long)__float2int_rn(rem);
+}
+// int64 -> float-float (~48 significant bits) from three 21-bit pieces, each
+// converted exactly by a 32-bit conversion, summed with error-free additions
+__device__ __forceinline__ ff ff_from_ll(long long d) {
+  const float f1 = __fmul_rn(__int2float_rn(int(d >> 42)), 4398046511104.f);
+  const float f2 = __fmul_rn(__int2float_rn(int((d >> 21) & 0x1fffffll)), 2097152.f);
+  const float f3 = __int2float_rn(int(d & 0x1fffffll));
+  const ff s = ff_two_sum(f1, f2);
+  const ff u = ff_two_sum(s.hi, f3);
+  return ff_quick(u.hi, __fadd_rn(u.lo, s.lo));
 }
 // float-float -> int64 (both parts rounded separately)
 __device__ __forceinline__ long long ff2ll(ff v) { return f2ll_rn(v.hi) + f2ll_rn(v.lo); }

@@ -164,12 +164,9 @@ struct SPos {
   __device__ __forceinline__ unsigned long long operator()(int i, int q) const { return s[3 * (i - a0) + q]; }
 };
 
-// exact 64-bit fixed-point difference a - b, scaled to Angstrom
+// exact 64-bit fixed-point difference a - b, scaled to Angstrom (float-float)
 __device__ __forceinline__ ff ff_fixed_diff(unsigned long long a, unsigned long long b, ff scale) {
-  const long long d = (long long)(a - b);
-  const float hi = __ll2float_rn(d);
-  const float lo = __ll2float_rn(d - __float2ll_rn(hi));
-  return ff_mul(ff_quick(hi, lo), scale);
+  return ff_mul(ff_from_ll((long long)(a - b)), scale);
 }
 template <class X>
 __device__ __forceinline__ void ff_vec(const X& x, int a, int b, ff s0, ff s1, ff s2, ff v[3]) {
@@ -742,7 +739,8 @@ struct DriftSegArgs {
 };
 
 template <typename R, bool EV>
-__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 6 : 1) k_drift_seg(DriftSegArgs<R> a) {
+__global__ void __launch_bounds__(kSegAtoms, std::is_same<R, float>::value ? 6 * kThreads / kSegAtoms : 1)
+    k_drift_seg(DriftSegArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* sx = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSegAtoms][3]
   ForceT<R>* slot = reinterpret_cast<ForceT<R>*>(smem_raw + sizeof(unsigned long long) * 3 * kSegAtoms);
@@ -753,7 +751,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 6 : 
   const int i = a0 + threadIdx.x;
   // loads that do not depend on the drift, issued before it: the records of
   // this thread's first two bond/angle terms and its atom's incident-term range
-  const int q0 = threadIdx.x, q1 = threadIdx.x + kThreads;
+  const int q0 = threadIdx.x, q1 = threadIdx.x + kSegAtoms;
   const int4 rec0 = q0 < nb ? a.B.bonds[b0 + q0] : (q0 < nb + na ? a.B.angles[g0 + q0 - nb] : make_int4(0, 0, 0, 0));
   const int4 rec1 = q1 < nb ? a.B.bonds[b0 + q1] : (q1 < nb + na ? a.B.angles[g0 + q1 - nb] : make_int4(0, 0, 0, 0));
   const int e0 = i < a1 ? a.inc_off[i] : 0, e1 = i < a1 ? a.inc_off[i + 1] : 0;
@@ -1335,9 +1333,9 @@ static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d
     const size_t smem = sizeof(unsigned long long) * 3 * kSegAtoms +
                         size_t(c->seg_slots) * (std::is_same<R, float>::value ? 16 : 24);
     if (ev)
-      k_drift_seg<R, true><<<c->n_seg, kThreads, smem, c->stream>>>(a);
+      k_drift_seg<R, true><<<c->n_seg, kSegAtoms, smem, c->stream>>>(a);
     else
-      k_drift_seg<R, false><<<c->n_seg, kThreads, smem, c->stream>>>(a);
+      k_drift_seg<R, false><<<c->n_seg, kSegAtoms, smem, c->stream>>>(a);
   } else {
     k_drift<R><<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(drift_args<R>(c, sp, d_vel));
   }

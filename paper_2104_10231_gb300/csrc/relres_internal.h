@@ -109,7 +109,10 @@ constexpr int kNQ = 7;  // E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
 // accumulator slots: FG pair sums, CG pair sums, kinetic energy, bonded energy
 constexpr int kAccFg = 0, kAccCg = kNQ, kAccKe = 2 * kNQ, kAccEb = 2 * kNQ + 1, kNAcc = 2 * kNQ + 2;
 constexpr int kBlockSteps = 100;  // steps between host status checks in relres_step
-constexpr int kSegAtoms = 256;       // atoms per segment (one block of the fused force sum)
+#ifndef RELRES_SEG_ATOMS
+#define RELRES_SEG_ATOMS 256
+#endif
+constexpr int kSegAtoms = RELRES_SEG_ATOMS;  // atoms per segment (one block of the segment kernels)
 constexpr size_t kSegSmemMax = 48 * 1024;  // shared memory of a segment kernel (term slots + positions)
 constexpr double kPruneDelta = 0.5;   // default margin of the pruned lists (Angstrom)
 constexpr double kPruneSlack = 1e-3;  // added to the pruning radius: covers FP32 rounding of distances
