@@ -393,7 +393,9 @@ void relres_batch_destroy(relres_batch* batch);
  * choice; the paper has no counterpart): config -1 (the default) lets the
  * first relres_step time every configuration -- threads sharing one atom's
  * list (1, 2, 4, 8) x block size -- on the context's own lists and keep the
- * fastest (systems under 20 000 atoms keep configuration 0); config 0..6
+ * fastest (systems under 20 000 atoms keep configuration 0; with list pruning
+ * on only the one-thread configurations 0-2 are timed, since the others need a
+ * separate pruning pass); config 0..6
  * fixes one (0: one thread per atom, 256 per block).  The choice is reported
  * in relres_stats.  Results agree within rounding (the summation order of an
  * atom's partners changes with the number of threads).

@@ -690,6 +690,9 @@ static relres_status autotune_pairs(relres_ctx* c) {
   int best_cfg = 0;
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < kNPairConfigs && err == cudaSuccess; ++k) {
+    // with pruning, launches with one thread per slot prune as they go; the
+    // others need a separate pruning pass, so they are not candidates
+    if (c->prune_on && kPairConfigs[k].tpa != 1) continue;
     c->pair_cfg = k;
     err = launch_pairs(c, false);  // warm-up
     if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);

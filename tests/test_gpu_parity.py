@@ -271,16 +271,19 @@ def test_every_pair_launch_configuration_matches_oracle(torch):
     ctx.close()
 
 
-def test_autotuner_picks_a_configuration(torch):
+@pytest.mark.parametrize("prune", [0.5, 0.0])
+def test_autotuner_picks_a_configuration(torch, prune):
     s = S.neopentane(n_mol=5000, seed=2)  # 25 000 atoms: above the tuning threshold
     ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    ctx.set_prune(prune)
     p = _dev(torch, s.pos)
     v = _dev(torch, s.vel)
     ctx.build_neighbors(p, s.box)
     ctx.step(5, 2.0, p, v)
     st = ctx.stats()
-    assert st["pair_tpa"] in (1, 2, 4, 8) and st["pair_block"] in (128, 256, 512)
-    print(f"autotuned: tpa {st['pair_tpa']} block {st['pair_block']}")
+    # with pruning only one thread per atom (the launches that prune as they go)
+    assert st["pair_tpa"] in ((1,) if prune > 0 else (1, 2, 4, 8)) and st["pair_block"] in (128, 256, 512)
+    print(f"autotuned (prune {prune}): tpa {st['pair_tpa']} block {st['pair_block']}")
     ctx.close()
 
 
