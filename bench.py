@@ -171,6 +171,23 @@ class ClockSampler:
 _THERMO = {}
 
 
+def max_over_ranks(dist, secs, device="cuda"):
+    """The largest of the ranks' times (every rank gets it); secs when not distributed."""
+    if dist is None:
+        return secs
+    import torch
+
+    t = torch.tensor([float(secs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, steps, secs_max):
+    """Units processed by all ranks per second of the slowest rank (replicas:
+    every rank advances its own system of units_per_rank atoms)."""
+    return world * units_per_rank * steps / secs_max
+
+
 def run_md_timed(torch, R, ctx, pos, vel, steps, dt, t_target, seed, thermo_every):
     """K steps of relres_step bracketed by CUDA events on the context stream,
     with a thermo row (energies, virial, temperature) every `thermo_every`
@@ -251,10 +268,8 @@ def ours(args):
         run_md_timed(torch, R, ctx, pos, vel, min(200, args.steps), dt, temp, 10, args.thermo_every)
         tim = ctx.timings()
         ctx.set_timing(False)
+        secs = max_over_ranks(dist, secs)
         if dist:
-            t = torch.tensor([secs], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            secs = float(t.item())
             dist.barrier()
 
         # end to end through the C ABI with host buffers: per step, copy the
@@ -267,6 +282,8 @@ def ours(args):
         ke = max(1, args.e2e_steps)
         ctx.step(1, dt, pos, vel, t_target=temp, tau_fs=100.0, seed=10)  # one-step graph captured here
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(ke):
             pos.copy_(hp, non_blocking=True)
@@ -275,10 +292,10 @@ def ours(args):
             hp.copy_(pos, non_blocking=True)
             hv.copy_(vel, non_blocking=True)
         torch.cuda.synchronize()
-        e2e_secs = time.perf_counter() - t0
-        e2e_value = n * ke / e2e_secs
+        e2e_secs = max_over_ranks(dist, time.perf_counter() - t0)
+        e2e_value = whole_job_rate(world, n, ke, e2e_secs)
 
-    value = world * n * args.steps / secs
+    value = whole_job_rate(world, n, args.steps, secs)
     ms_step = secs / args.steps * 1e3
 
     # FG-only reference on the same configuration
@@ -302,12 +319,9 @@ def ours(args):
             secs_f = run_md_timed(torch, R, ctxf, posf, velf, args.steps, dt, temp, 9, args.thermo_every)
             timf = ctxf.timings()
             stf = ctxf.stats()
-            if dist:
-                t = torch.tensor([secs_f], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                secs_f = float(t.item())
+            secs_f = max_over_ranks(dist, secs_f)
             ctxf.close()
-        fg = {"value": world * n * args.steps / secs_f, "ms_per_step": secs_f / args.steps * 1e3,
+        fg = {"value": whole_job_rate(world, n, args.steps, secs_f), "ms_per_step": secs_f / args.steps * 1e3,
               "pair_ms_per_launch": timf["pair"][0] / max(1, timf["pair"][1]),
               "mean_list": stf["mean_fg"], "mean_list_pruned": stf["mean_fg_pruned"], "rebuilds": stf["n_builds"]}
     ctx_stats = st1
