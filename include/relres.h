@@ -167,6 +167,8 @@ typedef struct relres_stats {
   double prune_delta;            /* pruning margin in Angstrom (0: pruning off) */
   long long n_prunes;            /* pruning passes since create (each build is followed by one) */
   double mean_fg_pruned, mean_cg_pruned;  /* mean pruned list length over all passes */
+  int step_segments;             /* 1: MD steps evaluate bonded terms per segment of whole molecules
+                                    inside the drift kernel; 0: separate bonded-term kernel */
 } relres_stats;
 
 /* Kernel classes of relres_get_timings. */

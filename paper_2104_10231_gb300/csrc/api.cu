@@ -1472,6 +1472,7 @@ relres_status relres_get_stats(relres_ctx* c, relres_stats* o) {
   o->has_cg = c->has_cg ? 1 : 0;
   o->n_launches = c->n_launches;
   o->prune_delta = c->prune_on ? c->prune_delta : 0.0;
+  o->step_segments = step_segments(c) ? 1 : 0;
   o->n_prunes = (long long)c->h_state->n_prunes;
   if (c->h_state->n_prunes > 0) {
     const double np = double(c->h_state->n_prunes);

@@ -243,3 +243,48 @@ def test_chains_longer_than_a_force_segment(torch, precision, f_tol, e_tol):
     s = S.block_copolymer(n_chain=12, n_bead=300, block=150, density=0.5)
     assert s.n_atoms == 3600
     _check_full(torch, s, precision, f_tol, e_tol)
+
+
+def _wrapped(a, b, L):
+    d = a - b
+    return d - L * np.round(d / L)
+
+
+@pytest.mark.parametrize("system,precision,segments", [
+    ("copolymer", R.RELRES_PREC_FP32, 1),  # dihedrals inside the segmented drift kernel
+    ("copolymer", R.RELRES_PREC_FP64, 1),
+    ("long_chains", R.RELRES_PREC_FP32, 0),  # 300-bead chains: no segment holds a molecule
+    ("long_chains", R.RELRES_PREC_FP64, 0),
+])
+def test_md_step_paths_track_the_oracle(torch, system, precision, segments):
+    # both MD step paths (bonded terms in the segmented drift kernel, or the
+    # separate bonded-term kernel + force sum + thermostat kernel) against the
+    # oracle's velocity Verlet + CSVR over 20 steps
+    if system == "copolymer":
+        s = S.block_copolymer(n_chain=20)
+    else:
+        s = S.block_copolymer(n_chain=12, n_bead=300, block=150, density=0.5)
+    ctx = R.Context(R.params_for(s, precision), R.topology_for(s))
+    p = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+    v = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+    ctx.build_neighbors(p, s.box)
+    th = torch.zeros((2, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+    ctx.step(20, 1.0, p, v, t_target=s.temperature, tau_fs=100.0, seed=5, thermo_every=10, d_thermo=th)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ctx.close()
+    assert st["step_segments"] == segments
+    tab = O.table_for(s)
+    po, vo, tho = O.md(s.pos, s.vel, s.box, s.masses, s.types, tab, s.n_types, s.excl, s.topo, 20, 1.0,
+                       t_target=s.temperature, tau=100.0, seed=5)
+    dx = float(np.abs(_wrapped(p.cpu().numpy(), po, s.box)).max())
+    dv = float(np.abs(v.cpu().numpy() - vo).max() / np.abs(vo).max())
+    ke = th.cpu().numpy()[-1, 3]
+    print(f"{system} prec={precision} segments={segments}: max |dx| {dx:.2e} A, dv {dv:.2e}, "
+          f"KE {ke:.6f} vs {tho[-1, 2]:.6f}")
+    if precision == R.RELRES_PREC_FP64:
+        assert dx < 1e-9 and dv < 1e-9
+        assert ke == pytest.approx(tho[-1, 2], rel=1e-9)
+    else:
+        assert dx < 1e-4 and dv < 1e-4
+        assert ke == pytest.approx(tho[-1, 2], rel=1e-5)
