@@ -233,6 +233,12 @@ def ours(args):
         dist.barrier()
     R.load()
 
+    # rates of this GPU (probe kernels of the library): FLOP side of the roofline
+    scratch = torch.empty(2 << 30, dtype=torch.uint8, device="cuda")
+    rates = R.relres_measure_rates(scratch)
+    del scratch
+    torch.cuda.empty_cache()
+
     s = S.neopentane(n_mol=args.n_mol, seed=2104 + rank, temperature=260.0)
     n = s.n_atoms
     dt, temp = 2.0, 260.0
@@ -357,6 +363,16 @@ def ours(args):
     alg_prune = full * 20.0 + walked * 4.0 + (n + n_h) * 44.0 + n * 16.0
     alg_bytes = (1.0 - p_prune) * alg_plain + p_prune * alg_prune
     achieved = alg_bytes / (pair_ms * 1e-3) / 1e9
+    # FLOP side (the method's roofline is the larger of the two fractions): ~10 FP32
+    # operations per list entry walked + ~30 per pair inside the cutoff
+    vol = float(s.box[0]) * float(s.box[1]) * float(s.box[2])
+    pairs_in = (4.0 * math.pi / 3.0) * (7.0 ** 3 * n * n / vol + 14.0 ** 3 * n_h * n_h / vol)
+    walked_entries = (1.0 - p_prune) * walked + p_prune * full
+    flops = 10.0 * walked_entries + 30.0 * pairs_in
+    flop_side = {"flops_per_launch": flops, "achieved_tflops": round(flops / (pair_ms * 1e-3) / 1e12, 3),
+                 "fp32_peak_tflops": round(rates["fp32_tflops"], 2),
+                 "frac": round(flops / (pair_ms * 1e-3) / 1e12 / rates["fp32_tflops"], 4),
+                 "peak_source": "measured here (FFMA probe, relres_measure_rates)"}
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": recorded_traffic(p_prune),
@@ -365,7 +381,8 @@ def ours(args):
                 "pruning_launch_fraction": p_prune,
                 "launches_timed": tim_pair["pair"][1],
                 "how": "CUDA events around the pair launch on 1 step in 10 of the timed region; bytes are "
-                       "the mean over plain launches (pruned lists) and pruning launches (full lists)"}
+                       "the mean over plain launches (pruned lists) and pruning launches (full lists)",
+                "flop_side": flop_side}
     kernel_ms = {k: round(v[0] / max(1, v[1]), 5) for k, v in tim.items()}
     kernel_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in tim.values())), 4) for k, v in tim.items()}
 
@@ -399,6 +416,7 @@ def ours(args):
         "pair_launch": {"threads_per_atom": ctx_stats["pair_tpa"], "block": ctx_stats["pair_block"],
                         "chosen_by": "autotuner (first relres_step)"},
         "gpu_launches": ctx_stats["n_launches"] - st0["n_launches"],
+        "device_rates": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in rates.items()},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": "atom-steps/s", "h2d_bytes_per_step": 2 * 24 * n,
                 "d2h_bytes_per_step": 2 * 24 * n,

@@ -382,6 +382,26 @@ relres_status relres_set_prune(relres_ctx* ctx, double delta);
  * replica (relres_batch_last_error).  Per-class kernel timing is not recorded
  * in batches.
  */
+/*
+ * Rates of the GPU this process runs on that the design of the library rests
+ * on (not part of the method): FP32 and FP64 fused multiply-adds and
+ * conversions from 64-bit integers to FP32 per clock per SM (issue-bound probe
+ * kernels with independent chains), and the bandwidth of a plain float4 copy
+ * from the first to the second half of d_scratch (count both the read and the
+ * written bytes).  d_scratch: caller-owned device memory, 16-byte aligned, at
+ * least 1 MiB and at least 2 KiB per SM; use a buffer well above the L2 size
+ * (e.g. 2 GiB) for the copy to measure DRAM.  Runs on cuda_stream (NULL: the
+ * default stream) and synchronises with it.  Errors: RELRES_ERR_ARG,
+ * RELRES_ERR_CUDA.
+ */
+typedef struct relres_rates {
+  double ffma_per_clk_sm, dfma_per_clk_sm, conv64_per_clk_sm;
+  double copy_gbs;
+  double fp32_tflops, fp64_tflops;  /* 2 flops per FMA at the SM count and the device's clock attribute */
+  int sm_count, clock_mhz;
+} relres_rates;
+relres_status relres_measure_rates(void* d_scratch, size_t scratch_bytes, void* cuda_stream, relres_rates* out);
+
 typedef struct relres_batch relres_batch;
 relres_status relres_batch_create(relres_batch** out, relres_ctx* const* ctxs, int n_ctx, void* cuda_stream);
 relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, double* const* d_pos,

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librelres.so")
-SOURCES = ["params.cpp", "neighbor.cu", "pair.cu", "md.cu", "api.cu", "noalloc.cu", "grad.cu"]
+SOURCES = ["params.cpp", "neighbor.cu", "pair.cu", "md.cu", "api.cu", "noalloc.cu", "grad.cu", "rates.cu"]
 HEADERS = ["relres_internal.h", "common.cuh", os.path.join("..", "..", "include", "relres.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -36,7 +36,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
             "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled",
-            "relres_set_list_caps", "relres_set_prune"]
+            "relres_set_list_caps", "relres_set_prune", "relres_measure_rates"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev", "prune"]
 
@@ -91,6 +91,12 @@ class relres_stats(C.Structure):
 _lib = None
 
 
+class relres_rates(C.Structure):
+    _fields_ = [("ffma_per_clk_sm", C.c_double), ("dfma_per_clk_sm", C.c_double),
+                ("conv64_per_clk_sm", C.c_double), ("copy_gbs", C.c_double), ("fp32_tflops", C.c_double),
+                ("fp64_tflops", C.c_double), ("sm_count", C.c_int), ("clock_mhz", C.c_int)]
+
+
 def load():
     """Load librelres.so from the package directory (raises if it is absent)."""
     global _lib
@@ -115,6 +121,7 @@ def load():
     L.relres_set_timing_sampled.argtypes = [vp, C.c_uint, C.c_int]
     L.relres_set_list_caps.argtypes = [vp, C.c_int, C.c_int]
     L.relres_set_prune.argtypes = [vp, C.c_double]
+    L.relres_measure_rates.argtypes = [vp, C.c_size_t, vp, C.POINTER(relres_rates)]
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
     L.relres_set_pair_config.argtypes = [vp, C.c_int]
@@ -250,6 +257,16 @@ def topology_for(system):
 
 
 # ------------------------------------------------------------- C entry points
+
+def relres_measure_rates(d_scratch, stream=None):
+    """Measured FP32/FP64 FMA and 64-bit conversion rates (per clock per SM)
+    and copy bandwidth of this GPU; d_scratch: a CUDA tensor (bytes), large."""
+    out = relres_rates()
+    nbytes = d_scratch.numel() * d_scratch.element_size()
+    st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(load().relres_measure_rates(_ptr(d_scratch), nbytes, st, C.byref(out)))
+    return {k: getattr(out, k) for k, _ in out._fields_}
+
 
 def relres_prepare_table(params):
     n = params.n_types * params.n_types * RELRES_PAIR_FIELDS

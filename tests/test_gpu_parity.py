@@ -351,3 +351,17 @@ def test_nonfinite_position_is_an_error(torch):
     # the context stays usable
     ctx.compute(p, f)
     ctx.close()
+
+
+def test_measured_device_rates_are_plausible(torch):
+    # the probe kernels behind the design choices and the FLOP side of the roofline
+    scratch = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    r = R.relres_measure_rates(scratch)
+    print(r)
+    assert r["sm_count"] > 0 and r["clock_mhz"] > 0
+    assert 32 <= r["ffma_per_clk_sm"] <= 160
+    assert 0 < r["dfma_per_clk_sm"] < r["ffma_per_clk_sm"]
+    assert 0 < r["conv64_per_clk_sm"] < r["ffma_per_clk_sm"]
+    assert 500 < r["copy_gbs"] < 20000
+    with pytest.raises(R.RelresError):
+        R.relres_measure_rates(scratch[:1024])  # too small
