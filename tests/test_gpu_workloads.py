@@ -288,3 +288,29 @@ def test_md_step_paths_track_the_oracle(torch, system, precision, segments):
     else:
         assert dx < 1e-4 and dv < 1e-4
         assert ke == pytest.approx(tho[-1, 2], rel=1e-5)
+
+
+@pytest.mark.parametrize("precision,f_tol,e_tol", [(R.RELRES_PREC_FP64, 1e-10, 1e-10),
+                                                   (R.RELRES_PREC_FP32, F_TOL, E_TOL)])
+def test_orthorhombic_box_with_unequal_edges(torch, precision, f_tol, e_tol):
+    # the neopentane liquid with its box and coordinates stretched by 1.25 along
+    # y and compressed by 0.9 along z: different cell counts and fixed-point
+    # scales per axis (forces, energies, virial and a short MD run)
+    base = S.neopentane(n_mol=1500, seed=41)
+    stretch = np.array([1.0, 1.25, 0.9])
+    s = base.subset_copy(pos=np.mod(base.pos * stretch, base.box * stretch), box=base.box * stretch,
+                         name="neopentane_orthorhombic")
+    _check_full(torch, s, precision, f_tol, e_tol)
+    ctx = R.Context(R.params_for(s, precision), R.topology_for(s))
+    p = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+    v = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+    ctx.build_neighbors(p, s.box)
+    st = ctx.stats()
+    assert len(set(st["grid_fg"])) > 1  # the cell grid differs per axis
+    ctx.step(20, 1.0, p, v)
+    torch.cuda.synchronize()
+    ctx.close()
+    po, vo, _ = O.md(s.pos, s.vel, s.box, s.masses, s.types, O.table_for(s), s.n_types, s.excl, s.topo, 20, 1.0)
+    dx = float(np.abs(_wrapped(p.cpu().numpy(), po, s.box)).max())
+    print(f"orthorhombic prec={precision}: grid {st['grid_fg']}, max |dx| after 20 steps {dx:.2e} A")
+    assert dx < (1e-9 if precision == R.RELRES_PREC_FP64 else 1e-4)
