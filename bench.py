@@ -567,11 +567,34 @@ def _oracle_rows_rate(s, seconds, rng_seed=0):
     return n_rows, el, cores
 
 
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(s, seconds):
     n_rows, el, cores = _oracle_rows_rate(s, seconds)
+    # the same oracle on one core, on a smaller sample
+    import numpy as np
+
+    from oracle import core as O
+
+    table = O.table_for(s)
+    rows1 = np.random.default_rng(3).choice(s.n_atoms, size=max(1, n_rows // max(1, cores) // 4), replace=False)
+    t0 = time.perf_counter()
+    O.pair_forces_rows(s.pos, s.box, s.types, table, s.n_types, rows1, s.excl, n_threads=1)
+    el1 = time.perf_counter() - t0
     return {"value": n_rows / el, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"FP64 all-pairs Eq. 20 force rows of {n_rows} random atoms of the "
-                      f"{s.n_atoms}-atom system ({el:.1f} s); one step needs all rows"}
+                      f"{s.n_atoms}-atom system ({el:.1f} s); one step needs all rows",
+            "single_core": {"value": len(rows1) / el1, "rows": int(len(rows1)), "seconds": round(el1, 2)},
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
 
 
 def reference(args):
