@@ -345,6 +345,18 @@ relres_status relres_set_graphs(relres_ctx* ctx, int enable);
 relres_status relres_set_list_caps(relres_ctx* ctx, int cap_fg, int cap_cg);
 
 /*
+ * Testing and inspection (slow, synchronous): the entries of one neighbour
+ * list as atom index pairs (i, j), i the list's owner, in list order.
+ * which: 0 FG list, 1 CG list, 2 pruned FG list, 3 pruned CG list (as the
+ * last build / pruning pass left them).  Writes min(*n_pairs, cap_pairs)
+ * pairs to the host arrays h_i, h_j (may be NULL when cap_pairs == 0) and
+ * the total count to *n_pairs.  Errors: RELRES_ERR_ARG, RELRES_ERR_STATE (no
+ * lists yet; a pruned list with pruning off).
+ */
+relres_status relres_get_list(relres_ctx* ctx, int which, int* h_i, int* h_j, long long cap_pairs,
+                              long long* n_pairs);
+
+/*
  * Dynamic pruning of the two lists (Section 2.6 keeps the lists; pruning is a
  * property of this implementation).  The lists hold every pair within the
  * interaction cutoff (r_s+ for the FG list, r_c+ for the CG list) + skin at

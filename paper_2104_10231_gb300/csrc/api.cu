@@ -727,6 +727,39 @@ relres_status relres_set_list_caps(relres_ctx* c, int cap_fg, int cap_cg) {
   return RELRES_OK;
 }
 
+relres_status relres_get_list(relres_ctx* c, int which, int* h_i, int* h_j, long long cap_pairs,
+                              long long* n_pairs) {
+  if (!c || !n_pairs || which < 0 || which > 3 || cap_pairs < 0 || (cap_pairs > 0 && (!h_i || !h_j)))
+    return RELRES_ERR_ARG;
+  if (!c->have_lists) return fail(c, RELRES_ERR_STATE, "relres_build_neighbors first");
+  const bool cg = (which & 1) != 0, pruned = which >= 2;
+  if (pruned && !c->prune_on) return fail(c, RELRES_ERR_STATE, "pruning is off");
+  const int nslots = cg ? ((c->has_cg && c->n_h > 0) ? c->n_h : 0) : c->n;
+  *n_pairs = 0;
+  if (nslots == 0) return RELRES_OK;
+  const int cap = cg ? c->cap_cg : c->cap_fg;
+  const int* d_nbr = pruned ? (cg ? c->d_nbr_cg_in : c->d_nbr_fg_in) : (cg ? c->d_nbr_cg : c->d_nbr_fg);
+  const int* d_cnt = pruned ? (cg ? c->d_cnt_cg_in : c->d_cnt_fg_in) : (cg ? c->d_cnt_cg : c->d_cnt_fg);
+  const int* d_perm = cg ? c->d_perm_cg : c->d_perm_fg;
+  const size_t ns = static_cast<size_t>(nslots);
+  std::vector<int> cnt(ns), perm(ns), nbr(static_cast<size_t>(cap) * ns);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(cnt.data(), d_cnt, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(perm.data(), d_perm, sizeof(int) * perm.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(nbr.data(), d_nbr, sizeof(int) * nbr.size(), cudaMemcpyDeviceToHost));
+  long long k = 0;
+  for (int sl = 0; sl < nslots; ++sl)
+    for (int e = 0; e < std::min(cnt[sl], cap); ++e, ++k) {
+      if (k < cap_pairs) {
+        const int j = nbr[(size_t(e >> 2) * nslots + sl) * 4 + (e & 3)];
+        h_i[k] = perm[sl];
+        h_j[k] = (j >= 0 && j < nslots) ? perm[j] : -1;
+      }
+    }
+  *n_pairs = k;
+  return RELRES_OK;
+}
+
 relres_status relres_set_prune(relres_ctx* c, double delta) {
   if (!c || !std::isfinite(delta)) return RELRES_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));

@@ -36,7 +36,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
             "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled",
-            "relres_set_list_caps", "relres_set_prune", "relres_measure_rates"]
+            "relres_set_list_caps", "relres_set_prune", "relres_measure_rates", "relres_get_list"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev", "prune"]
 
@@ -122,6 +122,7 @@ def load():
     L.relres_set_list_caps.argtypes = [vp, C.c_int, C.c_int]
     L.relres_set_prune.argtypes = [vp, C.c_double]
     L.relres_measure_rates.argtypes = [vp, C.c_size_t, vp, C.POINTER(relres_rates)]
+    L.relres_get_list.argtypes = [vp, C.c_int, _ip, _ip, C.c_longlong, C.POINTER(C.c_longlong)]
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
     L.relres_set_pair_config.argtypes = [vp, C.c_int]
@@ -430,6 +431,19 @@ class Context:
 
     def set_list_caps(self, cap_fg, cap_cg):
         _check(load().relres_set_list_caps(self.ctx, int(cap_fg), int(cap_cg)), self.ctx)
+
+    def get_list(self, which):
+        """Entries of one list as an (n, 2) int array of atom pairs (i, j):
+        which = 0 FG, 1 CG, 2 pruned FG, 3 pruned CG."""
+        import numpy as np
+
+        n = C.c_longlong(0)
+        _check(load().relres_get_list(self.ctx, int(which), None, None, 0, C.byref(n)), self.ctx)
+        pi = np.zeros(max(1, n.value), dtype=np.int32)
+        pj = np.zeros(max(1, n.value), dtype=np.int32)
+        _check(load().relres_get_list(self.ctx, int(which), pi.ctypes.data_as(_ip), pj.ctypes.data_as(_ip),
+                                      n.value, C.byref(n)), self.ctx)
+        return np.stack([pi[: n.value], pj[: n.value]], axis=1)
 
     def set_prune(self, delta):
         """Pruning margin of the lists in Angstrom (<= 0: no pruning)."""
