@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-fg-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable (backward) leg")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the full-step timings of the two small systems (GPU and oracle)")
     ap.add_argument("--batch-replicas", type=int, default=128,
                     help="replicas of the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=200)
@@ -429,11 +431,52 @@ def ours(args):
         out["batched"] = batched_leg(torch, R, S, args.batch_replicas, args.batch_steps)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
+    if rank == 0 and world == 1 and not args.no_small:
+        out["small_systems"] = small_systems_leg(torch, R, S, with_oracle=not args.no_cpu)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def small_systems_leg(torch, R, S, with_oracle=True):
+    """Full MD steps of the two small systems the parity tests use: 216
+    propane-like molecules (648 atoms, FP64, NVE, dt 1 fs) and 4000
+    neopentane-like molecules (20 000 atoms, FP32, CSVR 260 K, dt 2 fs), on
+    the GPU (CUDA events around relres_step) and, for the same systems, the
+    oracle's own velocity Verlet over all host cores (whole steps, O(N^2))."""
+    out = {}
+    cases = (("propane_648_fp64_nve", S.propane(), R.RELRES_PREC_FP64, 0.0, 1000, 100),
+             ("neopentane_20000_fp32_csvr", S.neopentane(n_mol=4000, seed=2104), R.RELRES_PREC_FP32, 260.0, 1000, 2))
+    for name, s, prec, temp, gpu_steps, cpu_steps in cases:
+        ctx = R.Context(R.params_for(s, prec), R.topology_for(s))
+        pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+        vel = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+        ctx.build_neighbors(pos, s.box)
+        ctx.step(100, s.dt, pos, vel, t_target=temp, tau_fs=100.0, seed=3)  # warm-up, graphs captured
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ctx.step(gpu_steps, s.dt, pos, vel, t_target=temp, tau_fs=100.0, seed=4)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ctx.close()
+        row = {"n_atoms": s.n_atoms, "steps": gpu_steps, "gpu_ms_per_step": ms / gpu_steps,
+               "gpu_atom_steps_per_s": s.n_atoms * gpu_steps / (ms * 1e-3)}
+        if with_oracle:
+            from oracle import core as O
+
+            O.build_oracle()
+            t0 = time.perf_counter()
+            O.md(s.pos, s.vel, s.box, s.masses, s.types, O.table_for(s), s.n_types, s.excl, s.topo, cpu_steps,
+                 s.dt, t_target=temp, tau=100.0, seed=4)
+            el = time.perf_counter() - t0
+            row.update({"oracle_steps": cpu_steps, "oracle_ms_per_step": el / cpu_steps * 1e3,
+                        "oracle_atom_steps_per_s": s.n_atoms * cpu_steps / el, "oracle_cores": os.cpu_count()})
+        out[name] = row
+    return out
 
 
 def batched_leg(torch, R, S, n_rep, steps, seed=4242):

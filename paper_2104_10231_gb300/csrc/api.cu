@@ -1124,6 +1124,7 @@ static relres_status step_begin(relres_ctx* c, int n_steps, double dt_fs, double
   sp.tau = tau_fs;
   sp.n_f = 3.0 * c->n - 3.0;
   sp.kt = 0.5 * sp.n_f * kBoltz * t_target;
+  sp.csvr_e = std::exp(-dt_fs / tau_fs);
   sp.seed = seed;
   sp.thermo_every = (d_thermo && thermo_every > 0) ? thermo_every : 0;
   sp.thermo = sp.thermo_every ? d_thermo : nullptr;

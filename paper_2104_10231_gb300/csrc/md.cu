@@ -84,6 +84,19 @@ __device__ __forceinline__ void scatter_sorted(int i, int t, unsigned long long 
   }
 }
 
+// The same with the atom's slots given (sc < 0: no CG slot).
+__device__ __forceinline__ void scatter_sorted_at(int sf, int sc, int t, unsigned long long x, unsigned long long y,
+                                                  unsigned long long z, int4* pos_fg, int4* pos_cg, int fp64,
+                                                  Pos64* pos_fg64, Pos64* pos_cg64) {
+  const int4 h = make_int4(hi32(x), hi32(y), hi32(z), t);
+  pos_fg[sf] = h;
+  if (fp64) pos_fg64[sf] = Pos64{(long long)x, (long long)y, (long long)z, t};
+  if (sc >= 0) {
+    pos_cg[sc] = h;
+    if (fp64) pos_cg64[sc] = Pos64{(long long)x, (long long)y, (long long)z, t};
+  }
+}
+
 __device__ __forceinline__ bool moved_beyond(int4 ref, unsigned long long x, unsigned long long y,
                                              unsigned long long z, Sc3<float> s, float thr2) {
   const float dx = dfix32(hi32(x), ref.x, s.s0);
@@ -663,12 +676,26 @@ struct DriftArgs {
 
 // One atom of the drift: u <- a u + b c F, x <- x + dt u, the sorted copies
 // of x, and the two displacement triggers.  Returns the new position in x.
+// Every load of the atom is issued before its first store, so that no load
+// waits behind a store to memory the compiler cannot tell apart from it.
 template <typename R>
 __device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, unsigned long long x[3], bool& rebuild,
                                            bool& reprune) {
   const int t = a.type[i];
   R f[3];
   load_force(a.f_tot, i, f);
+  VelT<R> v[3];
+  unsigned long long x0[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    v[q] = a.vel[3 * i + q];
+    x0[q] = a.xfx[3 * i + q];
+  }
+  const int sf = a.rank_fg[i];
+  const int sc = a.with_cg ? a.rank_cg[i] : -1;
+  const int4 ref = a.ref[i];
+  const int4 ref_p = a.prune ? a.ref_p[i] : make_int4(0, 0, 0, 0);
+  VelT<R> un[3];
   if constexpr (std::is_same<R, float>::value) {
     // float-float: u <- a u + b c F and the increment u dt 2^64 / L, with no
     // FP64 instruction (FP64 runs at a small fraction of the FP32 rate here)
@@ -678,11 +705,9 @@ __device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, unsigne
     const ff dts[3] = {ff{a.dts0h, a.dts0l}, ff{a.dts1h, a.dts1l}, ff{a.dts2h, a.dts2l}};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const float2 v = a.vel[3 * i + q];
-      const ff u = ff_add(ff_mul(ca, ff{v.x, v.y}), ff_mul_f(bc, f[q]));
-      a.vel[3 * i + q] = make_float2(u.hi, u.lo);
-      x[q] = a.xfx[3 * i + q] + (unsigned long long)ff2ll(ff_mul(u, dts[q]));
-      a.xfx[3 * i + q] = x[q];
+      const ff u = ff_add(ff_mul(ca, ff{v[q].x, v[q].y}), ff_mul_f(bc, f[q]));
+      un[q] = make_float2(u.hi, u.lo);
+      x[q] = x0[q] + (unsigned long long)ff2ll(ff_mul(u, dts[q]));
     }
   } else {
     const double ca = a.st->a, cb = a.st->b;
@@ -691,16 +716,19 @@ __device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, unsigne
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       // the kick increment in the force's precision, accumulated in FP64
-      const double u = fma(ca, a.vel[3 * i + q], double(bc * f[q]));
-      a.vel[3 * i + q] = u;
-      x[q] = a.xfx[3 * i + q] + (unsigned long long)__double2ll_rn(u * dts[q]);
-      a.xfx[3 * i + q] = x[q];
+      const double u = fma(ca, v[q], double(bc * f[q]));
+      un[q] = u;
+      x[q] = x0[q] + (unsigned long long)__double2ll_rn(u * dts[q]);
     }
   }
-  scatter_sorted(i, t, x[0], x[1], x[2], a.rank_fg, a.rank_cg, a.with_cg, a.pos_fg, a.pos_cg, a.fp64,
-                 a.pos_fg64, a.pos_cg64);
-  rebuild = moved_beyond(a.ref[i], x[0], x[1], x[2], a.s32, a.thr2);
-  if (a.prune) reprune = moved_beyond(a.ref_p[i], x[0], x[1], x[2], a.s32, a.thr2_p);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    a.vel[3 * i + q] = un[q];
+    a.xfx[3 * i + q] = x[q];
+  }
+  scatter_sorted_at(sf, sc, t, x[0], x[1], x[2], a.pos_fg, a.pos_cg, a.fp64, a.pos_fg64, a.pos_cg64);
+  rebuild = moved_beyond(ref, x[0], x[1], x[2], a.s32, a.thr2);
+  if (a.prune) reprune = moved_beyond(ref_p, x[0], x[1], x[2], a.s32, a.thr2_p);
 }
 
 template <typename R>
@@ -739,7 +767,7 @@ struct DriftSegArgs {
 };
 
 template <typename R, bool EV>
-__global__ void __launch_bounds__(kSegAtoms, std::is_same<R, float>::value ? 6 * kThreads / kSegAtoms : 1)
+__global__ void __launch_bounds__(kSegAtoms, std::is_same<R, float>::value ? 5 * kThreads / kSegAtoms : 1)
     k_drift_seg(DriftSegArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* sx = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSegAtoms][3]
@@ -860,8 +888,8 @@ __device__ void csvr_draws(double n_f, unsigned long long seed, unsigned long lo
   r1 = gauss(seed, c);
   s = 2.0 * gamma_mt(0.5 * (n_f - 1.0), seed, c);
 }
-__device__ double csvr_alpha(double ke, double dt, double tau, double n_f, double kt, double r1, double s) {
-  const double e = exp(-dt / tau);
+// e = exp(-dt / tau), computed once per call on the host
+__device__ double csvr_alpha(double ke, double e, double n_f, double kt, double r1, double s) {
   const double kn = ke + (1.0 - e) * (kt / n_f * (r1 * r1 + s) - ke) +
                     2.0 * r1 * sqrt(e * (1.0 - e) * ke * kt / n_f);
   return sqrt(kn / ke);
@@ -882,11 +910,11 @@ __global__ void k_csvr_draws(double n_f, unsigned long long seed, int count, con
 // thermo row on energy steps, counters, and the accumulators cleared for the
 // next step.  `draw` points at this step's (r1, s).  The accumulators are read
 // through volatile loads (other blocks of the calling kernel added to them).
-__device__ void end_of_step(volatile long long* acc, const StepParams& sp, DevState* st, const double* draw) {
+__device__ void end_of_step(volatile long long* acc, const StepParams& sp, DevState* st, double r1, double s) {
   const bool ev = st->ev != 0;
   const double ke = double(acc[kAccKe]) / kFix;
   double alpha = 1.0;
-  if (sp.t_target > 0.0 && ke > 0.0) alpha = csvr_alpha(ke, sp.dt, sp.tau, sp.n_f, sp.kt, draw[0], draw[1]);
+  if (sp.t_target > 0.0 && ke > 0.0) alpha = csvr_alpha(ke, sp.csvr_e, sp.n_f, sp.kt, r1, s);
   st->alpha = alpha;
   st->a = alpha;
   st->b = alpha + 1.0;
@@ -917,7 +945,7 @@ __device__ void end_of_step(volatile long long* acc, const StepParams& sp, DevSt
 }
 
 __global__ void k_thermo(long long* acc, StepParams sp, DevState* st, const double* draw) {
-  end_of_step(acc, sp, st, draw);
+  end_of_step(acc, sp, st, sp.t_target > 0.0 ? draw[0] : 0.0, sp.t_target > 0.0 ? draw[1] : 0.0);
 }
 
 // ---- end of a step with bonded forces from k_drift_seg: per atom the total
@@ -946,23 +974,40 @@ struct SumArgs {
   const double* draw;
 };
 
+// The inputs of one atom of the force sum.
 template <typename R>
-__device__ __forceinline__ R sum_atom(const SumArgs<R>& a, int i, bool& bad) {
-  const int t = a.type[i];
+struct SumIn {
+  int t;
   R f[3], h[3], b[3];
-  load_force(a.f_fg, i, f);
+  VelT<R> v[3];
+};
+
+template <typename R>
+__device__ __forceinline__ void sum_load(const SumArgs<R>& a, int i, SumIn<R>& in) {
+  in.t = a.type[i];
+  load_force(a.f_fg, i, in.f);
   // the CG part is zero for ordinary atoms (never written): loaded without
   // waiting for the type, added only for hybrids
-  if (a.with_cg) load_force(a.f_cg, i, h);
-  load_force(a.f_bond, i, b);
+  if (a.with_cg) load_force(a.f_cg, i, in.h);
+  load_force(a.f_bond, i, in.b);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) in.v[q] = a.vel[3 * i + q];
+}
+
+// F = F_FG + F_CG + F_bonded of one atom, stored; returns the kinetic energy
+// of u + c F.
+template <typename R>
+__device__ __forceinline__ R sum_atom(const SumArgs<R>& a, int i, SumIn<R>& in, bool& bad) {
+  const int t = in.t;
+  R* f = in.f;
   if (a.with_cg && ((a.hyb_mask >> t) & 1)) {
-    f[0] += h[0];
-    f[1] += h[1];
-    f[2] += h[2];
+    f[0] += in.h[0];
+    f[1] += in.h[1];
+    f[2] += in.h[2];
   }
-  f[0] += b[0];
-  f[1] += b[1];
-  f[2] += b[2];
+  f[0] += in.b[0];
+  f[1] += in.b[1];
+  f[2] += in.b[2];
   bad |= !(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]));
   save_force(a.f_tot, i, f);
   R c, kc;
@@ -976,7 +1021,7 @@ __device__ __forceinline__ R sum_atom(const SumArgs<R>& a, int i, bool& bad) {
   R v2 = R(0);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const R v = vel_r(a.vel, 3 * i + q) + c * f[q];
+    const R v = vel_r(&in.v[q], 0) + c * f[q];
     v2 += v * v;
   }
   return kc * v2;
@@ -986,16 +1031,29 @@ __device__ __forceinline__ R sum_atom(const SumArgs<R>& a, int i, bool& bad) {
 // ticket per block
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_sum(SumArgs<R> a) {
+  // this step's thermostat draws, read early (the last block uses them)
+  double r1 = 0.0, rs = 0.0;
+  if (threadIdx.x == 0 && a.sp.t_target > 0.0) {
+    r1 = a.draw[0];
+    rs = a.draw[1];
+  }
   R ke = R(0);  // a few atoms per thread
   bool bad = false;
   const int stride = gridDim.x * blockDim.x;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + stride < a.n; i += 2 * stride) {  // two atoms in flight
-    const R k0 = sum_atom(a, i, bad);
-    const R k1 = sum_atom(a, i + stride, bad);
+  for (; i + stride < a.n; i += 2 * stride) {  // two atoms in flight: both loaded before either store
+    SumIn<R> in0, in1;
+    sum_load(a, i, in0);
+    sum_load(a, i + stride, in1);
+    const R k0 = sum_atom(a, i, in0, bad);
+    const R k1 = sum_atom(a, i + stride, in1, bad);
     ke += k0 + k1;
   }
-  if (i < a.n) ke += sum_atom(a, i, bad);
+  if (i < a.n) {
+    SumIn<R> in;
+    sum_load(a, i, in);
+    ke += sum_atom(a, i, in, bad);
+  }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&a.st->flags, F_NONFINITE);
   double v[1] = {double(ke)};
   __shared__ double sh_k[kThreads / 32];
@@ -1007,7 +1065,7 @@ __global__ void __launch_bounds__(kThreads) k_sum(SumArgs<R> a) {
     if (ticket == gridDim.x - 1) {
       __threadfence();
       a.st->done_blocks = 0u;
-      end_of_step(a.acc, a.sp, a.st, a.draw);
+      end_of_step(a.acc, a.sp, a.st, r1, rs);
     }
   }
 }
@@ -1372,7 +1430,7 @@ static cudaError_t launch_sum_t(relres_ctx* c, const StepParams& sp, int k, cons
   }
   a.draw = c->d_draws + 2 * k;
   // one wave of resident blocks (44 registers a thread: five blocks per SM)
-  const int nb = std::max(1, std::min((c->n + kThreads - 1) / kThreads, 152 * 5));
+  const int nb = std::max(1, std::min((c->n + kThreads - 1) / kThreads, 152 * 4));  // one wave (56 registers)
   k_sum<R><<<nb, kThreads, 0, c->stream>>>(a);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();

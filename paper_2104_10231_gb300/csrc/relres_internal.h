@@ -134,6 +134,7 @@ struct Pos64 {  // FP64 mode sorted position: 64-bit fixed-point x, y, z and typ
 struct StepParams {
   double dt;
   double t_target, tau, n_f, kt;  // CSVR
+  double csvr_e;                  // exp(-dt / tau)
   unsigned long long seed;
   int thermo_every;
   double* thermo;  // device [rows][RELRES_THERMO_COLS] or null
