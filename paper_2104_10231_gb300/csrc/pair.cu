@@ -59,11 +59,26 @@ __device__ __forceinline__ int ptype(const Pos64& p) { return int(p.t); }
 __device__ __forceinline__ int4 load_pos(const int4* p, int j) { return __ldg(p + j); }
 __device__ __forceinline__ Pos64 load_pos(const Pos64* p, int j) { return p[j]; }
 
+// 1/x in FP32: the hardware estimate (rcp.approx, about one ulp) refined by
+// one Newton-Raphson step y + y (1 - x y), which leaves about one ulp as well.
+// The correctly rounded __frcp_rn costs several more instructions plus a
+// special-case branch; in the pair kernel's LJ core that was 12 % of the
+// forces-only launch time.  The padding distance (3e38) gives 0.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_nr(float x) {
+  const float y = rcp_approx(x);
+  return fmaf(y, fmaf(-x, y, 1.f), y);
+}
+
 // FP64 1/x and 1/sqrt(x) from the FP32 hardware estimate plus one Newton
-// step (relative error ~1e-14; FP64 division and square root are many times
+// step (relative error ~1e-13; FP64 division and square root are many times
 // slower on this part).
 __device__ __forceinline__ double rcp_d(double x) {
-  const double y = double(__frcp_rn(float(x)));
+  const double y = double(rcp_approx(float(x)));
   return y * fma(-x, y, 2.0);
 }
 __device__ __forceinline__ double rsqrt_d(double x) {
@@ -71,7 +86,7 @@ __device__ __forceinline__ double rsqrt_d(double x) {
   return y * fma(-0.5 * x * y, y, 1.5);
 }
 
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float recip(float x) { return rcp_nr(x); }
 __device__ __forceinline__ double recip(double x) { return rcp_d(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt_d(x); }
@@ -136,15 +151,13 @@ __device__ __forceinline__ bool cg_term(const PairTab<R>& T, R r2, R& fr, R& ep)
 // FP32 force coefficients of one type pair, packed for 16-byte shared-memory
 // loads (built in shared memory from PairTab<float> at kernel start).
 struct FgRow {
-  float4 a;  // r_s-^2, r_s+^2, 48 eps sig^12, 24 eps sig^6
+  float4 a;  // 4 g4, r_s+^2, 48 eps sig^12, 24 eps sig^6
   float4 b;  // r_s-, derivative of f_{s-}^{FG}: g1, 2 g2, 3 g3
-  float4 c;  // 4 g4, -, -, -
 };
 struct CgRow {
-  float4 a;  // r_s-^2, r_s+^2, r_c-^2, r_c+^2
-  float4 b;  // r_s-, 3 gamma_3+, 4 gamma_4+, r_c-
-  float4 c;  // 48 eps sig^12, 24 eps sig^6 (CG), derivative of f_{c-}^{CG}: g1, 2 g2
-  float4 d;  // 3 g3, 4 g4, -, -
+  float4 a;  // r_s+^2, r_c+^2, r_s-, r_c-
+  float4 b;  // 3 gamma_3+, 4 gamma_4+, 48 eps sig^12, 24 eps sig^6 (CG)
+  float4 c;  // derivative of f_{c-}^{CG}: g1, 2 g2, 3 g3, 4 g4
 };
 
 // Energy constants of one type pair for the FP32 path (energy steps) as
@@ -216,48 +229,52 @@ __device__ __forceinline__ ff cg_energy_ff(const CgE& T, float4 radii2, ff r2) {
 }
 
 __device__ __forceinline__ void pack_rows(const PairTab<float>& t, FgRow& f, CgRow& g) {
-  f.a = make_float4(t.rsm2, t.rsp2, t.f12f, t.f6f);
+  f.a = make_float4(t.fgd[3], t.rsp2, t.f12f, t.f6f);
   f.b = make_float4(t.rsm, t.fgd[0], t.fgd[1], t.fgd[2]);
-  f.c = make_float4(t.fgd[3], 0.f, 0.f, 0.f);
-  g.a = make_float4(t.rsm2, t.rsp2, t.rcm2, t.rcp2);
-  g.b = make_float4(t.rsm, t.ond3, t.ond4, t.rcm);
-  g.c = make_float4(t.f12c, t.f6c, t.cgod[0], t.cgod[1]);
-  g.d = make_float4(t.cgod[2], t.cgod[3], 0.f, 0.f);
+  g.a = make_float4(t.rsp2, t.rcp2, t.rsm, t.rcm);
+  g.b = make_float4(t.ond3, t.ond4, t.f12c, t.f6c);
+  g.c = make_float4(t.cgod[0], t.cgod[1], t.cgod[2], t.cgod[3]);
 }
 
 // -dU/dr / r of the FG part, every region evaluated and the right one
-// selected (same arithmetic as fg_term<float>).  r2 >= r_s+^2 gives 0.
+// selected (the arithmetic of fg_term, the LJ core chosen by the sign of
+// r - r_s-).  r2 >= r_s+^2 gives 0.
 __device__ __forceinline__ float fg_force(const FgRow& T, float r2) {
   const float4 a = T.a, b = T.b;
-  const float g4 = T.c.x;
-  const float r2i = __frcp_rn(r2);
+  const float g4 = a.x;
+  const float r2i = rcp_nr(r2);
   const float r6i = r2i * r2i * r2i;
   const float flj = r6i * (a.z * r6i - a.w) * r2i;
   const float ri = rsqrtf(r2);
   const float d = r2 * ri - b.x;
   const float fp = ((g4 * d + b.w) * d + b.z) * d + b.y;
   const float fsh = -fp * ri;
-  const float fr = r2 < a.x ? flj : fsh;
+  const float fr = d < 0.f ? flj : fsh;  // r < r_s-: LJ core
   return r2 < a.y ? fr : 0.f;
 }
 
-// -dU/dr / r of the CG part (same arithmetic as cg_term<float>): zero below
+// -dU/dr / r of the CG part (the arithmetic of cg_term, the regions below
+// r_s- and r_c- chosen by the signs of r - r_s- and r - r_c-): zero below
 // r_s- (the constant region) and from r_c+ on.
 __device__ __forceinline__ float cg_force(const CgRow& T, float r2) {
   const float4 a = T.a, b = T.b, c = T.c;
-  const float2 dd = make_float2(T.d.x, T.d.y);
   const float ri = rsqrtf(r2);
   const float r = r2 * ri;
-  const float d = r - b.x;
-  const float fon = -(d * d * (b.z * d + b.y)) * ri;
+  const float d = r - a.z;
+  const float fon = -(d * d * (b.y * d + b.x)) * ri;
   const float r2i = ri * ri;
   const float r6i = r2i * r2i * r2i;
-  const float flj = r6i * (c.x * r6i - c.y) * r2i;
-  const float e = r - b.w;
-  const float foff = -(((dd.y * e + dd.x) * e + c.w) * e + c.z) * ri;
-  float fr = r2 < a.z ? flj : foff;
-  fr = r2 < a.y ? fon : fr;
-  return (r2 < a.x || !(r2 < a.w)) ? 0.f : fr;
+  const float flj = r6i * (b.z * r6i - b.w) * r2i;
+  const float e = r - a.w;
+  const float foff = -(((c.w * e + c.z) * e + c.y) * e + c.x) * ri;
+  float fr = e < 0.f ? flj : foff;
+  fr = r2 < a.x ? fon : fr;
+  return (d < 0.f || !(r2 < a.y)) ? 0.f : fr;
+}
+
+// (r_s-^2, r_s+^2, r_c-^2, r_c+^2) of a CG row, for the energy regions
+__device__ __forceinline__ float4 cg_radii2(const CgRow& T) {
+  return make_float4(T.a.z * T.a.z, T.a.x, T.a.w * T.a.w, T.a.y);
 }
 
 template <typename R>
@@ -336,14 +353,14 @@ __device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typenam
       // float-float energy inside the cutoff only (padding entries carry
       // r2 = 3e38; the energy and its slope vanish at the cutoff, so the FP32
       // decision is harmless), from the exact integer coordinate differences
-      const float rcut2 = CG ? S.cgr[row].a.w : S.fgr[row].a.y;
+      const float rcut2 = CG ? S.cgr[row].a.y : S.fgr[row].a.y;
       if (r2 < rcut2) {
         const ff ex = ff_fixed_diff32(pi.x, pj.x, ff{a.sx, a.sxl});
         const ff ey = ff_fixed_diff32(pi.y, pj.y, ff{a.sy, a.syl});
         const ff ez = ff_fixed_diff32(pi.z, pj.z, ff{a.sz, a.szl});
         const ff r2e = ff_add(ff_add(ff_mul(ex, ex), ff_mul(ey, ey)), ff_mul(ez, ez));
-        A.eff = ff_add(A.eff, CG ? cg_energy_ff(S.cge[row], S.cgr[row].a, r2e)
-                                 : fg_energy_ff(S.fge[row], S.fgr[row].a.x, r2e));
+        A.eff = ff_add(A.eff, CG ? cg_energy_ff(S.cge[row], cg_radii2(S.cgr[row]), r2e)
+                                 : fg_energy_ff(S.fge[row], S.fgr[row].b.x * S.fgr[row].b.x, r2e));
       }
     }
     return r2;
