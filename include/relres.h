@@ -414,6 +414,19 @@ typedef struct relres_rates {
 } relres_rates;
 relres_status relres_measure_rates(void* d_scratch, size_t scratch_bytes, void* cuda_stream, relres_rates* out);
 
+/*
+ * Testing (synchronous): the reciprocals the pair kernels use in place of
+ * correctly rounded division, on n inputs d_x[k] (device, FP64):
+ *   d_out32[k]    = 1/x in FP32: hardware estimate of 1/float(x) plus one
+ *                   Newton-Raphson step (results below the smallest normal
+ *                   float are 0);
+ *   d_out64[k]    = 1/x in FP64, and d_out64[n + k] = 1/sqrt(x): FP32
+ *                   estimate plus one FP64 Newton-Raphson step.
+ * d_out32 holds n floats, d_out64 2n doubles (device, caller-owned).
+ * Errors: RELRES_ERR_ARG (null pointer, n < 0), RELRES_ERR_CUDA.
+ */
+relres_status relres_eval_recip(const double* d_x, float* d_out32, double* d_out64, int n, void* cuda_stream);
+
 typedef struct relres_batch relres_batch;
 relres_status relres_batch_create(relres_batch** out, relres_ctx* const* ctxs, int n_ctx, void* cuda_stream);
 relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, double* const* d_pos,

@@ -205,4 +205,33 @@ __device__ __forceinline__ void acc_add(long long* acc, double v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)to_fix_sum(v));
 }
 
+// 1/x in FP32: the hardware estimate (rcp.approx, about one ulp) refined by
+// one Newton-Raphson step y + y (1 - x y), which leaves about one ulp as well.
+// The correctly rounded __frcp_rn costs several more instructions plus a
+// special-case branch; in the pair kernel's LJ core that was 12 % of the
+// forces-only launch time.  Results below the smallest normal float are
+// flushed to 0 (the pair kernel's padding distance, 3e38, gives 0).
+// relres_eval_recip evaluates these functions for the tests.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_nr(float x) {
+  const float y = rcp_approx(x);
+  return fmaf(y, fmaf(-x, y, 1.f), y);
+}
+
+// FP64 1/x and 1/sqrt(x) from the FP32 hardware estimate plus one Newton
+// step (relative error ~1e-13; FP64 division and square root are many times
+// slower on this part).
+__device__ __forceinline__ double rcp_d(double x) {
+  const double y = double(rcp_approx(float(x)));
+  return y * fma(-x, y, 2.0);
+}
+__device__ __forceinline__ double rsqrt_d(double x) {
+  const double y = double(rsqrtf(float(x)));
+  return y * fma(-0.5 * x * y, y, 1.5);
+}
+
 }  // namespace relres

@@ -59,33 +59,6 @@ __device__ __forceinline__ int ptype(const Pos64& p) { return int(p.t); }
 __device__ __forceinline__ int4 load_pos(const int4* p, int j) { return __ldg(p + j); }
 __device__ __forceinline__ Pos64 load_pos(const Pos64* p, int j) { return p[j]; }
 
-// 1/x in FP32: the hardware estimate (rcp.approx, about one ulp) refined by
-// one Newton-Raphson step y + y (1 - x y), which leaves about one ulp as well.
-// The correctly rounded __frcp_rn costs several more instructions plus a
-// special-case branch; in the pair kernel's LJ core that was 12 % of the
-// forces-only launch time.  The padding distance (3e38) gives 0.
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rcp_nr(float x) {
-  const float y = rcp_approx(x);
-  return fmaf(y, fmaf(-x, y, 1.f), y);
-}
-
-// FP64 1/x and 1/sqrt(x) from the FP32 hardware estimate plus one Newton
-// step (relative error ~1e-13; FP64 division and square root are many times
-// slower on this part).
-__device__ __forceinline__ double rcp_d(double x) {
-  const double y = double(rcp_approx(float(x)));
-  return y * fma(-x, y, 2.0);
-}
-__device__ __forceinline__ double rsqrt_d(double x) {
-  const double y = double(rsqrtf(float(x)));
-  return y * fma(-0.5 * x * y, y, 1.5);
-}
-
 __device__ __forceinline__ float recip(float x) { return rcp_nr(x); }
 __device__ __forceinline__ double recip(double x) { return rcp_d(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }

@@ -9,6 +9,7 @@
 // of the measured instruction decides the time.
 #include <cuda_runtime.h>
 
+#include "common.cuh"
 #include "relres_internal.h"
 
 namespace relres {
@@ -62,6 +63,16 @@ __global__ void k_rate_conv64(long long seed, float* out) {
 __global__ void k_rate_copy(const float4* __restrict__ src, float4* __restrict__ dst, size_t n) {
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
     dst[i] = src[i];
+}
+
+__global__ void k_eval_recip(const double* __restrict__ x, float* __restrict__ out32,
+                             double* __restrict__ out64, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double v = x[k];
+    out32[k] = rcp_nr(float(v));
+    out64[k] = rcp_d(v);
+    out64[n + k] = rsqrt_d(v);
+  }
 }
 
 // milliseconds of one launch (after one warm-up launch)
@@ -136,5 +147,16 @@ extern "C" relres_status relres_measure_rates(void* d_scratch, size_t scratch_by
   out->clock_mhz = clk_khz / 1000;
   out->fp32_tflops = out->ffma_per_clk_sm * 2.0 * per_sm_clk / 1e12;
   out->fp64_tflops = out->dfma_per_clk_sm * 2.0 * per_sm_clk / 1e12;
+  return RELRES_OK;
+}
+
+extern "C" relres_status relres_eval_recip(const double* d_x, float* d_out32, double* d_out64, int n,
+                                           void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_out32 || !d_out64))) return RELRES_ERR_ARG;
+  if (n == 0) return RELRES_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int blocks = (n + kRateThreads - 1) / kRateThreads;
+  k_eval_recip<<<blocks < 1024 ? blocks : 1024, kRateThreads, 0, st>>>(d_x, d_out32, d_out64, n);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return RELRES_ERR_CUDA;
   return RELRES_OK;
 }

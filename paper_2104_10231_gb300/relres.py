@@ -36,7 +36,8 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
             "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled",
-            "relres_set_list_caps", "relres_set_prune", "relres_measure_rates", "relres_get_list"]
+            "relres_set_list_caps", "relres_set_prune", "relres_measure_rates", "relres_get_list",
+            "relres_eval_recip"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev", "prune"]
 
@@ -123,6 +124,7 @@ def load():
     L.relres_set_prune.argtypes = [vp, C.c_double]
     L.relres_measure_rates.argtypes = [vp, C.c_size_t, vp, C.POINTER(relres_rates)]
     L.relres_get_list.argtypes = [vp, C.c_int, _ip, _ip, C.c_longlong, C.POINTER(C.c_longlong)]
+    L.relres_eval_recip.argtypes = [vp, vp, vp, C.c_int, vp]
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
     L.relres_set_pair_config.argtypes = [vp, C.c_int]
@@ -267,6 +269,13 @@ def relres_measure_rates(d_scratch, stream=None):
     st = C.c_void_p(stream.cuda_stream) if stream is not None else None
     _check(load().relres_measure_rates(_ptr(d_scratch), nbytes, st, C.byref(out)))
     return {k: getattr(out, k) for k, _ in out._fields_}
+
+
+def relres_eval_recip(d_x, d_out32, d_out64, stream=None):
+    """The pair kernels' reciprocals on the FP64 CUDA tensor d_x (n): FP32 1/x
+    into d_out32 (n floats), FP64 1/x and 1/sqrt(x) into d_out64 (2n)."""
+    st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(load().relres_eval_recip(_ptr(d_x), _ptr(d_out32), _ptr(d_out64), int(d_x.numel()), st))
 
 
 def relres_prepare_table(params):
