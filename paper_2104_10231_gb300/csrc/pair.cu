@@ -250,6 +250,8 @@ __device__ __forceinline__ float4 cg_radii2(const CgRow& T) {
   return make_float4(T.a.z * T.a.z, T.a.x, T.a.w * T.a.w, T.a.y);
 }
 
+constexpr int kSmallGridSMs = 152;  // SMs of the part
+
 template <typename R>
 struct ListWalk {
   int nslots;
@@ -574,6 +576,11 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
     tpa = kPairConfigs[c->pair_cfg].tpa;
     bs = kPairConfigs[c->pair_cfg].bs;
   }
+  // FP64 runs at under 2 FMA per clock per SM on this part: a system with
+  // fewer 256-slot blocks than SMs spreads its slots over more SMs in 32-slot
+  // blocks (one thread per slot either way, so the forces are the same bits)
+  const bool fp64_small = !std::is_same<R, float>::value && (c->n + kThreads - 1) / kThreads < kSmallGridSMs;
+  if (fp64_small) bs = 32;
   a.prune_on = (c->prune_on && tpa == 1) ? 1 : 0;
   const int per = bs / tpa;  // slots per block
   const int nb_fg = do_fg ? (c->n + per - 1) / per : 0;
@@ -581,7 +588,14 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   if (nb_fg + nb_cg == 0) return cudaSuccess;
   a.nblk_cg = nb_cg;
   const int grid = nb_cg + nb_fg;
-  if (ev) {
+  if (fp64_small) {
+    if constexpr (!std::is_same<R, float>::value) {
+      if (ev)
+        k_pair<R, true, 1, 32><<<grid, 32, smem, c->stream>>>(a);
+      else
+        k_pair<R, false, 1, 32><<<grid, 32, smem, c->stream>>>(a);
+    }
+  } else if (ev) {
     k_pair<R, true, 1, kThreads><<<grid, kThreads, smem, c->stream>>>(a);
   } else if (!std::is_same<R, float>::value) {
     k_pair<R, false, 1, kThreads><<<grid, kThreads, smem, c->stream>>>(a);
