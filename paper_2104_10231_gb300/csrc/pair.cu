@@ -569,8 +569,9 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
     a.cg = a.fg;
   }
   const size_t smem = pair_smem<R>(c->n_types, ev);
-  // energy steps and FP64: one thread per slot, 256 per block; forces-only
-  // FP32: the autotuned (threads per slot, block size)
+  // energy steps and FP64: one thread per slot, 256 per block (32 for small
+  // FP64 systems, below); forces-only FP32: the autotuned (threads per slot,
+  // block size)
   int tpa = 1, bs = kThreads;
   if (std::is_same<R, float>::value && !ev) {
     tpa = kPairConfigs[c->pair_cfg].tpa;
