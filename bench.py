@@ -405,6 +405,7 @@ def ours(args):
         "ns_per_day": dt * 1e-6 * (args.steps / secs) * 86400.0,
         "fg_only": fg,
         "speedup_vs_fg_only": (value / fg["value"]) if fg else None,
+        "eq21": efficiency_eq21(fg, pair_ms, ms_step, full / n, walked / n) if fg else None,
         "roofline": roofline,
         "kernel_ms_per_launch": kernel_ms,
         "kernel_time_share": kernel_share,
@@ -438,6 +439,26 @@ def ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def efficiency_eq21(fg, pair_ms, step_ms, entries_full, entries_walked):
+    """The paper's efficiency analysis (Section 2.6): the pair-time speedup
+    against the FG reference, eta~* = 1 / tau~*, set beside 1 / N* (Eq. 21),
+    N* the RelRes list size over the reference's, per atom; and the total
+    speedup eta*_tot beside chi / N* (Eq. 22), which gives chi.  N* is given
+    for the lists with the skin (the paper's list size) and for the pruned
+    lists the pair kernel walks."""
+    try:
+        n_full = entries_full / fg["mean_list"]
+        n_walked = entries_walked / fg["mean_list_pruned"]
+        eta_pair = fg["pair_ms_per_launch"] / pair_ms
+        eta_tot = fg["ms_per_step"] / step_ms
+        return {"n_star_lists": round(n_full, 4), "n_star_walked": round(n_walked, 4),
+                "one_over_n_star_lists": round(1.0 / n_full, 3), "one_over_n_star_walked": round(1.0 / n_walked, 3),
+                "eta_pair": round(eta_pair, 3), "eta_pair_times_n_star_walked": round(eta_pair * n_walked, 3),
+                "eta_tot": round(eta_tot, 3), "chi_walked": round(eta_tot * n_walked, 3)}
+    except (KeyError, TypeError, ZeroDivisionError):
+        return None
 
 
 def small_systems_leg(torch, R, S, with_oracle=True):

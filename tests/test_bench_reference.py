@@ -36,3 +36,15 @@ def test_reference_arm_other_ranks_do_nothing():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [x for x in r.stdout.splitlines() if x.startswith("{")]
+
+
+def test_efficiency_against_eq21():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    fg = {"mean_list": 409.5, "mean_list_pruned": 304.3, "pair_ms_per_launch": 0.736, "ms_per_step": 1.05}
+    e = bench.efficiency_eq21(fg, 0.162, 0.317, 85.8, 52.5)
+    assert abs(e["n_star_walked"] - 52.5 / 304.3) < 1e-4 and abs(e["n_star_lists"] - 85.8 / 409.5) < 1e-4
+    assert abs(e["eta_pair"] - 0.736 / 0.162) < 1e-3 and abs(e["eta_tot"] - 1.05 / 0.317) < 1e-3
+    assert abs(e["chi_walked"] - e["eta_tot"] * e["n_star_walked"]) < 2e-3
+    assert bench.efficiency_eq21({}, 0.1, 0.3, 1.0, 1.0) is None
