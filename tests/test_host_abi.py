@@ -127,3 +127,38 @@ def test_invalid_parameters_are_rejected(lib, bad):
     with pytest.raises(R.RelresError) as ei:
         R.relres_prepare_table(p)
     assert ei.value.status == 1
+
+
+def test_null_handles_and_bad_arguments_fail_before_any_cuda_call(lib):
+    # every entry point checks its handle and arguments first: these calls
+    # return RELRES_ERR_ARG (or a message) on a machine without a GPU
+    import ctypes as C
+
+    ERR = 1  # RELRES_ERR_ARG
+    n = C.c_longlong(0)
+    st = R.relres_stats()
+    assert lib.relres_get_list(None, 0, None, None, 0, C.byref(n)) == ERR
+    assert lib.relres_set_prune(None, 0.5) == ERR
+    assert lib.relres_set_pair_config(None, 0) == ERR
+    assert lib.relres_set_graphs(None, 1) == ERR
+    assert lib.relres_set_list_caps(None, 8, 8) == ERR
+    assert lib.relres_set_timing(None, 1) == ERR
+    assert lib.relres_set_timing_sampled(None, 1, 1) == ERR
+    assert lib.relres_get_stats(None, C.byref(st)) == ERR
+    assert lib.relres_build_neighbors(None, None, None) == ERR
+    assert lib.relres_compute(None, None, None, None, None) == ERR
+    assert lib.relres_step(None, 1, 1.0, None, None, 0.0, 100.0, 0, 0, None) == ERR
+    assert lib.relres_set_step_counter(None, 0) == ERR
+    assert lib.relres_backward(None, None, None, 0.0, None, None, None, None, None, None) == ERR
+    assert lib.relres_set_topology(None, None) == ERR
+    assert lib.relres_set_params(None, None) == ERR
+    assert lib.relres_batch_step(None, 1, 1.0, None, None, None, 100.0, None, 0, None) == ERR
+    assert lib.relres_measure_rates(None, 0, None, None) == ERR
+    assert lib.relres_eval_recip(None, None, None, 4, None) == ERR
+    assert lib.relres_eval_recip(None, None, None, -1, None) == ERR
+    assert lib.relres_eval_recip(None, None, None, 0, None) == R.RELRES_OK
+    assert lib.relres_create(None, None, None) == ERR
+    assert lib.relres_last_error(None) == b"null context"
+    assert lib.relres_batch_last_error(None) == b"null batch"
+    lib.relres_destroy(None)
+    lib.relres_batch_destroy(None)
