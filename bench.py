@@ -97,10 +97,12 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(p_prune):
-    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
-    was taken on the current pair.cu (sha256 prefix recorded there): the mean
-    over plain launches and pruning launches (a fraction p_prune)."""
+def recorded_pair_counters(p_prune):
+    """ncu counters of one pair-kernel launch from the committed summary, if
+    it was taken on the current pair.cu (sha256 prefix recorded there): DRAM
+    bytes and warp instructions executed, each the mean over plain launches
+    and pruning launches (a fraction p_prune)."""
+    out = {}
     try:
         src_sha = hashlib.sha256(open(PAIR_SRC, "rb").read()).hexdigest()[:16]
         vals = {}
@@ -109,12 +111,15 @@ def recorded_traffic(p_prune):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
         if vals.get("pair_cu_sha256_16") != src_sha:
-            return None
-        plain = float(vals["dram_bytes_plain_launch_full_size"])
-        prune = float(vals["dram_bytes_pruning_launch_full_size"])
-        return (1.0 - p_prune) * plain + p_prune * prune
+            return out
+        for key, name in (("dram_bytes", "dram_bytes_%s_launch_full_size"),
+                          ("inst_executed", "inst_executed_%s_launch_full_size")):
+            if name % "plain" in vals and name % "pruning" in vals:
+                out[key] = ((1.0 - p_prune) * float(vals[name % "plain"]) +
+                            p_prune * float(vals[name % "pruning"]))
     except Exception:
-        return None
+        pass
+    return out
 
 
 class ClockSampler:
@@ -257,20 +262,21 @@ def ours(args):
         if args.equil:
             ctx.step(args.equil, dt, pos, vel, t_target=temp, tau_fs=100.0, seed=7)
         ctx.step(args.warmup, dt, pos, vel, t_target=temp, tau_fs=100.0, seed=8)
-        torch.cuda.synchronize()
-        # inside the timed region only the pair kernel is timed, on 1 step in 10
-        # (event records in the step graphs cost microseconds each)
-        ctx.set_timing_sampled(["pair", "pair_ev"], 10)
-        # the 100-step graph of the timed run is captured here, not in the timed region
-        run_md_timed(torch, R, ctx, pos, vel, 100, dt, temp, 9, args.thermo_every)
-        ctx.set_timing_sampled(["pair", "pair_ev"], 10)  # clears the warm-up's totals
+        # the timed call, untimed once: every block shape it runs (blocks of 100
+        # steps and the remainder) is captured and instantiated here, so no graph
+        # capture falls inside the timed region
+        ctx.set_timing(False)
+        run_md_timed(torch, R, ctx, pos, vel, args.steps, dt, temp, 9, args.thermo_every)
         st0 = ctx.stats()
         if dist:
             dist.barrier()
         with ClockSampler(local) as clk:
             secs = run_md_timed(torch, R, ctx, pos, vel, args.steps, dt, temp, 9, args.thermo_every)
         st1 = ctx.stats()
-        tim_pair = ctx.timings()
+        # roofline pass: every forces-only pair launch of ROOF_STEPS further steps
+        # timed with CUDA events (no energy steps, so every launch is of that
+        # class); the bytes are weighted by the pruning launches of the same pass
+        roof = pair_pass(torch, R, ctx, pos, vel, dt, temp)
         # every kernel class timed on every step: a separate, shorter run
         ctx.set_timing(True)
         run_md_timed(torch, R, ctx, pos, vel, min(200, args.steps), dt, temp, 10, args.thermo_every)
@@ -326,65 +332,34 @@ def ours(args):
             velf = vel.clone()
             ctxf.build_neighbors(posf, s.box)
             ctxf.step(args.warmup, dt, posf, velf, t_target=temp, tau_fs=100.0, seed=8)
-            torch.cuda.synchronize()
-            ctxf.set_timing_sampled(["pair", "pair_ev"], 10)
-            run_md_timed(torch, R, ctxf, posf, velf, 100, dt, temp, 9, args.thermo_every)
-            ctxf.set_timing_sampled(["pair", "pair_ev"], 10)
+            run_md_timed(torch, R, ctxf, posf, velf, args.steps, dt, temp, 9, args.thermo_every)  # captures
             if dist:
                 dist.barrier()
             secs_f = run_md_timed(torch, R, ctxf, posf, velf, args.steps, dt, temp, 9, args.thermo_every)
-            timf = ctxf.timings()
-            stf = ctxf.stats()
             secs_f = max_over_ranks(dist, secs_f)
+            roof_f = pair_pass(torch, R, ctxf, posf, velf, dt, temp)
+            stf = ctxf.stats()
             ctxf.close()
         fg = {"value": whole_job_rate(world, n, args.steps, secs_f), "ms_per_step": secs_f / args.steps * 1e3,
-              "pair_ms_per_launch": timf["pair"][0] / max(1, timf["pair"][1]),
-              "mean_list": stf["mean_fg"], "mean_list_pruned": stf["mean_fg_pruned"], "rebuilds": stf["n_builds"]}
+              "pair_ms_per_launch": roof_f["ms_per_launch"], "pair_launches_timed": roof_f["launches"],
+              "pruning_launch_fraction": roof_f["p_prune"],
+              "mean_list": stf["mean_fg"], "mean_list_pruned": roof_f["mean_fg_walked"], "rebuilds": stf["n_builds"]}
     ctx_stats = st1
     ctx.close()
 
     # roofline of the dominant kernel: the RelRes pair kernel (FG and CG lists,
     # one launch) as it runs on every step that needs no energy
-    pair_ms = tim_pair["pair"][0] / max(1, tim_pair["pair"][1])
     n_h = ctx_stats["n_hybrid"]
     prunes = ctx_stats["n_prunes"] - st0["n_prunes"]
     full = ctx_stats["mean_fg"] * n + ctx_stats["mean_cg"] * n_h
-    if args.prune > 0 and prunes > 0:
-        # entries the pair kernel walked: the pruned lists of the passes in the
-        # timed region, except on pruning steps (a fraction p_prune of the
-        # launches), which walk the full lists and write the pruned ones
-        mean_fg = (ctx_stats["mean_fg_pruned"] * ctx_stats["n_prunes"] - st0["mean_fg_pruned"] * st0["n_prunes"]) / prunes
-        mean_cg = (ctx_stats["mean_cg_pruned"] * ctx_stats["n_prunes"] - st0["mean_cg_pruned"] * st0["n_prunes"]) / prunes
-        p_prune = prunes / args.steps
-    else:
-        mean_fg, mean_cg, p_prune = ctx_stats["mean_fg"], ctx_stats["mean_cg"], 0.0
-    walked = mean_fg * n + mean_cg * n_h
-    # 4 B index + 16 B gather per entry; per slot 16 B position, 4 B count, 4 B slot map, 16 B force;
-    # a pruning launch also writes 4 B per kept entry, 4 B per slot count and 16 B per atom reference
-    alg_plain = walked * 20.0 + (n + n_h) * 40.0
-    alg_prune = full * 20.0 + walked * 4.0 + (n + n_h) * 44.0 + n * 16.0
-    alg_bytes = (1.0 - p_prune) * alg_plain + p_prune * alg_prune
-    achieved = alg_bytes / (pair_ms * 1e-3) / 1e9
-    # FLOP side (the method's roofline is the larger of the two fractions): ~10 FP32
-    # operations per list entry walked + ~30 per pair inside the cutoff
-    vol = float(s.box[0]) * float(s.box[1]) * float(s.box[2])
-    pairs_in = (4.0 * math.pi / 3.0) * (7.0 ** 3 * n * n / vol + 14.0 ** 3 * n_h * n_h / vol)
-    walked_entries = (1.0 - p_prune) * walked + p_prune * full
-    flops = 10.0 * walked_entries + 30.0 * pairs_in
-    flop_side = {"flops_per_launch": flops, "achieved_tflops": round(flops / (pair_ms * 1e-3) / 1e12, 3),
-                 "fp32_peak_tflops": round(rates["fp32_tflops"], 2),
-                 "frac": round(flops / (pair_ms * 1e-3) / 1e12 / rates["fp32_tflops"], 4),
-                 "peak_source": "measured here (FFMA probe, relres_measure_rates)"}
-    peak, peak_kind = peaks()
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(p_prune),
-                "peak_source": peak_kind + " (hbm_gbs, copy)", "kernel": "k_pair<float, forces only> (FG + CG lists)",
-                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": pair_ms,
-                "pruning_launch_fraction": p_prune,
-                "launches_timed": tim_pair["pair"][1],
-                "how": "CUDA events around the pair launch on 1 step in 10 of the timed region; bytes are "
-                       "the mean over plain launches (pruned lists) and pruning launches (full lists)",
-                "flop_side": flop_side}
+    walked = roof["mean_fg_walked"] * n + roof["mean_cg_walked"] * n_h
+    pair_ms = roof["ms_per_launch"]
+    p_prune = roof["p_prune"]
+    alg_bytes = pair_alg_bytes(n, n_h, roof["mean_fg_full"] * n + roof["mean_cg_full"] * n_h, walked, p_prune)
+    clk_sum = clk.summary()
+    roofline = pair_roofline(alg_bytes, pair_ms, p_prune, peaks(), rates, clk_sum, n, n_h, walked,
+                             roof["mean_fg_full"] * n + roof["mean_cg_full"] * n_h, float(s.box[0]) ** 3)
+    roofline["launches_timed"] = roof["launches"]
     kernel_ms = {k: round(v[0] / max(1, v[1]), 5) for k, v in tim.items()}
     kernel_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in tim.values())), 4) for k, v in tim.items()}
 
@@ -410,17 +385,20 @@ def ours(args):
         "kernel_ms_per_launch": kernel_ms,
         "kernel_time_share": kernel_share,
         "kernel_breakdown_run": f"{min(200, args.steps)} further steps with every kernel class timed (events slow "
-                                "the steps by ~8 %, so the headline run times the pair kernel only)",
+                                "the steps by ~8 %, so the headline run records no events inside its steps)",
         "lists": {"mean_fg": ctx_stats["mean_fg"], "mean_cg": ctx_stats["mean_cg"],
                   "cap_fg": ctx_stats["cap_fg"], "cap_cg": ctx_stats["cap_cg"],
                   "rebuilds_in_timed_region": ctx_stats["n_builds"] - st0["n_builds"],
+                  "rebuild_ms_per_step": kernel_ms.get("rebuild"),
+                  "rebuild_share_of_step": kernel_share.get("rebuild"),
+                  "rebuilds_per_step_long_run": roof["rebuilds"] / ROOF_STEPS,
                   "prune_delta": ctx_stats["prune_delta"], "prunes_in_timed_region": prunes,
-                  "mean_fg_walked": mean_fg, "mean_cg_walked": mean_cg},
+                  "mean_fg_walked": roof["mean_fg_walked"], "mean_cg_walked": roof["mean_cg_walked"]},
         "pair_launch": {"threads_per_atom": ctx_stats["pair_tpa"], "block": ctx_stats["pair_block"],
                         "chosen_by": "autotuner (first relres_step)"},
         "gpu_launches": ctx_stats["n_launches"] - st0["n_launches"],
         "device_rates": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in rates.items()},
-        "clocks": clk.summary(),
+        "clocks": clk_sum,
         "e2e": {"value": e2e_value, "unit": "atom-steps/s", "h2d_bytes_per_step": 2 * 24 * n,
                 "d2h_bytes_per_step": 2 * 24 * n,
                 "steps": ke, "how": "relres_step(1) per step with H2D/D2H of positions+velocities (pinned; the two "
@@ -439,6 +417,86 @@ def ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+ROOF_STEPS = 300
+
+
+def pair_pass(torch, R, ctx, pos, vel, dt, temp, steps=ROOF_STEPS):
+    """ROOF_STEPS MD steps with a CUDA-event pair around every forces-only pair
+    launch (no energy steps).  The launches that prune (rebuild or pruning
+    trigger) walk the full lists, the others the pruned lists of the last
+    pass; the pass reports the mean time per launch, the fraction of pruning
+    launches and the list sizes of the same launches."""
+    st_a = ctx.stats()
+    ctx.set_timing_sampled(["pair"], 1)
+    run_md_timed(torch, R, ctx, pos, vel, steps, dt, temp, 11, 0)
+    tim = ctx.timings()
+    st_b = ctx.stats()
+    ctx.set_timing(False)
+    prunes = st_b["n_prunes"] - st_a["n_prunes"]
+    if st_b["prune_delta"] > 0 and prunes > 0:
+        mfg = (st_b["mean_fg_pruned"] * st_b["n_prunes"] - st_a["mean_fg_pruned"] * st_a["n_prunes"]) / prunes
+        mcg = (st_b["mean_cg_pruned"] * st_b["n_prunes"] - st_a["mean_cg_pruned"] * st_a["n_prunes"]) / prunes
+        p_prune = prunes / steps
+    else:
+        mfg, mcg, p_prune = st_b["mean_fg"], st_b["mean_cg"], 0.0
+    launches = tim["pair"][1]
+    return {"ms_per_launch": tim["pair"][0] / max(1, launches), "launches": launches, "p_prune": p_prune,
+            "mean_fg_walked": mfg, "mean_cg_walked": mcg, "mean_fg_full": st_b["mean_fg"],
+            "mean_cg_full": st_b["mean_cg"], "rebuilds": st_b["n_builds"] - st_a["n_builds"]}
+
+
+def pair_alg_bytes(n, n_h, full, walked, p_prune):
+    """Algorithmic bytes of one forces-only pair launch, the mean over plain
+    launches (pruned lists: 4 B index + 16 B gathered position per entry; per
+    slot 16 B own position, 4 B count, 4 B slot map, 16 B force) and pruning
+    launches (full lists, plus 4 B per kept entry, 4 B per slot count and
+    16 B per atom of the pruning reference)."""
+    alg_plain = walked * 20.0 + (n + n_h) * 40.0
+    alg_prune = full * 20.0 + walked * 4.0 + (n + n_h) * 44.0 + n * 16.0
+    return (1.0 - p_prune) * alg_plain + p_prune * alg_prune
+
+
+def pair_roofline(alg_bytes, pair_ms, p_prune, peak_info, rates, clk, n, n_h, walked, full, vol):
+    """Roofline record of the pair kernel.  frac: algorithmic bytes over HBM
+    copy bandwidth (gathers are L1/L2 hits, so it can pass 1); dram_frac:
+    measured DRAM bytes per launch over the same peak; issue_frac: warp
+    instructions per launch over the issue peak (one per clock per scheduler,
+    4 per SM); flop_side: FP32 FLOPs over the FFMA peak."""
+    peak, peak_kind = peak_info
+    secs = pair_ms * 1e-3
+    achieved = alg_bytes / secs / 1e9
+    rec = recorded_pair_counters(p_prune)
+    traffic = rec.get("dram_bytes")
+    insts = rec.get("inst_executed")
+    mhz = (clk or {}).get("sm_mhz") or rates.get("clock_mhz")
+    sms = rates.get("sm_count") or 152
+    pairs_in = (4.0 * math.pi / 3.0) * (7.0 ** 3 * n * n / vol + 14.0 ** 3 * n_h * n_h / vol)
+    walked_entries = (1.0 - p_prune) * walked + p_prune * full
+    flops = 10.0 * walked_entries + 30.0 * pairs_in
+    flop_side = {"flops_per_launch": flops, "achieved_tflops": flops / secs / 1e12,
+                 "fp32_peak_tflops": rates["fp32_tflops"],
+                 "frac": flops / secs / 1e12 / rates["fp32_tflops"],
+                 "peak_source": "measured here (FFMA probe, relres_measure_rates)"}
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_source": peak_kind + " (hbm_gbs, copy)",
+           "kernel": "k_pair<float, forces only> (FG + CG lists)",
+           "alg_bytes_per_launch": alg_bytes, "ms_per_launch": pair_ms, "pruning_launch_fraction": p_prune,
+           "how": "frac = alg_bytes_per_launch / (ms_per_launch * 1e-3) / 1e9 / peak; every forces-only pair "
+                  "launch of a separate 300-step pass timed with CUDA events on the context stream, bytes "
+                  "weighted by that pass's pruning launches (full lists) and plain launches (pruned lists)",
+           "flop_side": flop_side}
+    if traffic is not None:
+        out["dram_frac"] = traffic / secs / 1e9 / peak
+        out["dram_how"] = ("traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, plain and "
+                           "pruning launches weighted alike) / (ms_per_launch * 1e-3) / 1e9 / peak")
+    if insts is not None and mhz:
+        out["issue_frac"] = insts / (secs * mhz * 1e6 * sms * 4)
+        out["inst_executed_per_launch"] = insts
+        out["issue_how"] = (f"inst_executed_per_launch (ncu smsp__inst_executed.sum) / (ms_per_launch * 1e-3 * "
+                            f"{mhz:.0f} MHz * {sms} SMs * 4 schedulers)")
+    return out
 
 
 def efficiency_eq21(fg, pair_ms, step_ms, entries_full, entries_walked):

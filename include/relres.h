@@ -205,9 +205,12 @@ relres_status relres_cg_params(int n_types, const double* eps_fg, const double* 
                                double* eps_cg, double* sig_cg);
 
 /*
- * Create a context on the current CUDA device.  cuda_stream is a
- * cudaStream_t (NULL = legacy default stream).  The context owns every
- * internal device buffer and frees it in relres_destroy.
+ * Create a context on the current CUDA device for the lj/relres pair style of
+ * Section 2.5: its parameters (FG eps and sigma per type, the hybrid flag, CG
+ * eps and sigma per hybrid pair or Eq. 13 from group compositions) and the
+ * four radii in the order r_s- <= r_s+ <= r_c- <= r_c+ the style requires.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).  The context
+ * owns every internal device buffer and frees it in relres_destroy.
  * Errors: RELRES_ERR_ARG (invalid parameters, as relres_prepare_table),
  * RELRES_ERR_CUDA, RELRES_ERR_NOMEM.  *out is NULL on failure.
  */
@@ -219,9 +222,10 @@ relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda
 relres_status relres_set_topology(relres_ctx* ctx, const relres_topology* t);
 
 /*
- * Bin atoms into cells and build both Verlet lists (the FG list over all
- * atoms within max r_s+ + skin, the CG list over hybrid sites within max r_c+
- * + skin_cg), with exclusions removed.  d_pos: [n_atoms*3] device doubles, any
+ * Bin atoms into cells and build both Verlet lists -- the two neighbour lists
+ * of Section 2.6 that give RelRes its speed: the FG list over all atoms within
+ * max r_s+ + skin, and the CG list over hybrid sites within max r_c+ +
+ * skin_cg -- with exclusions removed.  d_pos: [n_atoms*3] device doubles, any
  * periodic image.  box: host double[3], orthorhombic edge lengths.
  * Sets the box used by later calls.  Synchronises the stream.
  * The CG skin is clamped to L/2 - r_c+ - 1e-6 when the box is small
@@ -249,8 +253,9 @@ relres_status relres_compute(relres_ctx* ctx, const double* d_pos, double* d_for
                              double* d_energy, double* d_virial);
 
 /*
- * n_steps of velocity Verlet (dt_fs) on d_pos/d_vel [n_atoms*3] (device,
- * updated in place; positions are returned wrapped into [0, L)).  Velocities
+ * Molecular dynamics in the canonical ensemble, as the simulations of Section
+ * 3.2 run it: n_steps of velocity Verlet (dt_fs) on d_pos/d_vel [n_atoms*3]
+ * (device, updated in place; positions are returned wrapped into [0, L)).  Velocities
  * are A/fs.  Lists are rebuilt on the device whenever an atom has moved more
  * than skin/2.  t_target > 0 applies the CSVR thermostat (Bussi, Donadio &
  * Parrinello 2007) with time constant tau_fs after each step, N_f = 3N - 3,
@@ -497,10 +502,15 @@ relres_status relres_get_timings(relres_ctx* ctx, double* ms, long long* counts,
  *   cuda_stream    cudaStream_t the work is enqueued on.
  * All calls on a GPU share the static array: calls whose work overlaps on the
  * GPU race on it and must be serialised by the caller.  Each call rewrites
- * every part of it that it reads.  The first call on each device (with that
- * device current) looks up the array's address; make that first call before
- * any stream capture begins.  O(n_atoms^2) work: meant for small systems.
- * Errors: RELRES_ERR_ARG, RELRES_ERR_BOX, RELRES_ERR_CUDA.
+ * every part of it that it reads and clears its bad-type flag first.  The
+ * first call on each device (with that device current) looks up the array's
+ * address; that first call should come before any stream capture.
+ * Atom types are read on the device only: a type outside [0, n_types) is
+ * never used to index the parameter table; that atom's forces and the
+ * energy and virial of the call are written as NaN instead.  O(n_atoms^2)
+ * work: meant for small systems.
+ * Errors: RELRES_ERR_ARG, RELRES_ERR_BOX, RELRES_ERR_CUDA (returned for a
+ * failure of this call's own copies or launches only).
  */
 #define RELRES_STATIC_MAX_ATOMS 16384
 relres_status relres_pair_forces_static(const relres_params* p, int n_atoms, const int* d_type,

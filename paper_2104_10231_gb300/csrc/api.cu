@@ -789,10 +789,16 @@ relres_status relres_set_pair_config(relres_ctx* c, int config) {
 // rebuild kernels gated on the device flag) or into a CUDA graph (the
 // rebuild of each step behind a conditional node).
 
+static void drop_one_graph(relres_ctx::StepGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (cudaEvent_t e : g.events) cudaEventDestroy(e);
+  g = relres_ctx::StepGraph{};
+}
+
 static void drop_step_graph(relres_ctx* c) {
-  if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
-  for (cudaEvent_t e : c->sg.events) cudaEventDestroy(e);
-  c->sg = relres_ctx::StepGraph{};
+  for (relres_ctx::StepGraph& g : c->sgs) drop_one_graph(g);
+  c->sgs.clear();
+  c->sg_cur = -1;
 }
 
 // A conditional (IF) node added to the graph being captured on c->stream
@@ -910,16 +916,36 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
 
 // Instantiated graph for this block (re-captured when an input changed).
 static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_vel, int blk, int done) {
-  relres_ctx::StepGraph& g = c->sg;
   const int phase = sp.thermo_every > 0 ? done % sp.thermo_every : 0;
   const int t_phase = done % c->timing_every;
-  if (g.valid && g.blk == blk && g.ev_phase == phase && g.thermo_every == sp.thermo_every &&
-      g.t_mask == c->timing_mask && g.t_every == c->timing_every && g.t_phase == t_phase &&
-      g.timing == int(c->timing) && g.pair_cfg == c->pair_cfg && g.dt == sp.dt && g.t_target == sp.t_target && g.tau == sp.tau &&
-      g.n_f == sp.n_f && g.kt == sp.kt && g.seed == sp.seed && g.vel == d_vel && g.thermo == sp.thermo &&
-      g.gen == c->buf_gen)
-    return RELRES_OK;
-  drop_step_graph(c);
+  for (size_t k = 0; k < c->sgs.size(); ++k) {
+    const relres_ctx::StepGraph& g = c->sgs[k];
+    if (g.valid && g.blk == blk && g.ev_phase == phase && g.thermo_every == sp.thermo_every &&
+        g.t_mask == c->timing_mask && g.t_every == c->timing_every && g.t_phase == t_phase &&
+        g.timing == int(c->timing) && g.pair_cfg == c->pair_cfg && g.dt == sp.dt && g.t_target == sp.t_target &&
+        g.tau == sp.tau && g.n_f == sp.n_f && g.kt == sp.kt && g.seed == sp.seed && g.vel == d_vel &&
+        g.thermo == sp.thermo && g.gen == c->buf_gen) {
+      c->sg_cur = int(k);
+      c->sgs[k].last_use = ++c->sg_clock;
+      return RELRES_OK;
+    }
+  }
+  // a free slot: graphs of reallocated buffers first, else the least recently used
+  int slot = -1;
+  for (size_t k = 0; k < c->sgs.size() && slot < 0; ++k)
+    if (!c->sgs[k].valid || c->sgs[k].gen != c->buf_gen) slot = int(k);
+  if (slot < 0 && int(c->sgs.size()) < relres_ctx::kMaxStepGraphs) {
+    c->sgs.emplace_back();
+    slot = int(c->sgs.size()) - 1;
+  }
+  if (slot < 0) {
+    slot = 0;
+    for (size_t k = 1; k < c->sgs.size(); ++k)
+      if (c->sgs[k].last_use < c->sgs[slot].last_use) slot = int(k);
+  }
+  c->sg_cur = -1;
+  drop_one_graph(c->sgs[slot]);
+  relres_ctx::StepGraph& g = c->sgs[slot];
   if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   if (!c->body_stream) CK(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking));
   if (c->timing) {
@@ -950,7 +976,7 @@ static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_v
   }
   if (graph) cudaGraphDestroy(graph);
   if (s != RELRES_OK) {
-    drop_step_graph(c);
+    drop_one_graph(g);
     return s;
   }
   // kernels: per step the rebuild body holds 6 (5 binning stages + lists),
@@ -976,6 +1002,8 @@ static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_v
   g.vel = d_vel;
   g.thermo = sp.thermo;
   g.gen = c->buf_gen;
+  g.last_use = ++c->sg_clock;
+  c->sg_cur = slot;
   return RELRES_OK;
 }
 
@@ -1164,10 +1192,11 @@ static relres_status block_end(relres_ctx* c, double* d_pos, double* d_vel, doub
   s = flush_timing(c);
   if (s != RELRES_OK) return s;
   if (graph) {
-    c->n_launches += c->sg.k_parent + c->sg.k_body * std::max(0LL, c->h_state->n_builds - builds0) +
-                     c->sg.k_prune * std::max(0LL, (long long)c->h_state->n_prunes - prunes0);
+    const relres_ctx::StepGraph& sg = c->sgs[c->sg_cur];
+    c->n_launches += sg.k_parent + sg.k_body * std::max(0LL, c->h_state->n_builds - builds0) +
+                     sg.k_prune * std::max(0LL, (long long)c->h_state->n_prunes - prunes0);
     if (c->timing)
-      for (const relres_ctx::Mark& m : c->sg.marks) {
+      for (const relres_ctx::Mark& m : sg.marks) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, m.a, m.b));
         c->t_ms[m.cls] += ms;
@@ -1454,7 +1483,7 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
     if (c->use_graphs) {
       s = step_graph(c, sp, d_vel, blk, done);
       if (s != RELRES_OK) return s;
-      CK(cudaGraphLaunch(c->sg.exec, c->stream));
+      CK(cudaGraphLaunch(c->sgs[c->sg_cur].exec, c->stream));
     } else {
       s = record_block(c, sp, d_vel, blk, done, false);
       if (s != RELRES_OK) return s;

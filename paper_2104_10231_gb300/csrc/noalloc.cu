@@ -14,12 +14,19 @@
 // library and stays allocated until the process exits.  All calls on a GPU
 // share it: calls whose work overlaps on the GPU (different streams, or
 // several host threads) race on it and must be serialised by the caller.
-// Each call rewrites the table and every partial sum it reads, so nothing has
-// to start at zero; stale contents from an earlier call are never used.
+// Each call rewrites the table and every partial sum it reads, and clears the
+// bad-type flag before its kernels run, so stale contents from an earlier
+// call are never used.
+//
+// Atom types live on the device, so the host cannot check them: the kernel
+// skips every pair whose type index is outside [0, n_types) (no table read
+// with it), writes NaN forces for such an atom and raises a flag in the static
+// array, and the reduction then writes NaN energy and virial.
 //
 // Set-up: the first call on each device (with that device current) looks up
-// the array's device address with cudaGetSymbolAddress; make that first call
-// before any stream capture begins.
+// the array's device address with cudaGetSymbolAddress.  That first call
+// should come before any stream capture.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -35,12 +42,14 @@ constexpr int kMaxDevices = 64;
 struct StaticScratch {
   PairTab<double> tab[RELRES_MAX_TYPES * RELRES_MAX_TYPES];
   long long partial[kStaticMaxBlocks][kNQ];
+  unsigned bad_type;  // set when an atom type was outside [0, n_types)
 };
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
-// host-side cache of the array's device address, per device
-static StaticScratch* s_scratch_ptr[kMaxDevices] = {};
+// host-side cache of the array's device address, per device (several host
+// threads may look it up at once; each finds the same address)
+static std::atomic<StaticScratch*> s_scratch_ptr[kMaxDevices];
 
 __device__ __forceinline__ double poly5(const double* g, double d) {
   return (((g[4] * d + g[3]) * d + g[2]) * d + g[1]) * d + g[0];
@@ -97,11 +106,17 @@ __global__ void __launch_bounds__(kStaticThreads)
   const bool live = i < n;
   double xi = 0.0, yi = 0.0, zi = 0.0;
   int ti = 0, e0 = 0, e1 = 0;
+  bool bad_i = false;
   if (live) {
     xi = pos[3 * i];
     yi = pos[3 * i + 1];
     zi = pos[3 * i + 2];
     ti = type[i];
+    bad_i = ti < 0 || ti >= nt;
+    if (bad_i) {
+      ti = 0;
+      atomicOr(&scratch->bad_type, 1u);
+    }
     if (with_excl) {
       e0 = eoff[i];
       e1 = eoff[i + 1];
@@ -124,7 +139,8 @@ __global__ void __launch_bounds__(kStaticThreads)
     if (live) {
       for (int k = 0; k < m; ++k) {
         const int j = base + k;
-        if (j == i) continue;
+        const int tj = stype[k];
+        if (j == i || bad_i || tj < 0 || tj >= nt) continue;  // out-of-range types: no table read
         bool ex = false;
         for (int e = e0; e < e1; ++e) ex |= eidx[e] == j;
         if (ex) continue;
@@ -133,7 +149,7 @@ __global__ void __launch_bounds__(kStaticThreads)
         dy -= l1 * rint(dy / l1);
         dz -= l2 * rint(dz / l2);
         double fr, u;
-        relres_pair(scratch->tab[ti * nt + stype[k]], dx * dx + dy * dy + dz * dz, &fr, &u);
+        relres_pair(scratch->tab[ti * nt + tj], dx * dx + dy * dy + dz * dz, &fr, &u);
         fx += fr * dx;
         fy += fr * dy;
         fz += fr * dz;
@@ -149,9 +165,10 @@ __global__ void __launch_bounds__(kStaticThreads)
     __syncthreads();
   }
   if (live) {
-    forces[3 * i] = fx;
-    forces[3 * i + 1] = fy;
-    forces[3 * i + 2] = fz;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    forces[3 * i] = bad_i ? nan : fx;
+    forces[3 * i + 1] = bad_i ? nan : fy;
+    forces[3 * i + 2] = bad_i ? nan : fz;
   }
   __shared__ double sh[(kStaticThreads / 32) * kNQ];
   block_sum<double, kNQ>(acc, sh);
@@ -166,9 +183,11 @@ __global__ void k_allpairs_static_reduce(int nblocks, const StaticScratch* scrat
   long long tot[kNQ] = {0, 0, 0, 0, 0, 0, 0};
   for (int b = 0; b < nblocks; ++b)
     for (int q = 0; q < kNQ; ++q) tot[q] += scratch->partial[b][q];
-  if (with_energy) energy[0] = double(tot[0]) / kFix;
+  const bool bad = scratch->bad_type != 0u;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  if (with_energy) energy[0] = bad ? nan : double(tot[0]) / kFix;
   if (with_virial)
-    for (int q = 1; q < kNQ; ++q) virial[q - 1] = double(tot[q]) / kFix;
+    for (int q = 1; q < kNQ; ++q) virial[q - 1] = bad ? nan : double(tot[q]) / kFix;
 }
 
 }  // namespace
@@ -231,27 +250,40 @@ extern "C" relres_status relres_pair_forces_static(const relres_params* p, int n
   if (!(rmax < 0.5 * std::fmin(box[0], std::fmin(box[1], box[2])))) return RELRES_ERR_BOX;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RELRES_ERR_CUDA;
-  if (s_scratch_ptr[dev] == nullptr) {
+  StaticScratch* scratch = s_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (scratch == nullptr) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || ptr == nullptr) return RELRES_ERR_CUDA;
-    s_scratch_ptr[dev] = static_cast<StaticScratch*>(ptr);
+    scratch = static_cast<StaticScratch*>(ptr);
+    s_scratch_ptr[dev].store(scratch, std::memory_order_release);
   }
-  StaticScratch* scratch = s_scratch_ptr[dev];
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   // the table for this call (copied from the stack; a pageable-source copy
-  // returns once the source has been read)
+  // returns once the source has been read) and a cleared bad-type flag
   if (cudaMemcpyAsync(scratch->tab, tabs, sizeof(PairTab<double>) * nt * nt, cudaMemcpyHostToDevice,
                       stream) != cudaSuccess)
     return RELRES_ERR_CUDA;
-  const int nblocks = (n_atoms + kStaticThreads - 1) / kStaticThreads;
-  const int with_excl = d_excl_offsets ? 1 : 0;
-  k_allpairs_static<<<nblocks, kStaticThreads, 0, stream>>>(
-      n_atoms, nt, d_pos, d_type, box[0], box[1], box[2], with_excl ? d_excl_offsets : d_type,
-      with_excl ? d_excl_index : d_type, with_excl, d_forces, scratch);
-  if (cudaGetLastError() != cudaSuccess) return RELRES_ERR_CUDA;
-  k_allpairs_static_reduce<<<1, 1, 0, stream>>>(nblocks, scratch, d_energy ? d_energy : d_forces,
-                                                d_energy ? 1 : 0, d_virial ? d_virial : d_forces,
-                                                d_virial ? 1 : 0);
-  if (cudaGetLastError() != cudaSuccess) return RELRES_ERR_CUDA;
+  if (cudaMemsetAsync(&scratch->bad_type, 0, sizeof(unsigned), stream) != cudaSuccess) return RELRES_ERR_CUDA;
+  int nblocks = (n_atoms + kStaticThreads - 1) / kStaticThreads;
+  int with_excl = d_excl_offsets ? 1 : 0;
+  // cudaLaunchKernel returns the status of this launch only: an earlier
+  // error of unrelated work is neither reported as this call's nor cleared
+  int n = n_atoms, ntt = nt;
+  double l0 = box[0], l1 = box[1], l2 = box[2];
+  const int* eoff = with_excl ? d_excl_offsets : d_type;
+  const int* eidx = with_excl ? d_excl_index : d_type;
+  void* args1[] = {&n, &ntt, const_cast<double**>(&d_pos), const_cast<int**>(&d_type), &l0, &l1, &l2,
+                   const_cast<int**>(&eoff), const_cast<int**>(&eidx), &with_excl, &d_forces, &scratch};
+  if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_allpairs_static), dim3(nblocks), dim3(kStaticThreads),
+                       args1, 0, stream) != cudaSuccess)
+    return RELRES_ERR_CUDA;
+  const StaticScratch* cscratch = scratch;
+  double* e_out = d_energy ? d_energy : d_forces;
+  double* w_out = d_virial ? d_virial : d_forces;
+  int with_e = d_energy ? 1 : 0, with_w = d_virial ? 1 : 0;
+  void* args2[] = {&nblocks, &cscratch, &e_out, &with_e, &w_out, &with_w};
+  if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_allpairs_static_reduce), dim3(1), dim3(1), args2, 0,
+                       stream) != cudaSuccess)
+    return RELRES_ERR_CUDA;
   return RELRES_OK;
 }

@@ -330,7 +330,15 @@ struct relres_ctx {
     long long k_parent = 0;           // kernels per launch outside the rebuild bodies
     long long k_body = 0;             // kernels per executed rebuild body
     long long k_prune = 0;            // kernels per executed pruning body (separate pruning pass)
-  } sg;
+    unsigned long long last_use = 0;  // cache recency
+  };
+  // Captured step graphs, one per block shape in use (a call of n steps runs
+  // blocks of 100 and one shorter remainder, so a repeated call needs two);
+  // the least recently used one is dropped when the cache is full.
+  static constexpr int kMaxStepGraphs = 4;
+  std::vector<StepGraph> sgs;
+  int sg_cur = -1;                  // graph of the block being run
+  unsigned long long sg_clock = 0;
   cudaStream_t cap_stream = nullptr;   // capture of the step graph
   cudaStream_t body_stream = nullptr;  // capture of the conditional rebuild bodies
   std::vector<Mark>* cap_marks = nullptr;     // non-null while capturing with timing
