@@ -65,6 +65,9 @@ def parse():
                     help="pruning margin of the neighbour lists in Angstrom (0: pair kernels walk the full lists)")
     ap.add_argument("--pair-config", type=int, default=-1,
                     help="fix the pair-kernel launch configuration (0..6) instead of autotuning")
+    ap.add_argument("--force-acc", type=int, default=-1,
+                    help="per-atom pair-force sums: 0 FP32, 1 compensated float-float, 2 FP64 "
+                         "(default: the library's)")
     return ap.parse_args()
 
 
@@ -254,6 +257,8 @@ def ours(args):
         ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s), stream=stream)
         ctx.set_graphs(not args.no_graphs)
         ctx.set_pair_config(args.pair_config)
+        if args.force_acc >= 0:
+            ctx.set_force_accumulation(args.force_acc)
         ctx.set_prune(args.prune)
         pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
         vel = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
@@ -327,6 +332,8 @@ def ours(args):
         with torch.cuda.stream(stream):
             ctxf = R.Context(R.params_for(sf, R.RELRES_PREC_FP32), R.topology_for(sf), stream=stream)
             ctxf.set_graphs(not args.no_graphs)
+            if args.force_acc >= 0:
+                ctxf.set_force_accumulation(args.force_acc)
             ctxf.set_prune(args.prune)
             posf = pos.clone()
             velf = vel.clone()
@@ -395,7 +402,8 @@ def ours(args):
                   "prune_delta": ctx_stats["prune_delta"], "prunes_in_timed_region": prunes,
                   "mean_fg_walked": roof["mean_fg_walked"], "mean_cg_walked": roof["mean_cg_walked"]},
         "pair_launch": {"threads_per_atom": ctx_stats["pair_tpa"], "block": ctx_stats["pair_block"],
-                        "chosen_by": "autotuner (first relres_step)"},
+                        "chosen_by": "autotuner (first relres_step)",
+                        "force_accumulation": ["FP32", "compensated float-float", "FP64"][ctx_stats["force_acc"]]},
         "gpu_launches": ctx_stats["n_launches"] - st0["n_launches"],
         "device_rates": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in rates.items()},
         "clocks": clk_sum,

@@ -59,6 +59,15 @@ enum relres_mixing { RELRES_MIX_GEOMETRIC = 0, RELRES_MIX_LB = 1 };
  * positions in FP64 (64-bit fixed point for positions inside relres_step). */
 enum relres_precision { RELRES_PREC_FP64 = 0, RELRES_PREC_FP32 = 1 };
 
+/* How the FP32 pair kernels sum one atom's pair forces (relres_set_force_accumulation):
+ * RELRES_ACC_FP32         FP32 running sums;
+ * RELRES_ACC_COMPENSATED  float-float running sums (every term added with an
+ *                         error-free two-sum: ~48-bit sums in FP32 arithmetic);
+ * RELRES_ACC_FP64         FP64 running sums (each FP32 pair term converted and
+ *                         added in FP64).
+ * The sum is rounded to FP32 once, when the force is stored. */
+enum relres_accumulation { RELRES_ACC_FP32 = 0, RELRES_ACC_COMPENSATED = 1, RELRES_ACC_FP64 = 2 };
+
 typedef struct relres_ctx relres_ctx;
 
 /*
@@ -169,6 +178,7 @@ typedef struct relres_stats {
   double mean_fg_pruned, mean_cg_pruned;  /* mean pruned list length over all passes */
   int step_segments;             /* 1: MD steps evaluate bonded terms per segment of whole molecules
                                     inside the drift kernel; 0: separate bonded-term kernel */
+  int force_acc;                 /* relres_accumulation of the FP32 pair kernels */
 } relres_stats;
 
 /* Kernel classes of relres_get_timings. */
@@ -453,6 +463,15 @@ void relres_batch_destroy(relres_batch* batch);
  * atom's partners changes with the number of threads).
  */
 relres_status relres_set_pair_config(relres_ctx* ctx, int config);
+
+/*
+ * Accumulation of each atom's pair-force sum in the FP32 pair kernels
+ * (mode: relres_accumulation; an implementation choice, the paper names no
+ * precision).  Applies to every later force evaluation and MD step of the
+ * context; FP64 contexts ignore it.  Captured step graphs are dropped.
+ * Errors: RELRES_ERR_ARG (null context, unknown mode).
+ */
+relres_status relres_set_force_accumulation(relres_ctx* ctx, int mode);
 
 /*
  * Kernel timing.  enable != 0 makes relres_compute and relres_step record a

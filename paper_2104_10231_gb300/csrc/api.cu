@@ -15,6 +15,7 @@ using namespace relres;
 
 extern "C" {
 static relres_status autotune_pairs(relres_ctx* c);  // defined with the C entry points below
+static void drop_step_graph(relres_ctx* c);
 }
 
 namespace {
@@ -777,6 +778,17 @@ relres_status relres_set_prune(relres_ctx* c, double delta) {
   return RELRES_OK;
 }
 
+relres_status relres_set_force_accumulation(relres_ctx* c, int mode) {
+  if (!c) return RELRES_ERR_ARG;
+  if (mode != RELRES_ACC_FP32 && mode != RELRES_ACC_COMPENSATED && mode != RELRES_ACC_FP64)
+    return fail(c, RELRES_ERR_ARG, "unknown force accumulation mode");
+  CK(cudaStreamSynchronize(c->stream));
+  c->force_acc = mode;
+  drop_step_graph(c);
+  ++c->buf_gen;  // batch graphs bake the launches in too
+  return RELRES_OK;
+}
+
 relres_status relres_set_pair_config(relres_ctx* c, int config) {
   if (!c || config < -1 || config >= kNPairConfigs) return RELRES_ERR_ARG;
   c->tune_mode = config;
@@ -1536,6 +1548,7 @@ relres_status relres_get_stats(relres_ctx* c, relres_stats* o) {
   o->n_launches = c->n_launches;
   o->prune_delta = c->prune_on ? c->prune_delta : 0.0;
   o->step_segments = step_segments(c) ? 1 : 0;
+  o->force_acc = c->force_acc;
   o->n_prunes = (long long)c->h_state->n_prunes;
   if (c->h_state->n_prunes > 0) {
     const double np = double(c->h_state->n_prunes);

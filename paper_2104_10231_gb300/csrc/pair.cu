@@ -293,18 +293,78 @@ struct SmemTabs {
   const CgE* cge;
 };
 
-// Per-thread accumulators of one walk.
+// Per-thread accumulators of one walk.  The owner's force sum of the FP32
+// path is kept in one of three ways (ACC, relres_set_force_accumulation):
+// FP32 running sums (fx, fy, fz); compensated sums, where the (up to) four
+// entries of a list chunk are summed in FP32 (kx, ...) and each chunk sum is
+// added to a float-float total (fx + cx, ...) with an error-free two-sum; or
+// FP64 running sums (dfx, ...), one conversion and FP64 add per entry.  The
+// members a variant does not use are removed by the compiler.
 template <typename R>
 struct Acc {
   R fx = R(0), fy = R(0), fz = R(0);
+  float kx = 0.f, ky = 0.f, kz = 0.f;
+  float cx = 0.f, cy = 0.f, cz = 0.f;
+  double dfx = 0.0, dfy = 0.0, dfz = 0.0;
   R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
   R e = R(0);            // FP64 path: per-thread energy
   ff eff = ff{0.f, 0.f};  // FP32 path: per-thread energy in float-float
 };
 
+template <int ACC>
+__device__ __forceinline__ void acc_force(Acc<float>& A, float tx, float ty, float tz) {
+  if constexpr (ACC == RELRES_ACC_COMPENSATED) {
+    A.kx += tx;
+    A.ky += ty;
+    A.kz += tz;
+  } else if constexpr (ACC == RELRES_ACC_FP64) {
+    A.dfx += double(tx);
+    A.dfy += double(ty);
+    A.dfz += double(tz);
+  } else {
+    A.fx += tx;
+    A.fy += ty;
+    A.fz += tz;
+  }
+}
+
+// end of a list chunk: the compensated variant moves the chunk sum into its
+// float-float total
+template <int ACC>
+__device__ __forceinline__ void acc_chunk(Acc<float>& A) {
+  if constexpr (ACC == RELRES_ACC_COMPENSATED) {
+    const ff sx = ff_two_sum(A.fx, A.kx), sy = ff_two_sum(A.fy, A.ky), sz = ff_two_sum(A.fz, A.kz);
+    A.fx = sx.hi;
+    A.fy = sy.hi;
+    A.fz = sz.hi;
+    A.cx = __fadd_rn(A.cx, sx.lo);
+    A.cy = __fadd_rn(A.cy, sy.lo);
+    A.cz = __fadd_rn(A.cz, sz.lo);
+    A.kx = A.ky = A.kz = 0.f;
+  }
+}
+template <int ACC>
+__device__ __forceinline__ void acc_chunk(Acc<double>&) {}
+
+// the owner's force sum rounded to FP32 (the width of the force buffers)
+template <int ACC>
+__device__ __forceinline__ void acc_final(Acc<float>& A) {
+  if constexpr (ACC == RELRES_ACC_COMPENSATED) {
+    A.fx = __fadd_rn(A.fx, A.cx);
+    A.fy = __fadd_rn(A.fy, A.cy);
+    A.fz = __fadd_rn(A.fz, A.cz);
+  } else if constexpr (ACC == RELRES_ACC_FP64) {
+    A.fx = float(A.dfx);
+    A.fy = float(A.dfy);
+    A.fz = float(A.dfz);
+  }
+}
+template <int ACC>
+__device__ __forceinline__ void acc_final(Acc<double>&) {}
+
 // One list entry; returns its squared distance (past every cutoff for a
 // padding entry), which a pruning launch compares with the pruning radius.
-template <typename R, bool CG, bool EV>
+template <typename R, bool CG, bool EV, int ACC>
 __device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typename PosOf<R>::T& pj,
                                    bool valid, int row0, const SmemTabs& S, const PairLaunch<R>& a,
                                    Acc<R>& A) {
@@ -315,9 +375,7 @@ __device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typenam
     float r2 = dx * dx + dy * dy + dz * dz;
     r2 = valid ? r2 : 3.0e38f;  // padding entry: past every cutoff
     const float fr = CG ? cg_force(S.cgr[row], r2) : fg_force(S.fgr[row], r2);
-    A.fx += fr * dx;
-    A.fy += fr * dy;
-    A.fz += fr * dz;
+    acc_force<ACC>(A, fr * dx, fr * dy, fr * dz);
     if (EV) {
       A.w[0] += fr * dx * dx;
       A.w[1] += fr * dy * dy;
@@ -376,7 +434,7 @@ __device__ __forceinline__ int4 ref_of(const Pos64& p) {
 // entry within the pruning radius is appended, in list order, to its pruned
 // list; the forces are the same bits as a walk of the pruned list (a dropped
 // entry adds exactly zero).
-template <typename R, bool CG, bool EV, int TPA, bool PRN>
+template <typename R, bool CG, bool EV, int TPA, bool PRN, int ACC>
 __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTabs& S,
                                      const PairLaunch<R>& a) {
   static_assert(!PRN || TPA == 1, "pruning launches use one thread per slot");
@@ -404,10 +462,11 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
       const auto p1 = load_pos(L.pos, j1);
       const auto p2 = load_pos(L.pos, j2);
       const auto p3 = load_pos(L.pos, j3);
-      const R r0 = entry<R, CG, EV>(pi, p0, true, row0, S, a, A);
-      const R r1 = entry<R, CG, EV>(pi, p1, rem > 1, row0, S, a, A);
-      const R r2 = entry<R, CG, EV>(pi, p2, rem > 2, row0, S, a, A);
-      const R r3 = entry<R, CG, EV>(pi, p3, rem > 3, row0, S, a, A);
+      const R r0 = entry<R, CG, EV, ACC>(pi, p0, true, row0, S, a, A);
+      const R r1 = entry<R, CG, EV, ACC>(pi, p1, rem > 1, row0, S, a, A);
+      const R r2 = entry<R, CG, EV, ACC>(pi, p2, rem > 2, row0, S, a, A);
+      const R r3 = entry<R, CG, EV, ACC>(pi, p3, rem > 3, row0, S, a, A);
+      acc_chunk<ACC>(A);
       if (PRN) {
         keep_entry(r0 < L.rp2, jj.x, kept, buf, out4, L.nslots);
         keep_entry(r1 < L.rp2, j1, kept, buf, out4, L.nslots);
@@ -431,6 +490,7 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
       if (blockIdx.x == 0) atomicAdd(&a.st->n_prunes, 1ull);
     }
   }
+  acc_final<ACC>(A);
   if (TPA > 1) {  // every lane of the warp takes part (TPA divides 32)
 #pragma unroll
     for (int o = TPA / 2; o > 0; o >>= 1) {
@@ -466,7 +526,7 @@ constexpr int pair_min_blocks(int bs) {
 // One launch per step: with pruning on (one thread per slot) the kernel reads
 // the device flags and, if a rebuild or the pruning trigger fired this step,
 // walks the full lists and writes the pruned ones as it goes.
-template <typename R, bool EV, int TPA, int BS>
+template <typename R, bool EV, int TPA, int BS, int ACC>
 __global__ void __launch_bounds__(BS, pair_min_blocks<R, EV>(BS)) k_pair(PairLaunch<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrow = a.nt * a.nt;
@@ -504,16 +564,16 @@ __global__ void __launch_bounds__(BS, pair_min_blocks<R, EV>(BS)) k_pair(PairLau
   if constexpr (TPA == 1) {
     if (a.prune_on && (*(volatile const unsigned*)a.gate & (F_REBUILD | F_PRUNE)) != 0u) {
       if (cg)
-        walk<R, true, EV, 1, true>(a.cg, blk, S, a);
+        walk<R, true, EV, 1, true, ACC>(a.cg, blk, S, a);
       else
-        walk<R, false, EV, 1, true>(a.fg, blk, S, a);
+        walk<R, false, EV, 1, true, ACC>(a.fg, blk, S, a);
       return;
     }
   }
   if (cg)
-    walk<R, true, EV, TPA, false>(a.cg, blk, S, a);
+    walk<R, true, EV, TPA, false, ACC>(a.cg, blk, S, a);
   else
-    walk<R, false, EV, TPA, false>(a.fg, blk, S, a);
+    walk<R, false, EV, TPA, false, ACC>(a.fg, blk, S, a);
 }
 
 template <typename R>
@@ -524,6 +584,33 @@ static size_t pair_smem(int nt, bool ev) {
     return up(sizeof(FgRow) * nrow) + up(sizeof(CgRow) * nrow) +
            (ev ? up(sizeof(FgE) * nrow) + up(sizeof(CgE) * nrow) : 0);
   return up(sizeof(PairTab<R>) * nrow);
+}
+
+// FP32 launches with the owner's force sum kept as ACC (relres_accumulation)
+template <int ACC>
+static cudaError_t launch_pairs_f32(relres_ctx* c, const PairLaunch<float>& a, bool ev, int grid, size_t smem) {
+  if (ev) {
+    k_pair<float, true, 1, kThreads, ACC><<<grid, kThreads, smem, c->stream>>>(a);
+  } else {
+    switch (c->pair_cfg) {
+#define RELRES_PAIR_CASE(k, T, B) \
+  case k:                         \
+    k_pair<float, false, T, B, ACC><<<grid, B, smem, c->stream>>>(a); \
+    break;
+      RELRES_PAIR_CASE(0, 1, 256)
+      RELRES_PAIR_CASE(1, 1, 128)
+      RELRES_PAIR_CASE(2, 1, 512)
+      RELRES_PAIR_CASE(3, 2, 256)
+      RELRES_PAIR_CASE(4, 4, 256)
+      RELRES_PAIR_CASE(5, 8, 256)
+      RELRES_PAIR_CASE(6, 2, 128)
+#undef RELRES_PAIR_CASE
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
+  RELRES_LAUNCHED(c);
+  return cudaGetLastError();
 }
 
 template <typename R>
@@ -589,31 +676,25 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   if (nb_fg + nb_cg == 0) return cudaSuccess;
   a.nblk_cg = nb_cg;
   const int grid = nb_cg + nb_fg;
-  if (fp64_small) {
-    if constexpr (!std::is_same<R, float>::value) {
+  if constexpr (!std::is_same<R, float>::value) {
+    if (fp64_small) {
       if (ev)
-        k_pair<R, true, 1, 32><<<grid, 32, smem, c->stream>>>(a);
+        k_pair<R, true, 1, 32, 0><<<grid, 32, smem, c->stream>>>(a);
       else
-        k_pair<R, false, 1, 32><<<grid, 32, smem, c->stream>>>(a);
+        k_pair<R, false, 1, 32, 0><<<grid, 32, smem, c->stream>>>(a);
+    } else if (ev) {
+      k_pair<R, true, 1, kThreads, 0><<<grid, kThreads, smem, c->stream>>>(a);
+    } else {
+      k_pair<R, false, 1, kThreads, 0><<<grid, kThreads, smem, c->stream>>>(a);
     }
-  } else if (ev) {
-    k_pair<R, true, 1, kThreads><<<grid, kThreads, smem, c->stream>>>(a);
-  } else if (!std::is_same<R, float>::value) {
-    k_pair<R, false, 1, kThreads><<<grid, kThreads, smem, c->stream>>>(a);
   } else {
-    switch (c->pair_cfg) {
-#define RELRES_PAIR_CASE(k, T, B) \
-  case k:                         \
-    k_pair<R, false, T, B><<<grid, B, smem, c->stream>>>(a); \
-    break;
-      RELRES_PAIR_CASE(0, 1, 256)
-      RELRES_PAIR_CASE(1, 1, 128)
-      RELRES_PAIR_CASE(2, 1, 512)
-      RELRES_PAIR_CASE(3, 2, 256)
-      RELRES_PAIR_CASE(4, 4, 256)
-      RELRES_PAIR_CASE(5, 8, 256)
-      RELRES_PAIR_CASE(6, 2, 128)
-#undef RELRES_PAIR_CASE
+    switch (c->force_acc) {
+      case RELRES_ACC_FP32:
+        return launch_pairs_f32<RELRES_ACC_FP32>(c, a, ev, grid, smem);
+      case RELRES_ACC_COMPENSATED:
+        return launch_pairs_f32<RELRES_ACC_COMPENSATED>(c, a, ev, grid, smem);
+      case RELRES_ACC_FP64:
+        return launch_pairs_f32<RELRES_ACC_FP64>(c, a, ev, grid, smem);
       default:
         return cudaErrorInvalidValue;
     }

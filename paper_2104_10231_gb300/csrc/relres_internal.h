@@ -115,6 +115,7 @@ constexpr int kBlockSteps = 100;  // steps between host status checks in relres_
 constexpr int kSegAtoms = RELRES_SEG_ATOMS;  // atoms per segment (one block of the segment kernels)
 constexpr size_t kSegSmemMax = 48 * 1024;  // shared memory of a segment kernel (term slots + positions)
 constexpr double kPruneDelta = 0.5;   // default margin of the pruned lists (Angstrom)
+#define RELRES_ACC_DEFAULT RELRES_ACC_COMPENSATED
 constexpr double kPruneSlack = 1e-3;  // added to the pruning radius: covers FP32 rounding of distances
 
 // Launch configurations of the forces-only FP32 pair kernel: threads per slot
@@ -311,6 +312,7 @@ struct relres_ctx {
   // the device displacement trigger.  Everything below is baked into the
   // instantiated graph; it is re-captured when any of it changes.
   int pair_cfg = 0;        // index into kPairConfigs
+  int force_acc = RELRES_ACC_DEFAULT;  // relres_accumulation of the FP32 pair kernels
   int tune_mode = -1;      // -1: autotune on the first relres_step; >= 0: fixed configuration
   bool tuned = false;
   bool use_graphs = true;

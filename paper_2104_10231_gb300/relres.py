@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "RELRES_OK", 1: "RELRES_ERR_ARG", 2: "RELRES_ERR_CUDA", 3: "R
                 7: "RELRES_ERR_NOMEM"}
 RELRES_MIX_GEOMETRIC, RELRES_MIX_LB = 0, 1
 RELRES_PREC_FP64, RELRES_PREC_FP32 = 0, 1
+RELRES_ACC_FP32, RELRES_ACC_COMPENSATED, RELRES_ACC_FP64 = 0, 1, 2
 RELRES_MAX_TYPES = 8
 RELRES_THERMO_COLS = 10
 RELRES_PAIR_FIELDS = 26
@@ -37,7 +38,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
             "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled",
             "relres_set_list_caps", "relres_set_prune", "relres_measure_rates", "relres_get_list",
-            "relres_eval_recip"]
+            "relres_eval_recip", "relres_set_force_accumulation"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev", "prune"]
 
@@ -80,7 +81,7 @@ class relres_stats(C.Structure):
                 ("n_builds", C.c_longlong), ("n_steps", C.c_longlong), ("has_cg", C.c_int),
                 ("n_launches", C.c_longlong), ("pair_tpa", C.c_int), ("pair_block", C.c_int),
                 ("prune_delta", C.c_double), ("n_prunes", C.c_longlong), ("mean_fg_pruned", C.c_double),
-                ("mean_cg_pruned", C.c_double), ("step_segments", C.c_int)]
+                ("mean_cg_pruned", C.c_double), ("step_segments", C.c_int), ("force_acc", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,6 +129,7 @@ def load():
     L.relres_set_graphs.argtypes = [vp, C.c_int]
     L.relres_set_params.argtypes = [vp, C.POINTER(relres_params)]
     L.relres_set_pair_config.argtypes = [vp, C.c_int]
+    L.relres_set_force_accumulation.argtypes = [vp, C.c_int]
     L.relres_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
     L.relres_batch_step.argtypes = [vp, C.c_int, C.c_double, C.POINTER(vp), C.POINTER(vp), _dp, C.c_double,
                                     C.POINTER(C.c_uint64), C.c_int, C.POINTER(vp)]
@@ -460,6 +462,11 @@ class Context:
 
     def set_pair_config(self, config):
         relres_set_pair_config(self.ctx, config)
+
+    def set_force_accumulation(self, mode):
+        """RELRES_ACC_FP32, RELRES_ACC_COMPENSATED or RELRES_ACC_FP64: how the FP32
+        pair kernels sum each atom's pair forces."""
+        _check(load().relres_set_force_accumulation(self.ctx, int(mode)), self.ctx)
 
     def set_params(self, params):
         self.params = params

@@ -90,3 +90,47 @@ def test_batch_with_autotuned_replicas_runs_and_conserves_momentum(torch):
     batch.close()
     for c, _, _, _ in ctxs:
         c.close()
+
+
+def test_fp64_batch_of_uneven_replicas_matches_oracle_md(torch):
+    """Four replicas of different sizes and chemistries stepped together in
+    FP64 for 30 steps with the CSVR thermostat: each replica's positions,
+    velocities and thermo rows against the oracle's velocity Verlet + CSVR of
+    the same replica alone (Section 3.2, MD in the canonical ensemble), to the
+    tolerances of the single-context FP64 CSVR trajectory test."""
+    from oracle import core as O
+
+    systems = [S.propane(n_mol=216, temperature=230.0, seed=21),
+               S.neopentane(n_mol=300, temperature=200.0, seed=22),
+               S.propane(n_mol=343, box=31.8 * 7 / 6, temperature=280.0, seed=23),
+               S.neopentane(n_mol=500, temperature=260.0, seed=24)]
+    seeds = [31, 32, 33, 34]
+    steps, dt = 30, 1.0
+    ctxs = []
+    for s in systems:
+        ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP64), R.topology_for(s))
+        p = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+        v = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+        ctx.build_neighbors(p, s.box)
+        th = torch.zeros((steps, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+        ctxs.append((ctx, p, v, th))
+    batch = R.Batch([c for c, _, _, _ in ctxs])
+    batch.step(steps, dt, [p for _, p, _, _ in ctxs], [v for _, _, v, _ in ctxs],
+               [s.temperature for s in systems], 100.0, seeds, thermo_every=1,
+               d_thermo=[th for _, _, _, th in ctxs])
+    torch.cuda.synchronize()
+    for k, ((ctx, p, v, th), s, sd) in enumerate(zip(ctxs, systems, seeds)):
+        po, vo, tho = O.md(s.pos, s.vel, s.box, s.masses, s.types, O.table_for(s), s.n_types, s.excl, s.topo,
+                           steps, dt, t_target=s.temperature, tau=100.0, seed=sd)
+        pg, vg, tg = p.cpu().numpy(), v.cpu().numpy(), th.cpu().numpy()
+        d = pg - po
+        d -= s.box * np.round(d / s.box)
+        assert np.abs(d).max() < 1e-8, k
+        assert np.abs(vg - vo).max() < 1e-9, k
+        np.testing.assert_allclose(tg[:, 3], tho[:, 2], rtol=1e-8, err_msg=f"replica {k} KE")
+        np.testing.assert_allclose(tg[:, 0] + tg[:, 1], tho[:, 0], rtol=1e-8, err_msg=f"replica {k} pair E")
+        np.testing.assert_allclose(tg[:, 2], tho[:, 1], rtol=1e-7, atol=1e-9, err_msg=f"replica {k} bonded E")
+        assert ctx.stats()["n_steps"] == steps
+    batch.close()
+    for c, _, _, _ in ctxs:
+        c.close()

@@ -35,8 +35,10 @@ def _dev(torch, a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def _errors(torch, s, precision):
+def _errors(torch, s, precision, acc=None):
     ctx = R.Context(R.params_for(s, precision), R.topology_for(s))
+    if acc is not None:
+        ctx.set_force_accumulation(acc)
     p = _dev(torch, s.pos)
     ctx.build_neighbors(p, s.box)
     f = torch.empty_like(p)
@@ -107,3 +109,44 @@ def test_precision_modes_per_result(torch):
         d64, d32 = table[("FP64", label)], table[("FP32", label)]
         assert d32["drift"] < 3.0 * d64["drift"] + 2e-4, (label, d32, d64)
         assert d32["fluct"] < 1.5 * d64["fluct"] + 1e-5, (label, d32, d64)
+
+
+ACC_MODES = ((R.RELRES_ACC_FP32, "FP32-acc"), (R.RELRES_ACC_COMPENSATED, "compensated"),
+             (R.RELRES_ACC_FP64, "FP64-acc"))
+
+
+def test_force_accumulation_modes(torch):
+    """The three ways the FP32 pair kernel can sum an atom's pair forces, each
+    against the FP64 oracle, on the propane-like and neopentane-like liquids
+    and on the FG reference at 14 A (lists of ~300 entries per atom).  The
+    accumulation changes only the force sums: energies, which are float-float
+    already, must not change beyond rounding.  Plain FP32 sums are a study
+    column only: over the FG reference's long lists they reach the 1e-5 force
+    bound; the compensated and FP64 sums hold it on every system."""
+    base = S.neopentane(n_mol=500, seed=7)
+    systems = [S.propane(), base, S.fg_only(base)]
+    table = {}
+    for acc, name in ACC_MODES:
+        for s in systems:
+            table[(name, s.name)] = _errors(torch, s, R.RELRES_PREC_FP32, acc)
+    for (mode, sysname), errs in table.items():
+        print(f"{mode:12s} {sysname:40s} " + "  ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    for (mode, sysname), errs in table.items():
+        assert errs["E_pair"] < 1e-7 and errs["E_bonded"] < 1e-7 and errs["virial"] < 1e-4, (mode, sysname, errs)
+        if mode != "FP32-acc":
+            assert errs["force"] < 1e-5, (mode, sysname, errs)
+    for s in systems:
+        f32 = table[("FP32-acc", s.name)]["force"]
+        f64 = table[("FP64-acc", s.name)]["force"]
+        # compensated sums of FP32 chunk sums come within rounding of exact (FP64) sums
+        assert table[("compensated", s.name)]["force"] <= 1.1 * f64 + 2e-7, (s.name, table)
+        assert f64 <= 1.02 * f32, (s.name, table)
+    # the long lists of the FG reference are where the accumulation shows
+    assert table[("FP32-acc", "neopentane_fg_only")]["force"] > 1.2 * table[("FP64-acc", "neopentane_fg_only")]["force"]
+
+
+def test_default_accumulation_is_compensated(torch):
+    s = S.propane()
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    assert ctx.stats()["force_acc"] == R.RELRES_ACC_COMPENSATED
+    ctx.close()

@@ -147,6 +147,37 @@ def test_fp32_neopentane_1m_atoms_bench_configuration(torch):
     assert row[2] == pytest.approx(e[2], rel=1e-6)
 
 
+def test_fp32_neopentane_200k_atoms_against_the_full_oracle(torch):
+    """200 000 atoms (40 000 molecules, L = 202 A) in the benchmark's FP32
+    configuration after 60 MD steps (device-side rebuilds, pruning passes,
+    Morton-ordered cells, several waves of pair blocks): forces, pair energy
+    E_fg + E_cg and virial against the oracle's full all-pairs FP64 sum of
+    Eq. 20 at the same positions."""
+    s = S.neopentane(n_mol=40_000, seed=2105)
+    assert s.n_atoms == 200_000
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    p = _dev(torch, s.pos)
+    v = _dev(torch, s.vel)
+    ctx.build_neighbors(p, s.box)
+    ctx.step(60, 2.0, p, v, t_target=260.0, tau_fs=100.0, seed=6)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    assert st["n_builds"] >= 2 and st["n_prunes"] > st["n_builds"]
+    pos = p.cpu().numpy()
+    f, e, w = _compute(torch, s, R.RELRES_PREC_FP32, pos=pos, ctx=ctx)
+    ctx.close()
+    fr, er, ebr, wr = _oracle(s, pos=pos)
+    ferr = _ferr(f, fr)
+    eerr = abs(e[0] + e[1] - er) / abs(er)
+    berr = abs(e[2] - ebr) / max(1.0, abs(ebr))
+    werr = float(np.abs(w - wr).max() / np.abs(wr[:3]).max())
+    print(f"200k atoms vs full oracle: force {ferr:.2e} energy {eerr:.2e} bonded {berr:.2e} virial {werr:.2e}")
+    assert ferr <= F_TOL, ferr
+    assert eerr <= E_TOL, eerr
+    assert berr <= E_TOL, berr
+    assert werr <= 10 * F_TOL, werr
+
+
 def test_zero_width_shells(torch):
     # r_s- = r_s+ and r_c- = r_c+: no smoothing shells, hard switches of Eq. 20
     s = S.neopentane(n_mol=400, seed=9).subset_copy(radii=(6.5, 6.5, 13.5, 13.5))
