@@ -1,9 +1,12 @@
 """Dynamic pruning of the neighbour lists (relres_set_prune): the pair kernels
 walk lists pruned to the interaction cutoff + delta, re-pruned whenever an atom
 has moved delta/2 since the last pass.  Dropped entries contribute exactly
-zero, so with one thread per list the trajectory must be the same bits as
-without pruning; forces after displacements between the pruning and the
-rebuild thresholds must still match the FP64 oracle."""
+zero, so with one thread per list and running (FP32 or FP64) force sums the
+trajectory must be the same bits as without pruning; with the default
+compensated sums, which add the entries four at a time, the grouping of the
+pruned list differs and the forces agree to rounding.  Forces after
+displacements between the pruning and the rebuild thresholds must still match
+the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -30,8 +33,9 @@ def _dev(torch, a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def _run(torch, s, precision, delta, n_steps, dt, graphs=True, t_target=0.0):
+def _run(torch, s, precision, delta, n_steps, dt, graphs=True, t_target=0.0, acc=R.RELRES_ACC_FP32):
     ctx = R.Context(R.params_for(s, precision), R.topology_for(s))
+    ctx.set_force_accumulation(acc)
     ctx.set_pair_config(0)
     ctx.set_graphs(graphs)
     ctx.set_prune(delta)
@@ -149,3 +153,25 @@ def test_separate_pruning_pass_with_two_threads_per_slot(torch):
     ref = fr + fb
     err = float(np.abs(f.cpu().numpy() - ref).max() / np.sqrt((ref * ref).sum(1).mean()))
     assert err <= 1e-5, err
+
+
+def test_pruned_forces_with_compensated_sums_agree_to_rounding(torch):
+    # the default accumulation groups list entries in fours, so pruned and full
+    # walks round differently: the forces agree to a few FP32 ulps of the sum
+    s = S.neopentane(n_mol=1000, seed=31)
+    rng = np.random.default_rng(8)
+    pos = np.mod(s.pos + rng.normal(scale=0.1, size=s.pos.shape), s.box)
+    out = []
+    for delta in (0.5, 0.0):
+        ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+        assert ctx.stats()["force_acc"] == R.RELRES_ACC_COMPENSATED
+        ctx.set_prune(delta)
+        p = _dev(torch, pos)
+        ctx.build_neighbors(p, s.box)
+        f = torch.empty_like(p)
+        ctx.compute(p, f)
+        torch.cuda.synchronize()
+        out.append(f.cpu().numpy())
+        ctx.close()
+    rms = np.sqrt((out[1] ** 2).sum(1).mean())
+    assert np.abs(out[0] - out[1]).max() / rms < 1e-6
