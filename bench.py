@@ -348,6 +348,7 @@ def ours(args):
             stf = ctxf.stats()
             ctxf.close()
         fg = {"value": whole_job_rate(world, n, args.steps, secs_f), "ms_per_step": secs_f / args.steps * 1e3,
+              "long_run_ms_per_step": roof_f["ms_per_step"],
               "pair_ms_per_launch": roof_f["ms_per_launch"], "pair_launches_timed": roof_f["launches"],
               "pruning_launch_fraction": roof_f["p_prune"],
               "mean_list": stf["mean_fg"], "mean_list_pruned": roof_f["mean_fg_walked"], "rebuilds": stf["n_builds"]}
@@ -399,6 +400,12 @@ def ours(args):
                   "rebuild_ms_per_step": kernel_ms.get("rebuild"),
                   "rebuild_share_of_step": kernel_share.get("rebuild"),
                   "rebuilds_per_step_long_run": roof["rebuilds"] / ROOF_STEPS,
+                  "long_run_context": {"steps": ROOF_STEPS, "ms_per_step": roof["ms_per_step"],
+                                       "rebuilds": roof["rebuilds"],
+                                       "how": "the same system continued for ROOF_STEPS steps after the timed "
+                                              "region, CUDA events around the call, a CUDA-event pair around "
+                                              "every pair launch (no energy steps); a short timed region holds "
+                                              "0 or 1 list rebuilds, this one the long-run share"},
                   "prune_delta": ctx_stats["prune_delta"], "prunes_in_timed_region": prunes,
                   "mean_fg_walked": roof["mean_fg_walked"], "mean_cg_walked": roof["mean_cg_walked"]},
         "pair_launch": {"threads_per_atom": ctx_stats["pair_tpa"], "block": ctx_stats["pair_block"],
@@ -438,7 +445,7 @@ def pair_pass(torch, R, ctx, pos, vel, dt, temp, steps=ROOF_STEPS):
     launches and the list sizes of the same launches."""
     st_a = ctx.stats()
     ctx.set_timing_sampled(["pair"], 1)
-    run_md_timed(torch, R, ctx, pos, vel, steps, dt, temp, 11, 0)
+    secs = run_md_timed(torch, R, ctx, pos, vel, steps, dt, temp, 11, 0)
     tim = ctx.timings()
     st_b = ctx.stats()
     ctx.set_timing(False)
@@ -452,7 +459,8 @@ def pair_pass(torch, R, ctx, pos, vel, dt, temp, steps=ROOF_STEPS):
     launches = tim["pair"][1]
     return {"ms_per_launch": tim["pair"][0] / max(1, launches), "launches": launches, "p_prune": p_prune,
             "mean_fg_walked": mfg, "mean_cg_walked": mcg, "mean_fg_full": st_b["mean_fg"],
-            "mean_cg_full": st_b["mean_cg"], "rebuilds": st_b["n_builds"] - st_a["n_builds"]}
+            "mean_cg_full": st_b["mean_cg"], "rebuilds": st_b["n_builds"] - st_a["n_builds"],
+            "ms_per_step": secs / steps * 1e3}
 
 
 def pair_alg_bytes(n, n_h, full, walked, p_prune):
@@ -595,32 +603,39 @@ def batched_leg(torch, R, S, n_rep, steps, seed=4242):
         return ctxs
 
     seeds = list(range(n_rep))
-    # batched
+
+    def timed(stream, fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    # batched: every replica in the same drift, pair and force-sum launches
     ctxs = make()
-    batch = R.Batch([c for c, _, _ in ctxs])
+    bstream = torch.cuda.Stream()
+    batch = R.Batch([c for c, _, _ in ctxs], stream=bstream)
     pos = [p for _, p, _ in ctxs]
     vel = [v for _, _, v in ctxs]
     batch.step(20, 2.0, pos, vel, temps, 100.0, seeds)  # warm-up: autotuning, graph capture
     batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)  # capture of the timed block shape
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
+    t_batch = timed(bstream, lambda: batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds))
     batch.close()
     for c, _, _ in ctxs:
         c.close()
-    # one after the other
+    # one after the other (each context on the legacy default stream)
     ctxs = make()
     for (c, p, v), t, sd in zip(ctxs, temps, seeds):
         c.step(20, 2.0, p, v, t_target=t, seed=sd)
         c.step(steps, 2.0, p, v, t_target=t, seed=sd)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for (c, p, v), t, sd in zip(ctxs, temps, seeds):
-        c.step(steps, 2.0, p, v, t_target=t, seed=sd)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
+
+    def seq():
+        for (c, p, v), t, sd in zip(ctxs, temps, seeds):
+            c.step(steps, 2.0, p, v, t_target=t, seed=sd)
+
+    t_seq = timed(torch.cuda.default_stream(), seq)
     for c, _, _ in ctxs:
         c.close()
     return {"workload": f"{n_rep} replicas, seeded sizes 1k-50k atoms ({n_atoms} atoms in all), alternately "
@@ -628,7 +643,9 @@ def batched_leg(torch, R, S, n_rep, steps, seed=4242):
             "steps": steps, "value": n_atoms * steps / t_batch, "unit": "atom-steps/s",
             "ms_per_step": t_batch / steps * 1e3,
             "one_after_the_other": {"value": n_atoms * steps / t_seq, "ms_per_step": t_seq / steps * 1e3},
-            "timing": "host wall clock around relres_batch_step with a device synchronize on both sides"}
+            "timing": "CUDA events on the batch stream around one relres_batch_step call (the per-call set-up "
+                      "of every replica included); the sequential run: events on the default stream around "
+                      "one relres_step per replica"}
 
 
 def differentiable_leg(torch, R, S, stream, n_snap=64, n_mol=4000):

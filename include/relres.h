@@ -402,8 +402,11 @@ relres_status relres_set_prune(relres_ctx* ctx, double delta);
  *   t_target[r], seed[r] thermostat target (<= 0: NVE) and random stream,
  *   d_thermo             NULL or per-replica thermo buffers (may be NULL),
  * and common dt_fs, tau_fs, thermo_every.  Each block of up to 100 steps is
- * one CUDA graph launch holding every replica's block on its own branch (its
- * list rebuilds as conditional nodes), so the replicas run concurrently.
+ * one CUDA graph launch.  Where the replicas allow it (relres_batch_get_info)
+ * each step is one drift, one pair and one force-sum launch covering every
+ * replica (each kernel finds its replica from a table of block offsets), with
+ * each replica's list rebuild a conditional node opened by one decide kernel;
+ * otherwise every replica's block sits on its own branch of the graph.
  * Results are bit-identical to stepping each context alone with the same
  * arguments.  If any replica's list overflows, every replica returns to the
  * block start and the block is repeated with larger lists.  cuda_stream: the
@@ -450,6 +453,13 @@ relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, 
                                 double* const* d_vel, const double* t_target, double tau_fs, const uint64_t* seed,
                                 int thermo_every, double* const* d_thermo);
 const char* relres_batch_last_error(relres_batch* batch);
+/* Which form the last relres_batch_step ran: *single_launch = 1 when every
+ * replica shared one drift, one pair and one force-sum launch per step (all
+ * replicas with the same precision and force accumulation, molecules of at
+ * most 256 atoms; the pair kernel then runs one thread per atom in 256-thread
+ * blocks whatever relres_set_pair_config chose), 0 when each replica ran its
+ * own kernels on a branch of the graph; -1 before the first step. */
+relres_status relres_batch_get_info(relres_batch* batch, int* single_launch);
 void relres_batch_destroy(relres_batch* batch);
 
 /*

@@ -1284,7 +1284,56 @@ struct relres_batch {
   std::vector<long long> k_parent;
   bool own_stream = false;
   std::string err;
+  // single-launch path: one drift, one pair and one force-sum launch per step
+  // for every replica (argument tables in device memory), one decide kernel
+  // opening each replica's conditional rebuild node
+  bool fused = false;
+  BatchLaunch bl_pair, bl_drift, bl_sum;
+  DevState** d_states = nullptr;                 // [nrep]
+  cudaGraphConditionalHandle* d_handles = nullptr;  // [blk][nrep]
+  int handles_cap = 0;
+  std::vector<cudaGraphConditionalHandle> h_handles;
 };
+
+// Replicas can share single launches when the kernels' template arguments
+// agree: the same precision and force accumulation, and segmented steps.
+static bool batch_can_fuse(const relres_batch* b) {
+  for (relres_ctx* c : b->ctx)
+    if (c->fp64 != b->ctx[0]->fp64 || c->force_acc != b->ctx[0]->force_acc || !step_segments(c)) return false;
+  return true;
+}
+
+}  // extern "C"
+namespace relres {
+cudaError_t upload_batch(BatchLaunch* b, const void* args, size_t bytes, const std::vector<int>& off) {
+  if (bytes > b->args_bytes) {
+    if (b->d_args) cudaFree(b->d_args);
+    b->d_args = nullptr;
+    b->args_bytes = 0;
+    const cudaError_t e = cudaMalloc(&b->d_args, bytes);
+    if (e != cudaSuccess) return e;
+    b->args_bytes = bytes;
+  }
+  if (int(off.size()) > b->n_off) {
+    if (b->d_off) cudaFree(b->d_off);
+    b->d_off = nullptr;
+    b->n_off = 0;
+    const cudaError_t e = cudaMalloc(&b->d_off, sizeof(int) * off.size());
+    if (e != cudaSuccess) return e;
+    b->n_off = int(off.size());
+  }
+  cudaError_t e = cudaMemcpy(b->d_args, args, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void free_batch(BatchLaunch* b) {
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->d_off) cudaFree(b->d_off);
+  *b = BatchLaunch{};
+}
+}  // namespace relres
+extern "C" {
 
 static relres_status batch_fail(relres_batch* b, relres_status s, const std::string& m) {
   b->err = m;
@@ -1296,6 +1345,9 @@ static void batch_drop_graph(relres_batch* b) {
   b->exec = nullptr;
   b->valid = false;
 }
+
+static relres_status batch_graph_fused(relres_batch* b, const std::vector<StepParams>& sp, double* const* d_vel,
+                                       int blk, int done);
 
 static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>& sp, double* const* d_vel, int blk,
                                  int done) {
@@ -1309,6 +1361,19 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
       b->dt == sp[0].dt && b->tau == sp[0].tau && b->keys == keys)
     return RELRES_OK;
   batch_drop_graph(b);
+  b->fused = batch_can_fuse(b);
+  if (b->fused) {
+    const relres_status fs = batch_graph_fused(b, sp, d_vel, blk, done);
+    if (fs != RELRES_OK) return fs;
+    b->valid = true;
+    b->blk = blk;
+    b->phase = phase;
+    b->thermo_every = sp[0].thermo_every;
+    b->dt = sp[0].dt;
+    b->tau = sp[0].tau;
+    b->keys = keys;
+    return RELRES_OK;
+  }
   for (int r = 0; r < nr; ++r)  // each replica captures its rebuild bodies on its own stream
     if (!b->ctx[r]->body_stream) {
       const cudaError_t eb = cudaStreamCreateWithFlags(&b->ctx[r]->body_stream, cudaStreamNonBlocking);
@@ -1359,6 +1424,114 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
   b->tau = sp[0].tau;
   b->keys = keys;
   return RELRES_OK;
+}
+
+// The fused form of one block of steps (see relres_batch::fused), captured
+// on the batch stream: per replica the rollback snapshot and thermostat
+// draws, then per step the batched drift, the batched decide kernel, every
+// replica's conditional rebuild node on its own branch, the batched pair
+// kernel and the batched force sum.
+static relres_status batch_graph_fused(relres_batch* b, const std::vector<StepParams>& sp, double* const* d_vel,
+                                       int blk, int done) {
+  const int nr = int(b->ctx.size());
+  const bool fp64 = b->ctx[0]->fp64;
+  const int acc = b->ctx[0]->force_acc;
+  // device tables, uploaded before the capture
+  cudaError_t e = prepare_pairs_batch(b->ctx, &b->bl_pair);
+  if (e == cudaSuccess) e = prepare_drift_batch(b->ctx, sp, d_vel, &b->bl_drift);
+  if (e == cudaSuccess) e = prepare_sum_batch(b->ctx, sp, d_vel, &b->bl_sum);
+  if (e == cudaSuccess && !b->d_states) e = cudaMalloc(&b->d_states, sizeof(DevState*) * nr);
+  if (e == cudaSuccess) {
+    std::vector<DevState*> st(nr);
+    for (int r = 0; r < nr; ++r) st[r] = b->ctx[r]->d_state;
+    e = cudaMemcpy(b->d_states, st.data(), sizeof(DevState*) * nr, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && b->handles_cap < blk * nr) {
+    if (b->d_handles) cudaFree(b->d_handles);
+    b->d_handles = nullptr;
+    b->handles_cap = 0;
+    e = cudaMalloc(&b->d_handles, sizeof(cudaGraphConditionalHandle) * size_t(blk) * nr);
+    if (e == cudaSuccess) b->handles_cap = blk * nr;
+  }
+  if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  b->h_handles.assign(size_t(blk) * nr, 0);
+  for (int r = 0; r < nr; ++r)
+    if (!b->ctx[r]->body_stream) {
+      e = cudaStreamCreateWithFlags(&b->ctx[r]->body_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+    }
+  e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  relres_status s = RELRES_OK;
+  std::vector<cudaStream_t> own(nr);
+  for (int r = 0; r < nr; ++r) own[r] = b->ctx[r]->stream;
+  b->k_parent.assign(nr, 0);
+  // snapshot of each replica for the rollback, and its thermostat draws
+  for (int r = 0; r < nr && e == cudaSuccess; ++r) {
+    relres_ctx* c = b->ctx[r];
+    const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
+    e = cudaMemcpyAsync(c->d_snap_x, c->d_xfx, xb, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_snap_v, vel_state(c, d_vel[r]), vb, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_snap_f, c->d_f_tot, force_bytes(c), cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) {
+      c->stream = b->stream;
+      const long long n0 = c->n_launches;
+      e = launch_csvr_draws(c, sp[r], blk);
+      b->k_parent[r] += c->n_launches - n0;
+      c->n_launches = n0;
+      c->stream = own[r];
+    }
+  }
+  for (int k = 0; k < blk && e == cudaSuccess && s == RELRES_OK; ++k) {
+    const bool ev_step = sp[0].thermo_every > 0 && ((done + k + 1) % sp[0].thermo_every) == 0;
+    e = launch_drift_batch(b->stream, fp64, ev_step, b->bl_drift, nr);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(b->stream, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+    for (int r = 0; r < nr && e == cudaSuccess; ++r)
+      e = cudaGraphConditionalHandleCreate(&b->h_handles[size_t(k) * nr + r], g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = launch_decide_batch(b->stream, b->d_states, b->d_handles + size_t(k) * nr, nr);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
+    for (int r = 0; r < nr && e == cudaSuccess && s == RELRES_OK; ++r) {
+      relres_ctx* c = b->ctx[r];
+      e = cudaStreamWaitEvent(b->fork[r], b->ev_fork, 0);
+      if (e != cudaSuccess) break;
+      const long long n0 = c->n_launches;
+      c->stream = b->fork[r];
+      s = add_conditional(c, b->h_handles[size_t(k) * nr + r], [c]() {
+        const cudaError_t eb = launch_rebuild(c, c->d_open);
+        return eb == cudaSuccess ? launch_lists(c, c->d_open) : eb;
+      });
+      c->stream = own[r];
+      c->n_launches = n0;
+      if (s != RELRES_OK) b->err = "replica " + std::to_string(r) + " (capture): " + c->err;
+      if (s == RELRES_OK) e = cudaEventRecord(b->ev_join[r], b->fork[r]);
+      if (s == RELRES_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[r], 0);
+    }
+    if (e == cudaSuccess && s == RELRES_OK) e = launch_pairs_batch(b->stream, fp64, acc, ev_step, b->bl_pair, nr);
+    if (e == cudaSuccess && s == RELRES_OK) e = launch_sum_batch(b->stream, fp64, k, b->bl_sum, nr);
+  }
+  // every replica takes part in the step's drift, decide, pair and force-sum launches
+  for (int r = 0; r < nr; ++r) b->k_parent[r] += 4LL * blk;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (s == RELRES_OK && e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  if (s == RELRES_OK && e2 != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e2));
+  if (s == RELRES_OK) {
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (g) cudaGraphDestroy(g);
+  if (s == RELRES_OK) {
+    e = cudaMemcpy(b->d_handles, b->h_handles.data(), sizeof(cudaGraphConditionalHandle) * b->h_handles.size(),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (s != RELRES_OK) batch_drop_graph(b);
+  return s;
 }
 
 relres_status relres_batch_create(relres_batch** out, relres_ctx* const* ctxs, int n_ctx, void* cuda_stream) {
@@ -1427,7 +1600,7 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
       relres_ctx* c = b->ctx[r];
       s = read_state(c);
       if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + c->err);
-      const long long kpr = (c->prune_on && !pairs_prune(c)) ? 1 : 0;
+      const long long kpr = (!b->fused && c->prune_on && !pairs_prune(c)) ? 1 : 0;
       c->n_launches += b->k_parent[r] + 6LL * std::max(0LL, c->h_state->n_builds - builds0[r]) +
                        kpr * std::max(0LL, (long long)c->h_state->n_prunes - prunes0[r]);
       flags[r] = c->h_state->flags;
@@ -1468,10 +1641,21 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
 
 const char* relres_batch_last_error(relres_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
+relres_status relres_batch_get_info(relres_batch* b, int* single_launch) {
+  if (!b || !single_launch) return RELRES_ERR_ARG;
+  *single_launch = b->valid ? (b->fused ? 1 : 0) : -1;
+  return RELRES_OK;
+}
+
 void relres_batch_destroy(relres_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_drop_graph(b);
+  free_batch(&b->bl_pair);
+  free_batch(&b->bl_drift);
+  free_batch(&b->bl_sum);
+  if (b->d_states) cudaFree(b->d_states);
+  if (b->d_handles) cudaFree(b->d_handles);
   for (cudaStream_t st : b->fork)
     if (st) cudaStreamDestroy(st);
   for (cudaEvent_t ev : b->ev_join)

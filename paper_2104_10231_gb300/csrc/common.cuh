@@ -58,6 +58,20 @@ __device__ __forceinline__ int cell_of(int h, int n) { return int(__umulhi(unsig
 // flag and a valid (possibly unused) pointer.  `gate` points at the device flag
 // word of a step (rebuild only when F_REBUILD is set; pruning when F_REBUILD
 // or F_PRUNE is set) or at a word that always has F_REBUILD set.
+// Replica of block b in a batched launch: the r with off[r] <= b < off[r + 1]
+// (off: cumulative block counts of the nrep replicas, off[0] = 0).
+__device__ __forceinline__ int batch_replica(const int* __restrict__ off, int nrep, int b) {
+  int lo = 0, hi = nrep - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ bool gate_closed(const unsigned* gate, unsigned mask = F_REBUILD) {
   return (*(volatile const unsigned*)gate & mask) == 0u;
 }

@@ -766,13 +766,13 @@ struct DriftSegArgs {
   long long* acc;
 };
 
+// The work of block `bid` (segment bid) of one system's drift launch.
 template <typename R, bool EV>
-__global__ void __launch_bounds__(kSegAtoms, std::is_same<R, float>::value ? 5 * kThreads / kSegAtoms : 1)
-    k_drift_seg(DriftSegArgs<R> a) {
+__device__ __forceinline__ void drift_seg_block(const DriftSegArgs<R>& a, int bid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* sx = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSegAtoms][3]
   ForceT<R>* slot = reinterpret_cast<ForceT<R>*>(smem_raw + sizeof(unsigned long long) * 3 * kSegAtoms);
-  const int* g = a.seg + 8 * blockIdx.x;
+  const int* g = a.seg + 8 * bid;
   const int a0 = g[0], a1 = g[1], b0 = g[2], b1 = g[3], g0 = g[4], g1 = g[5], d0 = g[6], d1 = g[7];
   const int nb = b1 - b0, na = g1 - g0, nd = d1 - d0;
   const int base_a = 2 * nb, base_d = base_a + 3 * na;
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(kSegAtoms, std::is_same<R, float>::value ? 5 *
   const int4 rec0 = q0 < nb ? a.B.bonds[b0 + q0] : (q0 < nb + na ? a.B.angles[g0 + q0 - nb] : make_int4(0, 0, 0, 0));
   const int4 rec1 = q1 < nb ? a.B.bonds[b0 + q1] : (q1 < nb + na ? a.B.angles[g0 + q1 - nb] : make_int4(0, 0, 0, 0));
   const int e0 = i < a1 ? a.inc_off[i] : 0, e1 = i < a1 ? a.inc_off[i + 1] : 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0)
+  if (bid == 0 && threadIdx.x == 0)
     a.d.st->ev = a.d.thermo_every > 0 && ((a.d.st->local_step + 1) % a.d.thermo_every) == 0;
   bool rebuild = false, reprune = false;
   if (i < a1) {
@@ -845,6 +845,20 @@ __global__ void __launch_bounds__(kSegAtoms, std::is_same<R, float>::value ? 5 *
     }
     save_force(a.f_bond, i, f);
   }
+}
+
+template <typename R, bool EV>
+__global__ void __launch_bounds__(kSegAtoms, std::is_same<R, float>::value ? 5 * kThreads / kSegAtoms : 1)
+    k_drift_seg(DriftSegArgs<R> a) {
+  drift_seg_block<R, EV>(a, blockIdx.x);
+}
+
+// Batches: one launch over the segments of every replica (see k_pair_batch).
+template <typename R, bool EV>
+__global__ void __launch_bounds__(kSegAtoms, std::is_same<R, float>::value ? 5 * kThreads / kSegAtoms : 1)
+    k_drift_seg_batch(const DriftSegArgs<R>* __restrict__ args, const int* __restrict__ off, int nrep) {
+  const int r = batch_replica(off, nrep, blockIdx.x);
+  drift_seg_block<R, EV>(args[r], int(blockIdx.x) - off[r]);
 }
 
 // ----------------------------------------------------------------- thermostat
@@ -1027,20 +1041,21 @@ __device__ __forceinline__ R sum_atom(const SumArgs<R>& a, int i, SumIn<R>& in, 
   return kc * v2;
 }
 
-// grid-stride (a few blocks per SM), one kinetic-energy atomic and one
-// ticket per block
+// grid-stride over the nblk blocks of one system (a few blocks per SM), one
+// kinetic-energy atomic and one ticket per block; step k of the block of
+// steps (its thermostat draws)
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_sum(SumArgs<R> a) {
+__device__ __forceinline__ void sum_block(const SumArgs<R>& a, int bid, int nblk, int k) {
   // this step's thermostat draws, read early (the last block uses them)
   double r1 = 0.0, rs = 0.0;
   if (threadIdx.x == 0 && a.sp.t_target > 0.0) {
-    r1 = a.draw[0];
-    rs = a.draw[1];
+    r1 = a.draw[2 * k];
+    rs = a.draw[2 * k + 1];
   }
   R ke = R(0);  // a few atoms per thread
   bool bad = false;
-  const int stride = gridDim.x * blockDim.x;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = nblk * blockDim.x;
+  int i = bid * blockDim.x + threadIdx.x;
   for (; i + stride < a.n; i += 2 * stride) {  // two atoms in flight: both loaded before either store
     SumIn<R> in0, in1;
     sum_load(a, i, in0);
@@ -1062,12 +1077,26 @@ __global__ void __launch_bounds__(kThreads) k_sum(SumArgs<R> a) {
     acc_add(a.acc + kAccKe, v[0]);
     __threadfence();
     const unsigned ticket = atomicAdd(&a.st->done_blocks, 1u);
-    if (ticket == gridDim.x - 1) {
+    if (ticket == unsigned(nblk - 1)) {
       __threadfence();
       a.st->done_blocks = 0u;
       end_of_step(a.acc, a.sp, a.st, r1, rs);
     }
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_sum(SumArgs<R> a, int k) {
+  sum_block<R>(a, blockIdx.x, gridDim.x, k);
+}
+
+// Batches: one launch over every replica (see k_pair_batch); replica r's
+// blocks count their own tickets, so its last block runs its thermostat.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_sum_batch(const SumArgs<R>* __restrict__ args,
+                                                        const int* __restrict__ off, int nrep, int k) {
+  const int r = batch_replica(off, nrep, blockIdx.x);
+  sum_block<R>(args[r], int(blockIdx.x) - off[r], off[r + 1] - off[r], k);
 }
 
 // Energies and virial of relres_compute (one thread); clears the accumulators.
@@ -1373,23 +1402,33 @@ static DriftArgs<R> drift_args(relres_ctx* c, const StepParams& sp, double* d_ve
 }
 
 template <typename R>
+static DriftSegArgs<R> drift_seg_args(relres_ctx* c, const StepParams& sp, double* d_vel) {
+  const double k = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
+  DriftSegArgs<R> a{};
+  a.d = drift_args<R>(c, sp, d_vel);
+  a.seg = c->d_seg;
+  a.B = bonded_args(c);
+  a.sc = Sc3<R>{R(c->box[0] / k), R(c->box[1] / k), R(c->box[2] / k)};
+  ff_split(c->box[0] / 18446744073709551616.0, &a.q0h, &a.q0l);
+  ff_split(c->box[1] / 18446744073709551616.0, &a.q1h, &a.q1l);
+  ff_split(c->box[2] / 18446744073709551616.0, &a.q2h, &a.q2l);
+  a.inc_off = c->d_inc_off;
+  a.inc = c->d_inc;
+  a.f_bond = static_cast<ForceT<R>*>(c->d_f_bond);
+  a.acc = c->d_acc;
+  return a;
+}
+
+template <typename R>
+static size_t drift_seg_smem(const relres_ctx* c) {
+  return sizeof(unsigned long long) * 3 * kSegAtoms + size_t(c->seg_slots) * (std::is_same<R, float>::value ? 16 : 24);
+}
+
+template <typename R>
 static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev) {
   if (step_segments(c)) {
-    const double k = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
-    DriftSegArgs<R> a{};
-    a.d = drift_args<R>(c, sp, d_vel);
-    a.seg = c->d_seg;
-    a.B = bonded_args(c);
-    a.sc = Sc3<R>{R(c->box[0] / k), R(c->box[1] / k), R(c->box[2] / k)};
-    ff_split(c->box[0] / 18446744073709551616.0, &a.q0h, &a.q0l);
-    ff_split(c->box[1] / 18446744073709551616.0, &a.q1h, &a.q1l);
-    ff_split(c->box[2] / 18446744073709551616.0, &a.q2h, &a.q2l);
-    a.inc_off = c->d_inc_off;
-    a.inc = c->d_inc;
-    a.f_bond = static_cast<ForceT<R>*>(c->d_f_bond);
-    a.acc = c->d_acc;
-    const size_t smem = sizeof(unsigned long long) * 3 * kSegAtoms +
-                        size_t(c->seg_slots) * (std::is_same<R, float>::value ? 16 : 24);
+    const DriftSegArgs<R> a = drift_seg_args<R>(c, sp, d_vel);
+    const size_t smem = drift_seg_smem<R>(c);
     if (ev)
       k_drift_seg<R, true><<<c->n_seg, kSegAtoms, smem, c->stream>>>(a);
     else
@@ -1405,8 +1444,14 @@ cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel, boo
   return c->fp64 ? launch_drift_t<double>(c, sp, d_vel, ev) : launch_drift_t<float>(c, sp, d_vel, ev);
 }
 
+// blocks of the force sum: one wave of resident blocks (56 registers a
+// thread: four blocks per SM); batches give each replica the same blocks, so
+// its kinetic-energy partial sums, and with them its trajectory, are the same
+// bits as stepping it alone
+static int sum_blocks(const relres_ctx* c) { return std::max(1, std::min((c->n + kThreads - 1) / kThreads, 152 * 4)); }
+
 template <typename R>
-static cudaError_t launch_sum_t(relres_ctx* c, const StepParams& sp, int k, const double* d_vel) {
+static SumArgs<R> sum_args(relres_ctx* c, const StepParams& sp, const double* d_vel) {
   SumArgs<R> a{};
   a.n = c->n;
   a.f_fg = static_cast<const ForceT<R>*>(c->d_f_fg);
@@ -1428,10 +1473,14 @@ static cudaError_t launch_sum_t(relres_ctx* c, const StepParams& sp, int k, cons
     a.sp.thermo = static_cast<double*>(c->d_dummy);
     a.sp.thermo_every = 0;
   }
-  a.draw = c->d_draws + 2 * k;
-  // one wave of resident blocks (44 registers a thread: five blocks per SM)
-  const int nb = std::max(1, std::min((c->n + kThreads - 1) / kThreads, 152 * 4));  // one wave (56 registers)
-  k_sum<R><<<nb, kThreads, 0, c->stream>>>(a);
+  a.draw = c->d_draws;
+  return a;
+}
+
+template <typename R>
+static cudaError_t launch_sum_t(relres_ctx* c, const StepParams& sp, int k, const double* d_vel) {
+  const SumArgs<R> a = sum_args<R>(c, sp, d_vel);
+  k_sum<R><<<sum_blocks(c), kThreads, 0, c->stream>>>(a, k);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
@@ -1464,6 +1513,74 @@ cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev) {
 cudaError_t launch_flags_and(relres_ctx* c, unsigned keep) {
   k_flags_and<<<1, 1, 0, c->stream>>>(c->d_state, keep);
   RELRES_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+// ---- batches (relres_batch_step): argument tables of every replica
+template <typename R>
+static cudaError_t prepare_drift_batch_t(const std::vector<relres_ctx*>& cs, const std::vector<StepParams>& sp,
+                                         double* const* d_vel, BatchLaunch* b) {
+  std::vector<DriftSegArgs<R>> args(cs.size());
+  std::vector<int> off(cs.size() + 1, 0);
+  size_t smem = 0;
+  for (size_t r = 0; r < cs.size(); ++r) {
+    args[r] = drift_seg_args<R>(cs[r], sp[r], d_vel[r]);
+    off[r + 1] = off[r] + cs[r]->n_seg;
+    smem = std::max(smem, drift_seg_smem<R>(cs[r]));
+  }
+  b->nblk = off.back();
+  b->smem = b->smem_ev = smem;
+  return upload_batch(b, args.data(), sizeof(DriftSegArgs<R>) * args.size(), off);
+}
+
+cudaError_t prepare_drift_batch(const std::vector<relres_ctx*>& cs, const std::vector<StepParams>& sp,
+                                double* const* d_vel, BatchLaunch* b) {
+  return cs[0]->fp64 ? prepare_drift_batch_t<double>(cs, sp, d_vel, b) : prepare_drift_batch_t<float>(cs, sp, d_vel, b);
+}
+
+template <typename R>
+static void launch_drift_batch_t(cudaStream_t s, bool ev, const BatchLaunch& b, int nrep) {
+  const auto* args = static_cast<const DriftSegArgs<R>*>(b.d_args);
+  if (ev)
+    k_drift_seg_batch<R, true><<<b.nblk, kSegAtoms, b.smem, s>>>(args, b.d_off, nrep);
+  else
+    k_drift_seg_batch<R, false><<<b.nblk, kSegAtoms, b.smem, s>>>(args, b.d_off, nrep);
+}
+
+cudaError_t launch_drift_batch(cudaStream_t s, bool fp64, bool ev, const BatchLaunch& b, int nrep) {
+  if (b.nblk == 0) return cudaSuccess;
+  if (fp64)
+    launch_drift_batch_t<double>(s, ev, b, nrep);
+  else
+    launch_drift_batch_t<float>(s, ev, b, nrep);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t prepare_sum_batch_t(const std::vector<relres_ctx*>& cs, const std::vector<StepParams>& sp,
+                                       double* const* d_vel, BatchLaunch* b) {
+  std::vector<SumArgs<R>> args(cs.size());
+  std::vector<int> off(cs.size() + 1, 0);
+  for (size_t r = 0; r < cs.size(); ++r) {
+    args[r] = sum_args<R>(cs[r], sp[r], d_vel[r]);
+    off[r + 1] = off[r] + sum_blocks(cs[r]);
+  }
+  b->nblk = off.back();
+  b->smem = b->smem_ev = 0;
+  return upload_batch(b, args.data(), sizeof(SumArgs<R>) * args.size(), off);
+}
+
+cudaError_t prepare_sum_batch(const std::vector<relres_ctx*>& cs, const std::vector<StepParams>& sp,
+                              double* const* d_vel, BatchLaunch* b) {
+  return cs[0]->fp64 ? prepare_sum_batch_t<double>(cs, sp, d_vel, b) : prepare_sum_batch_t<float>(cs, sp, d_vel, b);
+}
+
+cudaError_t launch_sum_batch(cudaStream_t s, bool fp64, int k, const BatchLaunch& b, int nrep) {
+  if (b.nblk == 0) return cudaSuccess;
+  if (fp64)
+    k_sum_batch<double><<<b.nblk, kThreads, 0, s>>>(static_cast<const SumArgs<double>*>(b.d_args), b.d_off, nrep, k);
+  else
+    k_sum_batch<float><<<b.nblk, kThreads, 0, s>>>(static_cast<const SumArgs<float>*>(b.d_args), b.d_off, nrep, k);
   return cudaGetLastError();
 }
 

@@ -533,6 +533,18 @@ __global__ void k_decide(const DevState* st, cudaGraphConditionalHandle h, cudaG
   if (with_prune) cudaGraphSetConditional(hp, (f & (F_REBUILD | F_PRUNE)) ? 1u : 0u);
 }
 
+// Batches: thread r opens replica r's rebuild node iff its trigger fired.
+__global__ void k_decide_batch(DevState* const* st, const cudaGraphConditionalHandle* h, int nrep) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrep) cudaGraphSetConditional(h[r], (st[r]->flags & F_REBUILD) ? 1u : 0u);
+}
+
+cudaError_t launch_decide_batch(cudaStream_t s, DevState* const* d_states, const cudaGraphConditionalHandle* d_h,
+                                int nrep) {
+  k_decide_batch<<<(nrep + 127) / 128, 128, 0, s>>>(d_states, d_h, nrep);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_decide(relres_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle hp,
                           int with_prune) {
   k_decide<<<1, 1, 0, c->stream>>>(c->d_state, h, hp, with_prune);

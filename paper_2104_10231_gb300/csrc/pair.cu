@@ -436,7 +436,7 @@ __device__ __forceinline__ int4 ref_of(const Pos64& p) {
 // entry adds exactly zero).
 template <typename R, bool CG, bool EV, int TPA, bool PRN, int ACC>
 __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTabs& S,
-                                     const PairLaunch<R>& a) {
+                                     const PairLaunch<R>& a, bool first_block) {
   static_assert(!PRN || TPA == 1, "pruning launches use one thread per slot");
   const int t = blk * blockDim.x + threadIdx.x;
   const int s = t / TPA;
@@ -487,7 +487,7 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
     block_sum<unsigned long long, 1>(v, sh_k);
     if (threadIdx.x == 0) {
       atomicAdd(L.tot_in, v[0]);
-      if (blockIdx.x == 0) atomicAdd(&a.st->n_prunes, 1ull);
+      if (first_block) atomicAdd(&a.st->n_prunes, 1ull);
     }
   }
   acc_final<ACC>(A);
@@ -526,8 +526,9 @@ constexpr int pair_min_blocks(int bs) {
 // One launch per step: with pruning on (one thread per slot) the kernel reads
 // the device flags and, if a rebuild or the pruning trigger fired this step,
 // walks the full lists and writes the pruned ones as it goes.
-template <typename R, bool EV, int TPA, int BS, int ACC>
-__global__ void __launch_bounds__(BS, pair_min_blocks<R, EV>(BS)) k_pair(PairLaunch<R> a) {
+// The work of block `bid` of one system's pair launch.
+template <typename R, bool EV, int TPA, int ACC>
+__device__ __forceinline__ void pair_block(const PairLaunch<R>& a, int bid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nrow = a.nt * a.nt;
   size_t off = 0;
@@ -559,21 +560,36 @@ __global__ void __launch_bounds__(BS, pair_min_blocks<R, EV>(BS)) k_pair(PairLau
     S.tab = tab;
   }
   __syncthreads();
-  const bool cg = int(blockIdx.x) < a.nblk_cg;
-  const int blk = cg ? blockIdx.x : blockIdx.x - a.nblk_cg;
+  const bool cg = bid < a.nblk_cg;
+  const int blk = cg ? bid : bid - a.nblk_cg;
   if constexpr (TPA == 1) {
     if (a.prune_on && (*(volatile const unsigned*)a.gate & (F_REBUILD | F_PRUNE)) != 0u) {
       if (cg)
-        walk<R, true, EV, 1, true, ACC>(a.cg, blk, S, a);
+        walk<R, true, EV, 1, true, ACC>(a.cg, blk, S, a, bid == 0);
       else
-        walk<R, false, EV, 1, true, ACC>(a.fg, blk, S, a);
+        walk<R, false, EV, 1, true, ACC>(a.fg, blk, S, a, bid == 0);
       return;
     }
   }
   if (cg)
-    walk<R, true, EV, TPA, false, ACC>(a.cg, blk, S, a);
+    walk<R, true, EV, TPA, false, ACC>(a.cg, blk, S, a, bid == 0);
   else
-    walk<R, false, EV, TPA, false, ACC>(a.fg, blk, S, a);
+    walk<R, false, EV, TPA, false, ACC>(a.fg, blk, S, a, bid == 0);
+}
+
+template <typename R, bool EV, int TPA, int BS, int ACC>
+__global__ void __launch_bounds__(BS, pair_min_blocks<R, EV>(BS)) k_pair(PairLaunch<R> a) {
+  pair_block<R, EV, TPA, ACC>(a, blockIdx.x);
+}
+
+// Batches (relres_batch_step): one launch over the pair work of every replica.
+// Block b belongs to the replica r with off[r] <= b < off[r + 1]; its
+// arguments are the replica's PairLaunch in device memory.
+template <typename R, bool EV, int ACC>
+__global__ void __launch_bounds__(kThreads, pair_min_blocks<R, EV>(kThreads))
+    k_pair_batch(const PairLaunch<R>* __restrict__ args, const int* __restrict__ off, int nrep) {
+  const int r = batch_replica(off, nrep, blockIdx.x);
+  pair_block<R, EV, 1, ACC>(args[r], int(blockIdx.x) - off[r]);
 }
 
 template <typename R>
@@ -613,8 +629,10 @@ static cudaError_t launch_pairs_f32(relres_ctx* c, const PairLaunch<float>& a, b
   return cudaGetLastError();
 }
 
+// Arguments of one system's pair launch with `per` slots per block; returns
+// the number of blocks (0: nothing to do).
 template <typename R>
-static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
+static int make_pair_launch(const relres_ctx* c, int which, int tpa, int per, PairLaunch<R>* out) {
   const double unit = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
   PairLaunch<R> a{};
   a.sx = R(c->box[0] / unit);
@@ -655,6 +673,16 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   } else {
     a.cg = a.fg;
   }
+  a.prune_on = (c->prune_on && tpa == 1) ? 1 : 0;
+  const int nb_fg = do_fg ? (c->n + per - 1) / per : 0;
+  const int nb_cg = do_cg ? (c->n_h + per - 1) / per : 0;
+  a.nblk_cg = nb_cg;
+  *out = a;
+  return nb_cg + nb_fg;
+}
+
+template <typename R>
+static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   const size_t smem = pair_smem<R>(c->n_types, ev);
   // energy steps and FP64: one thread per slot, 256 per block (32 for small
   // FP64 systems, below); forces-only FP32: the autotuned (threads per slot,
@@ -669,13 +697,9 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   // blocks (one thread per slot either way, so the forces are the same bits)
   const bool fp64_small = !std::is_same<R, float>::value && (c->n + kThreads - 1) / kThreads < kSmallGridSMs;
   if (fp64_small) bs = 32;
-  a.prune_on = (c->prune_on && tpa == 1) ? 1 : 0;
-  const int per = bs / tpa;  // slots per block
-  const int nb_fg = do_fg ? (c->n + per - 1) / per : 0;
-  const int nb_cg = do_cg ? (c->n_h + per - 1) / per : 0;
-  if (nb_fg + nb_cg == 0) return cudaSuccess;
-  a.nblk_cg = nb_cg;
-  const int grid = nb_cg + nb_fg;
+  PairLaunch<R> a;
+  const int grid = make_pair_launch<R>(c, which, tpa, bs / tpa, &a);
+  if (grid == 0) return cudaSuccess;
   if constexpr (!std::is_same<R, float>::value) {
     if (fp64_small) {
       if (ev)
@@ -700,6 +724,54 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
     }
   }
   RELRES_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+// ---- batches: the argument table of every replica (one thread per slot,
+// 256-slot blocks, pruning in the walk) uploaded once per captured graph
+template <typename R>
+static cudaError_t prepare_pairs_batch_t(const std::vector<relres_ctx*>& cs, BatchLaunch* b) {
+  std::vector<PairLaunch<R>> args(cs.size());
+  std::vector<int> off(cs.size() + 1, 0);
+  int nt_max = 1;
+  for (size_t r = 0; r < cs.size(); ++r) {
+    off[r + 1] = off[r] + make_pair_launch<R>(cs[r], 3, 1, kThreads, &args[r]);
+    nt_max = std::max(nt_max, cs[r]->n_types);
+  }
+  b->nblk = off.back();
+  b->smem = pair_smem<R>(nt_max, false);
+  b->smem_ev = pair_smem<R>(nt_max, true);
+  return upload_batch(b, args.data(), sizeof(PairLaunch<R>) * args.size(), off);
+}
+
+cudaError_t prepare_pairs_batch(const std::vector<relres_ctx*>& cs, BatchLaunch* b) {
+  return cs[0]->fp64 ? prepare_pairs_batch_t<double>(cs, b) : prepare_pairs_batch_t<float>(cs, b);
+}
+
+template <int ACC>
+static void launch_pairs_batch_f32(cudaStream_t s, bool ev, const BatchLaunch& b, int nrep) {
+  const auto* args = static_cast<const PairLaunch<float>*>(b.d_args);
+  if (ev)
+    k_pair_batch<float, true, ACC><<<b.nblk, kThreads, b.smem_ev, s>>>(args, b.d_off, nrep);
+  else
+    k_pair_batch<float, false, ACC><<<b.nblk, kThreads, b.smem, s>>>(args, b.d_off, nrep);
+}
+
+cudaError_t launch_pairs_batch(cudaStream_t s, bool fp64, int acc, bool ev, const BatchLaunch& b, int nrep) {
+  if (b.nblk == 0) return cudaSuccess;
+  if (fp64) {
+    const auto* args = static_cast<const PairLaunch<double>*>(b.d_args);
+    if (ev)
+      k_pair_batch<double, true, 0><<<b.nblk, kThreads, b.smem_ev, s>>>(args, b.d_off, nrep);
+    else
+      k_pair_batch<double, false, 0><<<b.nblk, kThreads, b.smem, s>>>(args, b.d_off, nrep);
+  } else if (acc == RELRES_ACC_FP32) {
+    launch_pairs_batch_f32<RELRES_ACC_FP32>(s, ev, b, nrep);
+  } else if (acc == RELRES_ACC_COMPENSATED) {
+    launch_pairs_batch_f32<RELRES_ACC_COMPENSATED>(s, ev, b, nrep);
+  } else {
+    launch_pairs_batch_f32<RELRES_ACC_FP64>(s, ev, b, nrep);
+  }
   return cudaGetLastError();
 }
 

@@ -409,6 +409,34 @@ inline void* vel_state(relres_ctx* c, double* d_vel) {
 }
 cudaError_t launch_flags_and(relres_ctx* c, unsigned keep);
 
+// ---- batched launches (relres_batch_step): one launch of a kernel class
+// covers every replica.  d_args holds one argument struct per replica and
+// d_off the cumulative block counts (block b works for the replica r with
+// d_off[r] <= b < d_off[r + 1]); both are uploaded before the step graph is
+// captured and stay valid while the replicas' buffers do.
+struct BatchLaunch {
+  void* d_args = nullptr;
+  int* d_off = nullptr;
+  size_t args_bytes = 0;
+  int n_off = 0;
+  int nblk = 0;
+  size_t smem = 0, smem_ev = 0;
+};
+// (re)allocates the device tables of b as needed and copies args and off in (synchronous)
+cudaError_t upload_batch(BatchLaunch* b, const void* args, size_t bytes, const std::vector<int>& off);
+void free_batch(BatchLaunch* b);
+cudaError_t prepare_pairs_batch(const std::vector<relres_ctx*>& cs, BatchLaunch* b);
+cudaError_t launch_pairs_batch(cudaStream_t s, bool fp64, int acc, bool ev, const BatchLaunch& b, int nrep);
+cudaError_t prepare_drift_batch(const std::vector<relres_ctx*>& cs, const std::vector<StepParams>& sp,
+                                double* const* d_vel, BatchLaunch* b);
+cudaError_t launch_drift_batch(cudaStream_t s, bool fp64, bool ev, const BatchLaunch& b, int nrep);
+cudaError_t prepare_sum_batch(const std::vector<relres_ctx*>& cs, const std::vector<StepParams>& sp,
+                              double* const* d_vel, BatchLaunch* b);
+cudaError_t launch_sum_batch(cudaStream_t s, bool fp64, int k, const BatchLaunch& b, int nrep);
+// one thread per replica: opens replica r's rebuild node h[r] iff its displacement trigger fired
+cudaError_t launch_decide_batch(cudaStream_t s, DevState* const* d_states, const cudaGraphConditionalHandle* d_h,
+                                int nrep);
+
 // MD steps take the segmented drift + bonded kernel and k_sum
 inline bool step_segments(const relres_ctx* c) { return c->seg_ok && c->use_seg; }
 

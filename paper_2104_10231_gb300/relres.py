@@ -38,7 +38,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
             "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled",
             "relres_set_list_caps", "relres_set_prune", "relres_measure_rates", "relres_get_list",
-            "relres_eval_recip", "relres_set_force_accumulation"]
+            "relres_eval_recip", "relres_set_force_accumulation", "relres_batch_get_info"]
 RELRES_STATIC_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev", "prune"]
 
@@ -133,6 +133,7 @@ def load():
     L.relres_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
     L.relres_batch_step.argtypes = [vp, C.c_int, C.c_double, C.POINTER(vp), C.POINTER(vp), _dp, C.c_double,
                                     C.POINTER(C.c_uint64), C.c_int, C.POINTER(vp)]
+    L.relres_batch_get_info.argtypes = [vp, C.POINTER(C.c_int)]
     L.relres_batch_last_error.argtypes = [vp]
     L.relres_batch_last_error.restype = C.c_char_p
     L.relres_batch_destroy.argtypes = [vp]
@@ -518,6 +519,13 @@ class Batch:
         if st != RELRES_OK:
             msg = (load().relres_batch_last_error(self.handle) or b"").decode()
             raise RelresError(st, msg)
+
+    def single_launch(self):
+        """1: the last step ran every replica in shared launches; 0: one graph
+        branch per replica; -1: no step yet."""
+        v = C.c_int(-1)
+        _check(load().relres_batch_get_info(self.handle, C.byref(v)))
+        return v.value
 
     def close(self):
         if self.handle:

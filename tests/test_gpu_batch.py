@@ -1,6 +1,9 @@
 """Batches of independent replicas (relres_batch_step): every block of steps of
-all replicas runs as one CUDA graph; the results must be bit-identical to
-stepping each context alone with the same arguments."""
+all replicas runs as one CUDA graph, with one drift, one pair and one
+force-sum launch per step covering every replica where the replicas allow it
+(same precision and accumulation) and one graph branch per replica otherwise.
+Both forms must give the bits of stepping each context alone with the same
+arguments, and FP64 batches the oracle's velocity Verlet + CSVR."""
 import numpy as np
 import pytest
 
@@ -69,6 +72,7 @@ def test_batch_matches_each_replica_stepped_alone(torch):
         assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy()), k
         assert np.array_equal(t1.cpu().numpy(), t2.cpu().numpy()), k
     assert max(c.stats()["n_builds"] for c, _, _, _ in batch_ctx) >= 3
+    assert batch.single_launch() == 1
     batch.close()
     for c, _, _, _ in solo + batch_ctx:
         c.close()
@@ -119,6 +123,7 @@ def test_fp64_batch_of_uneven_replicas_matches_oracle_md(torch):
                [s.temperature for s in systems], 100.0, seeds, thermo_every=1,
                d_thermo=[th for _, _, _, th in ctxs])
     torch.cuda.synchronize()
+    assert batch.single_launch() == 1
     for k, ((ctx, p, v, th), s, sd) in enumerate(zip(ctxs, systems, seeds)):
         po, vo, tho = O.md(s.pos, s.vel, s.box, s.masses, s.types, O.table_for(s), s.n_types, s.excl, s.topo,
                            steps, dt, t_target=s.temperature, tau=100.0, seed=sd)
@@ -133,4 +138,38 @@ def test_fp64_batch_of_uneven_replicas_matches_oracle_md(torch):
         assert ctx.stats()["n_steps"] == steps
     batch.close()
     for c, _, _, _ in ctxs:
+        c.close()
+
+
+def test_mixed_precision_batch_takes_graph_branches_and_matches_solo(torch):
+    """Replicas whose kernels cannot share a launch (one FP64, one FP32) run
+    on graph branches, with the bits of stepping each alone."""
+    systems = [S.propane(n_mol=216, temperature=230.0, seed=41), S.neopentane(n_mol=400, temperature=250.0, seed=42)]
+    precs = [R.RELRES_PREC_FP64, R.RELRES_PREC_FP32]
+
+    def make():
+        out = []
+        for s, pr in zip(systems, precs):
+            ctx = R.Context(R.params_for(s, pr), R.topology_for(s))
+            ctx.set_pair_config(0)
+            p = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+            v = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+            ctx.build_neighbors(p, s.box)
+            out.append((ctx, p, v))
+        return out
+
+    temps = [s.temperature for s in systems]
+    solo = make()
+    for (c, p, v), t, sd in zip(solo, temps, (3, 4)):
+        c.step(60, 1.0, p, v, t_target=t, tau_fs=100.0, seed=sd)
+    both = make()
+    batch = R.Batch([c for c, _, _ in both])
+    batch.step(60, 1.0, [p for _, p, _ in both], [v for _, _, v in both], temps, 100.0, [3, 4])
+    torch.cuda.synchronize()
+    assert batch.single_launch() == 0
+    for (c1, p1, v1), (c2, p2, v2) in zip(solo, both):
+        assert np.array_equal(p1.cpu().numpy(), p2.cpu().numpy())
+        assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy())
+    batch.close()
+    for c, _, _ in solo + both:
         c.close()

@@ -84,6 +84,7 @@ def test_compute_after_displacements_between_the_thresholds(torch):
     out = []
     for delta in (0.5, 0.0):
         ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+        ctx.set_force_accumulation(R.RELRES_ACC_FP32)  # running sums: pruning keeps the bits
         ctx.set_prune(delta)
         p = _dev(torch, s.pos)
         ctx.build_neighbors(p, s.box)
@@ -112,6 +113,7 @@ def test_compute_after_displacements_between_the_thresholds(torch):
 def test_prune_can_be_switched_on_and_off(torch):
     s = S.neopentane(n_mol=400, seed=3)
     ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+    ctx.set_force_accumulation(R.RELRES_ACC_FP32)  # running sums: pruning keeps the bits
     p = _dev(torch, s.pos)
     ctx.build_neighbors(p, s.box)
     forces = []
