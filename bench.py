@@ -423,6 +423,7 @@ def ours(args):
         out["differentiable"] = differentiable_leg(torch, R, S, stream)
     if args.batch_replicas > 0:
         out["batched"] = batched_leg(torch, R, S, args.batch_replicas, args.batch_steps)
+        out["batched_small"] = small_batch_leg(torch, R, S, args.batch_replicas, args.batch_steps)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
     if rank == 0 and world == 1 and not args.no_small:
@@ -613,15 +614,24 @@ def batched_leg(torch, R, S, n_rep, steps, seed=4242):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
-    # batched: every replica in the same drift, pair and force-sum launches
+    # batched, both forms on the same replicas: one graph branch per replica
+    # (its own kernels) and single launches covering every replica
     ctxs = make()
     bstream = torch.cuda.Stream()
     batch = R.Batch([c for c, _, _ in ctxs], stream=bstream)
     pos = [p for _, p, _ in ctxs]
     vel = [v for _, _, v in ctxs]
-    batch.step(20, 2.0, pos, vel, temps, 100.0, seeds)  # warm-up: autotuning, graph capture
-    batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)  # capture of the timed block shape
-    t_batch = timed(bstream, lambda: batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds))
+    forms = {}
+    for mode, name in ((0, "graph_branches"), (1, "single_launch")):
+        batch.set_mode(mode)
+        batch.step(20, 2.0, pos, vel, temps, 100.0, seeds)  # warm-up: autotuning, graph capture
+        batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)  # capture of the timed block shape
+        secs = timed(bstream, lambda: batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds))
+        forms[name] = {"value": n_atoms * steps / secs, "ms_per_step": secs / steps * 1e3}
+    batch.set_mode(-1)
+    batch.step(1, 2.0, pos, vel, temps, 100.0, seeds)
+    auto = "single_launch" if batch.single_launch() == 1 else "graph_branches"
+    t_batch = n_atoms * steps / forms[auto]["value"]
     batch.close()
     for c, _, _ in ctxs:
         c.close()
@@ -641,11 +651,47 @@ def batched_leg(torch, R, S, n_rep, steps, seed=4242):
     return {"workload": f"{n_rep} replicas, seeded sizes 1k-50k atoms ({n_atoms} atoms in all), alternately "
                         "propane-like (k^3 molecules) and neopentane-like, T in U[200, 300] K, CSVR, dt 2 fs, FP32",
             "steps": steps, "value": n_atoms * steps / t_batch, "unit": "atom-steps/s",
-            "ms_per_step": t_batch / steps * 1e3,
+            "ms_per_step": t_batch / steps * 1e3, "form": auto, "forms": forms,
             "one_after_the_other": {"value": n_atoms * steps / t_seq, "ms_per_step": t_seq / steps * 1e3},
             "timing": "CUDA events on the batch stream around one relres_batch_step call (the per-call set-up "
                       "of every replica included); the sequential run: events on the default stream around "
                       "one relres_step per replica"}
+
+
+def small_batch_leg(torch, R, S, n_rep=128, steps=200):
+    """Many small replicas (648-atom propane-like liquids, seeded), where the
+    launch overhead of separate systems dominates: the batch in its two forms
+    (single launches covering every replica, one graph branch per replica)."""
+    systems = [S.propane(seed=100 + k) for k in range(n_rep)]
+    n_atoms = sum(s.n_atoms for s in systems)
+    ctxs = []
+    for s in systems:
+        ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+        p = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+        v = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+        ctx.build_neighbors(p, s.box)
+        ctxs.append((ctx, p, v))
+    st = torch.cuda.Stream()
+    batch = R.Batch([c for c, _, _ in ctxs], stream=st)
+    pos, vel = [p for _, p, _ in ctxs], [v for _, _, v in ctxs]
+    temps, seeds = [s.temperature for s in systems], list(range(n_rep))
+    out = {"workload": f"{n_rep} replicas of the 648-atom propane-like liquid ({n_atoms} atoms), FP32, CSVR, dt 2 fs",
+           "steps": steps, "unit": "atom-steps/s"}
+    for mode, name in ((1, "single_launch"), (0, "graph_branches")):
+        batch.set_mode(mode)
+        batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)
+        e1.record(st)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) * 1e-3
+        out[name] = {"value": n_atoms * steps / secs, "ms_per_step": secs / steps * 1e3}
+    batch.close()
+    for c, _, _ in ctxs:
+        c.close()
+    return out
 
 
 def differentiable_leg(torch, R, S, stream, n_snap=64, n_mol=4000):

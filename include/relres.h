@@ -454,12 +454,24 @@ relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, 
                                 int thermo_every, double* const* d_thermo);
 const char* relres_batch_last_error(relres_batch* batch);
 /* Which form the last relres_batch_step ran: *single_launch = 1 when every
- * replica shared one drift, one pair and one force-sum launch per step (all
- * replicas with the same precision and force accumulation, molecules of at
- * most 256 atoms; the pair kernel then runs one thread per atom in 256-thread
- * blocks whatever relres_set_pair_config chose), 0 when each replica ran its
- * own kernels on a branch of the graph; -1 before the first step. */
+ * replica shared one drift, one pair and one force-sum launch per step (and
+ * the list rebuilds of the replicas that needed one shared six launches), 0
+ * when each replica ran its own kernels on a branch of the graph; -1 before
+ * the first step. */
 relres_status relres_batch_get_info(relres_batch* batch, int* single_launch);
+
+/* Form of later relres_batch_step calls.  mode 1: single launches, which
+ * need every replica with the same precision and force accumulation and
+ * molecules of at most 256 atoms (RELRES_ERR_ARG at the next step otherwise);
+ * the pair kernel then runs one thread per atom in 256-thread blocks whatever
+ * relres_set_pair_config chose.  mode 0: one graph branch per replica with
+ * its own kernels.  mode -1 (the default): single launches when the replicas
+ * allow them and hold at most RELRES_BATCH_FUSE_MEAN_ATOMS atoms on average
+ * (there the launch overhead of many small systems dominates; for larger
+ * replicas the kernels of each system alone run faster), else branches.
+ * Drops the captured graph.  Errors: RELRES_ERR_ARG (unknown mode). */
+#define RELRES_BATCH_FUSE_MEAN_ATOMS 16384
+relres_status relres_batch_set_mode(relres_batch* batch, int mode);
 void relres_batch_destroy(relres_batch* batch);
 
 /*

@@ -1285,14 +1285,13 @@ struct relres_batch {
   bool own_stream = false;
   std::string err;
   // single-launch path: one drift, one pair and one force-sum launch per step
-  // for every replica (argument tables in device memory), one decide kernel
-  // opening each replica's conditional rebuild node
+  // for every replica (argument tables in device memory), and the list
+  // rebuilds of the replicas that need one in seven launches for all of them
   bool fused = false;
+  int mode = -1;  // relres_batch_set_mode
   BatchLaunch bl_pair, bl_drift, bl_sum;
-  DevState** d_states = nullptr;                 // [nrep]
-  cudaGraphConditionalHandle* d_handles = nullptr;  // [blk][nrep]
-  int handles_cap = 0;
-  std::vector<cudaGraphConditionalHandle> h_handles;
+  RebuildBatch rebuild;
+  DevState** d_states = nullptr;  // [nrep]
 };
 
 // Replicas can share single launches when the kernels' template arguments
@@ -1361,7 +1360,13 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
       b->dt == sp[0].dt && b->tau == sp[0].tau && b->keys == keys)
     return RELRES_OK;
   batch_drop_graph(b);
-  b->fused = batch_can_fuse(b);
+  const bool can = batch_can_fuse(b);
+  if (b->mode == 1 && !can)
+    return batch_fail(b, RELRES_ERR_ARG,
+                      "single launches need replicas of one precision and force accumulation, molecules <= 256 atoms");
+  long long atoms = 0;
+  for (relres_ctx* c : b->ctx) atoms += c->n;
+  b->fused = b->mode == 1 || (b->mode == -1 && can && atoms <= (long long)RELRES_BATCH_FUSE_MEAN_ATOMS * nr);
   if (b->fused) {
     const relres_status fs = batch_graph_fused(b, sp, d_vel, blk, done);
     if (fs != RELRES_OK) return fs;
@@ -1428,9 +1433,9 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
 
 // The fused form of one block of steps (see relres_batch::fused), captured
 // on the batch stream: per replica the rollback snapshot and thermostat
-// draws, then per step the batched drift, the batched decide kernel, every
-// replica's conditional rebuild node on its own branch, the batched pair
-// kernel and the batched force sum.
+// draws, then per step the batched drift, the batched list rebuild of the
+// replicas whose trigger fired, the batched pair kernel and the batched force
+// sum.
 static relres_status batch_graph_fused(relres_batch* b, const std::vector<StepParams>& sp, double* const* d_vel,
                                        int blk, int done) {
   const int nr = int(b->ctx.size());
@@ -1440,31 +1445,18 @@ static relres_status batch_graph_fused(relres_batch* b, const std::vector<StepPa
   cudaError_t e = prepare_pairs_batch(b->ctx, &b->bl_pair);
   if (e == cudaSuccess) e = prepare_drift_batch(b->ctx, sp, d_vel, &b->bl_drift);
   if (e == cudaSuccess) e = prepare_sum_batch(b->ctx, sp, d_vel, &b->bl_sum);
+  if (e == cudaSuccess) e = prepare_rebuild_batch(b->ctx, &b->rebuild);
   if (e == cudaSuccess && !b->d_states) e = cudaMalloc(&b->d_states, sizeof(DevState*) * nr);
   if (e == cudaSuccess) {
     std::vector<DevState*> st(nr);
     for (int r = 0; r < nr; ++r) st[r] = b->ctx[r]->d_state;
     e = cudaMemcpy(b->d_states, st.data(), sizeof(DevState*) * nr, cudaMemcpyHostToDevice);
   }
-  if (e == cudaSuccess && b->handles_cap < blk * nr) {
-    if (b->d_handles) cudaFree(b->d_handles);
-    b->d_handles = nullptr;
-    b->handles_cap = 0;
-    e = cudaMalloc(&b->d_handles, sizeof(cudaGraphConditionalHandle) * size_t(blk) * nr);
-    if (e == cudaSuccess) b->handles_cap = blk * nr;
-  }
+  if (e == cudaSuccess && !b->ctx[0]->body_stream)
+    e = cudaStreamCreateWithFlags(&b->ctx[0]->body_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
-  b->h_handles.assign(size_t(blk) * nr, 0);
-  for (int r = 0; r < nr; ++r)
-    if (!b->ctx[r]->body_stream) {
-      e = cudaStreamCreateWithFlags(&b->ctx[r]->body_stream, cudaStreamNonBlocking);
-      if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
-    }
   e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
-  relres_status s = RELRES_OK;
-  std::vector<cudaStream_t> own(nr);
-  for (int r = 0; r < nr; ++r) own[r] = b->ctx[r]->stream;
   b->k_parent.assign(nr, 0);
   // snapshot of each replica for the rollback, and its thermostat draws
   for (int r = 0; r < nr && e == cudaSuccess; ++r) {
@@ -1477,44 +1469,39 @@ static relres_status batch_graph_fused(relres_batch* b, const std::vector<StepPa
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) {
+      const cudaStream_t own = c->stream;
       c->stream = b->stream;
       const long long n0 = c->n_launches;
       e = launch_csvr_draws(c, sp[r], blk);
       b->k_parent[r] += c->n_launches - n0;
       c->n_launches = n0;
-      c->stream = own[r];
+      c->stream = own;
     }
   }
+  relres_status s = RELRES_OK;
   for (int k = 0; k < blk && e == cudaSuccess && s == RELRES_OK; ++k) {
     const bool ev_step = sp[0].thermo_every > 0 && ((done + k + 1) % sp[0].thermo_every) == 0;
     e = launch_drift_batch(b->stream, fp64, ev_step, b->bl_drift, nr);
+    // the work list kernel opens one conditional node holding the six batched
+    // rebuild kernels when any replica's trigger fired
     cudaStreamCaptureStatus cst;
-    cudaGraph_t g = nullptr;
-    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(b->stream, &cst, nullptr, &g, nullptr, nullptr, nullptr);
-    for (int r = 0; r < nr && e == cudaSuccess; ++r)
-      e = cudaGraphConditionalHandleCreate(&b->h_handles[size_t(k) * nr + r], g, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) e = launch_decide_batch(b->stream, b->d_states, b->d_handles + size_t(k) * nr, nr);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
-    for (int r = 0; r < nr && e == cudaSuccess && s == RELRES_OK; ++r) {
-      relres_ctx* c = b->ctx[r];
-      e = cudaStreamWaitEvent(b->fork[r], b->ev_fork, 0);
-      if (e != cudaSuccess) break;
-      const long long n0 = c->n_launches;
-      c->stream = b->fork[r];
-      s = add_conditional(c, b->h_handles[size_t(k) * nr + r], [c]() {
-        const cudaError_t eb = launch_rebuild(c, c->d_open);
-        return eb == cudaSuccess ? launch_lists(c, c->d_open) : eb;
-      });
-      c->stream = own[r];
-      c->n_launches = n0;
-      if (s != RELRES_OK) b->err = "replica " + std::to_string(r) + " (capture): " + c->err;
-      if (s == RELRES_OK) e = cudaEventRecord(b->ev_join[r], b->fork[r]);
-      if (s == RELRES_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[r], 0);
+    cudaGraph_t cg = nullptr;
+    cudaGraphConditionalHandle any = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(b->stream, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&any, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = launch_worklist(b->stream, b->rebuild, b->d_states, nr, any);
+    if (e == cudaSuccess) {
+      relres_ctx* c0 = b->ctx[0];  // lends its body stream for the capture of the node's body
+      const cudaStream_t own = c0->stream;
+      c0->stream = b->stream;
+      s = add_conditional(c0, any, [b, nr, c0]() { return launch_rebuild_batch(c0->stream, b->rebuild, nr); });
+      c0->stream = own;
+      if (s != RELRES_OK) b->err = "batch rebuild node (capture): " + c0->err;
     }
     if (e == cudaSuccess && s == RELRES_OK) e = launch_pairs_batch(b->stream, fp64, acc, ev_step, b->bl_pair, nr);
     if (e == cudaSuccess && s == RELRES_OK) e = launch_sum_batch(b->stream, fp64, k, b->bl_sum, nr);
   }
-  // every replica takes part in the step's drift, decide, pair and force-sum launches
+  // every replica takes part in the step's drift, work-list, pair and force-sum launches
   for (int r = 0; r < nr; ++r) b->k_parent[r] += 4LL * blk;
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -1525,11 +1512,6 @@ static relres_status batch_graph_fused(relres_batch* b, const std::vector<StepPa
     if (e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
   }
   if (g) cudaGraphDestroy(g);
-  if (s == RELRES_OK) {
-    e = cudaMemcpy(b->d_handles, b->h_handles.data(), sizeof(cudaGraphConditionalHandle) * b->h_handles.size(),
-                   cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
-  }
   if (s != RELRES_OK) batch_drop_graph(b);
   return s;
 }
@@ -1601,6 +1583,8 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
       s = read_state(c);
       if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + c->err);
       const long long kpr = (!b->fused && c->prune_on && !pairs_prune(c)) ? 1 : 0;
+      // a rebuild body of six kernels runs per rebuild (the fused form's
+      // batched kernels are counted for every replica they rebuild)
       c->n_launches += b->k_parent[r] + 6LL * std::max(0LL, c->h_state->n_builds - builds0[r]) +
                        kpr * std::max(0LL, (long long)c->h_state->n_prunes - prunes0[r]);
       flags[r] = c->h_state->flags;
@@ -1641,6 +1625,14 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
 
 const char* relres_batch_last_error(relres_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
+relres_status relres_batch_set_mode(relres_batch* b, int mode) {
+  if (!b || mode < -1 || mode > 1) return RELRES_ERR_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  b->mode = mode;
+  return RELRES_OK;
+}
+
 relres_status relres_batch_get_info(relres_batch* b, int* single_launch) {
   if (!b || !single_launch) return RELRES_ERR_ARG;
   *single_launch = b->valid ? (b->fused ? 1 : 0) : -1;
@@ -1654,8 +1646,8 @@ void relres_batch_destroy(relres_batch* b) {
   free_batch(&b->bl_pair);
   free_batch(&b->bl_drift);
   free_batch(&b->bl_sum);
+  free_rebuild_batch(&b->rebuild);
   if (b->d_states) cudaFree(b->d_states);
-  if (b->d_handles) cudaFree(b->d_handles);
   for (cudaStream_t st : b->fork)
     if (st) cudaStreamDestroy(st);
   for (cudaEvent_t ev : b->ev_join)

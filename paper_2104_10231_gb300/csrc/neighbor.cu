@@ -46,16 +46,18 @@ __device__ __forceinline__ int linear_cell(int h0, int h1, int h2, int n0, int n
 
 // Cell (dense Morton rank) of every atom in each grid, and its arrival rank
 // inside that cell (the value the count had before this atom was added).
-__global__ void k_bin(int n, const unsigned* gate, const unsigned long long* __restrict__ xfx,
-                      const int* __restrict__ type, int hyb_mask, int f0, int f1, int f2,
-                      const int* __restrict__ frank, int* fcount, int with_cg, int c0, int c1, int c2,
-                      const int* __restrict__ crank, int* ccount, int* __restrict__ cell_fg,
-                      int* __restrict__ slot_fg, int* __restrict__ cell_cg, int* __restrict__ slot_cg,
-                      unsigned* flags) {
+// (block bid of nblk; the single-system kernel passes blockIdx.x, gridDim.x)
+__device__ __forceinline__ void bin_body(int bid, int nblk, int n, const unsigned* gate,
+                                        const unsigned long long* __restrict__ xfx, const int* __restrict__ type,
+                                        int hyb_mask, int f0, int f1, int f2, const int* __restrict__ frank,
+                                        int* fcount, int with_cg, int c0, int c1, int c2,
+                                        const int* __restrict__ crank, int* ccount, int* __restrict__ cell_fg,
+                                        int* __restrict__ slot_fg, int* __restrict__ cell_cg,
+                                        int* __restrict__ slot_cg, unsigned* flags) {
   if (gate_closed(gate)) return;
   const int nf = f0 * f1 * f2, nc = c0 * c1 * c2;
   bool bad = false;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     const int h0 = hi32(xfx[3 * i]), h1 = hi32(xfx[3 * i + 1]), h2 = hi32(xfx[3 * i + 2]);
     // self-check: every index is tested before it is used (a failure is
     // reported through F_BADCELL and the access skipped)
@@ -83,22 +85,33 @@ __global__ void k_bin(int n, const unsigned* gate, const unsigned long long* __r
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, F_BADCELL);
 }
 
+__global__ void k_bin(int n, const unsigned* gate, const unsigned long long* __restrict__ xfx,
+                      const int* __restrict__ type, int hyb_mask, int f0, int f1, int f2,
+                      const int* __restrict__ frank, int* fcount, int with_cg, int c0, int c1, int c2,
+                      const int* __restrict__ crank, int* ccount, int* __restrict__ cell_fg,
+                      int* __restrict__ slot_fg, int* __restrict__ cell_cg, int* __restrict__ slot_cg,
+                      unsigned* flags) {
+  bin_body(blockIdx.x, gridDim.x, n, gate, xfx, type, hyb_mask, f0, f1, f2, frank, fcount, with_cg, c0, c1, c2,
+           crank, ccount, cell_fg, slot_fg, cell_cg, slot_cg, flags);
+}
+
 // One block per grid: exclusive scan of counts into start[0..ncell], counts
 // reset to zero (they become the scatter cursors).  Tiles of 4 cells per
 // thread, scanned block-wide with warp shuffles, a running carry between tiles.
-__global__ void k_scan(const unsigned* gate, int valid0, int ncell0, int* start0, int* count0, int valid1,
-                       int ncell1, int* start1, int* count1, DevState* st) {
+__device__ __forceinline__ void scan_body(int bid, const unsigned* gate, int valid0, int ncell0, int* start0,
+                                         int* count0, int valid1, int ncell1, int* start1, int* count1,
+                                         DevState* st) {
   if (gate_closed(gate)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {  // list statistics of this build
+  if (bid == 0 && threadIdx.x == 0) {  // list statistics of this build
     st->max_fg = 0;
     st->max_cg = 0;
     st->tot_fg = 0;
     st->tot_cg = 0;
   }
-  const int valid = blockIdx.x == 0 ? valid0 : valid1;
-  const int ncell = blockIdx.x == 0 ? ncell0 : ncell1;
-  int* const start = blockIdx.x == 0 ? start0 : start1;
-  int* const count = blockIdx.x == 0 ? count0 : count1;
+  const int valid = bid == 0 ? valid0 : valid1;
+  const int ncell = bid == 0 ? ncell0 : ncell1;
+  int* const start = bid == 0 ? start0 : start1;
+  int* const count = bid == 0 ? count0 : count1;
   if (!valid) return;
   __shared__ int sh[1024 / 32];
   __shared__ int s_carry;
@@ -145,16 +158,32 @@ __global__ void k_scan(const unsigned* gate, int valid0, int ncell0, int* start0
   if (threadIdx.x == 0) start[ncell] = s_carry;
 }
 
+__global__ void k_scan(const unsigned* gate, int valid0, int ncell0, int* start0, int* count0, int valid1,
+                       int ncell1, int* start1, int* count1, DevState* st) {
+  scan_body(blockIdx.x, gate, valid0, ncell0, start0, count0, valid1, ncell1, start1, count1, st);
+}
+
+__device__ __forceinline__ void scatter_body(int bid, int nblk, int n, const unsigned* gate,
+                                            const int* __restrict__ type, int hyb_mask,
+                                            const int* __restrict__ fstart, int with_cg,
+                                            const int* __restrict__ cstart, const int* __restrict__ cell_fg,
+                                            const int* __restrict__ slot_fg, const int* __restrict__ cell_cg,
+                                            const int* __restrict__ slot_cg, int* __restrict__ perm_fg,
+                                            int* __restrict__ perm_cg) {
+  if (gate_closed(gate)) return;
+  for (int i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
+    perm_fg[fstart[cell_fg[i]] + slot_fg[i]] = i;
+    if (with_cg && ((hyb_mask >> type[i]) & 1)) perm_cg[cstart[cell_cg[i]] + slot_cg[i]] = i;
+  }
+}
+
 __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ type, int hyb_mask,
                           const int* __restrict__ fstart, int with_cg, const int* __restrict__ cstart,
                           const int* __restrict__ cell_fg, const int* __restrict__ slot_fg,
                           const int* __restrict__ cell_cg, const int* __restrict__ slot_cg,
                           int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
-  if (gate_closed(gate)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    perm_fg[fstart[cell_fg[i]] + slot_fg[i]] = i;
-    if (with_cg && ((hyb_mask >> type[i]) & 1)) perm_cg[cstart[cell_cg[i]] + slot_cg[i]] = i;
-  }
+  scatter_body(blockIdx.x, gridDim.x, n, gate, type, hyb_mask, fstart, with_cg, cstart, cell_fg, slot_fg, cell_cg,
+               slot_cg, perm_fg, perm_cg);
 }
 
 // One warp per cell: the cell's atoms put in index order (the scatter order
@@ -163,14 +192,14 @@ __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ t
 // per-warp shared-memory copy; larger cells fall back to an insertion sort by
 // one lane.  Resets the cell cursor.
 constexpr int kSortSmem = 256;
-__global__ void __launch_bounds__(kThreads) k_sort_cells(const unsigned* gate, int fn, const int* fstart,
-                                                         int* fcount, int cn, const int* cstart, int* ccount,
-                                                         int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
+__device__ __forceinline__ void sort_body(int bid, int nblk, const unsigned* gate, int fn, const int* fstart,
+                                         int* fcount, int cn, const int* cstart, int* ccount,
+                                         int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
   if (gate_closed(gate)) return;
   __shared__ int s_v[kThreads / 32][kSortSmem];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < fn + cn; t += nwarps) {
+  const int nwarps = (nblk * blockDim.x) >> 5;
+  for (int t = (bid * blockDim.x + threadIdx.x) >> 5; t < fn + cn; t += nwarps) {
     const bool fg = t < fn;
     const int c = fg ? t : t - fn;
     const int* const start = fg ? fstart : cstart;
@@ -209,14 +238,21 @@ __global__ void __launch_bounds__(kThreads) k_sort_cells(const unsigned* gate, i
   }
 }
 
-__global__ void k_pack(int n, int n_h, const unsigned* gate, const unsigned long long* __restrict__ xfx,
-                       const int* __restrict__ type, const int* __restrict__ perm_fg,
-                       const int* __restrict__ perm_cg, int* __restrict__ rank_fg,
-                       int* __restrict__ rank_cg, int4* __restrict__ pos_fg,
-                       int4* __restrict__ pos_cg, Pos64* __restrict__ pos_fg64,
-                       Pos64* __restrict__ pos_cg64, int fp64, int4* __restrict__ ref) {
+__global__ void __launch_bounds__(kThreads) k_sort_cells(const unsigned* gate, int fn, const int* fstart,
+                                                         int* fcount, int cn, const int* cstart, int* ccount,
+                                                         int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
+  sort_body(blockIdx.x, gridDim.x, gate, fn, fstart, fcount, cn, cstart, ccount, perm_fg, perm_cg);
+}
+
+__device__ __forceinline__ void pack_body(int bid, int nblk, int n, int n_h, const unsigned* gate,
+                                         const unsigned long long* __restrict__ xfx, const int* __restrict__ type,
+                                         const int* __restrict__ perm_fg, const int* __restrict__ perm_cg,
+                                         int* __restrict__ rank_fg, int* __restrict__ rank_cg,
+                                         int4* __restrict__ pos_fg, int4* __restrict__ pos_cg,
+                                         Pos64* __restrict__ pos_fg64, Pos64* __restrict__ pos_cg64, int fp64,
+                                         int4* __restrict__ ref) {
   if (gate_closed(gate)) return;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+  for (int s = bid * blockDim.x + threadIdx.x; s < n; s += nblk * blockDim.x) {
     const int i = perm_fg[s];
     const unsigned long long x = xfx[3 * i], y = xfx[3 * i + 1], z = xfx[3 * i + 2];
     const int t = type[i];
@@ -233,6 +269,16 @@ __global__ void k_pack(int n, int n_h, const unsigned* gate, const unsigned long
       if (fp64) pos_cg64[s] = Pos64{(long long)xj, (long long)yj, (long long)zj, type[j]};
     }
   }
+}
+
+__global__ void k_pack(int n, int n_h, const unsigned* gate, const unsigned long long* __restrict__ xfx,
+                       const int* __restrict__ type, const int* __restrict__ perm_fg,
+                       const int* __restrict__ perm_cg, int* __restrict__ rank_fg,
+                       int* __restrict__ rank_cg, int4* __restrict__ pos_fg,
+                       int4* __restrict__ pos_cg, Pos64* __restrict__ pos_fg64,
+                       Pos64* __restrict__ pos_cg64, int fp64, int4* __restrict__ ref) {
+  pack_body(blockIdx.x, gridDim.x, n, n_h, gate, xfx, type, perm_fg, perm_cg, rank_fg, rank_cg, pos_fg, pos_cg,
+            pos_fg64, pos_cg64, fp64, ref);
 }
 
 struct ListArgs {
@@ -488,16 +534,225 @@ static int blocks_for(int n) {
   return b < 1 ? 1 : (b > 152 * 4 ? 152 * 4 : b);
 }
 
+// ---- batches (relres_batch_step): the list rebuild of every replica whose
+// displacement trigger fired, in six launches for the whole batch.  After the
+// drift, k_worklist lists those replicas and, per kernel class, the prefix
+// sums of the blocks each of them takes in its own rebuild (the same counts as
+// launch_rebuild / launch_lists); each batched kernel then walks the work
+// items (replica, block) with a fixed grid, so a step in which few replicas
+// rebuild costs six short launches, and one in which none does, six empty ones.
+
+// Everything one replica's rebuild kernels take.
+struct BuildArgs {
+  int n, n_h_pack, hyb_mask, fp64;
+  const unsigned* gate;
+  const unsigned long long* xfx;
+  const int* type;
+  GridArgs gf, gc;
+  int* cell_fg;
+  int* slot_fg;
+  int* cell_cg;
+  int* slot_cg;
+  unsigned* flags;
+  int* perm_fg;
+  int* perm_cg;
+  int* rank_fg;
+  int* rank_cg;
+  int4* pos_fg;
+  int4* pos_cg;
+  Pos64* p64f;
+  Pos64* p64c;
+  int4* ref;
+  DevState* st;
+  ListArgs lfg, lcg;
+  int ncell_cg;
+};
+
+enum { kRbBin = 0, kRbScan, kRbScatter, kRbSort, kRbPack, kRbList, kRbClasses };
+
+// one block: wl[0] = number of rebuilding replicas, wl[1 .. nrep] their
+// indices, then per class k the prefix sums pre_k[0 .. count] at
+// wl + 1 + nrep + k (nrep + 1); nbt[k * nrep + r] = blocks of class k of replica r
+__global__ void __launch_bounds__(1024) k_worklist(DevState* const* st, int nrep, const int* __restrict__ nbt,
+                                                    int* __restrict__ wl, cudaGraphConditionalHandle any) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  int* rep = wl + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  for (int r0 = 0; r0 < nrep; r0 += blockDim.x) {
+    const int r = r0 + threadIdx.x;
+    const int f = (r < nrep && (st[r]->flags & F_REBUILD)) ? 1 : 0;
+    int incl = f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    int before = s_base;
+    for (int w = 0; w < wid; ++w) before += s_warp[w];
+    if (f) rep[before + incl - 1] = r;
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int w = 0; w < nw; ++w) s_base += s_warp[w];
+    __syncthreads();
+  }
+  const int count = s_base;
+  if (threadIdx.x == 0) {
+    wl[0] = count;
+    cudaGraphSetConditional(any, count > 0 ? 1u : 0u);  // the rebuild node runs iff a replica needs one
+  }
+  if (threadIdx.x < kRbClasses) {
+    int* pre = wl + 1 + nrep + threadIdx.x * (nrep + 1);
+    int acc = 0;
+    for (int i = 0; i < count; ++i) {
+      pre[i] = acc;
+      acc += nbt[threadIdx.x * nrep + rep[i]];
+    }
+    pre[count] = acc;
+  }
+}
+
+// Work item w of class K: replica *r, its block *b of *nb.
+template <int K>
+__device__ __forceinline__ int work_total(const int* wl, int nrep) {
+  return wl[1 + nrep + K * (nrep + 1) + wl[0]];
+}
+template <int K>
+__device__ __forceinline__ void work_item(const int* wl, const int* nbt, int nrep, int w, int* r, int* b, int* nb) {
+  const int count = wl[0];
+  const int* pre = wl + 1 + nrep + K * (nrep + 1);
+  int lo = 0, hi = count - 1;  // the last i with pre[i] <= w
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  *r = wl[1 + lo];
+  *b = w - pre[lo];
+  *nb = nbt[K * nrep + *r];
+}
+
+#define RELRES_BATCH_LOOP(K)                                       \
+  const int total = work_total<K>(wl, nrep);                       \
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {            \
+    int r, b, nb;                                                  \
+    work_item<K>(wl, nbt, nrep, w, &r, &b, &nb);                   \
+    const BuildArgs& sa = args[r];
+
+#define RELRES_BATCH_END \
+  }
+
+__global__ void __launch_bounds__(kThreads, 6) k_bin_batch(const BuildArgs* __restrict__ args, const int* __restrict__ wl,
+                            const int* __restrict__ nbt, int nrep) {
+  RELRES_BATCH_LOOP(kRbBin)
+  bin_body(b, nb, sa.n, sa.gate, sa.xfx, sa.type, sa.hyb_mask, sa.gf.n0, sa.gf.n1, sa.gf.n2, sa.gf.rank_of,
+           sa.gf.count, sa.gc.valid, sa.gc.n0, sa.gc.n1, sa.gc.n2, sa.gc.rank_of, sa.gc.count, sa.cell_fg,
+           sa.slot_fg, sa.cell_cg, sa.slot_cg, sa.flags);
+  RELRES_BATCH_END
+}
+
+__global__ void __launch_bounds__(1024) k_scan_batch(const BuildArgs* __restrict__ args, const int* __restrict__ wl,
+                                                     const int* __restrict__ nbt, int nrep) {
+  RELRES_BATCH_LOOP(kRbScan)
+  (void)nb;
+  scan_body(b, sa.gate, 1, sa.gf.ncell, sa.gf.start, sa.gf.count, sa.gc.valid, sa.gc.ncell, sa.gc.start,
+            sa.gc.count, sa.st);
+  RELRES_BATCH_END
+}
+
+__global__ void __launch_bounds__(kThreads, 6) k_scatter_batch(const BuildArgs* __restrict__ args, const int* __restrict__ wl,
+                                const int* __restrict__ nbt, int nrep) {
+  RELRES_BATCH_LOOP(kRbScatter)
+  scatter_body(b, nb, sa.n, sa.gate, sa.type, sa.hyb_mask, sa.gf.start, sa.gc.valid, sa.gc.start, sa.cell_fg,
+               sa.slot_fg, sa.cell_cg, sa.slot_cg, sa.perm_fg, sa.perm_cg);
+  RELRES_BATCH_END
+}
+
+__global__ void __launch_bounds__(kThreads, 6) k_sort_batch(const BuildArgs* __restrict__ args,
+                                                         const int* __restrict__ wl, const int* __restrict__ nbt,
+                                                         int nrep) {
+  RELRES_BATCH_LOOP(kRbSort)
+  sort_body(b, nb, sa.gate, sa.gf.ncell, sa.gf.start, sa.gf.count, sa.gc.valid ? sa.gc.ncell : 0, sa.gc.start,
+            sa.gc.count, sa.perm_fg, sa.perm_cg);
+  RELRES_BATCH_END
+}
+
+__global__ void __launch_bounds__(kThreads, 6) k_pack_batch(const BuildArgs* __restrict__ args, const int* __restrict__ wl,
+                             const int* __restrict__ nbt, int nrep) {
+  RELRES_BATCH_LOOP(kRbPack)
+  pack_body(b, nb, sa.n, sa.n_h_pack, sa.gate, sa.xfx, sa.type, sa.perm_fg, sa.perm_cg, sa.rank_fg, sa.rank_cg,
+            sa.pos_fg, sa.pos_cg, sa.p64f, sa.p64c, sa.fp64, sa.ref);
+  RELRES_BATCH_END
+}
+
+__global__ void __launch_bounds__(kListThreads, 8) k_list_batch(const BuildArgs* __restrict__ args,
+                                                             const int* __restrict__ wl,
+                                                             const int* __restrict__ nbt, int nrep) {
+  RELRES_BATCH_LOOP(kRbList)
+  const int ncell = sa.ncell_cg + sa.lfg.g.ncell;
+  for (int cb = b; cb < ncell; cb += nb) list_cell(sa.lfg, sa.lcg, sa.ncell_cg, cb);
+  RELRES_BATCH_END
+}
+
+#undef RELRES_BATCH_LOOP
+#undef RELRES_BATCH_END
+
+// Arguments of one system's rebuild (binning and both lists), gated on `gate`.
+static ListArgs list_args_fg(relres_ctx* c);
+static bool list_args_cg(relres_ctx* c, ListArgs* cg, int* ncell_cg);
+
+static BuildArgs build_args(relres_ctx* c, const unsigned* gate) {
+  BuildArgs b{};
+  b.gf = grid_args(c->gfg);
+  b.gc = grid_args(c->gcg);
+  if (!c->has_cg || c->n_h == 0) {
+    b.gc = b.gf;  // stand-in pointers, never used
+    b.gc.valid = 0;
+  }
+  b.n = c->n;
+  b.n_h_pack = b.gc.valid ? c->n_h : 0;
+  b.hyb_mask = c->hyb_mask;
+  b.fp64 = c->fp64 ? 1 : 0;
+  b.gate = gate;
+  b.xfx = c->d_xfx;
+  b.type = c->d_type;
+  b.cell_fg = c->d_cell_fg;
+  b.slot_fg = c->d_slot_fg;
+  b.cell_cg = c->d_cell_cg;
+  b.slot_cg = c->d_slot_cg;
+  b.flags = &c->d_state->flags;
+  b.perm_fg = c->d_perm_fg;
+  b.perm_cg = c->d_perm_cg;
+  b.rank_fg = c->d_rank_fg;
+  b.rank_cg = c->d_rank_cg;
+  b.pos_fg = c->d_pos_fg;
+  b.pos_cg = c->d_pos_cg;
+  b.p64f = c->fp64 ? c->d_pos_fg64 : static_cast<Pos64*>(c->d_dummy);
+  b.p64c = c->fp64 ? c->d_pos_cg64 : static_cast<Pos64*>(c->d_dummy);
+  b.ref = c->d_ref;
+  b.st = c->d_state;
+  b.lfg = list_args_fg(c);
+  b.lcg = b.lfg;  // stand-in when there is no CG list (its blocks are not launched)
+  b.ncell_cg = 0;
+  list_args_cg(c, &b.lcg, &b.ncell_cg);
+  return b;
+}
+
+// list-kernel blocks: persistent, one wave walks the cells (a closed gate costs one small launch)
+static int list_blocks(const BuildArgs& b) { return std::min(b.ncell_cg + b.gf.ncell, 152 * 8); }
+static int sort_cells_of(const BuildArgs& b) { return b.gf.ncell + (b.gc.valid ? b.gc.ncell : 0); }
+
 cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
   if (gate == nullptr) gate = c->d_open;
-  const GridArgs gf = grid_args(c->gfg);
-  GridArgs gc = grid_args(c->gcg);
-  if (!c->has_cg || c->n_h == 0) {
-    gc = gf;  // stand-in pointers, never used
-    gc.valid = 0;
-  }
-  Pos64* p64f = c->fp64 ? c->d_pos_fg64 : static_cast<Pos64*>(c->d_dummy);
-  Pos64* p64c = c->fp64 ? c->d_pos_cg64 : static_cast<Pos64*>(c->d_dummy);
+  const BuildArgs b = build_args(c, gate);
+  const GridArgs& gf = b.gf;
+  const GridArgs& gc = b.gc;
   const int nb = blocks_for(c->n);
   k_bin<<<nb, kThreads, 0, c->stream>>>(c->n, gate, c->d_xfx, c->d_type, c->hyb_mask, gf.n0, gf.n1,
                                         gf.n2, gf.rank_of, gf.count, gc.valid, gc.n0, gc.n1, gc.n2,
@@ -511,16 +766,68 @@ cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
                                             c->d_cell_fg, c->d_slot_fg, c->d_cell_cg, c->d_slot_cg,
                                             c->d_perm_fg, c->d_perm_cg);
   RELRES_LAUNCHED(c);
-  const int ncells = gf.ncell + (gc.valid ? gc.ncell : 0);
-  k_sort_cells<<<blocks_for(32 * ncells), kThreads, 0, c->stream>>>(gate, gf.ncell, gf.start, gf.count,
-                                                               gc.valid ? gc.ncell : 0, gc.start, gc.count,
-                                                               c->d_perm_fg, c->d_perm_cg);
+  k_sort_cells<<<blocks_for(32 * sort_cells_of(b)), kThreads, 0, c->stream>>>(
+      gate, gf.ncell, gf.start, gf.count, gc.valid ? gc.ncell : 0, gc.start, gc.count, c->d_perm_fg, c->d_perm_cg);
   RELRES_LAUNCHED(c);
-  k_pack<<<nb, kThreads, 0, c->stream>>>(c->n, gc.valid ? c->n_h : 0, gate, c->d_xfx, c->d_type,
-                                         c->d_perm_fg, c->d_perm_cg, c->d_rank_fg, c->d_rank_cg,
-                                         c->d_pos_fg, c->d_pos_cg, p64f, p64c, c->fp64 ? 1 : 0, c->d_ref);
+  k_pack<<<nb, kThreads, 0, c->stream>>>(c->n, b.n_h_pack, gate, c->d_xfx, c->d_type, c->d_perm_fg, c->d_perm_cg,
+                                         c->d_rank_fg, c->d_rank_cg, c->d_pos_fg, c->d_pos_cg, b.p64f, b.p64c,
+                                         b.fp64, c->d_ref);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_rebuild_batch(const std::vector<relres_ctx*>& cs, RebuildBatch* rb) {
+  const int nr = int(cs.size());
+  std::vector<BuildArgs> args(nr);
+  std::vector<int> nbt(size_t(kRbClasses) * nr);
+  for (int r = 0; r < nr; ++r) {
+    relres_ctx* c = cs[r];
+    args[r] = build_args(c, &c->d_state->flags);
+    nbt[kRbBin * nr + r] = blocks_for(c->n);
+    nbt[kRbScan * nr + r] = 2;
+    nbt[kRbScatter * nr + r] = blocks_for(c->n);
+    nbt[kRbSort * nr + r] = blocks_for(32 * sort_cells_of(args[r]));
+    nbt[kRbPack * nr + r] = blocks_for(c->n);
+    nbt[kRbList * nr + r] = list_blocks(args[r]);
+  }
+  const std::vector<int> off{0, nr};
+  cudaError_t e = upload_batch(&rb->args, args.data(), sizeof(BuildArgs) * nr, off);
+  if (e == cudaSuccess) e = upload_batch(&rb->nbt, nbt.data(), sizeof(int) * nbt.size(), off);
+  const size_t wl_ints = 1 + size_t(nr) + size_t(kRbClasses) * (nr + 1);
+  if (e == cudaSuccess && rb->wl_ints < wl_ints) {
+    if (rb->d_wl) cudaFree(rb->d_wl);
+    rb->d_wl = nullptr;
+    rb->wl_ints = 0;
+    e = cudaMalloc(&rb->d_wl, sizeof(int) * wl_ints);
+    if (e == cudaSuccess) rb->wl_ints = wl_ints;
+  }
+  return e;
+}
+
+cudaError_t launch_worklist(cudaStream_t s, const RebuildBatch& rb, DevState* const* d_states, int nrep,
+                            cudaGraphConditionalHandle any) {
+  k_worklist<<<1, 1024, 0, s>>>(d_states, nrep, static_cast<const int*>(rb.nbt.d_args), rb.d_wl, any);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild_batch(cudaStream_t s, const RebuildBatch& rb, int nrep) {
+  const auto* args = static_cast<const BuildArgs*>(rb.args.d_args);
+  const int* nbt = static_cast<const int*>(rb.nbt.d_args);
+  const int* wl = rb.d_wl;
+  k_bin_batch<<<152 * 4, kThreads, 0, s>>>(args, wl, nbt, nrep);
+  k_scan_batch<<<152, 1024, 0, s>>>(args, wl, nbt, nrep);
+  k_scatter_batch<<<152 * 4, kThreads, 0, s>>>(args, wl, nbt, nrep);
+  k_sort_batch<<<152 * 4, kThreads, 0, s>>>(args, wl, nbt, nrep);
+  k_pack_batch<<<152 * 4, kThreads, 0, s>>>(args, wl, nbt, nrep);
+  k_list_batch<<<152 * 8, kListThreads, 0, s>>>(args, wl, nbt, nrep);
+  return cudaGetLastError();
+}
+
+void free_rebuild_batch(RebuildBatch* rb) {
+  free_batch(&rb->args);
+  free_batch(&rb->nbt);
+  if (rb->d_wl) cudaFree(rb->d_wl);
+  *rb = RebuildBatch{};
 }
 
 // One thread: open the rebuild node of this step of a CUDA graph iff the
@@ -531,18 +838,6 @@ __global__ void k_decide(const DevState* st, cudaGraphConditionalHandle h, cudaG
   const unsigned f = st->flags;
   cudaGraphSetConditional(h, (f & F_REBUILD) ? 1u : 0u);
   if (with_prune) cudaGraphSetConditional(hp, (f & (F_REBUILD | F_PRUNE)) ? 1u : 0u);
-}
-
-// Batches: thread r opens replica r's rebuild node iff its trigger fired.
-__global__ void k_decide_batch(DevState* const* st, const cudaGraphConditionalHandle* h, int nrep) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < nrep) cudaGraphSetConditional(h[r], (st[r]->flags & F_REBUILD) ? 1u : 0u);
-}
-
-cudaError_t launch_decide_batch(cudaStream_t s, DevState* const* d_states, const cudaGraphConditionalHandle* d_h,
-                                int nrep) {
-  k_decide_batch<<<(nrep + 127) / 128, 128, 0, s>>>(d_states, d_h, nrep);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_decide(relres_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle hp,
@@ -667,24 +962,36 @@ cudaError_t launch_prune(relres_ctx* c, const unsigned* gate) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
-  if (gate == nullptr) gate = c->d_open;
+static ListArgs list_args_fg(relres_ctx* c) {
   const float s0 = float(c->box[0] / 4294967296.0), s1 = float(c->box[1] / 4294967296.0),
               s2 = float(c->box[2] / 4294967296.0);
   DevState* st = c->d_state;
   const double rf = c->rlist_fg_cut + c->prm.skin;
-  const ListArgs fg{c->n, c->d_pos_fg, c->d_perm_fg, grid_args(c->gfg), s0, s1, s2, float(rf * rf),
-                    c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_fg, c->d_nbr_fg, c->d_cnt_fg,
-                    &st->max_fg, &st->tot_fg, &st->flags, F_OVERFLOW_FG};
+  return ListArgs{c->n, c->d_pos_fg, c->d_perm_fg, grid_args(c->gfg), s0, s1, s2, float(rf * rf),
+                  c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_fg, c->d_nbr_fg, c->d_cnt_fg,
+                  &st->max_fg, &st->tot_fg, &st->flags, F_OVERFLOW_FG};
+}
+
+// the CG list's arguments and cells; false (arguments untouched) without a CG list
+static bool list_args_cg(relres_ctx* c, ListArgs* cg, int* ncell_cg) {
+  if (!(c->has_cg && c->n_h > 0)) return false;
+  const float s0 = float(c->box[0] / 4294967296.0), s1 = float(c->box[1] / 4294967296.0),
+              s2 = float(c->box[2] / 4294967296.0);
+  DevState* st = c->d_state;
+  const double rc = c->rlist_cg_cut + c->skin_cg;
+  *cg = ListArgs{c->n_h, c->d_pos_cg, c->d_perm_cg, grid_args(c->gcg), s0, s1, s2, float(rc * rc),
+                 c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg,
+                 &st->max_cg, &st->tot_cg, &st->flags, F_OVERFLOW_CG};
+  *ncell_cg = c->gcg.ncell;
+  return true;
+}
+
+cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
+  if (gate == nullptr) gate = c->d_open;
+  const ListArgs fg = list_args_fg(c);
   ListArgs cg = fg;  // stand-in when there is no CG list (its blocks are not launched)
   int ncell_cg = 0;
-  if (c->has_cg && c->n_h > 0) {
-    const double rc = c->rlist_cg_cut + c->skin_cg;
-    cg = ListArgs{c->n_h, c->d_pos_cg, c->d_perm_cg, grid_args(c->gcg), s0, s1, s2, float(rc * rc),
-                  c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg,
-                  &st->max_cg, &st->tot_cg, &st->flags, F_OVERFLOW_CG};
-    ncell_cg = c->gcg.ncell;
-  }
+  list_args_cg(c, &cg, &ncell_cg);
   // persistent: one wave of blocks walks the cells (a closed gate costs one small launch)
   const int nb = std::min(ncell_cg + c->gfg.ncell, 152 * 8);
   k_list<<<nb, kListThreads, 0, c->stream>>>(gate, fg, cg, ncell_cg);

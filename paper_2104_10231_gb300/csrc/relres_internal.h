@@ -433,9 +433,22 @@ cudaError_t launch_drift_batch(cudaStream_t s, bool fp64, bool ev, const BatchLa
 cudaError_t prepare_sum_batch(const std::vector<relres_ctx*>& cs, const std::vector<StepParams>& sp,
                               double* const* d_vel, BatchLaunch* b);
 cudaError_t launch_sum_batch(cudaStream_t s, bool fp64, int k, const BatchLaunch& b, int nrep);
-// one thread per replica: opens replica r's rebuild node h[r] iff its displacement trigger fired
-cudaError_t launch_decide_batch(cudaStream_t s, DevState* const* d_states, const cudaGraphConditionalHandle* d_h,
-                                int nrep);
+// the list rebuild of every replica whose displacement trigger fired (d_states[r]->flags & F_REBUILD):
+// a work-list kernel and six batched rebuild kernels (neighbor.cu)
+struct RebuildBatch {
+  BatchLaunch args;  // BuildArgs per replica
+  BatchLaunch nbt;   // blocks of each kernel class per replica
+  int* d_wl = nullptr;  // work list written on the device each step
+  size_t wl_ints = 0;
+};
+cudaError_t prepare_rebuild_batch(const std::vector<relres_ctx*>& cs, RebuildBatch* rb);
+// the work list of this step; sets `any` (a graph conditional) iff some replica rebuilds
+cudaError_t launch_worklist(cudaStream_t s, const RebuildBatch& rb, DevState* const* d_states, int nrep,
+                            cudaGraphConditionalHandle any);
+// the six batched rebuild kernels over the work list
+cudaError_t launch_rebuild_batch(cudaStream_t s, const RebuildBatch& rb, int nrep);
+void free_rebuild_batch(RebuildBatch* rb);
+constexpr long long kRebuildBatchKernels = 6;
 
 // MD steps take the segmented drift + bonded kernel and k_sum
 inline bool step_segments(const relres_ctx* c) { return c->seg_ok && c->use_seg; }

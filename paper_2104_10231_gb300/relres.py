@@ -38,8 +38,10 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_backward", "relres_set_pair_config", "relres_batch_create", "relres_batch_step",
             "relres_batch_last_error", "relres_batch_destroy", "relres_set_timing_sampled",
             "relres_set_list_caps", "relres_set_prune", "relres_measure_rates", "relres_get_list",
-            "relres_eval_recip", "relres_set_force_accumulation", "relres_batch_get_info"]
+            "relres_eval_recip", "relres_set_force_accumulation", "relres_batch_get_info",
+            "relres_batch_set_mode"]
 RELRES_STATIC_MAX_ATOMS = 16384
+RELRES_BATCH_FUSE_MEAN_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev", "prune"]
 
 
@@ -134,6 +136,7 @@ def load():
     L.relres_batch_step.argtypes = [vp, C.c_int, C.c_double, C.POINTER(vp), C.POINTER(vp), _dp, C.c_double,
                                     C.POINTER(C.c_uint64), C.c_int, C.POINTER(vp)]
     L.relres_batch_get_info.argtypes = [vp, C.POINTER(C.c_int)]
+    L.relres_batch_set_mode.argtypes = [vp, C.c_int]
     L.relres_batch_last_error.argtypes = [vp]
     L.relres_batch_last_error.restype = C.c_char_p
     L.relres_batch_destroy.argtypes = [vp]
@@ -519,6 +522,10 @@ class Batch:
         if st != RELRES_OK:
             msg = (load().relres_batch_last_error(self.handle) or b"").decode()
             raise RelresError(st, msg)
+
+    def set_mode(self, mode):
+        """-1: automatic; 0: one graph branch per replica; 1: single launches."""
+        _check(load().relres_batch_set_mode(self.handle, int(mode)))
 
     def single_launch(self):
         """1: the last step ran every replica in shared launches; 0: one graph

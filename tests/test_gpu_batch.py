@@ -48,7 +48,8 @@ def _contexts(torch, systems, pair_cfg):
     return out
 
 
-def test_batch_matches_each_replica_stepped_alone(torch):
+@pytest.mark.parametrize("mode", [-1, 0, 1])
+def test_batch_matches_each_replica_stepped_alone(torch, mode):
     systems = _systems()
     temps = [s.temperature for s in systems]
     seeds = [11, 12, 13, 14, 15]
@@ -61,6 +62,7 @@ def test_batch_matches_each_replica_stepped_alone(torch):
     # batched (two calls: the captured graph is reused for the second)
     batch_ctx = _contexts(torch, systems, 0)
     batch = R.Batch([c for c, _, _, _ in batch_ctx])
+    batch.set_mode(mode)
     for _ in range(2):
         batch.step(125, 2.0, [p for _, p, _, _ in batch_ctx], [v for _, _, v, _ in batch_ctx], temps, 100.0, seeds,
                    thermo_every=10, d_thermo=[th for _, _, _, th in batch_ctx])
@@ -72,7 +74,8 @@ def test_batch_matches_each_replica_stepped_alone(torch):
         assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy()), k
         assert np.array_equal(t1.cpu().numpy(), t2.cpu().numpy()), k
     assert max(c.stats()["n_builds"] for c, _, _, _ in batch_ctx) >= 3
-    assert batch.single_launch() == 1
+    # mean size 6170 atoms: the automatic choice is single launches
+    assert batch.single_launch() == (0 if mode == 0 else 1)
     batch.close()
     for c, _, _, _ in solo + batch_ctx:
         c.close()
@@ -167,6 +170,10 @@ def test_mixed_precision_batch_takes_graph_branches_and_matches_solo(torch):
     batch.step(60, 1.0, [p for _, p, _ in both], [v for _, _, v in both], temps, 100.0, [3, 4])
     torch.cuda.synchronize()
     assert batch.single_launch() == 0
+    # single launches cannot mix precisions
+    batch.set_mode(1)
+    with pytest.raises(R.RelresError):
+        batch.step(10, 1.0, [p for _, p, _ in both], [v for _, _, v in both], temps, 100.0, [3, 4])
     for (c1, p1, v1), (c2, p2, v2) in zip(solo, both):
         assert np.array_equal(p1.cpu().numpy(), p2.cpu().numpy())
         assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy())
