@@ -100,12 +100,18 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_pair_counters(p_prune):
+COUNTER_ATOMS = 1_000_000  # the summary's counters are scaled to the 1M-atom workload
+
+
+def recorded_pair_counters(p_prune, n_atoms):
     """ncu counters of one pair-kernel launch from the committed summary, if
-    it was taken on the current pair.cu (sha256 prefix recorded there): DRAM
-    bytes and warp instructions executed, each the mean over plain launches
-    and pruning launches (a fraction p_prune)."""
+    it was taken on the current pair.cu (sha256 prefix recorded there) and the
+    run is the workload they were scaled to: DRAM bytes and warp instructions
+    executed, each the mean over plain launches and pruning launches (a
+    fraction p_prune)."""
     out = {}
+    if n_atoms != COUNTER_ATOMS:
+        return out
     try:
         src_sha = hashlib.sha256(open(PAIR_SRC, "rb").read()).hexdigest()[:16]
         vals = {}
@@ -484,7 +490,7 @@ def pair_roofline(alg_bytes, pair_ms, p_prune, peak_info, rates, clk, n, n_h, wa
     peak, peak_kind = peak_info
     secs = pair_ms * 1e-3
     achieved = alg_bytes / secs / 1e9
-    rec = recorded_pair_counters(p_prune)
+    rec = recorded_pair_counters(p_prune, n)
     traffic = rec.get("dram_bytes")
     insts = rec.get("inst_executed")
     mhz = (clk or {}).get("sm_mhz") or rates.get("clock_mhz")
@@ -614,24 +620,23 @@ def batched_leg(torch, R, S, n_rep, steps, seed=4242):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
-    # batched, both forms on the same replicas: one graph branch per replica
-    # (its own kernels) and single launches covering every replica
+    # batched, three forms on the same replicas: one graph branch per replica
+    # (its own kernels), shared launches covering every replica, and the
+    # automatic split (small replicas shared, the others on branches)
     ctxs = make()
     bstream = torch.cuda.Stream()
     batch = R.Batch([c for c, _, _ in ctxs], stream=bstream)
     pos = [p for _, p, _ in ctxs]
     vel = [v for _, _, v in ctxs]
     forms = {}
-    for mode, name in ((0, "graph_branches"), (1, "single_launch")):
+    for mode, name in ((0, "graph_branches"), (1, "all_shared"), (-1, "automatic")):
         batch.set_mode(mode)
         batch.step(20, 2.0, pos, vel, temps, 100.0, seeds)  # warm-up: autotuning, graph capture
         batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)  # capture of the timed block shape
         secs = timed(bstream, lambda: batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds))
-        forms[name] = {"value": n_atoms * steps / secs, "ms_per_step": secs / steps * 1e3}
-    batch.set_mode(-1)
-    batch.step(1, 2.0, pos, vel, temps, 100.0, seeds)
-    auto = "single_launch" if batch.single_launch() == 1 else "graph_branches"
-    t_batch = n_atoms * steps / forms[auto]["value"]
+        forms[name] = {"value": n_atoms * steps / secs, "ms_per_step": secs / steps * 1e3,
+                       "replicas_in_shared_launches": batch.n_shared()}
+    t_batch = n_atoms * steps / forms["automatic"]["value"]
     batch.close()
     for c, _, _ in ctxs:
         c.close()
@@ -651,7 +656,7 @@ def batched_leg(torch, R, S, n_rep, steps, seed=4242):
     return {"workload": f"{n_rep} replicas, seeded sizes 1k-50k atoms ({n_atoms} atoms in all), alternately "
                         "propane-like (k^3 molecules) and neopentane-like, T in U[200, 300] K, CSVR, dt 2 fs, FP32",
             "steps": steps, "value": n_atoms * steps / t_batch, "unit": "atom-steps/s",
-            "ms_per_step": t_batch / steps * 1e3, "form": auto, "forms": forms,
+            "ms_per_step": t_batch / steps * 1e3, "form": "automatic", "forms": forms,
             "one_after_the_other": {"value": n_atoms * steps / t_seq, "ms_per_step": t_seq / steps * 1e3},
             "timing": "CUDA events on the batch stream around one relres_batch_step call (the per-call set-up "
                       "of every replica included); the sequential run: events on the default stream around "
@@ -677,7 +682,7 @@ def small_batch_leg(torch, R, S, n_rep=128, steps=200):
     temps, seeds = [s.temperature for s in systems], list(range(n_rep))
     out = {"workload": f"{n_rep} replicas of the 648-atom propane-like liquid ({n_atoms} atoms), FP32, CSVR, dt 2 fs",
            "steps": steps, "unit": "atom-steps/s"}
-    for mode, name in ((1, "single_launch"), (0, "graph_branches")):
+    for mode, name in ((1, "all_shared"), (0, "graph_branches")):
         batch.set_mode(mode)
         batch.step(steps, 2.0, pos, vel, temps, 100.0, seeds)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -453,24 +453,25 @@ relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, 
                                 double* const* d_vel, const double* t_target, double tau_fs, const uint64_t* seed,
                                 int thermo_every, double* const* d_thermo);
 const char* relres_batch_last_error(relres_batch* batch);
-/* Which form the last relres_batch_step ran: *single_launch = 1 when every
- * replica shared one drift, one pair and one force-sum launch per step (and
- * the list rebuilds of the replicas that needed one shared six launches), 0
- * when each replica ran its own kernels on a branch of the graph; -1 before
- * the first step. */
-relres_status relres_batch_get_info(relres_batch* batch, int* single_launch);
+/* *n_shared: how many replicas the last relres_batch_step ran in shared
+ * launches (one drift, one pair and one force-sum launch per step covering all
+ * of them, their list rebuilds in six launches); the other replicas ran their
+ * own kernels on branches of the same graph.  -1 before the first step. */
+relres_status relres_batch_get_info(relres_batch* batch, int* n_shared);
 
-/* Form of later relres_batch_step calls.  mode 1: single launches, which
- * need every replica with the same precision and force accumulation and
- * molecules of at most 256 atoms (RELRES_ERR_ARG at the next step otherwise);
- * the pair kernel then runs one thread per atom in 256-thread blocks whatever
- * relres_set_pair_config chose.  mode 0: one graph branch per replica with
- * its own kernels.  mode -1 (the default): single launches when the replicas
- * allow them and hold at most RELRES_BATCH_FUSE_MEAN_ATOMS atoms on average
- * (there the launch overhead of many small systems dominates; for larger
- * replicas the kernels of each system alone run faster), else branches.
- * Drops the captured graph.  Errors: RELRES_ERR_ARG (unknown mode). */
-#define RELRES_BATCH_FUSE_MEAN_ATOMS 16384
+/* Which replicas later relres_batch_step calls run in shared launches.
+ * mode 1: every replica, which needs all of them with the same precision and
+ * force accumulation and molecules of at most 256 atoms (RELRES_ERR_ARG at
+ * the next step otherwise).  mode 0: none; every replica on its own branch of
+ * the graph with its own kernels.  mode -1 (the default): the replicas of at
+ * most RELRES_BATCH_SHARED_MAX_ATOMS atoms that share precision and force
+ * accumulation (at least two); there the launch overhead of separate small
+ * systems dominates, while a larger system runs faster with kernels of its
+ * own (shared launches read each replica's arguments from device memory).
+ * The pair kernel of shared launches runs one thread per atom in 256-thread
+ * blocks whatever relres_set_pair_config chose.  Drops the captured graph.
+ * Errors: RELRES_ERR_ARG (unknown mode). */
+#define RELRES_BATCH_SHARED_MAX_ATOMS 16384
 relres_status relres_batch_set_mode(relres_batch* batch, int mode);
 void relres_batch_destroy(relres_batch* batch);
 
@@ -482,7 +483,8 @@ void relres_batch_destroy(relres_batch* batch);
  * fastest (systems under 20 000 atoms keep configuration 0; with list pruning
  * on only the one-thread configurations 0-2 are timed, since the others need a
  * separate pruning pass); config 0..6
- * fixes one (0: one thread per atom, 256 per block).  The choice is reported
+ * fixes one (0: one thread per atom, 256 per block; 1, 2: one thread per
+ * atom, 128, 512 per block; 3-6: 2, 4, 8, 2 threads per atom).  The choice is reported
  * in relres_stats.  Results agree within rounding (the summation order of an
  * atom's partners changes with the number of threads).
  */

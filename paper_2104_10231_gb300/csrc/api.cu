@@ -1287,19 +1287,51 @@ struct relres_batch {
   // single-launch path: one drift, one pair and one force-sum launch per step
   // for every replica (argument tables in device memory), and the list
   // rebuilds of the replicas that need one in seven launches for all of them
-  bool fused = false;
-  int mode = -1;  // relres_batch_set_mode
+  int mode = -1;                 // relres_batch_set_mode
+  std::vector<int> shared;       // replicas in the shared launches of the captured graph
+  std::vector<char> is_shared;   // [nrep]
   BatchLaunch bl_pair, bl_drift, bl_sum;
   RebuildBatch rebuild;
   DevState** d_states = nullptr;  // [nrep]
 };
 
-// Replicas can share single launches when the kernels' template arguments
-// agree: the same precision and force accumulation, and segmented steps.
-static bool batch_can_fuse(const relres_batch* b) {
-  for (relres_ctx* c : b->ctx)
-    if (c->fp64 != b->ctx[0]->fp64 || c->force_acc != b->ctx[0]->force_acc || !step_segments(c)) return false;
-  return true;
+static relres_status batch_fail(relres_batch* b, relres_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+
+// Replicas can share launches when the kernels' template arguments agree: the
+// same precision and force accumulation, and segmented steps.
+static bool batch_compatible(const relres_ctx* c, const relres_ctx* ref) {
+  return step_segments(c) && c->fp64 == ref->fp64 && c->force_acc == ref->force_acc;
+}
+
+// The replicas of the shared launches (relres_batch_set_mode): mode 1 every
+// replica (all must be compatible), mode 0 none, mode -1 the compatible
+// replicas of at most RELRES_BATCH_SHARED_MAX_ATOMS atoms (at least two).
+static relres_status batch_partition(relres_batch* b, std::vector<int>* shared) {
+  const int nr = int(b->ctx.size());
+  shared->clear();
+  if (b->mode == 0) return RELRES_OK;
+  if (b->mode == 1) {
+    for (int r = 0; r < nr; ++r) {
+      if (!batch_compatible(b->ctx[r], b->ctx[0]))
+        return batch_fail(b, RELRES_ERR_ARG,
+                          "shared launches need replicas of one precision and force accumulation, molecules <= 256 "
+                          "atoms");
+      shared->push_back(r);
+    }
+    return RELRES_OK;
+  }
+  const relres_ctx* ref = nullptr;
+  for (int r = 0; r < nr; ++r) {
+    relres_ctx* c = b->ctx[r];
+    if (c->n > RELRES_BATCH_SHARED_MAX_ATOMS || !step_segments(c)) continue;
+    if (!ref) ref = c;
+    if (batch_compatible(c, ref)) shared->push_back(r);
+  }
+  if (shared->size() < 2) shared->clear();
+  return RELRES_OK;
 }
 
 }  // extern "C"
@@ -1334,20 +1366,69 @@ void free_batch(BatchLaunch* b) {
 }  // namespace relres
 extern "C" {
 
-static relres_status batch_fail(relres_batch* b, relres_status s, const std::string& m) {
-  b->err = m;
-  return s;
-}
-
 static void batch_drop_graph(relres_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = nullptr;
   b->valid = false;
 }
 
-static relres_status batch_graph_fused(relres_batch* b, const std::vector<StepParams>& sp, double* const* d_vel,
-                                       int blk, int done);
+// The shared-launch part of one block of steps, captured on the batch stream
+// (tables uploaded beforehand): per replica the rollback snapshot and the
+// thermostat draws, then per step the batched drift, the work list of
+// replicas whose trigger fired with one conditional node holding the six
+// batched rebuild kernels, the batched pair kernel and the batched force sum.
+static relres_status capture_shared(relres_batch* b, const std::vector<relres_ctx*>& cs,
+                                    const std::vector<StepParams>& sp, const std::vector<double*>& vel, int blk,
+                                    int done) {
+  const int ns = int(cs.size());
+  const bool fp64 = cs[0]->fp64;
+  const int acc = cs[0]->force_acc;
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < ns && e == cudaSuccess; ++q) {
+    relres_ctx* c = cs[q];
+    const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
+    e = cudaMemcpyAsync(c->d_snap_x, c->d_xfx, xb, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_snap_v, vel_state(c, vel[q]), vb, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_snap_f, c->d_f_tot, force_bytes(c), cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) {
+      const cudaStream_t own = c->stream;
+      const long long n0 = c->n_launches;  // counted per executed block in k_parent
+      c->stream = b->stream;
+      e = launch_csvr_draws(c, sp[q], blk);
+      c->stream = own;
+      c->n_launches = n0;
+    }
+  }
+  relres_status s = RELRES_OK;
+  for (int k = 0; k < blk && e == cudaSuccess && s == RELRES_OK; ++k) {
+    const bool ev_step = sp[0].thermo_every > 0 && ((done + k + 1) % sp[0].thermo_every) == 0;
+    e = launch_drift_batch(b->stream, fp64, ev_step, b->bl_drift, ns);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    cudaGraphConditionalHandle any = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(b->stream, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&any, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = launch_worklist(b->stream, b->rebuild, b->d_states, ns, any);
+    if (e == cudaSuccess) {
+      relres_ctx* c0 = cs[0];  // lends its body stream for the capture of the node's body
+      const cudaStream_t own = c0->stream;
+      c0->stream = b->stream;
+      s = add_conditional(c0, any, [b, ns, c0]() { return launch_rebuild_batch(c0->stream, b->rebuild, ns); });
+      c0->stream = own;
+      if (s != RELRES_OK) b->err = "shared rebuild node (capture): " + c0->err;
+    }
+    if (e == cudaSuccess && s == RELRES_OK) e = launch_pairs_batch(b->stream, fp64, acc, ev_step, b->bl_pair, ns);
+    if (e == cudaSuccess && s == RELRES_OK) e = launch_sum_batch(b->stream, fp64, k, b->bl_sum, ns);
+  }
+  if (s == RELRES_OK && e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  return s;
+}
 
+// Instantiated graph for this block of steps (re-captured when an input
+// changed): the replicas of the shared launches on the batch stream, every
+// other replica's block on its own branch, all of them concurrently.
 static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>& sp, double* const* d_vel, int blk,
                                  int done) {
   const int nr = int(b->ctx.size());
@@ -1360,36 +1441,46 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
       b->dt == sp[0].dt && b->tau == sp[0].tau && b->keys == keys)
     return RELRES_OK;
   batch_drop_graph(b);
-  const bool can = batch_can_fuse(b);
-  if (b->mode == 1 && !can)
-    return batch_fail(b, RELRES_ERR_ARG,
-                      "single launches need replicas of one precision and force accumulation, molecules <= 256 atoms");
-  long long atoms = 0;
-  for (relres_ctx* c : b->ctx) atoms += c->n;
-  b->fused = b->mode == 1 || (b->mode == -1 && can && atoms <= (long long)RELRES_BATCH_FUSE_MEAN_ATOMS * nr);
-  if (b->fused) {
-    const relres_status fs = batch_graph_fused(b, sp, d_vel, blk, done);
-    if (fs != RELRES_OK) return fs;
-    b->valid = true;
-    b->blk = blk;
-    b->phase = phase;
-    b->thermo_every = sp[0].thermo_every;
-    b->dt = sp[0].dt;
-    b->tau = sp[0].tau;
-    b->keys = keys;
-    return RELRES_OK;
+  std::vector<int> shared;
+  relres_status s = batch_partition(b, &shared);
+  if (s != RELRES_OK) return s;
+  b->is_shared.assign(nr, 0);
+  for (int r : shared) b->is_shared[r] = 1;
+  std::vector<relres_ctx*> cs;
+  std::vector<StepParams> ssp;
+  std::vector<double*> svel;
+  for (int r : shared) {
+    cs.push_back(b->ctx[r]);
+    ssp.push_back(sp[r]);
+    svel.push_back(d_vel[r]);
   }
-  for (int r = 0; r < nr; ++r)  // each replica captures its rebuild bodies on its own stream
-    if (!b->ctx[r]->body_stream) {
-      const cudaError_t eb = cudaStreamCreateWithFlags(&b->ctx[r]->body_stream, cudaStreamNonBlocking);
-      if (eb != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(eb));
+  const int ns = int(cs.size());
+  // device tables of the shared launches, uploaded before the capture
+  cudaError_t e = cudaSuccess;
+  if (ns > 0) {
+    e = prepare_pairs_batch(cs, &b->bl_pair);
+    if (e == cudaSuccess) e = prepare_drift_batch(cs, ssp, svel.data(), &b->bl_drift);
+    if (e == cudaSuccess) e = prepare_sum_batch(cs, ssp, svel.data(), &b->bl_sum);
+    if (e == cudaSuccess) e = prepare_rebuild_batch(cs, &b->rebuild);
+    if (e == cudaSuccess && !b->d_states) e = cudaMalloc(&b->d_states, sizeof(DevState*) * nr);
+    if (e == cudaSuccess) {
+      std::vector<DevState*> st(ns);
+      for (int q = 0; q < ns; ++q) st[q] = cs[q]->d_state;
+      e = cudaMemcpy(b->d_states, st.data(), sizeof(DevState*) * ns, cudaMemcpyHostToDevice);
     }
-  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  }
+  // every branch replica (and the shared part) captures its conditional bodies on a stream of its own
+  for (int r = 0; r < nr && e == cudaSuccess; ++r)
+    if ((!b->is_shared[r] || r == (ns ? shared[0] : -1)) && !b->ctx[r]->body_stream)
+      e = cudaStreamCreateWithFlags(&b->ctx[r]->body_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
+  e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
   e = cudaEventRecord(b->ev_fork, b->stream);
-  relres_status s = RELRES_OK;
   b->k_parent.assign(nr, 0);
+  std::vector<int> joins;
   for (int r = 0; r < nr && s == RELRES_OK && e == cudaSuccess; ++r) {
+    if (b->is_shared[r]) continue;
     relres_ctx* c = b->ctx[r];
     e = cudaStreamWaitEvent(b->fork[r], b->ev_fork, 0);
     if (e != cudaSuccess) break;
@@ -1406,8 +1497,15 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
     c->timing = timing;
     c->n_launches = n0;
     if (s == RELRES_OK) e = cudaEventRecord(b->ev_join[r], b->fork[r]);
-    if (s == RELRES_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[r], 0);
+    if (s == RELRES_OK && e == cudaSuccess) joins.push_back(r);
   }
+  if (ns > 0 && s == RELRES_OK && e == cudaSuccess) {
+    s = capture_shared(b, cs, ssp, svel, blk, done);
+    // every shared replica takes part in the step's drift, work-list, pair and force-sum launches
+    for (int q = 0; q < ns; ++q) b->k_parent[shared[q]] = 4LL * blk + (ssp[q].t_target > 0.0 ? 1 : 0);
+  }
+  for (int r : joins)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[r], 0);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   if (s == RELRES_OK && e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
@@ -1421,6 +1519,7 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
     batch_drop_graph(b);
     return s;
   }
+  b->shared = shared;
   b->valid = true;
   b->blk = blk;
   b->phase = phase;
@@ -1429,91 +1528,6 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
   b->tau = sp[0].tau;
   b->keys = keys;
   return RELRES_OK;
-}
-
-// The fused form of one block of steps (see relres_batch::fused), captured
-// on the batch stream: per replica the rollback snapshot and thermostat
-// draws, then per step the batched drift, the batched list rebuild of the
-// replicas whose trigger fired, the batched pair kernel and the batched force
-// sum.
-static relres_status batch_graph_fused(relres_batch* b, const std::vector<StepParams>& sp, double* const* d_vel,
-                                       int blk, int done) {
-  const int nr = int(b->ctx.size());
-  const bool fp64 = b->ctx[0]->fp64;
-  const int acc = b->ctx[0]->force_acc;
-  // device tables, uploaded before the capture
-  cudaError_t e = prepare_pairs_batch(b->ctx, &b->bl_pair);
-  if (e == cudaSuccess) e = prepare_drift_batch(b->ctx, sp, d_vel, &b->bl_drift);
-  if (e == cudaSuccess) e = prepare_sum_batch(b->ctx, sp, d_vel, &b->bl_sum);
-  if (e == cudaSuccess) e = prepare_rebuild_batch(b->ctx, &b->rebuild);
-  if (e == cudaSuccess && !b->d_states) e = cudaMalloc(&b->d_states, sizeof(DevState*) * nr);
-  if (e == cudaSuccess) {
-    std::vector<DevState*> st(nr);
-    for (int r = 0; r < nr; ++r) st[r] = b->ctx[r]->d_state;
-    e = cudaMemcpy(b->d_states, st.data(), sizeof(DevState*) * nr, cudaMemcpyHostToDevice);
-  }
-  if (e == cudaSuccess && !b->ctx[0]->body_stream)
-    e = cudaStreamCreateWithFlags(&b->ctx[0]->body_stream, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
-  e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
-  b->k_parent.assign(nr, 0);
-  // snapshot of each replica for the rollback, and its thermostat draws
-  for (int r = 0; r < nr && e == cudaSuccess; ++r) {
-    relres_ctx* c = b->ctx[r];
-    const size_t xb = sizeof(unsigned long long) * 3 * size_t(c->n), vb = sizeof(double) * 3 * size_t(c->n);
-    e = cudaMemcpyAsync(c->d_snap_x, c->d_xfx, xb, cudaMemcpyDeviceToDevice, b->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->d_snap_v, vel_state(c, d_vel[r]), vb, cudaMemcpyDeviceToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_snap_f, c->d_f_tot, force_bytes(c), cudaMemcpyDeviceToDevice, b->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->d_snap_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, b->stream);
-    if (e == cudaSuccess) {
-      const cudaStream_t own = c->stream;
-      c->stream = b->stream;
-      const long long n0 = c->n_launches;
-      e = launch_csvr_draws(c, sp[r], blk);
-      b->k_parent[r] += c->n_launches - n0;
-      c->n_launches = n0;
-      c->stream = own;
-    }
-  }
-  relres_status s = RELRES_OK;
-  for (int k = 0; k < blk && e == cudaSuccess && s == RELRES_OK; ++k) {
-    const bool ev_step = sp[0].thermo_every > 0 && ((done + k + 1) % sp[0].thermo_every) == 0;
-    e = launch_drift_batch(b->stream, fp64, ev_step, b->bl_drift, nr);
-    // the work list kernel opens one conditional node holding the six batched
-    // rebuild kernels when any replica's trigger fired
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t cg = nullptr;
-    cudaGraphConditionalHandle any = 0;
-    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(b->stream, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&any, cg, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) e = launch_worklist(b->stream, b->rebuild, b->d_states, nr, any);
-    if (e == cudaSuccess) {
-      relres_ctx* c0 = b->ctx[0];  // lends its body stream for the capture of the node's body
-      const cudaStream_t own = c0->stream;
-      c0->stream = b->stream;
-      s = add_conditional(c0, any, [b, nr, c0]() { return launch_rebuild_batch(c0->stream, b->rebuild, nr); });
-      c0->stream = own;
-      if (s != RELRES_OK) b->err = "batch rebuild node (capture): " + c0->err;
-    }
-    if (e == cudaSuccess && s == RELRES_OK) e = launch_pairs_batch(b->stream, fp64, acc, ev_step, b->bl_pair, nr);
-    if (e == cudaSuccess && s == RELRES_OK) e = launch_sum_batch(b->stream, fp64, k, b->bl_sum, nr);
-  }
-  // every replica takes part in the step's drift, work-list, pair and force-sum launches
-  for (int r = 0; r < nr; ++r) b->k_parent[r] += 4LL * blk;
-  cudaGraph_t g = nullptr;
-  const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-  if (s == RELRES_OK && e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
-  if (s == RELRES_OK && e2 != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e2));
-  if (s == RELRES_OK) {
-    e = cudaGraphInstantiate(&b->exec, g, 0);
-    if (e != cudaSuccess) s = batch_fail(b, RELRES_ERR_CUDA, cudaGetErrorString(e));
-  }
-  if (g) cudaGraphDestroy(g);
-  if (s != RELRES_OK) batch_drop_graph(b);
-  return s;
 }
 
 relres_status relres_batch_create(relres_batch** out, relres_ctx* const* ctxs, int n_ctx, void* cuda_stream) {
@@ -1582,8 +1596,8 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
       relres_ctx* c = b->ctx[r];
       s = read_state(c);
       if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + c->err);
-      const long long kpr = (!b->fused && c->prune_on && !pairs_prune(c)) ? 1 : 0;
-      // a rebuild body of six kernels runs per rebuild (the fused form's
+      const long long kpr = (!b->is_shared[r] && c->prune_on && !pairs_prune(c)) ? 1 : 0;
+      // a rebuild body of six kernels runs per rebuild (the shared launches'
       // batched kernels are counted for every replica they rebuild)
       c->n_launches += b->k_parent[r] + 6LL * std::max(0LL, c->h_state->n_builds - builds0[r]) +
                        kpr * std::max(0LL, (long long)c->h_state->n_prunes - prunes0[r]);
@@ -1633,9 +1647,9 @@ relres_status relres_batch_set_mode(relres_batch* b, int mode) {
   return RELRES_OK;
 }
 
-relres_status relres_batch_get_info(relres_batch* b, int* single_launch) {
-  if (!b || !single_launch) return RELRES_ERR_ARG;
-  *single_launch = b->valid ? (b->fused ? 1 : 0) : -1;
+relres_status relres_batch_get_info(relres_batch* b, int* n_shared) {
+  if (!b || !n_shared) return RELRES_ERR_ARG;
+  *n_shared = b->valid ? int(b->shared.size()) : -1;
   return RELRES_OK;
 }
 

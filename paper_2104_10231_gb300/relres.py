@@ -41,7 +41,7 @@ EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres
             "relres_eval_recip", "relres_set_force_accumulation", "relres_batch_get_info",
             "relres_batch_set_mode"]
 RELRES_STATIC_MAX_ATOMS = 16384
-RELRES_BATCH_FUSE_MEAN_ATOMS = 16384
+RELRES_BATCH_SHARED_MAX_ATOMS = 16384
 TIMING_CLASSES = ["drift", "rebuild", "lists", "pair", "finish", "thermo", "pair_ev", "prune"]
 
 
@@ -524,12 +524,12 @@ class Batch:
             raise RelresError(st, msg)
 
     def set_mode(self, mode):
-        """-1: automatic; 0: one graph branch per replica; 1: single launches."""
+        """-1: small compatible replicas share launches, the rest own branches;
+        0: every replica on its own branch; 1: every replica in shared launches."""
         _check(load().relres_batch_set_mode(self.handle, int(mode)))
 
-    def single_launch(self):
-        """1: the last step ran every replica in shared launches; 0: one graph
-        branch per replica; -1: no step yet."""
+    def n_shared(self):
+        """Replicas the last step ran in shared launches (-1: no step yet)."""
         v = C.c_int(-1)
         _check(load().relres_batch_get_info(self.handle, C.byref(v)))
         return v.value

@@ -1,8 +1,8 @@
 """Batches of independent replicas (relres_batch_step): every block of steps of
-all replicas runs as one CUDA graph, with one drift, one pair and one
-force-sum launch per step covering every replica where the replicas allow it
-(same precision and accumulation) and one graph branch per replica otherwise.
-Both forms must give the bits of stepping each context alone with the same
+all replicas runs as one CUDA graph, where replicas that allow it (same
+precision and accumulation) share one drift, one pair and one force-sum launch
+per step and the others run their own kernels on branches of the graph.  Every
+form must give the bits of stepping each context alone with the same
 arguments, and FP64 batches the oracle's velocity Verlet + CSVR."""
 import numpy as np
 import pytest
@@ -74,8 +74,9 @@ def test_batch_matches_each_replica_stepped_alone(torch, mode):
         assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy()), k
         assert np.array_equal(t1.cpu().numpy(), t2.cpu().numpy()), k
     assert max(c.stats()["n_builds"] for c, _, _, _ in batch_ctx) >= 3
-    # mean size 6170 atoms: the automatic choice is single launches
-    assert batch.single_launch() == (0 if mode == 0 else 1)
+    # automatic: the four replicas of at most 16 384 atoms share launches, the
+    # 25 000-atom one runs on its own branch
+    assert batch.n_shared() == {-1: 4, 0: 0, 1: 5}[mode]
     batch.close()
     for c, _, _, _ in solo + batch_ctx:
         c.close()
@@ -126,7 +127,7 @@ def test_fp64_batch_of_uneven_replicas_matches_oracle_md(torch):
                [s.temperature for s in systems], 100.0, seeds, thermo_every=1,
                d_thermo=[th for _, _, _, th in ctxs])
     torch.cuda.synchronize()
-    assert batch.single_launch() == 1
+    assert batch.n_shared() == 4
     for k, ((ctx, p, v, th), s, sd) in enumerate(zip(ctxs, systems, seeds)):
         po, vo, tho = O.md(s.pos, s.vel, s.box, s.masses, s.types, O.table_for(s), s.n_types, s.excl, s.topo,
                            steps, dt, t_target=s.temperature, tau=100.0, seed=sd)
@@ -169,8 +170,8 @@ def test_mixed_precision_batch_takes_graph_branches_and_matches_solo(torch):
     batch = R.Batch([c for c, _, _ in both])
     batch.step(60, 1.0, [p for _, p, _ in both], [v for _, _, v in both], temps, 100.0, [3, 4])
     torch.cuda.synchronize()
-    assert batch.single_launch() == 0
-    # single launches cannot mix precisions
+    assert batch.n_shared() == 0
+    # shared launches cannot mix precisions
     batch.set_mode(1)
     with pytest.raises(R.RelresError):
         batch.step(10, 1.0, [p for _, p, _ in both], [v for _, _, v in both], temps, 100.0, [3, 4])
