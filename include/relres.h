@@ -455,7 +455,7 @@ relres_status relres_batch_step(relres_batch* batch, int n_steps, double dt_fs, 
 const char* relres_batch_last_error(relres_batch* batch);
 /* *n_shared: how many replicas the last relres_batch_step ran in shared
  * launches (one drift, one pair and one force-sum launch per step covering all
- * of them, their list rebuilds in six launches); the other replicas ran their
+ * of them, their list rebuilds in seven launches); the other replicas ran their
  * own kernels on branches of the same graph.  -1 before the first step. */
 relres_status relres_batch_get_info(relres_batch* batch, int* n_shared);
 

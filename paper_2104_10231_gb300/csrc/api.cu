@@ -60,27 +60,44 @@ unsigned long long morton3(unsigned x, unsigned y, unsigned z) {
   return spread(x) | (spread(y) << 1) | (spread(z) << 2);
 }
 
-// Cells per axis: the largest count whose cells are at least r_list wide.
+// Cells per axis: the largest count whose cells are at least r_list wide,
+// cut into kXSplit slabs along x when every axis has four or more (see Grid).
 relres_status setup_grid(relres_ctx* c, Grid* g, double rlist) {
   ++c->buf_gen;
-  int n[3];
-  for (int d = 0; d < 3; ++d) n[d] = std::max(1, int(std::floor(c->box[d] / rlist)));
-  if (g->d_rank_of && n[0] == g->n[0] && n[1] == g->n[1] && n[2] == g->n[2]) return RELRES_OK;
-  const long long nc = (long long)n[0] * n[1] * n[2];
+  int nf[3];
+  for (int d = 0; d < 3; ++d) nf[d] = std::max(1, int(std::floor(c->box[d] / rlist)));
+  const int xs = (nf[0] >= 4 && nf[1] >= 4 && nf[2] >= 4) ? kXSplit : 1;
+  const int n[3] = {nf[0] * xs, nf[1], nf[2]};
+  if (g->d_rank_of && g->xsplit == xs && nf[0] == g->nf[0] && nf[1] == g->nf[1] && nf[2] == g->nf[2])
+    return RELRES_OK;
+  const long long ncf = (long long)nf[0] * nf[1] * nf[2];
+  const long long nc = ncf * xs;
   if (nc > (1ll << 28)) return fail(c, RELRES_ERR_ARG, "too many cells");
   std::vector<std::pair<unsigned long long, int>> order;
-  order.reserve(size_t(nc));
+  order.reserve(size_t(ncf));
+  for (int x = 0; x < nf[0]; ++x)
+    for (int y = 0; y < nf[1]; ++y)
+      for (int z = 0; z < nf[2]; ++z) order.push_back({morton3(x, y, z), (x * nf[1] + y) * nf[2] + z});
+  std::sort(order.begin(), order.end());
+  std::vector<int> rank_full(static_cast<size_t>(ncf));
+  for (size_t k = 0; k < order.size(); ++k) rank_full[size_t(order[k].second)] = int(k);
+  std::vector<int> rank(static_cast<size_t>(nc));
   for (int x = 0; x < n[0]; ++x)
     for (int y = 0; y < n[1]; ++y)
-      for (int z = 0; z < n[2]; ++z) order.push_back({morton3(x, y, z), (x * n[1] + y) * n[2] + z});
-  std::sort(order.begin(), order.end());
-  std::vector<int> rank(static_cast<size_t>(nc));
-  for (size_t k = 0; k < order.size(); ++k) rank[size_t(order[k].second)] = int(k);
-  for (int d = 0; d < 3; ++d) g->n[d] = n[d];
+      for (int z = 0; z < n[2]; ++z)
+        rank[size_t((x * n[1] + y) * n[2] + z)] = rank_full[size_t(((x / xs) * nf[1] + y) * nf[2] + z)] * xs + x % xs;
+  for (int d = 0; d < 3; ++d) {
+    g->n[d] = n[d];
+    g->nf[d] = nf[d];
+  }
+  g->xsplit = xs;
   g->ncell = int(nc);
+  g->ncell_full = int(ncf);
+  g->ntile = int((nc + kScanTile - 1) / kScanTile);
   CK(dalloc(&g->d_rank_of, size_t(nc)));
   CK(dalloc(&g->d_start, size_t(nc) + 1));
   CK(dalloc(&g->d_count, size_t(nc)));
+  CK(dalloc(&g->d_tile, size_t(g->ntile)));
   CK(cudaMemcpy(g->d_rank_of, rank.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
   CK(cudaMemset(g->d_count, 0, sizeof(int) * nc));
   CK(cudaMemset(g->d_start, 0, sizeof(int) * (nc + 1)));
@@ -991,9 +1008,9 @@ static relres_status step_graph(relres_ctx* c, const StepParams& sp, double* d_v
     drop_one_graph(g);
     return s;
   }
-  // kernels: per step the rebuild body holds 6 (5 binning stages + lists),
-  // the pruning body 1, and the decide kernel sits in the parent
-  g.k_body = 6;
+  // kernels: per step the rebuild body holds kRebuildKernels (binning stages +
+  // lists), the pruning body 1, and the decide kernel sits in the parent
+  g.k_body = kRebuildKernels;
   g.k_prune = (c->prune_on && !pairs_prune(c)) ? 1 : 0;
   g.k_parent = captured - (g.k_body + g.k_prune) * blk;
   g.valid = true;
@@ -1375,7 +1392,7 @@ static void batch_drop_graph(relres_batch* b) {
 // The shared-launch part of one block of steps, captured on the batch stream
 // (tables uploaded beforehand): per replica the rollback snapshot and the
 // thermostat draws, then per step the batched drift, the work list of
-// replicas whose trigger fired with one conditional node holding the six
+// replicas whose trigger fired with one conditional node holding the seven
 // batched rebuild kernels, the batched pair kernel and the batched force sum.
 static relres_status capture_shared(relres_batch* b, const std::vector<relres_ctx*>& cs,
                                     const std::vector<StepParams>& sp, const std::vector<double*>& vel, int blk,
@@ -1492,7 +1509,7 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
     s = record_block(c, sp[r], d_vel[r], blk, done, true);
     if (s != RELRES_OK) b->err = "replica " + std::to_string(r) + " (capture): " + c->err;
     const long long kpr = (c->prune_on && !pairs_prune(c)) ? 1 : 0;
-    b->k_parent[r] = (c->n_launches - n0) - (6LL + kpr) * blk;
+    b->k_parent[r] = (c->n_launches - n0) - (kRebuildKernels + kpr) * blk;
     c->stream = own;
     c->timing = timing;
     c->n_launches = n0;
@@ -1597,9 +1614,9 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
       s = read_state(c);
       if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + c->err);
       const long long kpr = (!b->is_shared[r] && c->prune_on && !pairs_prune(c)) ? 1 : 0;
-      // a rebuild body of six kernels runs per rebuild (the shared launches'
-      // batched kernels are counted for every replica they rebuild)
-      c->n_launches += b->k_parent[r] + 6LL * std::max(0LL, c->h_state->n_builds - builds0[r]) +
+      // a rebuild body of kRebuildKernels kernels runs per rebuild (the shared
+      // launches' batched kernels are counted for every replica they rebuild)
+      c->n_launches += b->k_parent[r] + kRebuildKernels * std::max(0LL, c->h_state->n_builds - builds0[r]) +
                        kpr * std::max(0LL, (long long)c->h_state->n_prunes - prunes0[r]);
       flags[r] = c->h_state->flags;
       if (flags[r] & F_BADCELL)
@@ -1822,6 +1839,7 @@ void relres_destroy(relres_ctx* c) {
     dfree(g->d_rank_of);
     dfree(g->d_start);
     dfree(g->d_count);
+    dfree(g->d_tile);
   }
   dfree(c->d_xfx);
   dfree(c->d_ref);

@@ -29,10 +29,13 @@ struct GridArgs {
   const int* rank_of;
   int* start;
   int* count;
+  int nf0, nf1, nf2, xsplit, ncell_full, ntile;
+  int* tile;
 };
 
 static GridArgs grid_args(const Grid& g) {
-  return GridArgs{g.n[0], g.n[1], g.n[2], g.ncell, 1, g.d_rank_of, g.d_start, g.d_count};
+  return GridArgs{g.n[0], g.n[1], g.n[2], g.ncell, 1, g.d_rank_of, g.d_start, g.d_count,
+                  g.nf[0], g.nf[1], g.nf[2], g.xsplit, g.ncell_full, g.ntile, g.d_tile};
 }
 
 // The binning kernels take plain scalar and pointer parameters only.  A
@@ -95,72 +98,111 @@ __global__ void k_bin(int n, const unsigned* gate, const unsigned long long* __r
            crank, ccount, cell_fg, slot_fg, cell_cg, slot_cg, flags);
 }
 
-// One block per grid: exclusive scan of counts into start[0..ncell], counts
-// reset to zero (they become the scatter cursors).  Tiles of 4 cells per
-// thread, scanned block-wide with warp shuffles, a running carry between tiles.
-__device__ __forceinline__ void scan_body(int bid, const unsigned* gate, int valid0, int ncell0, int* start0,
-                                         int* count0, int valid1, int ncell1, int* start1, int* count1,
-                                         DevState* st) {
+// Exclusive scan of the cell counts into start[0..ncell] in two passes over
+// tiles of kScanTile cells: scan_tile_body scans one tile locally (4 cells per
+// thread of 1024, warp shuffles, then the warp totals), writes the tile total
+// and resets the counts to zero for the next build; scan_add_body adds the sum
+// of the tile totals before its tile.  Tile t of a build: the tiles of the FG
+// grid, then those of the CG grid.
+struct ScanGrid {
+  int valid, ncell, ntile;
+  int* start;
+  int* count;
+  int* tile;
+};
+
+__device__ __forceinline__ void pick_scan(const ScanGrid& g0, const ScanGrid& g1, int t, ScanGrid* g, int* tile) {
+  if (t < g0.ntile) {
+    *g = g0;
+    *tile = t;
+  } else {
+    *g = g1;
+    *tile = t - g0.ntile;
+  }
+}
+
+__device__ __forceinline__ void scan_tile_body(int t, const unsigned* gate, const ScanGrid& g0, const ScanGrid& g1,
+                                              DevState* st) {
   if (gate_closed(gate)) return;
-  if (bid == 0 && threadIdx.x == 0) {  // list statistics of this build
+  if (t == 0 && threadIdx.x == 0) {  // list statistics of this build
     st->max_fg = 0;
     st->max_cg = 0;
     st->tot_fg = 0;
     st->tot_cg = 0;
   }
-  const int valid = bid == 0 ? valid0 : valid1;
-  const int ncell = bid == 0 ? ncell0 : ncell1;
-  int* const start = bid == 0 ? start0 : start1;
-  int* const count = bid == 0 ? count0 : count1;
-  if (!valid) return;
-  __shared__ int sh[1024 / 32];
-  __shared__ int s_carry;
+  ScanGrid g;
+  int tile;
+  pick_scan(g0, g1, t, &g, &tile);
+  __shared__ int sh[kScanTile / 4 / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int base = 0; base < ncell; base += 4 * blockDim.x) {
-    const int c0 = base + 4 * threadIdx.x;
-    int v[4];
+  const int c0 = tile * kScanTile + 4 * threadIdx.x;
+  int v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = c0 + q < ncell ? count[c0 + q] : 0;
-    const int tsum = v[0] + v[1] + v[2] + v[3];
-    int incl = tsum;
+  for (int q = 0; q < 4; ++q) v[q] = c0 + q < g.ncell ? g.count[c0 + q] : 0;
+  const int tsum = v[0] + v[1] + v[2] + v[3];
+  int incl = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) sh[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < nw ? sh[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+      const int u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
     }
-    if (lane == 31) sh[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      int w = lane < nw ? sh[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += t;
-      }
-      if (lane < nw) sh[lane] = w;  // inclusive warp totals
-    }
-    __syncthreads();
-    const int carry = s_carry;
-    int run = carry + (wid > 0 ? sh[wid - 1] : 0) + incl - tsum;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (c0 + q < ncell) {
-        start[c0 + q] = run;
-        count[c0 + q] = 0;
-        run += v[q];
-      }
-    __syncthreads();  // every thread has read s_carry and sh
-    if (threadIdx.x == 0) s_carry = carry + sh[nw - 1];
-    __syncthreads();
+    if (lane < nw) sh[lane] = w;  // inclusive warp totals
   }
-  if (threadIdx.x == 0) start[ncell] = s_carry;
+  __syncthreads();
+  int run = (wid > 0 ? sh[wid - 1] : 0) + incl - tsum;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (c0 + q < g.ncell) {
+      g.start[c0 + q] = run;
+      g.count[c0 + q] = 0;
+      run += v[q];
+    }
+  if (threadIdx.x == 0) g.tile[tile] = sh[nw - 1];
+  __syncthreads();  // sh is reused by a batched kernel's next work item
 }
 
-__global__ void k_scan(const unsigned* gate, int valid0, int ncell0, int* start0, int* count0, int valid1,
-                       int ncell1, int* start1, int* count1, DevState* st) {
-  scan_body(blockIdx.x, gate, valid0, ncell0, start0, count0, valid1, ncell1, start1, count1, st);
+__device__ __forceinline__ void scan_add_body(int t, const unsigned* gate, const ScanGrid& g0, const ScanGrid& g1) {
+  if (gate_closed(gate)) return;
+  ScanGrid g;
+  int tile;
+  pick_scan(g0, g1, t, &g, &tile);
+  __shared__ int sh[kScanTile / 4 / 32];
+  int part = 0;
+  for (int u = threadIdx.x; u < tile; u += blockDim.x) part += g.tile[u];
+  part = warp_sum(part);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) sh[wid] = part;
+  __syncthreads();
+  int off = 0;
+  for (int w = 0; w < nw; ++w) off += sh[w];
+  const int c0 = tile * kScanTile + 4 * threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (c0 + q < g.ncell) g.start[c0 + q] += off;
+  if (tile == g.ntile - 1 && threadIdx.x == 0) g.start[g.ncell] = off + g.tile[tile];
+  __syncthreads();  // sh is reused by a batched kernel's next work item
+}
+
+__global__ void __launch_bounds__(kScanTile / 4) k_scan_tiles(const unsigned* gate, ScanGrid g0, ScanGrid g1,
+                                                               DevState* st) {
+  scan_tile_body(blockIdx.x, gate, g0, g1, st);
+}
+
+__global__ void __launch_bounds__(kScanTile / 4) k_scan_add(const unsigned* gate, ScanGrid g0, ScanGrid g1) {
+  scan_add_body(blockIdx.x, gate, g0, g1);
+}
+
+__host__ __device__ __forceinline__ ScanGrid scan_grid(const GridArgs& g) {
+  return ScanGrid{g.valid, g.ncell, g.valid ? g.ntile : 0, g.start, g.count, g.tile};
 }
 
 __device__ __forceinline__ void scatter_body(int bid, int nblk, int n, const unsigned* gate,
@@ -186,62 +228,35 @@ __global__ void k_scatter(int n, const unsigned* gate, const int* __restrict__ t
                slot_cg, perm_fg, perm_cg);
 }
 
-// One warp per cell: the cell's atoms put in index order (the scatter order
-// is arbitrary).  Each atom's new place is the number of smaller indices in
-// its cell: up to 32 atoms counted from registers (shuffles), up to 256 from a
-// per-warp shared-memory copy; larger cells fall back to an insertion sort by
-// one lane.  Resets the cell cursor.
-constexpr int kSortSmem = 256;
-__device__ __forceinline__ void sort_body(int bid, int nblk, const unsigned* gate, int fn, const int* fstart,
-                                         int* fcount, int cn, const int* cstart, int* ccount,
-                                         int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
+// One thread per cell: the cell's atoms put in index order (the scatter order
+// is arbitrary) by an insertion sort in place; cells hold ~5 atoms.
+__device__ __forceinline__ void sort_body(int bid, int nblk, const unsigned* gate, int fn, const int* fstart, int cn,
+                                         const int* cstart, int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
   if (gate_closed(gate)) return;
-  __shared__ int s_v[kThreads / 32][kSortSmem];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nwarps = (nblk * blockDim.x) >> 5;
-  for (int t = (bid * blockDim.x + threadIdx.x) >> 5; t < fn + cn; t += nwarps) {
+  for (int t = bid * blockDim.x + threadIdx.x; t < fn + cn; t += nblk * blockDim.x) {
     const bool fg = t < fn;
     const int c = fg ? t : t - fn;
     const int* const start = fg ? fstart : cstart;
-    int* const count = fg ? fcount : ccount;
     int* const perm = fg ? perm_fg : perm_cg;
-    const int lo = start[c], hi = start[c + 1], m = hi - lo;
-    if (m <= 32) {
-      const int v = lane < m ? perm[lo + lane] : 0x7fffffff;
-      int rank = 0;
-      for (int k = 0; k < m; ++k) rank += __shfl_sync(0xffffffffu, v, k) < v ? 1 : 0;
-      __syncwarp();
-      if (lane < m) perm[lo + rank] = v;
-    } else if (m <= kSortSmem) {
-      int* const sv = s_v[wid];
-      for (int k = lane; k < m; k += 32) sv[k] = perm[lo + k];
-      __syncwarp();
-      for (int k = lane; k < m; k += 32) {
-        const int v = sv[k];
-        int rank = 0;
-        for (int q = 0; q < m; ++q) rank += sv[q] < v ? 1 : 0;
-        perm[lo + rank] = v;
+    const int lo = start[c], hi = start[c + 1];
+    for (int k = lo + 1; k < hi; ++k) {
+      const int v = perm[k];
+      int q = k - 1;
+      int u = perm[q];
+      while (u > v) {
+        perm[q + 1] = u;
+        if (--q < lo) break;
+        u = perm[q];
       }
-      __syncwarp();  // the copy is reused by this warp's next cell
-    } else if (lane == 0) {
-      for (int k = lo + 1; k < hi; ++k) {
-        const int v = perm[k];
-        int q = k - 1;
-        while (q >= lo && perm[q] > v) {
-          perm[q + 1] = perm[q];
-          --q;
-        }
-        perm[q + 1] = v;
-      }
+      perm[q + 1] = v;
     }
-    if (lane == 0) count[c] = 0;
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_sort_cells(const unsigned* gate, int fn, const int* fstart,
-                                                         int* fcount, int cn, const int* cstart, int* ccount,
-                                                         int* __restrict__ perm_fg, int* __restrict__ perm_cg) {
-  sort_body(blockIdx.x, gridDim.x, gate, fn, fstart, fcount, cn, cstart, ccount, perm_fg, perm_cg);
+__global__ void __launch_bounds__(kThreads) k_sort_cells(const unsigned* gate, int fn, const int* fstart, int cn,
+                                                         const int* cstart, int* __restrict__ perm_fg,
+                                                         int* __restrict__ perm_cg) {
+  sort_body(blockIdx.x, gridDim.x, gate, fn, fstart, cn, cstart, perm_fg, perm_cg);
 }
 
 __device__ __forceinline__ void pack_body(int bid, int nblk, int n, int n_h, const unsigned* gate,
@@ -300,45 +315,34 @@ struct ListArgs {
   unsigned overflow_bit;
 };
 
-__device__ __forceinline__ int axis_cells(int c, int n, int (&out)[3]) {
-  if (n >= 3) {
-    out[0] = c == 0 ? n - 1 : c - 1;
-    out[1] = c;
-    out[2] = c == n - 1 ? 0 : c + 1;
-    return 3;
-  }
-  for (int k = 0; k < n; ++k) out[k] = k;  // 1 or 2 cells: visit each once
-  return n;
-}
-
 constexpr int kListThreads = 128;  // 4 warps per cell
 
 __device__ __forceinline__ float wrap1(float d, float l, float il) { return d - l * rintf(d * il); }
 
-// One cell atom (slot s, atom id ai, relative position p) against a staged
-// window padded to a multiple of 32 (padding sits far outside every cutoff):
-// 32 candidates per iteration, accepted ones appended at k in window order.
-// Exclusions: a candidate whose atom id lies within the exclusion window of
-// ai (this includes ai itself) is checked against ai's exclusion list; all
-// others cannot be excluded.  Returns the new count.
+// One cell atom (slot s, atom id ai, relative position p) against the staged
+// candidates beg .. end - 1 of the window: 32 candidates per iteration,
+// accepted ones appended at k in window order.  Exclusions: a candidate whose
+// atom id lies within the exclusion window of ai (this includes ai itself) is
+// checked against ai's exclusion list; all others cannot be excluded.
+// Returns the new count.
 template <bool WRAP>
-__device__ __forceinline__ int scan_window(const float4* s_pos, const int* s_atom, int wn32, int ai,
-                                           float px, float py, float pz, float rl2, float lx, float ly,
-                                           float lz, const int (&ex)[8], int e0, int e1, const int* excl_idx,
-                                           int win, int* nbr_s, unsigned stride, int cap, int k) {
+__device__ __forceinline__ int scan_range(const float4* s_pos, const int* s_atom, int beg, int end, int ai,
+                                          float px, float py, float pz, float rl2, float lx, float ly,
+                                          float lz, const int (&ex)[8], int e0, int e1, const int* excl_idx,
+                                          int win, int* nbr_s, unsigned stride, int cap, int k) {
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
-  for (int j0 = 0; j0 < wn32; j0 += 32) {
-    const float4 q = s_pos[j0 + lane];
+  for (int j0 = beg; j0 < end; j0 += 32) {
+    const int j = j0 + lane < end ? j0 + lane : beg;
+    const float4 q = s_pos[j];
     float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
     if (WRAP) {
       dx = wrap1(dx, lx, 1.f / lx);
       dy = wrap1(dy, ly, 1.f / ly);
       dz = wrap1(dz, lz, 1.f / lz);
     }
-    bool acc = dx * dx + dy * dy + dz * dz < rl2;
-    const int aj = s_atom[j0 + lane];
-    if (WRAP) acc = acc && aj >= 0;  // wrapped padding can land anywhere
+    bool acc = j0 + lane < end && dx * dx + dy * dy + dz * dz < rl2;
+    const int aj = s_atom[j];
     if (acc && unsigned(aj - ai + win) <= unsigned(2 * win)) {
       // the first eight excluded partners are in registers (-1 where unused)
       acc = aj != ai;
@@ -358,18 +362,24 @@ __device__ __forceinline__ int scan_window(const float4* s_pos, const int* s_ato
 constexpr int kListWindow = 1024;  // candidates staged in shared memory at a time (a multiple of 32)
 constexpr int kListGroup = 64;     // cell atoms handled per pass
 
-// One block per cell (CG-grid cells first, then FG-grid cells).  The block
-// stages the atoms of the cell's 27-cell neighbourhood in shared memory as
-// FP32 coordinates relative to the cell's first atom (from the exact wrapped
-// 32-bit differences; the list radius carries the skin, so FP32 rounding
-// near the list radius cannot lose a pair inside the interaction range), then
-// each warp takes one atom of the cell at a time and tests 32 staged
-// candidates per iteration; accepted candidates are appended in candidate
-// order (ballot + prefix count), so the list is deterministic.
+constexpr int kStageMax = 3 * kXSplit * 9;  // staged cells: 3 x kXSplit x-slabs by 3 by 3 cells
+
+// One block per full cell (CG-grid cells first, then FG-grid cells).  The
+// block stages the atoms of the 27 full cells around its cell in shared
+// memory, x-slab after x-slab (on a split grid each full cell is kXSplit
+// slabs along x), as FP32 coordinates relative to the cell's first atom (from
+// the exact wrapped 32-bit differences; the list radius carries the skin, so
+// FP32 rounding near the list radius cannot lose a pair inside the interaction
+// range).  Each warp then takes one atom of the cell at a time and tests 32
+// staged candidates per iteration: on a split grid only the run of x-slabs
+// within the list radius of the atom (a contiguous range of the staged
+// candidates, about 3/4 of them), otherwise all of them.  Accepted candidates
+// are appended in staging order (ballot + prefix count), so the list is
+// deterministic.
 __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg, int ncell_cg, int cb) {
   __shared__ float4 s_pos[kListWindow];  // x, y, z relative; w = slot index bits
   __shared__ int s_atom[kListWindow];    // atom id of each staged candidate
-  __shared__ int s_cstart[27], s_coff[28];
+  __shared__ int s_cstart[kStageMax], s_coff[kStageMax + 1];
   __shared__ int s_k[kListGroup];
   __shared__ int s_max;
   __shared__ unsigned long long s_tot;
@@ -380,7 +390,7 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
     const int4* pos;
     const int* perm;
     int excl_window;
-    int n0, n1, n2;
+    int n0, n1, n2, nf0, nf1, nf2, xsplit;
     const int* rank_of;
     const int* start;
     float sx, sy, sz, rl2;
@@ -413,44 +423,74 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
   RELRES_PICK(flags);
   RELRES_PICK(overflow_bit);
 #undef RELRES_PICK
-  a.n0 = is_cg ? cg.g.n0 : fg.g.n0;
-  a.n1 = is_cg ? cg.g.n1 : fg.g.n1;
-  a.n2 = is_cg ? cg.g.n2 : fg.g.n2;
-  a.rank_of = is_cg ? cg.g.rank_of : fg.g.rank_of;
-  a.start = is_cg ? cg.g.start : fg.g.start;
-  const int c = is_cg ? cb : cb - ncell_cg;
-  const int i0 = a.start[c];
-  const int ni = a.start[c + 1] - i0;
+#define RELRES_PICKG(f) a.f = is_cg ? cg.g.f : fg.g.f
+  RELRES_PICKG(n0);
+  RELRES_PICKG(n1);
+  RELRES_PICKG(n2);
+  RELRES_PICKG(nf0);
+  RELRES_PICKG(nf1);
+  RELRES_PICKG(nf2);
+  RELRES_PICKG(xsplit);
+  RELRES_PICKG(rank_of);
+  RELRES_PICKG(start);
+#undef RELRES_PICKG
+  const int S = a.xsplit;
+  const int cf = is_cg ? cb : cb - ncell_cg;  // dense rank of the full cell
+  const int i0 = a.start[cf * S];
+  const int ni = a.start[(cf + 1) * S] - i0;
   if (ni == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int4 ref = a.pos[i0];
-  if (threadIdx.x == 0) {
-    int cx[3], cy[3], cz[3];
-    const int nx = axis_cells(cell_of(ref.x, a.n0), a.n0, cx);
-    const int ny = axis_cells(cell_of(ref.y, a.n1), a.n1, cy);
-    const int nz = axis_cells(cell_of(ref.z, a.n2), a.n2, cz);
-    int m = 0, off = 0;
-    for (int ix = 0; ix < nx; ++ix)
-      for (int iy = 0; iy < ny; ++iy)
-        for (int iz = 0; iz < nz; ++iz) {
-          const int cc = a.rank_of[(cx[ix] * a.n1 + cy[iy]) * a.n2 + cz[iz]];
-          const int b = a.start[cc];
-          s_cstart[m] = b;
-          s_coff[m] = off;
-          off += a.start[cc + 1] - b;
-          ++m;
-        }
-    for (int k = m; k < 28; ++k) s_coff[k] = off;
-    s_max = 0;
-    s_tot = 0ull;
+  // staged cells, x-major: per axis the full cells F-1, F, F+1 (x: as S slabs
+  // each), or every cell of an axis with fewer than three
+  const int fx = cell_of(ref.x, a.n0) / S, fy = cell_of(ref.y, a.n1), fz = cell_of(ref.z, a.n2);
+  const int d0 = a.nf0 >= 3 ? 3 * S : a.n0, d1 = a.nf1 >= 3 ? 3 : a.n1, d2 = a.nf2 >= 3 ? 3 : a.n2;
+  const int b0 = a.nf0 >= 3 ? S * (fx - 1) + a.n0 : 0, b1 = a.nf1 >= 3 ? fy - 1 + a.n1 : 0,
+            b2 = a.nf2 >= 3 ? fz - 1 + a.n2 : 0;
+  const int ms = d0 * d1 * d2;
+  for (int t = threadIdx.x; t < ms; t += blockDim.x) {
+    const int i = t / (d1 * d2), j = (t / d2) % d1, k = t % d2;
+    const int gx = (b0 + i) % a.n0, gy = (b1 + j) % a.n1, gz = (b2 + k) % a.n2;
+    const int cc = a.rank_of[(gx * a.n1 + gy) * a.n2 + gz];
+    const int b = a.start[cc];
+    s_cstart[t] = b;
+    s_coff[t] = a.start[cc + 1] - b;  // count, scanned below
   }
   __syncthreads();
-  const int total = s_coff[27];
-  // With 4 or more cells per axis every staged offset from the reference atom
-  // and every candidate offset is below L/2, so plain differences of the
+  if (warp == 0) {  // exclusive scan of the staged counts, up to 4 cells per lane
+    const int per = (ms + 31) / 32;
+    const int lo = min(ms, lane * per), hi = min(ms, lo + per);
+    int sum = 0;
+    for (int t = lo; t < hi; ++t) sum += s_coff[t];
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    int run = incl - sum;
+    for (int t = lo; t < hi; ++t) {
+      const int cnt = s_coff[t];
+      s_coff[t] = run;
+      run += cnt;
+    }
+    if (lane == 31) s_coff[ms] = incl;
+    if (lane == 0) {
+      s_max = 0;
+      s_tot = 0ull;
+    }
+  }
+  __syncthreads();
+  const int total = s_coff[ms];
+  // With 4 or more full cells per axis every staged offset from the reference
+  // atom and every candidate offset is below L/2, so plain differences of the
   // relative coordinates are minimum images; smaller grids wrap explicitly.
-  const bool wrap = a.n0 < 4 || a.n1 < 4 || a.n2 < 4;
+  const bool wrap = a.nf0 < 4 || a.nf1 < 4 || a.nf2 < 4;
+  const bool slabs = S > 1 && !wrap;  // each atom tests its run of x-slabs only
   const float lx = a.sx * 4294967296.f, ly = a.sy * 4294967296.f, lz = a.sz * 4294967296.f;
+  // list radius (+ a margin above the rounding of the positions) in x-slab widths
+  const float reach = (sqrtf(a.rl2) + 1e-3f) * float(a.n0) / lx;
+  const int slab_cells = d1 * d2;
   int blk_max = 0;
   unsigned long long blk_tot = 0ull;
   for (int g0 = 0; g0 < ni; g0 += kListGroup) {
@@ -459,23 +499,17 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
     for (int w0 = 0; w0 < total; w0 += kListWindow) {
       const int wn = min(kListWindow, total - w0);
       __syncthreads();
-      const int wn32 = (wn + 31) & ~31;
-      for (int k = threadIdx.x; k < wn32; k += blockDim.x) {
-        if (k < wn) {
-          const int gidx = w0 + k;
-          int m = 0;  // stencil cell holding candidate gidx
+      for (int k = threadIdx.x; k < wn; k += blockDim.x) {
+        const int gidx = w0 + k;
+        int m = 0;  // staged cell holding candidate gidx: the last one starting at or before it
 #pragma unroll
-          for (int step = 16; step > 0; step >>= 1)
-            if (m + step < 28 && s_coff[m + step] <= gidx) m += step;
-          const int t = s_cstart[m] + (gidx - s_coff[m]);
-          const int4 q = a.pos[t];
-          s_pos[k] = make_float4(dfix32(q.x, ref.x, a.sx), dfix32(q.y, ref.y, a.sy),
-                                 dfix32(q.z, ref.z, a.sz), __int_as_float(t));
-          s_atom[k] = a.perm[t];
-        } else {  // padding: never within a list radius
-          s_pos[k] = make_float4(3.0e18f, 3.0e18f, 3.0e18f, __int_as_float(0));
-          s_atom[k] = -1;
-        }
+        for (int step = 64; step > 0; step >>= 1)
+          if (m + step < ms && s_coff[m + step] <= gidx) m += step;
+        const int t = s_cstart[m] + (gidx - s_coff[m]);
+        const int4 q = a.pos[t];
+        s_pos[k] = make_float4(dfix32(q.x, ref.x, a.sx), dfix32(q.y, ref.y, a.sy), dfix32(q.z, ref.z, a.sz),
+                               __int_as_float(t));
+        s_atom[k] = a.perm[t];
       }
       __syncthreads();
       for (int il = warp; il < ng; il += blockDim.x >> 5) {
@@ -489,10 +523,23 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
         for (int e = 0; e < 8; ++e) ex[e] = e0 + e < e1 ? a.excl_idx[e0 + e] : -1;
         int* const nbr_s = a.nbr + 4 * size_t(s);
         const unsigned stride = 4u * unsigned(a.nslots);
-        const int k = wrap ? scan_window<true>(s_pos, s_atom, wn32, ai, px, py, pz, a.rl2, lx, ly, lz, ex, e0,
-                                               e1, a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il])
-                           : scan_window<false>(s_pos, s_atom, wn32, ai, px, py, pz, a.rl2, lx, ly, lz, ex, e0,
-                                                e1, a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il]);
+        int beg = 0, end = total;
+        if (slabs) {
+          // the atom's x in slab widths from the first staged slab: its own
+          // slab (S .. 2S - 1) plus its place in it
+          const int cx = cell_of(p.x, a.n0);
+          const float ux = float(unsigned(p.x) * unsigned(a.n0)) * 2.3283064365386963e-10f;
+          const float xs = float(cx - S * fx + S) + ux;
+          const int lo = max(0, int(floorf(xs - reach))), hi = min(d0 - 1, int(floorf(xs + reach)));
+          beg = s_coff[lo * slab_cells];
+          end = s_coff[(hi + 1) * slab_cells];
+        }
+        beg = max(beg, w0) - w0;
+        end = min(end, w0 + wn) - w0;
+        const int k = wrap ? scan_range<true>(s_pos, s_atom, beg, end, ai, px, py, pz, a.rl2, lx, ly, lz, ex, e0,
+                                              e1, a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il])
+                           : scan_range<false>(s_pos, s_atom, beg, end, ai, px, py, pz, a.rl2, lx, ly, lz, ex, e0,
+                                               e1, a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il]);
         if (lane == 0) s_k[il] = k;
       }
     }
@@ -524,7 +571,7 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
 __global__ void __launch_bounds__(kListThreads) k_list(const unsigned* gate, ListArgs fg, ListArgs cg,
                                                        int ncell_cg) {
   if (gate_closed(gate)) return;
-  const int ncell = ncell_cg + fg.g.ncell;
+  const int ncell = ncell_cg + fg.g.ncell_full;
   for (int cb = blockIdx.x; cb < ncell; cb += gridDim.x) list_cell(fg, cg, ncell_cg, cb);
 }
 
@@ -535,12 +582,12 @@ static int blocks_for(int n) {
 }
 
 // ---- batches (relres_batch_step): the list rebuild of every replica whose
-// displacement trigger fired, in six launches for the whole batch.  After the
+// displacement trigger fired, in seven launches for the whole batch.  After the
 // drift, k_worklist lists those replicas and, per kernel class, the prefix
 // sums of the blocks each of them takes in its own rebuild (the same counts as
 // launch_rebuild / launch_lists); each batched kernel then walks the work
 // items (replica, block) with a fixed grid, so a step in which few replicas
-// rebuild costs six short launches, and one in which none does, six empty ones.
+// rebuild costs seven short launches, and one in which none does, seven empty ones.
 
 // Everything one replica's rebuild kernels take.
 struct BuildArgs {
@@ -568,7 +615,7 @@ struct BuildArgs {
   int ncell_cg;
 };
 
-enum { kRbBin = 0, kRbScan, kRbScatter, kRbSort, kRbPack, kRbList, kRbClasses };
+enum { kRbBin = 0, kRbScanTiles, kRbScanAdd, kRbScatter, kRbSort, kRbPack, kRbList, kRbClasses };
 
 // one block: wl[0] = number of rebuilding replicas, wl[1 .. nrep] their
 // indices, then per class k the prefix sums pre_k[0 .. count] at
@@ -657,12 +704,21 @@ __global__ void __launch_bounds__(kThreads, 6) k_bin_batch(const BuildArgs* __re
   RELRES_BATCH_END
 }
 
-__global__ void __launch_bounds__(1024) k_scan_batch(const BuildArgs* __restrict__ args, const int* __restrict__ wl,
-                                                     const int* __restrict__ nbt, int nrep) {
-  RELRES_BATCH_LOOP(kRbScan)
+__global__ void __launch_bounds__(kScanTile / 4) k_scan_tiles_batch(const BuildArgs* __restrict__ args,
+                                                                     const int* __restrict__ wl,
+                                                                     const int* __restrict__ nbt, int nrep) {
+  RELRES_BATCH_LOOP(kRbScanTiles)
   (void)nb;
-  scan_body(b, sa.gate, 1, sa.gf.ncell, sa.gf.start, sa.gf.count, sa.gc.valid, sa.gc.ncell, sa.gc.start,
-            sa.gc.count, sa.st);
+  scan_tile_body(b, sa.gate, scan_grid(sa.gf), scan_grid(sa.gc), sa.st);
+  RELRES_BATCH_END
+}
+
+__global__ void __launch_bounds__(kScanTile / 4) k_scan_add_batch(const BuildArgs* __restrict__ args,
+                                                                   const int* __restrict__ wl,
+                                                                   const int* __restrict__ nbt, int nrep) {
+  RELRES_BATCH_LOOP(kRbScanAdd)
+  (void)nb;
+  scan_add_body(b, sa.gate, scan_grid(sa.gf), scan_grid(sa.gc));
   RELRES_BATCH_END
 }
 
@@ -678,8 +734,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_sort_batch(const BuildArgs* __r
                                                          const int* __restrict__ wl, const int* __restrict__ nbt,
                                                          int nrep) {
   RELRES_BATCH_LOOP(kRbSort)
-  sort_body(b, nb, sa.gate, sa.gf.ncell, sa.gf.start, sa.gf.count, sa.gc.valid ? sa.gc.ncell : 0, sa.gc.start,
-            sa.gc.count, sa.perm_fg, sa.perm_cg);
+  sort_body(b, nb, sa.gate, sa.gf.ncell, sa.gf.start, sa.gc.valid ? sa.gc.ncell : 0, sa.gc.start, sa.perm_fg,
+            sa.perm_cg);
   RELRES_BATCH_END
 }
 
@@ -695,7 +751,7 @@ __global__ void __launch_bounds__(kListThreads, 8) k_list_batch(const BuildArgs*
                                                              const int* __restrict__ wl,
                                                              const int* __restrict__ nbt, int nrep) {
   RELRES_BATCH_LOOP(kRbList)
-  const int ncell = sa.ncell_cg + sa.lfg.g.ncell;
+  const int ncell = sa.ncell_cg + sa.lfg.g.ncell_full;
   for (int cb = b; cb < ncell; cb += nb) list_cell(sa.lfg, sa.lcg, sa.ncell_cg, cb);
   RELRES_BATCH_END
 }
@@ -745,7 +801,7 @@ static BuildArgs build_args(relres_ctx* c, const unsigned* gate) {
 }
 
 // list-kernel blocks: persistent, one wave walks the cells (a closed gate costs one small launch)
-static int list_blocks(const BuildArgs& b) { return std::min(b.ncell_cg + b.gf.ncell, 152 * 8); }
+static int list_blocks(const BuildArgs& b) { return std::min(b.ncell_cg + b.gf.ncell_full, 152 * 8); }
 static int sort_cells_of(const BuildArgs& b) { return b.gf.ncell + (b.gc.valid ? b.gc.ncell : 0); }
 
 cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
@@ -759,15 +815,17 @@ cudaError_t launch_rebuild(relres_ctx* c, const unsigned* gate) {
                                         gc.rank_of, gc.count, c->d_cell_fg, c->d_slot_fg, c->d_cell_cg,
                                         c->d_slot_cg, &c->d_state->flags);
   RELRES_LAUNCHED(c);
-  k_scan<<<2, 1024, 0, c->stream>>>(gate, 1, gf.ncell, gf.start, gf.count, gc.valid, gc.ncell, gc.start,
-                                    gc.count, c->d_state);
+  const ScanGrid sf = scan_grid(gf), sc = scan_grid(gc);
+  k_scan_tiles<<<sf.ntile + sc.ntile, kScanTile / 4, 0, c->stream>>>(gate, sf, sc, c->d_state);
+  RELRES_LAUNCHED(c);
+  k_scan_add<<<sf.ntile + sc.ntile, kScanTile / 4, 0, c->stream>>>(gate, sf, sc);
   RELRES_LAUNCHED(c);
   k_scatter<<<nb, kThreads, 0, c->stream>>>(c->n, gate, c->d_type, c->hyb_mask, gf.start, gc.valid, gc.start,
                                             c->d_cell_fg, c->d_slot_fg, c->d_cell_cg, c->d_slot_cg,
                                             c->d_perm_fg, c->d_perm_cg);
   RELRES_LAUNCHED(c);
-  k_sort_cells<<<blocks_for(32 * sort_cells_of(b)), kThreads, 0, c->stream>>>(
-      gate, gf.ncell, gf.start, gf.count, gc.valid ? gc.ncell : 0, gc.start, gc.count, c->d_perm_fg, c->d_perm_cg);
+  k_sort_cells<<<blocks_for(sort_cells_of(b)), kThreads, 0, c->stream>>>(
+      gate, gf.ncell, gf.start, gc.valid ? gc.ncell : 0, gc.start, c->d_perm_fg, c->d_perm_cg);
   RELRES_LAUNCHED(c);
   k_pack<<<nb, kThreads, 0, c->stream>>>(c->n, b.n_h_pack, gate, c->d_xfx, c->d_type, c->d_perm_fg, c->d_perm_cg,
                                          c->d_rank_fg, c->d_rank_cg, c->d_pos_fg, c->d_pos_cg, b.p64f, b.p64c,
@@ -784,9 +842,11 @@ cudaError_t prepare_rebuild_batch(const std::vector<relres_ctx*>& cs, RebuildBat
     relres_ctx* c = cs[r];
     args[r] = build_args(c, &c->d_state->flags);
     nbt[kRbBin * nr + r] = blocks_for(c->n);
-    nbt[kRbScan * nr + r] = 2;
+    const int ntiles = args[r].gf.ntile + (args[r].gc.valid ? args[r].gc.ntile : 0);
+    nbt[kRbScanTiles * nr + r] = ntiles;
+    nbt[kRbScanAdd * nr + r] = ntiles;
     nbt[kRbScatter * nr + r] = blocks_for(c->n);
-    nbt[kRbSort * nr + r] = blocks_for(32 * sort_cells_of(args[r]));
+    nbt[kRbSort * nr + r] = blocks_for(sort_cells_of(args[r]));
     nbt[kRbPack * nr + r] = blocks_for(c->n);
     nbt[kRbList * nr + r] = list_blocks(args[r]);
   }
@@ -815,7 +875,8 @@ cudaError_t launch_rebuild_batch(cudaStream_t s, const RebuildBatch& rb, int nre
   const int* nbt = static_cast<const int*>(rb.nbt.d_args);
   const int* wl = rb.d_wl;
   k_bin_batch<<<152 * 4, kThreads, 0, s>>>(args, wl, nbt, nrep);
-  k_scan_batch<<<152, 1024, 0, s>>>(args, wl, nbt, nrep);
+  k_scan_tiles_batch<<<152, kScanTile / 4, 0, s>>>(args, wl, nbt, nrep);
+  k_scan_add_batch<<<152, kScanTile / 4, 0, s>>>(args, wl, nbt, nrep);
   k_scatter_batch<<<152 * 4, kThreads, 0, s>>>(args, wl, nbt, nrep);
   k_sort_batch<<<152 * 4, kThreads, 0, s>>>(args, wl, nbt, nrep);
   k_pack_batch<<<152 * 4, kThreads, 0, s>>>(args, wl, nbt, nrep);
@@ -982,7 +1043,7 @@ static bool list_args_cg(relres_ctx* c, ListArgs* cg, int* ncell_cg) {
   *cg = ListArgs{c->n_h, c->d_pos_cg, c->d_perm_cg, grid_args(c->gcg), s0, s1, s2, float(rc * rc),
                  c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg,
                  &st->max_cg, &st->tot_cg, &st->flags, F_OVERFLOW_CG};
-  *ncell_cg = c->gcg.ncell;
+  *ncell_cg = c->gcg.ncell_full;
   return true;
 }
 
@@ -992,8 +1053,8 @@ cudaError_t launch_lists(relres_ctx* c, const unsigned* gate) {
   ListArgs cg = fg;  // stand-in when there is no CG list (its blocks are not launched)
   int ncell_cg = 0;
   list_args_cg(c, &cg, &ncell_cg);
-  // persistent: one wave of blocks walks the cells (a closed gate costs one small launch)
-  const int nb = std::min(ncell_cg + c->gfg.ncell, 152 * 8);
+  // persistent: one wave of blocks walks the full cells (a closed gate costs one small launch)
+  const int nb = std::min(ncell_cg + c->gfg.ncell_full, 152 * 8);
   k_list<<<nb, kListThreads, 0, c->stream>>>(gate, fg, cg, ncell_cg);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();

@@ -141,13 +141,27 @@ struct StepParams {
   double* thermo;  // device [rows][RELRES_THERMO_COLS] or null
 };
 
+// Cell grid of one list.  Full cells are at least one list radius wide (nf
+// per axis).  With four or more of them on every axis each is cut into
+// kXSplit slabs along x (xsplit), atoms are binned into those sub-cells, and
+// the dense rank of a sub-cell is xsplit x the Morton rank of its full cell +
+// its slab, so the atoms of a full cell are contiguous slots and the list
+// build can give each atom the contiguous run of x-slabs within its list
+// radius.
+constexpr int kXSplit = 4;
 struct Grid {
-  int n[3];
-  int ncell;
-  int* d_rank_of = nullptr;  // [n0*n1*n2] -> dense cell rank (Morton order)
+  int n[3];                  // binning cells per axis (x: nf[0] * xsplit)
+  int nf[3];                 // full cells per axis
+  int xsplit = 1;
+  int ncell;                 // binning cells
+  int ncell_full;
+  int ntile;                 // tiles of the cell scan
+  int* d_rank_of = nullptr;  // [n0*n1*n2] -> dense cell rank
   int* d_start = nullptr;    // [ncell+1]
   int* d_count = nullptr;    // [ncell] counts / cursors (zero between builds)
+  int* d_tile = nullptr;     // [ntile] per-tile cell counts of the scan
 };
+constexpr int kScanTile = 4096;  // cells per block of the two-pass cell scan
 
 // ------------------------------------------------------------------ context
 }  // namespace relres
@@ -434,7 +448,7 @@ cudaError_t prepare_sum_batch(const std::vector<relres_ctx*>& cs, const std::vec
                               double* const* d_vel, BatchLaunch* b);
 cudaError_t launch_sum_batch(cudaStream_t s, bool fp64, int k, const BatchLaunch& b, int nrep);
 // the list rebuild of every replica whose displacement trigger fired (d_states[r]->flags & F_REBUILD):
-// a work-list kernel and six batched rebuild kernels (neighbor.cu)
+// a work-list kernel and seven batched rebuild kernels (neighbor.cu)
 struct RebuildBatch {
   BatchLaunch args;  // BuildArgs per replica
   BatchLaunch nbt;   // blocks of each kernel class per replica
@@ -445,10 +459,12 @@ cudaError_t prepare_rebuild_batch(const std::vector<relres_ctx*>& cs, RebuildBat
 // the work list of this step; sets `any` (a graph conditional) iff some replica rebuilds
 cudaError_t launch_worklist(cudaStream_t s, const RebuildBatch& rb, DevState* const* d_states, int nrep,
                             cudaGraphConditionalHandle any);
-// the six batched rebuild kernels over the work list
+// the seven batched rebuild kernels over the work list
 cudaError_t launch_rebuild_batch(cudaStream_t s, const RebuildBatch& rb, int nrep);
 void free_rebuild_batch(RebuildBatch* rb);
-constexpr long long kRebuildBatchKernels = 6;
+// kernels of one list rebuild: k_bin, k_scan_tiles, k_scan_add, k_scatter,
+// k_sort_cells, k_pack, k_list
+constexpr long long kRebuildKernels = 7;
 
 // MD steps take the segmented drift + bonded kernel and k_sum
 inline bool step_segments(const relres_ctx* c) { return c->seg_ok && c->use_seg; }
