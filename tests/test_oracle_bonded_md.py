@@ -9,7 +9,8 @@
   2 K_t^2 / N_f), which also pins the Box-Muller normal and the
   Marsaglia-Tsang chi-squared draws it is made of.
 * Velocity Verlet: bounded NVE energy error that shrinks ~4x when dt halves
-  (second order), and no drift of the total momentum.
+  (second order), and no drift of the total momentum; 1000 steps of 1 fs on
+  the propane-like configuration with neither energy drift nor momentum.
 """
 import math
 
@@ -151,3 +152,23 @@ def test_nve_energy_error_is_second_order():
     assert 2.5 < ratio < 6.0, ratio
     p = (v1 * masses[:, None]).sum(0)
     assert np.abs(p).max() < 1e-9
+
+
+def test_nve_1000_steps_on_the_propane_configuration():
+    """The propane-like configuration (216 molecules, FP64) for 1000 NVE steps
+    of 1 fs: after the lattice start has relaxed (100 fs), the total energy
+    neither drifts nor fluctuates by more than 2e-3 of the mean kinetic
+    energy, and the total momentum stays zero."""
+    s = _propane_small()
+    table = O.table_for(s)
+    p, v, th = O.md(s.pos, s.vel, s.box, s.masses, s.types, table, s.n_types, s.excl, s.topo, 1000, 1.0,
+                    n_threads=0)
+    etot = th.sum(1)
+    ke = th[:, 2].mean()
+    tail = etot[100:]
+    drift = abs(tail[-1] - tail[0]) / ke
+    fluct = tail.std() / ke
+    print(f"oracle NVE 1000 x 1 fs: drift {drift:.2e}, fluctuation {fluct:.2e} of <KE>")
+    assert drift < 2e-3 and fluct < 2e-3, (drift, fluct)
+    mom = (v * s.masses[:, None]).sum(0)
+    assert np.abs(mom).max() < 1e-8
