@@ -179,6 +179,9 @@ typedef struct relres_stats {
   int step_segments;             /* 1: MD steps evaluate bonded terms per segment of whole molecules
                                     inside the drift kernel; 0: separate bonded-term kernel */
   int force_acc;                 /* relres_accumulation of the FP32 pair kernels */
+  int n_segments;                /* segments of whole molecules (0: no segmentation) */
+  int n_segment_protos;          /* distinct segments: the others read the term records of an
+                                    identical earlier one, shifted to their own atoms */
 } relres_stats;
 
 /* Kernel classes of relres_get_timings. */

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -501,9 +502,45 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
       const int b0 = first_ge(hb, t->n_bonds, 0, a0), b1 = first_ge(hb, t->n_bonds, 0, a1);
       const int g0 = first_ge(ha, t->n_angles, 1, a0), g1 = first_ge(ha, t->n_angles, 1, a1);
       const int d0 = first_ge(hd, t->n_dihedrals, 2, a0), d1 = first_ge(hd, t->n_dihedrals, 2, a1);
-      seg.insert(seg.end(), {a0, a1, b0, b1, g0, g1, d0, d1});
+      seg.insert(seg.end(), {a0, a1, b0, b1, g0, g1, d0, d1, a0});
       seg_slots = std::max(seg_slots, 2 * (b1 - b0) + 3 * (g1 - g0) + 4 * (d1 - d0));
       a0 = a1;
+    }
+    // Prototypes: a segment whose term records and incident-term lists, taken
+    // relative to its first atom and first term of each kind, equal those of
+    // an earlier segment reads that segment's records instead of its own (the
+    // same terms in the same order, so the same arithmetic): in a liquid of
+    // identical molecules every full segment shares one prototype, whose
+    // records stay in L1/L2.
+    if (seg_ok) {
+      std::map<std::vector<int>, int> first;  // normalised segment -> its first segment
+      std::vector<int> key;
+      for (size_t q = 0; q * kSegRec < seg.size(); ++q) {
+        int* r = &seg[q * kSegRec];
+        const int s0 = r[0], s1 = r[1], rb0 = r[2], rb1 = r[3], rg0 = r[4], rg1 = r[5], rd0 = r[6], rd1 = r[7];
+        key.assign({s1 - s0, rb1 - rb0, rg1 - rg0, rd1 - rd0});
+        for (int k = rb0; k < rb1; ++k) key.insert(key.end(), {hb[k].x - s0, hb[k].y - s0, hb[k].z});
+        for (int k = rg0; k < rg1; ++k) key.insert(key.end(), {ha[k].x - s0, ha[k].y - s0, ha[k].z - s0, ha[k].w});
+        for (int k = rd0; k < rd1; ++k)
+          key.insert(key.end(), {hd[k].x - s0, hd[k].y - s0, hd[k].z - s0, hd[k].w - s0, hdt[k]});
+        for (int i = s0; i < s1; ++i) {
+          key.push_back(ioff[i + 1] - ioff[i]);
+          for (int m = ioff[i]; m < ioff[i + 1]; ++m) {
+            const int item = iall[m], kind = (item >> 30) & 3, term = item & 0x0fffffff;
+            const int rel = term - (kind == 0 ? rb0 : (kind == 1 ? rg0 : rd0));
+            key.push_back((item & ~0x0fffffff) ^ rel);
+          }
+        }
+        const auto it = first.find(key);
+        if (it == first.end()) {
+          first.emplace(key, int(q));
+          continue;
+        }
+        const int* p0 = &seg[size_t(it->second) * kSegRec];
+        for (int w = 2; w < 8; ++w) r[w] = p0[w];
+        r[8] = p0[0];
+      }
+      c->n_seg_proto = int(first.size());
     }
     // shared memory of the segment kernels: term slots (float4 or 3 doubles)
     // plus the segment's positions in the drift kernel
@@ -617,7 +654,7 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(cudaMemcpy(c->d_inc_off, ioff.data(), sizeof(int) * ioff.size(), cudaMemcpyHostToDevice));
   if (!iall.empty()) CK(cudaMemcpy(c->d_inc, iall.data(), sizeof(int) * iall.size(), cudaMemcpyHostToDevice));
   c->seg_ok = seg_ok && !seg.empty();
-  c->n_seg = int(seg.size() / 8);
+  c->n_seg = int(seg.size() / kSegRec);
   c->seg_slots = std::max(1, seg_slots);
   if (c->seg_ok) {
     CK(dalloc(&c->d_seg, seg.size()));
@@ -1755,6 +1792,8 @@ relres_status relres_get_stats(relres_ctx* c, relres_stats* o) {
   o->n_launches = c->n_launches;
   o->prune_delta = c->prune_on ? c->prune_delta : 0.0;
   o->step_segments = step_segments(c) ? 1 : 0;
+  o->n_segments = c->seg_ok ? c->n_seg : 0;
+  o->n_segment_protos = c->seg_ok ? c->n_seg_proto : 0;
   o->force_acc = c->force_acc;
   o->n_prunes = (long long)c->h_state->n_prunes;
   if (c->h_state->n_prunes > 0) {

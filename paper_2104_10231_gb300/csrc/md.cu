@@ -176,6 +176,12 @@ struct SPos {
   int a0;
   __device__ __forceinline__ unsigned long long operator()(int i, int q) const { return s[3 * (i - a0) + q]; }
 };
+// global positions of atoms named by a prototype's records: atom i + off
+struct GPosOff {
+  const unsigned long long* x;
+  int off;
+  __device__ __forceinline__ unsigned long long operator()(int i, int q) const { return x[3 * (i + off) + q]; }
+};
 
 // exact 64-bit fixed-point difference a - b, scaled to Angstrom (float-float)
 __device__ __forceinline__ ff ff_fixed_diff(unsigned long long a, unsigned long long b, ff scale) {
@@ -527,7 +533,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs<R> a) {
 
 template <typename R>
 struct SegArgs {
-  const int* seg;  // [n_seg][8]: atoms [a0, a1), bonds [b0, b1), angles, dihedrals
+  const int* seg;  // [n_seg][kSegRec]: atoms [a0, a1), the prototype's term ranges, its first atom
   BondedArgs B;
   const unsigned long long* xfx;
   Sc3<R> sc;
@@ -554,32 +560,34 @@ template <typename R, bool EV>
 __global__ void __launch_bounds__(kThreads) k_finish_seg(SegArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceT<R>* slot = reinterpret_cast<ForceT<R>*>(smem_raw);
-  const int* g = a.seg + 8 * blockIdx.x;
-  const int a0 = g[0], a1 = g[1], b0 = g[2], b1 = g[3], g0 = g[4], g1 = g[5], d0 = g[6], d1 = g[7];
+  const int* g = a.seg + kSegRec * blockIdx.x;
+  const int a0 = g[0], a1 = g[1], b0 = g[2], b1 = g[3], g0 = g[4], g1 = g[5], d0 = g[6], d1 = g[7], base = g[8];
   const int nb = b1 - b0, na = g1 - g0, nd = d1 - d0;
   const int base_a = 2 * nb, base_d = base_a + 3 * na;
   const Sc3<R> sc = a.sc;
+  // the terms are the prototype's (atoms from `base`): shifted onto this segment
+  const GPosOff xg{a.xfx, a0 - base};
   R e = R(0);
   for (int q = threadIdx.x; q < nb + na + nd; q += blockDim.x) {
     if (q < nb) {
       R f[2][3];
       if constexpr (std::is_same<R, float>::value)
-        e += bond_forces_ff(a.B, GPos{a.xfx}, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, a.B.bonds[b0 + q], f);
+        e += bond_forces_ff(a.B, xg, ff{a.q0h, a.q0l}, ff{a.q1h, a.q1l}, ff{a.q2h, a.q2l}, a.B.bonds[b0 + q], f);
       else
-        e += bond_forces<R>(a.B, GPos{a.xfx}, sc, a.B.bonds[b0 + q], f);
+        e += bond_forces<R>(a.B, xg, sc, a.B.bonds[b0 + q], f);
       save_slots<2, R>(slot, 2 * size_t(q), f);
     } else if (q < nb + na) {
       const int u = q - nb;
       R f[3][3];
       if constexpr (std::is_same<R, float>::value)
-        e += angle_forces_f32(a.B, GPos{a.xfx}, sc, a.B.angles[g0 + u], f);
+        e += angle_forces_f32(a.B, xg, sc, a.B.angles[g0 + u], f);
       else
-        e += angle_forces<R>(a.B, GPos{a.xfx}, sc, a.B.angles[g0 + u], f);
+        e += angle_forces<R>(a.B, xg, sc, a.B.angles[g0 + u], f);
       save_slots<3, R>(slot, base_a + 3 * size_t(u), f);
     } else {
       const int u = q - nb - na;
       R f[4][3];
-      e += dihedral_forces<R>(a.B, GPos{a.xfx}, sc, d0 + u, f);
+      e += dihedral_forces<R>(a.B, xg, sc, d0 + u, f);
       save_slots<4, R>(slot, base_d + 4 * size_t(u), f);
     }
   }
@@ -604,8 +612,9 @@ __global__ void __launch_bounds__(kThreads) k_finish_seg(SegArgs<R> a) {
       f[1] += h[1];
       f[2] += h[2];
     }
-    const int k1 = a.inc_off[i + 1];
-    for (int k = a.inc_off[i]; k < k1; ++k) {
+    const int ip = base + threadIdx.x;  // the prototype's atom: its incident terms
+    const int k1 = a.inc_off[ip + 1];
+    for (int k = a.inc_off[ip]; k < k1; ++k) {
       const int item = a.inc[k];
       const int kind = (item >> 30) & 3, role = (item >> 28) & 3, term = item & 0x0fffffff;
       const int s = kind == 0 ? 2 * (term - b0) + role
@@ -756,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) k_drift(DriftArgs<R> a) {
 template <typename R>
 struct DriftSegArgs {
   DriftArgs<R> d;
-  const int* seg;  // [n_seg][8]: atoms [a0, a1), bonds [b0, b1), angles, dihedrals
+  const int* seg;  // [n_seg][kSegRec]: atoms [a0, a1), the prototype's term ranges, its first atom
   BondedArgs B;
   Sc3<R> sc;
   float q0h, q0l, q1h, q1l, q2h, q2l;
@@ -772,17 +781,18 @@ __device__ __forceinline__ void drift_seg_block(const DriftSegArgs<R>& a, int bi
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* sx = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSegAtoms][3]
   ForceT<R>* slot = reinterpret_cast<ForceT<R>*>(smem_raw + sizeof(unsigned long long) * 3 * kSegAtoms);
-  const int* g = a.seg + 8 * bid;
-  const int a0 = g[0], a1 = g[1], b0 = g[2], b1 = g[3], g0 = g[4], g1 = g[5], d0 = g[6], d1 = g[7];
+  const int* g = a.seg + kSegRec * bid;
+  const int a0 = g[0], a1 = g[1], b0 = g[2], b1 = g[3], g0 = g[4], g1 = g[5], d0 = g[6], d1 = g[7], base = g[8];
   const int nb = b1 - b0, na = g1 - g0, nd = d1 - d0;
   const int base_a = 2 * nb, base_d = base_a + 3 * na;
   const int i = a0 + threadIdx.x;
+  const int ip = base + threadIdx.x;  // the prototype's atom (its incident terms)
   // loads that do not depend on the drift, issued before it: the records of
   // this thread's first two bond/angle terms and its atom's incident-term range
   const int q0 = threadIdx.x, q1 = threadIdx.x + kSegAtoms;
   const int4 rec0 = q0 < nb ? a.B.bonds[b0 + q0] : (q0 < nb + na ? a.B.angles[g0 + q0 - nb] : make_int4(0, 0, 0, 0));
   const int4 rec1 = q1 < nb ? a.B.bonds[b0 + q1] : (q1 < nb + na ? a.B.angles[g0 + q1 - nb] : make_int4(0, 0, 0, 0));
-  const int e0 = i < a1 ? a.inc_off[i] : 0, e1 = i < a1 ? a.inc_off[i + 1] : 0;
+  const int e0 = i < a1 ? a.inc_off[ip] : 0, e1 = i < a1 ? a.inc_off[ip + 1] : 0;
   if (bid == 0 && threadIdx.x == 0)
     a.d.st->ev = a.d.thermo_every > 0 && ((a.d.st->local_step + 1) % a.d.thermo_every) == 0;
   bool rebuild = false, reprune = false;
@@ -794,8 +804,9 @@ __device__ __forceinline__ void drift_seg_block(const DriftSegArgs<R>& a, int bi
   }
   if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(&a.d.st->flags, F_REBUILD);
   if (__syncthreads_or(reprune) && threadIdx.x == 0) atomicOr(&a.d.st->flags, F_PRUNE);
-  // bonded terms of the segment from the new positions
-  const SPos xs{sx, a0};
+  // bonded terms of the segment from the new positions (the records name the
+  // prototype's atoms, base .. base + a1 - a0 - 1: the same local indices)
+  const SPos xs{sx, base};
   const Sc3<R> sc = a.sc;
   R e = R(0);
   for (int q = threadIdx.x, r = 0; q < nb + na + nd; q += blockDim.x, ++r) {

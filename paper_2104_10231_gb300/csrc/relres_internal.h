@@ -113,6 +113,10 @@ constexpr int kBlockSteps = 100;  // steps between host status checks in relres_
 #define RELRES_SEG_ATOMS 256
 #endif
 constexpr int kSegAtoms = RELRES_SEG_ATOMS;  // atoms per segment (one block of the segment kernels)
+// A segment record: atoms [a0, a1), then the bond, angle and dihedral ranges
+// and the first atom of its prototype (a segment whose terms and incident-term
+// lists are those of this one shifted by a0 - base; base = a0 where none).
+constexpr int kSegRec = 9;
 constexpr size_t kSegSmemMax = 48 * 1024;  // shared memory of a segment kernel (term slots + positions)
 constexpr double kPruneDelta = 0.5;   // default margin of the pruned lists (Angstrom)
 #define RELRES_ACC_DEFAULT RELRES_ACC_COMPENSATED
@@ -283,9 +287,10 @@ struct relres_ctx {
   // bonded-term force slots: bonds 2 per term, then angles 3, then dihedrals 4
   void* d_tf = nullptr;
   // segments of whole molecules for the fused bonded + force-sum kernel:
-  // [n_seg][8] = atom range, then the bond, angle and dihedral ranges
+  // [n_seg][kSegRec] = atom range, the prototype's bond, angle and dihedral
+  // ranges, the prototype's first atom
   int* d_seg = nullptr;
-  int n_seg = 0, seg_slots = 0;
+  int n_seg = 0, seg_slots = 0, n_seg_proto = 0;
   bool seg_ok = false;
   bool use_seg = true;  // the fused kernel where segments exist (relres_set_option)
   // reductions: 64-bit fixed-point accumulators (kNAcc), cleared by their reader

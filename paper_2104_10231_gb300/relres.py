@@ -83,7 +83,8 @@ class relres_stats(C.Structure):
                 ("n_builds", C.c_longlong), ("n_steps", C.c_longlong), ("has_cg", C.c_int),
                 ("n_launches", C.c_longlong), ("pair_tpa", C.c_int), ("pair_block", C.c_int),
                 ("prune_delta", C.c_double), ("n_prunes", C.c_longlong), ("mean_fg_pruned", C.c_double),
-                ("mean_cg_pruned", C.c_double), ("step_segments", C.c_int), ("force_acc", C.c_int)]
+                ("mean_cg_pruned", C.c_double), ("step_segments", C.c_int), ("force_acc", C.c_int),
+                ("n_segments", C.c_int), ("n_segment_protos", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
