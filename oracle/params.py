@@ -333,3 +333,78 @@ def chain_to_types(grad_rows, eps, sig, mixing: str = MIX_GEOMETRIC):
                 d_sig[p] += g[p, q, 1] * 0.5 * math.sqrt(sig[q] / sig[p])
                 d_sig[q] += g[p, q, 1] * 0.5 * math.sqrt(sig[p] / sig[q])
     return d_eps, d_sig, g[:, :, 2].copy(), g[:, :, 3].copy()
+
+
+def cg_pair_eq13_vjp(comp_i, comp_j, eps, sig, g_eps_cg: float, g_sig_cg: float,
+                     rule: str = MIX_GEOMETRIC):
+    """Vector-Jacobian product of Eq. 13 for one group pair: the derivatives of
+    g_eps_cg * eps^CG + g_sig_cg * sig^CG with respect to the per-type FG
+    parameters (eps[t], sig[t]), through the mixing rule.
+
+    With A_k = sum_{mu nu} n_mu n_nu eps_{mu nu} sig_{mu nu}^k (Eq. 13),
+    eps^CG = A6^2 / A12 and sig^CG = (A12 / A6)^(1/6), so
+      d eps^CG = (2 A6 / A12) dA6 - (A6^2 / A12^2) dA12,
+      d sig^CG = sig^CG / 6 (dA12 / A12 - dA6 / A6),
+      dA_k = sum n_mu n_nu (sig_{mu nu}^k d eps_{mu nu} + k eps_{mu nu} sig_{mu nu}^(k-1) d sig_{mu nu}),
+    and eps_{mu nu} = sqrt(eps_mu eps_nu), sig_{mu nu} = (sig_mu + sig_nu) / 2 or
+    sqrt(sig_mu sig_nu).  A pair with eps_mu = 0 or eps_nu = 0 contributes no eps
+    derivative (the convention of ``chain_to_types``).  Zero CG parameters
+    (A6 or A12 not positive) depend on nothing.  Returns (d_eps[nt], d_sig[nt])."""
+    eps = np.asarray(eps, dtype=np.float64)
+    sig = np.asarray(sig, dtype=np.float64)
+    nt = len(eps)
+    d_eps = np.zeros(nt)
+    d_sig = np.zeros(nt)
+    E, S = mix_fg(eps, sig, rule)
+    A6 = 0.0
+    A12 = 0.0
+    for mu in range(nt):
+        for nu in range(nt):
+            mult = comp_i[mu] * comp_j[nu]
+            if mult == 0:
+                continue
+            A6 += mult * E[mu, nu] * S[mu, nu] ** 6
+            A12 += mult * E[mu, nu] * S[mu, nu] ** 12
+    if A6 <= 0.0 or A12 <= 0.0:
+        return d_eps, d_sig
+    sig_cg = (A12 / A6) ** (1.0 / 6.0)
+    gA6 = g_eps_cg * 2.0 * A6 / A12 - g_sig_cg * sig_cg / (6.0 * A6)
+    gA12 = -g_eps_cg * A6 * A6 / (A12 * A12) + g_sig_cg * sig_cg / (6.0 * A12)
+    for mu in range(nt):
+        for nu in range(nt):
+            mult = comp_i[mu] * comp_j[nu]
+            if mult == 0:
+                continue
+            e, s = E[mu, nu], S[mu, nu]
+            g_e = mult * (gA6 * s ** 6 + gA12 * s ** 12)
+            g_s = mult * e * (gA6 * 6.0 * s ** 5 + gA12 * 12.0 * s ** 11)
+            if eps[mu] > 0.0 and eps[nu] > 0.0:
+                d_eps[mu] += g_e * 0.5 * math.sqrt(eps[nu] / eps[mu])
+                d_eps[nu] += g_e * 0.5 * math.sqrt(eps[mu] / eps[nu])
+            if rule == MIX_LB:
+                d_sig[mu] += 0.5 * g_s
+                d_sig[nu] += 0.5 * g_s
+            else:
+                d_sig[mu] += g_s * 0.5 * math.sqrt(sig[nu] / sig[mu])
+                d_sig[nu] += g_s * 0.5 * math.sqrt(sig[mu] / sig[nu])
+    return d_eps, d_sig
+
+
+def chain_cg_eq13(d_eps, d_sig, d_eps_cg, d_sig_cg, eps, sig, is_hybrid, group_comp,
+                  rule: str = MIX_GEOMETRIC):
+    """Total per-type FG gradients when the CG parameters of every hybrid type
+    pair follow Eq. 13 from the FG ones: the direct FG gradients (d_eps, d_sig,
+    e.g. from ``chain_to_types``) plus, for every record (a, b) with both types
+    hybrid (Eq. 14), ``cg_pair_eq13_vjp`` of its CG gradients
+    (d_eps_cg[a, b], d_sig_cg[a, b]) with the compositions of the two groups."""
+    out_e = np.array(d_eps, dtype=np.float64, copy=True)
+    out_s = np.array(d_sig, dtype=np.float64, copy=True)
+    nt = len(eps)
+    for a in range(nt):
+        for b in range(nt):
+            if not (is_hybrid[a] and is_hybrid[b]):
+                continue
+            ge, gs = cg_pair_eq13_vjp(group_comp[a], group_comp[b], eps, sig, d_eps_cg[a][b], d_sig_cg[a][b], rule)
+            out_e += ge
+            out_s += gs
+    return out_e, out_s

@@ -185,3 +185,75 @@ def test_energy_gradient_geometric_mixing():
     an = _grads(s, eps, sig, ecg, scg, 1.0, None)
     fd = _fd_params(lambda *a: _energy(s, *a)[0], eps, sig, ecg, scg)
     _check_against_fd(an, fd, 2e-6)
+
+
+@pytest.mark.parametrize("rule", [P.MIX_LB, P.MIX_GEOMETRIC])
+def test_eq13_vector_jacobian_product_matches_finite_differences(rule):
+    # d(gE eps^CG + gS sig^CG)/d(eps_t, sig_t) of every hybrid group pair of
+    # three systems (one, one and two hybrid types) against Richardson
+    # differences of Eq. 13 through the mixing rule
+    rng = np.random.default_rng(4)
+    for s in (S.neopentane(n_mol=250, seed=21), S.propane(), S.block_copolymer(n_chain=4)):
+        eps, sig = s.eps_fg.astype(float), s.sig_fg.astype(float)
+        nt = len(eps)
+        for a in range(nt):
+            for b in range(nt):
+                if not (s.is_hybrid[a] and s.is_hybrid[b]):
+                    continue
+                ci, cj = s.group_comp[a], s.group_comp[b]
+                g_e, g_s = rng.normal(), rng.normal()
+                d_eps, d_sig = P.cg_pair_eq13_vjp(ci, cj, eps, sig, g_e, g_s, rule)
+
+                def f(e, sg):
+                    E, Sm = P.mix_fg(e, sg, rule)
+                    ec, sc = P.cg_pair_eq13(ci, cj, E, Sm)
+                    return g_e * ec + g_s * sc
+
+                for t in range(nt):
+                    for k, arr, d in ((0, eps, d_eps), (1, sig, d_sig)):
+                        h = 1e-4 * arr[t]
+
+                        def central(step):
+                            up, dn = arr.copy(), arr.copy()
+                            up[t] += step
+                            dn[t] -= step
+                            if k == 0:
+                                return (f(up, sig) - f(dn, sig)) / (2 * step)
+                            return (f(eps, up) - f(eps, dn)) / (2 * step)
+
+                        fd = (4.0 * central(h) - central(2 * h)) / 3.0
+                        assert abs(d[t] - fd) <= 1e-8 * abs(fd) + 1e-12, (s.name, rule, a, b, k, t, d[t], fd)
+
+
+def test_energy_gradient_through_eq13_matches_finite_differences():
+    # CG parameters that follow Eq. 13 from the FG ones: the chained gradient
+    # (direct FG part + Eq. 13 vector-Jacobian products of the CG part)
+    # against differences of the energy with the CG table recomputed at every
+    # displaced FG parameter
+    s = _system()
+    eps, sig = s.eps_fg.astype(float), s.sig_fg.astype(float)
+    ecg, scg = _cg(s)
+    d_eps, d_sig, d_ecg, d_scg = _grads(s, eps, sig, ecg, scg, 1.0, None)
+    t_eps, t_sig = P.chain_cg_eq13(d_eps, d_sig, d_ecg, d_scg, eps, sig, s.is_hybrid, s.group_comp, s.mixing)
+
+    def energy(e, sg):
+        ec, sc = P.cg_table_eq13(e, sg, s.is_hybrid, s.group_comp, s.mixing)
+        return _energy(s, e, sg, ec, sc)[0]
+
+    scale = max(np.abs(t_eps).max(), np.abs(t_sig).max())
+    for k, arr, an in ((0, eps, t_eps), (1, sig, t_sig)):
+        for t in range(len(arr)):
+            h = 1e-4 * arr[t]
+
+            def central(step):
+                up, dn = arr.copy(), arr.copy()
+                up[t] += step
+                dn[t] -= step
+                if k == 0:
+                    return (energy(up, sig) - energy(dn, sig)) / (2 * step)
+                return (energy(eps, up) - energy(eps, dn)) / (2 * step)
+
+            fd = (4.0 * central(h) - central(2 * h)) / 3.0
+            assert abs(an[t] - fd) <= 2e-6 * abs(fd) + 1e-7 * scale, (k, t, an[t], fd)
+    # the CG path matters here: the chained gradient differs from the direct one
+    assert np.abs(t_eps - d_eps).max() > 1e-3 * np.abs(t_eps).max()
