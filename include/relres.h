@@ -218,6 +218,29 @@ relres_status relres_cg_params(int n_types, const double* eps_fg, const double* 
                                double* eps_cg, double* sig_cg);
 
 /*
+ * Host-only: the chain rule through Eq. 13 when the CG parameters follow the
+ * FG ones (p->group_comp gives the group compositions; the Eq. 13 CG
+ * parameters of every hybrid type pair a, b are functions of p->eps_fg,
+ * p->sig_fg and p->mixing).  Given the gradients of some scalar with respect
+ * to the CG parameters of every type pair, g_eps_cg, g_sig_cg
+ * [n_types*n_types] row-major (as relres_backward returns them), ADDS their
+ * contribution to the gradients with respect to the per-type FG parameters,
+ * g_eps_fg, g_sig_fg [n_types] (which the caller holds, e.g. initialised with
+ * relres_backward's direct FG gradients):
+ *   g_eps_fg[t] += sum_{a,b hybrid} g_eps_cg[ab] d eps^CG_ab / d eps_t
+ *                                  + g_sig_cg[ab] d sig^CG_ab / d eps_t,
+ * and likewise for sig_t.  Entries of pairs with an ordinary type are
+ * ignored (Eq. 14: no CG term).  The eps derivative of a mixed pair
+ * eps_{mu nu} = sqrt(eps_mu eps_nu) is taken as zero where eps_mu or eps_nu
+ * is zero; Eq. 13 parameters that come out zero contribute nothing.
+ * p->eps_cg must be NULL (the parameters follow Eq. 13).  Errors:
+ * RELRES_ERR_ARG (invalid p as relres_prepare_table, NULL arrays, no
+ * group_comp, explicit eps_cg, a non-finite gradient).
+ */
+relres_status relres_chain_cg_grads(const relres_params* p, const double* g_eps_cg, const double* g_sig_cg,
+                                    double* g_eps_fg, double* g_sig_fg);
+
+/*
  * Create a context on the current CUDA device for the lj/relres pair style of
  * Section 2.5: its parameters (FG eps and sigma per type, the hybrid flag, CG
  * eps and sigma per hybrid pair or Eq. 13 from group compositions) and the

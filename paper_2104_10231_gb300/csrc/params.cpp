@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 namespace relres {
 
@@ -298,6 +299,79 @@ extern "C" relres_status relres_prepare_table(const relres_params* p, double* ou
     o[24] = r.gam_sp;
     o[25] = r.gam_sm;
   }
+  return RELRES_OK;
+}
+
+namespace relres {
+namespace {
+
+// Vector-Jacobian product of Eq. 13 for one group pair: adds to g_eps[t],
+// g_sig[t] the derivatives of ge * eps^CG + gs * sig^CG with respect to the
+// per-type FG eps_t, sig_t.  With A_k = sum n_mu n_nu eps_{mu nu} sig_{mu nu}^k,
+// eps^CG = A6^2 / A12 and sig^CG = (A12 / A6)^(1/6):
+//   d eps^CG = (2 A6 / A12) dA6 - (A6 / A12)^2 dA12,
+//   d sig^CG = sig^CG / 6 (dA12 / A12 - dA6 / A6),
+// and each mixed pair passes its share back through eps_{mu nu} =
+// sqrt(eps_mu eps_nu) (no eps derivative where either is 0) and the sigma rule.
+// Zero CG parameters (A6 or A12 not positive) depend on nothing.
+void sum_rule_vjp(int nt, const double* eps, const double* sig, int mixing, const int* ci, const int* cj,
+                  double ge, double gs, double* g_eps, double* g_sig) {
+  double a6 = 0.0, a12 = 0.0;
+  for (int m = 0; m < nt; ++m)
+    for (int n = 0; n < nt; ++n) {
+      const double mult = double(ci[m]) * double(cj[n]);
+      if (mult == 0.0) continue;
+      double e, s;
+      mix_pair(mixing, eps[m], sig[m], eps[n], sig[n], &e, &s);
+      const double s6 = s * s * s * s * s * s;
+      a6 += mult * e * s6;
+      a12 += mult * e * s6 * s6;
+    }
+  if (!(a6 > 0.0) || !(a12 > 0.0)) return;
+  const double sig_cg = std::pow(a12 / a6, 1.0 / 6.0);
+  const double g6 = ge * 2.0 * a6 / a12 - gs * sig_cg / (6.0 * a6);
+  const double g12 = -ge * (a6 / a12) * (a6 / a12) + gs * sig_cg / (6.0 * a12);
+  for (int m = 0; m < nt; ++m)
+    for (int n = 0; n < nt; ++n) {
+      const double mult = double(ci[m]) * double(cj[n]);
+      if (mult == 0.0) continue;
+      double e, s;
+      mix_pair(mixing, eps[m], sig[m], eps[n], sig[n], &e, &s);
+      const double s5 = s * s * s * s * s, s6 = s5 * s, s11 = s6 * s5;
+      const double de = mult * (g6 * s6 + g12 * s6 * s6);               // d / d eps_{mu nu}
+      const double ds = mult * e * (6.0 * g6 * s5 + 12.0 * g12 * s11);  // d / d sig_{mu nu}
+      if (eps[m] > 0.0 && eps[n] > 0.0) {
+        g_eps[m] += de * 0.5 * std::sqrt(eps[n] / eps[m]);
+        g_eps[n] += de * 0.5 * std::sqrt(eps[m] / eps[n]);
+      }
+      if (mixing == RELRES_MIX_LB) {
+        g_sig[m] += 0.5 * ds;
+        g_sig[n] += 0.5 * ds;
+      } else {
+        g_sig[m] += ds * 0.5 * std::sqrt(sig[n] / sig[m]);
+        g_sig[n] += ds * 0.5 * std::sqrt(sig[m] / sig[n]);
+      }
+    }
+}
+
+}  // namespace
+}  // namespace relres
+
+extern "C" relres_status relres_chain_cg_grads(const relres_params* p, const double* g_eps_cg,
+                                               const double* g_sig_cg, double* g_eps_fg, double* g_sig_fg) {
+  using namespace relres;
+  if (!p || !g_eps_cg || !g_sig_cg || !g_eps_fg || !g_sig_fg || !p->group_comp || p->eps_cg) return RELRES_ERR_ARG;
+  std::vector<PairRecord> recs;
+  if (!build_pair_records(p, &recs).empty()) return RELRES_ERR_ARG;
+  const int nt = p->n_types;
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      if (!(p->is_hybrid[a] && p->is_hybrid[b])) continue;
+      const double ge = g_eps_cg[a * nt + b], gs = g_sig_cg[a * nt + b];
+      if (!std::isfinite(ge) || !std::isfinite(gs)) return RELRES_ERR_ARG;
+      sum_rule_vjp(nt, p->eps_fg, p->sig_fg, p->mixing, p->group_comp + a * nt, p->group_comp + b * nt, ge, gs,
+                   g_eps_fg, g_sig_fg);
+    }
   return RELRES_OK;
 }
 

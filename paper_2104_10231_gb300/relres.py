@@ -31,7 +31,7 @@ RELRES_MAX_TYPES = 8
 RELRES_THERMO_COLS = 10
 RELRES_PAIR_FIELDS = 26
 
-EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_create", "relres_set_topology",
+EXPORTED = ["relres_prepare_table", "relres_cg_params", "relres_chain_cg_grads", "relres_create", "relres_set_topology",
             "relres_build_neighbors", "relres_compute", "relres_step", "relres_set_step_counter",
             "relres_get_stats", "relres_set_timing", "relres_get_timings", "relres_last_error",
             "relres_destroy", "relres_pair_forces_static", "relres_set_graphs", "relres_set_params",
@@ -114,6 +114,7 @@ def load():
     vp = C.c_void_p
     L.relres_prepare_table.argtypes = [C.POINTER(relres_params), _dp, C.c_int]
     L.relres_cg_params.argtypes = [C.c_int, _dp, _dp, C.c_int, _ip, _ip, _dp, _dp]
+    L.relres_chain_cg_grads.argtypes = [C.POINTER(relres_params), _dp, _dp, _dp, _dp]
     L.relres_create.argtypes = [C.POINTER(vp), C.POINTER(relres_params), vp]
     L.relres_set_topology.argtypes = [vp, C.POINTER(relres_topology)]
     L.relres_build_neighbors.argtypes = [vp, vp, _dp]
@@ -299,6 +300,23 @@ def relres_cg_params(eps_fg, sig_fg, mixing, comp_i, comp_j):
     _check(load().relres_cg_params(len(eps_fg), keep.d(eps_fg), keep.d(sig_fg), int(mixing),
                                    keep.i(comp_i), keep.i(comp_j), C.byref(e), C.byref(s)))
     return e.value, s.value
+
+
+def relres_chain_cg_grads(params, g_eps_cg, g_sig_cg, g_eps_fg, g_sig_fg):
+    """Chain rule through Eq. 13 (host-only): returns (g_eps_fg, g_sig_fg)
+    [n_types] plus the contributions of g_eps_cg, g_sig_cg [n_types, n_types]
+    when the CG parameters follow the FG ones (params: group_comp, no
+    explicit eps_cg)."""
+    ge = np.array(g_eps_fg, dtype=np.float64, copy=True).reshape(-1)
+    gs = np.array(g_sig_fg, dtype=np.float64, copy=True).reshape(-1)
+    ec = np.ascontiguousarray(g_eps_cg, dtype=np.float64).reshape(-1)
+    sc = np.ascontiguousarray(g_sig_cg, dtype=np.float64).reshape(-1)
+    nt = params.n_types
+    if ge.size != nt or gs.size != nt or ec.size != nt * nt or sc.size != nt * nt:
+        raise ValueError("relres_chain_cg_grads: FG gradients need n_types entries, CG ones n_types^2")
+    _check(load().relres_chain_cg_grads(C.byref(params), ec.ctypes.data_as(_dp), sc.ctypes.data_as(_dp),
+                                        ge.ctypes.data_as(_dp), gs.ctypes.data_as(_dp)))
+    return ge, gs
 
 
 def relres_create(params, stream=None):

@@ -177,3 +177,83 @@ def test_fp64_gradient_matches_central_differences_of_the_gpu_forward(torch):
         print(f"FD check param {k}{idx}: analytic {an:.10e} fd {fd:.10e}")
         assert an == pytest.approx(fd, rel=1e-6)
     m.close()
+
+
+def _compare_eq13(torch, s, precision, tol_p, tol_x):
+    # CG parameters that follow Eq. 13: the leaves are the FG parameters only
+    from paper_2104_10231_gb300 import diff
+
+    m = diff.RelResPair.for_system(s, precision=precision)
+    pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda", requires_grad=True)
+    m.bind(pos.detach(), s.box)
+    ec, sc = P.cg_table_eq13(s.eps_fg, s.sig_fg, s.is_hybrid, s.group_comp, s.mixing)
+    tab_ref = P.pair_table(s.eps_fg * 1.1, s.sig_fg * 0.98, s.is_hybrid, s.radii, s.mixing,
+                           eps_cg=ec * 0.9, sig_cg=sc * 1.02)
+    f_ref, _, _ = O.pair_forces(s.pos, s.box, s.types, tab_ref, s.n_types, s.excl)
+    eps = torch.tensor(s.eps_fg.astype(float), requires_grad=True)
+    sig = torch.tensor(s.sig_fg.astype(float), requires_grad=True)
+    e, f = m(pos, eps, sig)
+    loss = e + ((f - torch.tensor(f_ref, device="cuda")) ** 2).sum()
+    loss.backward()
+    g_forces = 2.0 * (f.detach().cpu().numpy() - f_ref)
+    (d_eps, d_sig, d_ecg, d_scg), dx, _, _ = _oracle_grads(s, ec, sc, s.pos, 1.0, g_forces)
+    t_eps, t_sig = P.chain_cg_eq13(d_eps, d_sig, d_ecg, d_scg, s.eps_fg.astype(float), s.sig_fg.astype(float),
+                                   s.is_hybrid, s.group_comp, s.mixing)
+    errs = {"eps_fg": _rel(eps.grad.numpy(), t_eps), "sig_fg": _rel(sig.grad.numpy(), t_sig),
+            "pos": _rel(pos.grad.cpu().numpy(), dx)}
+    print(f"Eq. 13 chain {s.name} N={s.n_atoms} prec={precision}: " + " ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    assert errs["eps_fg"] <= tol_p and errs["sig_fg"] <= tol_p, errs
+    assert errs["pos"] <= tol_x, errs
+    # the CG path is part of the answer: the direct FG gradient alone is far off
+    assert _rel(d_eps, t_eps) > 10 * tol_p
+    m.close()
+
+
+def test_fp64_gradient_through_eq13_matches_oracle(torch):
+    _compare_eq13(torch, S.neopentane(n_mol=250, seed=21), R.RELRES_PREC_FP64, 1e-9, 1e-9)
+
+
+def test_fp64_gradient_through_eq13_propane(torch):
+    _compare_eq13(torch, S.propane(), R.RELRES_PREC_FP64, 1e-9, 1e-9)
+
+
+def test_fp32_gradient_through_eq13_block_copolymer(torch):
+    # two hybrid types: the A-A, A-B and B-B CG pairs all depend on every FG type
+    _compare_eq13(torch, S.block_copolymer(n_chain=20), R.RELRES_PREC_FP32, 2e-5, 1e-4)
+
+
+def test_fp64_eq13_gradient_matches_central_differences_of_the_gpu_forward(torch):
+    # independent of the oracle: differences of the GPU loss with the CG
+    # parameters re-derived by the library (Eq. 13) at every displaced FG value
+    from paper_2104_10231_gb300 import diff
+
+    s = S.neopentane(n_mol=250, seed=8)
+    m = diff.RelResPair.for_system(s, precision=R.RELRES_PREC_FP64)
+    pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+    m.bind(pos, s.box)
+
+    def loss(eps, sig):
+        e, f = m(pos, torch.tensor(eps), torch.tensor(sig))
+        return float(e) + float((f ** 2).sum()) * 1e-3
+
+    eps = torch.tensor(s.eps_fg.astype(float), requires_grad=True)
+    sig = torch.tensor(s.sig_fg.astype(float), requires_grad=True)
+    e, f = m(pos, eps, sig)
+    (e + (f ** 2).sum() * 1e-3).backward()
+    e0, s0 = s.eps_fg.astype(float), s.sig_fg.astype(float)
+    for k, (arr, grad) in enumerate(((e0, eps.grad.numpy()), (s0, sig.grad.numpy()))):
+        for t in range(len(arr)):
+            h = 1e-4 * arr[t]
+
+            def central(step):
+                up, dn = arr.copy(), arr.copy()
+                up[t] += step
+                dn[t] -= step
+                if k == 0:
+                    return (loss(up, s0) - loss(dn, s0)) / (2 * step)
+                return (loss(e0, up) - loss(e0, dn)) / (2 * step)
+
+            fd = (4.0 * central(h) - central(2 * h)) / 3.0
+            print(f"d/d{'eps' if k == 0 else 'sig'}[{t}]: {grad[t]:.10e} vs {fd:.10e}")
+            assert abs(grad[t] - fd) <= 1e-6 * abs(fd) + 1e-9, (k, t, grad[t], fd)
+    m.close()

@@ -162,3 +162,37 @@ def test_null_handles_and_bad_arguments_fail_before_any_cuda_call(lib):
     assert lib.relres_batch_last_error(None) == b"null batch"
     lib.relres_destroy(None)
     lib.relres_batch_destroy(None)
+
+
+@pytest.mark.parametrize("mixing", [R.RELRES_MIX_LB, R.RELRES_MIX_GEOMETRIC])
+def test_chain_cg_grads_matches_oracle(lib, mixing):
+    # relres_chain_cg_grads (C++) against the oracle's chain through Eq. 13
+    # (pinned by differences of Eq. 13 in test_oracle_grad.py)
+    rule = P.MIX_LB if mixing == R.RELRES_MIX_LB else P.MIX_GEOMETRIC
+    rng = np.random.default_rng(2)
+    for s in (S.neopentane(n_mol=250, seed=21), S.propane(), S.block_copolymer(n_chain=4)):
+        nt = s.n_types
+        gec, gsc = rng.normal(size=(nt, nt)), rng.normal(size=(nt, nt))
+        gef, gsf = rng.normal(size=nt), rng.normal(size=nt)
+        p = R.make_params(s.eps_fg, s.sig_fg, s.is_hybrid, s.radii, s.skin, mixing=mixing, group_comp=s.group_comp)
+        ge, gs = R.relres_chain_cg_grads(p, gec, gsc, gef, gsf)
+        oe, os_ = P.chain_cg_eq13(gef, gsf, gec, gsc, s.eps_fg.astype(float), s.sig_fg.astype(float), s.is_hybrid,
+                                  s.group_comp, rule)
+        assert np.allclose(ge, oe, rtol=1e-13, atol=1e-13 * np.abs(oe).max()), (s.name, ge, oe)
+        assert np.allclose(gs, os_, rtol=1e-13, atol=1e-13 * np.abs(os_).max()), (s.name, gs, os_)
+
+
+def test_chain_cg_grads_rejects_bad_input(lib):
+    s = S.propane()
+    nt = s.n_types
+    g2, g1 = np.ones((nt, nt)), np.zeros(nt)
+    ec, sc = P.cg_table_eq13(s.eps_fg, s.sig_fg, s.is_hybrid, s.group_comp, s.mixing)
+    explicit = R.make_params(s.eps_fg, s.sig_fg, s.is_hybrid, s.radii, s.skin, eps_cg=ec, sig_cg=sc)
+    no_comp = R.make_params(s.eps_fg, s.sig_fg, s.is_hybrid, s.radii, s.skin)
+    ok = R.make_params(s.eps_fg, s.sig_fg, s.is_hybrid, s.radii, s.skin, group_comp=s.group_comp)
+    for p, a in ((explicit, g2), (no_comp, g2), (ok, np.full((nt, nt), np.nan))):
+        with pytest.raises(R.RelresError) as e:
+            R.relres_chain_cg_grads(p, a, g2, g1, g1)
+        assert e.value.status == 1  # RELRES_ERR_ARG
+    with pytest.raises(ValueError):
+        R.relres_chain_cg_grads(ok, g2[:1], g2, g1, g1)
