@@ -581,6 +581,14 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(&c->d_mass, RELRES_MAX_TYPES));
   CK(dalloc(&c->d_excl_off, size_t(n) + 1));
   CK(dalloc(&c->d_excl_idx, std::max<size_t>(1, eidx.size())));
+  dfree(c->d_excl_mask);
+  if (c->excl_window <= kExclMaskHalf) {
+    std::vector<unsigned> em(size_t(n), 1u << kExclMaskHalf);  // the atom itself
+    for (int i = 0; i < n; ++i)
+      for (int m = eoff[i]; m < eoff[i + 1]; ++m) em[i] |= 1u << (eidx[m] - i + kExclMaskHalf);
+    CK(dalloc(&c->d_excl_mask, size_t(n)));
+    CK(cudaMemcpy(c->d_excl_mask, em.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice));
+  }
   CK(dalloc(&c->d_bonds, hb.size()));
   CK(dalloc(&c->d_angles, ha.size()));
   CK(dalloc(&c->d_dihs, hd.size()));
@@ -1862,6 +1870,7 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_type);
   dfree(c->d_excl_off);
   dfree(c->d_excl_idx);
+  dfree(c->d_excl_mask);
   dfree(c->d_bonds);
   dfree(c->d_angles);
   dfree(c->d_dihs);

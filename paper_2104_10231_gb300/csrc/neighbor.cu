@@ -313,6 +313,9 @@ struct ListArgs {
   unsigned long long* total_out;
   unsigned* flags;
   unsigned overflow_bit;
+  // per-atom exclusion masks (bit j - i + kExclMaskHalf), or NULL: then the
+  // exclusion lists are searched (excl_window above kExclMaskHalf)
+  const unsigned* excl_mask;
 };
 
 constexpr int kListThreads = 128;  // 4 warps per cell
@@ -321,19 +324,24 @@ __device__ __forceinline__ float wrap1(float d, float l, float il) { return d - 
 
 // One cell atom (slot s, atom id ai, relative position p) against the staged
 // candidates beg .. end - 1 of the window: 32 candidates per iteration,
-// accepted ones appended at k in window order.  Exclusions: a candidate whose
-// atom id lies within the exclusion window of ai (this includes ai itself) is
-// checked against ai's exclusion list; all others cannot be excluded.
-// Returns the new count.
-template <bool WRAP>
+// accepted ones appended at k in window order.  A lane past `end` reads either
+// a staged candidate of an x-slab beyond the atom's list radius (farther than
+// the list radius by construction of the slab run) or the NaN padding after
+// the window, so the distance test alone rejects it.  Exclusions: with MASK,
+// bit aj - ai + kExclMaskHalf of the atom's mask (its own bit included); else
+// a candidate whose atom id lies within the exclusion window of ai (this
+// includes ai itself) is checked against ai's exclusion list, and all others
+// cannot be excluded.  Returns the new count.
+template <bool WRAP, bool MASK>
 __device__ __forceinline__ int scan_range(const float4* s_pos, const int* s_atom, int beg, int end, int ai,
                                           float px, float py, float pz, float rl2, float lx, float ly,
-                                          float lz, const int (&ex)[8], int e0, int e1, const int* excl_idx,
-                                          int win, int* nbr_s, unsigned stride, int cap, int k) {
+                                          float lz, unsigned emask, const int (&ex)[8], int e0, int e1,
+                                          const int* excl_idx, int win, int* nbr_s, unsigned stride, int cap,
+                                          int k) {
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
   for (int j0 = beg; j0 < end; j0 += 32) {
-    const int j = j0 + lane < end ? j0 + lane : beg;
+    const int j = j0 + lane;
     const float4 q = s_pos[j];
     float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
     if (WRAP) {
@@ -341,9 +349,12 @@ __device__ __forceinline__ int scan_range(const float4* s_pos, const int* s_atom
       dy = wrap1(dy, ly, 1.f / ly);
       dz = wrap1(dz, lz, 1.f / lz);
     }
-    bool acc = j0 + lane < end && dx * dx + dy * dy + dz * dz < rl2;
+    bool acc = dx * dx + dy * dy + dz * dz < rl2;
     const int aj = s_atom[j];
-    if (acc && unsigned(aj - ai + win) <= unsigned(2 * win)) {
+    if (MASK) {
+      const unsigned d = unsigned(aj - ai + kExclMaskHalf);
+      acc = acc && !(d < unsigned(2 * kExclMaskHalf + 1) && ((emask >> d) & 1u));
+    } else if (acc && unsigned(aj - ai + win) <= unsigned(2 * win)) {
       // the first eight excluded partners are in registers (-1 where unused)
       acc = aj != ai;
 #pragma unroll
@@ -377,10 +388,16 @@ constexpr int kStageMax = 3 * kXSplit * 9;  // staged cells: 3 x kXSplit x-slabs
 // are appended in staging order (ballot + prefix count), so the list is
 // deterministic.
 __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg, int ncell_cg, int cb) {
-  __shared__ float4 s_pos[kListWindow];  // x, y, z relative; w = slot index bits
-  __shared__ int s_atom[kListWindow];    // atom id of each staged candidate
+  // x, y, z relative, w = slot index bits; atom ids; 32 NaN entries after the window
+  __shared__ float4 s_pos[kListWindow + 32];
+  __shared__ int s_atom[kListWindow + 32];
   __shared__ int s_cstart[kStageMax], s_coff[kStageMax + 1];
   __shared__ int s_k[kListGroup];
+  // the group's atoms, read once per group: relative position (w = atom id
+  // bits), exclusion mask, run [beg, end) of staged candidates
+  __shared__ float4 s_gp[kListGroup];
+  __shared__ unsigned s_gm[kListGroup];
+  __shared__ int2 s_gr[kListGroup];
   __shared__ int s_max;
   __shared__ unsigned long long s_tot;
   const bool is_cg = cb < ncell_cg;
@@ -403,6 +420,7 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
     unsigned long long* total_out;
     unsigned* flags;
     unsigned overflow_bit;
+    const unsigned* excl_mask;
   } a;
 #define RELRES_PICK(f) a.f = is_cg ? cg.f : fg.f
   RELRES_PICK(nslots);
@@ -422,6 +440,7 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
   RELRES_PICK(total_out);
   RELRES_PICK(flags);
   RELRES_PICK(overflow_bit);
+  RELRES_PICK(excl_mask);
 #undef RELRES_PICK
 #define RELRES_PICKG(f) a.f = is_cg ? cg.g.f : fg.g.f
   RELRES_PICKG(n0);
@@ -495,7 +514,27 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
   unsigned long long blk_tot = 0ull;
   for (int g0 = 0; g0 < ni; g0 += kListGroup) {
     const int ng = min(kListGroup, ni - g0);
-    for (int k = threadIdx.x; k < ng; k += blockDim.x) s_k[k] = 0;
+    for (int k = threadIdx.x; k < ng; k += blockDim.x) {
+      s_k[k] = 0;
+      const int s = i0 + g0 + k;
+      const int4 p = a.pos[s];
+      const int ai = a.perm[s];
+      s_gp[k] = make_float4(dfix32(p.x, ref.x, a.sx), dfix32(p.y, ref.y, a.sy), dfix32(p.z, ref.z, a.sz),
+                            __int_as_float(ai));
+      s_gm[k] = a.excl_mask != nullptr ? a.excl_mask[ai] : 0u;
+      int beg = 0, end = total;
+      if (slabs) {
+        // the atom's x in slab widths from the first staged slab: its own
+        // slab (S .. 2S - 1) plus its place in it
+        const int cx = cell_of(p.x, a.n0);
+        const float ux = float(unsigned(p.x) * unsigned(a.n0)) * 2.3283064365386963e-10f;
+        const float xs = float(cx - S * fx + S) + ux;
+        const int lo = max(0, int(floorf(xs - reach))), hi = min(d0 - 1, int(floorf(xs + reach)));
+        beg = s_coff[lo * slab_cells];
+        end = s_coff[(hi + 1) * slab_cells];
+      }
+      s_gr[k] = make_int2(beg, end);
+    }
     for (int w0 = 0; w0 < total; w0 += kListWindow) {
       const int wn = min(kListWindow, total - w0);
       __syncthreads();
@@ -511,35 +550,34 @@ __device__ __forceinline__ void list_cell(const ListArgs& fg, const ListArgs& cg
                                __int_as_float(t));
         s_atom[k] = a.perm[t];
       }
+      if (threadIdx.x < 32) {  // padding read by the lanes past the end of a run
+        const float nan = __int_as_float(0x7fc00000);
+        s_pos[wn + threadIdx.x] = make_float4(nan, nan, nan, nan);
+        s_atom[wn + threadIdx.x] = -1;
+      }
       __syncthreads();
       for (int il = warp; il < ng; il += blockDim.x >> 5) {
         const int s = i0 + g0 + il;
-        const int4 p = a.pos[s];
-        const float px = dfix32(p.x, ref.x, a.sx), py = dfix32(p.y, ref.y, a.sy), pz = dfix32(p.z, ref.z, a.sz);
-        const int ai = a.perm[s];
-        const int e0 = a.excl_off[ai], e1 = a.excl_off[ai + 1];
+        const float4 gp = s_gp[il];
+        const float px = gp.x, py = gp.y, pz = gp.z;
+        const int ai = __float_as_int(gp.w);
+        const bool mask = a.excl_mask != nullptr;
+        const unsigned emask = s_gm[il];
+        const int e0 = mask ? 0 : a.excl_off[ai], e1 = mask ? 0 : a.excl_off[ai + 1];
         int ex[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) ex[e] = e0 + e < e1 ? a.excl_idx[e0 + e] : -1;
         int* const nbr_s = a.nbr + 4 * size_t(s);
         const unsigned stride = 4u * unsigned(a.nslots);
-        int beg = 0, end = total;
-        if (slabs) {
-          // the atom's x in slab widths from the first staged slab: its own
-          // slab (S .. 2S - 1) plus its place in it
-          const int cx = cell_of(p.x, a.n0);
-          const float ux = float(unsigned(p.x) * unsigned(a.n0)) * 2.3283064365386963e-10f;
-          const float xs = float(cx - S * fx + S) + ux;
-          const int lo = max(0, int(floorf(xs - reach))), hi = min(d0 - 1, int(floorf(xs + reach)));
-          beg = s_coff[lo * slab_cells];
-          end = s_coff[(hi + 1) * slab_cells];
-        }
-        beg = max(beg, w0) - w0;
-        end = min(end, w0 + wn) - w0;
-        const int k = wrap ? scan_range<true>(s_pos, s_atom, beg, end, ai, px, py, pz, a.rl2, lx, ly, lz, ex, e0,
-                                              e1, a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il])
-                           : scan_range<false>(s_pos, s_atom, beg, end, ai, px, py, pz, a.rl2, lx, ly, lz, ex, e0,
-                                               e1, a.excl_idx, a.excl_window, nbr_s, stride, a.cap, s_k[il]);
+        const int2 run = s_gr[il];
+        const int beg = max(run.x, w0) - w0;
+        const int end = min(run.y, w0 + wn) - w0;
+#define RELRES_SCAN(W, M)                                                                                  \
+  scan_range<W, M>(s_pos, s_atom, beg, end, ai, px, py, pz, a.rl2, lx, ly, lz, emask, ex, e0, e1, a.excl_idx, \
+                   a.excl_window, nbr_s, stride, a.cap, s_k[il])
+        const int k = wrap ? (mask ? RELRES_SCAN(true, true) : RELRES_SCAN(true, false))
+                           : (mask ? RELRES_SCAN(false, true) : RELRES_SCAN(false, false));
+#undef RELRES_SCAN
         if (lane == 0) s_k[il] = k;
       }
     }
@@ -1030,7 +1068,7 @@ static ListArgs list_args_fg(relres_ctx* c) {
   const double rf = c->rlist_fg_cut + c->prm.skin;
   return ListArgs{c->n, c->d_pos_fg, c->d_perm_fg, grid_args(c->gfg), s0, s1, s2, float(rf * rf),
                   c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_fg, c->d_nbr_fg, c->d_cnt_fg,
-                  &st->max_fg, &st->tot_fg, &st->flags, F_OVERFLOW_FG};
+                  &st->max_fg, &st->tot_fg, &st->flags, F_OVERFLOW_FG, c->d_excl_mask};
 }
 
 // the CG list's arguments and cells; false (arguments untouched) without a CG list
@@ -1042,7 +1080,7 @@ static bool list_args_cg(relres_ctx* c, ListArgs* cg, int* ncell_cg) {
   const double rc = c->rlist_cg_cut + c->skin_cg;
   *cg = ListArgs{c->n_h, c->d_pos_cg, c->d_perm_cg, grid_args(c->gcg), s0, s1, s2, float(rc * rc),
                  c->d_excl_off, c->d_excl_idx, c->excl_window, c->cap_cg, c->d_nbr_cg, c->d_cnt_cg,
-                 &st->max_cg, &st->tot_cg, &st->flags, F_OVERFLOW_CG};
+                 &st->max_cg, &st->tot_cg, &st->flags, F_OVERFLOW_CG, c->d_excl_mask};
   *ncell_cg = c->gcg.ncell_full;
   return true;
 }

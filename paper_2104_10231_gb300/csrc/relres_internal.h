@@ -117,6 +117,8 @@ constexpr int kSegAtoms = RELRES_SEG_ATOMS;  // atoms per segment (one block of 
 // and the first atom of its prototype (a segment whose terms and incident-term
 // lists are those of this one shifted by a0 - base; base = a0 where none).
 constexpr int kSegRec = 9;
+// exclusions as a per-atom bit mask over atom-id offsets -15 .. 15
+constexpr int kExclMaskHalf = 15;
 constexpr size_t kSegSmemMax = 48 * 1024;  // shared memory of a segment kernel (term slots + positions)
 constexpr double kPruneDelta = 0.5;   // default margin of the pruned lists (Angstrom)
 #define RELRES_ACC_DEFAULT RELRES_ACC_COMPENSATED
@@ -217,6 +219,9 @@ struct relres_ctx {
   int* d_excl_off = nullptr;
   int excl_window = 0;  // max |i - j| over excluded pairs
   int* d_excl_idx = nullptr;
+  // per atom i, bit (j - i + kExclMaskHalf) set for every excluded j and for
+  // j = i; allocated only when excl_window <= kExclMaskHalf
+  unsigned* d_excl_mask = nullptr;
   int n_bonds = 0, n_angles = 0, n_dih = 0;
   int4* d_bonds = nullptr;      // i, j, type, 0
   int4* d_angles = nullptr;     // i, vertex, k, type
