@@ -963,7 +963,7 @@ static relres_status record_block(relres_ctx* c, const StepParams& sp, double* d
     c->cur_step = done + k;
     // energy steps are known here: the device sets DevState::ev by the same rule
     const bool ev_step = sp.thermo_every > 0 && ((done + k + 1) % sp.thermo_every) == 0;
-    TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel, ev_step));
+    TIMED(RELRES_T_DRIFT, launch_drift(c, sp, d_vel, ev_step, k > 0));
     cudaGraphConditionalHandle hp = 0;
     if (graph) {
       const bool t_ = timed_now(c, RELRES_T_REBUILD);

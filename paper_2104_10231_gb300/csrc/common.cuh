@@ -24,6 +24,15 @@ namespace relres {
 
 constexpr int kThreads = 256;
 
+// Programmatic dependent launch: a kernel launched with the
+// programmatic-stream-serialization attribute may start before the previous
+// kernel of its stream has finished.  grid_dependency_wait() blocks until that
+// kernel has finished and its memory is visible (it returns at once for a
+// kernel launched the ordinary way); grid_dependents_launch() lets the next
+// such kernel start once every block of this grid has called it or exited.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // Positions are periodic 64-bit fixed point: u = frac(x / L) * 2^64.  Integer
 // differences wrap modulo 2^64, which is exactly the minimum image of an
 // orthorhombic box, and the upper 32 bits give the 32-bit form the FP32 pair

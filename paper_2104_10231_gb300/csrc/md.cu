@@ -683,27 +683,44 @@ struct DriftArgs {
   DevState* st;
 };
 
+// The inputs of one atom's drift that the force sum of the step does not
+// write (the drift kernel loads them before waiting for that kernel).
+template <typename R>
+struct DriftIn {
+  int t, sf, sc;
+  VelT<R> v[3];
+  unsigned long long x0[3];
+  int4 ref, ref_p;
+};
+
+template <typename R>
+__device__ __forceinline__ void drift_load(const DriftArgs<R>& a, int i, DriftIn<R>& in) {
+  in.t = a.type[i];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    in.v[q] = a.vel[3 * i + q];
+    in.x0[q] = a.xfx[3 * i + q];
+  }
+  in.sf = a.rank_fg[i];
+  in.sc = a.with_cg ? a.rank_cg[i] : -1;
+  in.ref = a.ref[i];
+  in.ref_p = a.prune ? a.ref_p[i] : make_int4(0, 0, 0, 0);
+}
+
 // One atom of the drift: u <- a u + b c F, x <- x + dt u, the sorted copies
 // of x, and the two displacement triggers.  Returns the new position in x.
 // Every load of the atom is issued before its first store, so that no load
 // waits behind a store to memory the compiler cannot tell apart from it.
 template <typename R>
-__device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, unsigned long long x[3], bool& rebuild,
-                                           bool& reprune) {
-  const int t = a.type[i];
+__device__ __forceinline__ void drift_rest(const DriftArgs<R>& a, int i, const DriftIn<R>& in,
+                                           unsigned long long x[3], bool& rebuild, bool& reprune) {
+  const int t = in.t;
   R f[3];
   load_force(a.f_tot, i, f);
-  VelT<R> v[3];
-  unsigned long long x0[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    v[q] = a.vel[3 * i + q];
-    x0[q] = a.xfx[3 * i + q];
-  }
-  const int sf = a.rank_fg[i];
-  const int sc = a.with_cg ? a.rank_cg[i] : -1;
-  const int4 ref = a.ref[i];
-  const int4 ref_p = a.prune ? a.ref_p[i] : make_int4(0, 0, 0, 0);
+  const VelT<R>* v = in.v;
+  const unsigned long long* x0 = in.x0;
+  const int sf = in.sf, sc = in.sc;
+  const int4 ref = in.ref, ref_p = in.ref_p;
   VelT<R> un[3];
   if constexpr (std::is_same<R, float>::value) {
     // float-float: u <- a u + b c F and the increment u dt 2^64 / L, with no
@@ -738,6 +755,14 @@ __device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, unsigne
   scatter_sorted_at(sf, sc, t, x[0], x[1], x[2], a.pos_fg, a.pos_cg, a.fp64, a.pos_fg64, a.pos_cg64);
   rebuild = moved_beyond(ref, x[0], x[1], x[2], a.s32, a.thr2);
   if (a.prune) reprune = moved_beyond(ref_p, x[0], x[1], x[2], a.s32, a.thr2_p);
+}
+
+template <typename R>
+__device__ __forceinline__ void drift_atom(const DriftArgs<R>& a, int i, unsigned long long x[3], bool& rebuild,
+                                           bool& reprune) {
+  DriftIn<R> in;
+  drift_load(a, i, in);
+  drift_rest(a, i, in, x, rebuild, reprune);
 }
 
 template <typename R>
@@ -793,12 +818,18 @@ __device__ __forceinline__ void drift_seg_block(const DriftSegArgs<R>& a, int bi
   const int4 rec0 = q0 < nb ? a.B.bonds[b0 + q0] : (q0 < nb + na ? a.B.angles[g0 + q0 - nb] : make_int4(0, 0, 0, 0));
   const int4 rec1 = q1 < nb ? a.B.bonds[b0 + q1] : (q1 < nb + na ? a.B.angles[g0 + q1 - nb] : make_int4(0, 0, 0, 0));
   const int e0 = i < a1 ? a.inc_off[ip] : 0, e1 = i < a1 ? a.inc_off[ip + 1] : 0;
+  DriftIn<R> in;
+  if (i < a1) drift_load(a.d, i, in);
+  // launched as a programmatic dependent of the force sum: everything above
+  // was written before that kernel started; the total force, the thermostat
+  // factor and the step counter are read after it has finished
+  grid_dependency_wait();
   if (bid == 0 && threadIdx.x == 0)
     a.d.st->ev = a.d.thermo_every > 0 && ((a.d.st->local_step + 1) % a.d.thermo_every) == 0;
   bool rebuild = false, reprune = false;
   if (i < a1) {
     unsigned long long x[3];
-    drift_atom(a.d, i, x, rebuild, reprune);
+    drift_rest(a.d, i, in, x, rebuild, reprune);
 #pragma unroll
     for (int q = 0; q < 3; ++q) sx[3 * threadIdx.x + q] = x[q];
   }
@@ -1063,6 +1094,11 @@ __device__ __forceinline__ void sum_block(const SumArgs<R>& a, int bid, int nblk
     r1 = a.draw[2 * k];
     rs = a.draw[2 * k + 1];
   }
+  // launched as a programmatic dependent of the pair kernel: wait for its
+  // forces, then let the next drift launch (its early loads read nothing that
+  // this kernel or the pair kernel writes after this point)
+  grid_dependency_wait();
+  grid_dependents_launch();
   R ke = R(0);  // a few atoms per thread
   bool bad = false;
   const int stride = nblk * blockDim.x;
@@ -1435,15 +1471,39 @@ static size_t drift_seg_smem(const relres_ctx* c) {
   return sizeof(unsigned long long) * 3 * kSegAtoms + size_t(c->seg_slots) * (std::is_same<R, float>::value ? 16 : 24);
 }
 
+// A launch that may overlap the tail of the previous kernel of the stream
+// (programmatic dependent launch) when pdl is set: the kernel waits for that
+// kernel (grid_dependency_wait) before reading what it writes.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Programmatic dependent launches only without timing events between the
+// kernels (an event between them would stand in the way).
+static bool pdl_ok(const relres_ctx* c) { return c->use_pdl && !c->timing; }
+
 template <typename R>
-static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev) {
+static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev, bool after_sum) {
   if (step_segments(c)) {
     const DriftSegArgs<R> a = drift_seg_args<R>(c, sp, d_vel);
     const size_t smem = drift_seg_smem<R>(c);
-    if (ev)
-      k_drift_seg<R, true><<<c->n_seg, kSegAtoms, smem, c->stream>>>(a);
-    else
-      k_drift_seg<R, false><<<c->n_seg, kSegAtoms, smem, c->stream>>>(a);
+    // after the force sum of the previous step: overlap its tail
+    const bool pdl = after_sum && pdl_ok(c);
+    const cudaError_t e = ev ? launch_pdl(pdl, k_drift_seg<R, true>, c->n_seg, kSegAtoms, smem, c->stream, a)
+                             : launch_pdl(pdl, k_drift_seg<R, false>, c->n_seg, kSegAtoms, smem, c->stream, a);
+    if (e != cudaSuccess) return e;
   } else {
     k_drift<R><<<(c->n + kThreads - 1) / kThreads, kThreads, 0, c->stream>>>(drift_args<R>(c, sp, d_vel));
   }
@@ -1451,8 +1511,9 @@ static cudaError_t launch_drift_t(relres_ctx* c, const StepParams& sp, double* d
   return cudaGetLastError();
 }
 
-cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev) {
-  return c->fp64 ? launch_drift_t<double>(c, sp, d_vel, ev) : launch_drift_t<float>(c, sp, d_vel, ev);
+cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev, bool after_sum) {
+  return c->fp64 ? launch_drift_t<double>(c, sp, d_vel, ev, after_sum)
+                 : launch_drift_t<float>(c, sp, d_vel, ev, after_sum);
 }
 
 // blocks of the force sum: one wave of resident blocks (56 registers a
@@ -1491,7 +1552,9 @@ static SumArgs<R> sum_args(relres_ctx* c, const StepParams& sp, const double* d_
 template <typename R>
 static cudaError_t launch_sum_t(relres_ctx* c, const StepParams& sp, int k, const double* d_vel) {
   const SumArgs<R> a = sum_args<R>(c, sp, d_vel);
-  k_sum<R><<<sum_blocks(c), kThreads, 0, c->stream>>>(a, k);
+  // after the pair kernel: overlap its tail
+  const cudaError_t e = launch_pdl(pdl_ok(c), k_sum<R>, sum_blocks(c), kThreads, 0, c->stream, a, k);
+  if (e != cudaSuccess) return e;
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }

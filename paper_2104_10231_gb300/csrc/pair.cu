@@ -579,6 +579,9 @@ __device__ __forceinline__ void pair_block(const PairLaunch<R>& a, int bid) {
 
 template <typename R, bool EV, int TPA, int BS, int ACC>
 __global__ void __launch_bounds__(BS, pair_min_blocks<R, EV>(BS)) k_pair(PairLaunch<R> a) {
+  // the force sum that follows may start launching once every block of this
+  // grid runs (it waits for this grid to finish before reading the forces)
+  grid_dependents_launch();
   pair_block<R, EV, TPA, ACC>(a, blockIdx.x);
 }
 

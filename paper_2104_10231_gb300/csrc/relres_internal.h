@@ -298,6 +298,8 @@ struct relres_ctx {
   int n_seg = 0, seg_slots = 0, n_seg_proto = 0;
   bool seg_ok = false;
   bool use_seg = true;  // the fused kernel where segments exist (relres_set_option)
+  // force sum and drift as programmatic dependent launches (untimed steps)
+  bool use_pdl = true;
   // reductions: 64-bit fixed-point accumulators (kNAcc), cleared by their reader
   long long* d_acc = nullptr;
   double* d_draws = nullptr;  // CSVR random numbers of the current block of steps, 2 per step
@@ -417,7 +419,9 @@ cudaError_t launch_pair_grad(relres_ctx* c, const double* d_grad_forces, double 
 cudaError_t upload_type_consts(relres_ctx* c, double dt);
 // drift of one step; where the atoms form segments of whole molecules it also
 // evaluates the bonded forces of the new positions (d_f_bond; energy if ev)
-cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev);
+// after_sum: the previous kernel of the stream is the force sum of the
+// previous step (the drift may then be a programmatic dependent launch)
+cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel, bool ev, bool after_sum);
 // after the pair kernel: total forces, kinetic energy, thermostat and step
 // bookkeeping (k_sum with the thermostat in its last block, or the
 // finish + k_thermo pair where there are no segments)
