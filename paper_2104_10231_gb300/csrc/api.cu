@@ -1547,11 +1547,15 @@ static relres_status batch_graph(relres_batch* b, const std::vector<StepParams>&
     e = cudaStreamWaitEvent(b->fork[r], b->ev_fork, 0);
     if (e != cudaSuccess) break;
     const cudaStream_t own = c->stream;
-    const bool timing = c->timing;
+    const bool timing = c->timing, pdl = c->use_pdl;
     const long long n0 = c->n_launches;
     c->stream = b->fork[r];
     c->timing = false;  // per-class timing is not recorded in batches
+    // no programmatic dependent launches on branches: a kernel waiting for its
+    // predecessor would hold SM resources that other branches' kernels can use
+    c->use_pdl = false;
     s = record_block(c, sp[r], d_vel[r], blk, done, true);
+    c->use_pdl = pdl;
     if (s != RELRES_OK) b->err = "replica " + std::to_string(r) + " (capture): " + c->err;
     const long long kpr = (c->prune_on && !pairs_prune(c)) ? 1 : 0;
     b->k_parent[r] = (c->n_launches - n0) - (kRebuildKernels + kpr) * blk;
