@@ -518,9 +518,12 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
 
 // Forces-only FP32 launches are held to 64 registers a thread (the occupancy
 // of the walk without pruning); the pruning walk lives in the same kernel.
+// FP32 energy-step launches (256-thread blocks) are held to three blocks per
+// SM (80 registers; unbounded they take 95, two blocks per SM: 1.03 against
+// 0.93 ms per launch at 1M atoms).
 template <typename R, bool EV>
 constexpr int pair_min_blocks(int bs) {
-  return (std::is_same<R, float>::value && !EV) ? 65536 / (64 * bs) : 1;
+  return !std::is_same<R, float>::value ? 1 : (EV ? 3 * 256 / bs : 65536 / (64 * bs));
 }
 
 // One launch per step: with pruning on (one thread per slot) the kernel reads

@@ -252,6 +252,37 @@ def test_graph_and_stream_paths_agree_bitwise(torch):
     assert sg["n_launches"] < ss["n_launches"]
 
 
+def test_programmatic_dependent_launches_change_no_bit(torch):
+    # untimed steps launch the force sum and the next drift as programmatic
+    # dependents of their predecessors (each starts during the previous
+    # kernel's tail and waits for it before reading its results); timed steps
+    # launch every kernel the ordinary way.  Both, as graphs and as stream
+    # launches, over 300 steps with rebuilds, pruning passes and energy steps:
+    # the same bits.
+    s = S.neopentane(n_mol=2000, seed=14)
+    outs = []
+    for graphs in (True, False):
+        for timing in (False, True):
+            ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
+            ctx.set_graphs(graphs)
+            p = _dev(torch, s.pos)
+            v = _dev(torch, s.vel)
+            ctx.build_neighbors(p, s.box)
+            th = torch.zeros((30, R.RELRES_THERMO_COLS), dtype=torch.float64, device="cuda")
+            ctx.set_timing(timing)
+            for _ in range(3):
+                ctx.step(100, 2.0, p, v, t_target=260.0, tau_fs=100.0, seed=4, thermo_every=10, d_thermo=th)
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            outs.append((p.cpu().numpy(), v.cpu().numpy(), th.cpu().numpy(), st["n_builds"], st["n_prunes"]))
+            ctx.close()
+    p0, v0, t0, b0, n0 = outs[0]
+    assert b0 >= 3 and n0 > b0
+    for p1, v1, t1, b1, n1 in outs[1:]:
+        assert np.array_equal(p0, p1) and np.array_equal(v0, v1) and np.array_equal(t0, t1)
+        assert (b1, n1) == (b0, n0)
+
+
 def test_every_pair_launch_configuration_matches_oracle(torch):
     # threads per atom 1/2/4/8 x block sizes: each within the force tolerance
     s = S.neopentane(n_mol=500, seed=6)
