@@ -253,8 +253,9 @@ relres_status relres_chain_cg_grads(const relres_params* p, const double* g_eps_
 relres_status relres_create(relres_ctx** out, const relres_params* p, void* cuda_stream);
 
 /* Set atoms, masses, exclusions and bonded terms (replaces earlier ones).
- * Errors: RELRES_ERR_ARG (index out of range, asymmetric exclusions, type out
- * of range), RELRES_ERR_NOMEM, RELRES_ERR_CUDA. */
+ * A system has at least one atom.  Errors: RELRES_ERR_ARG (no atoms, index
+ * out of range, asymmetric exclusions, type out of range), RELRES_ERR_NOMEM,
+ * RELRES_ERR_CUDA. */
 relres_status relres_set_topology(relres_ctx* ctx, const relres_topology* t);
 
 /*

@@ -206,6 +206,73 @@ def _pair_system(r):
                     2.0, S._empty_topo(), eo, np.zeros(0, np.int32), 0.0, 1.0, 0)
 
 
+def test_empty_and_one_atom_systems(torch):
+    # no atoms: refused; one atom: no pair, zero force, energy and virial; an
+    # NVE step moves it in free flight (x + v dt, v unchanged: no force), and
+    # the thermostat refuses a system with fewer than two atoms
+    import dataclasses
+
+    two = _pair_system(5.0)
+    one = dataclasses.replace(two, pos=two.pos[:1].copy(), vel=np.array([[0.01, -0.02, 0.005]]),
+                              types=two.types[:1].copy(), mol=two.mol[:1].copy(),
+                              excl_off=np.zeros(2, np.int32), excl_idx=np.zeros(0, np.int32))
+    for prec in (R.RELRES_PREC_FP64, R.RELRES_PREC_FP32):
+        ctx = R.Context(R.params_for(one, prec))
+        with pytest.raises(R.RelresError) as ei:
+            ctx.set_topology(R.make_topology(np.zeros(0, np.int32), one.mass_by_type))
+        assert ei.value.status == 1  # RELRES_ERR_ARG
+        ctx.set_topology(R.topology_for(one))
+        p = _dev(torch, one.pos)
+        v = _dev(torch, one.vel)
+        ctx.build_neighbors(p, one.box)
+        f = torch.empty_like(p)
+        e = torch.zeros(4, dtype=torch.float64, device="cuda")
+        w = torch.zeros(6, dtype=torch.float64, device="cuda")
+        ctx.compute(p, f, e, w)
+        assert float(f.abs().max()) == 0.0 and float(e.abs().max()) == 0.0 and float(w.abs().max()) == 0.0
+        ctx.step(10, 1.0, p, v)
+        x = p.cpu().numpy()
+        assert np.allclose(x, one.pos + 10.0 * one.vel, rtol=0, atol=1e-9), (x, one.pos + 10.0 * one.vel)
+        # unchanged up to the float-float velocity state of the FP32 path
+        assert np.allclose(v.cpu().numpy(), one.vel, rtol=1e-13, atol=0)
+        with pytest.raises(R.RelresError):
+            ctx.step(1, 1.0, p, v, t_target=300.0)
+        ctx.close()
+
+
+def _eight_types(seed=31):
+    """The neopentane-like liquid relabelled with the largest number of types,
+    RELRES_MAX_TYPES = 8: four ordinary types for the CH3 sites and four
+    hybrid types for the central sites, all with different eps and sigma, and
+    a group composition per hybrid type (its own site plus four ordinary sites
+    in a type-dependent mix) from which Eq. 13 gives all 16 CG pairs."""
+    import dataclasses
+
+    base = S.neopentane(n_mol=1000, seed=seed)
+    rng = np.random.default_rng(seed)
+    mol = base.mol
+    types = np.where(base.types == 0, 4 + mol % 4, (mol + np.arange(base.n_atoms)) % 4).astype(np.int32)
+    comp = np.zeros((8, 8), np.int32)
+    for h in range(4):
+        comp[4 + h, 4 + h] = 1
+        comp[4 + h, h] += 2
+        comp[4 + h, (h + 1) % 4] += 1
+        comp[4 + h, (h + 2) % 4] += 1
+    return dataclasses.replace(
+        base, name="eight_types", types=types, type_names=[f"T{k}" for k in range(8)],
+        mass_by_type=np.concatenate([np.full(4, 15.035), np.full(4, 12.011)]),
+        eps_fg=rng.uniform(0.08, 0.2, 8), sig_fg=rng.uniform(3.6, 4.0, 8),
+        is_hybrid=np.array([0, 0, 0, 0, 1, 1, 1, 1], np.int32), group_comp=comp)
+
+
+@pytest.mark.parametrize("precision,f_tol,e_tol", [(R.RELRES_PREC_FP64, 1e-10, 1e-10),
+                                                   (R.RELRES_PREC_FP32, F_TOL, E_TOL)])
+def test_largest_number_of_types(torch, precision, f_tol, e_tol):
+    s = _eight_types()
+    assert s.n_types == R.RELRES_MAX_TYPES and len(np.unique(s.types)) == 8
+    _check_full(torch, s, precision, f_tol, e_tol)
+
+
 def test_single_pair_through_all_regions(torch):
     # below r_s-, in the FG shell, CG LJ, CG shell, beyond r_c+
     for r in (3.9, 5.5, 6.4, 6.999, 7.0, 9.0, 12.9, 13.5, 13.999, 14.5):
