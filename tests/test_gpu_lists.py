@@ -90,7 +90,35 @@ def _subsequence_per_owner(inner, outer):
         last[i] = k
 
 
+def _shuffled(s, seed):
+    """The same system with its atoms numbered in a random order: each
+    molecule's atoms (and so its excluded pairs) lie far apart in atom ids,
+    beyond the 15-id reach of the per-atom exclusion masks, so the list build
+    searches the exclusion lists instead; bonded terms and exclusions are
+    renumbered with the atoms."""
+    import dataclasses
+
+    n = s.n_atoms
+    perm = np.random.default_rng(seed).permutation(n)  # new atom k is old atom perm[k]
+    inv = np.empty(n, np.int64)
+    inv[perm] = np.arange(n)
+    off, idx = s.excl
+    rows = [np.sort(inv[idx[off[o]:off[o + 1]]]) for o in perm]
+    excl_off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    excl_idx = (np.concatenate(rows) if rows else np.zeros(0)).astype(np.int32)
+    topo = dict(s.topo)
+    for key in ("bonds", "angles", "dihedrals"):
+        topo[key] = inv[np.asarray(topo[key], np.int64)].astype(np.int32)
+    out = dataclasses.replace(s, name=s.name + "_shuffled", pos=s.pos[perm].copy(), vel=s.vel[perm].copy(),
+                              types=s.types[perm].copy(), mol=s.mol[perm].copy(), topo=topo,
+                              excl_off=excl_off, excl_idx=excl_idx)
+    gaps = [abs(int(j) - k) for k in range(n) for j in excl_idx[excl_off[k]:excl_off[k + 1]]]
+    assert max(gaps) > 15
+    return out
+
+
 SYSTEMS = [("propane", lambda: S.propane()),
+           ("neopentane shuffled", lambda: _shuffled(S.neopentane(n_mol=500, seed=11), seed=5)),
            ("neopentane", lambda: S.neopentane(n_mol=500, seed=11)),
            ("copolymer", lambda: S.block_copolymer(n_chain=20)),
            ("propane FG only", lambda: S.fg_only(S.propane(), r_inner=9.0, r_outer=10.0))]
