@@ -291,6 +291,7 @@ struct SmemTabs {
   const CgRow* cgr;
   const FgE* fge;
   const CgE* cge;
+  int4* evq;  // FP32 energy steps: kEvQueue queued pairs per warp
 };
 
 // Per-thread accumulators of one walk.  The owner's force sum of the FP32
@@ -364,7 +365,7 @@ __device__ __forceinline__ void acc_final(Acc<double>&) {}
 
 // One list entry; returns its squared distance (past every cutoff for a
 // padding entry), which a pruning launch compares with the pruning radius.
-template <typename R, bool CG, bool EV, int ACC>
+template <typename R, bool CG, bool EV, int ACC, bool EN = EV>
 __device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typename PosOf<R>::T& pj,
                                    bool valid, int row0, const SmemTabs& S, const PairLaunch<R>& a,
                                    Acc<R>& A) {
@@ -387,7 +388,7 @@ __device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typenam
       // r2 = 3e38; the energy and its slope vanish at the cutoff, so the FP32
       // decision is harmless), from the exact integer coordinate differences
       const float rcut2 = CG ? S.cgr[row].a.y : S.fgr[row].a.y;
-      if (r2 < rcut2) {
+      if (EN && r2 < rcut2) {
         const ff ex = ff_fixed_diff32(pi.x, pj.x, ff{a.sx, a.sxl});
         const ff ey = ff_fixed_diff32(pi.y, pj.y, ff{a.sy, a.syl});
         const ff ez = ff_fixed_diff32(pi.z, pj.z, ff{a.sz, a.szl});
@@ -421,6 +422,53 @@ __device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typenam
   }
 }
 
+// Float-float energy of one pair from its exact 32-bit coordinate
+// differences d = (pi - pj).xyz and type-pair row d.w (the arithmetic of the
+// energy part of entry()).
+template <bool CG>
+__device__ __forceinline__ ff pair_energy_ff(int4 d, const SmemTabs& S, const PairLaunch<float>& a) {
+  const ff ex = ff_fixed_diff32(d.x, 0, ff{a.sx, a.sxl});
+  const ff ey = ff_fixed_diff32(d.y, 0, ff{a.sy, a.syl});
+  const ff ez = ff_fixed_diff32(d.z, 0, ff{a.sz, a.szl});
+  const ff r2e = ff_add(ff_add(ff_mul(ex, ex), ff_mul(ey, ey)), ff_mul(ez, ez));
+  const int row = d.w;
+  return CG ? cg_energy_ff(S.cge[row], cg_radii2(S.cgr[row]), r2e)
+            : fg_energy_ff(S.fge[row], S.fgr[row].b.x * S.fgr[row].b.x, r2e);
+}
+
+// Energy steps of the FP32 path: each pair's energy is evaluated once (by the
+// owner of the lower slot; the lists hold every pair from both ends) and not
+// where it is met: the warp queues (pair, row) items in shared memory and
+// evaluates 32 of them at a time, one per lane, so no lane idles through the
+// float-float arithmetic of another's entry.  kEvQueue items per warp: fewer
+// than 32 wait between two drains, and one pass adds at most 32.
+constexpr int kEvQueue = 64;
+struct EvQueue {
+  int4* q;  // this warp's kEvQueue items
+  int n;    // items waiting (the same in every lane)
+};
+
+template <bool CG>
+__device__ __forceinline__ void ev_push(EvQueue& Q, bool need, int4 item, const SmemTabs& S,
+                                        const PairLaunch<float>& a, ff& eff) {
+  const int lane = threadIdx.x & 31;
+  const unsigned b = __ballot_sync(0xffffffffu, need);
+  if (need) Q.q[Q.n + __popc(b & ((1u << lane) - 1u))] = item;
+  Q.n += __popc(b);
+  if (Q.n >= 32) {
+    __syncwarp();
+    const int4 d = Q.q[Q.n - 32 + lane];
+    __syncwarp();
+    Q.n -= 32;
+    eff = ff_add(eff, pair_energy_ff<CG>(d, S, a));
+  }
+}
+
+__device__ __forceinline__ int4 fixed_delta(const int4& pi, const int4& pj, int row) {
+  return make_int4(int(unsigned(pi.x) - unsigned(pj.x)), int(unsigned(pi.y) - unsigned(pj.y)),
+                   int(unsigned(pi.z) - unsigned(pj.z)), row);
+}
+
 __device__ __forceinline__ int4 ref_of(const int4& p) { return p; }
 __device__ __forceinline__ int4 ref_of(const Pos64& p) {
   return make_int4(int(p.x >> 32), int(p.y >> 32), int(p.z >> 32), int(p.t));
@@ -443,7 +491,69 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
   const int q = t % TPA;
   Acc<R> A;
   int kept = 0;
-  if (s < L.nslots) {
+  constexpr bool EVQ = EV && std::is_same<R, float>::value;  // queued energies (TPA = 1)
+  static_assert(!EVQ || TPA == 1, "energy steps use one thread per slot");
+  if constexpr (EVQ) {
+    // every lane of the warp runs the same number of chunk passes (the
+    // warp's longest list; lanes past their own list or past the last slot
+    // add nothing) so that the queue's ballots see all 32 lanes
+    EvQueue Q{S.evq + (threadIdx.x >> 5) * kEvQueue, 0};
+    const bool own = s < L.nslots;
+    const int ss = own ? s : 0;  // a valid slot for the loads of the other lanes
+    const auto pi = L.pos[ss];
+    const int row0 = ptype(pi) * a.nt;
+    const int m = own ? (PRN ? L.cnt_full[s] : L.cnt[s]) : 0;
+    const int nch = (m + 3) >> 2;
+    const int nch_w = __reduce_max_sync(0xffffffffu, nch);
+    const int4* nb4 = reinterpret_cast<const int4*>(PRN ? L.nbr_full : L.nbr) + ss;
+    int4* out4 = reinterpret_cast<int4*>(L.nbr_in) + ss;
+    int4 buf = make_int4(ss, ss, ss, ss);
+    int4 jj = make_int4(ss, ss, ss, ss);
+    if (nch > 0) jj = __ldcs(nb4);
+    for (int ch = 0; ch < nch_w; ++ch) {
+      const bool live = ch < nch;
+      int4 jn = jj;
+      if (ch + 1 < nch) jn = __ldcs(nb4 + size_t(ch + 1) * L.nslots);
+      const int rem = live ? m - 4 * ch : 0;
+      const int j0 = rem > 0 ? jj.x : ss, j1 = rem > 1 ? jj.y : ss, j2 = rem > 2 ? jj.z : ss,
+                j3 = rem > 3 ? jj.w : ss;
+      const auto p0 = load_pos(L.pos, j0);
+      const auto p1 = load_pos(L.pos, j1);
+      const auto p2 = load_pos(L.pos, j2);
+      const auto p3 = load_pos(L.pos, j3);
+      const R r0 = entry<R, CG, EV, ACC, false>(pi, p0, rem > 0, row0, S, a, A);
+      const R r1 = entry<R, CG, EV, ACC, false>(pi, p1, rem > 1, row0, S, a, A);
+      const R r2 = entry<R, CG, EV, ACC, false>(pi, p2, rem > 2, row0, S, a, A);
+      const R r3 = entry<R, CG, EV, ACC, false>(pi, p3, rem > 3, row0, S, a, A);
+      if (live) acc_chunk<ACC>(A);
+      if (PRN && live) {
+        keep_entry(r0 < L.rp2, j0, kept, buf, out4, L.nslots);
+        keep_entry(r1 < L.rp2, j1, kept, buf, out4, L.nslots);
+        keep_entry(r2 < L.rp2, j2, kept, buf, out4, L.nslots);
+        keep_entry(r3 < L.rp2, j3, kept, buf, out4, L.nslots);
+      }
+      // energies of the pairs inside the cutoff, each from its lower slot
+      const R rr[4] = {r0, r1, r2, r3};
+      const int jv[4] = {j0, j1, j2, j3};
+      const int4 pv[4] = {p0, p1, p2, p3};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = row0 + ptype(pv[e]);
+        const float rcut2 = CG ? S.cgr[row].a.y : S.fgr[row].a.y;
+        const bool need = rem > e && rr[e] < rcut2 && s < jv[e];
+        ev_push<CG>(Q, need, fixed_delta(pi, pv[e], row), S, a, A.eff);
+      }
+      jj = jn;
+    }
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    if (lane < Q.n) A.eff = ff_add(A.eff, pair_energy_ff<CG>(Q.q[lane], S, a));
+    if (PRN && own) {
+      keep_tail(kept, buf, out4, L.nslots);
+      L.cnt_in[s] = kept;
+      if (!CG) a.ref_p[L.perm[s]] = ref_of(pi);
+    }
+  } else if (s < L.nslots) {
     const auto pi = L.pos[s];
     const int row0 = ptype(pi) * a.nt;
     const int m = PRN ? L.cnt_full[s] : L.cnt[s];
@@ -503,7 +613,9 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
   if (EV) {
     // per-thread sums are R (FP64 for the energy); the block sum is taken in FP64
     double accd[kNQ];
-    accd[0] = std::is_same<R, float>::value ? double(A.eff.hi) + double(A.eff.lo) : double(A.e);
+    // FP32 path: each pair's energy was counted once (queued), so it is
+    // doubled here against the halving of the full-list sums below
+    accd[0] = std::is_same<R, float>::value ? 2.0 * (double(A.eff.hi) + double(A.eff.lo)) : double(A.e);
 #pragma unroll
     for (int k = 0; k < 6; ++k) accd[k + 1] = double(A.w[k]);
     __shared__ double sh[(1024 / 32) * kNQ];
@@ -553,6 +665,7 @@ __device__ __forceinline__ void pair_block(const PairLaunch<R>& a, int bid) {
       for (int r = threadIdx.x; r < nrow; r += blockDim.x) pack_energy_rows(a.tabd[r], fge[r], cge[r]);
       S.fge = fge;
       S.cge = cge;
+      S.evq = reinterpret_cast<int4*>(carve(sizeof(int4) * kEvQueue * (blockDim.x / 32)));
     }
   } else {
     PairTab<R>* tab = reinterpret_cast<PairTab<R>*>(carve(sizeof(PairTab<R>) * nrow));
@@ -604,7 +717,7 @@ static size_t pair_smem(int nt, bool ev) {
   auto up = [](size_t b) { return (b + 15) / 16 * 16; };
   if (std::is_same<R, float>::value)
     return up(sizeof(FgRow) * nrow) + up(sizeof(CgRow) * nrow) +
-           (ev ? up(sizeof(FgE) * nrow) + up(sizeof(CgE) * nrow) : 0);
+           (ev ? up(sizeof(FgE) * nrow) + up(sizeof(CgE) * nrow) + sizeof(int4) * kEvQueue * (kThreads / 32) : 0);
   return up(sizeof(PairTab<R>) * nrow);
 }
 
