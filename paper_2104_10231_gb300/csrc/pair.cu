@@ -425,8 +425,10 @@ __device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typenam
 // Float-float energy of one pair from its exact 32-bit coordinate
 // differences d = (pi - pj).xyz and type-pair row d.w (the arithmetic of the
 // energy part of entry()).
+// (one copy per list kind, called from the queue drains: inlined at each of
+// them the float-float code overflowed the instruction cache)
 template <bool CG>
-__device__ __forceinline__ ff pair_energy_ff(int4 d, const SmemTabs& S, const PairLaunch<float>& a) {
+__device__ __noinline__ ff pair_energy_ff(int4 d, const SmemTabs& S, const PairLaunch<float>& a) {
   const ff ex = ff_fixed_diff32(d.x, 0, ff{a.sx, a.sxl});
   const ff ey = ff_fixed_diff32(d.y, 0, ff{a.sy, a.syl});
   const ff ez = ff_fixed_diff32(d.z, 0, ff{a.sz, a.szl});
@@ -611,15 +613,46 @@ __device__ __forceinline__ void walk(const ListWalk<R>& L, int blk, const SmemTa
   }
   if (s < L.nslots && q == 0) store_force(L.f_out, L.perm[s], A.fx, A.fy, A.fz);
   if (EV) {
-    // per-thread sums are R (FP64 for the energy); the block sum is taken in FP64
     double accd[kNQ];
-    // FP32 path: each pair's energy was counted once (queued), so it is
-    // doubled here against the halving of the full-list sums below
-    accd[0] = std::is_same<R, float>::value ? 2.0 * (double(A.eff.hi) + double(A.eff.lo)) : double(A.e);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) accd[k + 1] = double(A.w[k]);
     __shared__ double sh[(1024 / 32) * kNQ];
-    block_sum<double, kNQ>(accd, sh);
+    if constexpr (std::is_same<R, float>::value) {
+      // FP32 path: warp sums in float-float (energy) and FP32 (virial: 32
+      // per-thread sums of FP32 terms), FP64 across the warps only (FP64
+      // arithmetic runs at a small fraction of the FP32 rate on this part).
+      // Each pair's energy was counted once (queued), so it is doubled here
+      // against the halving of the full-list sums below.
+      ff e = A.eff;
+      float w[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) w[k] = A.w[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e = ff_add(e, ff{__shfl_xor_sync(0xffffffffu, e.hi, o), __shfl_xor_sync(0xffffffffu, e.lo, o)});
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] += __shfl_xor_sync(0xffffffffu, w[k], o);
+      }
+      const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      if ((threadIdx.x & 31) == 0) {
+        sh[wid * kNQ] = 2.0 * (double(e.hi) + double(e.lo));
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sh[wid * kNQ + k + 1] = double(w[k]);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < kNQ; ++k) {
+          double v = 0.0;
+          for (int ww = 0; ww < nw; ++ww) v += sh[ww * kNQ + k];
+          accd[k] = v;
+        }
+      }
+    } else {
+      // FP64 path: per-thread FP64 sums, block sum in FP64
+      accd[0] = double(A.e);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) accd[k + 1] = double(A.w[k]);
+      block_sum<double, kNQ>(accd, sh);
+    }
     if (threadIdx.x == 0) {
       // full lists: every pair was visited from both ends
 #pragma unroll
