@@ -407,11 +407,13 @@ relres_status relres_get_list(relres_ctx* ctx, int which, int* h_i, int* h_j, lo
  * pair of lists of the same capacity, and the pair kernels walk those.  A pass
  * follows every build and runs again at the first step after an atom has
  * moved more than delta/2 since the last pass.  The entries a pass drops
- * contribute exactly zero, so forces, energies and trajectories are the same
+ * contribute exactly zero, so forces, virial and trajectories are the same
  * bits as without pruning when one thread walks each list (pair launch
  * configurations 0-2 of relres_set_pair_config) and the force sums are
  * running sums (RELRES_ACC_FP32, RELRES_ACC_FP64); the default compensated
- * sums add the entries four at a time, so there they agree to rounding.  delta <= 0 turns pruning
+ * sums add the entries four at a time, so there they agree to rounding, as do
+ * the pair energies of the FP32 path (summed in an order that follows the
+ * lists walked).  delta <= 0 turns pruning
  * off (the pair kernels then walk the full lists and the second pair of lists
  * is freed).  Default: delta = 0.5 A.  Rebuilds the lists at the current
  * positions if they exist.  Synchronous.  Errors: RELRES_ERR_ARG (null

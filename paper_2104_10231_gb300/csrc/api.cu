@@ -672,6 +672,7 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(cudaMemset(c->d_f_cg, 0, fb));
   c->have_topo = true;
   c->have_lists = false;
+  c->consts_dt = 0.0;  // masses may have changed
   c->forces_valid = false;
   c->cap_fg = c->cap_cg = 0;
   return RELRES_OK;
@@ -1239,20 +1240,27 @@ static relres_status step_begin(relres_ctx* c, int n_steps, double dt_fs, double
   CK(launch_check_cache(c, d_pos));
   relres_status s = read_state(c);
   if (s != RELRES_OK) return s;
+  bool fresh = false;  // host state read after the last device work that changes it
   if ((c->h_state->flags & F_DIRTY) || !c->forces_valid) {
     CK(launch_convert(c, d_pos));
     s = forces_now(c, 0, nullptr, nullptr, nullptr);
     if (s != RELRES_OK) return s;
+    fresh = true;
   }
   if (!c->tuned) {
     s = autotune_pairs(c);
     if (s != RELRES_OK) return s;
+    fresh = true;
   }
   CK(upload_type_consts(c, dt_fs));
   CK(launch_vel_in(c, d_vel));  // FP32: the float-float velocity state of the call
   CK(launch_set_ab(c, 1.0, 1.0, 0));
   CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
-  return read_state(c);  // also orders the setup before work on other streams
+  // Everything that follows runs on the context stream, after these launches.
+  // Without a force evaluation above, the state read at the start is still
+  // current for the block accounting (the set-up above changes no count), so
+  // no further round trip is needed; after one, read it again.
+  return fresh ? read_state(c) : RELRES_OK;
 }
 
 // After a block has run: status, timing and launch accounting; on a list

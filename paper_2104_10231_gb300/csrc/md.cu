@@ -1232,6 +1232,7 @@ static Sc3<float> s32_of(const relres_ctx* c) {
 }
 
 cudaError_t upload_type_consts(relres_ctx* c, double dt) {
+  if (c->consts_dt == dt) return cudaSuccess;  // already there (reset by relres_set_topology)
   std::vector<float2> cff(size_t(c->n_types));
   std::vector<float> kec(size_t(c->n_types));
   for (int k = 0; k < c->n_types; ++k) {
@@ -1249,6 +1250,7 @@ cudaError_t upload_type_consts(relres_ctx* c, double dt) {
     e = cudaMemcpyAsync(c->d_kec, kec.data(), sizeof(float) * c->n_types, cudaMemcpyHostToDevice, c->stream);
   // the host vectors must outlive the copies
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) c->consts_dt = dt;
   return e;
 }
 

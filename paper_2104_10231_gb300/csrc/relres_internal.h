@@ -209,6 +209,7 @@ struct relres_ctx {
   float* d_kec = nullptr;      // per type: m / 2 in kcal/mol per (A/fs)^2, FP32
   double* d_mass = nullptr;  // per type mass
   std::vector<double> h_cdt = std::vector<double>(RELRES_MAX_TYPES, 0.0);
+  double consts_dt = 0.0;  // time step of the per-type constants on the device (0: none yet)
 
   // topology
   int n = 0, n_h = 0;

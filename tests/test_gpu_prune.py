@@ -69,7 +69,17 @@ def test_pruned_trajectory_is_bit_identical(torch, precision, graphs):
     assert st1["mean_fg_pruned"] < 0.8 * st1["mean_fg"]
     if st1["n_hybrid"]:
         assert st1["mean_cg_pruned"] < 0.95 * st1["mean_cg"]
-    assert np.array_equal(p0, p1) and np.array_equal(v0, v1) and np.array_equal(t0, t1)
+    assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
+    # thermo rows: E_FG, E_CG, E_bonded, kinetic energy, six virial components.
+    # The trajectory, the kinetic and bonded energies and the virial are the
+    # same bits; the pair energies of the FP32 path agree to rounding: each
+    # pair's energy is evaluated once from a per-warp queue, whose grouping
+    # depends on where the entries sit in the lists walked
+    assert np.array_equal(t0[:, 2:], t1[:, 2:])
+    if precision == R.RELRES_PREC_FP64:
+        assert np.array_equal(t0, t1)
+    else:
+        assert np.allclose(t0[:, :2], t1[:, :2], rtol=1e-12, atol=0), np.abs(t0[:, :2] - t1[:, :2]).max()
 
 
 def test_compute_after_displacements_between_the_thresholds(torch):
