@@ -303,8 +303,9 @@ relres_status relres_compute(relres_ctx* ctx, const double* d_pos, double* d_for
  *   E_fg E_cg E_bonded KE Wxx Wyy Wzz Wxy Wxz Wyz at that step.
  * Forces at the incoming positions are reused from the previous call when
  * d_pos still holds the positions that call returned; otherwise recomputed.
- * On an error the state is rolled back to the last completed block of steps
- * (blocks of up to 100 steps) and the error is returned.
+ * On RELRES_ERR_NONFINITE or RELRES_ERR_LIST_OVERFLOW the state is rolled
+ * back to the last completed block of steps (blocks of up to 100 steps),
+ * d_pos/d_vel receive it, and the error is returned.
  * Errors: RELRES_ERR_STATE, RELRES_ERR_LIST_OVERFLOW, RELRES_ERR_NONFINITE,
  * RELRES_ERR_ARG, RELRES_ERR_CUDA.
  */

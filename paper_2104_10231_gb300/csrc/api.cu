@@ -1235,6 +1235,11 @@ static relres_status step_begin(relres_ctx* c, int n_steps, double dt_fs, double
   if (n_steps == 0) return RELRES_OK;
   if (c->n < 2 && t_target > 0.0) return fail(c, RELRES_ERR_ARG, "the thermostat needs at least 2 atoms");
 
+  // The call's velocity state and thermostat factors first: the GPU converts
+  // the velocities while the host waits for the cache check below (the force
+  // evaluation and the autotuner read neither).
+  CK(launch_vel_in(c, d_vel));  // FP32: the float-float velocity state of the call
+  CK(launch_set_ab(c, 1.0, 1.0, 0));
   // forces at the incoming positions: reuse when d_pos is what we returned last
   CK(launch_flags_and(c, ~(unsigned)F_DIRTY));
   CK(launch_check_cache(c, d_pos));
@@ -1253,8 +1258,6 @@ static relres_status step_begin(relres_ctx* c, int n_steps, double dt_fs, double
     fresh = true;
   }
   CK(upload_type_consts(c, dt_fs));
-  CK(launch_vel_in(c, d_vel));  // FP32: the float-float velocity state of the call
-  CK(launch_set_ab(c, 1.0, 1.0, 0));
   CK(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * kNAcc, c->stream));
   // Everything that follows runs on the context stream, after these launches.
   // Without a force evaluation above, the state read at the start is still
@@ -1296,7 +1299,11 @@ static relres_status block_end(relres_ctx* c, double* d_pos, double* d_vel, doub
       c->forces_valid = true;
       return fail(c, RELRES_ERR_NONFINITE, "non-finite force during relres_step");
     }
-    if (++*retries > 8) return fail(c, RELRES_ERR_LIST_OVERFLOW, "repeated list overflow");
+    if (++*retries > 8) {
+      CK(launch_write_back(c, d_pos, d_vel, dt_fs));  // the caller's copy of the restored state
+      CK(cudaStreamSynchronize(c->stream));
+      return fail(c, RELRES_ERR_LIST_OVERFLOW, "repeated list overflow");
+    }
     s = read_state(c);
     if (s != RELRES_OK) return s;
     if (fl & F_OVERFLOW_FG) c->cap_fg = round_cap(std::max(c->h_state->max_fg, c->cap_fg) * 1.25 + 8, c->n);
@@ -1310,14 +1317,20 @@ static relres_status block_end(relres_ctx* c, double* d_pos, double* d_vel, doub
   return RELRES_OK;
 }
 
-// Positions and velocities back to the caller, counters.
-static relres_status step_end(relres_ctx* c, int n_steps, double* d_pos, double* d_vel, double dt_fs) {
-  CK(launch_write_back(c, d_pos, d_vel, dt_fs));
-  relres_status s = read_state(c);
-  if (s != RELRES_OK) return s;
+// Counters of a completed call; the positions and velocities went back to the
+// caller behind its last block, before block_end's status read.
+static void step_end(relres_ctx* c, int n_steps) {
   c->n_steps += n_steps;
   c->step_counter = c->h_state->step;
   c->forces_valid = true;
+}
+
+// Positions and velocities back to the caller, then the counters (batches).
+static relres_status write_back_and_end(relres_ctx* c, int n_steps, double* d_pos, double* d_vel, double dt_fs) {
+  CK(launch_write_back(c, d_pos, d_vel, dt_fs));
+  relres_status s = read_state(c);
+  if (s != RELRES_OK) return s;
+  step_end(c, n_steps);
   return RELRES_OK;
 }
 
@@ -1680,7 +1693,7 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
         return batch_fail(b, RELRES_ERR_CUDA, "replica " + std::to_string(r) + ": out-of-range cell index");
       if (flags[r] & F_NONFINITE) {
         for (int q = 0; q < nr; ++q) rollback_block(b->ctx[q], d_vel[q]);
-        for (int q = 0; q < nr; ++q) step_end(b->ctx[q], 0, d_pos[q], d_vel[q], dt_fs);
+        for (int q = 0; q < nr; ++q) write_back_and_end(b->ctx[q], 0, d_pos[q], d_vel[q], dt_fs);
         return batch_fail(b, RELRES_ERR_NONFINITE, "replica " + std::to_string(r) + ": non-finite force");
       }
       overflow |= (flags[r] & (F_OVERFLOW_FG | F_OVERFLOW_CG)) != 0;
@@ -1705,7 +1718,7 @@ relres_status relres_batch_step(relres_batch* b, int n_steps, double dt_fs, doub
     done += blk;
   }
   for (int r = 0; r < nr; ++r) {
-    relres_status s = step_end(b->ctx[r], n_steps, d_pos[r], d_vel[r], dt_fs);
+    relres_status s = write_back_and_end(b->ctx[r], n_steps, d_pos[r], d_vel[r], dt_fs);
     if (s != RELRES_OK) return batch_fail(b, s, "replica " + std::to_string(r) + ": " + b->ctx[r]->err);
   }
   return RELRES_OK;
@@ -1764,12 +1777,17 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
       s = record_block(c, sp, d_vel, blk, done, false);
       if (s != RELRES_OK) return s;
     }
+    // behind the last block the positions and velocities go back to the
+    // caller, so that one status read covers both (a block that fails or is
+    // retried restores the state, and the caller's copy is written again)
+    if (done + blk == n_steps) CK(launch_write_back(c, d_pos, d_vel, dt_fs));
     bool retry = false;
     s = block_end(c, d_pos, d_vel, dt_fs, builds0, prunes0, c->use_graphs, &retries, &retry);
     if (s != RELRES_OK) return s;
     if (!retry) done += blk;
   }
-  return step_end(c, n_steps, d_pos, d_vel, dt_fs);
+  step_end(c, n_steps);
+  return RELRES_OK;
 }
 
 relres_status relres_set_step_counter(relres_ctx* c, long long step) {
