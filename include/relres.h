@@ -301,8 +301,13 @@ relres_status relres_compute(relres_ctx* ctx, const double* d_pos, double* d_for
  *   thermo_every > 0 and d_thermo != NULL: after every thermo_every-th step,
  *   row k of d_thermo [n_steps/thermo_every][RELRES_THERMO_COLS] receives
  *   E_fg E_cg E_bonded KE Wxx Wyy Wzz Wxy Wxz Wyz at that step.
- * Forces at the incoming positions are reused from the previous call when
- * d_pos still holds the positions that call returned; otherwise recomputed.
+ * A call given d_pos (and d_vel) still holding what the previous relres_step
+ * returned continues from that call's end state (compared word for word on
+ * the device): its forces are reused and, in FP32 mode with the same dt_fs,
+ * its velocity state and last thermostat factors too, so that a run split
+ * into calls of any length is the same bits as one call.  Arrays changed in
+ * between are read: new positions get their forces computed, new velocities
+ * replace the velocity state.
  * On RELRES_ERR_NONFINITE or RELRES_ERR_LIST_OVERFLOW the state is rolled
  * back to the last completed block of steps (blocks of up to 100 steps),
  * d_pos/d_vel receive it, and the error is returned.

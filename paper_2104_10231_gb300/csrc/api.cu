@@ -644,6 +644,9 @@ relres_status relres_set_topology(relres_ctx* c, const relres_topology* t) {
   CK(dalloc(&c->d_snap_x, 3 * size_t(n)));
   CK(dalloc(&c->d_snap_v, 3 * size_t(n)));
   CK(dalloc(&c->d_uff, 3 * size_t(n)));
+  CK(dalloc(&c->d_pos_ret, 3 * size_t(n)));
+  CK(dalloc(&c->d_vel_ret, 3 * size_t(n)));
+  c->io_valid = false;
   const size_t n_slots = 2 * size_t(c->n_bonds) + 3 * size_t(c->n_angles) + 4 * size_t(c->n_dih);
   CK(dalloc(reinterpret_cast<unsigned char**>(&c->d_tf),
             std::max<size_t>(1, n_slots) * (c->fp64 ? 24 : 16)));
@@ -715,6 +718,7 @@ relres_status relres_build_neighbors(relres_ctx* c, const double* d_pos, const d
   }
   const bool had = c->have_lists;
   c->have_lists = false;  // no sorted scatter before the first pack
+  c->io_valid = false;
   CK(launch_convert(c, d_pos));
   c->have_lists = had;
   s = read_state(c);
@@ -732,6 +736,7 @@ relres_status relres_compute(relres_ctx* c, const double* d_pos, double* d_force
   if (!c) return RELRES_ERR_ARG;
   if (!c->have_lists) return fail(c, RELRES_ERR_STATE, "relres_build_neighbors first");
   if (!d_pos || !d_forces) return fail(c, RELRES_ERR_ARG, "d_pos and d_forces are required");
+  c->io_valid = false;
   CK(launch_convert(c, d_pos));
   return forces_now(c, (d_energy || d_virial) ? 1 : 0, d_forces, d_energy, d_virial);
 }
@@ -1170,6 +1175,7 @@ relres_status relres_backward(relres_ctx* c, const double* d_pos, const double* 
   if (!c->have_lists) return fail(c, RELRES_ERR_STATE, "relres_build_neighbors first");
   if (!d_pos || !std::isfinite(grad_energy)) return fail(c, RELRES_ERR_ARG, "invalid backward arguments");
   // positions into the device state (lists rebuilt if an atom moved too far)
+  c->io_valid = false;
   CK(launch_convert(c, d_pos));
   relres_status s = read_state(c);
   if (s != RELRES_OK) return s;
@@ -1235,18 +1241,31 @@ static relres_status step_begin(relres_ctx* c, int n_steps, double dt_fs, double
   if (n_steps == 0) return RELRES_OK;
   if (c->n < 2 && t_target > 0.0) return fail(c, RELRES_ERR_ARG, "the thermostat needs at least 2 atoms");
 
-  // The call's velocity state and thermostat factors first: the GPU converts
-  // the velocities while the host waits for the cache check below (the force
-  // evaluation and the autotuner read neither).
-  CK(launch_vel_in(c, d_vel));  // FP32: the float-float velocity state of the call
-  CK(launch_set_ab(c, 1.0, 1.0, 0));
-  // forces at the incoming positions: reuse when d_pos is what we returned last
-  CK(launch_flags_and(c, ~(unsigned)F_DIRTY));
-  CK(launch_check_cache(c, d_pos));
-  relres_status s = read_state(c);
-  if (s != RELRES_OK) return s;
+  // The state at the call's start.  After a relres_step, a call given the
+  // arrays that step returned (compared word for word on the device)
+  // continues from its end state: the forces are reused and, in FP32 mode
+  // with the same time step, so are the velocity state and the last step's
+  // thermostat factors (the trajectory is then the bits of one longer call).
+  // Otherwise the positions are read and the forces evaluated, and the
+  // velocities are read (u = v, a = b = 1).
+  const bool cached = c->io_valid && c->forces_valid;
+  c->io_valid = false;  // until this call has returned its arrays
+  bool dirty = true, keep_u = false;
+  relres_status s = RELRES_OK;
+  if (cached) {
+    const bool try_u = !c->fp64 && dt_fs == c->io_dt;
+    CK(launch_flags_and(c, ~(unsigned)(F_DIRTY | F_VDIRTY)));
+    CK(launch_check_io(c, d_pos, try_u ? d_vel : nullptr));
+    s = read_state(c);
+    if (s != RELRES_OK) return s;
+    const unsigned fl = c->h_state->flags;
+    dirty = (fl & F_DIRTY) != 0;
+    keep_u = try_u && !dirty && !(fl & F_VDIRTY);
+  }
+  if (!keep_u) CK(launch_vel_in(c, d_vel));  // FP32: the float-float velocity state of the call
+  CK(launch_call_start(c, !keep_u));
   bool fresh = false;  // host state read after the last device work that changes it
-  if ((c->h_state->flags & F_DIRTY) || !c->forces_valid) {
+  if (dirty) {
     CK(launch_convert(c, d_pos));
     s = forces_now(c, 0, nullptr, nullptr, nullptr);
     if (s != RELRES_OK) return s;
@@ -1319,10 +1338,12 @@ static relres_status block_end(relres_ctx* c, double* d_pos, double* d_vel, doub
 
 // Counters of a completed call; the positions and velocities went back to the
 // caller behind its last block, before block_end's status read.
-static void step_end(relres_ctx* c, int n_steps) {
+static void step_end(relres_ctx* c, int n_steps, double dt_fs) {
   c->n_steps += n_steps;
   c->step_counter = c->h_state->step;
   c->forces_valid = true;
+  c->io_valid = true;
+  c->io_dt = dt_fs;
 }
 
 // Positions and velocities back to the caller, then the counters (batches).
@@ -1330,7 +1351,7 @@ static relres_status write_back_and_end(relres_ctx* c, int n_steps, double* d_po
   CK(launch_write_back(c, d_pos, d_vel, dt_fs));
   relres_status s = read_state(c);
   if (s != RELRES_OK) return s;
-  step_end(c, n_steps);
+  step_end(c, n_steps, dt_fs);
   return RELRES_OK;
 }
 
@@ -1786,7 +1807,7 @@ relres_status relres_step(relres_ctx* c, int n_steps, double dt_fs, double* d_po
     if (s != RELRES_OK) return s;
     if (!retry) done += blk;
   }
-  step_end(c, n_steps);
+  step_end(c, n_steps, dt_fs);
   return RELRES_OK;
 }
 
@@ -1962,6 +1983,8 @@ void relres_destroy(relres_ctx* c) {
   dfree(c->d_snap_x);
   dfree(c->d_snap_v);
   dfree(c->d_uff);
+  dfree(c->d_pos_ret);
+  dfree(c->d_vel_ret);
   dfree(c->d_cdt_ff);
   dfree(c->d_kec);
   dfree(c->d_snap_f);

@@ -137,18 +137,19 @@ __device__ __forceinline__ double back_to_double(unsigned long long u, double l6
   return x >= l ? 0.0 : x;
 }
 
-__global__ void k_check_cache(int n, const double* __restrict__ pos,
-                              const unsigned long long* __restrict__ xfx, BoxConsts b, DevState* st) {
-  const double a0 = b.l64_0, a1 = b.l64_1, a2 = b.l64_2, l0 = b.l0, l1 = b.l1, l2 = b.l2;
-  bool dirty = false;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    dirty |= __double_as_longlong(back_to_double(xfx[3 * i], a0, l0)) != __double_as_longlong(pos[3 * i]);
-    dirty |= __double_as_longlong(back_to_double(xfx[3 * i + 1], a1, l1)) !=
-             __double_as_longlong(pos[3 * i + 1]);
-    dirty |= __double_as_longlong(back_to_double(xfx[3 * i + 2], a2, l2)) !=
-             __double_as_longlong(pos[3 * i + 2]);
+// The caller's positions (and velocities, when vel is not NULL) against the
+// ones the last relres_step returned, word for word: F_DIRTY / F_VDIRTY when
+// any differs.
+__global__ void k_check_io(int n3, const unsigned long long* __restrict__ pos,
+                           const unsigned long long* __restrict__ pos_ret, const unsigned long long* __restrict__ vel,
+                           const unsigned long long* __restrict__ vel_ret, DevState* st) {
+  bool dp = false, dv = false;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n3; k += gridDim.x * blockDim.x) {
+    dp |= pos[k] != pos_ret[k];
+    if (vel != nullptr) dv |= vel[k] != vel_ret[k];
   }
-  if (__syncthreads_or(dirty) && threadIdx.x == 0) atomicOr(&st->flags, F_DIRTY);
+  if (__syncthreads_or(dp) && threadIdx.x == 0) atomicOr(&st->flags, F_DIRTY);
+  if (__syncthreads_or(dv) && threadIdx.x == 0) atomicOr(&st->flags, F_VDIRTY);
 }
 
 // ----------------------------------------------------------------- bonded
@@ -1163,13 +1164,18 @@ __global__ void k_reduce_out(long long* acc, double* energy, int with_e, double*
   for (int q = 0; q < kNAcc; ++q) acc[q] = 0;
 }
 
-__global__ void k_set_ab(DevState* st, double a, double b) {
-  st->a = a;
-  st->b = b;
-  st->a_hi = float(a);
-  st->a_lo = float(a - double(st->a_hi));
-  st->b_hi = float(b);
-  st->b_lo = float(b - double(st->b_hi));
+// Start of a relres_step call: its step and thermo-row counters, and (unless
+// the call continues the velocity state of the last one) the factors of the
+// first drift for velocities read from the caller, u = v: a = b = 1.
+__global__ void k_call_start(DevState* st, int reset_ab) {
+  if (reset_ab) {
+    st->a = 1.0;
+    st->b = 1.0;
+    st->a_hi = 1.f;
+    st->a_lo = 0.f;
+    st->b_hi = 1.f;
+    st->b_lo = 0.f;
+  }
   st->local_step = 0;
   st->thermo_row = 0;
   st->ev = 0;
@@ -1190,7 +1196,8 @@ template <typename R>
 __global__ void k_finish_md(int n, const DevState* st, const VelT<R>* vel_u,
                             const ForceT<R>* __restrict__ f_tot, const int* __restrict__ type,
                             const double* __restrict__ cdt, const unsigned long long* __restrict__ xfx,
-                            BoxConsts b, double* vel_out, double* __restrict__ pos_out) {
+                            BoxConsts b, double* vel_out, double* __restrict__ pos_out,
+                            double* __restrict__ pos_ret, double* __restrict__ vel_ret) {
   const double ca = st->a, cb1 = st->b - 1.0;
   const double a0 = b.l64_0, a1 = b.l64_1, a2 = b.l64_2, l0 = b.l0, l1 = b.l1, l2 = b.l2;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1199,10 +1206,18 @@ __global__ void k_finish_md(int n, const DevState* st, const VelT<R>* vel_u,
     load_force(f_tot, i, f);
     const R c = R(cb1 * cdt[t]);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) vel_out[3 * i + q] = fma(ca, vel_d(vel_u, 3 * i + q), double(c * f[q]));
-    pos_out[3 * i] = back_to_double(xfx[3 * i], a0, l0);
-    pos_out[3 * i + 1] = back_to_double(xfx[3 * i + 1], a1, l1);
-    pos_out[3 * i + 2] = back_to_double(xfx[3 * i + 2], a2, l2);
+    for (int q = 0; q < 3; ++q) {
+      const double v = fma(ca, vel_d(vel_u, 3 * i + q), double(c * f[q]));
+      vel_out[3 * i + q] = v;
+      if (vel_ret) vel_ret[3 * i + q] = v;
+    }
+    const double x[3] = {back_to_double(xfx[3 * i], a0, l0), back_to_double(xfx[3 * i + 1], a1, l1),
+                         back_to_double(xfx[3 * i + 2], a2, l2)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      pos_out[3 * i + q] = x[q];
+      if (pos_ret) pos_ret[3 * i + q] = x[q];
+    }
   }
 }
 
@@ -1276,9 +1291,12 @@ cudaError_t launch_convert(relres_ctx* c, const double* d_pos) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_check_cache(relres_ctx* c, const double* d_pos) {
-  k_check_cache<<<grid_for(c->n), kThreads, 0, c->stream>>>(c->n, d_pos, c->d_xfx, box_consts(c, 0.0),
-                                                            c->d_state);
+cudaError_t launch_check_io(relres_ctx* c, const double* d_pos, const double* d_vel) {
+  const int n3 = 3 * c->n;
+  k_check_io<<<std::max(1, std::min((n3 + kThreads - 1) / kThreads, 152 * 8)), kThreads, 0, c->stream>>>(
+      n3, reinterpret_cast<const unsigned long long*>(d_pos), reinterpret_cast<const unsigned long long*>(c->d_pos_ret),
+      reinterpret_cast<const unsigned long long*>(d_vel), reinterpret_cast<const unsigned long long*>(c->d_vel_ret),
+      c->d_state);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
@@ -1579,9 +1597,8 @@ cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp, int k) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev) {
-  (void)ev;
-  k_set_ab<<<1, 1, 0, c->stream>>>(c->d_state, a, b);
+cudaError_t launch_call_start(relres_ctx* c, bool reset_ab) {
+  k_call_start<<<1, 1, 0, c->stream>>>(c->d_state, reset_ab ? 1 : 0);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
@@ -1666,11 +1683,11 @@ cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, doubl
   if (c->fp64)
     k_finish_md<double><<<grid_for(c->n), kThreads, 0, c->stream>>>(
         c->n, c->d_state, static_cast<const double*>(vel_state(c, d_vel)), static_cast<const double*>(c->d_f_tot),
-        c->d_type, c->d_cdt, c->d_xfx, b, d_vel, d_pos);
+        c->d_type, c->d_cdt, c->d_xfx, b, d_vel, d_pos, c->d_pos_ret, nullptr);
   else
     k_finish_md<float><<<grid_for(c->n), kThreads, 0, c->stream>>>(
         c->n, c->d_state, static_cast<const float2*>(vel_state(c, d_vel)), static_cast<const float4*>(c->d_f_tot),
-        c->d_type, c->d_cdt, c->d_xfx, b, d_vel, d_pos);
+        c->d_type, c->d_cdt, c->d_xfx, b, d_vel, d_pos, c->d_pos_ret, c->d_vel_ret);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }

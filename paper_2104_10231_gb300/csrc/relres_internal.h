@@ -83,6 +83,7 @@ enum : unsigned {
   F_DIRTY = 16u,        // incoming positions differ from the cached state
   F_BADCELL = 32u,      // a computed cell index was out of range (access skipped)
   F_PRUNE = 64u,        // an atom moved more than delta/2 since the last pruning pass
+  F_VDIRTY = 128u,      // incoming velocities differ from the ones returned last
 };
 
 struct DevState {
@@ -289,6 +290,15 @@ struct relres_ctx {
   // and written at its end); the FP64 path keeps u in the caller's array
   float2* d_uff = nullptr;
   bool forces_valid = false;
+  // what the last relres_step returned ([3n] positions, [3n] velocities) and
+  // whether the state is still that call's end state (io_valid; io_dt its
+  // time step): a call given those same arrays continues from that state
+  // (FP32: the velocity state and the thermostat factors too) without
+  // reading the arrays again
+  double* d_pos_ret = nullptr;
+  double* d_vel_ret = nullptr;
+  bool io_valid = false;
+  double io_dt = 0.0;
 
   // bonded-term force slots: bonds 2 per term, then angles 3, then dihedrals 4
   void* d_tf = nullptr;
@@ -384,7 +394,7 @@ namespace relres {
 
 // positions
 cudaError_t launch_convert(relres_ctx* c, const double* d_pos);
-cudaError_t launch_check_cache(relres_ctx* c, const double* d_pos);
+cudaError_t launch_check_io(relres_ctx* c, const double* d_pos, const double* d_vel);
 cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, double dt);
 
 // neighbour lists; gate: device flag word (rebuild only if F_REBUILD set) or null
@@ -429,7 +439,7 @@ cudaError_t launch_drift(relres_ctx* c, const StepParams& sp, double* d_vel, boo
 cudaError_t launch_end_of_step(relres_ctx* c, const StepParams& sp, int k, bool ev, double* d_vel);
 cudaError_t launch_csvr_draws(relres_ctx* c, const StepParams& sp, int count);
 cudaError_t launch_thermo(relres_ctx* c, const StepParams& sp, int k);
-cudaError_t launch_set_ab(relres_ctx* c, double a, double b, int ev);
+cudaError_t launch_call_start(relres_ctx* c, bool reset_ab);
 // FP32 path: caller's velocities -> the float-float state (start of a call)
 cudaError_t launch_vel_in(relres_ctx* c, const double* d_vel);
 // the velocity state of a call: the float-float array (FP32) or the caller's (FP64)
