@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librelres.so")
 SOURCES = ["params.cpp", "neighbor.cu", "pair.cu", "md.cu", "api.cu", "noalloc.cu", "grad.cu", "rates.cu"]
-HEADERS = ["relres_internal.h", "common.cuh", os.path.join("..", "..", "include", "relres.h")]
+HEADERS = ["relres_internal.h", "common.cuh", "fbits.h", os.path.join("..", "..", "include", "relres.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

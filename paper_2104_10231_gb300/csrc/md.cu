@@ -20,6 +20,7 @@
 // reference, never indexed with a run-time index); per-type constants live in
 // small device arrays.
 #include "common.cuh"
+#include "fbits.h"
 
 namespace relres {
 
@@ -132,9 +133,13 @@ __global__ void k_convert(int n, const double* __restrict__ pos, const int* __re
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, F_NONFINITE);
 }
 
+// A 64-bit fixed-point coordinate as a double in [0, L): u L 2^-64, with u
+// converted to the nearest double by integer operations (the bits of
+// __ull2double_rn(u)); a product rounded up to L wraps to 0 (both positive:
+// compared as bit patterns).
 __device__ __forceinline__ double back_to_double(unsigned long long u, double l64, double l) {
-  const double x = from_fixed(u, l64);
-  return x >= l ? 0.0 : x;
+  const double x = double_of_u64(u) * l64;
+  return bits_of_double(x) >= bits_of_double(l) ? 0.0 : x;
 }
 
 // The caller's positions (and velocities, when vel is not NULL) against the
@@ -1195,21 +1200,39 @@ __global__ void k_vel_in(int n3, const double* __restrict__ vel, float2* __restr
 template <typename R>
 __global__ void k_finish_md(int n, const DevState* st, const VelT<R>* vel_u,
                             const ForceT<R>* __restrict__ f_tot, const int* __restrict__ type,
-                            const double* __restrict__ cdt, const unsigned long long* __restrict__ xfx,
-                            BoxConsts b, double* vel_out, double* __restrict__ pos_out,
-                            double* __restrict__ pos_ret, double* __restrict__ vel_ret) {
-  const double ca = st->a, cb1 = st->b - 1.0;
+                            const double* __restrict__ cdt, const float2* __restrict__ cdt_ff,
+                            const unsigned long long* __restrict__ xfx, BoxConsts b, double* vel_out,
+                            double* __restrict__ pos_out, double* __restrict__ pos_ret, double* __restrict__ vel_ret) {
   const double a0 = b.l64_0, a1 = b.l64_1, a2 = b.l64_2, l0 = b.l0, l1 = b.l1, l2 = b.l2;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int t = type[i];
     R f[3];
     load_force(f_tot, i, f);
-    const R c = R(cb1 * cdt[t]);
+    double v[3];
+    if constexpr (std::is_same<R, float>::value) {
+      // v = a u + (b - 1) c F in float-float, returned as the double nearest
+      // to hi + lo: the parts converted exactly with integer operations, one
+      // FP64 addition
+      const ff ca{st->a_hi, st->a_lo};
+      const ff cb1 = ff_add(ff{st->b_hi, st->b_lo}, ff{-1.f, 0.f});
+      const float2 cc = cdt_ff[t];
+      const ff cbc = ff_mul(cb1, ff{cc.x, cc.y});
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float2 u = vel_u[3 * i + q];
+        const ff w = ff_add(ff_mul(ca, ff{u.x, u.y}), ff_mul_f(cbc, f[q]));
+        v[q] = double_of_float(w.hi) + double_of_float(w.lo);
+      }
+    } else {
+      const double ca = st->a, cb1 = st->b - 1.0;
+      const R c = R(cb1 * cdt[t]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[q] = fma(ca, vel_d(vel_u, 3 * i + q), double(c * f[q]));
+    }
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const double v = fma(ca, vel_d(vel_u, 3 * i + q), double(c * f[q]));
-      vel_out[3 * i + q] = v;
-      if (vel_ret) vel_ret[3 * i + q] = v;
+      vel_out[3 * i + q] = v[q];
+      if (vel_ret) vel_ret[3 * i + q] = v[q];
     }
     const double x[3] = {back_to_double(xfx[3 * i], a0, l0), back_to_double(xfx[3 * i + 1], a1, l1),
                          back_to_double(xfx[3 * i + 2], a2, l2)};
@@ -1683,11 +1706,11 @@ cudaError_t launch_write_back(relres_ctx* c, double* d_pos, double* d_vel, doubl
   if (c->fp64)
     k_finish_md<double><<<grid_for(c->n), kThreads, 0, c->stream>>>(
         c->n, c->d_state, static_cast<const double*>(vel_state(c, d_vel)), static_cast<const double*>(c->d_f_tot),
-        c->d_type, c->d_cdt, c->d_xfx, b, d_vel, d_pos, c->d_pos_ret, nullptr);
+        c->d_type, c->d_cdt, c->d_cdt_ff, c->d_xfx, b, d_vel, d_pos, c->d_pos_ret, nullptr);
   else
     k_finish_md<float><<<grid_for(c->n), kThreads, 0, c->stream>>>(
         c->n, c->d_state, static_cast<const float2*>(vel_state(c, d_vel)), static_cast<const float4*>(c->d_f_tot),
-        c->d_type, c->d_cdt, c->d_xfx, b, d_vel, d_pos, c->d_pos_ret, c->d_vel_ret);
+        c->d_type, c->d_cdt, c->d_cdt_ff, c->d_xfx, b, d_vel, d_pos, c->d_pos_ret, c->d_vel_ret);
   RELRES_LAUNCHED(c);
   return cudaGetLastError();
 }
