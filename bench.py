@@ -132,13 +132,16 @@ def recorded_pair_counters(p_prune, n_atoms):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
+    """nvidia-smi clock/throttle samples during the timed region.  A region
+    shorter than the 200 ms sampling period may hold no sample: then the
+    samples on both sides of it (the last before, the first after) stand for
+    it, and the summary says so."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.lines = []
-        self.first = 0
+        self.lines = []  # (time read, csv line)
+        self.t_start = self.t_end = None
 
     def __enter__(self):
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -156,17 +159,23 @@ class ClockSampler:
             t0 = time.perf_counter()
             while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 10.0:
                 time.sleep(0.01)
-            self.first = len(self.lines)  # samples from here on fall in the timed region
         except Exception:
             self.proc = None
+        self.t_start = time.perf_counter()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *exc):
+        self.t_end = time.perf_counter()
         if self.proc:
+            # a region without a sample of its own: wait for the one after it
+            t0 = time.perf_counter()
+            while (not any(self.t_start <= t for t, _ in self.lines) and self.proc.poll() is None
+                   and time.perf_counter() - t0 < 2.0):
+                time.sleep(0.01)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -174,9 +183,17 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        inside = [ln for t, ln in self.lines if self.t_start <= t <= self.t_end]
+        window = "samples inside the timed region"
+        if not inside:
+            before = [ln for t, ln in self.lines if t < self.t_start][-1:]
+            after = [ln for t, ln in self.lines if t > self.t_end][:1]
+            inside = before + after
+            window = ("the samples just before and just after the timed region (shorter than the "
+                      "200 ms sampling period)")
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines[self.first:]:
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -189,7 +206,7 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 _THERMO = {}
