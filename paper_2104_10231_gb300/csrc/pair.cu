@@ -251,6 +251,7 @@ __device__ __forceinline__ float4 cg_radii2(const CgRow& T) {
 }
 
 constexpr int kSmallGridSMs = 152;  // SMs of the part
+constexpr int kFp64SmallTpa = 8;    // FP64 threads per slot of small systems (walk_ordered)
 
 template <typename R>
 struct ListWalk {
@@ -405,9 +406,11 @@ __device__ __forceinline__ R entry(const typename PosOf<R>::T& pi, const typenam
     R fr, ep;
     const bool hit = CG ? cg_term<R, EV>(T, r2, fr, ep) : fg_term<R, EV>(T, r2, fr, ep);
     if (hit) {
-      A.fx += fr * dx;
-      A.fy += fr * dy;
-      A.fz += fr * dz;
+      // one rounding per term (fma): the operation the ordered several-lane
+      // walk repeats (walk_ordered), so both give the same bits
+      A.fx = fma(fr, dx, A.fx);
+      A.fy = fma(fr, dy, A.fy);
+      A.fz = fma(fr, dz, A.fz);
       if (EV) {
         A.e += ep;
         A.w[0] += fr * dx * dx;
@@ -474,6 +477,71 @@ __device__ __forceinline__ int4 fixed_delta(const int4& pi, const int4& pj, int 
 __device__ __forceinline__ int4 ref_of(const int4& p) { return p; }
 __device__ __forceinline__ int4 ref_of(const Pos64& p) {
   return make_int4(int(p.x >> 32), int(p.y >> 32), int(p.z >> 32), int(p.t));
+}
+
+// FP64 force factor of one entry and its coordinate difference (the
+// arithmetic of entry()); zero for a padding entry or a pair past the cutoff.
+template <bool CG>
+__device__ __forceinline__ double term64(const Pos64& pi, const Pos64& pj, bool valid, int row0, const SmemTabs& S,
+                                         const PairLaunch<double>& a, double d[3]) {
+  double dx, dy, dz;
+  delta(pi, pj, a.sx, a.sy, a.sz, dx, dy, dz);
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const PairTab<double>& T = static_cast<const PairTab<double>*>(S.tab)[row0 + ptype(pj)];
+  double fr = 0.0, ep;
+  const bool hit = valid && (CG ? cg_term<double, false>(T, r2, fr, ep) : fg_term<double, false>(T, r2, fr, ep));
+  d[0] = hit ? dx : 0.0;
+  d[1] = hit ? dy : 0.0;
+  d[2] = hit ? dz : 0.0;
+  return hit ? fr : 0.0;
+}
+
+// FP64 forces of small systems (too few slots to occupy the part with one
+// thread each): TPA lanes per slot, and the same bits as one lane.  In each
+// round the TPA lanes of a slot evaluate one chunk each (TPA x 4 consecutive
+// entries); lanes 0, 1 and 2 of the slot then add the x, y and z terms of
+// those entries in list order with the one-lane walk's operation (fma),
+// taking each entry's force factor and difference from the lane that
+// evaluated it.  A padding entry or a pair past the cutoff adds fma(0, 0, f)
+// = f.  Every lane of the warp runs the warp's largest number of rounds (the
+// shuffles take all 32 lanes).
+template <bool CG, int TPA>
+__device__ __forceinline__ void walk_ordered(const ListWalk<double>& L, int blk, const SmemTabs& S,
+                                             const PairLaunch<double>& a) {
+  static_assert(TPA >= 4 && 32 % TPA == 0, "three lanes per slot add the components");
+  const int t = blk * blockDim.x + threadIdx.x;
+  const int s = t / TPA, q = t % TPA;
+  const int base = (threadIdx.x & 31) - q;  // the slot's first lane in the warp
+  const bool own = s < L.nslots;
+  const int ss = own ? s : 0;  // a valid slot for the loads of the other lanes
+  const Pos64 pi = L.pos[ss];
+  const int row0 = ptype(pi) * a.nt;
+  const int m = own ? L.cnt[s] : 0;
+  const int nch = (m + 3) >> 2;
+  const int nround_w = __reduce_max_sync(0xffffffffu, (nch + TPA - 1) / TPA);
+  const int4* nb4 = reinterpret_cast<const int4*>(L.nbr) + ss;
+  double f = 0.0;  // lanes 0, 1, 2 of the slot: its force component q
+  for (int r = 0; r < nround_w; ++r) {
+    const int ch = r * TPA + q;
+    const int rem = ch < nch ? m - 4 * ch : 0;
+    int4 jj = make_int4(ss, ss, ss, ss);
+    if (rem > 0) jj = __ldcs(nb4 + size_t(ch) * L.nslots);
+    const int jv[4] = {rem > 0 ? jj.x : ss, rem > 1 ? jj.y : ss, rem > 2 ? jj.z : ss, rem > 3 ? jj.w : ss};
+    double fr[4], d[4][3];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) fr[e] = term64<CG>(pi, load_pos(L.pos, jv[e]), rem > e, row0, S, a, d[e]);
+    for (int k = 0; k < TPA; ++k) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const double frk = __shfl_sync(0xffffffffu, fr[e], base + k);
+        const double xk = __shfl_sync(0xffffffffu, d[e][0], base + k);
+        const double yk = __shfl_sync(0xffffffffu, d[e][1], base + k);
+        const double zk = __shfl_sync(0xffffffffu, d[e][2], base + k);
+        f = fma(frk, q == 0 ? xk : (q == 1 ? yk : zk), f);
+      }
+    }
+  }
+  if (own && q < 3) L.f_out[3 * size_t(L.perm[s]) + q] = f;
 }
 
 // One slot's walk over its list, four entries per iteration.  TPA lanes share
@@ -711,19 +779,27 @@ __device__ __forceinline__ void pair_block(const PairLaunch<R>& a, int bid) {
   __syncthreads();
   const bool cg = bid < a.nblk_cg;
   const int blk = cg ? bid : bid - a.nblk_cg;
-  if constexpr (TPA == 1) {
-    if (a.prune_on && (*(volatile const unsigned*)a.gate & (F_REBUILD | F_PRUNE)) != 0u) {
-      if (cg)
-        walk<R, true, EV, 1, true, ACC>(a.cg, blk, S, a, bid == 0);
-      else
-        walk<R, false, EV, 1, true, ACC>(a.fg, blk, S, a, bid == 0);
-      return;
+  if constexpr (!std::is_same<R, float>::value && TPA > 1) {
+    static_assert(!EV, "FP64 energy steps use one thread per slot");
+    if (cg)
+      walk_ordered<true, TPA>(a.cg, blk, S, a);
+    else
+      walk_ordered<false, TPA>(a.fg, blk, S, a);
+  } else {
+    if constexpr (TPA == 1) {
+      if (a.prune_on && (*(volatile const unsigned*)a.gate & (F_REBUILD | F_PRUNE)) != 0u) {
+        if (cg)
+          walk<R, true, EV, 1, true, ACC>(a.cg, blk, S, a, bid == 0);
+        else
+          walk<R, false, EV, 1, true, ACC>(a.fg, blk, S, a, bid == 0);
+        return;
+      }
     }
+    if (cg)
+      walk<R, true, EV, TPA, false, ACC>(a.cg, blk, S, a, bid == 0);
+    else
+      walk<R, false, EV, TPA, false, ACC>(a.fg, blk, S, a, bid == 0);
   }
-  if (cg)
-    walk<R, true, EV, TPA, false, ACC>(a.cg, blk, S, a, bid == 0);
-  else
-    walk<R, false, EV, TPA, false, ACC>(a.fg, blk, S, a, bid == 0);
 }
 
 template <typename R, bool EV, int TPA, int BS, int ACC>
@@ -783,8 +859,18 @@ static cudaError_t launch_pairs_f32(relres_ctx* c, const PairLaunch<float>& a, b
 
 // Arguments of one system's pair launch with `per` slots per block; returns
 // the number of blocks (0: nothing to do).
+// FP64 threads per slot: several (walk_ordered) for systems whose slots fill
+// fewer than four warps per SM with one thread each, else one
+static int fp64_tpa(const relres_ctx* c) {
+  const long long slots = (long long)c->n + ((c->has_cg && c->n_h > 0) ? c->n_h : 0);
+  return slots < 4LL * 32 * kSmallGridSMs ? kFp64SmallTpa : 1;
+}
+
+// prune_in_kernel: a launch with one thread per slot prunes as it walks (else
+// the lists were pruned beforehand by k_prune, or pruning is off)
 template <typename R>
-static int make_pair_launch(const relres_ctx* c, int which, int tpa, int per, PairLaunch<R>* out) {
+static int make_pair_launch(const relres_ctx* c, int which, int tpa, int per, bool prune_in_kernel,
+                            PairLaunch<R>* out) {
   const double unit = std::is_same<R, float>::value ? 4294967296.0 : 18446744073709551616.0;
   PairLaunch<R> a{};
   a.sx = R(c->box[0] / unit);
@@ -825,7 +911,7 @@ static int make_pair_launch(const relres_ctx* c, int which, int tpa, int per, Pa
   } else {
     a.cg = a.fg;
   }
-  a.prune_on = (c->prune_on && tpa == 1) ? 1 : 0;
+  a.prune_on = (prune_in_kernel && tpa == 1) ? 1 : 0;
   const int nb_fg = do_fg ? (c->n + per - 1) / per : 0;
   const int nb_cg = do_cg ? (c->n_h + per - 1) / per : 0;
   a.nblk_cg = nb_cg;
@@ -845,17 +931,21 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
     bs = kPairConfigs[c->pair_cfg].bs;
   }
   // FP64 runs at under 2 FMA per clock per SM on this part: a system with
-  // fewer 256-slot blocks than SMs spreads its slots over more SMs in 32-slot
-  // blocks (one thread per slot either way, so the forces are the same bits)
+  // fewer 256-slot blocks than SMs spreads its slots over more SMs in 32-thread
+  // blocks, and a smaller one its forces-only walks over several threads per
+  // slot (walk_ordered: the same bits as one thread)
   const bool fp64_small = !std::is_same<R, float>::value && (c->n + kThreads - 1) / kThreads < kSmallGridSMs;
   if (fp64_small) bs = 32;
+  if (!std::is_same<R, float>::value && !ev) tpa = fp64_tpa(c);
   PairLaunch<R> a;
-  const int grid = make_pair_launch<R>(c, which, tpa, bs / tpa, &a);
+  const int grid = make_pair_launch<R>(c, which, tpa, bs / tpa, pairs_prune(c), &a);
   if (grid == 0) return cudaSuccess;
   if constexpr (!std::is_same<R, float>::value) {
     if (fp64_small) {
       if (ev)
         k_pair<R, true, 1, 32, 0><<<grid, 32, smem, c->stream>>>(a);
+      else if (tpa == kFp64SmallTpa)
+        k_pair<R, false, kFp64SmallTpa, 32, 0><<<grid, 32, smem, c->stream>>>(a);
       else
         k_pair<R, false, 1, 32, 0><<<grid, 32, smem, c->stream>>>(a);
     } else if (ev) {
@@ -887,7 +977,7 @@ static cudaError_t prepare_pairs_batch_t(const std::vector<relres_ctx*>& cs, Bat
   std::vector<int> off(cs.size() + 1, 0);
   int nt_max = 1;
   for (size_t r = 0; r < cs.size(); ++r) {
-    off[r + 1] = off[r] + make_pair_launch<R>(cs[r], 3, 1, kThreads, &args[r]);
+    off[r + 1] = off[r] + make_pair_launch<R>(cs[r], 3, 1, kThreads, cs[r]->prune_on, &args[r]);
     nt_max = std::max(nt_max, cs[r]->n_types);
   }
   b->nblk = off.back();
@@ -928,7 +1018,7 @@ cudaError_t launch_pairs_batch(cudaStream_t s, bool fp64, int acc, bool ev, cons
 }
 
 bool pairs_prune(const relres_ctx* c) {
-  return c->prune_on && (c->fp64 || kPairConfigs[c->pair_cfg].tpa == 1);
+  return c->prune_on && (c->fp64 ? fp64_tpa(c) == 1 : kPairConfigs[c->pair_cfg].tpa == 1);
 }
 
 cudaError_t launch_pairs(relres_ctx* c, bool ev, int which) {
