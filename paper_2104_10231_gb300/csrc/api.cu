@@ -1830,8 +1830,8 @@ relres_status relres_get_stats(relres_ctx* c, relres_stats* o) {
   std::memset(o, 0, sizeof(*o));
   o->n_atoms = c->n;
   o->n_hybrid = c->n_h;
-  o->pair_tpa = kPairConfigs[c->pair_cfg].tpa;
-  o->pair_block = kPairConfigs[c->pair_cfg].bs;
+  o->pair_tpa = c->fp64 ? fp64_pair_tpa(c) : kPairConfigs[c->pair_cfg].tpa;
+  o->pair_block = c->fp64 ? fp64_pair_block(c) : kPairConfigs[c->pair_cfg].bs;
   o->cap_fg = c->cap_fg;
   o->cap_cg = c->cap_cg;
   o->max_fg = c->h_state->max_fg;

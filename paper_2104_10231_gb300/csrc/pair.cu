@@ -250,8 +250,6 @@ __device__ __forceinline__ float4 cg_radii2(const CgRow& T) {
   return make_float4(T.a.z * T.a.z, T.a.x, T.a.w * T.a.w, T.a.y);
 }
 
-constexpr int kSmallGridSMs = 152;  // SMs of the part
-constexpr int kFp64SmallTpa = 8;    // FP64 threads per slot of small systems (walk_ordered)
 
 template <typename R>
 struct ListWalk {
@@ -859,13 +857,6 @@ static cudaError_t launch_pairs_f32(relres_ctx* c, const PairLaunch<float>& a, b
 
 // Arguments of one system's pair launch with `per` slots per block; returns
 // the number of blocks (0: nothing to do).
-// FP64 threads per slot: several (walk_ordered) for systems whose slots fill
-// fewer than four warps per SM with one thread each, else one
-static int fp64_tpa(const relres_ctx* c) {
-  const long long slots = (long long)c->n + ((c->has_cg && c->n_h > 0) ? c->n_h : 0);
-  return slots < 4LL * 32 * kSmallGridSMs ? kFp64SmallTpa : 1;
-}
-
 // prune_in_kernel: a launch with one thread per slot prunes as it walks (else
 // the lists were pruned beforehand by k_prune, or pruning is off)
 template <typename R>
@@ -934,9 +925,9 @@ static cudaError_t launch_pairs_t(relres_ctx* c, bool ev, int which) {
   // fewer 256-slot blocks than SMs spreads its slots over more SMs in 32-thread
   // blocks, and a smaller one its forces-only walks over several threads per
   // slot (walk_ordered: the same bits as one thread)
-  const bool fp64_small = !std::is_same<R, float>::value && (c->n + kThreads - 1) / kThreads < kSmallGridSMs;
+  const bool fp64_small = !std::is_same<R, float>::value && fp64_pair_block(c) == 32;
   if (fp64_small) bs = 32;
-  if (!std::is_same<R, float>::value && !ev) tpa = fp64_tpa(c);
+  if (!std::is_same<R, float>::value && !ev) tpa = fp64_pair_tpa(c);
   PairLaunch<R> a;
   const int grid = make_pair_launch<R>(c, which, tpa, bs / tpa, pairs_prune(c), &a);
   if (grid == 0) return cudaSuccess;
@@ -1018,7 +1009,7 @@ cudaError_t launch_pairs_batch(cudaStream_t s, bool fp64, int acc, bool ev, cons
 }
 
 bool pairs_prune(const relres_ctx* c) {
-  return c->prune_on && (c->fp64 ? fp64_tpa(c) == 1 : kPairConfigs[c->pair_cfg].tpa == 1);
+  return c->prune_on && (c->fp64 ? fp64_pair_tpa(c) == 1 : kPairConfigs[c->pair_cfg].tpa == 1);
 }
 
 cudaError_t launch_pairs(relres_ctx* c, bool ev, int which) {

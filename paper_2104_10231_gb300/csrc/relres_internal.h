@@ -494,6 +494,17 @@ constexpr long long kRebuildKernels = 7;
 // MD steps take the segmented drift + bonded kernel and k_sum
 inline bool step_segments(const relres_ctx* c) { return c->seg_ok && c->use_seg; }
 
+// FP64 forces-only pair launches: 32-thread blocks for a system with fewer
+// 256-slot blocks than SMs, else 256; eight threads per slot (walk_ordered)
+// for one whose slots fill fewer than four warps per SM with one thread each
+constexpr int kPartSMs = 152;
+constexpr int kFp64SmallTpa = 8;
+inline int fp64_pair_block(const relres_ctx* c) { return (c->n + 255) / 256 < kPartSMs ? 32 : 256; }
+inline int fp64_pair_tpa(const relres_ctx* c) {
+  const long long slots = (long long)c->n + ((c->has_cg && c->n_h > 0) ? c->n_h : 0);
+  return slots < 4LL * 32 * kPartSMs ? kFp64SmallTpa : 1;
+}
+
 // the lists the pair kernels walk: the pruned ones when pruning is on
 inline const int* walk_nbr_fg(const relres_ctx* c) { return c->prune_on ? c->d_nbr_fg_in : c->d_nbr_fg; }
 inline const int* walk_cnt_fg(const relres_ctx* c) { return c->prune_on ? c->d_cnt_fg_in : c->d_cnt_fg; }

@@ -303,6 +303,28 @@ def test_every_pair_launch_configuration_matches_oracle(torch):
 
 
 @pytest.mark.parametrize("prune", [0.5, 0.0])
+def test_fp64_several_threads_per_slot_keep_the_bits(torch, prune):
+    # small FP64 systems walk each slot with eight threads in forces-only
+    # launches; energy launches use one: the forces must be the same bits
+    s = S.propane()
+    ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP64), R.topology_for(s))
+    ctx.set_prune(prune)
+    p = _dev(torch, s.pos)
+    ctx.build_neighbors(p, s.box)
+    assert ctx.stats()["pair_tpa"] == 8 and ctx.stats()["pair_block"] == 32
+    f8 = torch.empty_like(p)
+    f1 = torch.empty_like(p)
+    e = torch.zeros(4, dtype=torch.float64, device="cuda")
+    ctx.compute(p, f8)
+    ctx.compute(p, f1, e)
+    torch.cuda.synchronize()
+    assert np.array_equal(f8.cpu().numpy(), f1.cpu().numpy())
+    fr, _, _, _ = oracle_compute(s)
+    assert force_err(f8.cpu().numpy(), fr) <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("prune", [0.5, 0.0])
 def test_autotuner_picks_a_configuration(torch, prune):
     s = S.neopentane(n_mol=5000, seed=2)  # 25 000 atoms: above the tuning threshold
     ctx = R.Context(R.params_for(s, R.RELRES_PREC_FP32), R.topology_for(s))
