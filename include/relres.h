@@ -584,7 +584,7 @@ relres_status relres_get_timings(relres_ctx* ctx, double* ms, long long* counts,
  * GPU race on it and must be serialised by the caller.  Each call rewrites
  * every part of it that it reads and clears its bad-type flag first.  The
  * first call on each device (with that device current) looks up the array's
- * address; that first call should come before any stream capture.
+ * address.
  * Atom types are read on the device only: a type outside [0, n_types) is
  * never used to index the parameter table; that atom's forces and the
  * energy and virial of the call are written as NaN instead.  O(n_atoms^2)

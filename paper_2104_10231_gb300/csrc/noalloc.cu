@@ -24,8 +24,7 @@
 // array, and the reduction then writes NaN energy and virial.
 //
 // Set-up: the first call on each device (with that device current) looks up
-// the array's device address with cudaGetSymbolAddress.  That first call
-// should come before any stream capture.
+// the array's device address with cudaGetSymbolAddress.
 #include <atomic>
 #include <cmath>
 #include <cstring>
